@@ -1,0 +1,121 @@
+"""Seeded synthetic inputs shared by the CUDA path and the CPU oracle.
+
+This module holds workload descriptions (plain numbers) and the seeded
+initial particle load.  It contains none of the method's arithmetic: the
+derived quantities (neutral density, macro weight, collision majorant,
+fields) are computed separately by the library and by the oracle.
+
+Workloads follow the paper's problem statement (arXiv 2206.14662, Sec. II.A
+and II.B): a coaxial gap with the inner electrode biased, an applied
+magnetic field, a uniform neutral gas at rest, and a volumetric seed load of
+electrons, uniform in space with a Maxwellian velocity distribution (Sec.
+II.A; n0 = 1e15 m^-3 and T0 = 1 eV, Sec. III.A).  The paper's own geometry
+(an elliptic bump on the outer electrode) and its LXCat neon cross-sections
+are replaced by straight coaxial walls and analytic cross-section fits.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Field names and order of the C struct pic_config (include/pic.h).
+_BASE = dict(
+    r_in=1.0e-3, r_out=10.0e-3, z_min=-20.0e-3, z_max=20.0e-3,
+    nr=32, nz=64,
+    v_inner=-10.0e3, v_outer=0.0,
+    bfield_kind=0, b0=0.2,
+    p_mbar=1.0e-4, t_gas_K=300.0,
+    sigma_el=1.0e-19,
+    ion_E_th_eV=15.0, ion_sigma_pk=1.0e-20, ion_E_pk_eV=100.0,
+    opal_B_eV=10.0, xi_param=0.0,
+    elastic_recoil=1, gas_mass_amu=20.1797,
+    n_init=10_000, n0=1.0e15, T0_eV=1.0,
+    weight=0.0,
+    dt=1.0e-12, sort_every=20,
+    poisson_rtol=1.0e-8, poisson_maxit=4,
+    capacity=0,
+    seed=1,
+    precision=32,
+    nu_max=0.0,
+)
+
+#: The synthetic workloads.  ``steps`` is the length of the run the workload
+#: describes; the benchmark times a window of it.
+WORKLOADS = {
+    # plain FP64 method, small: 32x64 cells, uniform Bz = 0.2 T, -10 kV
+    "coax_32x64_1e4": dict(_BASE, steps=500, precision=64),
+    # single run: 128x512 cells, mirror B0 = 0.3 T, -20 kV, 1e-5 mbar, 1e7
+    # macro-electrons, cell sort every 20 steps
+    "mirror_128x512_1e7": dict(
+        _BASE, nr=128, nz=512, bfield_kind=1, b0=0.3, v_inner=-20.0e3,
+        p_mbar=1.0e-5, n_init=10_000_000, steps=20_000, precision=32),
+    # large single run: 256x1024 cells, mirror B0 = 0.5 T, -30 kV, 1e-6 mbar,
+    # 2e8 macro-electrons with room for 3e8
+    "mirror_256x1024_2e8": dict(
+        _BASE, nr=256, nz=1024, bfield_kind=1, b0=0.5, v_inner=-30.0e3,
+        p_mbar=1.0e-6, n_init=200_000_000, capacity=300_000_000,
+        steps=50_000, precision=32),
+}
+
+
+def workload(name: str, **overrides) -> dict:
+    """A copy of a named workload with fields overridden."""
+    cfg = dict(WORKLOADS[name])
+    cfg.update(overrides)
+    return cfg
+
+
+ELECTRON_MASS = 9.1093837015e-31   # kg, CODATA 2018 (input recipe only)
+ELEMENTARY_CHARGE = 1.602176634e-19  # C
+
+
+def seed_particles(cfg: dict, n: int | None = None, seed: int | None = None,
+                   margin_cells: float = 0.0):
+    """Initial macro-electrons: r with density uniform in volume between the
+    walls (r = sqrt(a^2 + u (b^2 - a^2))), z uniform, each velocity component
+    normal with variance k T0 / m_e.  Returns float64 arrays
+    (r, z, vr, vtheta, vz) and uint64 uids 0..n-1.
+
+    ``margin_cells`` keeps the load that many cells away from every wall.
+    The generator is numpy's PCG64 seeded with ``seed`` (default cfg['seed']).
+    """
+    n = int(cfg["n_init"] if n is None else n)
+    rng = np.random.Generator(np.random.PCG64(cfg["seed"] if seed is None else seed))
+    a, b = cfg["r_in"], cfg["r_out"]
+    z0, z1 = cfg["z_min"], cfg["z_max"]
+    hr = (b - a) / cfg["nr"]
+    hz = (z1 - z0) / cfg["nz"]
+    a_ = a + margin_cells * hr
+    b_ = b - margin_cells * hr
+    u = rng.random(n)
+    r = np.sqrt(a_ * a_ + u * (b_ * b_ - a_ * a_))
+    z = (z0 + margin_cells * hz) + rng.random(n) * ((z1 - z0) - 2 * margin_cells * hz)
+    # keep strictly inside the open domain
+    r = np.clip(r, np.nextafter(a, b), np.nextafter(b, a))
+    z = np.clip(z, np.nextafter(z0, z1), np.nextafter(z1, z0))
+    vth = np.sqrt(cfg["T0_eV"] * ELEMENTARY_CHARGE / ELECTRON_MASS)
+    v = rng.standard_normal((3, n)) * vth
+    uid = np.arange(n, dtype=np.uint64)
+    return r, z, v[0].copy(), v[1].copy(), v[2].copy(), uid
+
+
+def uniform_field_node_arrays(cfg: dict, er_value: float, ez_value: float = 0.0):
+    """Constant node fields (E_r, E_z) for tests that inject E."""
+    shape = ((cfg["nr"] + 1) * (cfg["nz"] + 1),)
+    return np.full(shape, er_value), np.full(shape, ez_value)
+
+
+def random_field_node_arrays(cfg: dict, scale: float, seed: int = 7):
+    """Smooth random node fields for parity tests that inject E: a sum of a
+    few low-order sinusoids with random amplitudes of size ``scale``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nr, nz = cfg["nr"], cfg["nz"]
+    x = np.linspace(0.0, 1.0, nr + 1)[:, None]
+    y = np.linspace(0.0, 1.0, nz + 1)[None, :]
+    er = np.zeros((nr + 1, nz + 1))
+    ez = np.zeros((nr + 1, nz + 1))
+    for _ in range(4):
+        kx, ky = rng.integers(1, 4, size=2)
+        ph = rng.random(2) * 2 * np.pi
+        er += scale * rng.standard_normal() * np.sin(np.pi * kx * x + ph[0]) * np.cos(np.pi * ky * y + ph[1])
+        ez += 0.3 * scale * rng.standard_normal() * np.cos(np.pi * kx * x + ph[1]) * np.sin(np.pi * ky * y + ph[0])
+    return er.ravel(), ez.ravel()
