@@ -1,0 +1,303 @@
+"""Throughput of the PIC step (gather + push + MCC + deposit + field solve)
+on the synthetic workload "mirror_128x512_1e7": 128 x 512 cells, 1e7
+macro-electrons (FP32 particle path, FP64 field), mirror field B0 = 0.3 T,
+-20 kV coaxial bias, 1e-5 mbar, cell sort every 20 steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is particle-steps/s with the particles
+resident in HBM; ``e2e`` is the same metric through the C ABI from host
+buffers (load from pinned host memory, K steps, diagnostics with the
+density grid back to the host, all inside the timed region).  The
+particle store (1e7 x 28 B read + 24 B written per step) exceeds the 129 MB
+L2, so no flush is needed between steps.  ``--impl reference`` times the
+CPU oracle on a bounded sample of the same workload.  Under torchrun each
+rank runs an independent replica (weak scaling, no collective on the data
+path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2206_14662_gb300.inputs import seed_particles, workload  # noqa: E402
+
+WORKLOAD = "mirror_128x512_1e7"
+METRIC = "particle-steps/s (gather+push+MCC+deposit+field solve)"
+# algorithmic bytes per particle-step of the fused particle kernel (FP32):
+# read cell 4 + offsets 8 + velocity 12 + uid 4, write cell + offsets +
+# velocity 24
+BYTES_PER_PARTICLE_STEP = 52
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "particle_step_traffic.json")) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2206_14662_gb300", "csrc", "particle_step.cu"), "rb").read()
+        if rec.get("source_sha256") == hashlib.sha256(src).hexdigest():
+            return rec
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        dev = os.environ.get("LOCAL_RANK", "0")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", dev,
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0])); mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, ws, rank):
+    import torch
+    from paper_2206_14662_gb300._capi import Simulation
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg = workload(WORKLOAD, seed=1 + rank)
+    parts = seed_particles(cfg)
+    n0 = len(parts[0])
+    pinned = [torch.from_numpy(a).pin_memory() for a in parts[:5]]
+    pinned.append(torch.from_numpy(parts[5].view(np.int64)).pin_memory())
+
+    sim = Simulation(cfg)
+    sim.load_particles(*pinned)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks()
+    d0 = sim.diagnostics()
+    clocks.start()
+    torch.cuda.synchronize()
+    sim.profile_start()
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = sim.profile_stop()
+    clk = clocks.stop()
+    d1 = sim.diagnostics()
+    ms = ev0.elapsed_time(ev1)
+    units = d1["n_pushed"] - d0["n_pushed"]
+
+    # end to end through the C ABI from host buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.load_particles(*pinned)
+    sim.step(args.steps)
+    de = sim.diagnostics(density=True)
+    t1 = time.perf_counter()
+    e2e_units = de["n_pushed"]
+    sim.close()
+
+    if ws > 1:
+        t = torch.tensor([ms / 1e3, units, t1 - t0, e2e_units], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[0:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(mx[2:3], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(mx[1:2])
+        torch.distributed.all_reduce(mx[3:4])
+        sec, units, esec, e2e_units = mx.tolist()
+    else:
+        sec, esec = ms / 1e3, t1 - t0
+
+    if rank != 0:
+        return None
+    value = units / sec
+    peak, src = _peak_hbm()
+    kern_ms = prof["particle_ms"] / max(1, prof["particle_launches"])
+    per_launch_units = units / ws / max(1, prof["particle_launches"])
+    achieved = BYTES_PER_PARTICLE_STEP * per_launch_units / (kern_ms * 1e-3) / 1e9
+    traffic = _traffic_record()
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "particle-steps/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": sec * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 particles / f64 field",
+        "data": "synthetic (seeded volume-uniform 1 eV Maxwellian load)",
+        "config": {"workload": WORKLOAD, "particles": n0, "grid": "128x512", "sort_every": 20,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (particle store 520 MB per step)"},
+        "e2e": {"value": e2e_units * ws / esec, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": int(n0 * 48 / args.steps),
+                "d2h_bytes_per_step": int(((cfg["nr"] + 1) * (cfg["nz"] + 1) * 8 + 512) / args.steps)},
+        "gpu_launches": int(prof["kernels_launched"]),
+        "roofline": {"bound": "hbm", "kernel": "k_particle_step<float>", "achieved": achieved,
+                     "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": (traffic["dram_bytes_per_particle"] * per_launch_units) if traffic else None,
+                     "kernel_ms_per_launch": kern_ms,
+                     "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
+        "stage_ms_per_step": {"particle": prof["particle_ms"] / args.steps,
+                              "finalize": prof["finalize_ms"] / args.steps,
+                              "field": prof["field_ms"] / args.steps,
+                              "sort": prof["sort_ms"] / args.steps},
+        "clocks": clk,
+    }
+    if args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, parts)
+    return out
+
+
+def cpu_baseline(cfg, parts, n_sample=None, steps=2):
+    """The oracle as it stands (single thread) on a bounded sample: the full
+    1e7-particle load and field, ``steps`` steps."""
+    import oracle
+    oracle.build()
+    sel = slice(None) if n_sample is None else slice(0, n_sample)
+    o = oracle.OracleSim(cfg, *[a[sel] for a in parts])
+    t0 = time.perf_counter()
+    units = 0
+    for _ in range(steps):
+        units += o.n
+        o.step()
+    sec = time.perf_counter() - t0
+    return {"value": units / sec, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of {len(parts[0][sel])} particles of {WORKLOAD} "
+                      "(full grid, field solve included)", "seconds": sec}
+
+
+def run_reference(args, ws, rank):
+    """The CPU oracle on a bounded sample of the workload: each step is one
+    oracle step of 20 000 particles drawn from it, with the full grid and
+    field solve."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    cfg = workload(WORKLOAD)
+    n = 20_000
+    parts = seed_particles(cfg, n=n)
+    o = oracle.OracleSim(cfg, *parts)
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    units = 0
+    for _ in range(args.steps):
+        units += o.n
+        o.step()
+    sec = time.perf_counter() - t0
+    v = units / sec
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles": n, "grid": "128x512",
+                       "parallelism": "cpu oracle, rank 0 only"},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} particles of {WORKLOAD} per step, full grid and field solve"},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    ws, rank = _dist()
+    if ws > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.init_process_group("nccl")
+        args.cpu_baseline = args.cpu_baseline and rank == 0 and False
+    out = run_ours(args, ws, rank) if args.impl == "ours" else run_reference(args, ws, rank)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if ws > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * pic.h -- C ABI of libpic, a GB300 (sm_103a) implementation of one time
+ * step of the axisymmetric (r,z) 2D3V electrostatic particle-in-cell method
+ * with Monte-Carlo electron-neutral collisions of Le Bars et al.,
+ * arXiv 2206.14662, Sec. II.A ("Numerical model"):
+ *
+ *   gather E at each macro-electron -> Boris push in cylindrical form ->
+ *   perfectly absorbing walls -> null-collision elastic and ionisation
+ *   collisions with a uniform neutral gas at rest -> charge deposit onto the
+ *   (r,z) grid -> finite-element Poisson solve with Dirichlet metal walls and
+ *   Neumann open ends -> node field E = -grad phi.
+ *
+ * Conventions for every call:
+ *   - Units are SI.  Host arrays are FP64 unless stated; node arrays have
+ *     (nr + 1) * (nz + 1) entries, node (i, j) at i * (nz + 1) + j, i along r
+ *     (r_i = r_in + i h_r) and j along z (z_j = z_min + j h_z).
+ *   - Return value: PIC_OK (0) or a negative PIC_E* code; pic_strerror()
+ *     names it.  Errors found on the device (capacity, non-finite values,
+ *     unconverged field solve) are sticky: they are latched in device memory
+ *     and reported by the next synchronising call (pic_diagnostics,
+ *     pic_export_particles, pic_get_grid); pic_step then returns the same
+ *     code until particles are loaded again.
+ *   - Ownership: the handle owns its device memory; the caller owns every
+ *     host array it passes and the CUDA stream.  All device work is queued
+ *     on that stream.  pic_step never synchronises; the calls that move data
+ *     to or from the host (load, export, diagnostics, grids, field, solve,
+ *     checkpoint, restore, profile stop) do.
+ *   - Calls on one handle are not thread-safe.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PIC_OK = 0,
+  PIC_EINVAL = -1,      /* bad argument or configuration */
+  PIC_ENOMEM = -2,      /* device or host allocation failed */
+  PIC_ECAPACITY = -3,   /* particle or spawn capacity exceeded */
+  PIC_ENOCONV = -4,     /* field solve above poisson_rtol after poisson_maxit */
+  PIC_ETIMEOUT = -5,    /* a bounded device wait ran out */
+  PIC_ENONFINITE = -6,  /* a non-finite particle value was loaded or produced */
+  PIC_ECUDA = -7        /* a CUDA runtime call failed */
+};
+
+/* Problem statement (Sec. II.A and II.B): geometry and electrode bias, the
+ * applied magnetic field, the neutral gas (species mass, pressure and
+ * temperature, uniform and constant), the seed load (n0, T0 of Sec. III.A),
+ * the time step and the collision model parameters. */
+typedef struct pic_config {
+  double r_in, r_out;      /* inner / outer electrode radius a < b, m */
+  double z_min, z_max;     /* open (Neumann) ends of the gap, m */
+  int32_t nr, nz;          /* cells along r and z (nz >= 2, nr >= 2) */
+  double v_inner, v_outer; /* Dirichlet potentials of the two walls, V */
+  int32_t bfield_kind;     /* 0: uniform Bz = b0; 1: mirror
+                              Bz = b0 (1 + 0.5 (2 zeta / L)^2),
+                              Br = -2 b0 r zeta / L^2, zeta = z - z_mid */
+  double b0;               /* T */
+  double p_mbar, t_gas_K;  /* neutral density p / (k T) */
+  double sigma_el;         /* elastic cross-section, constant, m^2 */
+  double ion_E_th_eV;      /* ionisation threshold = binding energy, eV */
+  double ion_sigma_pk;     /* peak ionisation cross-section, m^2 */
+  double ion_E_pk_eV;      /* energy of the peak, eV; the fit is
+                              sigma_pk 2 s / (1 + s^2),
+                              s = (E - E_th) / (E_pk - E_th) */
+  double opal_B_eV;        /* width of the secondary-energy law, eV */
+  double xi_param;         /* angle-law anisotropy in [0, 1), 0 isotropic */
+  int32_t elastic_recoil;  /* 1: elastic loss E (2 m_e / M)(1 - cos chi) */
+  double gas_mass_amu;     /* neutral mass M, u */
+  int64_t n_init;          /* macro-electrons of the seed load */
+  double n0;               /* seed density, m^-3 (macro weight source) */
+  double T0_eV;            /* seed temperature (informational), eV */
+  double weight;           /* electrons per macro-electron; 0 derives
+                              n0 pi (b^2 - a^2) L / n_init */
+  double dt;               /* s */
+  int32_t sort_every;      /* counting sort by cell every this many steps;
+                              0 never */
+  double poisson_rtol;     /* ||b - A phi|| / ||b_lifted|| bound */
+  int32_t poisson_maxit;   /* refinement sweeps of the field solve */
+  int64_t capacity;        /* particle slots; 0 derives 1.25 n_init + 4096 */
+  uint64_t seed;           /* Philox key */
+  int32_t precision;       /* particle path: 32 (FP32) or 64 (FP64) */
+  double nu_max;           /* collision majorant, s^-1; 0 derives
+                              (1 + 1e-6) max_E n (sigma_el + sigma_io(E)) v
+                              over E = E_cap k / 1e5, k = 0..1e5,
+                              E_cap = 2 |v_inner - v_outer| eV */
+  int32_t fixed_efield;    /* 1: skip the field solve; E stays as set by
+                              pic_set_efield (particle-only stepping) */
+} pic_config;
+
+/* Diagnostics of one simulation (Sec. III.A: peak density and boundary
+ * currents; the energy ledger and event counts are this library's). */
+typedef struct pic_diag {
+  int64_t step;                  /* steps taken */
+  double t;                      /* step * dt, s */
+  int64_t n_particles;           /* live macro-electrons */
+  double I_inner, I_outer;       /* electron current into each wall, A,      */
+  double I_zmin, I_zmax;         /*   averaged since the previous call       */
+  double absorbed_weight[4];     /* cumulative electrons absorbed per wall:
+                                    inner, outer, z_min, z_max */
+  int64_t n_elastic, n_ionise, n_absorbed, n_candidates, n_over;
+  int64_t n_pushed;              /* cumulative particle-steps (live
+                                    particles advanced, summed over steps) */
+  double ke_total_J;             /* kinetic energy of the live particles */
+  double work_E_J;               /* cumulative work of E on the particles */
+  double ke_absorbed_J;          /* cumulative kinetic energy into walls */
+  double ion_loss_J;             /* cumulative binding energy removed */
+  double recoil_loss_J;          /* cumulative elastic recoil loss */
+  double ke_initial_J;           /* kinetic energy after the load */
+  double ledger_residual_J;      /* ke_total - ke_initial - (work_E -
+                                    ke_absorbed - ion_loss - recoil_loss) */
+  double n_peak;                 /* largest node density, m^-3 */
+  int32_t poisson_iters;         /* sweeps of the last field solve */
+  double poisson_relres;         /* its relative residual */
+  double nu_max;                 /* collision majorant in use, s^-1 */
+  double weight;                 /* macro weight in use */
+  int32_t error;                 /* sticky error code (0 none) */
+} pic_diag;
+
+typedef struct pic_handle pic_handle;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns a device pointer of at least `bytes` bytes, 256-byte
+ * aligned, usable on `stream`, or NULL; free releases it. */
+typedef struct pic_allocator {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} pic_allocator;
+
+/* Create a simulation (Sec. II.A: the PIC cycle; Sec. II.B: geometry and
+ * numerical parameters).  Validates cfg, derives the neutral density, the
+ * macro weight and the collision majorant in FP64 on the host, builds the
+ * field-solver tables and allocates all device memory (through `alloc`, or
+ * cudaMalloc when alloc is NULL).  n_sims must be 1.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  No particles are loaded.
+ * Returns PIC_EINVAL for an invalid configuration, PIC_ENOMEM, PIC_ECUDA. */
+int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
+             const pic_allocator* alloc, pic_handle** out);
+
+/* Load n macro-electrons from host FP64 arrays (structure of arrays):
+ * positions r, z (strictly inside the gap), velocity components vr, vtheta,
+ * vz (the velocity at half step -1/2 of the leapfrog) and unique uids
+ * (< 2^32).  Replaces any loaded particles, resets the step counter, the
+ * tallies and the uid counter (max uid + 1), deposits the charge and, unless
+ * fixed_efield, solves the field (Sec. II.A seed load and first field).
+ * Synchronises (page-locked host arrays make the copies faster).
+ * PIC_EINVAL for out-of-domain or non-finite values, uids at or above 2^32,
+ * or n > capacity. */
+int pic_load_particles(pic_handle* h, int sim, const double* r,
+                       const double* z, const double* vr, const double* vt,
+                       const double* vz, const uint64_t* uid, int64_t n);
+
+/* Advance nsteps time steps (Sec. II.A): per step the fused particle kernel
+ * (gather, Boris, absorb, null-collision MCC, spawn, deposit), child uid
+ * assignment, the FP64 field solve and E = -grad phi; every sort_every
+ * steps a counting sort by cell that also drops absorbed particles.  The
+ * Philox stream of a particle is keyed by (seed) with counter
+ * (uid, step, draw).  Asynchronous; never synchronises. */
+int pic_step(pic_handle* h, int64_t nsteps);
+
+/* Synchronise and fill *out; if density is not NULL, also write the node
+ * density (b_i / q) / V_i of the last deposit ((nr + 1) * (nz + 1) FP64,
+ * V_i the volume of the hat function).  Currents are averaged since the
+ * previous call. */
+int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density);
+
+/* Synchronise and copy the live particles, sorted by uid, to host FP64
+ * arrays of length cap.  *n receives the live count; PIC_ECAPACITY (and
+ * nothing written) if cap is smaller. */
+int pic_export_particles(pic_handle* h, int sim, double* r, double* z,
+                         double* vr, double* vt, double* vz, uint64_t* uid,
+                         int64_t cap, int64_t* n);
+
+/* Replace the node field (E_r, E_z) used by the next step's gather.  Used
+ * with fixed_efield = 1 for particle-only stepping in a given field.
+ * Synchronises. */
+int pic_set_efield(pic_handle* h, int sim, const double* er,
+                   const double* ez);
+
+enum {
+  PIC_GRID_PHI = 0,   /* potential phi, V */
+  PIC_GRID_RHS = 1,   /* last deposit b_i = sum q w Lambda_i, C */
+  PIC_GRID_ER = 2,    /* node field E_r in the particle precision, V/m */
+  PIC_GRID_EZ = 3     /* node field E_z, V/m */
+};
+
+/* Synchronise and copy one node grid (see PIC_GRID_*) to host FP64. */
+int pic_get_grid(pic_handle* h, int sim, int which, double* out);
+
+/* Solve the field for a host right-hand side b (node array, C) and write
+ * phi (host FP64): the same solver pic_step uses (Sec. II.A, finite
+ * elements with Dirichlet walls and Neumann ends).  Synchronises.  Leaves
+ * the simulation's own field untouched. */
+int pic_solve_field(pic_handle* h, const double* b, double* phi,
+                    double* relres);
+
+/* Write the full state (particles, field, counters, tallies) to `path`;
+ * pic_restore reads it into a handle made with the same configuration.
+ * Stepping on after a restore gives the same particles as never stopping
+ * (the random streams depend only on seed, uid and step). */
+int pic_checkpoint(pic_handle* h, const char* path);
+int pic_restore(pic_handle* h, const char* path);
+
+/* Device time of the step's kernels, measured with CUDA events recorded on
+ * the handle's stream around each stage of every pic_step call made while
+ * profiling is on.  enable = 1 starts (and clears) the record; enable = 0
+ * stops it, synchronises and fills *out (out may be NULL when starting). */
+typedef struct pic_kernel_times {
+  double particle_ms;          /* fused particle kernel, total */
+  int64_t particle_launches;
+  double finalize_ms;          /* child-uid assignment, total */
+  double field_ms;             /* field solve + E + residual check, total */
+  int64_t field_solves;
+  double sort_ms;              /* counting sorts, total */
+  int64_t sorts;
+  int64_t kernels_launched;    /* all kernels pic_step launched meanwhile */
+} pic_kernel_times;
+int pic_profile(pic_handle* h, int enable, pic_kernel_times* out);
+
+/* Release the handle and its device memory (after the stream is idle). */
+void pic_free(pic_handle* h);
+
+/* Static string for a PIC_* code. */
+const char* pic_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

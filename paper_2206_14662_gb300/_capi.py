@@ -1,0 +1,264 @@
+"""ctypes binding of libpic (include/pic.h): the same entry points, argument
+marshalling only.  Every step of the method runs in the library's CUDA
+kernels; there is no CPU path.  Importing works without a GPU, but loading
+the library requires it to have been built (``build.build()``), and any call
+that reaches the device requires a CUDA GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECAPACITY = 0, -1, -2, -3
+PIC_ENOCONV, PIC_ETIMEOUT, PIC_ENONFINITE, PIC_ECUDA = -4, -5, -6, -7
+PIC_GRID_PHI, PIC_GRID_RHS, PIC_GRID_ER, PIC_GRID_EZ = 0, 1, 2, 3
+
+c_d, c_i32, c_i64, c_u64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+
+
+class PicConfig(ctypes.Structure):
+    _fields_ = [
+        ("r_in", c_d), ("r_out", c_d), ("z_min", c_d), ("z_max", c_d),
+        ("nr", c_i32), ("nz", c_i32), ("v_inner", c_d), ("v_outer", c_d),
+        ("bfield_kind", c_i32), ("b0", c_d), ("p_mbar", c_d), ("t_gas_K", c_d),
+        ("sigma_el", c_d), ("ion_E_th_eV", c_d), ("ion_sigma_pk", c_d),
+        ("ion_E_pk_eV", c_d), ("opal_B_eV", c_d), ("xi_param", c_d),
+        ("elastic_recoil", c_i32), ("gas_mass_amu", c_d), ("n_init", c_i64),
+        ("n0", c_d), ("T0_eV", c_d), ("weight", c_d), ("dt", c_d),
+        ("sort_every", c_i32), ("poisson_rtol", c_d), ("poisson_maxit", c_i32),
+        ("capacity", c_i64), ("seed", c_u64), ("precision", c_i32),
+        ("nu_max", c_d), ("fixed_efield", c_i32),
+    ]
+
+
+class PicDiag(ctypes.Structure):
+    _fields_ = [
+        ("step", c_i64), ("t", c_d), ("n_particles", c_i64),
+        ("I_inner", c_d), ("I_outer", c_d), ("I_zmin", c_d), ("I_zmax", c_d),
+        ("absorbed_weight", c_d * 4),
+        ("n_elastic", c_i64), ("n_ionise", c_i64), ("n_absorbed", c_i64),
+        ("n_candidates", c_i64), ("n_over", c_i64), ("n_pushed", c_i64),
+        ("ke_total_J", c_d), ("work_E_J", c_d), ("ke_absorbed_J", c_d),
+        ("ion_loss_J", c_d), ("recoil_loss_J", c_d), ("ke_initial_J", c_d),
+        ("ledger_residual_J", c_d), ("n_peak", c_d), ("poisson_iters", c_i32),
+        ("poisson_relres", c_d), ("nu_max", c_d), ("weight", c_d), ("error", c_i32),
+    ]
+
+
+class PicKernelTimes(ctypes.Structure):
+    _fields_ = [
+        ("particle_ms", c_d), ("particle_launches", c_i64), ("finalize_ms", c_d),
+        ("field_ms", c_d), ("field_solves", c_i64), ("sort_ms", c_d), ("sorts", c_i64),
+        ("kernels_launched", c_i64),
+    ]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class PicAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class PicError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {lib().pic_strerror(code).decode()} ({code})")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpic.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpic.so is not built ({LIB_PATH}); run "
+                               "paper_2206_14662_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, P = ctypes.c_void_p, ctypes.POINTER
+        L.pic_strerror.argtypes = [ctypes.c_int]
+        L.pic_strerror.restype = ctypes.c_char_p
+        L.pic_init.argtypes = [P(PicConfig), ctypes.c_int, vp, P(PicAllocator), P(vp)]
+        L.pic_load_particles.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, c_i64]
+        L.pic_step.argtypes = [vp, c_i64]
+        L.pic_diagnostics.argtypes = [vp, ctypes.c_int, P(PicDiag), vp]
+        L.pic_export_particles.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, c_i64, P(c_i64)]
+        L.pic_set_efield.argtypes = [vp, ctypes.c_int, vp, vp]
+        L.pic_get_grid.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+        L.pic_solve_field.argtypes = [vp, vp, vp, P(c_d)]
+        L.pic_checkpoint.argtypes = [vp, ctypes.c_char_p]
+        L.pic_restore.argtypes = [vp, ctypes.c_char_p]
+        L.pic_profile.argtypes = [vp, ctypes.c_int, P(PicKernelTimes)]
+        L.pic_free.argtypes = [vp]
+        L.pic_free.restype = None
+        for name in ("pic_init", "pic_load_particles", "pic_step", "pic_diagnostics",
+                     "pic_export_particles", "pic_set_efield", "pic_get_grid", "pic_solve_field",
+                     "pic_checkpoint", "pic_restore", "pic_profile"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != PIC_OK:
+        raise PicError(rc, where)
+
+
+def make_config(cfg: dict) -> PicConfig:
+    """pic_config from a workload dict (keys are the struct's field names;
+    other keys are ignored)."""
+    c = PicConfig()
+    for name, ctype in PicConfig._fields_:
+        if name in cfg:
+            setattr(c, name, ctype(cfg[name]).value if ctype in (c_i32, c_i64, c_u64) else float(cfg[name]))
+    return c
+
+
+def _f64(a):
+    """(pointer, keep-alive) of a contiguous float64 host array or tensor."""
+    if hasattr(a, "data_ptr"):
+        assert a.dtype.__str__() == "torch.float64" and a.is_contiguous() and not a.is_cuda
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return arr.ctypes.data_as(ctypes.c_void_p), arr
+
+
+def _u64(a):
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=np.uint64)
+    return arr.ctypes.data_as(ctypes.c_void_p), arr
+
+
+def _torch_allocator():
+    """A pic_allocator backed by PyTorch's CUDA caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      stream or 0)
+        except Exception:   # out of memory: the library reports PIC_ENOMEM
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+    return PicAllocator(fa, ff, None), (fa, ff)
+
+
+class Simulation:
+    """One simulation handle (pic_init ... pic_free)."""
+
+    def __init__(self, cfg: dict, stream=None, torch_allocator: bool = True):
+        L = lib()
+        self.cfg = dict(cfg)
+        self._c = make_config(cfg)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = int(stream)
+        self._keep = None
+        alloc_p = None
+        if torch_allocator:
+            al, self._keep = _torch_allocator()
+            self._alloc = al
+            alloc_p = ctypes.byref(self._alloc)
+        h = ctypes.c_void_p()
+        _check(L.pic_init(ctypes.byref(self._c), 1, ctypes.c_void_p(self.stream), alloc_p,
+                          ctypes.byref(h)), "pic_init")
+        self.h = h
+        self.nnodes = (cfg["nr"] + 1) * (cfg["nz"] + 1)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pic_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def load_particles(self, r, z, vr, vt, vz, uid):
+        ptrs = [_f64(a) for a in (r, z, vr, vt, vz)]
+        pu = _u64(uid)
+        n = len(r)
+        _check(lib().pic_load_particles(self.h, 0, *[p for p, _ in ptrs], pu[0], n),
+               "pic_load_particles")
+
+    def step(self, nsteps: int = 1):
+        _check(lib().pic_step(self.h, int(nsteps)), "pic_step")
+
+    def diagnostics(self, density: bool = False, raise_on_error: bool = True) -> dict:
+        d = PicDiag()
+        dens = np.zeros(self.nnodes) if density else None
+        rc = lib().pic_diagnostics(self.h, 0, ctypes.byref(d),
+                                   dens.ctypes.data_as(ctypes.c_void_p) if density else None)
+        if raise_on_error:
+            _check(rc, "pic_diagnostics")
+        out = {name: (list(getattr(d, name)) if name == "absorbed_weight" else getattr(d, name))
+               for name, _ in PicDiag._fields_}
+        if density:
+            out["density"] = dens
+        return out
+
+    def export_particles(self) -> dict:
+        cap = int(self.diagnostics(raise_on_error=False)["n_particles"])
+        arrs = [np.zeros(cap) for _ in range(5)]
+        uid = np.zeros(cap, dtype=np.uint64)
+        n = c_i64()
+        _check(lib().pic_export_particles(self.h, 0, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
+                                          uid.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n)),
+               "pic_export_particles")
+        k = n.value
+        return dict(r=arrs[0][:k], z=arrs[1][:k], vr=arrs[2][:k], vt=arrs[3][:k], vz=arrs[4][:k],
+                    uid=uid[:k])
+
+    def set_efield(self, er, ez):
+        pe, pz = _f64(er), _f64(ez)
+        _check(lib().pic_set_efield(self.h, 0, pe[0], pz[0]), "pic_set_efield")
+
+    def get_grid(self, which: int) -> np.ndarray:
+        out = np.zeros(self.nnodes)
+        _check(lib().pic_get_grid(self.h, 0, which, out.ctypes.data_as(ctypes.c_void_p)),
+               "pic_get_grid")
+        return out
+
+    def solve_field(self, b):
+        pb = _f64(b)
+        phi = np.zeros(self.nnodes)
+        rel = c_d()
+        _check(lib().pic_solve_field(self.h, pb[0], phi.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.byref(rel)), "pic_solve_field")
+        return phi, rel.value
+
+    def checkpoint(self, path: str):
+        _check(lib().pic_checkpoint(self.h, path.encode()), "pic_checkpoint")
+
+    def restore(self, path: str):
+        _check(lib().pic_restore(self.h, path.encode()), "pic_restore")
+
+    def profile_start(self):
+        _check(lib().pic_profile(self.h, 1, None), "pic_profile")
+
+    def profile_stop(self) -> dict:
+        t = PicKernelTimes()
+        _check(lib().pic_profile(self.h, 0, ctypes.byref(t)), "pic_profile")
+        return {name: getattr(t, name) for name, _ in PicKernelTimes._fields_}

@@ -1,0 +1,841 @@
+// capi.cu -- the C ABI of libpic (include/pic.h): handle life cycle, the
+// per-step launch sequence, diagnostics, particle exchange and
+// checkpointing.  Method: arXiv 2206.14662, Sec. II.A.
+//
+// Per step (pic_step), all on the caller's stream:
+//   1. k_particle_step     gather, push, absorb, collide, spawn, deposit
+//   2. k_spawn_finalize    child uids by parent rank; slot and step counters
+//   3. every sort_every steps: counting sort into the other buffer set
+//   4. field solve         DCT-I (z) / Thomas (r) / inverse DCT-I, then
+//                          E = -grad phi and the residual check
+// Counters live in device memory, so the host never waits inside pic_step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+using namespace pic;
+
+namespace pic {
+int particle_step_blocks_per_sm(int precision);
+}
+
+struct pic_handle {
+  pic_config cfg;
+  int prec;
+  cudaStream_t stream;
+  pic_allocator alloc;
+  bool has_alloc;
+  std::vector<void*> owned;
+
+  // derived on the host in FP64
+  double n_gas, weight, nu_max, p_null, hr, hz, gas_mass;
+  unsigned thr_null;
+  long long capacity, spawn_cap;
+  int nnodes, ncells, grid_particle, grid_sort;
+
+  // device memory
+  DevState* st;
+  Soa<float> sf[2];
+  Soa<double> sd[2];
+  int cur;
+  unsigned* spawn_parent;
+  int* cell_count;
+  double* rhs;
+  double* rho_last;
+  double* phi;
+  void* efield;
+  double* scratch2;   // two doubles for reductions
+  FieldTables T;
+  std::vector<double> phi_init;   // wall rows + vacuum interior
+
+  // host bookkeeping
+  long long step;
+  double ke_initial;
+  double last_abs[4];
+  long long last_diag_step;
+  int sticky;
+  long long kernels;
+
+  // profiling
+  bool profiling;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_marks;   // (event index, stage tag)
+  int ev_used;
+  long long prof_kernels0;
+  long long prof_counts[4];
+
+  PushParams<float> Pf;
+  PushParams<double> Pd;
+};
+
+namespace {
+
+void* default_alloc(size_t bytes, void*, void*) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+void default_free(void* p, void*, void*) { cudaFree(p); }
+
+struct AllocCtx {
+  pic_handle* h;
+};
+
+void* h_alloc(size_t bytes, void* ctx) {
+  pic_handle* h = (pic_handle*)ctx;
+  void* p = h->has_alloc ? h->alloc.alloc(bytes, (void*)h->stream, h->alloc.ctx)
+                         : default_alloc(bytes, nullptr, nullptr);
+  if (p) h->owned.push_back(p);
+  return p;
+}
+void h_free_one(void* p, void* ctx) {
+  pic_handle* h = (pic_handle*)ctx;
+  if (h->has_alloc) h->alloc.free(p, (void*)h->stream, h->alloc.ctx);
+  else default_free(p, nullptr, nullptr);
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    if ((call) != cudaSuccess) return PIC_ECUDA;  \
+  } while (0)
+
+double sigma_ion_host(const pic_config& c, double E_eV) {
+  if (E_eV <= c.ion_E_th_eV) return 0.0;
+  const double s = (E_eV - c.ion_E_th_eV) / (c.ion_E_pk_eV - c.ion_E_th_eV);
+  return c.ion_sigma_pk * 2.0 * s / (1.0 + s * s);
+}
+
+int validate(const pic_config& c) {
+  if (!(c.r_in > 0 && c.r_out > c.r_in && c.z_max > c.z_min)) return PIC_EINVAL;
+  // nz + 1 doubles of one z-line must fit the direct transform's 48 KB of
+  // shared memory; cell indices are packed in 16 bits
+  if (c.nr < 2 || c.nz < 2 || c.nr > 32767 || c.nz > 4096) return PIC_EINVAL;
+  if (!(c.dt > 0) || !std::isfinite(c.dt)) return PIC_EINVAL;
+  if (c.bfield_kind != 0 && c.bfield_kind != 1) return PIC_EINVAL;
+  if (c.precision != 32 && c.precision != 64) return PIC_EINVAL;
+  if (!(c.p_mbar >= 0) || !(c.t_gas_K > 0) || !(c.sigma_el >= 0)) return PIC_EINVAL;
+  if (!(c.ion_E_pk_eV > c.ion_E_th_eV) || !(c.ion_E_th_eV > 0)) return PIC_EINVAL;
+  if (!(c.opal_B_eV > 0) || !(c.xi_param >= 0 && c.xi_param < 1)) return PIC_EINVAL;
+  if (!(c.gas_mass_amu > 0)) return PIC_EINVAL;
+  if (c.weight <= 0 && (c.n_init <= 0 || !(c.n0 > 0))) return PIC_EINVAL;
+  if (c.sort_every < 0 || c.capacity < 0) return PIC_EINVAL;
+  if (!(c.poisson_rtol > 0)) return PIC_EINVAL;
+  if ((long long)(c.nr + 1) * (c.nz + 1) > (1ll << 30)) return PIC_EINVAL;
+  return PIC_OK;
+}
+
+template <typename Real>
+void fill_params(pic_handle* h, PushParams<Real>& P) {
+  const pic_config& c = h->cfg;
+  const double L = c.z_max - c.z_min;
+  P.r_in = (Real)c.r_in; P.hr = (Real)h->hr; P.inv_hr = (Real)(1.0 / h->hr);
+  P.z_min = (Real)c.z_min; P.hz = (Real)h->hz; P.inv_hz = (Real)(1.0 / h->hz);
+  P.z_mid = (Real)(0.5 * (c.z_min + c.z_max)); P.inv_L2 = (Real)(1.0 / (L * L));
+  P.b0 = (Real)c.b0;
+  P.nr = c.nr; P.nz = c.nz; P.bkind = c.bfield_kind;
+  P.qmdt2 = (Real)(-kQe * c.dt / (2.0 * kMe));
+  P.dt = (Real)c.dt;
+  P.thr_null = h->thr_null;
+  P.nsig_el = (Real)(h->n_gas * c.sigma_el);
+  P.n_gas = (Real)h->n_gas;
+  P.e_th = (Real)(c.ion_E_th_eV * kQe);
+  P.e_span_inv = (Real)(1.0 / ((c.ion_E_pk_eV - c.ion_E_th_eV) * kQe));
+  P.sig_pk = (Real)c.ion_sigma_pk;
+  P.opal_b = (Real)(c.opal_B_eV * kQe);
+  P.xi = (Real)c.xi_param;
+  P.recoil = c.elastic_recoil ? (Real)(2.0 * kMe / h->gas_mass) : (Real)0;
+  P.nu_max = (Real)h->nu_max;
+  P.half_m = (Real)(0.5 * kMe);
+  P.two_over_m = (Real)(2.0 / kMe);
+  P.work_scale = (Real)(-kQe * c.dt / 4.0);
+  P.weight = h->weight;
+  P.qw = -kQe * h->weight;
+  P.seed_lo = (unsigned)(c.seed & 0xFFFFFFFFull);
+  P.seed_hi = (unsigned)(c.seed >> 32);
+  P.capacity = h->capacity;
+  P.spawn_cap = h->spawn_cap;
+}
+
+template <typename Real>
+int alloc_soa(pic_handle* h, Soa<Real>& s) {
+  const size_t n = (size_t)h->capacity;
+  auto al = [&](size_t bytes) { return h_alloc(std::max<size_t>(bytes, 256), h); };
+  s.cell = (int*)al(n * sizeof(int));
+  s.offr = (Real*)al(n * sizeof(Real));
+  s.offz = (Real*)al(n * sizeof(Real));
+  s.vr = (Real*)al(n * sizeof(Real));
+  s.vt = (Real*)al(n * sizeof(Real));
+  s.vz = (Real*)al(n * sizeof(Real));
+  s.uid = (unsigned*)al(n * sizeof(unsigned));
+  if (!s.cell || !s.offr || !s.offz || !s.vr || !s.vt || !s.vz || !s.uid) return PIC_ENOMEM;
+  return PIC_OK;
+}
+
+// profiling: an event on the stream tagged with the stage that just ended
+void mark(pic_handle* h, int tag) {
+  if (!h->profiling) return;
+  if (h->ev_used == (int)h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    h->ev_pool.push_back(e);
+  }
+  cudaEventRecord(h->ev_pool[h->ev_used], h->stream);
+  h->ev_marks.push_back({h->ev_used, tag});
+  ++h->ev_used;
+}
+
+enum { kTagStart = -1, kTagParticle = 0, kTagFinalize = 1, kTagSort = 2, kTagField = 3 };
+
+template <typename Real>
+Soa<Real>& soa(pic_handle* h, int which);
+template <>
+Soa<float>& soa<float>(pic_handle* h, int which) { return h->sf[which]; }
+template <>
+Soa<double>& soa<double>(pic_handle* h, int which) { return h->sd[which]; }
+template <typename Real>
+const PushParams<Real>& params(pic_handle* h);
+template <>
+const PushParams<float>& params<float>(pic_handle* h) { return h->Pf; }
+template <>
+const PushParams<double>& params<double>(pic_handle* h) { return h->Pd; }
+
+template <typename Real>
+int step_impl(pic_handle* h, long long nsteps) {
+  const PushParams<Real>& P = params<Real>(h);
+  const bool solve = h->cfg.fixed_efield == 0;
+  for (long long s = 0; s < nsteps; ++s) {
+    mark(h, kTagStart);
+    if (!solve) {
+      CK(cudaMemsetAsync(h->rhs, 0, (size_t)h->nnodes * sizeof(double), h->stream));
+    }
+    launch_particle_step<Real>(soa<Real>(h, h->cur), h->efield, h->rhs, h->st,
+                               h->spawn_parent, P, h->grid_particle, h->stream);
+    mark(h, kTagParticle);
+    launch_spawn_finalize(h->st, soa<Real>(h, h->cur).uid, h->spawn_parent, h->spawn_cap,
+                          h->capacity, h->stream);
+    mark(h, kTagFinalize);
+    h->kernels += 2;
+    ++h->step;
+    if (h->cfg.sort_every > 0 && h->step % h->cfg.sort_every == 0) {
+      launch_sort<Real>(soa<Real>(h, h->cur), soa<Real>(h, h->cur ^ 1), h->st, h->cell_count,
+                        h->ncells, h->cfg.nz, h->grid_sort, h->stream);
+      h->cur ^= 1;
+      h->kernels += 4;
+      mark(h, kTagSort);
+    }
+    if (solve) {
+      launch_field_solve<Real>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true,
+                               h->stream);
+      h->kernels += 4;
+      mark(h, kTagField);
+    }
+  }
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int check_sticky(pic_handle* h) {
+  if (h->sticky) return h->sticky;
+  int err = 0;
+  if (cudaMemcpyAsync(&err, &h->st->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return h->sticky = PIC_ECUDA;
+  if (err) h->sticky = err;
+  return h->sticky;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" {
+
+const char* pic_strerror(int code) {
+  switch (code) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument or configuration";
+    case PIC_ENOMEM: return "out of memory";
+    case PIC_ECAPACITY: return "particle or spawn capacity exceeded";
+    case PIC_ENOCONV: return "field solve did not reach poisson_rtol";
+    case PIC_ETIMEOUT: return "bounded device wait timed out";
+    case PIC_ENONFINITE: return "non-finite particle value";
+    case PIC_ECUDA: return "CUDA runtime error";
+    default: return "unknown error";
+  }
+}
+
+int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
+             const pic_allocator* alloc, pic_handle** out) {
+  if (!cfg || !out) return PIC_EINVAL;
+  *out = nullptr;
+  if (n_sims != 1) return PIC_EINVAL;
+  int rc = validate(*cfg);
+  if (rc) return rc;
+  pic_handle* h = new (std::nothrow) pic_handle();
+  if (!h) return PIC_ENOMEM;
+  h->cfg = *cfg;
+  h->prec = cfg->precision;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->has_alloc = alloc && alloc->alloc && alloc->free;
+  if (h->has_alloc) h->alloc = *alloc;
+  const pic_config& c = h->cfg;
+
+  // derived quantities (FP64, host)
+  const double L = c.z_max - c.z_min;
+  h->hr = (c.r_out - c.r_in) / c.nr;
+  h->hz = L / c.nz;
+  h->n_gas = c.p_mbar * 100.0 / (kKb * c.t_gas_K);
+  h->weight = c.weight > 0 ? c.weight
+                           : c.n0 * kPi * (c.r_out * c.r_out - c.r_in * c.r_in) * L / (double)c.n_init;
+  h->gas_mass = c.gas_mass_amu * kAmu;
+  if (c.nu_max > 0) {
+    h->nu_max = c.nu_max;
+  } else {
+    const double E_cap = 2.0 * std::fabs(c.v_inner - c.v_outer);
+    double best = 0.0;
+    for (int k = 0; k <= 100000; ++k) {
+      const double E_eV = E_cap * (double)k / 100000.0;
+      const double v = std::sqrt(2.0 * E_eV * kQe / kMe);
+      const double nu = h->n_gas * c.sigma_el * v + h->n_gas * sigma_ion_host(c, E_eV) * v;
+      if (nu > best) best = nu;
+    }
+    h->nu_max = best * (1.0 + 1e-6);
+  }
+  h->p_null = 1.0 - std::exp(-h->nu_max * c.dt);
+  {
+    const double cthr = h->p_null * 16777216.0 - 0.5;
+    h->thr_null = cthr <= 0 ? 0u : (unsigned)std::min(16777216.0, std::ceil(cthr));
+  }
+  h->capacity = c.capacity > 0 ? c.capacity : (long long)(1.25 * (double)c.n_init) + 4096;
+  if (h->capacity > (1ll << 31) - 1) { delete h; return PIC_EINVAL; }
+  h->spawn_cap = std::min<long long>(h->capacity, 1 << 20);
+  h->nnodes = (c.nr + 1) * (c.nz + 1);
+  h->ncells = c.nr * c.nz;
+
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete h;
+    return PIC_ECUDA;
+  }
+  const int bps = std::max(1, particle_step_blocks_per_sm(h->prec));
+  const long long chunks = (h->capacity + 1023) / 1024;
+  h->grid_particle = (int)std::max<long long>(1, std::min<long long>((long long)sms * bps, chunks));
+  h->grid_sort = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8,
+                                                                 (h->capacity + 255) / 256));
+
+  // device memory
+  h->st = (DevState*)h_alloc(sizeof(DevState), h);
+  if (h->prec == 32) {
+    rc = alloc_soa(h, h->sf[0]);
+    if (!rc) rc = alloc_soa(h, h->sf[1]);
+  } else {
+    rc = alloc_soa(h, h->sd[0]);
+    if (!rc) rc = alloc_soa(h, h->sd[1]);
+  }
+  h->spawn_parent = (unsigned*)h_alloc((size_t)h->spawn_cap * sizeof(unsigned), h);
+  h->cell_count = (int*)h_alloc((size_t)h->ncells * sizeof(int), h);
+  h->rhs = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
+  h->rho_last = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
+  h->phi = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
+  h->efield = h_alloc((size_t)h->nnodes * (h->prec == 32 ? sizeof(float2) : sizeof(double2)), h);
+  h->scratch2 = (double*)h_alloc(2 * sizeof(double), h);
+  if (!rc && (!h->st || !h->spawn_parent || !h->cell_count || !h->rhs || !h->rho_last ||
+              !h->phi || !h->efield || !h->scratch2))
+    rc = PIC_ENOMEM;
+  if (!rc) rc = field_tables_build(c, h->T, h_alloc, h, h->stream);
+  if (!rc) {
+    // the vacuum field: wall rows plus the z-independent vacuum solution
+    std::vector<double> vac(c.nr + 1);
+    if (cudaMemcpy(vac.data(), h->T.phi_vac, vac.size() * sizeof(double),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = PIC_ECUDA;
+    h->phi_init.assign(h->nnodes, 0.0);
+    for (int i = 0; i <= c.nr; ++i)
+      for (int j = 0; j <= c.nz; ++j) h->phi_init[(size_t)i * (c.nz + 1) + j] = vac[i];
+  }
+  if (!rc) {
+    DevState s0;
+    std::memset(&s0, 0, sizeof(s0));
+    if (cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->rhs, 0, (size_t)h->nnodes * sizeof(double), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->rho_last, 0, (size_t)h->nnodes * sizeof(double), h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->phi, h->phi_init.data(), (size_t)h->nnodes * sizeof(double),
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      rc = PIC_ECUDA;
+  }
+  if (!rc) {
+    // vacuum E until particles are loaded
+    if (h->prec == 32)
+      launch_field_solve<float>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true, h->stream);
+    else
+      launch_field_solve<double>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = PIC_ECUDA;
+  }
+  if (rc) {
+    pic_free(h);
+    return rc;
+  }
+  fill_params<float>(h, h->Pf);
+  fill_params<double>(h, h->Pd);
+  *out = h;
+  return PIC_OK;
+}
+
+void pic_free(pic_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (void* p : h->owned) h_free_one(p, h);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+}
+
+int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
+                       const double* vr, const double* vt, const double* vz,
+                       const uint64_t* uid, int64_t n) {
+  if (!h || sim != 0 || n < 0 || n > h->capacity) return PIC_EINVAL;
+  if (n > 0 && (!r || !z || !vr || !vt || !vz || !uid)) return PIC_EINVAL;
+  const pic_config& c = h->cfg;
+  uint64_t umax = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    if (!(r[p] > c.r_in && r[p] < c.r_out && z[p] > c.z_min && z[p] < c.z_max)) return PIC_EINVAL;
+    if (!std::isfinite(vr[p]) || !std::isfinite(vt[p]) || !std::isfinite(vz[p]))
+      return PIC_ENONFINITE;
+    if (uid[p] >= 0xFFFFFFFFull) return PIC_EINVAL;
+    umax = std::max(umax, uid[p]);
+  }
+  h->sticky = 0;
+  // staging buffers for the FP64 host arrays
+  const size_t bytes = std::max<size_t>((size_t)n, 1) * sizeof(double);
+  double* d[5];
+  uint64_t* du = nullptr;
+  for (int k = 0; k < 5; ++k) {
+    d[k] = (double*)h_alloc(bytes, h);
+    if (!d[k]) return PIC_ENOMEM;
+  }
+  du = (uint64_t*)h_alloc(bytes, h);
+  if (!du) return PIC_ENOMEM;
+  const double* src[5] = {r, z, vr, vt, vz};
+  int rc = PIC_OK;
+  for (int k = 0; k < 5 && n > 0; ++k)
+    if (cudaMemcpyAsync(d[k], src[k], (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+      rc = PIC_ECUDA;
+  if (n > 0 && cudaMemcpyAsync(du, uid, (size_t)n * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                               h->stream) != cudaSuccess)
+    rc = PIC_ECUDA;
+  h->cur = 0;
+  if (!rc) {
+    if (h->prec == 32)
+      launch_load<float>(d[0], d[1], d[2], d[3], d[4], du, n, h->sf[0], h->Pf, h->st, h->stream);
+    else
+      launch_load<double>(d[0], d[1], d[2], d[3], d[4], du, n, h->sd[0], h->Pd, h->st, h->stream);
+  }
+  DevState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.n_slots = n;
+  s0.n_live = n;
+  s0.uid_next = n > 0 ? umax + 1 : 0;
+  if (!rc && (cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) !=
+                  cudaSuccess ||
+              cudaMemsetAsync(h->rhs, 0, (size_t)h->nnodes * sizeof(double), h->stream) !=
+                  cudaSuccess ||
+              cudaMemcpyAsync(h->phi, h->phi_init.data(), (size_t)h->nnodes * sizeof(double),
+                              cudaMemcpyHostToDevice, h->stream) != cudaSuccess))
+    rc = PIC_ECUDA;
+  if (!rc) {
+    if (h->prec == 32) launch_deposit_only<float>(h->sf[0], n, h->rhs, c.nz, -kQe * h->weight, h->stream);
+    else launch_deposit_only<double>(h->sd[0], n, h->rhs, c.nz, -kQe * h->weight, h->stream);
+    if (c.fixed_efield == 0) {
+      if (h->prec == 32)
+        launch_field_solve<float>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true, h->stream);
+      else
+        launch_field_solve<double>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true, h->stream);
+    }
+    // initial kinetic energy
+    cudaMemsetAsync(h->scratch2, 0, 2 * sizeof(double), h->stream);
+    if (h->prec == 32) launch_kinetic_energy<float>(h->sf[0], h->st, h->scratch2, h->stream);
+    else launch_kinetic_energy<double>(h->sd[0], h->st, h->scratch2, h->stream);
+    double ke[2] = {0, 0};
+    if (cudaMemcpyAsync(ke, h->scratch2, sizeof(ke), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      rc = PIC_ECUDA;
+    h->ke_initial = 0.5 * kMe * ke[0] * h->weight;
+  } else {
+    cudaStreamSynchronize(h->stream);
+  }
+  // release the staging buffers
+  for (int k = 0; k < 6; ++k) {
+    void* p = k < 5 ? (void*)d[k] : (void*)du;
+    auto it = std::find(h->owned.begin(), h->owned.end(), p);
+    if (it != h->owned.end()) h->owned.erase(it);
+    h_free_one(p, h);
+  }
+  h->step = 0;
+  h->last_diag_step = 0;
+  for (double& a : h->last_abs) a = 0.0;
+  return rc;
+}
+
+int pic_step(pic_handle* h, int64_t nsteps) {
+  if (!h || nsteps < 0) return PIC_EINVAL;
+  if (h->sticky) return h->sticky;
+  return h->prec == 32 ? step_impl<float>(h, nsteps) : step_impl<double>(h, nsteps);
+}
+
+int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
+  if (!h || sim != 0 || !out) return PIC_EINVAL;
+  const pic_config& c = h->cfg;
+  DevState s;
+  CK(cudaMemsetAsync(h->scratch2, 0, 2 * sizeof(double), h->stream));
+  if (h->prec == 32) launch_kinetic_energy<float>(h->sf[h->cur], h->st, h->scratch2, h->stream);
+  else launch_kinetic_energy<double>(h->sd[h->cur], h->st, h->scratch2, h->stream);
+  double ke[2];
+  CK(cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(ke, h->scratch2, sizeof(ke), cudaMemcpyDeviceToHost, h->stream));
+  std::vector<double> grid;
+  if (density) {
+    grid.resize(h->nnodes);
+    CK(cudaMemcpyAsync(grid.data(), c.fixed_efield ? h->rhs : h->rho_last,
+                       (size_t)h->nnodes * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  if (s.err && !h->sticky) h->sticky = s.err;
+  std::memset(out, 0, sizeof(*out));
+  out->step = h->step;
+  out->t = (double)h->step * c.dt;
+  out->n_particles = (int64_t)ke[1];
+  const double dtw = (double)(h->step - h->last_diag_step) * c.dt;
+  double* I[4] = {&out->I_inner, &out->I_outer, &out->I_zmin, &out->I_zmax};
+  for (int w = 0; w < 4; ++w) {
+    out->absorbed_weight[w] = s.tally[kAbsInner + w];
+    *I[w] = dtw > 0 ? (s.tally[kAbsInner + w] - h->last_abs[w]) * kQe / dtw : 0.0;
+    h->last_abs[w] = s.tally[kAbsInner + w];
+  }
+  h->last_diag_step = h->step;
+  out->n_elastic = (int64_t)s.tally[kNElastic];
+  out->n_ionise = (int64_t)s.tally[kNIonise];
+  out->n_absorbed = (int64_t)s.tally[kNAbsorbed];
+  out->n_candidates = (int64_t)s.tally[kNCandidate];
+  out->n_over = (int64_t)s.tally[kNOver];
+  out->n_pushed = (int64_t)s.tally[kNPushed];
+  out->ke_total_J = 0.5 * kMe * ke[0] * h->weight;
+  out->work_E_J = s.tally[kWorkE];
+  out->ke_absorbed_J = s.tally[kKeAbsorbed];
+  out->ion_loss_J = s.tally[kIonLoss];
+  out->recoil_loss_J = s.tally[kRecoilLoss];
+  out->ke_initial_J = h->ke_initial;
+  out->ledger_residual_J = (out->ke_total_J - h->ke_initial) -
+                           (out->work_E_J - out->ke_absorbed_J - out->ion_loss_J - out->recoil_loss_J);
+  out->poisson_iters = s.poisson_iters;
+  out->poisson_relres = s.relres_last;
+  out->nu_max = h->nu_max;
+  out->weight = h->weight;
+  out->error = h->sticky;
+  if (density) {
+    // node volume of each hat function: 2 pi R_i Z_j
+    const double hr = h->hr, hz = h->hz;
+    double peak = 0.0;
+    for (int i = 0; i <= c.nr; ++i) {
+      const double ri = c.r_in + i * hr;
+      const double R = i == 0 ? hr * (c.r_in / 2 + hr / 6)
+                              : (i == c.nr ? hr * (c.r_out / 2 - hr / 6) : ri * hr);
+      for (int j = 0; j <= c.nz; ++j) {
+        const double Z = (j == 0 || j == c.nz) ? hz / 2 : hz;
+        const size_t o = (size_t)i * (c.nz + 1) + j;
+        density[o] = grid[o] / (-kQe) / (2.0 * kPi * R * Z);
+        peak = std::max(peak, density[o]);
+      }
+    }
+    out->n_peak = peak;
+  }
+  return h->sticky;
+}
+
+int pic_export_particles(pic_handle* h, int sim, double* r, double* z, double* vr,
+                         double* vt, double* vz, uint64_t* uid, int64_t cap, int64_t* n) {
+  if (!h || sim != 0 || !n) return PIC_EINVAL;
+  DevState s;
+  CK(cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (s.err && !h->sticky) h->sticky = s.err;
+  const long long ns = s.n_slots;
+  std::vector<double> a[5];
+  std::vector<unsigned long long> u(ns);
+  std::vector<int> live(ns);
+  for (auto& v : a) v.resize(ns);
+  if (ns > 0) {
+    const size_t bytes = (size_t)ns * sizeof(double);
+    void* d[7];
+    for (int k = 0; k < 7; ++k) {
+      d[k] = h_alloc(bytes, h);
+      if (!d[k]) return PIC_ENOMEM;
+    }
+    if (h->prec == 32)
+      launch_export<float>(h->sf[h->cur], ns, h->Pf, (double*)d[0], (double*)d[1], (double*)d[2],
+                           (double*)d[3], (double*)d[4], (unsigned long long*)d[5], (int*)d[6],
+                           h->stream);
+    else
+      launch_export<double>(h->sd[h->cur], ns, h->Pd, (double*)d[0], (double*)d[1], (double*)d[2],
+                            (double*)d[3], (double*)d[4], (unsigned long long*)d[5], (int*)d[6],
+                            h->stream);
+    int rc = PIC_OK;
+    for (int k = 0; k < 5; ++k)
+      if (cudaMemcpyAsync(a[k].data(), d[k], bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        rc = PIC_ECUDA;
+    if (cudaMemcpyAsync(u.data(), d[5], bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(live.data(), d[6], (size_t)ns * sizeof(int), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      rc = PIC_ECUDA;
+    for (int k = 0; k < 7; ++k) {
+      auto it = std::find(h->owned.begin(), h->owned.end(), d[k]);
+      if (it != h->owned.end()) h->owned.erase(it);
+      h_free_one(d[k], h);
+    }
+    if (rc) return rc;
+  }
+  std::vector<long long> idx;
+  idx.reserve(ns);
+  for (long long p = 0; p < ns; ++p)
+    if (live[p]) idx.push_back(p);
+  *n = (int64_t)idx.size();
+  if ((int64_t)idx.size() > cap) return PIC_ECAPACITY;
+  std::sort(idx.begin(), idx.end(), [&](long long x, long long y) { return u[x] < u[y]; });
+  double* dst[5] = {r, z, vr, vt, vz};
+  for (size_t q = 0; q < idx.size(); ++q) {
+    for (int k = 0; k < 5; ++k)
+      if (dst[k]) dst[k][q] = a[k][idx[q]];
+    if (uid) uid[q] = u[idx[q]];
+  }
+  return h->sticky;
+}
+
+int pic_set_efield(pic_handle* h, int sim, const double* er, const double* ez) {
+  if (!h || sim != 0 || !er || !ez) return PIC_EINVAL;
+  const size_t bytes = (size_t)h->nnodes * sizeof(double);
+  double* d0 = (double*)h_alloc(bytes, h);
+  double* d1 = (double*)h_alloc(bytes, h);
+  if (!d0 || !d1) return PIC_ENOMEM;
+  int rc = PIC_OK;
+  if (cudaMemcpyAsync(d0, er, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d1, ez, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    rc = PIC_ECUDA;
+  if (!rc) {
+    if (h->prec == 32) launch_efield_set<float>(d0, d1, h->efield, h->nnodes, h->stream);
+    else launch_efield_set<double>(d0, d1, h->efield, h->nnodes, h->stream);
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = PIC_ECUDA;
+  for (double* p : {d0, d1}) {
+    auto it = std::find(h->owned.begin(), h->owned.end(), (void*)p);
+    if (it != h->owned.end()) h->owned.erase(it);
+    h_free_one(p, h);
+  }
+  return rc;
+}
+
+int pic_get_grid(pic_handle* h, int sim, int which, double* out) {
+  if (!h || sim != 0 || !out) return PIC_EINVAL;
+  const size_t bytes = (size_t)h->nnodes * sizeof(double);
+  if (which == PIC_GRID_PHI || which == PIC_GRID_RHS) {
+    const double* src = which == PIC_GRID_PHI ? h->phi : (h->cfg.fixed_efield ? h->rhs : h->rho_last);
+    CK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return check_sticky(h);
+  }
+  if (which != PIC_GRID_ER && which != PIC_GRID_EZ) return PIC_EINVAL;
+  double* d = (double*)h_alloc(bytes, h);
+  if (!d) return PIC_ENOMEM;
+  if (h->prec == 32) launch_efield_get<float>(h->efield, d, which == PIC_GRID_ER ? 0 : 1, h->nnodes, h->stream);
+  else launch_efield_get<double>(h->efield, d, which == PIC_GRID_ER ? 0 : 1, h->nnodes, h->stream);
+  int rc = PIC_OK;
+  if (cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    rc = PIC_ECUDA;
+  auto it = std::find(h->owned.begin(), h->owned.end(), (void*)d);
+  if (it != h->owned.end()) h->owned.erase(it);
+  h_free_one(d, h);
+  return rc ? rc : check_sticky(h);
+}
+
+int pic_solve_field(pic_handle* h, const double* b, double* phi, double* relres) {
+  if (!h || !b || !phi) return PIC_EINVAL;
+  const size_t bytes = (size_t)h->nnodes * sizeof(double);
+  double* d_b = (double*)h_alloc(bytes, h);
+  double* d_phi = (double*)h_alloc(bytes, h);
+  double* d_rho = (double*)h_alloc(bytes, h);
+  void* d_e = h_alloc((size_t)h->nnodes * sizeof(double2), h);
+  DevState* d_st = (DevState*)h_alloc(sizeof(DevState), h);
+  int rc = (d_b && d_phi && d_rho && d_e && d_st) ? PIC_OK : PIC_ENOMEM;
+  DevState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  if (!rc && (cudaMemcpyAsync(d_b, b, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+              cudaMemcpyAsync(d_phi, h->phi_init.data(), bytes, cudaMemcpyHostToDevice,
+                              h->stream) != cudaSuccess ||
+              cudaMemcpyAsync(d_st, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) != cudaSuccess))
+    rc = PIC_ECUDA;
+  if (!rc) {
+    launch_field_solve<double>(h->T, d_b, d_phi, d_e, d_rho, d_st, false, h->stream);
+    if (cudaMemcpyAsync(phi, d_phi, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&s0, d_st, sizeof(s0), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+      rc = PIC_ECUDA;
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = PIC_ECUDA;
+  if (!rc && relres) *relres = s0.relres_last;
+  for (void* p : {(void*)d_b, (void*)d_phi, (void*)d_rho, d_e, (void*)d_st}) {
+    if (!p) continue;
+    auto it = std::find(h->owned.begin(), h->owned.end(), p);
+    if (it != h->owned.end()) h->owned.erase(it);
+    h_free_one(p, h);
+  }
+  return rc;
+}
+
+// checkpoint layout: magic, version, precision, nr, nz, capacity, seed, host
+// step, ke_initial, last_abs[4], last_diag_step, DevState, n_slots, the
+// seven SoA arrays of the current buffer set (n_slots entries), phi, the
+// node field, rho_last and rhs
+static const char kMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
+
+int pic_checkpoint(pic_handle* h, const char* path) {
+  if (!h || !path) return PIC_EINVAL;
+  DevState s;
+  CK(cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return PIC_EINVAL;
+  const size_t rs = h->prec == 32 ? sizeof(float) : sizeof(double);
+  const long long ns = s.n_slots;
+  int64_t hdr[6] = {h->prec, h->cfg.nr, h->cfg.nz, h->capacity, (int64_t)h->cfg.seed, h->step};
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            std::fwrite(&h->ke_initial, sizeof(double), 1, f) == 1 &&
+            std::fwrite(h->last_abs, sizeof(double), 4, f) == 4 &&
+            std::fwrite(&h->last_diag_step, sizeof(long long), 1, f) == 1 &&
+            std::fwrite(&s, sizeof(s), 1, f) == 1;
+  std::vector<char> buf;
+  void* arrays[7];
+  size_t sizes[7];
+  if (h->prec == 32) {
+    Soa<float>& q = h->sf[h->cur];
+    void* a[7] = {q.cell, q.offr, q.offz, q.vr, q.vt, q.vz, q.uid};
+    std::copy(a, a + 7, arrays);
+  } else {
+    Soa<double>& q = h->sd[h->cur];
+    void* a[7] = {q.cell, q.offr, q.offz, q.vr, q.vt, q.vz, q.uid};
+    std::copy(a, a + 7, arrays);
+  }
+  for (int k = 0; k < 7; ++k) sizes[k] = (k == 0 || k == 6) ? 4 : rs;
+  for (int k = 0; k < 7 && ok; ++k) {
+    buf.resize(std::max<size_t>(1, (size_t)ns * sizes[k]));
+    if (ns > 0 && cudaMemcpy(buf.data(), arrays[k], (size_t)ns * sizes[k], cudaMemcpyDeviceToHost) != cudaSuccess) { ok = false; break; }
+    ok = std::fwrite(buf.data(), 1, (size_t)ns * sizes[k], f) == (size_t)ns * sizes[k];
+  }
+  const size_t gbytes = (size_t)h->nnodes * sizeof(double);
+  const size_t ebytes = (size_t)h->nnodes * 2 * rs;
+  const void* grids[4] = {h->phi, h->efield, h->rho_last, h->rhs};
+  const size_t gsz[4] = {gbytes, ebytes, gbytes, gbytes};
+  for (int k = 0; k < 4 && ok; ++k) {
+    buf.resize(gsz[k]);
+    if (cudaMemcpy(buf.data(), grids[k], gsz[k], cudaMemcpyDeviceToHost) != cudaSuccess) { ok = false; break; }
+    ok = std::fwrite(buf.data(), 1, gsz[k], f) == gsz[k];
+  }
+  std::fclose(f);
+  return ok ? check_sticky(h) : PIC_EINVAL;
+}
+
+int pic_restore(pic_handle* h, const char* path) {
+  if (!h || !path) return PIC_EINVAL;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return PIC_EINVAL;
+  char magic[8];
+  int64_t hdr[6];
+  DevState s;
+  double ke0, labs[4];
+  long long lds;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+            std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(&ke0, sizeof(double), 1, f) == 1 &&
+            std::fread(labs, sizeof(double), 4, f) == 4 &&
+            std::fread(&lds, sizeof(long long), 1, f) == 1 && std::fread(&s, sizeof(s), 1, f) == 1;
+  ok = ok && hdr[0] == h->prec && hdr[1] == h->cfg.nr && hdr[2] == h->cfg.nz &&
+       hdr[3] == h->capacity && (uint64_t)hdr[4] == h->cfg.seed && s.n_slots <= h->capacity;
+  if (!ok) { std::fclose(f); return PIC_EINVAL; }
+  const size_t rs = h->prec == 32 ? sizeof(float) : sizeof(double);
+  const long long ns = s.n_slots;
+  h->cur = 0;
+  void* arrays[7];
+  if (h->prec == 32) {
+    Soa<float>& q = h->sf[0];
+    void* a[7] = {q.cell, q.offr, q.offz, q.vr, q.vt, q.vz, q.uid};
+    std::copy(a, a + 7, arrays);
+  } else {
+    Soa<double>& q = h->sd[0];
+    void* a[7] = {q.cell, q.offr, q.offz, q.vr, q.vt, q.vz, q.uid};
+    std::copy(a, a + 7, arrays);
+  }
+  std::vector<char> buf;
+  for (int k = 0; k < 7 && ok; ++k) {
+    const size_t sz = (k == 0 || k == 6) ? 4 : rs;
+    buf.resize(std::max<size_t>(1, (size_t)ns * sz));
+    ok = std::fread(buf.data(), 1, (size_t)ns * sz, f) == (size_t)ns * sz;
+    if (ok && ns > 0 && cudaMemcpy(arrays[k], buf.data(), (size_t)ns * sz, cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+  }
+  const size_t gbytes = (size_t)h->nnodes * sizeof(double);
+  const size_t ebytes = (size_t)h->nnodes * 2 * rs;
+  void* grids[4] = {h->phi, h->efield, h->rho_last, h->rhs};
+  const size_t gsz[4] = {gbytes, ebytes, gbytes, gbytes};
+  for (int k = 0; k < 4 && ok; ++k) {
+    buf.resize(gsz[k]);
+    ok = std::fread(buf.data(), 1, gsz[k], f) == gsz[k];
+    if (ok && cudaMemcpy(grids[k], buf.data(), gsz[k], cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+  }
+  std::fclose(f);
+  if (!ok) return PIC_EINVAL;
+  CK(cudaMemcpy(h->st, &s, sizeof(s), cudaMemcpyHostToDevice));
+  h->step = hdr[5];
+  h->ke_initial = ke0;
+  std::copy(labs, labs + 4, h->last_abs);
+  h->last_diag_step = lds;
+  h->sticky = s.err;
+  return PIC_OK;
+}
+
+int pic_profile(pic_handle* h, int enable, pic_kernel_times* out) {
+  if (!h) return PIC_EINVAL;
+  if (enable) {
+    h->profiling = true;
+    h->ev_used = 0;
+    h->ev_marks.clear();
+    h->prof_kernels0 = h->kernels;
+    return PIC_OK;
+  }
+  if (!out) return PIC_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  h->profiling = false;
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t k = 1; k < h->ev_marks.size(); ++k) {
+    const int tag = h->ev_marks[k].second;
+    if (tag == kTagStart) continue;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev_pool[h->ev_marks[k - 1].first], h->ev_pool[h->ev_marks[k].first]));
+    switch (tag) {
+      case kTagParticle: out->particle_ms += ms; ++out->particle_launches; break;
+      case kTagFinalize: out->finalize_ms += ms; break;
+      case kTagSort: out->sort_ms += ms; ++out->sorts; break;
+      case kTagField: out->field_ms += ms; ++out->field_solves; break;
+    }
+  }
+  out->kernels_launched = h->kernels - h->prof_kernels0;
+  h->ev_marks.clear();
+  h->ev_used = 0;
+  return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,391 @@
+// field_solve.cu -- FP64 field solve of the PIC step (arXiv 2206.14662,
+// Sec. II.A: finite elements, Dirichlet on the metal walls, Neumann on the
+// open z ends).
+//
+// The finite-element matrix on bilinear elements of the (r,z) grid is
+//   A = 2 pi eps0 (K_r (x) M_z + M_r (x) K_z)
+// with r-weighted 1D matrices K_r, M_r (tridiagonal) and plain 1D matrices
+// K_z, M_z of the uniform z grid with natural (Neumann) end rows.  With
+// W = diag(1/2, 1, ..., 1, 1/2) and the operator Y (Y v)_j = v_{j-1} +
+// v_{j+1}, mirrored at the ends,
+//   K_z = W (2 I - Y) / h_z,   M_z = W h_z (4 I + Y) / 6,
+// and the cosines c_k(j) = cos(pi k j / M), k = 0..M, are the eigenvectors
+// of Y (eigenvalues 2 cos(pi k / M)).  So A separates: a DCT-I along z
+// turns the interior problem into M + 1 independent SPD tridiagonal systems
+// along r, (g_k K_r + f_k M_r) phihat_k = bhat_k, which are solved by
+// pre-factored Thomas sweeps, and the inverse DCT-I returns phi.  The
+// split phi = phi_vac + phi_rho takes the wall potentials into phi_vac, the
+// exact discrete vacuum solution (z-independent, one radial tridiagonal
+// solve on the host).
+//
+// The DCT-I of length M + 1 is the DFT of the even extension of length
+// 2M; two r-lines share one complex FFT as real and imaginary parts (both
+// transforms are real).  A radix-2 FFT runs in shared memory, one block per
+// pair of lines; M not a power of two takes a direct O(M^2) transform.
+//
+// Every solve is checked: ||b - A phi|| / ||b - A_ID phi_D|| over the
+// interior nodes must stay below poisson_rtol, else PIC_ENOCONV is latched.
+#include <cmath>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// ---------------------------------------------------------------- tables
+
+int field_tables_build(const pic_config& cfg, FieldTables& T,
+                       void* (*dev_alloc)(size_t, void*), void* ctx,
+                       cudaStream_t stream) {
+  const int nr = cfg.nr, nz = cfg.nz, M = nz, NI = nr - 1, M1 = M + 1;
+  T.nr = nr; T.nz = nz; T.M = M; T.NI = NI;
+  T.hr = (cfg.r_out - cfg.r_in) / nr;
+  T.hz = (cfg.z_max - cfg.z_min) / nz;
+  T.rtol = cfg.poisson_rtol;
+  int l2 = 0;
+  while ((1 << l2) < 2 * M) ++l2;
+  // FFT path for M a power of two whose 2M-point complex line fits the
+  // default 48 KB of dynamic shared memory; otherwise the direct transform
+  T.log2N = ((1 << l2) == 2 * M && 2 * M * (int)sizeof(double2) <= 48 * 1024) ? l2 : -1;
+  const double hr = T.hr, hz = T.hz;
+
+  std::vector<double> r(nr + 1);
+  for (int i = 0; i <= nr; ++i) r[i] = cfg.r_in + i * hr;
+  std::vector<double> kd(nr + 1, 0.0), ko(nr + 1, 0.0), md(nr + 1, 0.0), mo(nr + 1, 0.0);
+  for (int e = 0; e < nr; ++e) {
+    const double r0 = r[e], r1 = r[e + 1];
+    const double k = (r0 + r1) / (2.0 * hr);
+    kd[e] += k; kd[e + 1] += k; ko[e] = -k;
+    md[e] += hr / 12.0 * (3.0 * r0 + r1);
+    md[e + 1] += hr / 12.0 * (r0 + 3.0 * r1);
+    mo[e] = hr / 12.0 * (r0 + r1);
+  }
+
+  // vacuum solution: K_r restricted to the interior lines with the wall
+  // potentials moved to the right-hand side (M_r and K_z drop out for a
+  // z-independent field)
+  std::vector<double> vac(nr + 1);
+  vac[0] = cfg.v_inner;
+  vac[nr] = cfg.v_outer;
+  {
+    std::vector<double> cp(NI), y(NI);
+    for (int ii = 0; ii < NI; ++ii) {
+      const int i = ii + 1;
+      double rhs = 0.0;
+      if (i == 1) rhs -= ko[0] * cfg.v_inner;
+      if (i == nr - 1) rhs -= ko[nr - 1] * cfg.v_outer;
+      const double sub = ii > 0 ? ko[i - 1] : 0.0;
+      const double den = kd[i] - (ii > 0 ? sub * cp[ii - 1] : 0.0);
+      cp[ii] = ko[i] / den;
+      y[ii] = (rhs - (ii > 0 ? sub * y[ii - 1] : 0.0)) / den;
+    }
+    double xn = 0.0;
+    for (int ii = NI - 1; ii >= 0; --ii) {
+      xn = y[ii] - cp[ii] * xn;
+      vac[ii + 1] = xn;
+    }
+  }
+
+  // per-mode Thomas factors of g_k K_r + f_k M_r on the interior lines
+  std::vector<double> ta((size_t)NI * M1), tinv((size_t)NI * M1), tcp((size_t)NI * M1);
+  std::vector<double> scale(M1);
+  for (int k = 0; k <= M; ++k) {
+    const double lam = 2.0 * std::cos(kPi * k / M);
+    const double g = hz * (4.0 + lam) / 6.0, f = (2.0 - lam) / hz;
+    const double eps_k = (k == 0 || k == M) ? 0.5 : 1.0;
+    scale[k] = 2.0 * eps_k / (M * 2.0 * kPi * kEps0);
+    double cprev = 0.0;
+    for (int ii = 0; ii < NI; ++ii) {
+      const int i = ii + 1;
+      const double diag = g * kd[i] + f * md[i];
+      const double sub = ii > 0 ? g * ko[i - 1] + f * mo[i - 1] : 0.0;
+      const double sup = g * ko[i] + f * mo[i];
+      const double den = diag - sub * cprev;
+      const size_t o = (size_t)ii * M1 + k;
+      ta[o] = sub;
+      tinv[o] = 1.0 / den;
+      tcp[o] = sup / den;
+      cprev = tcp[o];
+    }
+  }
+
+  std::vector<double> tw;   // interleaved (re, im)
+  std::vector<double> ctab;
+  if (T.log2N > 0) {
+    const int N = 2 * M;
+    tw.resize(N);
+    for (int m = 0; m < N / 2; ++m) {
+      tw[2 * m] = std::cos(2.0 * kPi * m / N);
+      tw[2 * m + 1] = -std::sin(2.0 * kPi * m / N);
+    }
+  } else {
+    ctab.resize(2 * M);
+    for (int m = 0; m < 2 * M; ++m) ctab[m] = std::cos(kPi * m / M);
+  }
+
+  auto up = [&](const void* src, size_t bytes, void** dst) -> int {
+    *dst = dev_alloc(bytes, ctx);
+    if (!*dst) return PIC_ENOMEM;
+    if (src && cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+      return PIC_ECUDA;
+    return PIC_OK;
+  };
+  int rc = PIC_OK;
+  T.twiddle = nullptr; T.costab = nullptr;
+  if (T.log2N > 0) rc = rc ? rc : up(tw.data(), tw.size() * sizeof(double), (void**)&T.twiddle);
+  else rc = rc ? rc : up(ctab.data(), ctab.size() * sizeof(double), (void**)&T.costab);
+  rc = rc ? rc : up(scale.data(), scale.size() * sizeof(double), (void**)&T.fwd_scale);
+  rc = rc ? rc : up(ta.data(), ta.size() * sizeof(double), (void**)&T.tri_a);
+  rc = rc ? rc : up(tinv.data(), tinv.size() * sizeof(double), (void**)&T.tri_invd);
+  rc = rc ? rc : up(tcp.data(), tcp.size() * sizeof(double), (void**)&T.tri_cp);
+  rc = rc ? rc : up(vac.data(), vac.size() * sizeof(double), (void**)&T.phi_vac);
+  rc = rc ? rc : up(kd.data(), kd.size() * sizeof(double), (void**)&T.kr_d);
+  rc = rc ? rc : up(ko.data(), ko.size() * sizeof(double), (void**)&T.kr_o);
+  rc = rc ? rc : up(md.data(), md.size() * sizeof(double), (void**)&T.mr_d);
+  rc = rc ? rc : up(mo.data(), mo.size() * sizeof(double), (void**)&T.mr_o);
+  rc = rc ? rc : up(nullptr, (size_t)NI * M1 * sizeof(double), (void**)&T.bhat);
+  rc = rc ? rc : up(nullptr, (size_t)NI * M1 * sizeof(double), (void**)&T.phihat);
+  if (rc == PIC_OK && cudaStreamSynchronize(stream) != cudaSuccess) rc = PIC_ECUDA;
+  return rc;
+}
+
+void field_tables_free(FieldTables& T, void (*dev_free)(void*, void*), void* ctx) {
+  void* ptrs[] = {T.twiddle, T.costab, T.fwd_scale, T.tri_a, T.tri_invd, T.tri_cp,
+                  T.phi_vac, T.kr_d, T.kr_o, T.mr_d, T.mr_o, T.bhat, T.phihat};
+  for (void* p : ptrs)
+    if (p) dev_free(p, ctx);
+}
+
+// ---------------------------------------------------------------- DCT-I
+
+// y_k = sum_{j=0}^{M} x_j cos(pi k j / M) for two lines at once.
+// FWD: lines are interior r-lines 1..nr-1 of the right-hand side, output
+//      bhat[line][k] = scale_k y_k.
+// INV: lines are rows of phihat, output phi[line + 1][k] = phi_vac + y_k.
+template <bool FWD>
+__global__ void __launch_bounds__(512)
+k_dct_fft(const double* __restrict__ in, double* __restrict__ out,
+          const double2* __restrict__ tw, const double* __restrict__ scale,
+          const double* __restrict__ phi_vac, int NI, int M, int log2N) {
+  extern __shared__ double2 sh[];
+  const int N = 2 * M, M1 = M + 1;
+  const int line0 = blockIdx.x * 2;
+  const bool two = line0 + 1 < NI;
+  const double* x = in + (size_t)(FWD ? line0 + 1 : line0) * M1;
+  const double* y = x + M1;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    const int m = n <= M ? n : N - n;
+    sh[__brev(n) >> (32 - log2N)] = make_double2(x[m], two ? y[m] : 0.0);
+  }
+  __syncthreads();
+  for (int s = 1; s <= log2N; ++s) {
+    const int half = 1 << (s - 1), stride = N >> s;
+    for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+      const int pos = t & (half - 1);
+      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
+      const double2 w = __ldg(tw + pos * stride);
+      const double2 a = sh[i0], b = sh[i1];
+      const double2 bw = make_double2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
+      sh[i0] = make_double2(a.x + bw.x, a.y + bw.y);
+      sh[i1] = make_double2(a.x - bw.x, a.y - bw.y);
+    }
+    __syncthreads();
+  }
+  const double x0 = x[0], xM = x[M];
+  const double y0 = two ? y[0] : 0.0, yM = two ? y[M] : 0.0;
+  for (int k = threadIdx.x; k <= M; k += blockDim.x) {
+    const double sg = (k & 1) ? -1.0 : 1.0;
+    const double2 C = sh[k];
+    const double vx = 0.5 * (C.x + x0 + sg * xM);
+    const double vy = 0.5 * (C.y + y0 + sg * yM);
+    if (FWD) {
+      out[(size_t)line0 * M1 + k] = vx * scale[k];
+      if (two) out[(size_t)(line0 + 1) * M1 + k] = vy * scale[k];
+    } else {
+      out[(size_t)(line0 + 1) * M1 + k] = phi_vac[line0 + 1] + vx;
+      if (two) out[(size_t)(line0 + 2) * M1 + k] = phi_vac[line0 + 2] + vy;
+    }
+  }
+}
+
+// direct O(M^2) DCT-I for M that is not a power of two; one line per block
+template <bool FWD>
+__global__ void k_dct_direct(const double* __restrict__ in, double* __restrict__ out,
+                             const double* __restrict__ costab,
+                             const double* __restrict__ scale,
+                             const double* __restrict__ phi_vac, int NI, int M) {
+  extern __shared__ double xs[];
+  const int M1 = M + 1, line = blockIdx.x;
+  const double* x = in + (size_t)(FWD ? line + 1 : line) * M1;
+  for (int j = threadIdx.x; j <= M; j += blockDim.x) xs[j] = x[j];
+  __syncthreads();
+  for (int k = threadIdx.x; k <= M; k += blockDim.x) {
+    double acc = 0.0;
+    int m = 0;   // (k j) mod 2M
+    for (int j = 0; j <= M; ++j) {
+      acc += xs[j] * costab[m];
+      m += k;
+      if (m >= 2 * M) m -= 2 * M;
+    }
+    if (FWD) out[(size_t)line * M1 + k] = acc * scale[k];
+    else out[(size_t)(line + 1) * M1 + k] = phi_vac[line + 1] + acc;
+  }
+}
+
+// ------------------------------------------------------------- tridiag
+
+// one thread per z-mode: forward and back substitution of the pre-factored
+// Thomas recurrence along the interior r-lines
+__global__ void k_tridiag(const double* __restrict__ bhat, double* phihat,
+                          const double* __restrict__ a, const double* __restrict__ invd,
+                          const double* __restrict__ cp, int NI, int M1) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M1) return;
+  double y = 0.0;
+#pragma unroll 8
+  for (int i = 0; i < NI; ++i) {
+    const size_t o = (size_t)i * M1 + k;
+    y = (bhat[o] - a[o] * y) * invd[o];
+    phihat[o] = y;
+  }
+  double xn = 0.0;
+#pragma unroll 8
+  for (int i = NI - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M1 + k;
+    xn = phihat[o] - cp[o] * xn;
+    phihat[o] = xn;
+  }
+}
+
+// ------------------------------------------- E = -grad phi, residual check
+
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_efield_residual(const double* __restrict__ phi, double* rhs, double* rho_last,
+                  typename Vec2<Real>::type* E, FieldTables T, DevState* st,
+                  bool zero_rhs) {
+  const int nr = T.nr, M = T.M, M1 = M + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  double rn = 0.0, rd = 0.0;
+  if (i <= nr && j <= M) {
+    const size_t o = (size_t)i * M1 + j;
+    const double inv2hr = 0.5 / T.hr, inv2hz = 0.5 / T.hz;
+    double dr, dz;
+    if (i == 0) dr = (-3.0 * phi[o] + 4.0 * phi[o + M1] - phi[o + 2 * M1]) * inv2hr;
+    else if (i == nr) dr = (3.0 * phi[o] - 4.0 * phi[o - M1] + phi[o - 2 * M1]) * inv2hr;
+    else dr = (phi[o + M1] - phi[o - M1]) * inv2hr;
+    if (j == 0) dz = (-3.0 * phi[o] + 4.0 * phi[o + 1] - phi[o + 2]) * inv2hz;
+    else if (j == M) dz = (3.0 * phi[o] - 4.0 * phi[o - 1] + phi[o - 2]) * inv2hz;
+    else dz = (phi[o + 1] - phi[o - 1]) * inv2hz;
+    typename Vec2<Real>::type e;
+    e.x = (Real)(-dr);
+    e.y = (Real)(-dz);
+    E[o] = e;
+
+    const double b = rhs[o];
+    if (i > 0 && i < nr) {
+      // z operators of the 1D matrices on line i + di
+      const double hz = T.hz;
+      const bool end = (j == 0 || j == M);
+      const double mzd = end ? hz / 3.0 : 2.0 * hz / 3.0, mzo = hz / 6.0;
+      const double kzd = end ? 1.0 / hz : 2.0 / hz, kzo = -1.0 / hz;
+      double acc = 0.0;
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const size_t q = o + (ptrdiff_t)di * M1;
+        const double c = phi[q];
+        const double l = j > 0 ? phi[q - 1] : 0.0;
+        const double rr = j < M ? phi[q + 1] : 0.0;
+        const double mz = mzd * c + mzo * ((j > 0 ? l : 0.0) + (j < M ? rr : 0.0));
+        const double kz = kzd * c + kzo * ((j > 0 ? l : 0.0) + (j < M ? rr : 0.0));
+        double kr, mr;
+        if (di == 0) { kr = T.kr_d[i]; mr = T.mr_d[i]; }
+        else if (di < 0) { kr = T.kr_o[i - 1]; mr = T.mr_o[i - 1]; }
+        else { kr = T.kr_o[i]; mr = T.mr_o[i]; }
+        acc += kr * mz + mr * kz;
+      }
+      const double twopieps = 2.0 * kPi * kEps0;
+      const double res = b - twopieps * acc;
+      const double zsum = end ? 0.5 * hz : hz;
+      double lift = 0.0;
+      if (i == 1) lift += twopieps * T.kr_o[0] * zsum * phi[j];
+      if (i == nr - 1) lift += twopieps * T.kr_o[nr - 1] * zsum * phi[(size_t)nr * M1 + j];
+      rn = res * res;
+      rd = (b - lift) * (b - lift);
+    }
+    if (zero_rhs) {
+      rho_last[o] = b;
+      rhs[o] = 0.0;
+    }
+  }
+  // block reduction, then the last block evaluates the check
+  __shared__ double red[2][8];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, w = tid >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rn += __shfl_xor_sync(0xffffffffu, rn, o);
+    rd += __shfl_xor_sync(0xffffffffu, rd, o);
+  }
+  if (lane == 0) { red[0][w] = rn; red[1][w] = rd; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x * blockDim.y) / 32; ++k) { a += red[0][k]; b += red[1][k]; }
+    if (a != 0.0) atomicAdd(&st->res_num, a);
+    if (b != 0.0) atomicAdd(&st->res_den, b);
+    __threadfence();
+    const unsigned nb = gridDim.x * gridDim.y;
+    if (atomicAdd(&st->solve_blocks_done, 1u) == nb - 1) {
+      __threadfence();
+      const double num = *(volatile double*)&st->res_num;
+      const double den = *(volatile double*)&st->res_den;
+      const double rel = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? 1.0 : 0.0);
+      st->relres_last = rel;
+      st->poisson_iters = 1;
+      if (!(rel <= T.rtol)) atomicCAS(&st->err, 0, PIC_ENOCONV);
+      st->res_num = 0.0;
+      st->res_den = 0.0;
+      st->solve_blocks_done = 0u;
+    }
+  }
+}
+
+template <typename Real>
+void launch_field_solve(const FieldTables& T, double* rhs, double* phi,
+                        void* efield, double* rho_last, DevState* st,
+                        bool zero_rhs, cudaStream_t stream) {
+  const int M1 = T.M + 1, nlines = T.NI;
+  if (T.log2N > 0) {
+    const int N = 2 * T.M;
+    const int threads = std::min(512, std::max(64, N / 2));
+    const size_t smem = (size_t)N * sizeof(double2);
+    const int blocks = (nlines + 1) / 2;
+    k_dct_fft<true><<<blocks, threads, smem, stream>>>(rhs, T.bhat, T.twiddle, T.fwd_scale,
+                                                       T.phi_vac, nlines, T.M, T.log2N);
+    k_tridiag<<<(M1 + 127) / 128, 128, 0, stream>>>(T.bhat, T.phihat, T.tri_a, T.tri_invd,
+                                                    T.tri_cp, nlines, M1);
+    k_dct_fft<false><<<blocks, threads, smem, stream>>>(T.phihat, phi, T.twiddle, T.fwd_scale,
+                                                        T.phi_vac, nlines, T.M, T.log2N);
+  } else {
+    const size_t smem = (size_t)M1 * sizeof(double);
+    k_dct_direct<true><<<nlines, 256, smem, stream>>>(rhs, T.bhat, T.costab, T.fwd_scale,
+                                                      T.phi_vac, nlines, T.M);
+    k_tridiag<<<(M1 + 127) / 128, 128, 0, stream>>>(T.bhat, T.phihat, T.tri_a, T.tri_invd,
+                                                    T.tri_cp, nlines, M1);
+    k_dct_direct<false><<<nlines, 256, smem, stream>>>(T.phihat, phi, T.costab, T.fwd_scale,
+                                                       T.phi_vac, nlines, T.M);
+  }
+  if (efield) {
+    dim3 blk(32, 8), grd((M1 + 31) / 32, (T.nr + 1 + 7) / 8);
+    k_efield_residual<Real><<<grd, blk, 0, stream>>>(
+        phi, rhs, rho_last, (typename Vec2<Real>::type*)efield, T, st, zero_rhs);
+  }
+}
+
+template void launch_field_solve<float>(const FieldTables&, double*, double*, void*, double*,
+                                        DevState*, bool, cudaStream_t);
+template void launch_field_solve<double>(const FieldTables&, double*, double*, void*, double*,
+                                         DevState*, bool, cudaStream_t);
+
+}  // namespace pic

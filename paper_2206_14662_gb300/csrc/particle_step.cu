@@ -1,0 +1,645 @@
+// particle_step.cu -- the fused particle kernel of one PIC step and the
+// small kernels around it (load, export, child-uid assignment, kinetic
+// energy).  Method: arXiv 2206.14662, Sec. II.A.
+//
+// One pass over the particle store per step; per particle:
+//   gather   bilinear E from the node grid (FP32 or FP64 copy of -grad phi),
+//            analytic B (uniform, or the mirror field of A_theta = r Bz / 2)
+//   push     Boris half kick / rotation / half kick in the local (r,theta,z)
+//            basis, straight move in the local Cartesian frame, rotation of
+//            (vr, vtheta) into the basis at the new position
+//   absorb   perfectly absorbing walls, first crossing of the (r,z) segment
+//   collide  null-collision Monte Carlo: one Philox4x32-10 call per particle
+//            (candidate, type, scattering angle, azimuth); ionisation takes
+//            a second call (energy share, secondary angles) and appends a
+//            child whose uid is fixed after the kernel by parent-uid rank
+//   deposit  b_i += q w Lambda_i: the block's particles accumulate the hat
+//            weights into a shared-memory tile spanning their node bounding
+//            box, flushed to the FP64 grid with one atomic per touched node;
+//            blocks whose particles are spread too wide deposit directly.
+//
+// Memory traffic per particle-step: 28 B read (cell, two offsets, three
+// velocity components, uid) and 24 B written (all but the uid) in FP32.
+#include <cfloat>
+#include <climits>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+constexpr int kThreads = 256;
+constexpr int kPPT = 4;                 // particles per thread per chunk
+constexpr int kChunk = kThreads * kPPT;
+
+template <typename Real> struct TileT { using type = float; static constexpr int cap = 4096; };
+template <> struct TileT<double> { using type = double; static constexpr int cap = 2048; };
+
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float d_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double d_floor(double x) { return floor(x); }
+__device__ __forceinline__ void d_sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void d_sincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ float d_tan(float x) { return tanf(x); }
+__device__ __forceinline__ double d_tan(double x) { return tan(x); }
+__device__ __forceinline__ float d_atan(float x) { return atanf(x); }
+__device__ __forceinline__ double d_atan(double x) { return atan(x); }
+
+__device__ __forceinline__ void set_error(DevState* st, int code) {
+  atomicCAS(&st->err, 0, code);
+}
+
+// Direction after scattering through chi about the unit vector (vr,vt,vz):
+// mu = cos chi from the inverse CDF of the pdf ~ (1 - xi mu)^-2,
+// mu = 1 - 2u(1 - xi)/(1 + xi(1 - 2u)); azimuth 2 pi u_phi measured from
+// e1 = (v x zhat)/|v x zhat| (rhat instead of zhat within 1e-6 of the
+// axis), e2 = v x e1.
+template <typename Real>
+__device__ __forceinline__ void scatter_dir(Real vr, Real vt, Real vz,
+                                            Real u_chi, Real u_phi, Real xi,
+                                            Real& dr, Real& dt, Real& dz) {
+  const Real one = 1;
+  const Real mu = one - 2 * u_chi * (one - xi) / (one + xi * (one - 2 * u_chi));
+  const Real sn = d_sqrt(fmax(Real(0), one - mu * mu));
+  Real sp, cp;
+  d_sincospi(2 * u_phi, &sp, &cp);
+  Real e1r = vt, e1t = -vr, e1z = 0;
+  Real n1 = d_sqrt(vr * vr + vt * vt);
+  if (n1 < Real(1e-6)) {
+    e1r = 0; e1t = vz; e1z = -vt;
+    n1 = d_sqrt(vz * vz + vt * vt);
+  }
+  const Real in1 = one / n1;
+  e1r *= in1; e1t *= in1; e1z *= in1;
+  const Real e2r = vt * e1z - vz * e1t;
+  const Real e2t = vz * e1r - vr * e1z;
+  const Real e2z = vr * e1t - vt * e1r;
+  dr = mu * vr + sn * (cp * e1r + sp * e2r);
+  dt = mu * vt + sn * (cp * e1t + sp * e2t);
+  dz = mu * vz + sn * (cp * e1z + sp * e2z);
+}
+
+// per-block tallies in shared memory (raw: counts, weights in macro units,
+// energies per macro-electron; scaled by the weight at the flush)
+struct BlockTally {
+  double v[kTallyCount];
+};
+
+template <typename Real>
+struct Dep {
+  int ir, iz;   // ir < 0: nothing to deposit
+  Real fr, fz;
+};
+
+template <typename Real>
+__device__ __forceinline__ void deposit_global(double* rhs, int nzp, int ir,
+                                               int iz, Real fr, Real fz,
+                                               double qw) {
+  const int n00 = ir * nzp + iz;
+  const double a = (double)fr, c = (double)fz;
+  atomicAdd(rhs + n00, qw * ((1.0 - a) * (1.0 - c)));
+  atomicAdd(rhs + n00 + nzp, qw * (a * (1.0 - c)));
+  atomicAdd(rhs + n00 + 1, qw * ((1.0 - a) * c));
+  atomicAdd(rhs + n00 + nzp + 1, qw * (a * c));
+}
+
+// Gather, push, absorb and collide one particle held in registers.
+// Returns the deposit location of the particle (ir < 0 when absorbed).
+template <typename Real>
+__device__ __forceinline__ Dep<Real> advance(
+    long long p, int cell, Real fr, Real fz, Real vr, Real vt, Real vz,
+    unsigned uid, const typename Vec2<Real>::type* __restrict__ E,
+    const Soa<Real>& s, double* rhs, DevState* st, unsigned* spawn_parent,
+    long long n_slots, unsigned step, const PushParams<Real>& P,
+    BlockTally& bt, Real& work) {
+  using V2 = typename Vec2<Real>::type;
+  Dep<Real> dep;
+  const int nzp = P.nz + 1;
+  int ir = cell >> 16, iz = cell & 0xFFFF;
+  const Real r = P.r_in + ((Real)ir + fr) * P.hr;
+  const Real z = P.z_min + ((Real)iz + fz) * P.hz;
+
+  // gather: bilinear weights of the four nodes of the cell
+  const int n00 = ir * nzp + iz;
+  const V2 e00 = __ldg(E + n00), e01 = __ldg(E + n00 + 1);
+  const V2 e10 = __ldg(E + n00 + nzp), e11 = __ldg(E + n00 + nzp + 1);
+  const Real w00 = (1 - fr) * (1 - fz), w10 = fr * (1 - fz);
+  const Real w01 = (1 - fr) * fz, w11 = fr * fz;
+  const Real Er = w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x;
+  const Real Ez = w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y;
+  Real Br = 0, Bz = P.b0;
+  if (P.bkind == 1) {
+    const Real zeta = z - P.z_mid;
+    Bz = P.b0 * (1 + 2 * zeta * zeta * P.inv_L2);
+    Br = -2 * P.b0 * r * zeta * P.inv_L2;
+  }
+
+  // Boris: half kick, rotation about B, half kick (components r, theta, z)
+  const Real vmr = vr + P.qmdt2 * Er, vmt = vt, vmz = vz + P.qmdt2 * Ez;
+  const Real tr = P.qmdt2 * Br, tz = P.qmdt2 * Bz;
+  const Real sf = 2 / (1 + tr * tr + tz * tz);
+  const Real sr = sf * tr, sz = sf * tz;
+  const Real qr = vmr + vmt * tz;
+  const Real qt = vmt + (vmz * tr - vmr * tz);
+  const Real qz = vmz - vmt * tr;
+  const Real vpr = vmr + qt * sz;
+  const Real vpt = vmt + (qz * sr - qr * sz);
+  const Real vpz = vmz - qt * sr;
+  const Real vnr = vpr + P.qmdt2 * Er, vnt = vpt, vnz = vpz + P.qmdt2 * Ez;
+  // work of the two half kicks, (q dt / 4) E . (v + v- + v+ + v_new)
+  work += Er * (vr + vmr + vpr + vnr) + Ez * (vz + vmz + vpz + vnz);
+
+  // move in the local Cartesian frame; the radial step is formed without
+  // cancellation: r1 - r = dt (2 r vr + (vr^2 + vt^2) dt) / (r + r1)
+  const Real x = r + vnr * P.dt, y = vnt * P.dt;
+  const Real r1 = d_sqrt(x * x + y * y);
+  const Real dr_cells =
+      P.dt * (2 * r * vnr + (vnr * vnr + vnt * vnt) * P.dt) / (r + r1) * P.inv_hr;
+  const Real dz_cells = vnz * P.dt * P.inv_hz;
+  Real fr1 = fr + dr_cells, fz1 = fz + dz_cells;
+  // cell jumps beyond +-2^20 cells (non-physical speeds) are clamped before
+  // the integer conversion; they end outside the grid and are absorbed
+  const Real jmax = Real(1048576);
+  Real flr = fmin(fmax(d_floor(fr1), -jmax), jmax);
+  Real flz = fmin(fmax(d_floor(fz1), -jmax), jmax);
+  int ir1 = ir + (int)flr, iz1 = iz + (int)flz;
+  fr1 -= flr;
+  fz1 -= flz;
+  if (fr1 >= 1) { fr1 = 0; ++ir1; }
+  if (fz1 >= 1) { fz1 = 0; ++iz1; }
+
+  // absorbing walls: r1 <= a, r1 >= b, z1 <= z_min, z1 >= z_max
+  const bool out_in = ir1 < 0 || (ir1 == 0 && fr1 == 0);
+  const bool out_out = ir1 >= P.nr;
+  const bool out_zl = iz1 < 0 || (iz1 == 0 && fz1 == 0);
+  const bool out_zh = iz1 >= P.nz;
+  if (out_in || out_out || out_zl || out_zh) {
+    // first crossing along the straight (r,z) segment, ties in the order
+    // inner, outer, z_min, z_max
+    const Real s0r = (Real)ir + fr, s0z = (Real)iz + fz;
+    Real tb = 3;
+    int wall = 0;
+    if (out_in) { Real t = -s0r / dr_cells; if (t < tb) { tb = t; wall = 0; } }
+    if (out_out) { Real t = ((Real)P.nr - s0r) / dr_cells; if (t < tb) { tb = t; wall = 1; } }
+    if (out_zl) { Real t = -s0z / dz_cells; if (t < tb) { tb = t; wall = 2; } }
+    if (out_zh) { Real t = ((Real)P.nz - s0z) / dz_cells; if (t < tb) { tb = t; wall = 3; } }
+    atomicAdd(&bt.v[kAbsInner + wall], 1.0);
+    atomicAdd(&bt.v[kKeAbsorbed], (double)(P.half_m * (vnr * vnr + vnt * vnt + vnz * vnz)));
+    atomicAdd(&bt.v[kNAbsorbed], 1.0);
+    s.cell[p] = -1;
+    dep.ir = -1;
+    return dep;
+  }
+
+  // rotate (vr, vtheta) into the basis at the new position
+  const Real ir1f = 1 / r1;
+  const Real c = x * ir1f, sn = y * ir1f;
+  Real ur = c * vnr + sn * vnt;
+  Real ut = -sn * vnr + c * vnt;
+  Real uz = vnz;
+
+  // null-collision Monte Carlo
+  const uint4 xr = philox4x32_10(make_uint4(uid, 0u, step, 0u), P.seed_lo, P.seed_hi);
+  if ((xr.x >> 8) < P.thr_null) {
+    atomicAdd(&bt.v[kNCandidate], 1.0);
+    const Real v2 = ur * ur + ut * ut + uz * uz;
+    const Real speed = d_sqrt(v2);
+    const Real Ek = P.half_m * v2;
+    const Real nu_el = P.nsig_el * speed;
+    Real sig_io = 0;
+    if (Ek > P.e_th) {
+      const Real q = (Ek - P.e_th) * P.e_span_inv;
+      sig_io = P.sig_pk * 2 * q / (1 + q * q);
+    }
+    const Real nu_io = P.n_gas * sig_io * speed;
+    if (nu_el + nu_io > P.nu_max) atomicAdd(&bt.v[kNOver], 1.0);
+    const Real x1 = u01<Real>(xr.y) * P.nu_max;
+    if (x1 < nu_el + nu_io) {
+      const Real inv_s = 1 / speed;
+      const Real hr_ = ur * inv_s, ht_ = ut * inv_s, hz_ = uz * inv_s;
+      if (x1 < nu_el) {
+        Real dr, dt, dz;
+        scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), P.xi, dr, dt, dz);
+        Real E1 = Ek;
+        if (P.recoil != 0) {
+          const Real mu = dr * hr_ + dt * ht_ + dz * hz_;
+          E1 = Ek * (1 - P.recoil * (1 - mu));
+          atomicAdd(&bt.v[kRecoilLoss], (double)(Ek - E1));
+        }
+        const Real s1 = d_sqrt(P.two_over_m * E1);
+        ur = s1 * dr; ut = s1 * dt; uz = s1 * dz;
+        atomicAdd(&bt.v[kNElastic], 1.0);
+      } else {
+        const uint4 x2 = philox4x32_10(make_uint4(uid, 0u, step, 1u), P.seed_lo, P.seed_hi);
+        const Real E_rem = Ek - P.e_th;
+        const Real E2 = P.opal_b * d_tan(u01<Real>(x2.x) * d_atan(E_rem / (2 * P.opal_b)));
+        const Real E1 = E_rem - E2;
+        Real d1r, d1t, d1z, d2r, d2t, d2z;
+        scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), P.xi, d1r, d1t, d1z);
+        scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(x2.y), u01<Real>(x2.z), P.xi, d2r, d2t, d2z);
+        const Real s1 = d_sqrt(P.two_over_m * E1), s2 = d_sqrt(P.two_over_m * E2);
+        ur = s1 * d1r; ut = s1 * d1t; uz = s1 * d1z;
+        atomicAdd(&bt.v[kIonLoss], (double)P.e_th);
+        atomicAdd(&bt.v[kNIonise], 1.0);
+        const long long k = atomicAdd((unsigned long long*)&st->n_spawn, 1ull);
+        const long long slot = n_slots + k;
+        if (k < P.spawn_cap && slot < P.capacity) {
+          s.cell[slot] = (ir1 << 16) | iz1;
+          s.offr[slot] = fr1;
+          s.offz[slot] = fz1;
+          s.vr[slot] = s2 * d2r;
+          s.vt[slot] = s2 * d2t;
+          s.vz[slot] = s2 * d2z;
+          s.uid[slot] = 0u;   // fixed by the child-uid kernel
+          spawn_parent[k] = uid;
+          deposit_global<Real>(rhs, nzp, ir1, iz1, fr1, fz1, P.qw);
+        } else {
+          set_error(st, PIC_ECAPACITY);
+        }
+      }
+    }
+  }
+
+  s.cell[p] = (ir1 << 16) | iz1;
+  s.offr[p] = fr1;
+  s.offz[p] = fz1;
+  s.vr[p] = ur;
+  s.vt[p] = ut;
+  s.vz[p] = uz;
+  dep.ir = ir1; dep.iz = iz1; dep.fr = fr1; dep.fz = fz1;
+  return dep;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kThreads)
+k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E,
+                double* __restrict__ rhs, DevState* st,
+                unsigned* __restrict__ spawn_parent, PushParams<Real> P) {
+  using TT = typename TileT<Real>::type;
+  constexpr int kCap = TileT<Real>::cap;
+  __shared__ TT tile[kCap];
+  __shared__ int bbox[2][4];   // min ir, max ir, min iz, max iz
+  __shared__ BlockTally bt;
+
+  const int tid = threadIdx.x, lane = tid & 31;
+  const long long n_slots = *(volatile long long*)&st->n_slots;
+  const unsigned step = *(volatile unsigned*)&st->step;
+  const int nzp = P.nz + 1;
+  if (tid < kTallyCount) bt.v[tid] = 0.0;
+  if (tid < 8) {
+    bbox[tid >> 2][tid & 3] = (tid & 1) ? INT_MIN : INT_MAX;
+  }
+  __syncthreads();
+  Real work = 0;
+  int pushed = 0;
+  int buf = 0;
+
+  for (long long base = (long long)blockIdx.x * kChunk; base < n_slots;
+       base += (long long)gridDim.x * kChunk) {
+    // load the chunk's particles first (coalesced, one field array at a
+    // time) so that all loads are in flight before any arithmetic
+    int cell[kPPT];
+    Real fr[kPPT], fz[kPPT], vr[kPPT], vt[kPPT], vz[kPPT];
+    unsigned uid[kPPT];
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+      const long long p = base + k * kThreads + tid;
+      const bool in = p < n_slots;
+      cell[k] = in ? s.cell[p] : -1;
+      fr[k] = in ? s.offr[p] : Real(0);
+      fz[k] = in ? s.offz[p] : Real(0);
+      vr[k] = in ? s.vr[p] : Real(0);
+      vt[k] = in ? s.vt[p] : Real(0);
+      vz[k] = in ? s.vz[p] : Real(0);
+      uid[k] = in ? s.uid[p] : 0u;
+    }
+    Dep<Real> dep[kPPT];
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+      const long long p = base + k * kThreads + tid;
+      dep[k].ir = -1;
+      if (cell[k] >= 0) {
+        ++pushed;
+        dep[k] = advance<Real>(p, cell[k], fr[k], fz[k], vr[k], vt[k], vz[k], uid[k], E,
+                               s, rhs, st, spawn_parent, n_slots, step, P, bt, work);
+      }
+    }
+
+    // bounding box of the chunk's deposit cells
+    int lo_r = INT_MAX, hi_r = INT_MIN, lo_z = INT_MAX, hi_z = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+      if (dep[k].ir >= 0) {
+        lo_r = min(lo_r, dep[k].ir); hi_r = max(hi_r, dep[k].ir);
+        lo_z = min(lo_z, dep[k].iz); hi_z = max(hi_z, dep[k].iz);
+      }
+    }
+    lo_r = __reduce_min_sync(0xffffffffu, lo_r);
+    hi_r = __reduce_max_sync(0xffffffffu, hi_r);
+    lo_z = __reduce_min_sync(0xffffffffu, lo_z);
+    hi_z = __reduce_max_sync(0xffffffffu, hi_z);
+    if (lane == 0 && lo_r <= hi_r) {
+      atomicMin(&bbox[buf][0], lo_r); atomicMax(&bbox[buf][1], hi_r);
+      atomicMin(&bbox[buf][2], lo_z); atomicMax(&bbox[buf][3], hi_z);
+    }
+    __syncthreads();
+    const int br0 = bbox[buf][0], br1 = bbox[buf][1];
+    const int bz0 = bbox[buf][2], bz1 = bbox[buf][3];
+    if (tid < 4) bbox[buf ^ 1][tid] = (tid & 1) ? INT_MIN : INT_MAX;
+    const int rows = br1 - br0 + 2, cols = bz1 - bz0 + 2;
+    const bool any = br0 <= br1;
+    const bool use_tile = any && rows * cols <= kCap;
+    if (use_tile) {
+      for (int t = tid; t < rows * cols; t += kThreads) tile[t] = TT(0);
+    }
+    __syncthreads();
+    if (use_tile) {
+#pragma unroll
+      for (int k = 0; k < kPPT; ++k) {
+        if (dep[k].ir >= 0) {
+          const int t = (dep[k].ir - br0) * cols + (dep[k].iz - bz0);
+          const TT a = (TT)dep[k].fr, c = (TT)dep[k].fz;
+          atomicAdd(&tile[t], (TT(1) - a) * (TT(1) - c));
+          atomicAdd(&tile[t + cols], a * (TT(1) - c));
+          atomicAdd(&tile[t + 1], (TT(1) - a) * c);
+          atomicAdd(&tile[t + cols + 1], a * c);
+        }
+      }
+    } else if (any) {
+#pragma unroll
+      for (int k = 0; k < kPPT; ++k)
+        if (dep[k].ir >= 0)
+          deposit_global<Real>(rhs, nzp, dep[k].ir, dep[k].iz, dep[k].fr, dep[k].fz, P.qw);
+    }
+    __syncthreads();
+    if (use_tile) {
+      for (int t = tid; t < rows * cols; t += kThreads) {
+        const TT v = tile[t];
+        if (v != TT(0)) {
+          const int rr = t / cols, cc = t - rr * cols;
+          atomicAdd(rhs + (br0 + rr) * nzp + (bz0 + cc), P.qw * (double)v);
+        }
+      }
+    }
+    buf ^= 1;
+  }
+
+  // block tallies: the work sum, then one global atomic per non-zero slot
+  double w = (double)work;
+  int np = __reduce_add_sync(0xffffffffu, pushed);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  if (lane == 0 && w != 0.0) atomicAdd(&bt.v[kWorkE], w);
+  if (lane == 0 && np != 0) atomicAdd(&bt.v[kNPushed], (double)np);
+  __syncthreads();
+  if (tid < kTallyCount) {
+    double v = bt.v[tid];
+    if (v != 0.0) {
+      if (tid <= kAbsZmax) v *= P.weight;
+      else if (tid == kWorkE) v *= (double)P.work_scale * P.weight;
+      else if (tid <= kRecoilLoss) v *= P.weight;
+      atomicAdd(&st->tally[tid], v);
+    }
+  }
+}
+
+template <typename Real>
+void launch_particle_step(const Soa<Real>& s, const void* efield, double* rhs,
+                          DevState* st, unsigned* spawn_parent,
+                          const PushParams<Real>& P, int grid,
+                          cudaStream_t stream) {
+  k_particle_step<Real><<<grid, kThreads, 0, stream>>>(
+      s, (const typename Vec2<Real>::type*)efield, rhs, st, spawn_parent, P);
+}
+
+// ------------------------------------------------------------ child uids
+
+// Children of this step get uid_next + k, k the rank of the parent's uid
+// among this step's ionising parents; then the step counter advances.
+__global__ void k_spawn_finalize(DevState* st, unsigned* uid,
+                                 const unsigned* __restrict__ parent,
+                                 long long spawn_cap, long long capacity) {
+  const long long ns_raw = st->n_spawn;
+  const long long base = st->n_slots;
+  long long ns = ns_raw < spawn_cap ? ns_raw : spawn_cap;
+  if (base + ns > capacity) ns = capacity - base;
+  const unsigned long long next = st->uid_next;
+  if (next + (unsigned long long)ns > 0xFFFFFFFFull) {
+    if (threadIdx.x == 0) atomicCAS(&st->err, 0, PIC_ECAPACITY);
+  }
+  for (long long i = threadIdx.x; i < ns; i += blockDim.x) {
+    const unsigned pu = parent[i];
+    long long rank = 0;
+    for (long long j = 0; j < ns; ++j) rank += parent[j] < pu;
+    uid[base + i] = (unsigned)(next + (unsigned long long)rank);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->n_slots = base + ns;
+    st->uid_next = next + (unsigned long long)ns;
+    st->n_spawn = 0;
+    st->step = st->step + 1u;
+  }
+}
+
+void launch_spawn_finalize(DevState* st, unsigned* uid, const unsigned* parent,
+                           long long spawn_cap, long long capacity,
+                           cudaStream_t stream) {
+  k_spawn_finalize<<<1, 1024, 0, stream>>>(st, uid, parent, spawn_cap, capacity);
+}
+
+// ------------------------------------------------------------------ load
+
+template <typename Real>
+__global__ void k_load(const double* __restrict__ r, const double* __restrict__ z,
+                       const double* __restrict__ vr, const double* __restrict__ vt,
+                       const double* __restrict__ vz, const uint64_t* __restrict__ uid,
+                       long long n, Soa<Real> s, double r_in, double inv_hr,
+                       double z_min, double inv_hz, int nr, int nz) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double sr = (r[p] - r_in) * inv_hr, sz = (z[p] - z_min) * inv_hz;
+    int ir = (int)floor(sr), iz = (int)floor(sz);
+    ir = min(max(ir, 0), nr - 1);
+    iz = min(max(iz, 0), nz - 1);
+    Real fr = (Real)(sr - ir), fz = (Real)(sz - iz);
+    if (fr >= Real(1)) fr = nextafter(Real(1), Real(0));
+    if (fz >= Real(1)) fz = nextafter(Real(1), Real(0));
+    if (fr < Real(0)) fr = 0;
+    if (fz < Real(0)) fz = 0;
+    s.cell[p] = (ir << 16) | iz;
+    s.offr[p] = fr;
+    s.offz[p] = fz;
+    s.vr[p] = (Real)vr[p];
+    s.vt[p] = (Real)vt[p];
+    s.vz[p] = (Real)vz[p];
+    s.uid[p] = (unsigned)uid[p];
+  }
+}
+
+// deposit of the loaded particles at their positions (no push)
+template <typename Real>
+__global__ void k_deposit_only(Soa<Real> s, long long n, double* rhs, int nzp,
+                               double qw) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int c = s.cell[p];
+    if (c < 0) continue;
+    deposit_global<Real>(rhs, nzp, c >> 16, c & 0xFFFF, s.offr[p], s.offz[p], qw);
+  }
+}
+
+template <typename Real>
+void launch_load(const double* r, const double* z, const double* vr,
+                 const double* vt, const double* vz, const uint64_t* uid,
+                 long long n, Soa<Real> s, const PushParams<Real>& P,
+                 DevState*, cudaStream_t stream) {
+  if (n <= 0) return;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+  k_load<Real><<<grid, 256, 0, stream>>>(r, z, vr, vt, vz, uid, n, s, (double)P.r_in,
+                                         1.0 / (double)P.hr, (double)P.z_min,
+                                         1.0 / (double)P.hz, P.nr, P.nz);
+}
+
+template <typename Real>
+void launch_deposit_only(const Soa<Real>& s, long long n, double* rhs, int nz,
+                         double qw, cudaStream_t stream) {
+  if (n <= 0) return;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+  k_deposit_only<Real><<<grid, 256, 0, stream>>>(s, n, rhs, nz + 1, qw);
+}
+
+// ---------------------------------------------------------------- export
+
+template <typename Real>
+__global__ void k_export(Soa<Real> s, long long n, double r_in, double hr,
+                         double z_min, double hz, double* r, double* z,
+                         double* vr, double* vt, double* vz,
+                         unsigned long long* uid, int* live) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int c = s.cell[p];
+    live[p] = c >= 0;
+    if (c < 0) continue;
+    r[p] = r_in + ((double)(c >> 16) + (double)s.offr[p]) * hr;
+    z[p] = z_min + ((double)(c & 0xFFFF) + (double)s.offz[p]) * hz;
+    vr[p] = (double)s.vr[p];
+    vt[p] = (double)s.vt[p];
+    vz[p] = (double)s.vz[p];
+    uid[p] = s.uid[p];
+  }
+}
+
+template <typename Real>
+void launch_export(const Soa<Real>& s, long long n_slots,
+                   const PushParams<Real>& P, double* r, double* z,
+                   double* vr, double* vt, double* vz, unsigned long long* uid,
+                   int* live, cudaStream_t stream) {
+  if (n_slots <= 0) return;
+  const int grid = (int)std::min<long long>((n_slots + 255) / 256, 152 * 16);
+  k_export<Real><<<grid, 256, 0, stream>>>(s, n_slots, (double)P.r_in, (double)P.hr,
+                                           (double)P.z_min, (double)P.hz, r, z, vr, vt, vz,
+                                           uid, live);
+}
+
+// ------------------------------------------------------- kinetic energy
+
+template <typename Real>
+__global__ void k_kinetic_energy(Soa<Real> s, const DevState* st, double* out2) {
+  const long long n = st->n_slots;
+  double ke = 0.0, cnt = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (s.cell[p] < 0) continue;
+    const double a = s.vr[p], b = s.vt[p], c = s.vz[p];
+    ke += a * a + b * b + c * c;
+    cnt += 1.0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ke += __shfl_xor_sync(0xffffffffu, ke, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out2, ke);
+    atomicAdd(out2 + 1, cnt);
+  }
+}
+
+template <typename Real>
+void launch_kinetic_energy(const Soa<Real>& s, DevState* st, double* out2,
+                           cudaStream_t stream) {
+  k_kinetic_energy<Real><<<152 * 4, 256, 0, stream>>>(s, st, out2);
+}
+
+// ------------------------------------------------------------- E access
+
+template <typename Real>
+__global__ void k_efield_set(const double* er, const double* ez,
+                             typename Vec2<Real>::type* E, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    typename Vec2<Real>::type v;
+    v.x = (Real)er[i];
+    v.y = (Real)ez[i];
+    E[i] = v;
+  }
+}
+
+template <typename Real>
+__global__ void k_efield_get(const typename Vec2<Real>::type* E, double* out,
+                             int comp, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = comp == 0 ? (double)E[i].x : (double)E[i].y;
+}
+
+template <typename Real>
+void launch_efield_set(const double* er, const double* ez, void* efield,
+                       int nnodes, cudaStream_t stream) {
+  k_efield_set<Real><<<(nnodes + 255) / 256, 256, 0, stream>>>(
+      er, ez, (typename Vec2<Real>::type*)efield, nnodes);
+}
+
+template <typename Real>
+void launch_efield_get(const void* efield, double* out, int component,
+                       int nnodes, cudaStream_t stream) {
+  k_efield_get<Real><<<(nnodes + 255) / 256, 256, 0, stream>>>(
+      (const typename Vec2<Real>::type*)efield, out, component, nnodes);
+}
+
+// ---------------------------------------------------------- instantiate
+
+#define PIC_INSTANTIATE(R)                                                              \
+  template void launch_particle_step<R>(const Soa<R>&, const void*, double*, DevState*, \
+                                        unsigned*, const PushParams<R>&, int,           \
+                                        cudaStream_t);                                  \
+  template void launch_load<R>(const double*, const double*, const double*,             \
+                               const double*, const double*, const uint64_t*,           \
+                               long long, Soa<R>, const PushParams<R>&, DevState*,      \
+                               cudaStream_t);                                           \
+  template void launch_deposit_only<R>(const Soa<R>&, long long, double*, int, double,  \
+                                       cudaStream_t);                                   \
+  template void launch_export<R>(const Soa<R>&, long long, const PushParams<R>&,        \
+                                 double*, double*, double*, double*, double*,           \
+                                 unsigned long long*, int*, cudaStream_t);              \
+  template void launch_kinetic_energy<R>(const Soa<R>&, DevState*, double*,             \
+                                         cudaStream_t);                                 \
+  template void launch_efield_set<R>(const double*, const double*, void*, int,          \
+                                     cudaStream_t);                                     \
+  template void launch_efield_get<R>(const void*, double*, int, int, cudaStream_t);
+
+PIC_INSTANTIATE(float)
+PIC_INSTANTIATE(double)
+
+}  // namespace pic
+
+namespace pic {
+// resident blocks of the fused kernel per SM (sizes its persistent grid)
+int particle_step_blocks_per_sm(int precision) {
+  int b = 0;
+  if (precision == 32)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step<float>, kThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step<double>, kThreads, 0);
+  return b;
+}
+}  // namespace pic

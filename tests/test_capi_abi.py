@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+entry point include/pic.h declares, and the ctypes structures of the
+binding have the C layout (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pic.h")
+
+
+@pytest.fixture(scope="module")
+def libpic():
+    from paper_2206_14662_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(pic_[a-z_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(libpic):
+    names = declared_functions()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(libpic, n), n
+
+
+def test_strerror_without_gpu(libpic):
+    libpic.pic_strerror.restype = ctypes.c_char_p
+    assert libpic.pic_strerror(0) == b"ok"
+    assert b"capacity" in libpic.pic_strerror(-3)
+
+
+def test_binding_struct_layout(tmp_path):
+    from paper_2206_14662_gb300 import _capi
+    structs = {"pic_config": _capi.PicConfig, "pic_diag": _capi.PicDiag,
+               "pic_kernel_times": _capi.PicKernelTimes, "pic_allocator": _capi.PicAllocator}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pic.h"', "int main(void){"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    for line in filter(None, out):
+        cname, field, value = line.split()
+        cls = structs[cname]
+        got = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert got == int(value), (cname, field)
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2206_14662_gb300 import _capi
+    monkeypatch.setattr(_capi, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_capi, "_lib", None)
+    with pytest.raises(RuntimeError):
+        _capi.lib()

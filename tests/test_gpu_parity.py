@@ -1,0 +1,341 @@
+"""CUDA path (through the C ABI) against the CPU oracle on the same seeded
+inputs and the same random streams (arXiv 2206.14662, Sec. II.A).
+
+Tolerances: FP64 particle path 1e-12, FP32 particle path 1e-5 (positions in
+cells, velocities relative to the largest speed, node charges relative to
+the largest); the FP64 field solve to 1e-10 of the potential's scale (two
+exact solvers of one linear system differ by its condition number times the
+rounding unit).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_14662_gb300.inputs import (random_field_node_arrays, seed_particles,
+                                           workload)
+from parity import TOL, by_uid, compare_states, make_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2206_14662_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _collision_cfg(precision, **kw):
+    base = dict(p_mbar=1.0, T0_eV=100.0, n_init=20_000, precision=precision, fixed_efield=1,
+                sort_every=0)
+    base.update(kw)
+    return workload("coax_32x64_1e4", **base)
+
+
+# ------------------------------------------------------------ field solve
+
+@pytest.mark.parametrize("nr,nz", [(32, 64), (128, 512), (20, 48), (7, 6), (2, 2)])
+def test_field_solve_matches_oracle(nr, nz):
+    """Same right-hand side: the separable DCT/Thomas solve against the
+    sparse direct solve of the assembled finite-element system."""
+    from paper_2206_14662_gb300._capi import Simulation
+    cfg = workload("coax_32x64_1e4", nr=nr, nz=nz, precision=64)
+    rng = np.random.default_rng(nr * 1000 + nz)
+    b = -rng.random((nr + 1) * (nz + 1)) * 1e-12
+    with Simulation(cfg) as sim:
+        phi_g, rel = sim.solve_field(b)
+    phi_o = oracle.poisson_solve(cfg, b)
+    scale = np.abs(phi_o).max()
+    assert np.abs(phi_g - phi_o).max() <= 1e-10 * scale
+    assert rel <= 1e-12
+    assert oracle.poisson_relres(cfg, b, phi_g) <= 1e-12
+
+
+def test_vacuum_field_and_efield():
+    """No charge: phi is the exact discrete coaxial solution; E on the
+    nodes equals the oracle's differences of the same phi."""
+    from paper_2206_14662_gb300._capi import PIC_GRID_ER, PIC_GRID_EZ, PIC_GRID_PHI, Simulation
+    for prec in (64, 32):
+        cfg = workload("coax_32x64_1e4", precision=prec)
+        with Simulation(cfg) as sim:
+            phi = sim.get_grid(PIC_GRID_PHI)
+            er, ez = sim.get_grid(PIC_GRID_ER), sim.get_grid(PIC_GRID_EZ)
+        r, _ = oracle.grid(cfg)
+        S = np.concatenate([[0.0], np.cumsum(2.0 / (r[1:] + r[:-1]))])
+        exact = cfg["v_inner"] + (cfg["v_outer"] - cfg["v_inner"]) * S / S[-1]
+        f = phi.reshape(cfg["nr"] + 1, cfg["nz"] + 1)
+        assert np.abs(f - exact[:, None]).max() <= 1e-11 * abs(cfg["v_inner"])
+        er_o, ez_o = oracle.efield(cfg, phi)
+        tol = 1e-12 if prec == 64 else 1e-7
+        assert np.abs(er - er_o).max() <= tol * np.abs(er_o).max()
+        assert np.abs(ez - ez_o).max() <= tol * np.abs(er_o).max()
+
+
+# ------------------------------------------------------ one particle step
+
+def _one_step(cfg, n, seed=3, bkind=0, escale=3e5):
+    cfg = dict(cfg, bfield_kind=bkind)
+    parts = seed_particles(cfg, n=n, seed=seed)
+    er, ez = random_field_node_arrays(cfg, escale, seed=seed + 1)
+    o = oracle.OracleSim(cfg, *parts, efield_nodes=(er, ez), solve_field=False)
+    sim = make_gpu(cfg, parts, efield=(er, ez))
+    uid_before = o.uid.copy()
+    next0 = o.uid_next
+    b0_o = o.b.copy()
+    b0_g = sim.get_grid(1)
+    res = o.step()
+    sim.step(1)
+    d = sim.diagnostics()
+    g = by_uid(sim.export_particles())
+    b_g = sim.get_grid(1)
+    sim.close()
+    return cfg, o, res, d, g, b_g, uid_before, next0, b0_o, b0_g
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("bkind", [0, 1])
+def test_one_step_parity(precision, bkind):
+    """One step from an identical state in an identical field: particle
+    states, children (uids by parent rank), event counts, wall tallies and
+    the deposited charge agree with the oracle."""
+    cfg = _collision_cfg(precision)
+    n = 20_000 + 37          # many chunks and a ragged tail
+    cfg, o, res, d, g, b_g, uid0, next0, b0_o, b0_g = _one_step(cfg, n, bkind=bkind)
+    tol = TOL[precision]
+    # initial deposit
+    assert np.abs(b0_g - b0_o).max() <= tol * np.abs(b0_o).max()
+    amb = compare_states(cfg, precision, g, o, margin=res.margin, uid_before=uid0,
+                         child_uid0=next0)
+    assert amb <= 3
+    assert res.tally[oracle.T_N_ELASTIC] > 100 and res.tally[oracle.T_N_IONISE] > 5
+    assert res.tally[oracle.T_N_ABSORBED] > 0
+    for key, slot in (("n_elastic", oracle.T_N_ELASTIC), ("n_ionise", oracle.T_N_IONISE),
+                      ("n_absorbed", oracle.T_N_ABSORBED), ("n_candidates", oracle.T_N_CANDIDATE)):
+        assert abs(d[key] - res.tally[slot]) <= amb, key
+    if amb == 0:
+        assert np.array_equal(g["uid"][g["uid"] >= next0],
+                              np.arange(next0, next0 + res.n_children, dtype=np.uint64))
+        assert np.abs(b_g - res.b).max() <= tol * np.abs(res.b).max()
+        for w in range(4):
+            assert d["absorbed_weight"][w] == pytest.approx(res.tally[w], rel=1e-12, abs=1e-9)
+        assert d["ion_loss_J"] == pytest.approx(res.tally[oracle.T_ION_LOSS], rel=1e-12)
+        assert d["work_E_J"] == pytest.approx(res.tally[oracle.T_WORK_E], rel=10 * tol)
+    assert d["nu_max"] == pytest.approx(o.P.nu_max, rel=1e-14)
+
+
+def test_many_steps_with_sorting_fp64():
+    """Twelve steps in a fixed field with a counting sort every three steps:
+    the sort, hole removal and child merge leave every particle's history
+    unchanged."""
+    cfg = _collision_cfg(64, sort_every=3, n_init=5000)
+    parts = seed_particles(cfg, n=5000, seed=9)
+    er, ez = random_field_node_arrays(cfg, 3e5, seed=10)
+    o = oracle.OracleSim(cfg, *parts, efield_nodes=(er, ez), solve_field=False)
+    sim = make_gpu(cfg, parts, efield=(er, ez))
+    for _ in range(12):
+        o.step()
+    sim.step(12)
+    g = by_uid(sim.export_particles())
+    d = sim.diagnostics()
+    sim.close()
+    rep = {}
+    compare_states(cfg, 64, g, o, report=rep)
+    assert max(rep.values()) <= 1e-10
+    assert d["n_ionise"] == o.tally[oracle.T_N_IONISE]
+    assert d["n_absorbed"] == o.tally[oracle.T_N_ABSORBED]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_self_consistent_steps(precision):
+    """Ten full steps of the workload "coax_32x64_1e4" (field solve on):
+    particles and the potential follow the oracle."""
+    from paper_2206_14662_gb300._capi import PIC_GRID_PHI
+    cfg = workload("coax_32x64_1e4", precision=precision, p_mbar=0.3, T0_eV=30.0)
+    parts = seed_particles(cfg)
+    o = oracle.OracleSim(cfg, *parts)
+    sim = make_gpu(cfg, parts)
+    for _ in range(10):
+        o.step()
+    sim.step(10)
+    g = by_uid(sim.export_particles())
+    phi = sim.get_grid(PIC_GRID_PHI)
+    d = sim.diagnostics()
+    sim.close()
+    rep = {}
+    tol = 1e-9 if precision == 64 else 2e-5
+    hr = (cfg["r_out"] - cfg["r_in"]) / cfg["nr"]
+    keep = np.isin(o.uid, g["uid"])
+    assert keep.mean() > 0.999
+    assert np.abs(phi - o.phi).max() <= (1e-10 if precision == 64 else 1e-5) * np.abs(o.phi).max()
+    assert d["poisson_relres"] <= 1e-12
+    if precision == 64:
+        compare_states(cfg, 64, g, o, report=rep)
+        assert max(rep.values()) <= tol
+    else:
+        gi = np.searchsorted(g["uid"], o.uid[keep])
+        assert np.abs(g["r"][gi] - o.r[keep]).max() / hr <= tol
+
+
+def test_brute_force_tiny():
+    """N = 1..4 particles over 100 steps, fixed field, FP64: particle by
+    particle."""
+    for n in (1, 2, 3, 4):
+        cfg = _collision_cfg(64, n_init=n, p_mbar=0.05)
+        parts = seed_particles(cfg, n=n, seed=40 + n, margin_cells=4)
+        er, ez = random_field_node_arrays(cfg, 1e5, seed=n)
+        o = oracle.OracleSim(cfg, *parts, efield_nodes=(er, ez), solve_field=False)
+        sim = make_gpu(cfg, parts, efield=(er, ez))
+        for _ in range(100):
+            o.step()
+        sim.step(100)
+        g = by_uid(sim.export_particles())
+        sim.close()
+        rep = {}
+        compare_states(cfg, 64, g, o, report=rep)
+        assert max(rep.values()) <= 1e-11
+
+
+# --------------------------------------------------------------- edges
+
+def test_empty_and_all_absorbed():
+    from paper_2206_14662_gb300._capi import Simulation
+    cfg = workload("coax_32x64_1e4", precision=32)
+    with Simulation(cfg) as sim:
+        e = np.zeros(0)
+        sim.load_particles(e, e, e, e, e, np.zeros(0, dtype=np.uint64))
+        sim.step(5)
+        assert sim.diagnostics()["n_particles"] == 0
+    # every particle is fast and radial: all reach a wall in one step
+    with Simulation(cfg) as sim:
+        n = 3000
+        r = np.full(n, 5e-3); z = np.linspace(-0.019, 0.019, n)
+        v = np.full(n, 1e10)
+        sim.load_particles(r, z, v, np.zeros(n), np.zeros(n), np.arange(n, dtype=np.uint64))
+        sim.step(1)
+        d = sim.diagnostics()
+        assert d["n_particles"] == 0 and d["n_absorbed"] == n
+        assert d["absorbed_weight"][1] == pytest.approx(n * d["weight"])
+        sim.step(3)
+        assert sim.diagnostics()["n_particles"] == 0
+
+
+def test_capacity_overflow_is_reported():
+    from paper_2206_14662_gb300._capi import PIC_ECAPACITY, PicError, Simulation
+    cfg = _collision_cfg(32, p_mbar=30.0, T0_eV=300.0, capacity=1000, n_init=1000, fixed_efield=1,
+                         sigma_el=1e-22)
+    parts = seed_particles(cfg, n=1000, seed=5)
+    with Simulation(cfg) as sim:
+        sim.load_particles(*parts)
+        sim.step(3)
+        with pytest.raises(PicError) as ei:
+            sim.diagnostics()
+        assert ei.value.code == PIC_ECAPACITY
+        with pytest.raises(PicError):
+            sim.step(1)
+
+
+def test_invalid_inputs_rejected():
+    from paper_2206_14662_gb300._capi import PIC_EINVAL, PicError, Simulation
+    with pytest.raises(PicError) as ei:
+        Simulation(workload("coax_32x64_1e4", nr=1))
+    assert ei.value.code == PIC_EINVAL
+    with pytest.raises(PicError):
+        Simulation(workload("coax_32x64_1e4", precision=16))
+    cfg = workload("coax_32x64_1e4", precision=32)
+    with Simulation(cfg) as sim:
+        with pytest.raises(PicError):   # outside the gap
+            sim.load_particles([0.5e-3], [0.0], [0.0], [0.0], [0.0], np.array([0], dtype=np.uint64))
+        with pytest.raises(PicError):   # uid beyond 32 bits
+            sim.load_particles([5e-3], [0.0], [0.0], [0.0], [0.0], np.array([2**33], dtype=np.uint64))
+        with pytest.raises(PicError):   # non-finite velocity
+            sim.load_particles([5e-3], [0.0], [np.nan], [0.0], [0.0], np.array([0], dtype=np.uint64))
+
+
+def test_checkpoint_restore(tmp_path):
+    """Stepping on after a restore reproduces the uninterrupted run (bitwise
+    in a fixed field: the random streams depend on seed, uid and step)."""
+    from paper_2206_14662_gb300._capi import Simulation
+    cfg = _collision_cfg(32, sort_every=4, n_init=8000)
+    parts = seed_particles(cfg, n=8000, seed=12)
+    er, ez = random_field_node_arrays(cfg, 3e5, seed=13)
+    a = make_gpu(cfg, parts, efield=(er, ez))
+    a.step(6)
+    path = str(tmp_path / "ck.bin")
+    a.checkpoint(path)
+    a.step(7)
+    ga = by_uid(a.export_particles())
+    a.close()
+    with Simulation(cfg) as b:
+        b.restore(path)
+        b.step(7)
+        gb = by_uid(b.export_particles())
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k]), k
+
+
+def test_density_and_energy_ledger_fp64():
+    """Node density of the load against the oracle's (b / q) / V, and the
+    energy ledger of a run with collisions and wall losses."""
+    cfg = workload("coax_32x64_1e4", precision=64, p_mbar=1.0, T0_eV=50.0, n_init=3000)
+    parts = seed_particles(cfg)
+    sim = make_gpu(cfg, parts)
+    dens = sim.diagnostics(density=True)["density"]
+    dens_o = oracle.density(cfg, oracle.deposit(cfg, parts[0], parts[1]))
+    assert np.abs(dens - dens_o).max() <= 1e-12 * dens_o.max()
+    sim.step(60)
+    d = sim.diagnostics()
+    sim.close()
+    assert d["n_absorbed"] > 0 and d["n_elastic"] > 0
+    scale = abs(d["work_E_J"]) + d["ke_initial_J"] + d["ke_absorbed_J"]
+    assert abs(d["ledger_residual_J"]) <= 1e-11 * scale
+
+
+# ------------------------------------------------- full-size workload
+
+@pytest.mark.skipif(os.environ.get("PIC_SKIP_FULL") == "1", reason="full-size case disabled")
+def test_full_size_mirror_128x512_1e7_one_step():
+    """The benchmark workload at full size (1e7 macro-electrons, 128x512
+    cells, FP32 particles, field solve on, the benchmark's launch
+    configuration): the oracle deposits the load, solves its own field and
+    steps every particle once; the GPU's deposit after the step, its event
+    counts and a sample of particles must match."""
+    cfg = workload("mirror_128x512_1e7")
+    parts = seed_particles(cfg)
+    sim = make_gpu(cfg, parts)
+    sim.step(1)
+    d = sim.diagnostics()
+    b_g = sim.get_grid(1)
+    g = by_uid(sim.export_particles())
+    sim.close()
+    o = oracle.OracleSim(cfg, *parts)
+    uid0 = o.uid.copy()
+    next0 = o.uid_next
+    res = o.step()
+    assert np.abs(b_g - res.b).max() <= TOL[32] * np.abs(res.b).max()
+    amb = int((res.margin < 1e-5).sum())
+    assert amb < 50
+    for key, slot in (("n_absorbed", oracle.T_N_ABSORBED), ("n_candidates", oracle.T_N_CANDIDATE)):
+        assert abs(d[key] - res.tally[slot]) <= amb, key
+    # every particle the oracle keeps is live on the GPU (bar ambiguous ones)
+    keep = res.margin >= 1e-5
+    live_o = uid0[keep & (res.event < oracle.EV_WALL)]
+    assert np.isin(live_o, g["uid"]).all()
+    # sampled particles, one by one
+    rng = np.random.default_rng(0)
+    sample = rng.choice(live_o, 20000, replace=False)
+    oi = np.searchsorted(o.uid, sample)
+    gi = np.searchsorted(g["uid"], sample)
+    hr = (cfg["r_out"] - cfg["r_in"]) / cfg["nr"]
+    hz = (cfg["z_max"] - cfg["z_min"]) / cfg["nz"]
+    vmax = np.abs(o.vt).max()
+    assert np.abs(g["r"][gi] - o.r[oi]).max() / hr <= TOL[32]
+    assert np.abs(g["z"][gi] - o.z[oi]).max() / hz <= TOL[32]
+    for k, ov in (("vr", o.vr), ("vt", o.vt), ("vz", o.vz)):
+        assert np.abs(g[k][gi] - ov[oi]).max() / vmax <= TOL[32], k
+    assert d["n_particles"] == len(g["uid"])
+    del next0
