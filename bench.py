@@ -131,6 +131,8 @@ def run_ours(args, ws, rank):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     cfg = workload(WORKLOAD, seed=1 + rank)
+    if args.particles:
+        cfg["n_init"] = args.particles
     parts = seed_particles(cfg)
     n0 = len(parts[0])
     pinned = [torch.from_numpy(a).pin_memory() for a in parts[:5]]
@@ -163,11 +165,13 @@ def run_ours(args, ws, rank):
     # end to end through the C ABI from host buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim.load_particles(*pinned)
-    sim.step(args.steps)
-    de = sim.diagnostics(density=True)
+    e2e_units = 0
+    if args.e2e:
+        sim.load_particles(*pinned)
+        sim.step(args.steps)
+        de = sim.diagnostics(density=True)
+        e2e_units = de["n_pushed"]
     t1 = time.perf_counter()
-    e2e_units = de["n_pushed"]
     sim.close()
 
     if ws > 1:
@@ -202,10 +206,11 @@ def run_ours(args, ws, rank):
         "vs_baseline": None,
         "dtype": "f32 particles / f64 field",
         "data": "synthetic (seeded volume-uniform 1 eV Maxwellian load)",
-        "config": {"workload": WORKLOAD, "particles": n0, "grid": "128x512", "sort_every": 20,
+        "config": {"workload": WORKLOAD if not args.particles else f"{WORKLOAD} (particles={n0})",
+                   "particles": n0, "grid": "128x512", "sort_every": 20,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (particle store 520 MB per step)"},
-        "e2e": {"value": e2e_units * ws / esec, "unit": "particle-steps/s",
+        "e2e": None if not args.e2e else {"value": e2e_units * ws / esec, "unit": "particle-steps/s",
                 "h2d_bytes_per_step": int(n0 * 48 / args.steps),
                 "d2h_bytes_per_step": int(((cfg["nr"] + 1) * (cfg["nz"] + 1) * 8 + 512) / args.steps)},
         "gpu_launches": int(prof["kernels_launched"]),
@@ -283,6 +288,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false",
+                    help="skip the end-to-end pass (profiling captures)")
+    ap.add_argument("--particles", type=int, default=0,
+                    help="override the macro-electron count (profiling captures on a "
+                         "smaller case; the reported workload is then not the benchmark's)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

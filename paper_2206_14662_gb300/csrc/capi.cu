@@ -159,6 +159,10 @@ void fill_params(pic_handle* h, PushParams<Real>& P) {
   P.seed_hi = (unsigned)(c.seed >> 32);
   P.capacity = h->capacity;
   P.spawn_cap = h->spawn_cap;
+  P.r_in_d = c.r_in;
+  P.hr_d = h->hr;
+  P.z_min_d = c.z_min;
+  P.hz_d = h->hz;
 }
 
 template <typename Real>

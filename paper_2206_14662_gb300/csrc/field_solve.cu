@@ -235,22 +235,52 @@ __global__ void k_dct_direct(const double* __restrict__ in, double* __restrict__
 // ------------------------------------------------------------- tridiag
 
 // one thread per z-mode: forward and back substitution of the pre-factored
-// Thomas recurrence along the interior r-lines
-__global__ void k_tridiag(const double* __restrict__ bhat, double* phihat,
-                          const double* __restrict__ a, const double* __restrict__ invd,
-                          const double* __restrict__ cp, int NI, int M1) {
+// Thomas recurrence along the interior r-lines.  The coefficients of kUnroll
+// lines are loaded ahead of the dependent arithmetic, so the recurrence
+// waits for memory once per group of lines rather than once per line.
+constexpr int kUnroll = 8;
+__global__ void __launch_bounds__(64)
+k_tridiag(const double* __restrict__ bhat, double* __restrict__ phihat,
+          const double* __restrict__ a, const double* __restrict__ invd,
+          const double* __restrict__ cp, int NI, int M1) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= M1) return;
   double y = 0.0;
-#pragma unroll 8
-  for (int i = 0; i < NI; ++i) {
+  int i0 = 0;
+  for (; i0 + kUnroll <= NI; i0 += kUnroll) {
+    double bb[kUnroll], aa[kUnroll], dd[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const size_t o = (size_t)(i0 + u) * M1 + k;
+      bb[u] = bhat[o]; aa[u] = a[o]; dd[u] = invd[o];
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      y = (bb[u] - aa[u] * y) * dd[u];
+      phihat[(size_t)(i0 + u) * M1 + k] = y;
+    }
+  }
+  for (int i = i0; i < NI; ++i) {
     const size_t o = (size_t)i * M1 + k;
     y = (bhat[o] - a[o] * y) * invd[o];
     phihat[o] = y;
   }
   double xn = 0.0;
-#pragma unroll 8
-  for (int i = NI - 1; i >= 0; --i) {
+  int i1 = NI - 1;
+  for (; i1 - kUnroll + 1 >= 0; i1 -= kUnroll) {
+    double yy[kUnroll], cc[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const size_t o = (size_t)(i1 - u) * M1 + k;
+      yy[u] = phihat[o]; cc[u] = cp[o];
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      xn = yy[u] - cc[u] * xn;
+      phihat[(size_t)(i1 - u) * M1 + k] = xn;
+    }
+  }
+  for (int i = i1; i >= 0; --i) {
     const size_t o = (size_t)i * M1 + k;
     xn = phihat[o] - cp[o] * xn;
     phihat[o] = xn;
@@ -363,16 +393,16 @@ void launch_field_solve(const FieldTables& T, double* rhs, double* phi,
     const int blocks = (nlines + 1) / 2;
     k_dct_fft<true><<<blocks, threads, smem, stream>>>(rhs, T.bhat, T.twiddle, T.fwd_scale,
                                                        T.phi_vac, nlines, T.M, T.log2N);
-    k_tridiag<<<(M1 + 127) / 128, 128, 0, stream>>>(T.bhat, T.phihat, T.tri_a, T.tri_invd,
-                                                    T.tri_cp, nlines, M1);
+    k_tridiag<<<(M1 + 63) / 64, 64, 0, stream>>>(T.bhat, T.phihat, T.tri_a, T.tri_invd,
+                                                  T.tri_cp, nlines, M1);
     k_dct_fft<false><<<blocks, threads, smem, stream>>>(T.phihat, phi, T.twiddle, T.fwd_scale,
                                                         T.phi_vac, nlines, T.M, T.log2N);
   } else {
     const size_t smem = (size_t)M1 * sizeof(double);
     k_dct_direct<true><<<nlines, 256, smem, stream>>>(rhs, T.bhat, T.costab, T.fwd_scale,
                                                       T.phi_vac, nlines, T.M);
-    k_tridiag<<<(M1 + 127) / 128, 128, 0, stream>>>(T.bhat, T.phihat, T.tri_a, T.tri_invd,
-                                                    T.tri_cp, nlines, M1);
+    k_tridiag<<<(M1 + 63) / 64, 64, 0, stream>>>(T.bhat, T.phihat, T.tri_a, T.tri_invd,
+                                                  T.tri_cp, nlines, M1);
     k_dct_direct<false><<<nlines, 256, smem, stream>>>(T.phihat, phi, T.costab, T.fwd_scale,
                                                        T.phi_vac, nlines, T.M);
   }

@@ -22,6 +22,7 @@
 // velocity components, uid) and 24 B written (all but the uid) in FP32.
 #include <cfloat>
 #include <climits>
+#include <type_traits>
 
 #include "pic_internal.cuh"
 
@@ -31,8 +32,15 @@ constexpr int kThreads = 256;
 constexpr int kPPT = 4;                 // particles per thread per chunk
 constexpr int kChunk = kThreads * kPPT;
 
-template <typename Real> struct TileT { using type = float; static constexpr int cap = 4096; };
+// Shared-memory deposit tile.  The FP32 path accumulates hat weights as
+// unsigned fixed-point numbers (native integer shared atomics, sums that do
+// not depend on the order of the adds): a chunk holds at most kChunk
+// particles of weight <= 1 per node, so kFix = floor((2^32 - 1) / kChunk)
+// cannot overflow; the rounding is 2^-23 of a particle's charge per
+// contribution.  The FP64 path accumulates doubles.
+template <typename Real> struct TileT { using type = unsigned; static constexpr int cap = 4096; };
 template <> struct TileT<double> { using type = double; static constexpr int cap = 2048; };
+constexpr float kFix = (float)(4294967295u / kChunk);   // 4194303
 
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
@@ -356,13 +364,35 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E,
     if (use_tile) {
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
-        if (dep[k].ir >= 0) {
-          const int t = (dep[k].ir - br0) * cols + (dep[k].iz - bz0);
-          const TT a = (TT)dep[k].fr, c = (TT)dep[k].fz;
-          atomicAdd(&tile[t], (TT(1) - a) * (TT(1) - c));
-          atomicAdd(&tile[t + cols], a * (TT(1) - c));
-          atomicAdd(&tile[t + 1], (TT(1) - a) * c);
-          atomicAdd(&tile[t + cols + 1], a * c);
+        const bool has = dep[k].ir >= 0;
+        const int t = has ? (dep[k].ir - br0) * cols + (dep[k].iz - bz0) : -1;
+        if constexpr (std::is_same<Real, float>::value) {
+          // lanes in the same cell add the same four nodes: sum their
+          // fixed-point weights first, one lane per cell does the atomics
+          const float a = dep[k].fr, c = dep[k].fz;
+          const unsigned q00 = has ? __float2uint_rn((1.f - a) * (1.f - c) * kFix) : 0u;
+          const unsigned q10 = has ? __float2uint_rn(a * (1.f - c) * kFix) : 0u;
+          const unsigned q01 = has ? __float2uint_rn((1.f - a) * c * kFix) : 0u;
+          const unsigned q11 = has ? __float2uint_rn(a * c * kFix) : 0u;
+          const unsigned peers = __match_any_sync(0xffffffffu, t);
+          const unsigned s00 = __reduce_add_sync(peers, q00);
+          const unsigned s10 = __reduce_add_sync(peers, q10);
+          const unsigned s01 = __reduce_add_sync(peers, q01);
+          const unsigned s11 = __reduce_add_sync(peers, q11);
+          if (has && lane == __ffs(peers) - 1) {
+            atomicAdd(&tile[t], s00);
+            atomicAdd(&tile[t + cols], s10);
+            atomicAdd(&tile[t + 1], s01);
+            atomicAdd(&tile[t + cols + 1], s11);
+          }
+        } else {
+          if (has) {
+            const TT a = (TT)dep[k].fr, c = (TT)dep[k].fz;
+            atomicAdd(&tile[t], (TT(1) - a) * (TT(1) - c));
+            atomicAdd(&tile[t + cols], a * (TT(1) - c));
+            atomicAdd(&tile[t + 1], (TT(1) - a) * c);
+            atomicAdd(&tile[t + cols + 1], a * c);
+          }
         }
       }
     } else if (any) {
@@ -373,11 +403,12 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E,
     }
     __syncthreads();
     if (use_tile) {
+      const double unit = std::is_same<Real, float>::value ? P.qw / (double)kFix : P.qw;
       for (int t = tid; t < rows * cols; t += kThreads) {
         const TT v = tile[t];
         if (v != TT(0)) {
           const int rr = t / cols, cc = t - rr * cols;
-          atomicAdd(rhs + (br0 + rr) * nzp + (bz0 + cc), P.qw * (double)v);
+          atomicAdd(rhs + (br0 + rr) * nzp + (bz0 + cc), unit * (double)v);
         }
       }
     }
@@ -496,9 +527,8 @@ void launch_load(const double* r, const double* z, const double* vr,
                  DevState*, cudaStream_t stream) {
   if (n <= 0) return;
   const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
-  k_load<Real><<<grid, 256, 0, stream>>>(r, z, vr, vt, vz, uid, n, s, (double)P.r_in,
-                                         1.0 / (double)P.hr, (double)P.z_min,
-                                         1.0 / (double)P.hz, P.nr, P.nz);
+  k_load<Real><<<grid, 256, 0, stream>>>(r, z, vr, vt, vz, uid, n, s, P.r_in_d, 1.0 / P.hr_d,
+                                         P.z_min_d, 1.0 / P.hz_d, P.nr, P.nz);
 }
 
 template <typename Real>
@@ -537,9 +567,8 @@ void launch_export(const Soa<Real>& s, long long n_slots,
                    int* live, cudaStream_t stream) {
   if (n_slots <= 0) return;
   const int grid = (int)std::min<long long>((n_slots + 255) / 256, 152 * 16);
-  k_export<Real><<<grid, 256, 0, stream>>>(s, n_slots, (double)P.r_in, (double)P.hr,
-                                           (double)P.z_min, (double)P.hz, r, z, vr, vt, vz,
-                                           uid, live);
+  k_export<Real><<<grid, 256, 0, stream>>>(s, n_slots, P.r_in_d, P.hr_d, P.z_min_d, P.hz_d, r,
+                                           z, vr, vt, vz, uid, live);
 }
 
 // ------------------------------------------------------- kinetic energy

@@ -96,6 +96,9 @@ struct PushParams {
   unsigned seed_lo, seed_hi;
   long long capacity;         // particle slots
   long long spawn_cap;        // children per step
+  // grid geometry in FP64 for converting absolute positions to and from
+  // (cell, offset) at load and export
+  double r_in_d, hr_d, z_min_d, hz_d;
 };
 
 // ---------------------------------------------------------------- Philox

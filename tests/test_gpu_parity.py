@@ -316,9 +316,13 @@ def test_full_size_mirror_128x512_1e7_one_step():
     uid0 = o.uid.copy()
     next0 = o.uid_next
     res = o.step()
-    assert np.abs(b_g - res.b).max() <= TOL[32] * np.abs(res.b).max()
+    # a particle whose wall or collision decision lies within FP32 rounding
+    # of its threshold may go either way: it moves at most one particle's
+    # charge (weights sum to one) between the two deposits
     amb = int((res.margin < 1e-5).sum())
     assert amb < 50
+    qw = oracle.QE * o.P.weight
+    assert np.abs(b_g - res.b).max() <= TOL[32] * np.abs(res.b).max() + amb * qw
     for key, slot in (("n_absorbed", oracle.T_N_ABSORBED), ("n_candidates", oracle.T_N_CANDIDATE)):
         assert abs(d[key] - res.tally[slot]) <= amb, key
     # every particle the oracle keeps is live on the GPU (bar ambiguous ones)
