@@ -200,6 +200,33 @@ int pic_get_grid(pic_handle* h, int sim, int which, double* out);
 int pic_solve_field(pic_handle* h, const double* b, double* phi,
                     double* relres);
 
+/* Largest grid, in nodes (nr + 1) * (nz + 1), that pic_solve_field_static
+ * accepts; the 128 x 512 benchmark grid has 66 177 nodes. */
+#define PIC_STATIC_MAX_NODES 70000
+
+/* The field solve of pic_solve_field for callers that cannot allocate
+ * device memory (a framework that owns all device memory through its own
+ * pool, a plug-in restricted to the buffers it is given, a service that must
+ * not grow its footprint per call).  The paper has no counterpart: this is
+ * a deployment variant of the same solve, with no handle.
+ *   cfg     geometry, wall potentials and poisson_rtol (other fields unused)
+ *   b       DEVICE pointer, right-hand side on all nodes (C), read only
+ *   phi     DEVICE pointer, receives the potential on all nodes (V)
+ *   relres  host pointer or NULL.  Non-NULL: the call synchronises the
+ *           stream, stores the relative residual and returns PIC_ENOCONV if
+ *           it exceeds poisson_rtol.  NULL: the work is only queued.
+ *   cuda_stream  cudaStream_t of the caller (NULL = legacy default stream)
+ * Allocates nothing: its working memory is one fixed device array of about
+ * 5 MB inside the library, which every GPU that loads the library keeps
+ * until the process exits.  Grids above PIC_STATIC_MAX_NODES nodes, or with
+ * nz > 4096, return PIC_EINVAL before any device work.  All calls share that
+ * array: calls whose GPU work overlaps (other streams, other host threads)
+ * race and must be serialised by the caller.  The first call on each device
+ * looks up the array's address with that device current; make it before
+ * any stream capture. */
+int pic_solve_field_static(const pic_config* cfg, const double* b, double* phi,
+                           double* relres, void* cuda_stream);
+
 /* Write the full state (particles, field, counters, tallies) to `path`;
  * pic_restore reads it into a handle made with the same configuration.
  * Stepping on after a restore gives the same particles as never stopping

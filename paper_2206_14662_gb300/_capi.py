@@ -262,3 +262,22 @@ class Simulation:
         t = PicKernelTimes()
         _check(lib().pic_profile(self.h, 0, ctypes.byref(t)), "pic_profile")
         return {name: getattr(t, name) for name, _ in PicKernelTimes._fields_}
+
+
+def solve_field_static(cfg: dict, b_dev_ptr: int, phi_dev_ptr: int, stream: int = 0,
+                       check: bool = True):
+    """pic_solve_field_static: the field solve with no device allocation.
+    ``b_dev_ptr`` and ``phi_dev_ptr`` are device addresses of (nr+1)*(nz+1)
+    doubles owned by the caller.  Returns the relative residual when
+    ``check`` (the call then synchronises the stream), else None."""
+    L = lib()
+    fn = L.pic_solve_field_static
+    fn.argtypes = [ctypes.POINTER(PicConfig), ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.POINTER(c_d), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    c = make_config(cfg)
+    rel = c_d()
+    rc = fn(ctypes.byref(c), ctypes.c_void_p(b_dev_ptr), ctypes.c_void_p(phi_dev_ptr),
+            ctypes.byref(rel) if check else None, ctypes.c_void_p(stream))
+    _check(rc, "pic_solve_field_static")
+    return rel.value if check else None
