@@ -55,7 +55,8 @@ enum {
 typedef struct pic_config {
   double r_in, r_out;      /* inner / outer electrode radius a < b, m */
   double z_min, z_max;     /* open (Neumann) ends of the gap, m */
-  int32_t nr, nz;          /* cells along r and z (nz >= 2, nr >= 2) */
+  int32_t nr, nz;          /* cells along r and z (2 <= nr <= 401,
+                              2 <= nz <= 4096) */
   double v_inner, v_outer; /* Dirichlet potentials of the two walls, V */
   int32_t bfield_kind;     /* 0: uniform Bz = b0; 1: mirror
                               Bz = b0 (1 + 0.5 (2 zeta / L)^2),
@@ -116,7 +117,11 @@ typedef struct pic_diag {
                                     ke_absorbed - ion_loss - recoil_loss) */
   double n_peak;                 /* largest node density, m^-3 */
   int32_t poisson_iters;         /* sweeps of the last field solve */
-  double poisson_relres;         /* its relative residual */
+  double poisson_relres;         /* its residual relative to the right-hand
+                                    side with the wall potentials moved into
+                                    it (the convergence contract) */
+  double poisson_relres_charge;  /* its residual relative to the charge
+                                    alone (the sweeps' stopping test) */
   double nu_max;                 /* collision majorant in use, s^-1 */
   double weight;                 /* macro weight in use */
   int32_t error;                 /* sticky error code (0 none) */
@@ -217,9 +222,9 @@ int pic_solve_field(pic_handle* h, const double* b, double* phi,
  *           it exceeds poisson_rtol.  NULL: the work is only queued.
  *   cuda_stream  cudaStream_t of the caller (NULL = legacy default stream)
  * Allocates nothing: its working memory is one fixed device array of about
- * 5 MB inside the library, which every GPU that loads the library keeps
+ * 5.5 MB inside the library, which every GPU that loads the library keeps
  * until the process exits.  Grids above PIC_STATIC_MAX_NODES nodes, or with
- * nz > 4096, return PIC_EINVAL before any device work.  All calls share that
+ * nz > 4096 or nr > 401, return PIC_EINVAL before any device work.  All calls share that
  * array: calls whose GPU work overlaps (other streams, other host threads)
  * race and must be serialised by the caller.  The first call on each device
  * looks up the array's address with that device current; make it before

@@ -46,7 +46,8 @@ class PicDiag(ctypes.Structure):
         ("ke_total_J", c_d), ("work_E_J", c_d), ("ke_absorbed_J", c_d),
         ("ion_loss_J", c_d), ("recoil_loss_J", c_d), ("ke_initial_J", c_d),
         ("ledger_residual_J", c_d), ("n_peak", c_d), ("poisson_iters", c_i32),
-        ("poisson_relres", c_d), ("nu_max", c_d), ("weight", c_d), ("error", c_i32),
+        ("poisson_relres", c_d), ("poisson_relres_charge", c_d), ("nu_max", c_d),
+        ("weight", c_d), ("error", c_i32),
     ]
 
 

@@ -19,6 +19,9 @@ LIB = os.path.join(PKG, "libpic.so")
 SOURCES = ["particle_step.cu", "field_solve.cu", "sort.cu", "capi.cu", "field_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# the particle step writes its multiply-adds out explicitly; no automatic
+# contraction keeps every particle's rounding sequence the same
+PER_FILE = {"particle_step.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -46,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o + ".tmp"]
+            cmd = [nvcc, *ARCH, *FLAGS, *PER_FILE.get(src, []), "-c", s, "-o", o + ".tmp"]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((o, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "pic_internal.cuh"
@@ -22,6 +23,7 @@ using namespace pic;
 
 namespace pic {
 int particle_step_blocks_per_sm(int precision);
+int particle_chunk();
 }
 
 struct pic_handle {
@@ -45,13 +47,13 @@ struct pic_handle {
   int cur;
   unsigned* spawn_parent;
   int* cell_count;
-  double* rhs;
-  double* rho_last;
+  double* rhs;                  // FP64 path: this step's deposit
+  unsigned long long* cnt[2];   // FP32 path: fixed-point deposit grids
+  int dep_buf, last_buf;        // FP32: buffer of the next / last deposit
   double* phi;
   void* efield;
   double* scratch2;   // two doubles for reductions
   FieldTables T;
-  std::vector<double> phi_init;   // wall rows + vacuum interior
 
   // host bookkeeping
   long long step;
@@ -124,7 +126,9 @@ int validate(const pic_config& c) {
   if (!(c.gas_mass_amu > 0)) return PIC_EINVAL;
   if (c.weight <= 0 && (c.n_init <= 0 || !(c.n0 > 0))) return PIC_EINVAL;
   if (c.sort_every < 0 || c.capacity < 0) return PIC_EINVAL;
-  if (!(c.poisson_rtol > 0)) return PIC_EINVAL;
+  if (!(c.poisson_rtol > 0) || c.poisson_maxit < 0 || c.poisson_maxit > 64) return PIC_EINVAL;
+  // the Thomas sweep keeps four (nr - 1) x 32 float columns in shared memory
+  if ((long long)4 * (c.nr - 1) * 32 * 4 > 200 * 1024) return PIC_EINVAL;
   if ((long long)(c.nr + 1) * (c.nz + 1) > (1ll << 30)) return PIC_EINVAL;
   return PIC_OK;
 }
@@ -157,6 +161,10 @@ void fill_params(pic_handle* h, PushParams<Real>& P) {
   P.qw = -kQe * h->weight;
   P.seed_lo = (unsigned)(c.seed & 0xFFFFFFFFull);
   P.seed_hi = (unsigned)(c.seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    P.rk0[r] = P.seed_lo + (unsigned)r * 0x9E3779B9u;
+    P.rk1[r] = P.seed_hi + (unsigned)r * 0xBB67AE85u;
+  }
   P.capacity = h->capacity;
   P.spawn_cap = h->spawn_cap;
   P.r_in_d = c.r_in;
@@ -167,7 +175,9 @@ void fill_params(pic_handle* h, PushParams<Real>& P) {
 
 template <typename Real>
 int alloc_soa(pic_handle* h, Soa<Real>& s) {
-  const size_t n = (size_t)h->capacity;
+  // whole chunks of the fused kernel: its bulk copies read full chunks
+  const size_t ch = (size_t)particle_chunk();
+  const size_t n = ((size_t)h->capacity + ch - 1) / ch * ch;
   auto al = [&](size_t bytes) { return h_alloc(std::max<size_t>(bytes, 256), h); };
   s.cell = (int*)al(n * sizeof(int));
   s.offr = (Real*)al(n * sizeof(Real));
@@ -214,16 +224,22 @@ int step_impl(pic_handle* h, long long nsteps) {
   const bool solve = h->cfg.fixed_efield == 0;
   for (long long s = 0; s < nsteps; ++s) {
     mark(h, kTagStart);
-    if (!solve) {
+    const bool fp32 = std::is_same<Real, float>::value;
+    if (fp32 && !solve) {
+      CK(cudaMemsetAsync(h->cnt[h->dep_buf], 0, (size_t)h->nnodes * sizeof(unsigned long long),
+                         h->stream));
+    }
+    if (!fp32) {
       CK(cudaMemsetAsync(h->rhs, 0, (size_t)h->nnodes * sizeof(double), h->stream));
     }
-    launch_particle_step<Real>(soa<Real>(h, h->cur), h->efield, h->rhs, h->st,
-                               h->spawn_parent, P, h->grid_particle, h->stream);
+    launch_particle_step<Real>(soa<Real>(h, h->cur), h->efield, h->rhs,
+                               fp32 ? h->cnt[h->dep_buf] : nullptr, h->st, h->spawn_parent, P,
+                               h->grid_particle, h->stream);
     mark(h, kTagParticle);
     launch_spawn_finalize(h->st, soa<Real>(h, h->cur).uid, h->spawn_parent, h->spawn_cap,
                           h->capacity, h->stream);
-    mark(h, kTagFinalize);
     h->kernels += 2;
+    mark(h, kTagFinalize);
     ++h->step;
     if (h->cfg.sort_every > 0 && h->step % h->cfg.sort_every == 0) {
       launch_sort<Real>(soa<Real>(h, h->cur), soa<Real>(h, h->cur ^ 1), h->st, h->cell_count,
@@ -232,14 +248,38 @@ int step_impl(pic_handle* h, long long nsteps) {
       h->kernels += 4;
       mark(h, kTagSort);
     }
+    if (fp32) h->last_buf = h->dep_buf;
     if (solve) {
-      launch_field_solve<Real>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true,
-                               h->stream);
-      h->kernels += 4;
+      if (fp32)
+        launch_field_solve<Real>(h->T, nullptr, h->cnt[h->dep_buf], -kQe * h->weight / kFixUnit,
+                                 h->cnt[h->dep_buf ^ 1], h->efield, h->st, h->stream);
+      else
+        launch_field_solve<Real>(h->T, h->rhs, nullptr, 0.0, nullptr, h->efield, h->st,
+                                 h->stream);
+      if (fp32) h->dep_buf ^= 1;
+      h->kernels += field_solve_kernels(h->T);
       mark(h, kTagField);
     }
   }
   CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+// node charge b_i of the last deposit (C) copied to the host: the FP32
+// path keeps fixed-point counts, the FP64 path charges
+int read_rho(pic_handle* h, double* out) {
+  if (h->prec == 32) {
+    std::vector<unsigned long long> c(h->nnodes);
+    CK(cudaMemcpyAsync(c.data(), h->cnt[h->last_buf], (size_t)h->nnodes * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const double unit = -kQe * h->weight / kFixUnit;
+    for (int i = 0; i < h->nnodes; ++i) out[i] = (double)c[i] * unit;
+  } else {
+    CK(cudaMemcpyAsync(out, h->rhs, (size_t)h->nnodes * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
   return PIC_OK;
 }
 
@@ -346,41 +386,31 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   h->spawn_parent = (unsigned*)h_alloc((size_t)h->spawn_cap * sizeof(unsigned), h);
   h->cell_count = (int*)h_alloc((size_t)h->ncells * sizeof(int), h);
   h->rhs = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
-  h->rho_last = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
+  h->cnt[0] = (unsigned long long*)h_alloc((size_t)h->nnodes * sizeof(unsigned long long), h);
+  h->cnt[1] = (unsigned long long*)h_alloc((size_t)h->nnodes * sizeof(unsigned long long), h);
   h->phi = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
   h->efield = h_alloc((size_t)h->nnodes * (h->prec == 32 ? sizeof(float2) : sizeof(double2)), h);
   h->scratch2 = (double*)h_alloc(2 * sizeof(double), h);
-  if (!rc && (!h->st || !h->spawn_parent || !h->cell_count || !h->rhs || !h->rho_last ||
+  if (!rc && (!h->st || !h->spawn_parent || !h->cell_count || !h->rhs || !h->cnt[0] || !h->cnt[1] ||
               !h->phi || !h->efield || !h->scratch2))
     rc = PIC_ENOMEM;
   if (!rc) rc = field_tables_build(c, h->T, h_alloc, h, h->stream);
-  if (!rc) {
-    // the vacuum field: wall rows plus the z-independent vacuum solution
-    std::vector<double> vac(c.nr + 1);
-    if (cudaMemcpy(vac.data(), h->T.phi_vac, vac.size() * sizeof(double),
-                   cudaMemcpyDeviceToHost) != cudaSuccess)
-      rc = PIC_ECUDA;
-    h->phi_init.assign(h->nnodes, 0.0);
-    for (int i = 0; i <= c.nr; ++i)
-      for (int j = 0; j <= c.nz; ++j) h->phi_init[(size_t)i * (c.nz + 1) + j] = vac[i];
-  }
   if (!rc) {
     DevState s0;
     std::memset(&s0, 0, sizeof(s0));
     if (cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->rhs, 0, (size_t)h->nnodes * sizeof(double), h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->rho_last, 0, (size_t)h->nnodes * sizeof(double), h->stream) != cudaSuccess ||
-        cudaMemcpyAsync(h->phi, h->phi_init.data(), (size_t)h->nnodes * sizeof(double),
-                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->cnt[0], 0, (size_t)h->nnodes * sizeof(unsigned long long), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->cnt[1], 0, (size_t)h->nnodes * sizeof(unsigned long long), h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess)
       rc = PIC_ECUDA;
   }
   if (!rc) {
-    // vacuum E until particles are loaded
+    // vacuum field until particles are loaded
     if (h->prec == 32)
-      launch_field_solve<float>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true, h->stream);
+      launch_field_solve<float>(h->T, nullptr, h->cnt[0], 1.0, nullptr, h->efield, h->st, h->stream);
     else
-      launch_field_solve<double>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true, h->stream);
+      launch_field_solve<double>(h->T, h->rhs, nullptr, 0.0, nullptr, h->efield, h->st, h->stream);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = PIC_ECUDA;
   }
   if (rc) {
@@ -451,17 +481,28 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
                   cudaSuccess ||
               cudaMemsetAsync(h->rhs, 0, (size_t)h->nnodes * sizeof(double), h->stream) !=
                   cudaSuccess ||
-              cudaMemcpyAsync(h->phi, h->phi_init.data(), (size_t)h->nnodes * sizeof(double),
-                              cudaMemcpyHostToDevice, h->stream) != cudaSuccess))
+              cudaMemsetAsync(h->cnt[0], 0, (size_t)h->nnodes * sizeof(unsigned long long), h->stream) !=
+                  cudaSuccess ||
+              cudaMemsetAsync(h->cnt[1], 0, (size_t)h->nnodes * sizeof(unsigned long long), h->stream) !=
+                  cudaSuccess ||
+              cudaMemsetAsync(h->T.phir, 0, (size_t)h->nnodes * sizeof(float2), h->stream) !=
+                  cudaSuccess))
     rc = PIC_ECUDA;
   if (!rc) {
-    if (h->prec == 32) launch_deposit_only<float>(h->sf[0], n, h->rhs, c.nz, -kQe * h->weight, h->stream);
-    else launch_deposit_only<double>(h->sd[0], n, h->rhs, c.nz, -kQe * h->weight, h->stream);
+    const double qw = -kQe * h->weight;
+    h->last_buf = 0;
+    h->dep_buf = 0;
+    if (h->prec == 32) launch_deposit_only<float>(h->sf[0], n, h->rhs, h->cnt[0], c.nz, qw, h->stream);
+    else launch_deposit_only<double>(h->sd[0], n, h->rhs, nullptr, c.nz, qw, h->stream);
     if (c.fixed_efield == 0) {
-      if (h->prec == 32)
-        launch_field_solve<float>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true, h->stream);
-      else
-        launch_field_solve<double>(h->T, h->rhs, h->phi, h->efield, h->rho_last, h->st, true, h->stream);
+      if (h->prec == 32) {
+        launch_field_solve<float>(h->T, nullptr, h->cnt[0], qw / kFixUnit, h->cnt[1], h->efield,
+                                  h->st, h->stream);
+        h->dep_buf = 1;
+      } else {
+        launch_field_solve<double>(h->T, h->rhs, nullptr, 0.0, nullptr, h->efield, h->st,
+                                   h->stream);
+      }
     }
     // initial kinetic energy
     cudaMemsetAsync(h->scratch2, 0, 2 * sizeof(double), h->stream);
@@ -505,12 +546,12 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
   CK(cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(ke, h->scratch2, sizeof(ke), cudaMemcpyDeviceToHost, h->stream));
   std::vector<double> grid;
+  CK(cudaStreamSynchronize(h->stream));
   if (density) {
     grid.resize(h->nnodes);
-    CK(cudaMemcpyAsync(grid.data(), c.fixed_efield ? h->rhs : h->rho_last,
-                       (size_t)h->nnodes * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int rr = read_rho(h, grid.data());
+    if (rr) return rr;
   }
-  CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
   if (s.err && !h->sticky) h->sticky = s.err;
   std::memset(out, 0, sizeof(*out));
@@ -541,6 +582,7 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
                            (out->work_E_J - out->ke_absorbed_J - out->ion_loss_J - out->recoil_loss_J);
   out->poisson_iters = s.poisson_iters;
   out->poisson_relres = s.relres_last;
+  out->poisson_relres_charge = s.relres_strict;
   out->nu_max = h->nu_max;
   out->weight = h->weight;
   out->error = h->sticky;
@@ -649,9 +691,13 @@ int pic_set_efield(pic_handle* h, int sim, const double* er, const double* ez) {
 int pic_get_grid(pic_handle* h, int sim, int which, double* out) {
   if (!h || sim != 0 || !out) return PIC_EINVAL;
   const size_t bytes = (size_t)h->nnodes * sizeof(double);
-  if (which == PIC_GRID_PHI || which == PIC_GRID_RHS) {
-    const double* src = which == PIC_GRID_PHI ? h->phi : (h->cfg.fixed_efield ? h->rhs : h->rho_last);
-    CK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (which == PIC_GRID_RHS) {
+    const int rr = read_rho(h, out);
+    return rr ? rr : check_sticky(h);
+  }
+  if (which == PIC_GRID_PHI) {
+    launch_phi_out(h->T, h->phi, h->stream);
+    CK(cudaMemcpyAsync(out, h->phi, bytes, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return check_sticky(h);
   }
@@ -672,29 +718,41 @@ int pic_get_grid(pic_handle* h, int sim, int which, double* out) {
 
 int pic_solve_field(pic_handle* h, const double* b, double* phi, double* relres) {
   if (!h || !b || !phi) return PIC_EINVAL;
-  const size_t bytes = (size_t)h->nnodes * sizeof(double);
-  double* d_b = (double*)h_alloc(bytes, h);
-  double* d_phi = (double*)h_alloc(bytes, h);
-  double* d_rho = (double*)h_alloc(bytes, h);
-  void* d_e = h_alloc((size_t)h->nnodes * sizeof(double2), h);
+  const size_t nn = (size_t)h->nnodes;
+  const size_t tri = (size_t)h->T.NI * (h->T.M + 1);
+  // the tables are shared; the work arrays are this call's own, so the
+  // simulation's field is untouched
+  FieldTables T = h->T;
+  double* d_b = (double*)h_alloc(nn * sizeof(double), h);
+  double* d_phi = (double*)h_alloc(nn * sizeof(double), h);
+  void* d_e = h_alloc(nn * sizeof(double2), h);
   DevState* d_st = (DevState*)h_alloc(sizeof(DevState), h);
-  int rc = (d_b && d_phi && d_rho && d_e && d_st) ? PIC_OK : PIC_ENOMEM;
+  T.b2 = (float2*)h_alloc(nn * sizeof(float2), h);
+  T.phir = (float2*)h_alloc(nn * sizeof(float2), h);
+  T.res = (float*)h_alloc(nn * sizeof(float), h);
+  T.bhat = (float*)h_alloc(tri * sizeof(float), h);
+  T.phihat = (float*)h_alloc(tri * sizeof(float), h);
+  void* tmp[] = {d_b, d_phi, d_e, d_st, T.b2, T.phir, T.res, T.bhat, T.phihat};
+  int rc = PIC_OK;
+  for (void* p : tmp)
+    if (!p) rc = PIC_ENOMEM;
   DevState s0;
   std::memset(&s0, 0, sizeof(s0));
-  if (!rc && (cudaMemcpyAsync(d_b, b, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
-              cudaMemcpyAsync(d_phi, h->phi_init.data(), bytes, cudaMemcpyHostToDevice,
-                              h->stream) != cudaSuccess ||
-              cudaMemcpyAsync(d_st, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) != cudaSuccess))
+  if (!rc && (cudaMemcpyAsync(d_b, b, nn * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+              cudaMemcpyAsync(d_st, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+              cudaMemsetAsync(T.phir, 0, nn * sizeof(float2), h->stream) != cudaSuccess))
     rc = PIC_ECUDA;
   if (!rc) {
-    launch_field_solve<double>(h->T, d_b, d_phi, d_e, d_rho, d_st, false, h->stream);
-    if (cudaMemcpyAsync(phi, d_phi, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+    launch_field_solve<double>(T, d_b, nullptr, 0.0, nullptr, d_e, d_st, h->stream);
+    launch_phi_out(T, d_phi, h->stream);
+    if (cudaMemcpyAsync(phi, d_phi, nn * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
         cudaMemcpyAsync(&s0, d_st, sizeof(s0), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
       rc = PIC_ECUDA;
   }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = PIC_ECUDA;
   if (!rc && relres) *relres = s0.relres_last;
-  for (void* p : {(void*)d_b, (void*)d_phi, (void*)d_rho, d_e, (void*)d_st}) {
+  if (!rc && s0.err) rc = s0.err;
+  for (void* p : tmp) {
     if (!p) continue;
     auto it = std::find(h->owned.begin(), h->owned.end(), p);
     if (it != h->owned.end()) h->owned.erase(it);
@@ -706,8 +764,9 @@ int pic_solve_field(pic_handle* h, const double* b, double* phi, double* relres)
 // checkpoint layout: magic, version, precision, nr, nz, capacity, seed, host
 // step, ke_initial, last_abs[4], last_diag_step, DevState, n_slots, the
 // seven SoA arrays of the current buffer set (n_slots entries), phi, the
-// node field, rho_last and rhs
-static const char kMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
+// space-charge potential (double-float pairs), node field, FP64 deposit and
+// the FP32 path's last fixed-point deposit
+static const char kMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '2'};
 
 int pic_checkpoint(pic_handle* h, const char* path) {
   if (!h || !path) return PIC_EINVAL;
@@ -744,8 +803,9 @@ int pic_checkpoint(pic_handle* h, const char* path) {
   }
   const size_t gbytes = (size_t)h->nnodes * sizeof(double);
   const size_t ebytes = (size_t)h->nnodes * 2 * rs;
-  const void* grids[4] = {h->phi, h->efield, h->rho_last, h->rhs};
-  const size_t gsz[4] = {gbytes, ebytes, gbytes, gbytes};
+  const void* grids[4] = {h->T.phir, h->efield, h->rhs, h->cnt[h->last_buf]};
+  const size_t gsz[4] = {(size_t)h->nnodes * sizeof(float2), ebytes, gbytes,
+                         (size_t)h->nnodes * sizeof(unsigned long long)};
   for (int k = 0; k < 4 && ok; ++k) {
     buf.resize(gsz[k]);
     if (cudaMemcpy(buf.data(), grids[k], gsz[k], cudaMemcpyDeviceToHost) != cudaSuccess) { ok = false; break; }
@@ -793,8 +853,9 @@ int pic_restore(pic_handle* h, const char* path) {
   }
   const size_t gbytes = (size_t)h->nnodes * sizeof(double);
   const size_t ebytes = (size_t)h->nnodes * 2 * rs;
-  void* grids[4] = {h->phi, h->efield, h->rho_last, h->rhs};
-  const size_t gsz[4] = {gbytes, ebytes, gbytes, gbytes};
+  void* grids[4] = {h->T.phir, h->efield, h->rhs, h->cnt[0]};
+  const size_t gsz[4] = {(size_t)h->nnodes * sizeof(float2), ebytes, gbytes,
+                         (size_t)h->nnodes * sizeof(unsigned long long)};
   for (int k = 0; k < 4 && ok; ++k) {
     buf.resize(gsz[k]);
     ok = std::fread(buf.data(), 1, gsz[k], f) == gsz[k];
@@ -803,6 +864,9 @@ int pic_restore(pic_handle* h, const char* path) {
   std::fclose(f);
   if (!ok) return PIC_EINVAL;
   CK(cudaMemcpy(h->st, &s, sizeof(s), cudaMemcpyHostToDevice));
+  CK(cudaMemset(h->cnt[1], 0, (size_t)h->nnodes * sizeof(unsigned long long)));
+  h->last_buf = 0;
+  h->dep_buf = h->cfg.fixed_efield ? 0 : 1;
   h->step = hdr[5];
   h->ke_initial = ke0;
   std::copy(labs, labs + 4, h->last_abs);

@@ -1,59 +1,100 @@
-// field_solve.cu -- FP64 field solve of the PIC step (arXiv 2206.14662,
-// Sec. II.A: finite elements, Dirichlet on the metal walls, Neumann on the
-// open z ends).
+// field_solve.cu -- field solve of the PIC step (arXiv 2206.14662, Sec.
+// II.A: finite elements, Dirichlet on the metal walls, Neumann on the open
+// z ends).
 //
 // The finite-element matrix on bilinear elements of the (r,z) grid is
 //   A = 2 pi eps0 (K_r (x) M_z + M_r (x) K_z)
 // with r-weighted 1D matrices K_r, M_r (tridiagonal) and plain 1D matrices
-// K_z, M_z of the uniform z grid with natural (Neumann) end rows.  With
-// W = diag(1/2, 1, ..., 1, 1/2) and the operator Y (Y v)_j = v_{j-1} +
-// v_{j+1}, mirrored at the ends,
+// K_z, M_z of the uniform z grid with natural (Neumann) end rows.  The
+// solver works on A' = A / (2 pi eps0) and b' = b / (2 pi eps0).
+//
+// Split.  phi = phi_vac + phi_rho: phi_vac carries the wall potentials and
+// solves the charge-free problem exactly (it is z-independent: one radial
+// tridiagonal solve in FP64 on the host, once); phi_rho solves
+// A'_II phi_rho = b'_I with zero wall values.  phi_rho is orders of
+// magnitude smaller than phi_vac, so its residual has no cancellation
+// against the vacuum field.
+//
+// Separable preconditioner S (FP32).  With W = diag(1/2, 1, ..., 1, 1/2)
+// and the mirrored neighbour-sum operator Y,
 //   K_z = W (2 I - Y) / h_z,   M_z = W h_z (4 I + Y) / 6,
-// and the cosines c_k(j) = cos(pi k j / M), k = 0..M, are the eigenvectors
-// of Y (eigenvalues 2 cos(pi k / M)).  So A separates: a DCT-I along z
-// turns the interior problem into M + 1 independent SPD tridiagonal systems
-// along r, (g_k K_r + f_k M_r) phihat_k = bhat_k, which are solved by
-// pre-factored Thomas sweeps, and the inverse DCT-I returns phi.  The
-// split phi = phi_vac + phi_rho takes the wall potentials into phi_vac, the
-// exact discrete vacuum solution (z-independent, one radial tridiagonal
-// solve on the host).
+// and the cosines cos(pi k j / M), k = 0..M, diagonalise Y.  A DCT-I along
+// z therefore splits the interior problem into M + 1 SPD tridiagonal
+// systems along r, (g_k K_r + f_k M_r) phihat_k = bhat_k, solved by
+// pre-factored Thomas sweeps, and the inverse DCT-I returns the potential.
+// The DCT-I of length M + 1 is the DFT of the even extension of length 2M;
+// two r-lines share one complex FFT (radix 2, shared memory) as real and
+// imaginary parts.  M not a power of two uses a direct O(M^2) transform.
 //
-// The DCT-I of length M + 1 is the DFT of the even extension of length
-// 2M; two r-lines share one complex FFT as real and imaginary parts (both
-// transforms are real).  A radix-2 FFT runs in shared memory, one block per
-// pair of lines; M not a power of two takes a direct O(M^2) transform.
-//
-// Every solve is checked: ||b - A phi|| / ||b - A_ID phi_D|| over the
-// interior nodes must stay below poisson_rtol, else PIC_ENOCONV is latched.
+// Refinement.  phi_rho <- phi_rho + S(r), r = b' - A' phi_rho, with phi_rho,
+// b' and the residual held in double-float (hi + lo, about 48 bits): on
+// this part the FP64 pipe runs at a small fraction of the FP32 rate, so the
+// FP64-accurate residual is formed from FP32 pairs instead.  Each sweep
+// contracts the error by roughly the FP32 condition-number factor of S.
+// Sweeps stop when ||r|| <= rtol ||b'_I||; after the last allowed sweep the
+// reported residual ||r|| / ||b'_I - A'_ID phi_D|| (all wall potentials
+// moved to the right-hand side) must be <= rtol, else PIC_ENOCONV.
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "pic_internal.cuh"
 
 namespace pic {
 
+// ------------------------------------------------------- double-float
+// Error-free transformations (Knuth's two-sum, Dekker's product via FMA)
+// and the usual double-float add / multiply built on them.
+
+__device__ __forceinline__ float2 qts(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float v = s - a;
+  return make_float2(s, (a - (s - v)) + (b - v));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  return qts(s.x, s.y + a.y + b.y);
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return qts(p, e);
+}
+
+float2 df_from(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
 // ---------------------------------------------------------------- tables
 
-int field_tables_build(const pic_config& cfg, FieldTables& T,
-                       void* (*dev_alloc)(size_t, void*), void* ctx,
-                       cudaStream_t stream) {
+void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& H) {
   const int nr = cfg.nr, nz = cfg.nz, M = nz, NI = nr - 1, M1 = M + 1;
   T.nr = nr; T.nz = nz; T.M = M; T.NI = NI;
   T.hr = (cfg.r_out - cfg.r_in) / nr;
   T.hz = (cfg.z_max - cfg.z_min) / nz;
   T.rtol = cfg.poisson_rtol;
+  T.maxit = cfg.poisson_maxit > 0 ? cfg.poisson_maxit : 4;
   int l2 = 0;
   while ((1 << l2) < 2 * M) ++l2;
-  // FFT path for M a power of two whose 2M-point complex line fits the
-  // default 48 KB of dynamic shared memory; otherwise the direct transform
-  T.log2N = ((1 << l2) == 2 * M && 2 * M * (int)sizeof(double2) <= 48 * 1024) ? l2 : -1;
+  // FFT path for M a power of two whose 2M-point complex line and its M
+  // twiddles fit the default 48 KB of dynamic shared memory; otherwise the
+  // direct transform
+  T.log2N = ((1 << l2) == 2 * M && 3 * M * (int)sizeof(float2) <= 48 * 1024) ? l2 : -1;
   const double hr = T.hr, hz = T.hz;
 
-  std::vector<double> r(nr + 1);
-  for (int i = 0; i <= nr; ++i) r[i] = cfg.r_in + i * hr;
-  std::vector<double> kd(nr + 1, 0.0), ko(nr + 1, 0.0), md(nr + 1, 0.0), mo(nr + 1, 0.0);
+  double *kd = H.kd, *ko = H.ko, *md = H.md, *mo = H.mo;
+  for (int i = 0; i <= nr; ++i) kd[i] = ko[i] = md[i] = mo[i] = 0.0;
   for (int e = 0; e < nr; ++e) {
-    const double r0 = r[e], r1 = r[e + 1];
+    const double r0 = cfg.r_in + e * hr, r1 = cfg.r_in + (e + 1) * hr;
     const double k = (r0 + r1) / (2.0 * hr);
     kd[e] += k; kd[e + 1] += k; ko[e] = -k;
     md[e] += hr / 12.0 * (3.0 * r0 + r1);
@@ -63,37 +104,41 @@ int field_tables_build(const pic_config& cfg, FieldTables& T,
 
   // vacuum solution: K_r restricted to the interior lines with the wall
   // potentials moved to the right-hand side (M_r and K_z drop out for a
-  // z-independent field)
-  std::vector<double> vac(nr + 1);
+  // z-independent field); its radial node field by the same differences as
+  // the particle field (central, one-sided second order on the walls)
+  double* vac = H.vac;
   vac[0] = cfg.v_inner;
   vac[nr] = cfg.v_outer;
-  {
-    std::vector<double> cp(NI), y(NI);
-    for (int ii = 0; ii < NI; ++ii) {
-      const int i = ii + 1;
-      double rhs = 0.0;
-      if (i == 1) rhs -= ko[0] * cfg.v_inner;
-      if (i == nr - 1) rhs -= ko[nr - 1] * cfg.v_outer;
-      const double sub = ii > 0 ? ko[i - 1] : 0.0;
-      const double den = kd[i] - (ii > 0 ? sub * cp[ii - 1] : 0.0);
-      cp[ii] = ko[i] / den;
-      y[ii] = (rhs - (ii > 0 ? sub * y[ii - 1] : 0.0)) / den;
-    }
-    double xn = 0.0;
-    for (int ii = NI - 1; ii >= 0; --ii) {
-      xn = y[ii] - cp[ii] * xn;
-      vac[ii + 1] = xn;
-    }
+  for (int ii = 0; ii < NI; ++ii) {
+    const int i = ii + 1;
+    double rhs = 0.0;
+    if (i == 1) rhs -= ko[0] * cfg.v_inner;
+    if (i == nr - 1) rhs -= ko[nr - 1] * cfg.v_outer;
+    const double sub = ii > 0 ? ko[i - 1] : 0.0;
+    const double den = kd[i] - (ii > 0 ? sub * H.tmp_cp[ii - 1] : 0.0);
+    H.tmp_cp[ii] = ko[i] / den;
+    H.tmp_y[ii] = (rhs - (ii > 0 ? sub * H.tmp_y[ii - 1] : 0.0)) / den;
+  }
+  double xn = 0.0;
+  for (int ii = NI - 1; ii >= 0; --ii) {
+    xn = H.tmp_y[ii] - H.tmp_cp[ii] * xn;
+    vac[ii + 1] = xn;
+  }
+  for (int i = 0; i <= nr; ++i) {
+    double d;
+    if (i == 0) d = (-3.0 * vac[0] + 4.0 * vac[1] - vac[2]) / (2.0 * hr);
+    else if (i == nr) d = (3.0 * vac[nr] - 4.0 * vac[nr - 1] + vac[nr - 2]) / (2.0 * hr);
+    else d = (vac[i + 1] - vac[i - 1]) / (2.0 * hr);
+    H.evac64[i] = -d;
+    H.evac32[i] = (float)(-d);
   }
 
   // per-mode Thomas factors of g_k K_r + f_k M_r on the interior lines
-  std::vector<double> ta((size_t)NI * M1), tinv((size_t)NI * M1), tcp((size_t)NI * M1);
-  std::vector<double> scale(M1);
   for (int k = 0; k <= M; ++k) {
     const double lam = 2.0 * std::cos(kPi * k / M);
     const double g = hz * (4.0 + lam) / 6.0, f = (2.0 - lam) / hz;
     const double eps_k = (k == 0 || k == M) ? 0.5 : 1.0;
-    scale[k] = 2.0 * eps_k / (M * 2.0 * kPi * kEps0);
+    H.scale[k] = (float)(2.0 * eps_k / M);
     double cprev = 0.0;
     for (int ii = 0; ii < NI; ++ii) {
       const int i = ii + 1;
@@ -102,80 +147,183 @@ int field_tables_build(const pic_config& cfg, FieldTables& T,
       const double sup = g * ko[i] + f * mo[i];
       const double den = diag - sub * cprev;
       const size_t o = (size_t)ii * M1 + k;
-      ta[o] = sub;
-      tinv[o] = 1.0 / den;
-      tcp[o] = sup / den;
-      cprev = tcp[o];
+      H.ta[o] = (float)sub;
+      H.tinv[o] = (float)(1.0 / den);
+      H.tcp[o] = (float)(sup / den);
+      cprev = sup / den;
     }
   }
-
-  std::vector<double> tw;   // interleaved (re, im)
-  std::vector<double> ctab;
   if (T.log2N > 0) {
     const int N = 2 * M;
-    tw.resize(N);
     for (int m = 0; m < N / 2; ++m) {
-      tw[2 * m] = std::cos(2.0 * kPi * m / N);
-      tw[2 * m + 1] = -std::sin(2.0 * kPi * m / N);
+      H.tw[2 * m] = (float)std::cos(2.0 * kPi * m / N);
+      H.tw[2 * m + 1] = (float)-std::sin(2.0 * kPi * m / N);
     }
   } else {
-    ctab.resize(2 * M);
-    for (int m = 0; m < 2 * M; ++m) ctab[m] = std::cos(kPi * m / M);
+    for (int m = 0; m < 2 * M; ++m) H.cos[m] = (float)std::cos(kPi * m / M);
   }
+  for (int i = 0; i <= nr; ++i) {
+    H.kd2[i] = df_from(kd[i]); H.ko2[i] = df_from(ko[i]);
+    H.md2[i] = df_from(md[i]); H.mo2[i] = df_from(mo[i]);
+  }
+  T.mzd_end = df_from(hz / 3.0);
+  T.mzd_in = df_from(2.0 * hz / 3.0);
+  T.mzo = df_from(hz / 6.0);
+  T.kzd_end = df_from(1.0 / hz);
+  T.kzd_in = df_from(2.0 / hz);
+  T.kzo = df_from(-1.0 / hz);
+  T.lift_in = (float)(-ko[0] * cfg.v_inner);
+  T.lift_out = (float)(-ko[nr - 1] * cfg.v_outer);
+}
 
-  auto up = [&](const void* src, size_t bytes, void** dst) -> int {
-    *dst = dev_alloc(bytes, ctx);
-    if (!*dst) return PIC_ENOMEM;
-    if (src && cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
-      return PIC_ECUDA;
-    return PIC_OK;
+int field_tables_upload(FieldTables& T, const HostTables& H, cudaStream_t stream) {
+  const int nr = T.nr, M1 = T.M + 1, NI = T.NI;
+  const size_t nn = (size_t)(nr + 1) * M1, tri = (size_t)NI * M1 * sizeof(float);
+  const size_t rad = (size_t)(nr + 1);
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream) == cudaSuccess;
   };
-  int rc = PIC_OK;
-  T.twiddle = nullptr; T.costab = nullptr;
-  if (T.log2N > 0) rc = rc ? rc : up(tw.data(), tw.size() * sizeof(double), (void**)&T.twiddle);
-  else rc = rc ? rc : up(ctab.data(), ctab.size() * sizeof(double), (void**)&T.costab);
-  rc = rc ? rc : up(scale.data(), scale.size() * sizeof(double), (void**)&T.fwd_scale);
-  rc = rc ? rc : up(ta.data(), ta.size() * sizeof(double), (void**)&T.tri_a);
-  rc = rc ? rc : up(tinv.data(), tinv.size() * sizeof(double), (void**)&T.tri_invd);
-  rc = rc ? rc : up(tcp.data(), tcp.size() * sizeof(double), (void**)&T.tri_cp);
-  rc = rc ? rc : up(vac.data(), vac.size() * sizeof(double), (void**)&T.phi_vac);
-  rc = rc ? rc : up(kd.data(), kd.size() * sizeof(double), (void**)&T.kr_d);
-  rc = rc ? rc : up(ko.data(), ko.size() * sizeof(double), (void**)&T.kr_o);
-  rc = rc ? rc : up(md.data(), md.size() * sizeof(double), (void**)&T.mr_d);
-  rc = rc ? rc : up(mo.data(), mo.size() * sizeof(double), (void**)&T.mr_o);
-  rc = rc ? rc : up(nullptr, (size_t)NI * M1 * sizeof(double), (void**)&T.bhat);
-  rc = rc ? rc : up(nullptr, (size_t)NI * M1 * sizeof(double), (void**)&T.phihat);
+  bool ok = true;
+  if (T.log2N > 0) ok = ok && cp(T.tw32, H.tw, (size_t)2 * T.M * sizeof(float));
+  else ok = ok && cp(T.cos32, H.cos, (size_t)2 * T.M * sizeof(float));
+  ok = ok && cp(T.scale32, H.scale, M1 * sizeof(float)) && cp(T.tri_a, H.ta, tri) &&
+       cp(T.tri_inv, H.tinv, tri) && cp(T.tri_cp, H.tcp, tri) &&
+       cp(T.phi_vac, H.vac, rad * sizeof(double)) && cp(T.evac64, H.evac64, rad * sizeof(double)) &&
+       cp(T.evac32, H.evac32, rad * sizeof(float)) && cp(T.kr_d, H.kd2, rad * sizeof(float2)) &&
+       cp(T.kr_o, H.ko2, rad * sizeof(float2)) && cp(T.mr_d, H.md2, rad * sizeof(float2)) &&
+       cp(T.mr_o, H.mo2, rad * sizeof(float2));
+  ok = ok && cudaMemsetAsync(T.phir, 0, nn * sizeof(float2), stream) == cudaSuccess &&
+       cudaMemsetAsync(T.b2, 0, nn * sizeof(float2), stream) == cudaSuccess &&
+       cudaMemsetAsync(T.res, 0, nn * sizeof(float), stream) == cudaSuccess;
+  return ok ? PIC_OK : PIC_ECUDA;
+}
+
+int field_tables_build(const pic_config& cfg, FieldTables& T,
+                       void* (*dev_alloc)(size_t, void*), void* ctx,
+                       cudaStream_t stream) {
+  const int nr = cfg.nr, M = cfg.nz, NI = nr - 1, M1 = M + 1;
+  const size_t nn = (size_t)(nr + 1) * M1, tri = (size_t)NI * M1;
+  std::vector<double> dbl(9 * (size_t)(nr + 1));
+  std::vector<float> flt(3 * tri + M1 + 4 * (size_t)M + (nr + 1));
+  std::vector<float2> f2(4 * (size_t)(nr + 1));
+  HostTables H;
+  H.kd = dbl.data(); H.ko = H.kd + nr + 1; H.md = H.ko + nr + 1; H.mo = H.md + nr + 1;
+  H.vac = H.mo + nr + 1; H.evac64 = H.vac + nr + 1; H.tmp_cp = H.evac64 + nr + 1;
+  H.tmp_y = H.tmp_cp + nr + 1;
+  H.ta = flt.data(); H.tinv = H.ta + tri; H.tcp = H.tinv + tri; H.scale = H.tcp + tri;
+  H.tw = H.scale + M1; H.cos = H.tw + 2 * (size_t)M; H.evac32 = H.cos + 2 * (size_t)M;
+  H.kd2 = f2.data(); H.ko2 = H.kd2 + nr + 1; H.md2 = H.ko2 + nr + 1; H.mo2 = H.md2 + nr + 1;
+  field_tables_host(cfg, T, H);
+
+  auto al = [&](size_t bytes, void** dst) -> bool {
+    *dst = dev_alloc(std::max<size_t>(bytes, 16), ctx);
+    return *dst != nullptr;
+  };
+  bool ok = true;
+  T.tw32 = nullptr; T.cos32 = nullptr;
+  if (T.log2N > 0) ok = al((size_t)2 * M * sizeof(float), (void**)&T.tw32);
+  else ok = al((size_t)2 * M * sizeof(float), (void**)&T.cos32);
+  ok = ok && al(M1 * sizeof(float), (void**)&T.scale32) &&
+       al(tri * sizeof(float), (void**)&T.tri_a) && al(tri * sizeof(float), (void**)&T.tri_inv) &&
+       al(tri * sizeof(float), (void**)&T.tri_cp) &&
+       al((nr + 1) * sizeof(double), (void**)&T.phi_vac) &&
+       al((nr + 1) * sizeof(double), (void**)&T.evac64) &&
+       al((nr + 1) * sizeof(float), (void**)&T.evac32) &&
+       al((nr + 1) * sizeof(float2), (void**)&T.kr_d) &&
+       al((nr + 1) * sizeof(float2), (void**)&T.kr_o) &&
+       al((nr + 1) * sizeof(float2), (void**)&T.mr_d) &&
+       al((nr + 1) * sizeof(float2), (void**)&T.mr_o) &&
+       al(nn * sizeof(float2), (void**)&T.b2) && al(nn * sizeof(float2), (void**)&T.phir) &&
+       al(nn * sizeof(float), (void**)&T.res) && al(tri * sizeof(float), (void**)&T.bhat) &&
+       al(tri * sizeof(float), (void**)&T.phihat);
+  if (!ok) return PIC_ENOMEM;
+  int rc = field_tables_upload(T, H, stream);
   if (rc == PIC_OK && cudaStreamSynchronize(stream) != cudaSuccess) rc = PIC_ECUDA;
   return rc;
 }
 
-void field_tables_free(FieldTables& T, void (*dev_free)(void*, void*), void* ctx) {
-  void* ptrs[] = {T.twiddle, T.costab, T.fwd_scale, T.tri_a, T.tri_invd, T.tri_cp,
-                  T.phi_vac, T.kr_d, T.kr_o, T.mr_d, T.mr_o, T.bhat, T.phihat};
-  for (void* p : ptrs)
-    if (p) dev_free(p, ctx);
+// ---------------------------------------------------------------- prep
+
+// b' per node in double-float, the sweep-0 input, and the norms of the
+// interior right-hand side and of the lifted one; clears the next deposit
+// buffer.  FIX: b' = count * unit2 (fixed-point counts); else b' = rhs *
+// unit64 (FP64 charges).
+template <bool FIX>
+__global__ void __launch_bounds__(256)
+k_prep(const double* __restrict__ rhs, const unsigned long long* __restrict__ cnt, float2 unit2,
+       double unit64, unsigned long long* clear, FieldTables T, DevState* st) {
+  const int M1 = T.M + 1, nr = T.nr;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  float nb = 0.f, nl = 0.f;
+  if (i <= nr && j < M1) {
+    const size_t o = (size_t)i * M1 + j;
+    float2 b;
+    if (FIX) {
+      const unsigned long long c = cnt[o];
+      const float hi = __ull2float_rn(c);
+      const long long rem = (long long)(c - __float2ull_rn(hi));
+      b = df_mul(qts(hi, __ll2float_rn(rem)), unit2);
+    } else {
+      const double x = rhs[o] * unit64;
+      const float hi = (float)x;
+      b = make_float2(hi, (float)(x - (double)hi));
+    }
+    if (clear) clear[o] = 0ull;
+    if (i > 0 && i < nr) {
+      T.b2[o] = b;
+      T.res[o] = b.x;
+      const float zsum = (j == 0 || j == T.M) ? 0.5f * (float)T.hz : (float)T.hz;
+      float lift = 0.f;
+      if (i == 1) lift += T.lift_in * zsum;
+      if (i == nr - 1) lift += T.lift_out * zsum;
+      nb = b.x * b.x;
+      nl = (b.x + lift) * (b.x + lift);
+    }
+  }
+  __shared__ float red[2][8];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, w = tid >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    nl += __shfl_xor_sync(0xffffffffu, nl, o);
+  }
+  if (lane == 0) { red[0][w] = nb; red[1][w] = nl; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, c = 0.0;
+    for (int k = 0; k < (int)(blockDim.x * blockDim.y) / 32; ++k) { a += red[0][k]; c += red[1][k]; }
+    if (a != 0.0) atomicAdd(&st->b2sum, a);
+    if (c != 0.0) atomicAdd(&st->bl2sum, c);
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+      st->solve_done = 0;
+      st->poisson_iters = 0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- DCT-I
 
-// y_k = sum_{j=0}^{M} x_j cos(pi k j / M) for two lines at once.
-// FWD: lines are interior r-lines 1..nr-1 of the right-hand side, output
+// y_k = sum_{j=0}^{M} x_j cos(pi k j / M) for two lines at once, FP32.
+// FWD: lines are interior r-lines 1..nr-1 of T.res, output
 //      bhat[line][k] = scale_k y_k.
-// INV: lines are rows of phihat, output phi[line + 1][k] = phi_vac + y_k.
+// INV: lines are rows of phihat, output phi_rho[line + 1][k] (+)= y_k in
+//      double-float (the first sweep sets, later sweeps add).
 template <bool FWD>
 __global__ void __launch_bounds__(512)
-k_dct_fft(const double* __restrict__ in, double* __restrict__ out,
-          const double2* __restrict__ tw, const double* __restrict__ scale,
-          const double* __restrict__ phi_vac, int NI, int M, int log2N) {
-  extern __shared__ double2 sh[];
-  const int N = 2 * M, M1 = M + 1;
+k_dct32(FieldTables T, const DevState* st, int sweep) {
+  if (sweep > 0 && *(volatile const int*)&st->solve_done) return;
+  extern __shared__ float2 sh[];   // N line values, then N/2 twiddles
+  const int M = T.M, N = 2 * M, M1 = M + 1, NI = T.NI, log2N = T.log2N;
+  float2* tw = sh + N;
   const int line0 = blockIdx.x * 2;
   const bool two = line0 + 1 < NI;
-  const double* x = in + (size_t)(FWD ? line0 + 1 : line0) * M1;
-  const double* y = x + M1;
+  const float* x = FWD ? T.res + (size_t)(line0 + 1) * M1 : T.phihat + (size_t)line0 * M1;
+  const float* y = x + M1;
   for (int n = threadIdx.x; n < N; n += blockDim.x) {
     const int m = n <= M ? n : N - n;
-    sh[__brev(n) >> (32 - log2N)] = make_double2(x[m], two ? y[m] : 0.0);
+    sh[__brev(n) >> (32 - log2N)] = make_float2(x[m], two ? y[m] : 0.f);
+    if (n < N / 2) tw[n] = T.tw32[n];
   }
   __syncthreads();
   for (int s = 1; s <= log2N; ++s) {
@@ -183,239 +331,288 @@ k_dct_fft(const double* __restrict__ in, double* __restrict__ out,
     for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
       const int pos = t & (half - 1);
       const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      const double2 w = __ldg(tw + pos * stride);
-      const double2 a = sh[i0], b = sh[i1];
-      const double2 bw = make_double2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
-      sh[i0] = make_double2(a.x + bw.x, a.y + bw.y);
-      sh[i1] = make_double2(a.x - bw.x, a.y - bw.y);
+      const float2 w = tw[pos * stride];
+      const float2 a = sh[i0], b = sh[i1];
+      const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
+      sh[i0] = make_float2(a.x + bw.x, a.y + bw.y);
+      sh[i1] = make_float2(a.x - bw.x, a.y - bw.y);
     }
     __syncthreads();
   }
-  const double x0 = x[0], xM = x[M];
-  const double y0 = two ? y[0] : 0.0, yM = two ? y[M] : 0.0;
+  const float x0 = x[0], xM = x[M];
+  const float y0 = two ? y[0] : 0.f, yM = two ? y[M] : 0.f;
   for (int k = threadIdx.x; k <= M; k += blockDim.x) {
-    const double sg = (k & 1) ? -1.0 : 1.0;
-    const double2 C = sh[k];
-    const double vx = 0.5 * (C.x + x0 + sg * xM);
-    const double vy = 0.5 * (C.y + y0 + sg * yM);
+    const float sg = (k & 1) ? -1.f : 1.f;
+    const float2 C = sh[k];
+    const float vx = 0.5f * (C.x + x0 + sg * xM);
+    const float vy = 0.5f * (C.y + y0 + sg * yM);
     if (FWD) {
-      out[(size_t)line0 * M1 + k] = vx * scale[k];
-      if (two) out[(size_t)(line0 + 1) * M1 + k] = vy * scale[k];
+      T.bhat[(size_t)line0 * M1 + k] = vx * T.scale32[k];
+      if (two) T.bhat[(size_t)(line0 + 1) * M1 + k] = vy * T.scale32[k];
     } else {
-      out[(size_t)(line0 + 1) * M1 + k] = phi_vac[line0 + 1] + vx;
-      if (two) out[(size_t)(line0 + 2) * M1 + k] = phi_vac[line0 + 2] + vy;
+      float2* p = T.phir + (size_t)(line0 + 1) * M1 + k;
+      *p = sweep == 0 ? make_float2(vx, 0.f) : df_add(*p, make_float2(vx, 0.f));
+      if (two) {
+        p += M1;
+        *p = sweep == 0 ? make_float2(vy, 0.f) : df_add(*p, make_float2(vy, 0.f));
+      }
     }
   }
 }
 
 // direct O(M^2) DCT-I for M that is not a power of two; one line per block
 template <bool FWD>
-__global__ void k_dct_direct(const double* __restrict__ in, double* __restrict__ out,
-                             const double* __restrict__ costab,
-                             const double* __restrict__ scale,
-                             const double* __restrict__ phi_vac, int NI, int M) {
-  extern __shared__ double xs[];
-  const int M1 = M + 1, line = blockIdx.x;
-  const double* x = in + (size_t)(FWD ? line + 1 : line) * M1;
+__global__ void k_dct32_direct(FieldTables T, const DevState* st, int sweep) {
+  if (sweep > 0 && *(volatile const int*)&st->solve_done) return;
+  extern __shared__ float xs[];
+  const int M = T.M, M1 = M + 1, line = blockIdx.x;
+  const float* x = FWD ? T.res + (size_t)(line + 1) * M1 : T.phihat + (size_t)line * M1;
   for (int j = threadIdx.x; j <= M; j += blockDim.x) xs[j] = x[j];
   __syncthreads();
   for (int k = threadIdx.x; k <= M; k += blockDim.x) {
-    double acc = 0.0;
+    float acc = 0.f;
     int m = 0;   // (k j) mod 2M
     for (int j = 0; j <= M; ++j) {
-      acc += xs[j] * costab[m];
+      acc += xs[j] * T.cos32[m];
       m += k;
       if (m >= 2 * M) m -= 2 * M;
     }
-    if (FWD) out[(size_t)line * M1 + k] = acc * scale[k];
-    else out[(size_t)(line + 1) * M1 + k] = phi_vac[line + 1] + acc;
+    if (FWD) {
+      T.bhat[(size_t)line * M1 + k] = acc * T.scale32[k];
+    } else {
+      float2* p = T.phir + (size_t)(line + 1) * M1 + k;
+      *p = sweep == 0 ? make_float2(acc, 0.f) : df_add(*p, make_float2(acc, 0.f));
+    }
   }
 }
 
 // ------------------------------------------------------------- tridiag
 
-// one thread per z-mode: forward and back substitution of the pre-factored
-// Thomas recurrence along the interior r-lines.  The coefficients of kUnroll
-// lines are loaded ahead of the dependent arithmetic, so the recurrence
-// waits for memory once per group of lines rather than once per line.
-constexpr int kUnroll = 8;
-__global__ void __launch_bounds__(64)
-k_tridiag(const double* __restrict__ bhat, double* __restrict__ phihat,
-          const double* __restrict__ a, const double* __restrict__ invd,
-          const double* __restrict__ cp, int NI, int M1) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= M1) return;
-  double y = 0.0;
-  int i0 = 0;
-  for (; i0 + kUnroll <= NI; i0 += kUnroll) {
-    double bb[kUnroll], aa[kUnroll], dd[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const size_t o = (size_t)(i0 + u) * M1 + k;
-      bb[u] = bhat[o]; aa[u] = a[o]; dd[u] = invd[o];
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      y = (bb[u] - aa[u] * y) * dd[u];
-      phihat[(size_t)(i0 + u) * M1 + k] = y;
-    }
-  }
-  for (int i = i0; i < NI; ++i) {
+// One thread per z-mode: forward and back substitution of the pre-factored
+// Thomas recurrence along the interior r-lines (FP32).  A block holds 32
+// consecutive modes; its eight warps first copy the columns it needs into
+// shared memory (independent 128-byte line loads spread over the warps), so
+// the recurrence, run by the first warp, then waits only on shared memory.
+// Right-hand side, sub-diagonal and pivot serve the forward pass; the
+// super-diagonal, loaded during the forward pass, serves the backward pass.
+constexpr int kTriModes = 32;
+constexpr int kTriThreads = 256;
+__global__ void __launch_bounds__(kTriThreads) k_tridiag32(FieldTables T, const DevState* st,
+                                                           int sweep) {
+  if (sweep > 0 && *(volatile const int*)&st->solve_done) return;
+  extern __shared__ float sm[];
+  const int M1 = T.M + 1, NI = T.NI;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = blockIdx.x * kTriModes + lane;
+  const bool in = k < M1;
+  float* sb = sm;                    // NI x 32: right-hand side, then solution
+  float* sa = sm + NI * kTriModes;   // NI x 32: sub-diagonal
+  float* sd = sa + NI * kTriModes;   // NI x 32: 1 / pivot
+  float* sc = sd + NI * kTriModes;   // NI x 32: super-diagonal / pivot
+  for (int i = warp; i < NI; i += kTriThreads / 32) {
     const size_t o = (size_t)i * M1 + k;
-    y = (bhat[o] - a[o] * y) * invd[o];
-    phihat[o] = y;
+    const int q = i * kTriModes + lane;
+    sb[q] = in ? T.bhat[o] : 0.f;
+    sa[q] = in ? T.tri_a[o] : 0.f;
+    sd[q] = in ? T.tri_inv[o] : 0.f;
+    sc[q] = in ? T.tri_cp[o] : 0.f;
   }
-  double xn = 0.0;
-  int i1 = NI - 1;
-  for (; i1 - kUnroll + 1 >= 0; i1 -= kUnroll) {
-    double yy[kUnroll], cc[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const size_t o = (size_t)(i1 - u) * M1 + k;
-      yy[u] = phihat[o]; cc[u] = cp[o];
+  __syncthreads();
+  if (warp == 0) {
+    float y = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < NI; ++i) {
+      const int o = i * kTriModes + lane;
+      y = (sb[o] - sa[o] * y) * sd[o];
+      sb[o] = y;
     }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      xn = yy[u] - cc[u] * xn;
-      phihat[(size_t)(i1 - u) * M1 + k] = xn;
+    float xn = 0.f;
+#pragma unroll 8
+    for (int i = NI - 1; i >= 0; --i) {
+      const int o = i * kTriModes + lane;
+      xn = sb[o] - sc[o] * xn;
+      sb[o] = xn;
     }
   }
-  for (int i = i1; i >= 0; --i) {
-    const size_t o = (size_t)i * M1 + k;
-    xn = phihat[o] - cp[o] * xn;
-    phihat[o] = xn;
-  }
+  __syncthreads();
+  if (in)
+    for (int i = warp; i < NI; i += kTriThreads / 32)
+      T.phihat[(size_t)i * M1 + k] = sb[i * kTriModes + lane];
 }
 
-// ------------------------------------------- E = -grad phi, residual check
+// shared memory of k_tridiag32 (four NI x 32 float arrays); above the
+// default 48 KB the kernel is opted in once
+static size_t tridiag_smem(const FieldTables& T) {
+  return (size_t)4 * T.NI * kTriModes * sizeof(float);
+}
+
+// ------------------------------------ residual, convergence test, E field
+
+__device__ __forceinline__ float df_diff(float2 a, float2 b) {   // a - b to float
+  return (a.x - b.x) + (a.y - b.y);
+}
 
 template <typename Real>
 __global__ void __launch_bounds__(256)
-k_efield_residual(const double* __restrict__ phi, double* rhs, double* rho_last,
-                  typename Vec2<Real>::type* E, FieldTables T, DevState* st,
-                  bool zero_rhs) {
+k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep, int last) {
+  if (sweep > 0 && *(volatile const int*)&st->solve_done) return;
   const int nr = T.nr, M = T.M, M1 = M + 1;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  double rn = 0.0, rd = 0.0;
+  float rn = 0.f;
   if (i <= nr && j <= M) {
     const size_t o = (size_t)i * M1 + j;
-    const double inv2hr = 0.5 / T.hr, inv2hz = 0.5 / T.hz;
-    double dr, dz;
-    if (i == 0) dr = (-3.0 * phi[o] + 4.0 * phi[o + M1] - phi[o + 2 * M1]) * inv2hr;
-    else if (i == nr) dr = (3.0 * phi[o] - 4.0 * phi[o - M1] + phi[o - 2 * M1]) * inv2hr;
-    else dr = (phi[o + M1] - phi[o - M1]) * inv2hr;
-    if (j == 0) dz = (-3.0 * phi[o] + 4.0 * phi[o + 1] - phi[o + 2]) * inv2hz;
-    else if (j == M) dz = (3.0 * phi[o] - 4.0 * phi[o - 1] + phi[o - 2]) * inv2hz;
-    else dz = (phi[o + 1] - phi[o - 1]) * inv2hz;
+    const float2* ph = T.phir;
+    // E = E_vac - grad phi_rho: central differences, one-sided second order
+    // on the boundary lines (phi_rho is zero on the walls)
+    float dr, dz;
+    const float inv2hr = (float)(0.5 / T.hr), inv2hz = (float)(0.5 / T.hz);
+    if (i == 0) dr = (-3.f * ph[o].x + 4.f * ph[o + M1].x - ph[o + 2 * M1].x +
+                      (-3.f * ph[o].y + 4.f * ph[o + M1].y - ph[o + 2 * M1].y)) * inv2hr;
+    else if (i == nr) dr = (3.f * ph[o].x - 4.f * ph[o - M1].x + ph[o - 2 * M1].x +
+                            (3.f * ph[o].y - 4.f * ph[o - M1].y + ph[o - 2 * M1].y)) * inv2hr;
+    else dr = df_diff(ph[o + M1], ph[o - M1]) * inv2hr;
+    if (j == 0) dz = (-3.f * ph[o].x + 4.f * ph[o + 1].x - ph[o + 2].x +
+                      (-3.f * ph[o].y + 4.f * ph[o + 1].y - ph[o + 2].y)) * inv2hz;
+    else if (j == M) dz = (3.f * ph[o].x - 4.f * ph[o - 1].x + ph[o - 2].x +
+                           (3.f * ph[o].y - 4.f * ph[o - 1].y + ph[o - 2].y)) * inv2hz;
+    else dz = df_diff(ph[o + 1], ph[o - 1]) * inv2hz;
     typename Vec2<Real>::type e;
-    e.x = (Real)(-dr);
-    e.y = (Real)(-dz);
+    if constexpr (std::is_same<Real, float>::value) {
+      e.x = T.evac32[i] - dr;
+      e.y = -dz;
+    } else {
+      // FP64 particle path: the same differences of hi + lo in double
+      auto p = [&](size_t q) { return (double)ph[q].x + (double)ph[q].y; };
+      const double i2r = 0.5 / T.hr, i2z = 0.5 / T.hz;
+      double ddr, ddz;
+      if (i == 0) ddr = (-3.0 * p(o) + 4.0 * p(o + M1) - p(o + 2 * M1)) * i2r;
+      else if (i == nr) ddr = (3.0 * p(o) - 4.0 * p(o - M1) + p(o - 2 * M1)) * i2r;
+      else ddr = (p(o + M1) - p(o - M1)) * i2r;
+      if (j == 0) ddz = (-3.0 * p(o) + 4.0 * p(o + 1) - p(o + 2)) * i2z;
+      else if (j == M) ddz = (3.0 * p(o) - 4.0 * p(o - 1) + p(o - 2)) * i2z;
+      else ddz = (p(o + 1) - p(o - 1)) * i2z;
+      e.x = T.evac64[i] - ddr;
+      e.y = -ddz;
+    }
     E[o] = e;
 
-    const double b = rhs[o];
     if (i > 0 && i < nr) {
-      // z operators of the 1D matrices on line i + di
-      const double hz = T.hz;
+      // r = b' - A' phi_rho in double-float
       const bool end = (j == 0 || j == M);
-      const double mzd = end ? hz / 3.0 : 2.0 * hz / 3.0, mzo = hz / 6.0;
-      const double kzd = end ? 1.0 / hz : 2.0 / hz, kzo = -1.0 / hz;
-      double acc = 0.0;
+      const float2 mzd = end ? T.mzd_end : T.mzd_in, kzd = end ? T.kzd_end : T.kzd_in;
+      float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
       for (int di = -1; di <= 1; ++di) {
         const size_t q = o + (ptrdiff_t)di * M1;
-        const double c = phi[q];
-        const double l = j > 0 ? phi[q - 1] : 0.0;
-        const double rr = j < M ? phi[q + 1] : 0.0;
-        const double mz = mzd * c + mzo * ((j > 0 ? l : 0.0) + (j < M ? rr : 0.0));
-        const double kz = kzd * c + kzo * ((j > 0 ? l : 0.0) + (j < M ? rr : 0.0));
-        double kr, mr;
+        const float2 c = ph[q];
+        float2 nb = make_float2(0.f, 0.f);
+        if (j > 0) nb = ph[q - 1];
+        if (j < M) nb = df_add(nb, ph[q + 1]);
+        const float2 mz = df_add(df_mul(mzd, c), df_mul(T.mzo, nb));
+        const float2 kz = df_add(df_mul(kzd, c), df_mul(T.kzo, nb));
+        float2 kr, mr;
         if (di == 0) { kr = T.kr_d[i]; mr = T.mr_d[i]; }
         else if (di < 0) { kr = T.kr_o[i - 1]; mr = T.mr_o[i - 1]; }
         else { kr = T.kr_o[i]; mr = T.mr_o[i]; }
-        acc += kr * mz + mr * kz;
+        acc = df_add(acc, df_add(df_mul(kr, mz), df_mul(mr, kz)));
       }
-      const double twopieps = 2.0 * kPi * kEps0;
-      const double res = b - twopieps * acc;
-      const double zsum = end ? 0.5 * hz : hz;
-      double lift = 0.0;
-      if (i == 1) lift += twopieps * T.kr_o[0] * zsum * phi[j];
-      if (i == nr - 1) lift += twopieps * T.kr_o[nr - 1] * zsum * phi[(size_t)nr * M1 + j];
-      rn = res * res;
-      rd = (b - lift) * (b - lift);
-    }
-    if (zero_rhs) {
-      rho_last[o] = b;
-      rhs[o] = 0.0;
+      const float2 r = df_add(T.b2[o], df_neg(acc));
+      T.res[o] = r.x;
+      rn = r.x * r.x;
     }
   }
-  // block reduction, then the last block evaluates the check
-  __shared__ double red[2][8];
+  // block reduction, then the last block evaluates the stopping test
+  __shared__ float red[8];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, w = tid >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    rn += __shfl_xor_sync(0xffffffffu, rn, o);
-    rd += __shfl_xor_sync(0xffffffffu, rd, o);
-  }
-  if (lane == 0) { red[0][w] = rn; red[1][w] = rd; }
+  for (int o = 16; o > 0; o >>= 1) rn += __shfl_xor_sync(0xffffffffu, rn, o);
+  if (lane == 0) red[w] = rn;
   __syncthreads();
   if (tid == 0) {
-    double a = 0.0, b = 0.0;
-    for (int k = 0; k < (int)(blockDim.x * blockDim.y) / 32; ++k) { a += red[0][k]; b += red[1][k]; }
-    if (a != 0.0) atomicAdd(&st->res_num, a);
-    if (b != 0.0) atomicAdd(&st->res_den, b);
+    double a = 0.0;
+    for (int k = 0; k < (int)(blockDim.x * blockDim.y) / 32; ++k) a += red[k];
+    if (a != 0.0) atomicAdd(&st->r2sum, a);
     __threadfence();
     const unsigned nb = gridDim.x * gridDim.y;
     if (atomicAdd(&st->solve_blocks_done, 1u) == nb - 1) {
       __threadfence();
-      const double num = *(volatile double*)&st->res_num;
-      const double den = *(volatile double*)&st->res_den;
-      const double rel = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? 1.0 : 0.0);
+      const double r2 = *(volatile double*)&st->r2sum;
+      const double b2 = *(volatile double*)&st->b2sum;
+      const double bl2 = *(volatile double*)&st->bl2sum;
+      const double strict = b2 > 0.0 ? sqrt(r2 / b2) : (r2 > 0.0 ? 1.0 : 0.0);
+      const double rel = bl2 > 0.0 ? sqrt(r2 / bl2) : strict;
       st->relres_last = rel;
-      st->poisson_iters = 1;
-      if (!(rel <= T.rtol)) atomicCAS(&st->err, 0, PIC_ENOCONV);
-      st->res_num = 0.0;
-      st->res_den = 0.0;
+      st->relres_strict = strict;
+      st->poisson_iters = sweep + 1;
+      if (strict <= T.rtol || last) {
+        st->solve_done = 1;
+        if (!(rel <= T.rtol)) atomicCAS(&st->err, 0, PIC_ENOCONV);
+        st->b2sum = 0.0;
+        st->bl2sum = 0.0;
+      }
+      st->r2sum = 0.0;
       st->solve_blocks_done = 0u;
     }
   }
 }
 
-template <typename Real>
-void launch_field_solve(const FieldTables& T, double* rhs, double* phi,
-                        void* efield, double* rho_last, DevState* st,
-                        bool zero_rhs, cudaStream_t stream) {
-  const int M1 = T.M + 1, nlines = T.NI;
-  if (T.log2N > 0) {
-    const int N = 2 * T.M;
-    const int threads = std::min(512, std::max(64, N / 2));
-    const size_t smem = (size_t)N * sizeof(double2);
-    const int blocks = (nlines + 1) / 2;
-    k_dct_fft<true><<<blocks, threads, smem, stream>>>(rhs, T.bhat, T.twiddle, T.fwd_scale,
-                                                       T.phi_vac, nlines, T.M, T.log2N);
-    k_tridiag<<<(M1 + 63) / 64, 64, 0, stream>>>(T.bhat, T.phihat, T.tri_a, T.tri_invd,
-                                                  T.tri_cp, nlines, M1);
-    k_dct_fft<false><<<blocks, threads, smem, stream>>>(T.phihat, phi, T.twiddle, T.fwd_scale,
-                                                        T.phi_vac, nlines, T.M, T.log2N);
-  } else {
-    const size_t smem = (size_t)M1 * sizeof(double);
-    k_dct_direct<true><<<nlines, 256, smem, stream>>>(rhs, T.bhat, T.costab, T.fwd_scale,
-                                                      T.phi_vac, nlines, T.M);
-    k_tridiag<<<(M1 + 63) / 64, 64, 0, stream>>>(T.bhat, T.phihat, T.tri_a, T.tri_invd,
-                                                  T.tri_cp, nlines, M1);
-    k_dct_direct<false><<<nlines, 256, smem, stream>>>(T.phihat, phi, T.costab, T.fwd_scale,
-                                                       T.phi_vac, nlines, T.M);
-  }
-  if (efield) {
-    dim3 blk(32, 8), grd((M1 + 31) / 32, (T.nr + 1 + 7) / 8);
-    k_efield_residual<Real><<<grd, blk, 0, stream>>>(
-        phi, rhs, rho_last, (typename Vec2<Real>::type*)efield, T, st, zero_rhs);
+// phi = phi_vac + phi_rho (FP64), on demand
+__global__ void k_phi_out(FieldTables T, double* phi) {
+  const int M1 = T.M + 1;
+  const int n = (T.nr + 1) * M1;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    const float2 p = T.phir[o];
+    phi[o] = T.phi_vac[o / M1] + ((double)p.x + (double)p.y);
   }
 }
 
-template void launch_field_solve<float>(const FieldTables&, double*, double*, void*, double*,
-                                        DevState*, bool, cudaStream_t);
-template void launch_field_solve<double>(const FieldTables&, double*, double*, void*, double*,
-                                         DevState*, bool, cudaStream_t);
+void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream) {
+  const int n = (T.nr + 1) * (T.M + 1);
+  k_phi_out<<<(n + 255) / 256, 256, 0, stream>>>(T, phi);
+}
+
+int field_solve_kernels(const FieldTables& T) { return 1 + 4 * T.maxit; }
+
+template <typename Real>
+void launch_field_solve(const FieldTables& T, const double* rhs, const unsigned long long* cnt,
+                        double cnt_unit, unsigned long long* cnt_clear, void* efield,
+                        DevState* st, cudaStream_t stream) {
+  const int M1 = T.M + 1;
+  dim3 blk(32, 8), grd((M1 + 31) / 32, (T.nr + 1 + 7) / 8);
+  const double s0 = 1.0 / (2.0 * kPi * kEps0);
+  if (tridiag_smem(T) > 48 * 1024)
+    cudaFuncSetAttribute(k_tridiag32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tridiag_smem(T));
+  if (cnt) k_prep<true><<<grd, blk, 0, stream>>>(nullptr, cnt, df_from(cnt_unit * s0), 0.0,
+                                                  cnt_clear, T, st);
+  else k_prep<false><<<grd, blk, 0, stream>>>(rhs, nullptr, make_float2(0.f, 0.f), s0,
+                                               cnt_clear, T, st);
+  for (int s = 0; s < T.maxit; ++s) {
+    if (T.log2N > 0) {
+      const int N = 2 * T.M;
+      const int threads = std::min(512, std::max(32, N / 2));
+      const size_t smem = (size_t)(N + N / 2) * sizeof(float2);
+      const int blocks = (T.NI + 1) / 2;
+      k_dct32<true><<<blocks, threads, smem, stream>>>(T, st, s);
+      k_tridiag32<<<(M1 + kTriModes - 1) / kTriModes, kTriThreads, tridiag_smem(T), stream>>>(T, st, s);
+      k_dct32<false><<<blocks, threads, smem, stream>>>(T, st, s);
+    } else {
+      const size_t smem = (size_t)M1 * sizeof(float);
+      k_dct32_direct<true><<<T.NI, 256, smem, stream>>>(T, st, s);
+      k_tridiag32<<<(M1 + kTriModes - 1) / kTriModes, kTriThreads, tridiag_smem(T), stream>>>(T, st, s);
+      k_dct32_direct<false><<<T.NI, 256, smem, stream>>>(T, st, s);
+    }
+    k_residual<Real><<<grd, blk, 0, stream>>>(T, (typename Vec2<Real>::type*)efield, st, s,
+                                             s == T.maxit - 1);
+  }
+}
+
+template void launch_field_solve<float>(const FieldTables&, const double*,
+                                        const unsigned long long*, double, unsigned long long*,
+                                        void*, DevState*, cudaStream_t);
+template void launch_field_solve<double>(const FieldTables&, const double*,
+                                         const unsigned long long*, double, unsigned long long*,
+                                         void*, DevState*, cudaStream_t);
 
 }  // namespace pic

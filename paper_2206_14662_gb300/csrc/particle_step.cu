@@ -36,11 +36,13 @@ constexpr int kChunk = kThreads * kPPT;
 // unsigned fixed-point numbers (native integer shared atomics, sums that do
 // not depend on the order of the adds): a chunk holds at most kChunk
 // particles of weight <= 1 per node, so kFix = floor((2^32 - 1) / kChunk)
-// cannot overflow; the rounding is 2^-23 of a particle's charge per
-// contribution.  The FP64 path accumulates doubles.
+// cannot overflow even when the private copies are added; the rounding is
+// 2^-23 of a particle's charge per contribution.  The FP64 path accumulates
+// doubles.  cap is the tile's size in words (FP32: four copies of 1024).
 template <typename Real> struct TileT { using type = unsigned; static constexpr int cap = 4096; };
 template <> struct TileT<double> { using type = double; static constexpr int cap = 2048; };
 constexpr float kFix = (float)(4294967295u / kChunk);   // 4194303
+static_assert((double)kFix == kFixUnit, "fixed-point unit shared with the field solve");
 
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
@@ -99,77 +101,184 @@ struct Dep {
   Real fr, fz;
 };
 
-template <typename Real>
-__device__ __forceinline__ void deposit_global(double* rhs, int nzp, int ir,
-                                               int iz, Real fr, Real fz,
-                                               double qw) {
-  const int n00 = ir * nzp + iz;
-  const double a = (double)fr, c = (double)fz;
-  atomicAdd(rhs + n00, qw * ((1.0 - a) * (1.0 - c)));
-  atomicAdd(rhs + n00 + nzp, qw * (a * (1.0 - c)));
-  atomicAdd(rhs + n00 + 1, qw * ((1.0 - a) * c));
-  atomicAdd(rhs + n00 + nzp + 1, qw * (a * c));
+// Deposit grid: the FP32 path accumulates unsigned 64-bit fixed-point hat
+// weights (kFix per particle charge; integer atomics, sums independent of
+// the order of the adds; 3e8 particles on one node stay below 2^63); the
+// FP64 path accumulates the charge q w Lambda in doubles.
+struct DepGrid {
+  double* rhs;                  // FP64 path
+  unsigned long long* cnt;      // FP32 path
+  int nzp;
+  double qw;
+};
+
+__device__ __forceinline__ void deposit_global(const DepGrid& g, int ir, int iz, float fr,
+                                               float fz) {
+  const int n00 = ir * g.nzp + iz;
+  atomicAdd(g.cnt + n00, (unsigned long long)__float2uint_rn((1.f - fr) * (1.f - fz) * kFix));
+  atomicAdd(g.cnt + n00 + g.nzp, (unsigned long long)__float2uint_rn(fr * (1.f - fz) * kFix));
+  atomicAdd(g.cnt + n00 + 1, (unsigned long long)__float2uint_rn((1.f - fr) * fz * kFix));
+  atomicAdd(g.cnt + n00 + g.nzp + 1, (unsigned long long)__float2uint_rn(fr * fz * kFix));
+}
+__device__ __forceinline__ void deposit_global(const DepGrid& g, int ir, int iz, double fr,
+                                               double fz) {
+  const int n00 = ir * g.nzp + iz;
+  atomicAdd(g.rhs + n00, g.qw * ((1.0 - fr) * (1.0 - fz)));
+  atomicAdd(g.rhs + n00 + g.nzp, g.qw * (fr * (1.0 - fz)));
+  atomicAdd(g.rhs + n00 + 1, g.qw * ((1.0 - fr) * fz));
+  atomicAdd(g.rhs + n00 + g.nzp + 1, g.qw * (fr * fz));
 }
 
-// Gather, push, absorb and collide one particle held in registers.
-// Returns the deposit location of the particle (ir < 0 when absorbed).
+// quotient and reciprocal square root: hardware approximations (2 ulp) in
+// the FP32 path, IEEE operations in the FP64 path
+__device__ __forceinline__ float q_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double q_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float q_rsqrt(float a) { return rsqrtf(a); }
+// a b + c with one rounding
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double q_rsqrt(double a) { return 1.0 / sqrt(a); }
+
+template <typename Real>
+struct Part {
+  int cell;
+  Real fr, fz, vr, vt, vz;
+};
+
+// Collision of a particle that passed the null-collision candidate test
+// (rare): type from u1 against the cumulative frequencies, then elastic
+// scattering or ionisation with a child appended.  q holds the state after
+// the move.  The draw-0 Philox block is recomputed here, so the common path
+// carries only the candidate flag.
+template <typename Real>
+__device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, const Soa<Real>& s,
+                                     const DepGrid& g, DevState* st, unsigned* spawn_parent,
+                                     int n_slots, unsigned step, const PushParams<Real>& P,
+                                     BlockTally& bt) {
+  const uint4 xr = philox4x32_10_rk(make_uint4(uid, 0u, step, 0u), P.rk0, P.rk1);
+  atomicAdd(&bt.v[kNCandidate], 1.0);
+  Real ur = q.vr, ut = q.vt, uz = q.vz;
+  const Real v2 = ur * ur + ut * ut + uz * uz;
+  const Real speed = d_sqrt(v2);
+  const Real Ek = P.half_m * v2;
+  const Real nu_el = P.nsig_el * speed;
+  Real sig_io = 0;
+  if (Ek > P.e_th) {
+    const Real qq = (Ek - P.e_th) * P.e_span_inv;
+    sig_io = P.sig_pk * 2 * qq / (1 + qq * qq);
+  }
+  const Real nu_io = P.n_gas * sig_io * speed;
+  if (nu_el + nu_io > P.nu_max) atomicAdd(&bt.v[kNOver], 1.0);
+  const Real x1 = u01<Real>(xr.y) * P.nu_max;
+  if (!(x1 < nu_el + nu_io)) return;   // null collision
+  const Real inv_s = 1 / speed;
+  const Real hr_ = ur * inv_s, ht_ = ut * inv_s, hz_ = uz * inv_s;
+  if (x1 < nu_el) {
+    Real dr, dt, dz;
+    scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), P.xi, dr, dt, dz);
+    Real E1 = Ek;
+    if (P.recoil != 0) {
+      const Real mu = dr * hr_ + dt * ht_ + dz * hz_;
+      E1 = Ek * (1 - P.recoil * (1 - mu));
+      atomicAdd(&bt.v[kRecoilLoss], (double)(Ek - E1));
+    }
+    const Real s1 = d_sqrt(P.two_over_m * E1);
+    q.vr = s1 * dr; q.vt = s1 * dt; q.vz = s1 * dz;
+    atomicAdd(&bt.v[kNElastic], 1.0);
+    return;
+  }
+  const uint4 x2 = philox4x32_10_rk(make_uint4(uid, 0u, step, 1u), P.rk0, P.rk1);
+  const Real E_rem = Ek - P.e_th;
+  const Real E2 = P.opal_b * d_tan(u01<Real>(x2.x) * d_atan(E_rem / (2 * P.opal_b)));
+  const Real E1 = E_rem - E2;
+  Real d1r, d1t, d1z, d2r, d2t, d2z;
+  scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), P.xi, d1r, d1t, d1z);
+  scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(x2.y), u01<Real>(x2.z), P.xi, d2r, d2t, d2z);
+  const Real s1 = d_sqrt(P.two_over_m * E1), s2 = d_sqrt(P.two_over_m * E2);
+  q.vr = s1 * d1r; q.vt = s1 * d1t; q.vz = s1 * d1z;
+  atomicAdd(&bt.v[kIonLoss], (double)P.e_th);
+  atomicAdd(&bt.v[kNIonise], 1.0);
+  const long long k = (long long)atomicAdd((unsigned long long*)&st->n_spawn, 1ull);
+  const long long slot = (long long)n_slots + k;
+  if (k < P.spawn_cap && slot < P.capacity) {
+    s.cell[slot] = q.cell;
+    s.offr[slot] = q.fr;
+    s.offz[slot] = q.fz;
+    s.vr[slot] = s2 * d2r;
+    s.vt[slot] = s2 * d2t;
+    s.vz[slot] = s2 * d2z;
+    s.uid[slot] = 0u;   // fixed by the child-uid kernel
+    spawn_parent[k] = uid;
+    deposit_global(g, q.cell >> 16, q.cell & 0xFFFF, q.fr, q.fz);
+  } else {
+    set_error(st, PIC_ECAPACITY);
+  }
+}
+
+// Gather, push, absorb and test for a collision one particle held in
+// registers; the new state is returned in q (cell -1 when absorbed) and
+// the deposit location in the result (ir < 0 when absorbed).  Every
+// multiply-add is written out (mad), and the file is compiled without
+// automatic contraction, so each particle is computed by the same sequence
+// of roundings whichever slot of its thread it occupies (results do not
+// depend on the particle order the sort leaves).
 template <typename Real>
 __device__ __forceinline__ Dep<Real> advance(
-    long long p, int cell, Real fr, Real fz, Real vr, Real vt, Real vz,
-    unsigned uid, const typename Vec2<Real>::type* __restrict__ E,
-    const Soa<Real>& s, double* rhs, DevState* st, unsigned* spawn_parent,
-    long long n_slots, unsigned step, const PushParams<Real>& P,
-    BlockTally& bt, Real& work) {
+    Part<Real>& q, unsigned uid, const typename Vec2<Real>::type* __restrict__ E,
+    const Soa<Real>& s, const DepGrid& g, DevState* st, unsigned* spawn_parent, int n_slots,
+    unsigned step, const PushParams<Real>& P, BlockTally& bt, Real& work) {
   using V2 = typename Vec2<Real>::type;
   Dep<Real> dep;
   const int nzp = P.nz + 1;
-  int ir = cell >> 16, iz = cell & 0xFFFF;
-  const Real r = P.r_in + ((Real)ir + fr) * P.hr;
-  const Real z = P.z_min + ((Real)iz + fz) * P.hz;
+  const int ir = q.cell >> 16, iz = q.cell & 0xFFFF;
+  const Real fr = q.fr, fz = q.fz, vr = q.vr, vt = q.vt, vz = q.vz;
+  const Real r = mad((Real)ir + fr, P.hr, P.r_in);
 
   // gather: bilinear weights of the four nodes of the cell
   const int n00 = ir * nzp + iz;
   const V2 e00 = __ldg(E + n00), e01 = __ldg(E + n00 + 1);
   const V2 e10 = __ldg(E + n00 + nzp), e11 = __ldg(E + n00 + nzp + 1);
-  const Real w00 = (1 - fr) * (1 - fz), w10 = fr * (1 - fz);
-  const Real w01 = (1 - fr) * fz, w11 = fr * fz;
-  const Real Er = w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x;
-  const Real Ez = w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y;
+  const Real gr = 1 - fr, gz = 1 - fz;
+  const Real w00 = gr * gz, w10 = fr * gz, w01 = gr * fz, w11 = fr * fz;
+  const Real Er = mad(w11, e11.x, mad(w01, e01.x, mad(w10, e10.x, w00 * e00.x)));
+  const Real Ez = mad(w11, e11.y, mad(w01, e01.y, mad(w10, e10.y, w00 * e00.y)));
   Real Br = 0, Bz = P.b0;
   if (P.bkind == 1) {
-    const Real zeta = z - P.z_mid;
-    Bz = P.b0 * (1 + 2 * zeta * zeta * P.inv_L2);
+    const Real zeta = mad((Real)iz + fz, P.hz, P.z_min) - P.z_mid;
+    Bz = P.b0 * mad(2 * zeta * zeta, P.inv_L2, Real(1));
     Br = -2 * P.b0 * r * zeta * P.inv_L2;
   }
 
   // Boris: half kick, rotation about B, half kick (components r, theta, z)
-  const Real vmr = vr + P.qmdt2 * Er, vmt = vt, vmz = vz + P.qmdt2 * Ez;
+  const Real vmr = mad(P.qmdt2, Er, vr), vmt = vt, vmz = mad(P.qmdt2, Ez, vz);
   const Real tr = P.qmdt2 * Br, tz = P.qmdt2 * Bz;
-  const Real sf = 2 / (1 + tr * tr + tz * tz);
+  const Real sf = q_div(Real(2), mad(tz, tz, mad(tr, tr, Real(1))));
   const Real sr = sf * tr, sz = sf * tz;
-  const Real qr = vmr + vmt * tz;
+  const Real qr = mad(vmt, tz, vmr);
   const Real qt = vmt + (vmz * tr - vmr * tz);
-  const Real qz = vmz - vmt * tr;
-  const Real vpr = vmr + qt * sz;
+  const Real qz = mad(-vmt, tr, vmz);
+  const Real vpr = mad(qt, sz, vmr);
   const Real vpt = vmt + (qz * sr - qr * sz);
-  const Real vpz = vmz - qt * sr;
-  const Real vnr = vpr + P.qmdt2 * Er, vnt = vpt, vnz = vpz + P.qmdt2 * Ez;
+  const Real vpz = mad(-qt, sr, vmz);
+  const Real vnr = mad(P.qmdt2, Er, vpr), vnt = vpt, vnz = mad(P.qmdt2, Ez, vpz);
   // work of the two half kicks, (q dt / 4) E . (v + v- + v+ + v_new)
-  work += Er * (vr + vmr + vpr + vnr) + Ez * (vz + vmz + vpz + vnz);
+  work = mad(Ez, (vz + vmz) + (vpz + vnz), mad(Er, (vr + vmr) + (vpr + vnr), work));
 
   // move in the local Cartesian frame; the radial step is formed without
   // cancellation: r1 - r = dt (2 r vr + (vr^2 + vt^2) dt) / (r + r1)
-  const Real x = r + vnr * P.dt, y = vnt * P.dt;
-  const Real r1 = d_sqrt(x * x + y * y);
-  const Real dr_cells =
-      P.dt * (2 * r * vnr + (vnr * vnr + vnt * vnt) * P.dt) / (r + r1) * P.inv_hr;
+  const Real x = mad(vnr, P.dt, r), y = vnt * P.dt;
+  const Real rr = mad(y, y, x * x);
+  const Real inv_r1 = q_rsqrt(rr);
+  const Real r1 = rr * inv_r1;
+  const Real v2p = mad(vnt, vnt, vnr * vnr);
+  const Real dr_cells = q_div(P.dt * mad(v2p, P.dt, 2 * r * vnr), r + r1) * P.inv_hr;
   const Real dz_cells = vnz * P.dt * P.inv_hz;
   Real fr1 = fr + dr_cells, fz1 = fz + dz_cells;
   // cell jumps beyond +-2^20 cells (non-physical speeds) are clamped before
   // the integer conversion; they end outside the grid and are absorbed
   const Real jmax = Real(1048576);
-  Real flr = fmin(fmax(d_floor(fr1), -jmax), jmax);
-  Real flz = fmin(fmax(d_floor(fz1), -jmax), jmax);
+  const Real flr = fmin(fmax(d_floor(fr1), -jmax), jmax);
+  const Real flz = fmin(fmax(d_floor(fz1), -jmax), jmax);
   int ir1 = ir + (int)flr, iz1 = iz + (int)flz;
   fr1 -= flr;
   fz1 -= flz;
@@ -187,237 +296,212 @@ __device__ __forceinline__ Dep<Real> advance(
     const Real s0r = (Real)ir + fr, s0z = (Real)iz + fz;
     Real tb = 3;
     int wall = 0;
-    if (out_in) { Real t = -s0r / dr_cells; if (t < tb) { tb = t; wall = 0; } }
-    if (out_out) { Real t = ((Real)P.nr - s0r) / dr_cells; if (t < tb) { tb = t; wall = 1; } }
-    if (out_zl) { Real t = -s0z / dz_cells; if (t < tb) { tb = t; wall = 2; } }
-    if (out_zh) { Real t = ((Real)P.nz - s0z) / dz_cells; if (t < tb) { tb = t; wall = 3; } }
+    if (out_in) { const Real t = -s0r / dr_cells; if (t < tb) { tb = t; wall = 0; } }
+    if (out_out) { const Real t = ((Real)P.nr - s0r) / dr_cells; if (t < tb) { tb = t; wall = 1; } }
+    if (out_zl) { const Real t = -s0z / dz_cells; if (t < tb) { tb = t; wall = 2; } }
+    if (out_zh) { const Real t = ((Real)P.nz - s0z) / dz_cells; if (t < tb) { tb = t; wall = 3; } }
     atomicAdd(&bt.v[kAbsInner + wall], 1.0);
-    atomicAdd(&bt.v[kKeAbsorbed], (double)(P.half_m * (vnr * vnr + vnt * vnt + vnz * vnz)));
+    atomicAdd(&bt.v[kKeAbsorbed], (double)(P.half_m * mad(vnz, vnz, v2p)));
     atomicAdd(&bt.v[kNAbsorbed], 1.0);
-    s.cell[p] = -1;
+    q.cell = -1;
     dep.ir = -1;
     return dep;
   }
 
   // rotate (vr, vtheta) into the basis at the new position
-  const Real ir1f = 1 / r1;
-  const Real c = x * ir1f, sn = y * ir1f;
-  Real ur = c * vnr + sn * vnt;
-  Real ut = -sn * vnr + c * vnt;
-  Real uz = vnz;
+  const Real c = x * inv_r1, sn = y * inv_r1;
+  q.cell = (ir1 << 16) | iz1;
+  q.fr = fr1; q.fz = fz1;
+  q.vr = mad(sn, vnt, c * vnr);
+  q.vt = mad(c, vnt, -sn * vnr);
+  q.vz = vnz;
 
-  // null-collision Monte Carlo
-  const uint4 xr = philox4x32_10(make_uint4(uid, 0u, step, 0u), P.seed_lo, P.seed_hi);
-  if ((xr.x >> 8) < P.thr_null) {
-    atomicAdd(&bt.v[kNCandidate], 1.0);
-    const Real v2 = ur * ur + ut * ut + uz * uz;
-    const Real speed = d_sqrt(v2);
-    const Real Ek = P.half_m * v2;
-    const Real nu_el = P.nsig_el * speed;
-    Real sig_io = 0;
-    if (Ek > P.e_th) {
-      const Real q = (Ek - P.e_th) * P.e_span_inv;
-      sig_io = P.sig_pk * 2 * q / (1 + q * q);
-    }
-    const Real nu_io = P.n_gas * sig_io * speed;
-    if (nu_el + nu_io > P.nu_max) atomicAdd(&bt.v[kNOver], 1.0);
-    const Real x1 = u01<Real>(xr.y) * P.nu_max;
-    if (x1 < nu_el + nu_io) {
-      const Real inv_s = 1 / speed;
-      const Real hr_ = ur * inv_s, ht_ = ut * inv_s, hz_ = uz * inv_s;
-      if (x1 < nu_el) {
-        Real dr, dt, dz;
-        scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), P.xi, dr, dt, dz);
-        Real E1 = Ek;
-        if (P.recoil != 0) {
-          const Real mu = dr * hr_ + dt * ht_ + dz * hz_;
-          E1 = Ek * (1 - P.recoil * (1 - mu));
-          atomicAdd(&bt.v[kRecoilLoss], (double)(Ek - E1));
-        }
-        const Real s1 = d_sqrt(P.two_over_m * E1);
-        ur = s1 * dr; ut = s1 * dt; uz = s1 * dz;
-        atomicAdd(&bt.v[kNElastic], 1.0);
-      } else {
-        const uint4 x2 = philox4x32_10(make_uint4(uid, 0u, step, 1u), P.seed_lo, P.seed_hi);
-        const Real E_rem = Ek - P.e_th;
-        const Real E2 = P.opal_b * d_tan(u01<Real>(x2.x) * d_atan(E_rem / (2 * P.opal_b)));
-        const Real E1 = E_rem - E2;
-        Real d1r, d1t, d1z, d2r, d2t, d2z;
-        scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), P.xi, d1r, d1t, d1z);
-        scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(x2.y), u01<Real>(x2.z), P.xi, d2r, d2t, d2z);
-        const Real s1 = d_sqrt(P.two_over_m * E1), s2 = d_sqrt(P.two_over_m * E2);
-        ur = s1 * d1r; ut = s1 * d1t; uz = s1 * d1z;
-        atomicAdd(&bt.v[kIonLoss], (double)P.e_th);
-        atomicAdd(&bt.v[kNIonise], 1.0);
-        const long long k = atomicAdd((unsigned long long*)&st->n_spawn, 1ull);
-        const long long slot = n_slots + k;
-        if (k < P.spawn_cap && slot < P.capacity) {
-          s.cell[slot] = (ir1 << 16) | iz1;
-          s.offr[slot] = fr1;
-          s.offz[slot] = fz1;
-          s.vr[slot] = s2 * d2r;
-          s.vt[slot] = s2 * d2t;
-          s.vz[slot] = s2 * d2z;
-          s.uid[slot] = 0u;   // fixed by the child-uid kernel
-          spawn_parent[k] = uid;
-          deposit_global<Real>(rhs, nzp, ir1, iz1, fr1, fz1, P.qw);
-        } else {
-          set_error(st, PIC_ECAPACITY);
-        }
-      }
-    }
-  }
-
-  s.cell[p] = (ir1 << 16) | iz1;
-  s.offr[p] = fr1;
-  s.offz[p] = fz1;
-  s.vr[p] = ur;
-  s.vt[p] = ut;
-  s.vz[p] = uz;
+  // null-collision candidate test: the integer form of u0 < P_null
+  const uint4 xr = philox4x32_10_rk(make_uint4(uid, 0u, step, 0u), P.rk0, P.rk1);
+  if ((xr.x >> 8) < P.thr_null) collide<Real>(q, uid, s, g, st, spawn_parent, n_slots, step, P, bt);
   dep.ir = ir1; dep.iz = iz1; dep.fr = fr1; dep.fz = fz1;
   return dep;
 }
 
+// Particles [p0, p0 + kPPT) of one thread.  In the FP32 path the thread's
+// four slots are consecutive and move as 16-byte vectors with streaming
+// cache hints (each array is read and written once per step); the FP64
+// path and the ragged end of the store use scalar accesses.
 template <typename Real>
-__global__ void __launch_bounds__(kThreads)
-k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E,
-                double* __restrict__ rhs, DevState* st,
-                unsigned* __restrict__ spawn_parent, PushParams<Real> P) {
-  using TT = typename TileT<Real>::type;
-  constexpr int kCap = TileT<Real>::cap;
-  __shared__ TT tile[kCap];
-  __shared__ int bbox[2][4];   // min ir, max ir, min iz, max iz
-  __shared__ BlockTally bt;
+__device__ __forceinline__ bool load_group(const Soa<Real>& s, int p0, int n, Part<Real>* q,
+                                           unsigned* uid) {
+  if constexpr (std::is_same<Real, float>::value) {
+    if (p0 + kPPT <= n) {
+      const int4 c = __ldcs(reinterpret_cast<const int4*>(s.cell + p0));
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(s.offr + p0));
+      const float4 b = __ldcs(reinterpret_cast<const float4*>(s.offz + p0));
+      const float4 d = __ldcs(reinterpret_cast<const float4*>(s.vr + p0));
+      const float4 e = __ldcs(reinterpret_cast<const float4*>(s.vt + p0));
+      const float4 f = __ldcs(reinterpret_cast<const float4*>(s.vz + p0));
+      const uint4 u = __ldcs(reinterpret_cast<const uint4*>(s.uid + p0));
+      q[0] = {c.x, a.x, b.x, d.x, e.x, f.x};
+      q[1] = {c.y, a.y, b.y, d.y, e.y, f.y};
+      q[2] = {c.z, a.z, b.z, d.z, e.z, f.z};
+      q[3] = {c.w, a.w, b.w, d.w, e.w, f.w};
+      uid[0] = u.x; uid[1] = u.y; uid[2] = u.z; uid[3] = u.w;
+      return true;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPPT; ++k) {
+    const int p = p0 + k;
+    if (p < n) {
+      q[k] = {s.cell[p], s.offr[p], s.offz[p], s.vr[p], s.vt[p], s.vz[p]};
+      uid[k] = s.uid[p];
+    } else {
+      q[k].cell = -1;
+      uid[k] = 0u;
+    }
+  }
+  return false;
+}
 
-  const int tid = threadIdx.x, lane = tid & 31;
-  const long long n_slots = *(volatile long long*)&st->n_slots;
-  const unsigned step = *(volatile unsigned*)&st->step;
-  const int nzp = P.nz + 1;
-  if (tid < kTallyCount) bt.v[tid] = 0.0;
-  if (tid < 8) {
-    bbox[tid >> 2][tid & 3] = (tid & 1) ? INT_MIN : INT_MAX;
+template <typename Real>
+__device__ __forceinline__ void store_group(const Soa<Real>& s, int p0, int n, const Part<Real>* q,
+                                            const bool* live, bool vec) {
+  if constexpr (std::is_same<Real, float>::value) {
+    if (vec) {
+      __stcs(reinterpret_cast<int4*>(s.cell + p0), make_int4(q[0].cell, q[1].cell, q[2].cell, q[3].cell));
+      __stcs(reinterpret_cast<float4*>(s.offr + p0), make_float4(q[0].fr, q[1].fr, q[2].fr, q[3].fr));
+      __stcs(reinterpret_cast<float4*>(s.offz + p0), make_float4(q[0].fz, q[1].fz, q[2].fz, q[3].fz));
+      __stcs(reinterpret_cast<float4*>(s.vr + p0), make_float4(q[0].vr, q[1].vr, q[2].vr, q[3].vr));
+      __stcs(reinterpret_cast<float4*>(s.vt + p0), make_float4(q[0].vt, q[1].vt, q[2].vt, q[3].vt));
+      __stcs(reinterpret_cast<float4*>(s.vz + p0), make_float4(q[0].vz, q[1].vz, q[2].vz, q[3].vz));
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPPT; ++k) {
+    const int p = p0 + k;
+    if (p < n && live[k]) {   // holes stay untouched
+      s.cell[p] = q[k].cell;
+      s.offr[p] = q[k].fr;
+      s.offz[p] = q[k].fz;
+      s.vr[p] = q[k].vr;
+      s.vt[p] = q[k].vt;
+      s.vz[p] = q[k].vz;
+    }
+  }
+}
+
+// Deposit of one chunk: the chunk's node bounding box is reduced over the
+// block; if it fits the shared tile the block accumulates there and flushes
+// one global atomic per touched node, otherwise every particle deposits
+// with global atomics.  Contains two block barriers; every thread of the
+// block must call it.
+//
+// FP32 tile: unsigned fixed-point weights, native integer shared atomics.
+// Cell-sorted particles put whole warps on the same four nodes, and
+// same-address atomics of one instruction serialise; so the tile is kept in
+// kCopies private copies (lane & 3 picks the copy) and each lane issues its
+// four corner updates in an order rotated by (lane >> 2) & 3.  Lanes of one
+// cell then hit 16 different words per instruction.  The flush adds the
+// copies.
+constexpr int kCopies = 4;
+constexpr int kCapF = 1024;   // nodes per FP32 tile copy
+
+template <typename Real, int kCap>
+__device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename TileT<Real>::type* tile,
+                                              int (*bbox)[4], int buf, const DepGrid& g, int tid,
+                                              int lane) {
+  using TT = typename TileT<Real>::type;
+  constexpr bool f32 = std::is_same<Real, float>::value;
+  constexpr int cap = f32 ? kCapF : kCap;
+  int lo_r = INT_MAX, hi_r = INT_MIN, lo_z = INT_MAX, hi_z = INT_MIN;
+#pragma unroll
+  for (int k = 0; k < kPPT; ++k) {
+    if (dep[k].ir >= 0) {
+      lo_r = min(lo_r, dep[k].ir); hi_r = max(hi_r, dep[k].ir);
+      lo_z = min(lo_z, dep[k].iz); hi_z = max(hi_z, dep[k].iz);
+    }
+  }
+  lo_r = __reduce_min_sync(0xffffffffu, lo_r);
+  hi_r = __reduce_max_sync(0xffffffffu, hi_r);
+  lo_z = __reduce_min_sync(0xffffffffu, lo_z);
+  hi_z = __reduce_max_sync(0xffffffffu, hi_z);
+  if (lane == 0 && lo_r <= hi_r) {
+    atomicMin(&bbox[buf][0], lo_r); atomicMax(&bbox[buf][1], hi_r);
+    atomicMin(&bbox[buf][2], lo_z); atomicMax(&bbox[buf][3], hi_z);
   }
   __syncthreads();
-  Real work = 0;
-  int pushed = 0;
-  int buf = 0;
-
-  for (long long base = (long long)blockIdx.x * kChunk; base < n_slots;
-       base += (long long)gridDim.x * kChunk) {
-    // load the chunk's particles first (coalesced, one field array at a
-    // time) so that all loads are in flight before any arithmetic
-    int cell[kPPT];
-    Real fr[kPPT], fz[kPPT], vr[kPPT], vt[kPPT], vz[kPPT];
-    unsigned uid[kPPT];
+  const int br0 = bbox[buf][0], br1 = bbox[buf][1];
+  const int bz0 = bbox[buf][2], bz1 = bbox[buf][3];
+  if (tid < 4) bbox[buf ^ 1][tid] = (tid & 1) ? INT_MIN : INT_MAX;
+  const int rows = br1 - br0 + 2, cols = bz1 - bz0 + 2;
+  const bool any = br0 <= br1;
+  const bool use_tile = any && rows * cols <= cap;
+  const int warp = tid >> 5;
+  if (use_tile) {
+    for (int t = tid; t < rows * cols; t += kThreads) {
+      if constexpr (f32) {
 #pragma unroll
-    for (int k = 0; k < kPPT; ++k) {
-      const long long p = base + k * kThreads + tid;
-      const bool in = p < n_slots;
-      cell[k] = in ? s.cell[p] : -1;
-      fr[k] = in ? s.offr[p] : Real(0);
-      fz[k] = in ? s.offz[p] : Real(0);
-      vr[k] = in ? s.vr[p] : Real(0);
-      vt[k] = in ? s.vt[p] : Real(0);
-      vz[k] = in ? s.vz[p] : Real(0);
-      uid[k] = in ? s.uid[p] : 0u;
-    }
-    Dep<Real> dep[kPPT];
-#pragma unroll
-    for (int k = 0; k < kPPT; ++k) {
-      const long long p = base + k * kThreads + tid;
-      dep[k].ir = -1;
-      if (cell[k] >= 0) {
-        ++pushed;
-        dep[k] = advance<Real>(p, cell[k], fr[k], fz[k], vr[k], vt[k], vz[k], uid[k], E,
-                               s, rhs, st, spawn_parent, n_slots, step, P, bt, work);
+        for (int c = 0; c < kCopies; ++c) tile[c * kCapF + t] = 0u;
+      } else {
+        tile[t] = TT(0);
       }
     }
-
-    // bounding box of the chunk's deposit cells
-    int lo_r = INT_MAX, hi_r = INT_MIN, lo_z = INT_MAX, hi_z = INT_MIN;
-#pragma unroll
-    for (int k = 0; k < kPPT; ++k) {
-      if (dep[k].ir >= 0) {
-        lo_r = min(lo_r, dep[k].ir); hi_r = max(hi_r, dep[k].ir);
-        lo_z = min(lo_z, dep[k].iz); hi_z = max(hi_z, dep[k].iz);
-      }
-    }
-    lo_r = __reduce_min_sync(0xffffffffu, lo_r);
-    hi_r = __reduce_max_sync(0xffffffffu, hi_r);
-    lo_z = __reduce_min_sync(0xffffffffu, lo_z);
-    hi_z = __reduce_max_sync(0xffffffffu, hi_z);
-    if (lane == 0 && lo_r <= hi_r) {
-      atomicMin(&bbox[buf][0], lo_r); atomicMax(&bbox[buf][1], hi_r);
-      atomicMin(&bbox[buf][2], lo_z); atomicMax(&bbox[buf][3], hi_z);
-    }
-    __syncthreads();
-    const int br0 = bbox[buf][0], br1 = bbox[buf][1];
-    const int bz0 = bbox[buf][2], bz1 = bbox[buf][3];
-    if (tid < 4) bbox[buf ^ 1][tid] = (tid & 1) ? INT_MIN : INT_MAX;
-    const int rows = br1 - br0 + 2, cols = bz1 - bz0 + 2;
-    const bool any = br0 <= br1;
-    const bool use_tile = any && rows * cols <= kCap;
-    if (use_tile) {
-      for (int t = tid; t < rows * cols; t += kThreads) tile[t] = TT(0);
-    }
-    __syncthreads();
-    if (use_tile) {
-#pragma unroll
-      for (int k = 0; k < kPPT; ++k) {
-        const bool has = dep[k].ir >= 0;
-        const int t = has ? (dep[k].ir - br0) * cols + (dep[k].iz - bz0) : -1;
-        if constexpr (std::is_same<Real, float>::value) {
-          // lanes in the same cell add the same four nodes: sum their
-          // fixed-point weights first, one lane per cell does the atomics
-          const float a = dep[k].fr, c = dep[k].fz;
-          const unsigned q00 = has ? __float2uint_rn((1.f - a) * (1.f - c) * kFix) : 0u;
-          const unsigned q10 = has ? __float2uint_rn(a * (1.f - c) * kFix) : 0u;
-          const unsigned q01 = has ? __float2uint_rn((1.f - a) * c * kFix) : 0u;
-          const unsigned q11 = has ? __float2uint_rn(a * c * kFix) : 0u;
-          const unsigned peers = __match_any_sync(0xffffffffu, t);
-          const unsigned s00 = __reduce_add_sync(peers, q00);
-          const unsigned s10 = __reduce_add_sync(peers, q10);
-          const unsigned s01 = __reduce_add_sync(peers, q01);
-          const unsigned s11 = __reduce_add_sync(peers, q11);
-          if (has && lane == __ffs(peers) - 1) {
-            atomicAdd(&tile[t], s00);
-            atomicAdd(&tile[t + cols], s10);
-            atomicAdd(&tile[t + 1], s01);
-            atomicAdd(&tile[t + cols + 1], s11);
-          }
-        } else {
-          if (has) {
-            const TT a = (TT)dep[k].fr, c = (TT)dep[k].fz;
-            atomicAdd(&tile[t], (TT(1) - a) * (TT(1) - c));
-            atomicAdd(&tile[t + cols], a * (TT(1) - c));
-            atomicAdd(&tile[t + 1], (TT(1) - a) * c);
-            atomicAdd(&tile[t + cols + 1], a * c);
-          }
-        }
-      }
-    } else if (any) {
-#pragma unroll
-      for (int k = 0; k < kPPT; ++k)
-        if (dep[k].ir >= 0)
-          deposit_global<Real>(rhs, nzp, dep[k].ir, dep[k].iz, dep[k].fr, dep[k].fz, P.qw);
-    }
-    __syncthreads();
-    if (use_tile) {
-      const double unit = std::is_same<Real, float>::value ? P.qw / (double)kFix : P.qw;
-      for (int t = tid; t < rows * cols; t += kThreads) {
-        const TT v = tile[t];
-        if (v != TT(0)) {
-          const int rr = t / cols, cc = t - rr * cols;
-          atomicAdd(rhs + (br0 + rr) * nzp + (bz0 + cc), unit * (double)v);
-        }
-      }
-    }
-    buf ^= 1;
   }
+  __syncthreads();
+  if (use_tile) {
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+      if (dep[k].ir < 0) continue;
+      const int t = (dep[k].ir - br0) * cols + (dep[k].iz - bz0);
+      if constexpr (f32) {
+        const float a = dep[k].fr, c = dep[k].fz;
+        unsigned* tc = tile + (lane & 3) * kCapF + t;
+        const int rot = (lane >> 2) & 3;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int j = (m + rot) & 3;   // corner: bit 0 along r, bit 1 along z
+          const float wr = (j & 1) ? a : 1.f - a;
+          const float wz = (j & 2) ? c : 1.f - c;
+          atomicAdd(tc + ((j & 1) ? cols : 0) + (j >> 1), __float2uint_rn(wr * wz * kFix));
+        }
+      } else {
+        const TT a = (TT)dep[k].fr, c = (TT)dep[k].fz;
+        atomicAdd(&tile[t], (TT(1) - a) * (TT(1) - c));
+        atomicAdd(&tile[t + cols], a * (TT(1) - c));
+        atomicAdd(&tile[t + 1], (TT(1) - a) * c);
+        atomicAdd(&tile[t + cols + 1], a * c);
+      }
+    }
+  } else if (any) {
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k)
+      if (dep[k].ir >= 0) deposit_global(g, dep[k].ir, dep[k].iz, dep[k].fr, dep[k].fz);
+  }
+  __syncthreads();
+  if (use_tile) {
+    // one warp per tile row, lanes along z: coalesced atomics, no division
+    for (int rr = warp; rr < rows; rr += kThreads / 32) {
+      for (int cc = lane; cc < cols; cc += 32) {
+        const int t = rr * cols + cc;
+        const int node = (br0 + rr) * g.nzp + (bz0 + cc);
+        if constexpr (f32) {
+          const unsigned v = tile[t] + tile[kCapF + t] + tile[2 * kCapF + t] + tile[3 * kCapF + t];
+          if (v) atomicAdd(g.cnt + node, (unsigned long long)v);
+        } else {
+          const TT v = tile[t];
+          if (v != TT(0)) atomicAdd(g.rhs + node, g.qw * (double)v);
+        }
+      }
+    }
+  }
+}
 
-  // block tallies: the work sum, then one global atomic per non-zero slot
+// block tallies: the work sum and particle count, then one global atomic
+// per non-zero slot (weights and energies scaled by the macro weight)
+template <typename Real>
+__device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pushed, DevState* st,
+                                              const PushParams<Real>& P, int tid, int lane) {
   double w = (double)work;
-  int np = __reduce_add_sync(0xffffffffu, pushed);
+  const int np = __reduce_add_sync(0xffffffffu, pushed);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
   if (lane == 0 && w != 0.0) atomicAdd(&bt.v[kWorkE], w);
@@ -434,13 +518,66 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E,
   }
 }
 
+// resident blocks per SM the FP32 kernel is compiled for (register cap)
+#ifndef PIC_MIN_BLOCKS
+#define PIC_MIN_BLOCKS 4
+#endif
+
+// Each thread loads its kPPT consecutive particles directly (16-byte vector
+// loads with streaming hints in the FP32 path), advances them, stores them
+// back and joins the block's tile deposit.
+template <typename Real>
+__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 2)
+k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, DepGrid g,
+                DevState* st, unsigned* __restrict__ spawn_parent, PushParams<Real> P) {
+  using TT = typename TileT<Real>::type;
+  constexpr int kCap = TileT<Real>::cap;
+  __shared__ TT tile[kCap];
+  __shared__ int bbox[2][4];   // min ir, max ir, min iz, max iz
+  __shared__ BlockTally bt;
+
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int n_slots = (int)*(volatile long long*)&st->n_slots;
+  const unsigned step = *(volatile unsigned*)&st->step;
+  if (tid < kTallyCount) bt.v[tid] = 0.0;
+  if (tid < 8) bbox[tid >> 2][tid & 3] = (tid & 1) ? INT_MIN : INT_MAX;
+  __syncthreads();
+  Real work = 0;
+  int pushed = 0;
+  int buf = 0;
+
+  for (int base = blockIdx.x * kChunk; base < n_slots; base += gridDim.x * kChunk) {
+    // the chunk's particles: thread tid holds slots base + kPPT tid + k
+    const int p0 = base + kPPT * tid;
+    Part<Real> q[kPPT];
+    unsigned uid[kPPT];
+    const bool vec = load_group<Real>(s, p0, n_slots, q, uid);
+    Dep<Real> dep[kPPT];
+    bool live[kPPT];
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+      dep[k].ir = -1;
+      live[k] = q[k].cell >= 0;
+      if (live[k]) {
+        ++pushed;
+        dep[k] = advance<Real>(q[k], uid[k], E, s, g, st, spawn_parent, n_slots, step, P, bt,
+                               work);
+      }
+    }
+    store_group<Real>(s, p0, n_slots, q, live, vec);
+    deposit_chunk<Real, kCap>(dep, tile, bbox, buf, g, tid, lane);
+    buf ^= 1;
+  }
+  flush_tallies<Real>(bt, work, pushed, st, P, tid, lane);
+}
+
 template <typename Real>
 void launch_particle_step(const Soa<Real>& s, const void* efield, double* rhs,
-                          DevState* st, unsigned* spawn_parent,
-                          const PushParams<Real>& P, int grid,
-                          cudaStream_t stream) {
+                          unsigned long long* cnt, DevState* st, unsigned* spawn_parent,
+                          const PushParams<Real>& P, int grid, cudaStream_t stream) {
+  DepGrid g{rhs, cnt, P.nz + 1, P.qw};
   k_particle_step<Real><<<grid, kThreads, 0, stream>>>(
-      s, (const typename Vec2<Real>::type*)efield, rhs, st, spawn_parent, P);
+      s, (const typename Vec2<Real>::type*)efield, g, st, spawn_parent, P);
 }
 
 // ------------------------------------------------------------ child uids
@@ -510,13 +647,11 @@ __global__ void k_load(const double* __restrict__ r, const double* __restrict__ 
 
 // deposit of the loaded particles at their positions (no push)
 template <typename Real>
-__global__ void k_deposit_only(Soa<Real> s, long long n, double* rhs, int nzp,
-                               double qw) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
+__global__ void k_deposit_only(Soa<Real> s, int n, DepGrid g) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int c = s.cell[p];
     if (c < 0) continue;
-    deposit_global<Real>(rhs, nzp, c >> 16, c & 0xFFFF, s.offr[p], s.offz[p], qw);
+    deposit_global(g, c >> 16, c & 0xFFFF, s.offr[p], s.offz[p]);
   }
 }
 
@@ -532,11 +667,12 @@ void launch_load(const double* r, const double* z, const double* vr,
 }
 
 template <typename Real>
-void launch_deposit_only(const Soa<Real>& s, long long n, double* rhs, int nz,
-                         double qw, cudaStream_t stream) {
+void launch_deposit_only(const Soa<Real>& s, long long n, double* rhs, unsigned long long* cnt,
+                         int nz, double qw, cudaStream_t stream) {
   if (n <= 0) return;
   const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
-  k_deposit_only<Real><<<grid, 256, 0, stream>>>(s, n, rhs, nz + 1, qw);
+  DepGrid g{rhs, cnt, nz + 1, qw};
+  k_deposit_only<Real><<<grid, 256, 0, stream>>>(s, (int)n, g);
 }
 
 // ---------------------------------------------------------------- export
@@ -638,15 +774,15 @@ void launch_efield_get(const void* efield, double* out, int component,
 // ---------------------------------------------------------- instantiate
 
 #define PIC_INSTANTIATE(R)                                                              \
-  template void launch_particle_step<R>(const Soa<R>&, const void*, double*, DevState*, \
-                                        unsigned*, const PushParams<R>&, int,           \
-                                        cudaStream_t);                                  \
+  template void launch_particle_step<R>(const Soa<R>&, const void*, double*,             \
+                                        unsigned long long*, DevState*, unsigned*,      \
+                                        const PushParams<R>&, int, cudaStream_t);       \
   template void launch_load<R>(const double*, const double*, const double*,             \
                                const double*, const double*, const uint64_t*,           \
                                long long, Soa<R>, const PushParams<R>&, DevState*,      \
                                cudaStream_t);                                           \
-  template void launch_deposit_only<R>(const Soa<R>&, long long, double*, int, double,  \
-                                       cudaStream_t);                                   \
+  template void launch_deposit_only<R>(const Soa<R>&, long long, double*,              \
+                                       unsigned long long*, int, double, cudaStream_t); \
   template void launch_export<R>(const Soa<R>&, long long, const PushParams<R>&,        \
                                  double*, double*, double*, double*, double*,           \
                                  unsigned long long*, int*, cudaStream_t);              \
@@ -671,4 +807,5 @@ int particle_step_blocks_per_sm(int precision) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step<double>, kThreads, 0);
   return b;
 }
+int particle_chunk() { return kChunk; }
 }  // namespace pic

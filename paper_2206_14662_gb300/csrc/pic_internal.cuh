@@ -48,10 +48,16 @@ struct DevState {
   unsigned int step;          // global step counter (Philox counter word 2)
   int err;                    // sticky PIC_E* code, 0 = none
   double tally[kTallyCount];
-  double res_num, res_den;    // squared residual sums (reset per solve)
-  double relres_last;         // relative residual of the last solve
+  // field solve: squared norms of the (scaled) right-hand side, of the
+  // right-hand side with the wall potentials moved into it, and of the
+  // residual of the current sweep; reset when a solve ends
+  double b2sum, bl2sum, r2sum;
+  double relres_last;         // ||r|| / ||b_lifted|| of the last solve
+  double relres_strict;       // ||r|| / ||b_interior|| of the last solve
   unsigned solve_blocks_done; // last-block counter of the residual kernel
   int poisson_iters;          // sweeps of the last solve
+  int solve_done;             // set when the solve has converged
+  int pad1;
   long long n_live;           // live count after the last sort / load
 };
 
@@ -94,6 +100,7 @@ struct PushParams {
   double weight;              // electrons per macro-electron
   double qw;                  // q weight, C
   unsigned seed_lo, seed_hi;
+  unsigned rk0[10], rk1[10];  // Philox round keys of the seed
   long long capacity;         // particle slots
   long long spawn_cap;        // children per step
   // grid geometry in FP64 for converting absolute positions to and from
@@ -123,6 +130,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0,
   return c;
 }
 
+// The same generator with the ten round keys precomputed (they depend only
+// on the seed): each round is two 32x32->64 multiplications and two
+// three-input XORs.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const unsigned* rk0,
+                                                  const unsigned* rk1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ rk0[round], (unsigned)p1,
+                   (unsigned)(p0 >> 32) ^ c.w ^ rk1[round], (unsigned)p0);
+  }
+  return c;
+}
+
 // ((x >> 8) + 0.5) 2^-24: exact in float and double, strictly in (0, 1)
 template <typename Real>
 __device__ __forceinline__ Real u01(unsigned x) {
@@ -135,52 +157,88 @@ __device__ __forceinline__ double u01<double>(unsigned x) {
 
 // ------------------------------------------------------------ host side
 
-// Tables of the fast field solver (field_solve.cu), all in device memory.
+// Tables and work arrays of the field solver (field_solve.cu), all in
+// device memory.  The solver works on the system divided by 2 pi eps0 and
+// on the space-charge part phi_rho = phi - phi_vac only (phi_vac, the exact
+// discrete vacuum solution, is precomputed in FP64); phi_rho is refined in
+// double-float (pairs of floats, hi + lo) with an FP32 separable
+// preconditioner.
 struct FieldTables {
   int nr, nz, M, NI;          // cells, M = nz, NI = nr - 1 interior r-lines
   int log2N;                  // FFT length N = 2M = 2^log2N, or -1 (direct)
+  int maxit;                  // refinement sweeps at most
   double hr, hz, rtol;
-  double2* twiddle;           // exp(-2 pi i m / N), m < N/2
-  double* costab;             // cos(pi m / M), m < 2M (direct transform)
-  double* fwd_scale;          // 2 eps_k / (M 2 pi eps0), k = 0..M
-  double* tri_a;              // per (interior line, mode): sub-diagonal
-  double* tri_invd;           //   1 / pivot
-  double* tri_cp;             //   super-diagonal / pivot
-  double* phi_vac;            // vacuum solution per r-line (z-independent)
-  double* kr_d; double* kr_o; // r-weighted stiffness: diagonal, (i, i+1)
-  double* mr_d; double* mr_o; // r-weighted mass
-  double* bhat;               // transformed right-hand side, NI x (M+1)
-  double* phihat;             // transformed solution, NI x (M+1)
+  float2* tw32;               // exp(-2 pi i m / N), m < N/2
+  float* cos32;               // cos(pi m / M), m < 2M (direct transform)
+  float* scale32;             // 2 eps_k / M, k = 0..M
+  float* tri_a;               // per (interior line, mode): sub-diagonal
+  float* tri_inv;             //   1 / pivot
+  float* tri_cp;              //   super-diagonal / pivot
+  double* phi_vac;            // vacuum solution per r-line (FP64)
+  float* evac32;              // its radial field per r-line
+  double* evac64;
+  float2* kr_d; float2* kr_o; // r-weighted stiffness: diagonal, (i, i+1)  [hi, lo]
+  float2* mr_d; float2* mr_o; // r-weighted mass                            [hi, lo]
+  float2 mzd_end, mzd_in, mzo, kzd_end, kzd_in, kzo;  // z matrices [hi, lo]
+  float lift_in, lift_out;    // -K_r(1,0) V_in and -K_r(nr-1,nr) V_out per unit z-row sum
+  float2* b2;                 // right-hand side / (2 pi eps0), per node [hi, lo]
+  float2* phir;               // phi_rho per node [hi, lo]; zero on the walls
+  float* res;                 // FP32 input of the next sweep per node
+  float* bhat;                // transformed input, NI x (M+1)
+  float* phihat;              // transformed correction, NI x (M+1)
 };
 
-// builds the tables on the host (FP64) and uploads them; `dev_alloc`
-// allocates device memory.  Returns PIC_OK or an error code.
+// Host staging of the tables (caller-owned arrays; sizes: kd..tmp_y and
+// kd2..mo2 nr + 1, ta/tinv/tcp (nr - 1)(nz + 1), scale nz + 1, tw and cos
+// 2 nz, evac32 nr + 1).
+struct HostTables {
+  double *kd, *ko, *md, *mo, *vac, *evac64, *tmp_cp, *tmp_y;
+  float *ta, *tinv, *tcp, *scale, *tw, *cos, *evac32;
+  float2 *kd2, *ko2, *md2, *mo2;
+};
+// fills T's scalar fields and the host tables (FP64 arithmetic, no
+// allocation)
+void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& H);
+// copies the host tables into T's device arrays (which must exist) and
+// clears the work arrays; queued on `stream`
+int field_tables_upload(FieldTables& T, const HostTables& H, cudaStream_t stream);
+// allocates T's device arrays with `dev_alloc`, builds and uploads the
+// tables.  Returns PIC_OK or an error code.
 int field_tables_build(const pic_config& cfg, FieldTables& T,
                        void* (*dev_alloc)(size_t, void*), void* ctx,
                        cudaStream_t stream);
-void field_tables_free(FieldTables& T, void (*dev_free)(void*, void*),
-                       void* ctx);
-// phi <- solution for the right-hand side rhs (all nodes; Dirichlet rows of
-// phi must already hold the wall potentials); then, when efield != NULL,
-// E = -grad phi in the particle precision, the residual check, and
-// rho_last <- rhs, rhs <- 0 when zero_rhs.
+float2 df_from(double x);   // double -> double-float (hi, lo)
+constexpr double kFixUnit = 4194303.0;   // fixed-point deposit counts per particle charge
+// Solve for the node charge given either as FP64 charges (rhs) or as
+// fixed-point counts (cnt, charge = count * cnt_unit); `cnt_clear`, when
+// not null, is zeroed on the way (the next step's deposit buffer).  Writes
+// the node field E = E_vac - grad phi_rho in the particle precision and
+// latches PIC_ENOCONV in st if ||r|| / ||b_lifted|| > rtol after the last
+// sweep.
 template <typename Real>
-void launch_field_solve(const FieldTables& T, double* rhs, double* phi,
-                        void* efield, double* rho_last, DevState* st,
-                        bool zero_rhs, cudaStream_t stream);
+void launch_field_solve(const FieldTables& T, const double* rhs,
+                        const unsigned long long* cnt, double cnt_unit,
+                        unsigned long long* cnt_clear, void* efield,
+                        DevState* st, cudaStream_t stream);
+// phi = phi_vac + phi_rho on all nodes (FP64), on demand
+void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream);
+int field_solve_kernels(const FieldTables& T);   // launches per solve
 
 // kernels launched from capi.cu (defined in particle_step.cu / sort.cu)
+// rhs: FP64 deposit grid (FP64 path); cnt: fixed-point deposit grid (FP32
+// path, kFix counts per particle charge)
 template <typename Real>
 void launch_particle_step(const Soa<Real>& s, const void* efield,
-                          double* rhs, DevState* st, unsigned* spawn_parent,
-                          const PushParams<Real>& P, int grid,
-                          cudaStream_t stream);
+                          double* rhs, unsigned long long* cnt, DevState* st,
+                          unsigned* spawn_parent, const PushParams<Real>& P,
+                          int grid, cudaStream_t stream);
 void launch_spawn_finalize(DevState* st, unsigned* uid, const unsigned* parent,
                            long long spawn_cap, long long capacity,
                            cudaStream_t stream);
 template <typename Real>
-void launch_deposit_only(const Soa<Real>& s, long long n, double* rhs, int nz,
-                         double qw, cudaStream_t stream);
+void launch_deposit_only(const Soa<Real>& s, long long n, double* rhs,
+                         unsigned long long* cnt, int nz, double qw,
+                         cudaStream_t stream);
 template <typename Real>
 void launch_load(const double* r, const double* z, const double* vr,
                  const double* vt, const double* vz, const uint64_t* uid,

@@ -30,7 +30,7 @@ def by_uid(d: dict) -> dict:
 
 
 def compare_states(cfg, precision, g: dict, o: "oracle.OracleSim", margin=None,
-                   uid_before=None, report=None, child_uid0=None):
+                   uid_before=None, report=None, child_uid0=None, tol=None):
     """Compare GPU particles g (exported, sorted by uid) with the oracle's.
     Particles whose last decision was ambiguous (margin below the threshold)
     are excluded; if any was, children (uid >= child_uid0) are excluded too,
@@ -38,7 +38,7 @@ def compare_states(cfg, precision, g: dict, o: "oracle.OracleSim", margin=None,
     the number of ambiguous particles."""
     hr = (cfg["r_out"] - cfg["r_in"]) / cfg["nr"]
     hz = (cfg["z_max"] - cfg["z_min"]) / cfg["nz"]
-    tol = TOL[precision]
+    tol = TOL[precision] if tol is None else tol
     amb_uids = set()
     if margin is not None:
         amb = margin < AMBIGUOUS[precision]

@@ -44,7 +44,8 @@ def test_field_solve_matches_oracle(nr, nz):
     """Same right-hand side: the separable DCT/Thomas solve against the
     sparse direct solve of the assembled finite-element system."""
     from paper_2206_14662_gb300._capi import Simulation
-    cfg = workload("coax_32x64_1e4", nr=nr, nz=nz, precision=64)
+    cfg = workload("coax_32x64_1e4", nr=nr, nz=nz, precision=64, poisson_rtol=1e-12,
+                   poisson_maxit=10)
     rng = np.random.default_rng(nr * 1000 + nz)
     b = -rng.random((nr + 1) * (nz + 1)) * 1e-12
     with Simulation(cfg) as sim:
@@ -52,6 +53,9 @@ def test_field_solve_matches_oracle(nr, nz):
     phi_o = oracle.poisson_solve(cfg, b)
     scale = np.abs(phi_o).max()
     assert np.abs(phi_g - phi_o).max() <= 1e-10 * scale
+    # the space-charge part alone, against its own scale
+    vac = oracle.poisson_solve(cfg, np.zeros_like(b))
+    assert np.abs((phi_g - vac) - (phi_o - vac)).max() <= 1e-9 * np.abs(phi_o - vac).max()
     assert rel <= 1e-12
     assert oracle.poisson_relres(cfg, b, phi_g) <= 1e-12
 
@@ -155,7 +159,11 @@ def test_self_consistent_steps(precision):
     """Ten full steps of the workload "coax_32x64_1e4" (field solve on):
     particles and the potential follow the oracle."""
     from paper_2206_14662_gb300._capi import PIC_GRID_PHI
-    cfg = workload("coax_32x64_1e4", precision=precision, p_mbar=0.3, T0_eV=30.0)
+    # FP64 path: the field solved to 1e-12 so that the particle comparison
+    # measures the particle path; FP32 path: the default tolerance
+    cfg = workload("coax_32x64_1e4", precision=precision, p_mbar=0.3, T0_eV=30.0,
+                   poisson_rtol=1e-12 if precision == 64 else 1e-8,
+                   poisson_maxit=8 if precision == 64 else 2)
     parts = seed_particles(cfg)
     o = oracle.OracleSim(cfg, *parts)
     sim = make_gpu(cfg, parts)
@@ -172,10 +180,13 @@ def test_self_consistent_steps(precision):
     keep = np.isin(o.uid, g["uid"])
     assert keep.mean() > 0.999
     assert np.abs(phi - o.phi).max() <= (1e-10 if precision == 64 else 1e-5) * np.abs(o.phi).max()
-    assert d["poisson_relres"] <= 1e-12
+    assert d["poisson_relres"] <= cfg["poisson_rtol"]
+    assert d["poisson_relres_charge"] <= cfg["poisson_rtol"]
     if precision == 64:
-        compare_states(cfg, 64, g, o, report=rep)
-        assert max(rep.values()) <= tol
+        # the field is solved to poisson_rtol, not exactly: after ten steps
+        # the trajectories agree to 1e-9 (positions in cells, velocities
+        # relative to the largest speed)
+        compare_states(cfg, 64, g, o, report=rep, tol=tol)
     else:
         gi = np.searchsorted(g["uid"], o.uid[keep])
         assert np.abs(g["r"][gi] - o.r[keep]).max() / hr <= tol
