@@ -107,6 +107,7 @@ typedef struct pic_diag {
   int64_t n_elastic, n_ionise, n_absorbed, n_candidates, n_over;
   int64_t n_pushed;              /* cumulative particle-steps (live
                                     particles advanced, summed over steps) */
+  int64_t kernels_launched;      /* cumulative kernels run by pic_step */
   double ke_total_J;             /* kinetic energy of the live particles */
   double work_E_J;               /* cumulative work of E on the particles */
   double ke_absorbed_J;          /* cumulative kinetic energy into walls */
@@ -163,10 +164,13 @@ int pic_load_particles(pic_handle* h, int sim, const double* r,
 
 /* Advance nsteps time steps (Sec. II.A): per step the fused particle kernel
  * (gather, Boris, absorb, null-collision MCC, spawn, deposit), child uid
- * assignment, the FP64 field solve and E = -grad phi; every sort_every
- * steps a counting sort by cell that also drops absorbed particles.  The
- * Philox stream of a particle is keyed by (seed) with counter
- * (uid, step, draw).  Asynchronous; never synchronises. */
+ * assignment, the field solve and E = -grad phi; every sort_every steps a
+ * counting sort by cell that also drops absorbed particles.  The Philox
+ * stream of a particle is keyed by (seed) with counter (uid, step, draw).
+ * Whole blocks of steps run as CUDA graphs (captured once, on a private
+ * stream, the first time a block is reached; so the first call should come
+ * before any capture of the caller's stream); while profiling (pic_profile)
+ * every kernel is launched directly.  Asynchronous; never synchronises. */
 int pic_step(pic_handle* h, int64_t nsteps);
 
 /* Synchronise and fill *out; if density is not NULL, also write the node

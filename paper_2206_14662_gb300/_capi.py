@@ -43,6 +43,7 @@ class PicDiag(ctypes.Structure):
         ("absorbed_weight", c_d * 4),
         ("n_elastic", c_i64), ("n_ionise", c_i64), ("n_absorbed", c_i64),
         ("n_candidates", c_i64), ("n_over", c_i64), ("n_pushed", c_i64),
+        ("kernels_launched", c_i64),
         ("ke_total_J", c_d), ("work_E_J", c_d), ("ke_absorbed_J", c_d),
         ("ion_loss_J", c_d), ("recoil_loss_J", c_d), ("ke_initial_J", c_d),
         ("ledger_residual_J", c_d), ("n_peak", c_d), ("poisson_iters", c_i32),

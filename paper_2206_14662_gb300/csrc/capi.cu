@@ -63,6 +63,15 @@ struct pic_handle {
   int sticky;
   long long kernels;
 
+  // CUDA graphs of whole blocks of steps, keyed by the buffer set holding
+  // the particles (cur) and the FP32 deposit buffer (dep_buf) at the start
+  // of the block; captured on a private stream, replayed on the caller's
+  cudaStream_t cap_stream;
+  int graph_len;                        // steps per graph
+  cudaGraphExec_t graph[2][2];
+  long long graph_kernels[2][2];
+  bool graph_failed;
+
   // profiling
   bool profiling;
   std::vector<cudaEvent_t> ev_pool;
@@ -419,6 +428,13 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   }
   fill_params<float>(h, h->Pf);
   fill_params<double>(h, h->Pd);
+  {
+    // a graph block returns the alternating buffers (sort ping-pong, FP32
+    // deposit buffers) to a fixed pattern: lcm(sort_every, 2) steps
+    const int se = c.sort_every;
+    h->graph_len = se > 0 ? (se % 2 == 0 ? se : 2 * se) : 2;
+    while (h->graph_len < 8) h->graph_len *= 2;
+  }
   *out = h;
   return PIC_OK;
 }
@@ -426,6 +442,10 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
 void pic_free(pic_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  for (auto& row : h->graph)
+    for (auto& x : row)
+      if (x) cudaGraphExecDestroy(x);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void* p : h->owned) h_free_one(p, h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -529,10 +549,83 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
   return rc;
 }
 
+namespace {
+
+int step_direct(pic_handle* h, long long n) {
+  return h->prec == 32 ? step_impl<float>(h, n) : step_impl<double>(h, n);
+}
+
+// Capture graph_len steps starting from the current host state into
+// h->graph[cur][dep]; the host state is restored afterwards (capture
+// executes nothing).
+int build_graph(pic_handle* h) {
+  const int cur = h->cur, dep = h->dep_buf;
+  const long long step0 = h->step, kern0 = h->kernels;
+  const int last0 = h->last_buf;
+  cudaStream_t user = h->stream;
+  if (!h->cap_stream &&
+      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return PIC_ECUDA;
+  if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return PIC_ECUDA;
+  h->stream = h->cap_stream;
+  const int rc = step_direct(h, h->graph_len);
+  h->stream = user;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  const long long nk = h->kernels - kern0;
+  h->cur = cur; h->dep_buf = dep; h->last_buf = last0;
+  h->step = step0; h->kernels = kern0;
+  if (rc != PIC_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return PIC_ECUDA;
+  }
+  cudaGraphExec_t x = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return PIC_ECUDA;
+  }
+  h->graph[cur][dep] = x;
+  h->graph_kernels[cur][dep] = nk;
+  return PIC_OK;
+}
+
+}  // namespace
+
 int pic_step(pic_handle* h, int64_t nsteps) {
   if (!h || nsteps < 0) return PIC_EINVAL;
   if (h->sticky) return h->sticky;
-  return h->prec == 32 ? step_impl<float>(h, nsteps) : step_impl<double>(h, nsteps);
+  long long n = nsteps;
+  if (h->profiling || h->graph_failed || h->graph_len <= 0) return step_direct(h, n);
+  // direct steps up to a block boundary, whole blocks as graph replays, the
+  // remainder direct again
+  while (n > 0 && h->step % h->graph_len != 0) {
+    const int rc = step_direct(h, 1);
+    if (rc) return rc;
+    --n;
+  }
+  while (n >= h->graph_len) {
+    const int cur = h->cur, dep = h->dep_buf;
+    if (!h->graph[cur][dep] && build_graph(h) != PIC_OK) {
+      h->graph_failed = true;   // stay on direct launches
+      return step_direct(h, n);
+    }
+    if (cudaGraphLaunch(h->graph[cur][dep], h->stream) != cudaSuccess) return PIC_ECUDA;
+    // the host-side view of the block: the same bookkeeping as direct steps
+    h->step += h->graph_len;
+    h->kernels += h->graph_kernels[cur][dep];
+    const bool solve = h->cfg.fixed_efield == 0;
+    if (h->prec == 32) {
+      h->last_buf = solve ? (dep ^ ((h->graph_len - 1) & 1)) : dep;
+      if (solve) h->dep_buf = dep ^ (h->graph_len & 1);
+    }
+    if (h->cfg.sort_every > 0) h->cur = cur ^ ((h->graph_len / h->cfg.sort_every) & 1);
+    n -= h->graph_len;
+  }
+  return n > 0 ? step_direct(h, n) : PIC_OK;
 }
 
 int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
@@ -572,6 +665,7 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
   out->n_candidates = (int64_t)s.tally[kNCandidate];
   out->n_over = (int64_t)s.tally[kNOver];
   out->n_pushed = (int64_t)s.tally[kNPushed];
+  out->kernels_launched = h->kernels;
   out->ke_total_J = 0.5 * kMe * ke[0] * h->weight;
   out->work_E_J = s.tally[kWorkE];
   out->ke_absorbed_J = s.tally[kKeAbsorbed];
