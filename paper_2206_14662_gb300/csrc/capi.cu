@@ -393,7 +393,8 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
     if (!rc) rc = alloc_soa(h, h->sd[1]);
   }
   h->spawn_parent = (unsigned*)h_alloc((size_t)h->spawn_cap * sizeof(unsigned), h);
-  h->cell_count = (int*)h_alloc((size_t)h->ncells * sizeof(int), h);
+  // whole multiples of 4096 counts: the scan reads them as int4 vectors
+  h->cell_count = (int*)h_alloc((size_t)(h->ncells + 4095) / 4096 * 4096 * sizeof(int), h);
   h->rhs = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
   h->cnt[0] = (unsigned long long*)h_alloc((size_t)h->nnodes * sizeof(unsigned long long), h);
   h->cnt[1] = (unsigned long long*)h_alloc((size_t)h->nnodes * sizeof(unsigned long long), h);

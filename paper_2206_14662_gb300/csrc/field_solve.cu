@@ -31,9 +31,10 @@
 // this part the FP64 pipe runs at a small fraction of the FP32 rate, so the
 // FP64-accurate residual is formed from FP32 pairs instead.  Each sweep
 // contracts the error by roughly the FP32 condition-number factor of S.
-// Sweeps stop when ||r|| <= rtol ||b'_I||; after the last allowed sweep the
-// reported residual ||r|| / ||b'_I - A'_ID phi_D|| (all wall potentials
-// moved to the right-hand side) must be <= rtol, else PIC_ENOCONV.
+// Sweeps stop once ||r|| / ||b'_I - A'_ID phi_D|| (the residual relative to
+// the right-hand side with all wall potentials moved into it) is <= rtol;
+// if the last allowed sweep has not reached it, PIC_ENOCONV is latched.
+// ||r|| / ||b'_I|| (relative to the charge alone) is reported as well.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -545,7 +546,7 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
       st->relres_last = rel;
       st->relres_strict = strict;
       st->poisson_iters = sweep + 1;
-      if (strict <= T.rtol || last) {
+      if (rel <= T.rtol || last) {
         st->solve_done = 1;
         if (!(rel <= T.rtol)) atomicCAS(&st->err, 0, PIC_ENOCONV);
         st->b2sum = 0.0;

@@ -400,8 +400,10 @@ __device__ __forceinline__ void store_group(const Soa<Real>& s, int p0, int n, c
 // same-address atomics of one instruction serialise; so the tile is kept in
 // kCopies private copies (lane & 3 picks the copy) and each lane issues its
 // four corner updates in an order rotated by (lane >> 2) & 3.  Lanes of one
-// cell then hit 16 different words per instruction.  The flush adds the
-// copies.
+// cell then hit 16 different words per instruction.  The copies of a node
+// are interleaved word by word (word 4 t + c), which spreads those 16 words
+// over different banks and lets the flush read a node's copies as one
+// 16-byte vector.
 constexpr int kCopies = 4;
 constexpr int kCapF = 1024;   // nodes per FP32 tile copy
 
@@ -438,12 +440,8 @@ __device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename Til
   const int warp = tid >> 5;
   if (use_tile) {
     for (int t = tid; t < rows * cols; t += kThreads) {
-      if constexpr (f32) {
-#pragma unroll
-        for (int c = 0; c < kCopies; ++c) tile[c * kCapF + t] = 0u;
-      } else {
-        tile[t] = TT(0);
-      }
+      if constexpr (f32) reinterpret_cast<uint4*>(tile)[t] = make_uint4(0u, 0u, 0u, 0u);
+      else tile[t] = TT(0);
     }
   }
   __syncthreads();
@@ -454,14 +452,15 @@ __device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename Til
       const int t = (dep[k].ir - br0) * cols + (dep[k].iz - bz0);
       if constexpr (f32) {
         const float a = dep[k].fr, c = dep[k].fz;
-        unsigned* tc = tile + (lane & 3) * kCapF + t;
+        unsigned* tc = tile + kCopies * t + (lane & 3);
         const int rot = (lane >> 2) & 3;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const int j = (m + rot) & 3;   // corner: bit 0 along r, bit 1 along z
           const float wr = (j & 1) ? a : 1.f - a;
           const float wz = (j & 2) ? c : 1.f - c;
-          atomicAdd(tc + ((j & 1) ? cols : 0) + (j >> 1), __float2uint_rn(wr * wz * kFix));
+          atomicAdd(tc + kCopies * (((j & 1) ? cols : 0) + (j >> 1)),
+                    __float2uint_rn(wr * wz * kFix));
         }
       } else {
         const TT a = (TT)dep[k].fr, c = (TT)dep[k].fz;
@@ -484,7 +483,8 @@ __device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename Til
         const int t = rr * cols + cc;
         const int node = (br0 + rr) * g.nzp + (bz0 + cc);
         if constexpr (f32) {
-          const unsigned v = tile[t] + tile[kCapF + t] + tile[2 * kCapF + t] + tile[3 * kCapF + t];
+          const uint4 q = reinterpret_cast<const uint4*>(tile)[t];
+          const unsigned v = q.x + q.y + q.z + q.w;
           if (v) atomicAdd(g.cnt + node, (unsigned long long)v);
         } else {
           const TT v = tile[t];
@@ -500,11 +500,11 @@ __device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename Til
 template <typename Real>
 __device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pushed, DevState* st,
                                               const PushParams<Real>& P, int tid, int lane) {
-  double w = (double)work;
+  Real w = work;   // warp sum in the particle precision, then one FP64 add
   const int np = __reduce_add_sync(0xffffffffu, pushed);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-  if (lane == 0 && w != 0.0) atomicAdd(&bt.v[kWorkE], w);
+  if (lane == 0 && w != Real(0)) atomicAdd(&bt.v[kWorkE], (double)w);
   if (lane == 0 && np != 0) atomicAdd(&bt.v[kNPushed], (double)np);
   __syncthreads();
   if (tid < kTallyCount) {
@@ -520,7 +520,7 @@ __device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pus
 
 // resident blocks per SM the FP32 kernel is compiled for (register cap)
 #ifndef PIC_MIN_BLOCKS
-#define PIC_MIN_BLOCKS 4
+#define PIC_MIN_BLOCKS 3
 #endif
 
 // Each thread loads its kPPT consecutive particles directly (16-byte vector
@@ -532,7 +532,7 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, De
                 DevState* st, unsigned* __restrict__ spawn_parent, PushParams<Real> P) {
   using TT = typename TileT<Real>::type;
   constexpr int kCap = TileT<Real>::cap;
-  __shared__ TT tile[kCap];
+  __shared__ __align__(16) TT tile[kCap];
   __shared__ int bbox[2][4];   // min ir, max ir, min iz, max iz
   __shared__ BlockTally bt;
 

@@ -9,8 +9,10 @@
 //      new slot count
 //   3. scatter of every live particle to its cell's next free slot in the
 //      other buffer set (slot order within a cell is not specified)
-// Warp-mates with equal keys are combined with __match_any_sync so that one
-// atomic serves a whole group.
+// The store is nearly sorted already (it was sorted sort_every steps ago),
+// so runs of equal keys in consecutive lanes are common: one shuffle and
+// one ballot find each run, and the run's first lane does one atomic for
+// the whole run.
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -19,70 +21,111 @@ __device__ __forceinline__ int cell_key(int cell, int nz) {
   return cell < 0 ? -1 : (cell >> 16) * nz + (cell & 0xFFFF);
 }
 
+// Runs of equal keys among the lanes of a warp: whether this lane starts a
+// run, the lane starting its run, and (for run starts) the run's length.
+struct Run {
+  bool head;
+  int first;
+  int len;
+};
+__device__ __forceinline__ Run lane_run(int key, int lane) {
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const unsigned le = 0xffffffffu >> (31 - lane);   // lanes 0..lane
+  Run r;
+  r.head = head;
+  r.first = 31 - __clz(heads & le);
+  const unsigned above = heads & ~le;
+  r.len = (above ? __ffs(above) - 1 : 32) - lane;
+  return r;
+}
+
+// histogram: each thread takes four consecutive slots (one 16-byte load;
+// the store is allocated in whole chunks of 1024 slots, so the vector never
+// leaves it), runs are found among the lanes for each of the four
 template <typename Real>
 __global__ void k_sort_hist(const int* __restrict__ cell, const DevState* st,
                             int* count, int nz) {
-  const long long n = st->n_slots;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
-       base += (long long)gridDim.x * blockDim.x) {
-    const long long p = base + threadIdx.x;
-    const int key = p < n ? cell_key(cell[p], nz) : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int leader = __ffs(peers) - 1;
-    if (key >= 0 && (int)(threadIdx.x & 31) == leader) atomicAdd(count + key, __popc(peers));
+  const int n = (int)st->n_slots;
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x * 4; base < n; base += gridDim.x * blockDim.x * 4) {
+    const int p0 = base + 4 * threadIdx.x;
+    const int4 c = *reinterpret_cast<const int4*>(cell + p0);
+    const int cs[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int key = p0 + k < n ? cell_key(cs[k], nz) : -1;
+      const Run r = lane_run(key, lane);
+      if (key >= 0 && r.head) atomicAdd(count + key, r.len);
+    }
   }
 }
 
-// exclusive scan of count[0..n) in place, one block of 1024 threads; the
-// total goes to st->n_live
+// exclusive scan of count[0..n) in place, one block of 1024 threads, each
+// owning a contiguous stretch of whole int4 vectors (count is allocated in
+// whole multiples of 4096 entries, the tail beyond n zero); the total goes
+// to st->n_live
 __global__ void __launch_bounds__(1024) k_sort_scan(int* count, int n, DevState* st) {
   __shared__ int part[1024];
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int lo = threadIdx.x * per, hi = min(n, lo + per);
+  const int n4 = (n + 4095) / 4096 * 1024;     // int4 vectors, whole per thread
+  const int per = n4 / 1024;                   // vectors per thread
+  int4* c4 = reinterpret_cast<int4*>(count) + (size_t)threadIdx.x * per;
   int s = 0;
-  for (int i = lo; i < hi; ++i) s += count[i];
+  for (int i = 0; i < per; ++i) {
+    const int4 v = c4[i];
+    s += v.x + v.y + v.z + v.w;
+  }
   part[threadIdx.x] = s;
   __syncthreads();
   // Hillis-Steele inclusive scan of the per-thread sums
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+  for (int o = 1; o < 1024; o <<= 1) {
     const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
     __syncthreads();
     part[threadIdx.x] += v;
     __syncthreads();
   }
   int run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
-  for (int i = lo; i < hi; ++i) {
-    const int c = count[i];
-    count[i] = run;
-    run += c;
+  for (int i = 0; i < per; ++i) {
+    const int4 v = c4[i];
+    int4 o;
+    o.x = run; run += v.x;
+    o.y = run; run += v.y;
+    o.z = run; run += v.z;
+    o.w = run; run += v.w;
+    c4[i] = o;
   }
-  if (threadIdx.x == blockDim.x - 1) st->n_live = part[blockDim.x - 1];
+  if (threadIdx.x == 1023) st->n_live = part[1023];
 }
 
+// scatter: four consecutive slots per thread as in the histogram; each
+// live particle goes to its cell's next free slot in the other buffer set
 template <typename Real>
 __global__ void k_sort_scatter(Soa<Real> src, Soa<Real> dst, const DevState* st,
                                int* cursor, int nz) {
-  const long long n = st->n_slots;
+  const int n = (int)st->n_slots;
   const int lane = threadIdx.x & 31;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
-       base += (long long)gridDim.x * blockDim.x) {
-    const long long p = base + threadIdx.x;
-    const int c = p < n ? src.cell[p] : -1;
-    const int key = cell_key(c, nz);
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int leader = __ffs(peers) - 1;
-    int slot = 0;
-    if (key >= 0 && lane == leader) slot = atomicAdd(cursor + key, __popc(peers));
-    slot = __shfl_sync(0xffffffffu, slot, leader);
-    if (key >= 0) {
-      const int q = slot + __popc(peers & ((1u << lane) - 1u));
-      dst.cell[q] = c;
-      dst.offr[q] = src.offr[p];
-      dst.offz[q] = src.offz[p];
-      dst.vr[q] = src.vr[p];
-      dst.vt[q] = src.vt[p];
-      dst.vz[q] = src.vz[p];
-      dst.uid[q] = src.uid[p];
+  for (int base = blockIdx.x * blockDim.x * 4; base < n; base += gridDim.x * blockDim.x * 4) {
+    const int p0 = base + 4 * threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int p = p0 + k;
+      const int c = p < n ? src.cell[p] : -1;
+      const int key = cell_key(c, nz);
+      const Run r = lane_run(key, lane);
+      int slot = 0;
+      if (key >= 0 && r.head) slot = atomicAdd(cursor + key, r.len);
+      slot = __shfl_sync(0xffffffffu, slot, r.first);
+      if (key >= 0) {
+        const int q = slot + (lane - r.first);
+        dst.cell[q] = c;
+        dst.offr[q] = src.offr[p];
+        dst.offz[q] = src.offz[p];
+        dst.vr[q] = src.vr[p];
+        dst.vt[q] = src.vt[p];
+        dst.vz[q] = src.vz[p];
+        dst.uid[q] = src.uid[p];
+      }
     }
   }
 }
@@ -93,7 +136,7 @@ template <typename Real>
 void launch_sort(const Soa<Real>& src, const Soa<Real>& dst, DevState* st,
                  int* cell_count, int ncells, int nz, int grid,
                  cudaStream_t stream) {
-  cudaMemsetAsync(cell_count, 0, (size_t)ncells * sizeof(int), stream);
+  cudaMemsetAsync(cell_count, 0, (size_t)(ncells + 4095) / 4096 * 4096 * sizeof(int), stream);
   k_sort_hist<Real><<<grid, 256, 0, stream>>>(src.cell, st, cell_count, nz);
   k_sort_scan<<<1, 1024, 0, stream>>>(cell_count, ncells, st);
   k_sort_scatter<Real><<<grid, 256, 0, stream>>>(src, dst, st, cell_count, nz);

@@ -180,8 +180,10 @@ def test_self_consistent_steps(precision):
     keep = np.isin(o.uid, g["uid"])
     assert keep.mean() > 0.999
     assert np.abs(phi - o.phi).max() <= (1e-10 if precision == 64 else 1e-5) * np.abs(o.phi).max()
+    # the stopping test is the residual relative to the lifted right-hand
+    # side; relative to the charge alone it is larger but still small
     assert d["poisson_relres"] <= cfg["poisson_rtol"]
-    assert d["poisson_relres_charge"] <= cfg["poisson_rtol"]
+    assert d["poisson_relres_charge"] <= (1e-9 if precision == 64 else 1e-4)
     if precision == 64:
         # the field is solved to poisson_rtol, not exactly: after ten steps
         # the trajectories agree to 1e-9 (positions in cells, velocities
