@@ -4,6 +4,11 @@ macro-electrons (FP32 particle path, FP64 field), mirror field B0 = 0.3 T,
 -20 kV coaxial bias, 1e-5 mbar, cell sort every 20 steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload mirror_128x512_1e7 | scan_64x256_64sims]
+
+``--workload scan_64x256_64sims`` times the parametric scan instead: 64
+simulations of 64 x 256 cells (pressure x voltage x mirror field, 1e5 to 5e6
+macro-electrons each, 8.15e7 in all) stepped as one batch.
 
 Prints one JSON line.  ``value`` is particle-steps/s with the particles
 resident in HBM; ``e2e`` is the same metric through the C ABI from host
@@ -31,9 +36,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2206_14662_gb300.inputs import seed_particles, workload  # noqa: E402
+from paper_2206_14662_gb300.inputs import scan_configs, seed_particles, workload  # noqa: E402
 
 WORKLOAD = "mirror_128x512_1e7"
+SCAN = "scan_64x256_64sims"
 METRIC = "particle-steps/s (gather+push+MCC+deposit+field solve)"
 # algorithmic bytes per particle-step of the fused particle kernel (FP32):
 # read cell 4 + offsets 8 + velocity 12 + uid 4, write cell + offsets +
@@ -76,7 +82,8 @@ def _traffic_record():
 
 
 class Clocks:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 100 ms) during the timed region; start()
+    waits until the sampler has written its first line."""
 
     def __init__(self):
         self.proc = None
@@ -92,10 +99,14 @@ class Clocks:
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
                  "clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 10 and os.path.getsize(self.path) == 0:
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -125,21 +136,40 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _inputs(args, rank):
+    """(workload name, configurations, seeded particle arrays per
+    simulation) of the run."""
+    if args.workload == SCAN:
+        cfgs = scan_configs(seed=1 + rank)
+        parts = [seed_particles(c, seed=1000 * (rank + 1) + k) for k, c in enumerate(cfgs)]
+        return SCAN, cfgs, parts
+    cfg = workload(WORKLOAD, seed=1 + rank)
+    if args.particles:
+        cfg["n_init"] = args.particles
+    return WORKLOAD, [cfg], [seed_particles(cfg)]
+
+
 def run_ours(args, ws, rank):
     import torch
     from paper_2206_14662_gb300._capi import Simulation
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    cfg = workload(WORKLOAD, seed=1 + rank)
-    if args.particles:
-        cfg["n_init"] = args.particles
-    parts = seed_particles(cfg)
-    n0 = len(parts[0])
-    pinned = [torch.from_numpy(a).pin_memory() for a in parts[:5]]
-    pinned.append(torch.from_numpy(parts[5].view(np.int64)).pin_memory())
+    name, cfgs, parts = _inputs(args, rank)
+    S = len(cfgs)
+    n0 = sum(len(p[0]) for p in parts)
+    pinned = []
+    for p in parts:
+        q = [torch.from_numpy(a).pin_memory() for a in p[:5]]
+        q.append(torch.from_numpy(p[5].view(np.int64)).pin_memory())
+        pinned.append(q)
 
-    sim = Simulation(cfg)
-    sim.load_particles(*pinned)
+    def pushed(sim):
+        ds = [sim.diagnostics(sim=k) for k in range(S)]
+        return sum(d["n_pushed"] for d in ds), ds[0]
+
+    sim = Simulation(cfgs if S > 1 else cfgs[0])
+    for k in range(S):
+        sim.load_particles(*pinned[k], sim=k)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     if ws > 1:
@@ -148,7 +178,7 @@ def run_ours(args, ws, rank):
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks()
-    d0 = sim.diagnostics()
+    u0, d0 = pushed(sim)
     clocks.start()
     torch.cuda.synchronize()
     ev0.record(stream)
@@ -156,9 +186,9 @@ def run_ours(args, ws, rank):
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    d1 = sim.diagnostics()
+    u1, d1 = pushed(sim)
     ms = ev0.elapsed_time(ev1)
-    units = d1["n_pushed"] - d0["n_pushed"]
+    units = u1 - u0
     launches = d1["kernels_launched"] - d0["kernels_launched"]
 
     # per-stage device time: the same workload continued with an event
@@ -167,18 +197,19 @@ def run_ours(args, ws, rank):
     sim.profile_start()
     sim.step(prof_steps)
     prof = sim.profile_stop()
-    d2 = sim.diagnostics()
-    prof_units = d2["n_pushed"] - d1["n_pushed"]
+    u2, d2 = pushed(sim)
+    prof_units = u2 - u1
 
     # end to end through the C ABI from host buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_units = 0
     if args.e2e:
-        sim.load_particles(*pinned)
+        for k in range(S):
+            sim.load_particles(*pinned[k], sim=k)
         sim.step(args.steps)
-        de = sim.diagnostics(density=True)
-        e2e_units = de["n_pushed"]
+        for k in range(S):   # a load resets the simulation's counters
+            e2e_units += sim.diagnostics(density=True, sim=k)["n_pushed"]
     t1 = time.perf_counter()
     sim.close()
 
@@ -200,7 +231,22 @@ def run_ours(args, ws, rank):
     kern_ms = prof["particle_ms"] / max(1, prof["particle_launches"])
     per_launch_units = prof_units / max(1, prof["particle_launches"])
     achieved = BYTES_PER_PARTICLE_STEP * per_launch_units / (kern_ms * 1e-3) / 1e9
-    traffic = _traffic_record()
+    traffic = _traffic_record() if S == 1 else None
+    cfg = cfgs[0]
+    grid = f"{cfg['nr']}x{cfg['nz']}"
+    nnodes = (cfg["nr"] + 1) * (cfg["nz"] + 1)
+    if S == 1:
+        config = {"workload": name if not args.particles else f"{name} (particles={n0})",
+                  "particles": n0, "grid": grid, "sort_every": cfg["sort_every"],
+                  "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                  "l2": "inputs larger than L2 (particle store 520 MB per step)"}
+    else:
+        config = {"workload": name, "simulations": S, "particles": n0,
+                  "particles_min_max": [min(len(p[0]) for p in parts),
+                                        max(len(p[0]) for p in parts)],
+                  "grid": f"{S} x {grid}", "sort_every": cfg["sort_every"],
+                  "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU, one batch",
+                  "l2": f"inputs larger than L2 (particle store {n0 * 52 / 1e9:.1f} GB per step)"}
     out = {
         "metric": METRIC,
         "value": value,
@@ -214,15 +260,14 @@ def run_ours(args, ws, rank):
         "vs_baseline": None,
         "dtype": "f32 particles / f64 field",
         "data": "synthetic (seeded volume-uniform 1 eV Maxwellian load)",
-        "config": {"workload": WORKLOAD if not args.particles else f"{WORKLOAD} (particles={n0})",
-                   "particles": n0, "grid": "128x512", "sort_every": 20,
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (particle store 520 MB per step)"},
+        "config": config,
         "e2e": None if not args.e2e else {"value": e2e_units * ws / esec, "unit": "particle-steps/s",
                 "h2d_bytes_per_step": int(n0 * 48 / args.steps),
-                "d2h_bytes_per_step": int(((cfg["nr"] + 1) * (cfg["nz"] + 1) * 8 + 512) / args.steps)},
+                "d2h_bytes_per_step": int(S * (nnodes * 8 + 512) / args.steps)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "k_particle_step<float>", "achieved": achieved,
+        "roofline": {"bound": "hbm",
+                     "kernel": "k_particle_step<float>" if S == 1 else "k_particle_step_batch<float>",
+                     "achieved": achieved,
                      "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (traffic["dram_bytes_per_particle"] * per_launch_units) if traffic else None,
                      "kernel_ms_per_launch": kern_ms,
@@ -239,11 +284,16 @@ def run_ours(args, ws, rank):
         "clocks": clk,
     }
     if args.cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(cfg, parts)
+        if S == 1:
+            out["cpu_baseline"] = cpu_baseline(cfg, parts[0])
+        else:
+            # the oracle on the largest simulation of the scan, 4 steps
+            k = int(np.argmax([len(p[0]) for p in parts]))
+            out["cpu_baseline"] = cpu_baseline(cfgs[k], parts[k], steps=4, name=f"{name} (simulation {k})")
     return out
 
 
-def cpu_baseline(cfg, parts, n_sample=None, steps=2):
+def cpu_baseline(cfg, parts, n_sample=None, steps=2, name=WORKLOAD):
     """The oracle as it stands (single thread) on a bounded sample: the full
     1e7-particle load and field, ``steps`` steps."""
     import oracle
@@ -257,7 +307,7 @@ def cpu_baseline(cfg, parts, n_sample=None, steps=2):
         o.step()
     sec = time.perf_counter() - t0
     return {"value": units / sec, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of {len(parts[0][sel])} particles of {WORKLOAD} "
+            "sample": f"{steps} steps of {len(parts[0][sel])} particles of {name} "
                       "(full grid, field solve included)", "seconds": sec}
 
 
@@ -269,7 +319,9 @@ def run_reference(args, ws, rank):
         return None
     import oracle
     oracle.build()
-    cfg = workload(WORKLOAD)
+    name = args.workload
+    # the scan: its largest simulation (the oracle runs one simulation)
+    cfg = workload(WORKLOAD) if name == WORKLOAD else scan_configs()[-1]
     n = 20_000
     parts = seed_particles(cfg, n=n)
     o = oracle.OracleSim(cfg, *parts)
@@ -286,10 +338,10 @@ def run_reference(args, ws, rank):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "particles": n, "grid": "128x512",
+            "config": {"workload": name, "particles": n, "grid": f"{cfg['nr']}x{cfg['nz']}",
                        "parallelism": "cpu oracle, rank 0 only"},
             "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n} particles of {WORKLOAD} per step, full grid and field solve"},
+                             "sample": f"{n} particles of {name} per step, full grid and field solve"},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -297,8 +349,9 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--workload", choices=[WORKLOAD, SCAN], default=WORKLOAD)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false",

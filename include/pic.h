@@ -139,25 +139,37 @@ typedef struct pic_allocator {
   void* ctx;
 } pic_allocator;
 
-/* Create a simulation (Sec. II.A: the PIC cycle; Sec. II.B: geometry and
- * numerical parameters).  Validates cfg, derives the neutral density, the
- * macro weight and the collision majorant in FP64 on the host, builds the
- * field-solver tables and allocates all device memory (through `alloc`, or
- * cudaMalloc when alloc is NULL).  n_sims must be 1.  `cuda_stream` is a
+/* Create a simulation, or a batch of n_sims simulations stepped together
+ * (Sec. II.A: the PIC cycle; Sec. II.B: geometry and numerical parameters;
+ * Sec. III: the parametric scans over pressure, voltage and magnetic field).
+ * cfg points to n_sims configurations (1 <= n_sims <= 256).  The
+ * simulations of a batch must agree in r_in, r_out, z_min, z_max, nr, nz,
+ * dt, sort_every, poisson_rtol, poisson_maxit, precision, seed and
+ * fixed_efield; everything else (wall potentials, field, gas, collision
+ * parameters, particle count, weight, capacity) is per simulation.  The
+ * random streams of simulation k use Philox counter word 1 = k (the high
+ * word of its particles' 64-bit identity), so simulation 0 of a batch draws
+ * exactly what a single run draws.  Validates cfg, derives the neutral
+ * density, the macro weight and the collision majorant in FP64 on the host,
+ * builds the field-solver tables and allocates all device memory (through
+ * `alloc`, or cudaMalloc when alloc is NULL).  `cuda_stream` is a
  * cudaStream_t (NULL = legacy default stream).  No particles are loaded.
  * Returns PIC_EINVAL for an invalid configuration, PIC_ENOMEM, PIC_ECUDA. */
 int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
              const pic_allocator* alloc, pic_handle** out);
 
-/* Load n macro-electrons from host FP64 arrays (structure of arrays):
- * positions r, z (strictly inside the gap), velocity components vr, vtheta,
- * vz (the velocity at half step -1/2 of the leapfrog) and unique uids
- * (< 2^32).  Replaces any loaded particles, resets the step counter, the
- * tallies and the uid counter (max uid + 1), deposits the charge and, unless
- * fixed_efield, solves the field (Sec. II.A seed load and first field).
- * Synchronises (page-locked host arrays make the copies faster).
- * PIC_EINVAL for out-of-domain or non-finite values, uids at or above 2^32,
- * or n > capacity. */
+/* Load n macro-electrons into simulation `sim` (0 <= sim < n_sims) from
+ * host FP64 arrays (structure of arrays): positions r, z (strictly inside
+ * the gap), velocity components vr, vtheta, vz (the velocity at half step
+ * -1/2 of the leapfrog) and unique uids (< 2^32).  Replaces the
+ * simulation's particles, resets its tallies and uid counter (max uid + 1),
+ * deposits the charge and, unless fixed_efield, solves the field (Sec. II.A
+ * seed load and first field; in a batch every simulation is solved again
+ * from its last deposit, which leaves the others' fields as they were).  A
+ * single simulation restarts at step 0; a simulation of a batch joins at the
+ * batch's current step.  Synchronises (page-locked host arrays make the
+ * copies faster).  PIC_EINVAL for out-of-domain or non-finite values, uids
+ * at or above 2^32, or n above the simulation's capacity. */
 int pic_load_particles(pic_handle* h, int sim, const double* r,
                        const double* z, const double* vr, const double* vt,
                        const double* vz, const uint64_t* uid, int64_t n);
@@ -204,8 +216,9 @@ int pic_get_grid(pic_handle* h, int sim, int which, double* out);
 
 /* Solve the field for a host right-hand side b (node array, C) and write
  * phi (host FP64): the same solver pic_step uses (Sec. II.A, finite
- * elements with Dirichlet walls and Neumann ends).  Synchronises.  Leaves
- * the simulation's own field untouched. */
+ * elements with Dirichlet walls and Neumann ends), with the wall potentials
+ * of simulation 0.  Synchronises.  Leaves the simulations' own fields
+ * untouched. */
 int pic_solve_field(pic_handle* h, const double* b, double* phi,
                     double* relres);
 
@@ -239,7 +252,8 @@ int pic_solve_field_static(const pic_config* cfg, const double* b, double* phi,
 /* Write the full state (particles, field, counters, tallies) to `path`;
  * pic_restore reads it into a handle made with the same configuration.
  * Stepping on after a restore gives the same particles as never stopping
- * (the random streams depend only on seed, uid and step). */
+ * (the random streams depend only on seed, uid and step).  Single
+ * simulations only (PIC_EINVAL for a batch). */
 int pic_checkpoint(pic_handle* h, const char* path);
 int pic_restore(pic_handle* h, const char* path);
 

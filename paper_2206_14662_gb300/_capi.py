@@ -159,12 +159,17 @@ def _torch_allocator():
 
 
 class Simulation:
-    """One simulation handle (pic_init ... pic_free)."""
+    """One handle (pic_init ... pic_free): a single simulation (cfg a dict)
+    or a batch stepped together (cfg a list of dicts, one per simulation;
+    the per-simulation calls take ``sim``)."""
 
-    def __init__(self, cfg: dict, stream=None, torch_allocator: bool = True):
+    def __init__(self, cfg, stream=None, torch_allocator: bool = True):
         L = lib()
-        self.cfg = dict(cfg)
-        self._c = make_config(cfg)
+        cfgs = [dict(c) for c in cfg] if isinstance(cfg, (list, tuple)) else [dict(cfg)]
+        self.cfgs = cfgs
+        self.cfg = cfgs[0]
+        self.n_sims = len(cfgs)
+        self._c = (PicConfig * len(cfgs))(*[make_config(c) for c in cfgs])
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -176,10 +181,10 @@ class Simulation:
             self._alloc = al
             alloc_p = ctypes.byref(self._alloc)
         h = ctypes.c_void_p()
-        _check(L.pic_init(ctypes.byref(self._c), 1, ctypes.c_void_p(self.stream), alloc_p,
+        _check(L.pic_init(self._c, len(cfgs), ctypes.c_void_p(self.stream), alloc_p,
                           ctypes.byref(h)), "pic_init")
         self.h = h
-        self.nnodes = (cfg["nr"] + 1) * (cfg["nz"] + 1)
+        self.nnodes = (self.cfg["nr"] + 1) * (self.cfg["nz"] + 1)
 
     def close(self):
         if getattr(self, "h", None):
@@ -198,20 +203,21 @@ class Simulation:
     def __exit__(self, *exc):
         self.close()
 
-    def load_particles(self, r, z, vr, vt, vz, uid):
+    def load_particles(self, r, z, vr, vt, vz, uid, sim: int = 0):
         ptrs = [_f64(a) for a in (r, z, vr, vt, vz)]
         pu = _u64(uid)
         n = len(r)
-        _check(lib().pic_load_particles(self.h, 0, *[p for p, _ in ptrs], pu[0], n),
+        _check(lib().pic_load_particles(self.h, sim, *[p for p, _ in ptrs], pu[0], n),
                "pic_load_particles")
 
     def step(self, nsteps: int = 1):
         _check(lib().pic_step(self.h, int(nsteps)), "pic_step")
 
-    def diagnostics(self, density: bool = False, raise_on_error: bool = True) -> dict:
+    def diagnostics(self, density: bool = False, raise_on_error: bool = True,
+                    sim: int = 0) -> dict:
         d = PicDiag()
         dens = np.zeros(self.nnodes) if density else None
-        rc = lib().pic_diagnostics(self.h, 0, ctypes.byref(d),
+        rc = lib().pic_diagnostics(self.h, sim, ctypes.byref(d),
                                    dens.ctypes.data_as(ctypes.c_void_p) if density else None)
         if raise_on_error:
             _check(rc, "pic_diagnostics")
@@ -221,25 +227,25 @@ class Simulation:
             out["density"] = dens
         return out
 
-    def export_particles(self) -> dict:
-        cap = int(self.diagnostics(raise_on_error=False)["n_particles"])
+    def export_particles(self, sim: int = 0) -> dict:
+        cap = int(self.diagnostics(raise_on_error=False, sim=sim)["n_particles"])
         arrs = [np.zeros(cap) for _ in range(5)]
         uid = np.zeros(cap, dtype=np.uint64)
         n = c_i64()
-        _check(lib().pic_export_particles(self.h, 0, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
+        _check(lib().pic_export_particles(self.h, sim, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
                                           uid.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n)),
                "pic_export_particles")
         k = n.value
         return dict(r=arrs[0][:k], z=arrs[1][:k], vr=arrs[2][:k], vt=arrs[3][:k], vz=arrs[4][:k],
                     uid=uid[:k])
 
-    def set_efield(self, er, ez):
+    def set_efield(self, er, ez, sim: int = 0):
         pe, pz = _f64(er), _f64(ez)
-        _check(lib().pic_set_efield(self.h, 0, pe[0], pz[0]), "pic_set_efield")
+        _check(lib().pic_set_efield(self.h, sim, pe[0], pz[0]), "pic_set_efield")
 
-    def get_grid(self, which: int) -> np.ndarray:
+    def get_grid(self, which: int, sim: int = 0) -> np.ndarray:
         out = np.zeros(self.nnodes)
-        _check(lib().pic_get_grid(self.h, 0, which, out.ctypes.data_as(ctypes.c_void_p)),
+        _check(lib().pic_get_grid(self.h, sim, which, out.ctypes.data_as(ctypes.c_void_p)),
                "pic_get_grid")
         return out
 

@@ -9,6 +9,13 @@
 //   4. field solve         DCT-I (z) / Thomas (r) / inverse DCT-I, then
 //                          E = -grad phi and the residual check
 // Counters live in device memory, so the host never waits inside pic_step.
+//
+// A handle holds nsim >= 1 simulations on one grid geometry (a parametric
+// scan: pressure, wall potentials, field strength, particle count per
+// simulation).  Simulation k owns a segment of the particle store, its own
+// device state, grids and spawn records; a batch runs each stage above as
+// one launch over all simulations (the fused kernel walks a prefix-sum table
+// of every segment's chunks).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -22,26 +29,43 @@
 using namespace pic;
 
 namespace pic {
-int particle_step_blocks_per_sm(int precision);
+int particle_step_blocks_per_sm(int precision, bool batch);
 int particle_chunk();
 }
 
+// per-simulation quantities derived on the host in FP64, and host
+// bookkeeping
+struct SimHost {
+  double n_gas, weight, nu_max, p_null, gas_mass;
+  unsigned thr_null;
+  long long capacity, spawn_cap, base;
+  double ke_initial;
+  double last_abs[4];
+  long long last_diag_step;
+};
+
 struct pic_handle {
-  pic_config cfg;
+  pic_config cfg;                 // simulation 0 (the shared geometry)
+  std::vector<pic_config> cfgs;   // every simulation
+  int nsim;
   int prec;
   cudaStream_t stream;
   pic_allocator alloc;
   bool has_alloc;
   std::vector<void*> owned;
 
-  // derived on the host in FP64
-  double n_gas, weight, nu_max, p_null, hr, hz, gas_mass;
-  unsigned thr_null;
-  long long capacity, spawn_cap;
+  std::vector<SimHost> sims;
+  double hr, hz;
+  long long capacity;             // slots of all segments
+  long long spawn_stride;         // spawn records per simulation
   int nnodes, ncells, grid_particle, grid_sort;
 
   // device memory
-  DevState* st;
+  DevState* st;                   // nsim entries
+  SegInfo* seg;                   // nsim entries (batch kernels)
+  float2* cnt_units;              // nsim fixed-point charge units / (2 pi eps0)
+  PushParams<float>* Pf_dev;      // nsim entries (batch kernel)
+  PushParams<double>* Pd_dev;
   Soa<float> sf[2];
   Soa<double> sd[2];
   int cur;
@@ -57,9 +81,6 @@ struct pic_handle {
 
   // host bookkeeping
   long long step;
-  double ke_initial;
-  double last_abs[4];
-  long long last_diag_step;
   int sticky;
   long long kernels;
 
@@ -80,8 +101,8 @@ struct pic_handle {
   long long prof_kernels0;
   long long prof_counts[4];
 
-  PushParams<float> Pf;
-  PushParams<double> Pd;
+  std::vector<PushParams<float>> Pf;   // per simulation
+  std::vector<PushParams<double>> Pd;
 };
 
 namespace {
@@ -142,9 +163,26 @@ int validate(const pic_config& c) {
   return PIC_OK;
 }
 
+// simulations of one handle share the grid geometry, the time step, the
+// sort and field-solve settings, the precision and the seed (each
+// simulation's particles draw from the counter block of its index)
+int validate_batch(const pic_config* c, int n) {
+  const pic_config& a = c[0];
+  for (int k = 1; k < n; ++k) {
+    const pic_config& b = c[k];
+    if (b.r_in != a.r_in || b.r_out != a.r_out || b.z_min != a.z_min || b.z_max != a.z_max ||
+        b.nr != a.nr || b.nz != a.nz || b.dt != a.dt || b.sort_every != a.sort_every ||
+        b.poisson_rtol != a.poisson_rtol || b.poisson_maxit != a.poisson_maxit ||
+        b.precision != a.precision || b.seed != a.seed || b.fixed_efield != a.fixed_efield)
+      return PIC_EINVAL;
+  }
+  return PIC_OK;
+}
+
 template <typename Real>
-void fill_params(pic_handle* h, PushParams<Real>& P) {
-  const pic_config& c = h->cfg;
+void fill_params(pic_handle* h, int k, PushParams<Real>& P) {
+  const pic_config& c = h->cfgs[k];
+  const SimHost& m = h->sims[k];
   const double L = c.z_max - c.z_min;
   P.r_in = (Real)c.r_in; P.hr = (Real)h->hr; P.inv_hr = (Real)(1.0 / h->hr);
   P.z_min = (Real)c.z_min; P.hz = (Real)h->hz; P.inv_hz = (Real)(1.0 / h->hz);
@@ -153,29 +191,31 @@ void fill_params(pic_handle* h, PushParams<Real>& P) {
   P.nr = c.nr; P.nz = c.nz; P.bkind = c.bfield_kind;
   P.qmdt2 = (Real)(-kQe * c.dt / (2.0 * kMe));
   P.dt = (Real)c.dt;
-  P.thr_null = h->thr_null;
-  P.nsig_el = (Real)(h->n_gas * c.sigma_el);
-  P.n_gas = (Real)h->n_gas;
+  P.thr_null = m.thr_null;
+  P.nsig_el = (Real)(m.n_gas * c.sigma_el);
+  P.n_gas = (Real)m.n_gas;
   P.e_th = (Real)(c.ion_E_th_eV * kQe);
   P.e_span_inv = (Real)(1.0 / ((c.ion_E_pk_eV - c.ion_E_th_eV) * kQe));
   P.sig_pk = (Real)c.ion_sigma_pk;
   P.opal_b = (Real)(c.opal_B_eV * kQe);
   P.xi = (Real)c.xi_param;
-  P.recoil = c.elastic_recoil ? (Real)(2.0 * kMe / h->gas_mass) : (Real)0;
-  P.nu_max = (Real)h->nu_max;
+  P.recoil = c.elastic_recoil ? (Real)(2.0 * kMe / m.gas_mass) : (Real)0;
+  P.nu_max = (Real)m.nu_max;
   P.half_m = (Real)(0.5 * kMe);
   P.two_over_m = (Real)(2.0 / kMe);
   P.work_scale = (Real)(-kQe * c.dt / 4.0);
-  P.weight = h->weight;
-  P.qw = -kQe * h->weight;
+  P.weight = m.weight;
+  P.qw = -kQe * m.weight;
   P.seed_lo = (unsigned)(c.seed & 0xFFFFFFFFull);
   P.seed_hi = (unsigned)(c.seed >> 32);
+  P.uid_hi = (unsigned)k;
   for (int r = 0; r < 10; ++r) {
     P.rk0[r] = P.seed_lo + (unsigned)r * 0x9E3779B9u;
     P.rk1[r] = P.seed_hi + (unsigned)r * 0xBB67AE85u;
   }
-  P.capacity = h->capacity;
-  P.spawn_cap = h->spawn_cap;
+  P.capacity = m.capacity;
+  P.spawn_cap = m.spawn_cap;
+  P.base = m.base;
   P.r_in_d = c.r_in;
   P.hr_d = h->hr;
   P.z_min_d = c.z_min;
@@ -221,38 +261,61 @@ Soa<float>& soa<float>(pic_handle* h, int which) { return h->sf[which]; }
 template <>
 Soa<double>& soa<double>(pic_handle* h, int which) { return h->sd[which]; }
 template <typename Real>
-const PushParams<Real>& params(pic_handle* h);
+const PushParams<Real>& params(pic_handle* h, int k = 0);
 template <>
-const PushParams<float>& params<float>(pic_handle* h) { return h->Pf; }
+const PushParams<float>& params<float>(pic_handle* h, int k) { return h->Pf[k]; }
 template <>
-const PushParams<double>& params<double>(pic_handle* h) { return h->Pd; }
+const PushParams<double>& params<double>(pic_handle* h, int k) { return h->Pd[k]; }
+template <typename Real>
+const PushParams<Real>* params_dev(pic_handle* h);
+template <>
+const PushParams<float>* params_dev<float>(pic_handle* h) { return h->Pf_dev; }
+template <>
+const PushParams<double>* params_dev<double>(pic_handle* h) { return h->Pd_dev; }
 
 template <typename Real>
 int step_impl(pic_handle* h, long long nsteps) {
   const PushParams<Real>& P = params<Real>(h);
   const bool solve = h->cfg.fixed_efield == 0;
+  const bool batch = h->nsim > 1;
+  const size_t grid_nodes = (size_t)h->nsim * h->nnodes;
   for (long long s = 0; s < nsteps; ++s) {
     mark(h, kTagStart);
     const bool fp32 = std::is_same<Real, float>::value;
     if (fp32 && !solve) {
-      CK(cudaMemsetAsync(h->cnt[h->dep_buf], 0, (size_t)h->nnodes * sizeof(unsigned long long),
+      CK(cudaMemsetAsync(h->cnt[h->dep_buf], 0, grid_nodes * sizeof(unsigned long long),
                          h->stream));
     }
     if (!fp32) {
-      CK(cudaMemsetAsync(h->rhs, 0, (size_t)h->nnodes * sizeof(double), h->stream));
+      CK(cudaMemsetAsync(h->rhs, 0, grid_nodes * sizeof(double), h->stream));
     }
-    launch_particle_step<Real>(soa<Real>(h, h->cur), h->efield, h->rhs,
-                               fp32 ? h->cnt[h->dep_buf] : nullptr, h->st, h->spawn_parent, P,
-                               h->grid_particle, h->stream);
+    if (batch)
+      launch_particle_step_batch<Real>(soa<Real>(h, h->cur), h->efield, fp32 ? nullptr : h->rhs,
+                                       fp32 ? h->cnt[h->dep_buf] : nullptr, h->st,
+                                       h->spawn_parent, h->spawn_stride, params_dev<Real>(h),
+                                       h->nsim, h->nnodes, h->grid_particle, h->stream);
+    else
+      launch_particle_step<Real>(soa<Real>(h, h->cur), h->efield, h->rhs,
+                                 fp32 ? h->cnt[h->dep_buf] : nullptr, h->st, h->spawn_parent, P,
+                                 h->grid_particle, h->stream);
     mark(h, kTagParticle);
-    launch_spawn_finalize(h->st, soa<Real>(h, h->cur).uid, h->spawn_parent, h->spawn_cap,
-                          h->capacity, h->stream);
+    if (batch)
+      launch_spawn_finalize_batch(h->st, soa<Real>(h, h->cur).uid, h->spawn_parent,
+                                  h->spawn_stride, h->seg, h->nsim, h->stream);
+    else
+      launch_spawn_finalize(h->st, soa<Real>(h, h->cur).uid, h->spawn_parent,
+                            h->sims[0].spawn_cap, h->sims[0].capacity, h->stream);
     h->kernels += 2;
     mark(h, kTagFinalize);
     ++h->step;
     if (h->cfg.sort_every > 0 && h->step % h->cfg.sort_every == 0) {
-      launch_sort<Real>(soa<Real>(h, h->cur), soa<Real>(h, h->cur ^ 1), h->st, h->cell_count,
-                        h->ncells, h->cfg.nz, h->grid_sort, h->stream);
+      if (batch)
+        launch_sort_batch<Real>(soa<Real>(h, h->cur), soa<Real>(h, h->cur ^ 1), h->st, h->seg,
+                                h->nsim, h->cell_count, h->ncells, h->cfg.nz, h->grid_sort,
+                                h->stream);
+      else
+        launch_sort<Real>(soa<Real>(h, h->cur), soa<Real>(h, h->cur ^ 1), h->st, h->cell_count,
+                          h->ncells, h->cfg.nz, h->grid_sort, h->stream);
       h->cur ^= 1;
       h->kernels += 4;
       mark(h, kTagSort);
@@ -260,10 +323,12 @@ int step_impl(pic_handle* h, long long nsteps) {
     if (fp32) h->last_buf = h->dep_buf;
     if (solve) {
       if (fp32)
-        launch_field_solve<Real>(h->T, nullptr, h->cnt[h->dep_buf], -kQe * h->weight / kFixUnit,
-                                 h->cnt[h->dep_buf ^ 1], h->efield, h->st, h->stream);
+        launch_field_solve<Real>(h->T, nullptr, h->cnt[h->dep_buf],
+                                 -kQe * h->sims[0].weight / kFixUnit,
+                                 batch ? h->cnt_units : nullptr, h->cnt[h->dep_buf ^ 1],
+                                 h->efield, h->st, h->stream);
       else
-        launch_field_solve<Real>(h->T, h->rhs, nullptr, 0.0, nullptr, h->efield, h->st,
+        launch_field_solve<Real>(h->T, h->rhs, nullptr, 0.0, nullptr, nullptr, h->efield, h->st,
                                  h->stream);
       if (fp32) h->dep_buf ^= 1;
       h->kernels += field_solve_kernels(h->T);
@@ -276,17 +341,19 @@ int step_impl(pic_handle* h, long long nsteps) {
 
 // node charge b_i of the last deposit (C) copied to the host: the FP32
 // path keeps fixed-point counts, the FP64 path charges
-int read_rho(pic_handle* h, double* out) {
+int read_rho(pic_handle* h, int sim, double* out) {
+  const size_t go = (size_t)sim * h->nnodes;
   if (h->prec == 32) {
     std::vector<unsigned long long> c(h->nnodes);
-    CK(cudaMemcpyAsync(c.data(), h->cnt[h->last_buf], (size_t)h->nnodes * sizeof(unsigned long long),
-                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(c.data(), h->cnt[h->last_buf] + go,
+                       (size_t)h->nnodes * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    const double unit = -kQe * h->weight / kFixUnit;
+    const double unit = -kQe * h->sims[sim].weight / kFixUnit;
     for (int i = 0; i < h->nnodes; ++i) out[i] = (double)c[i] * unit;
   } else {
-    CK(cudaMemcpyAsync(out, h->rhs, (size_t)h->nnodes * sizeof(double), cudaMemcpyDeviceToHost,
-                       h->stream));
+    CK(cudaMemcpyAsync(out, h->rhs + go, (size_t)h->nnodes * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   }
   return PIC_OK;
@@ -294,13 +361,20 @@ int read_rho(pic_handle* h, double* out) {
 
 int check_sticky(pic_handle* h) {
   if (h->sticky) return h->sticky;
-  int err = 0;
-  if (cudaMemcpyAsync(&err, &h->st->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=
-          cudaSuccess ||
+  std::vector<DevState> s(h->nsim);
+  if (cudaMemcpyAsync(s.data(), h->st, s.size() * sizeof(DevState), cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return h->sticky = PIC_ECUDA;
-  if (err) h->sticky = err;
+  for (const DevState& x : s)
+    if (x.err && !h->sticky) h->sticky = x.err;
   return h->sticky;
+}
+
+// the store of the current buffer set as seen by simulation `sim`
+template <typename Real>
+Soa<Real> sim_soa(pic_handle* h, int sim, int which) {
+  return soa_offset(soa<Real>(h, which), h->sims[sim].base);
 }
 
 }  // namespace
@@ -327,49 +401,70 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
              const pic_allocator* alloc, pic_handle** out) {
   if (!cfg || !out) return PIC_EINVAL;
   *out = nullptr;
-  if (n_sims != 1) return PIC_EINVAL;
-  int rc = validate(*cfg);
+  if (n_sims < 1 || n_sims > kMaxSims) return PIC_EINVAL;
+  for (int k = 0; k < n_sims; ++k) {
+    const int rc = validate(cfg[k]);
+    if (rc) return rc;
+  }
+  int rc = validate_batch(cfg, n_sims);
   if (rc) return rc;
   pic_handle* h = new (std::nothrow) pic_handle();
   if (!h) return PIC_ENOMEM;
-  h->cfg = *cfg;
+  h->cfg = cfg[0];
+  h->cfgs.assign(cfg, cfg + n_sims);
+  h->nsim = n_sims;
   h->prec = cfg->precision;
   h->stream = (cudaStream_t)cuda_stream;
   h->has_alloc = alloc && alloc->alloc && alloc->free;
   if (h->has_alloc) h->alloc = *alloc;
   const pic_config& c = h->cfg;
 
-  // derived quantities (FP64, host)
+  // derived quantities (FP64, host), per simulation; segments of the store
+  // start on whole chunks of the fused kernel
   const double L = c.z_max - c.z_min;
   h->hr = (c.r_out - c.r_in) / c.nr;
   h->hz = L / c.nz;
-  h->n_gas = c.p_mbar * 100.0 / (kKb * c.t_gas_K);
-  h->weight = c.weight > 0 ? c.weight
-                           : c.n0 * kPi * (c.r_out * c.r_out - c.r_in * c.r_in) * L / (double)c.n_init;
-  h->gas_mass = c.gas_mass_amu * kAmu;
-  if (c.nu_max > 0) {
-    h->nu_max = c.nu_max;
-  } else {
-    const double E_cap = 2.0 * std::fabs(c.v_inner - c.v_outer);
-    double best = 0.0;
-    for (int k = 0; k <= 100000; ++k) {
-      const double E_eV = E_cap * (double)k / 100000.0;
-      const double v = std::sqrt(2.0 * E_eV * kQe / kMe);
-      const double nu = h->n_gas * c.sigma_el * v + h->n_gas * sigma_ion_host(c, E_eV) * v;
-      if (nu > best) best = nu;
+  const long long ch = particle_chunk();
+  h->sims.resize(n_sims);
+  long long base = 0, spawn_stride = 0;
+  for (int k = 0; k < n_sims; ++k) {
+    const pic_config& ck = h->cfgs[k];
+    SimHost& m = h->sims[k];
+    std::memset(&m, 0, sizeof(m));
+    m.n_gas = ck.p_mbar * 100.0 / (kKb * ck.t_gas_K);
+    m.weight = ck.weight > 0 ? ck.weight
+                             : ck.n0 * kPi * (ck.r_out * ck.r_out - ck.r_in * ck.r_in) * L /
+                                   (double)ck.n_init;
+    m.gas_mass = ck.gas_mass_amu * kAmu;
+    if (ck.nu_max > 0) {
+      m.nu_max = ck.nu_max;
+    } else {
+      const double E_cap = 2.0 * std::fabs(ck.v_inner - ck.v_outer);
+      double best = 0.0;
+      for (int q = 0; q <= 100000; ++q) {
+        const double E_eV = E_cap * (double)q / 100000.0;
+        const double v = std::sqrt(2.0 * E_eV * kQe / kMe);
+        const double nu = m.n_gas * ck.sigma_el * v + m.n_gas * sigma_ion_host(ck, E_eV) * v;
+        if (nu > best) best = nu;
+      }
+      m.nu_max = best * (1.0 + 1e-6);
     }
-    h->nu_max = best * (1.0 + 1e-6);
+    m.p_null = 1.0 - std::exp(-m.nu_max * ck.dt);
+    const double cthr = m.p_null * 16777216.0 - 0.5;
+    m.thr_null = cthr <= 0 ? 0u : (unsigned)std::min(16777216.0, std::ceil(cthr));
+    m.capacity = ck.capacity > 0 ? ck.capacity
+                                 : (long long)(1.25 * (double)std::max<int64_t>(ck.n_init, 0)) + 4096;
+    m.spawn_cap = std::min<long long>(m.capacity, 1 << 20);
+    m.base = base;
+    base += (m.capacity + ch - 1) / ch * ch;
+    spawn_stride = std::max(spawn_stride, m.spawn_cap);
   }
-  h->p_null = 1.0 - std::exp(-h->nu_max * c.dt);
-  {
-    const double cthr = h->p_null * 16777216.0 - 0.5;
-    h->thr_null = cthr <= 0 ? 0u : (unsigned)std::min(16777216.0, std::ceil(cthr));
-  }
-  h->capacity = c.capacity > 0 ? c.capacity : (long long)(1.25 * (double)c.n_init) + 4096;
+  h->capacity = base;
+  h->spawn_stride = spawn_stride;
   if (h->capacity > (1ll << 31) - 1) { delete h; return PIC_EINVAL; }
-  h->spawn_cap = std::min<long long>(h->capacity, 1 << 20);
   h->nnodes = (c.nr + 1) * (c.nz + 1);
   h->ncells = c.nr * c.nz;
+  const size_t S = (size_t)n_sims;
 
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -377,14 +472,19 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
     delete h;
     return PIC_ECUDA;
   }
-  const int bps = std::max(1, particle_step_blocks_per_sm(h->prec));
+  const bool batch = n_sims > 1;
+  const int bps = std::max(1, particle_step_blocks_per_sm(h->prec, batch));
   const long long chunks = (h->capacity + 1023) / 1024;
   h->grid_particle = (int)std::max<long long>(1, std::min<long long>((long long)sms * bps, chunks));
   h->grid_sort = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8,
                                                                  (h->capacity + 255) / 256));
 
   // device memory
-  h->st = (DevState*)h_alloc(sizeof(DevState), h);
+  h->st = (DevState*)h_alloc(S * sizeof(DevState), h);
+  h->seg = (SegInfo*)h_alloc(S * sizeof(SegInfo), h);
+  h->cnt_units = (float2*)h_alloc(S * sizeof(float2), h);
+  h->Pf_dev = (PushParams<float>*)h_alloc(S * sizeof(PushParams<float>), h);
+  h->Pd_dev = (PushParams<double>*)h_alloc(S * sizeof(PushParams<double>), h);
   if (h->prec == 32) {
     rc = alloc_soa(h, h->sf[0]);
     if (!rc) rc = alloc_soa(h, h->sf[1]);
@@ -392,43 +492,69 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
     rc = alloc_soa(h, h->sd[0]);
     if (!rc) rc = alloc_soa(h, h->sd[1]);
   }
-  h->spawn_parent = (unsigned*)h_alloc((size_t)h->spawn_cap * sizeof(unsigned), h);
-  // whole multiples of 4096 counts: the scan reads them as int4 vectors
-  h->cell_count = (int*)h_alloc((size_t)(h->ncells + 4095) / 4096 * 4096 * sizeof(int), h);
-  h->rhs = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
-  h->cnt[0] = (unsigned long long*)h_alloc((size_t)h->nnodes * sizeof(unsigned long long), h);
-  h->cnt[1] = (unsigned long long*)h_alloc((size_t)h->nnodes * sizeof(unsigned long long), h);
+  const size_t gn = S * (size_t)h->nnodes;
+  h->spawn_parent = (unsigned*)h_alloc(S * (size_t)h->spawn_stride * sizeof(unsigned), h);
+  // whole multiples of 4096 counts per simulation: the scan reads them as
+  // int4 vectors
+  h->cell_count = (int*)h_alloc(S * ((size_t)(h->ncells + 4095) / 4096 * 4096) * sizeof(int), h);
+  h->rhs = (double*)h_alloc(gn * sizeof(double), h);
+  h->cnt[0] = (unsigned long long*)h_alloc(gn * sizeof(unsigned long long), h);
+  h->cnt[1] = (unsigned long long*)h_alloc(gn * sizeof(unsigned long long), h);
   h->phi = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
-  h->efield = h_alloc((size_t)h->nnodes * (h->prec == 32 ? sizeof(float2) : sizeof(double2)), h);
+  h->efield = h_alloc(gn * (h->prec == 32 ? sizeof(float2) : sizeof(double2)), h);
   h->scratch2 = (double*)h_alloc(2 * sizeof(double), h);
-  if (!rc && (!h->st || !h->spawn_parent || !h->cell_count || !h->rhs || !h->cnt[0] || !h->cnt[1] ||
+  if (!rc && (!h->st || !h->seg || !h->cnt_units || !h->Pf_dev || !h->Pd_dev ||
+              !h->spawn_parent || !h->cell_count || !h->rhs || !h->cnt[0] || !h->cnt[1] ||
               !h->phi || !h->efield || !h->scratch2))
     rc = PIC_ENOMEM;
-  if (!rc) rc = field_tables_build(c, h->T, h_alloc, h, h->stream);
+  if (!rc) rc = field_tables_build(h->cfgs.data(), n_sims, h->T, h_alloc, h, h->stream);
   if (!rc) {
-    DevState s0;
-    std::memset(&s0, 0, sizeof(s0));
-    if (cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->rhs, 0, (size_t)h->nnodes * sizeof(double), h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->cnt[0], 0, (size_t)h->nnodes * sizeof(unsigned long long), h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->cnt[1], 0, (size_t)h->nnodes * sizeof(unsigned long long), h->stream) != cudaSuccess ||
+    h->Pf.resize(n_sims);
+    h->Pd.resize(n_sims);
+    std::vector<SegInfo> seg(n_sims);
+    std::vector<float2> units(n_sims);
+    const double s0 = 1.0 / (2.0 * kPi * kEps0);
+    for (int k = 0; k < n_sims; ++k) {
+      fill_params<float>(h, k, h->Pf[k]);
+      fill_params<double>(h, k, h->Pd[k]);
+      seg[k] = SegInfo{h->sims[k].base, h->sims[k].capacity, h->sims[k].spawn_cap};
+      units[k] = df_from(-kQe * h->sims[k].weight / kFixUnit * s0);
+    }
+    std::vector<DevState> s0v(n_sims);
+    std::memset(s0v.data(), 0, S * sizeof(DevState));
+    if (cudaMemcpyAsync(h->st, s0v.data(), S * sizeof(DevState), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->seg, seg.data(), S * sizeof(SegInfo), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->cnt_units, units.data(), S * sizeof(float2), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->Pf_dev, h->Pf.data(), S * sizeof(PushParams<float>),
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->Pd_dev, h->Pd.data(), S * sizeof(PushParams<double>),
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->rhs, 0, gn * sizeof(double), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->cnt[0], 0, gn * sizeof(unsigned long long), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->cnt[1], 0, gn * sizeof(unsigned long long), h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess)
       rc = PIC_ECUDA;
   }
   if (!rc) {
     // vacuum field until particles are loaded
     if (h->prec == 32)
-      launch_field_solve<float>(h->T, nullptr, h->cnt[0], 1.0, nullptr, h->efield, h->st, h->stream);
+      launch_field_solve<float>(h->T, nullptr, h->cnt[0], 1.0, nullptr, nullptr, h->efield,
+                                h->st, h->stream);
     else
-      launch_field_solve<double>(h->T, h->rhs, nullptr, 0.0, nullptr, h->efield, h->st, h->stream);
+      launch_field_solve<double>(h->T, h->rhs, nullptr, 0.0, nullptr, nullptr, h->efield, h->st,
+                                 h->stream);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = PIC_ECUDA;
   }
   if (rc) {
     pic_free(h);
     return rc;
   }
-  fill_params<float>(h, h->Pf);
-  fill_params<double>(h, h->Pd);
+  // the last deposit is in cnt[last_buf], the next goes to cnt[dep_buf]
+  h->last_buf = 0;
+  h->dep_buf = c.fixed_efield ? 0 : 1;
   {
     // a graph block returns the alternating buffers (sort ping-pong, FP32
     // deposit buffers) to a fixed pattern: lcm(sort_every, 2) steps
@@ -455,9 +581,10 @@ void pic_free(pic_handle* h) {
 int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
                        const double* vr, const double* vt, const double* vz,
                        const uint64_t* uid, int64_t n) {
-  if (!h || sim != 0 || n < 0 || n > h->capacity) return PIC_EINVAL;
+  if (!h || sim < 0 || sim >= h->nsim || n < 0 || n > h->sims[sim].capacity) return PIC_EINVAL;
   if (n > 0 && (!r || !z || !vr || !vt || !vz || !uid)) return PIC_EINVAL;
-  const pic_config& c = h->cfg;
+  const pic_config& c = h->cfgs[sim];
+  SimHost& m = h->sims[sim];
   uint64_t umax = 0;
   for (int64_t p = 0; p < n; ++p) {
     if (!(r[p] > c.r_in && r[p] < c.r_out && z[p] > c.z_min && z[p] < c.z_max)) return PIC_EINVAL;
@@ -486,54 +613,74 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
   if (n > 0 && cudaMemcpyAsync(du, uid, (size_t)n * sizeof(uint64_t), cudaMemcpyHostToDevice,
                                h->stream) != cudaSuccess)
     rc = PIC_ECUDA;
-  h->cur = 0;
+  // a single simulation restarts from step 0 in buffer set 0; a simulation
+  // of a batch is loaded into the current buffer set at the batch's step
+  const bool batch = h->nsim > 1;
+  if (!batch) {
+    h->cur = 0;
+    h->step = 0;
+    h->last_buf = 0;
+  }
   if (!rc) {
     if (h->prec == 32)
-      launch_load<float>(d[0], d[1], d[2], d[3], d[4], du, n, h->sf[0], h->Pf, h->st, h->stream);
+      launch_load<float>(d[0], d[1], d[2], d[3], d[4], du, n, sim_soa<float>(h, sim, h->cur),
+                         h->Pf[sim], h->st + sim, h->stream);
     else
-      launch_load<double>(d[0], d[1], d[2], d[3], d[4], du, n, h->sd[0], h->Pd, h->st, h->stream);
+      launch_load<double>(d[0], d[1], d[2], d[3], d[4], du, n, sim_soa<double>(h, sim, h->cur),
+                          h->Pd[sim], h->st + sim, h->stream);
   }
   DevState s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.n_slots = n;
   s0.n_live = n;
   s0.uid_next = n > 0 ? umax + 1 : 0;
-  if (!rc && (cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) !=
+  s0.step = (unsigned)h->step;
+  const size_t go = (size_t)sim * h->nnodes, gb = (size_t)h->nnodes;
+  const int ld = h->last_buf;   // the load's deposit becomes the last deposit
+  if (!rc && (cudaMemcpyAsync(h->st + sim, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) !=
                   cudaSuccess ||
-              cudaMemsetAsync(h->rhs, 0, (size_t)h->nnodes * sizeof(double), h->stream) !=
+              cudaMemsetAsync(h->rhs + go, 0, gb * sizeof(double), h->stream) != cudaSuccess ||
+              cudaMemsetAsync(h->cnt[0] + go, 0, gb * sizeof(unsigned long long), h->stream) !=
                   cudaSuccess ||
-              cudaMemsetAsync(h->cnt[0], 0, (size_t)h->nnodes * sizeof(unsigned long long), h->stream) !=
+              cudaMemsetAsync(h->cnt[1] + go, 0, gb * sizeof(unsigned long long), h->stream) !=
                   cudaSuccess ||
-              cudaMemsetAsync(h->cnt[1], 0, (size_t)h->nnodes * sizeof(unsigned long long), h->stream) !=
-                  cudaSuccess ||
-              cudaMemsetAsync(h->T.phir, 0, (size_t)h->nnodes * sizeof(float2), h->stream) !=
-                  cudaSuccess))
+              cudaMemsetAsync(h->T.phir + go, 0, gb * sizeof(float2), h->stream) != cudaSuccess))
     rc = PIC_ECUDA;
   if (!rc) {
-    const double qw = -kQe * h->weight;
-    h->last_buf = 0;
-    h->dep_buf = 0;
-    if (h->prec == 32) launch_deposit_only<float>(h->sf[0], n, h->rhs, h->cnt[0], c.nz, qw, h->stream);
-    else launch_deposit_only<double>(h->sd[0], n, h->rhs, nullptr, c.nz, qw, h->stream);
+    const double qw = -kQe * m.weight;
+    if (h->prec == 32)
+      launch_deposit_only<float>(sim_soa<float>(h, sim, h->cur), n, nullptr, h->cnt[ld] + go,
+                                 c.nz, qw, h->stream);
+    else
+      launch_deposit_only<double>(sim_soa<double>(h, sim, h->cur), n, h->rhs + go, nullptr, c.nz,
+                                  qw, h->stream);
     if (c.fixed_efield == 0) {
-      if (h->prec == 32) {
-        launch_field_solve<float>(h->T, nullptr, h->cnt[0], qw / kFixUnit, h->cnt[1], h->efield,
+      // every simulation is solved again from its last deposit (the others'
+      // fields come out as they were)
+      if (h->prec == 32)
+        launch_field_solve<float>(h->T, nullptr, h->cnt[ld], qw / kFixUnit,
+                                  batch ? h->cnt_units : nullptr, h->cnt[ld ^ 1], h->efield,
                                   h->st, h->stream);
-        h->dep_buf = 1;
-      } else {
-        launch_field_solve<double>(h->T, h->rhs, nullptr, 0.0, nullptr, h->efield, h->st,
-                                   h->stream);
-      }
+      else
+        launch_field_solve<double>(h->T, h->rhs, nullptr, 0.0, nullptr, nullptr, h->efield,
+                                   h->st, h->stream);
+      h->dep_buf = ld ^ 1;
+    } else {
+      h->dep_buf = ld;
     }
     // initial kinetic energy
     cudaMemsetAsync(h->scratch2, 0, 2 * sizeof(double), h->stream);
-    if (h->prec == 32) launch_kinetic_energy<float>(h->sf[0], h->st, h->scratch2, h->stream);
-    else launch_kinetic_energy<double>(h->sd[0], h->st, h->scratch2, h->stream);
+    if (h->prec == 32)
+      launch_kinetic_energy<float>(sim_soa<float>(h, sim, h->cur), h->st + sim, h->scratch2,
+                                   h->stream);
+    else
+      launch_kinetic_energy<double>(sim_soa<double>(h, sim, h->cur), h->st + sim, h->scratch2,
+                                    h->stream);
     double ke[2] = {0, 0};
     if (cudaMemcpyAsync(ke, h->scratch2, sizeof(ke), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
       rc = PIC_ECUDA;
-    h->ke_initial = 0.5 * kMe * ke[0] * h->weight;
+    m.ke_initial = 0.5 * kMe * ke[0] * m.weight;
   } else {
     cudaStreamSynchronize(h->stream);
   }
@@ -544,9 +691,8 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
     if (it != h->owned.end()) h->owned.erase(it);
     h_free_one(p, h);
   }
-  h->step = 0;
-  h->last_diag_step = 0;
-  for (double& a : h->last_abs) a = 0.0;
+  m.last_diag_step = h->step;
+  for (double& a : m.last_abs) a = 0.0;
   return rc;
 }
 
@@ -630,20 +776,25 @@ int pic_step(pic_handle* h, int64_t nsteps) {
 }
 
 int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
-  if (!h || sim != 0 || !out) return PIC_EINVAL;
-  const pic_config& c = h->cfg;
+  if (!h || sim < 0 || sim >= h->nsim || !out) return PIC_EINVAL;
+  const pic_config& c = h->cfgs[sim];
+  SimHost& m = h->sims[sim];
   DevState s;
   CK(cudaMemsetAsync(h->scratch2, 0, 2 * sizeof(double), h->stream));
-  if (h->prec == 32) launch_kinetic_energy<float>(h->sf[h->cur], h->st, h->scratch2, h->stream);
-  else launch_kinetic_energy<double>(h->sd[h->cur], h->st, h->scratch2, h->stream);
+  if (h->prec == 32)
+    launch_kinetic_energy<float>(sim_soa<float>(h, sim, h->cur), h->st + sim, h->scratch2,
+                                 h->stream);
+  else
+    launch_kinetic_energy<double>(sim_soa<double>(h, sim, h->cur), h->st + sim, h->scratch2,
+                                  h->stream);
   double ke[2];
-  CK(cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&s, h->st + sim, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(ke, h->scratch2, sizeof(ke), cudaMemcpyDeviceToHost, h->stream));
   std::vector<double> grid;
   CK(cudaStreamSynchronize(h->stream));
   if (density) {
     grid.resize(h->nnodes);
-    int rr = read_rho(h, grid.data());
+    int rr = read_rho(h, sim, grid.data());
     if (rr) return rr;
   }
   CK(cudaGetLastError());
@@ -652,14 +803,14 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
   out->step = h->step;
   out->t = (double)h->step * c.dt;
   out->n_particles = (int64_t)ke[1];
-  const double dtw = (double)(h->step - h->last_diag_step) * c.dt;
+  const double dtw = (double)(h->step - m.last_diag_step) * c.dt;
   double* I[4] = {&out->I_inner, &out->I_outer, &out->I_zmin, &out->I_zmax};
   for (int w = 0; w < 4; ++w) {
     out->absorbed_weight[w] = s.tally[kAbsInner + w];
-    *I[w] = dtw > 0 ? (s.tally[kAbsInner + w] - h->last_abs[w]) * kQe / dtw : 0.0;
-    h->last_abs[w] = s.tally[kAbsInner + w];
+    *I[w] = dtw > 0 ? (s.tally[kAbsInner + w] - m.last_abs[w]) * kQe / dtw : 0.0;
+    m.last_abs[w] = s.tally[kAbsInner + w];
   }
-  h->last_diag_step = h->step;
+  m.last_diag_step = h->step;
   out->n_elastic = (int64_t)s.tally[kNElastic];
   out->n_ionise = (int64_t)s.tally[kNIonise];
   out->n_absorbed = (int64_t)s.tally[kNAbsorbed];
@@ -667,19 +818,19 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
   out->n_over = (int64_t)s.tally[kNOver];
   out->n_pushed = (int64_t)s.tally[kNPushed];
   out->kernels_launched = h->kernels;
-  out->ke_total_J = 0.5 * kMe * ke[0] * h->weight;
+  out->ke_total_J = 0.5 * kMe * ke[0] * m.weight;
   out->work_E_J = s.tally[kWorkE];
   out->ke_absorbed_J = s.tally[kKeAbsorbed];
   out->ion_loss_J = s.tally[kIonLoss];
   out->recoil_loss_J = s.tally[kRecoilLoss];
-  out->ke_initial_J = h->ke_initial;
-  out->ledger_residual_J = (out->ke_total_J - h->ke_initial) -
+  out->ke_initial_J = m.ke_initial;
+  out->ledger_residual_J = (out->ke_total_J - m.ke_initial) -
                            (out->work_E_J - out->ke_absorbed_J - out->ion_loss_J - out->recoil_loss_J);
   out->poisson_iters = s.poisson_iters;
   out->poisson_relres = s.relres_last;
   out->poisson_relres_charge = s.relres_strict;
-  out->nu_max = h->nu_max;
-  out->weight = h->weight;
+  out->nu_max = m.nu_max;
+  out->weight = m.weight;
   out->error = h->sticky;
   if (density) {
     // node volume of each hat function: 2 pi R_i Z_j
@@ -703,9 +854,9 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
 
 int pic_export_particles(pic_handle* h, int sim, double* r, double* z, double* vr,
                          double* vt, double* vz, uint64_t* uid, int64_t cap, int64_t* n) {
-  if (!h || sim != 0 || !n) return PIC_EINVAL;
+  if (!h || sim < 0 || sim >= h->nsim || !n) return PIC_EINVAL;
   DevState s;
-  CK(cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&s, h->st + sim, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (s.err && !h->sticky) h->sticky = s.err;
   const long long ns = s.n_slots;
@@ -721,13 +872,13 @@ int pic_export_particles(pic_handle* h, int sim, double* r, double* z, double* v
       if (!d[k]) return PIC_ENOMEM;
     }
     if (h->prec == 32)
-      launch_export<float>(h->sf[h->cur], ns, h->Pf, (double*)d[0], (double*)d[1], (double*)d[2],
-                           (double*)d[3], (double*)d[4], (unsigned long long*)d[5], (int*)d[6],
-                           h->stream);
+      launch_export<float>(sim_soa<float>(h, sim, h->cur), ns, h->Pf[sim], (double*)d[0],
+                           (double*)d[1], (double*)d[2], (double*)d[3], (double*)d[4],
+                           (unsigned long long*)d[5], (int*)d[6], h->stream);
     else
-      launch_export<double>(h->sd[h->cur], ns, h->Pd, (double*)d[0], (double*)d[1], (double*)d[2],
-                            (double*)d[3], (double*)d[4], (unsigned long long*)d[5], (int*)d[6],
-                            h->stream);
+      launch_export<double>(sim_soa<double>(h, sim, h->cur), ns, h->Pd[sim], (double*)d[0],
+                            (double*)d[1], (double*)d[2], (double*)d[3], (double*)d[4],
+                            (unsigned long long*)d[5], (int*)d[6], h->stream);
     int rc = PIC_OK;
     for (int k = 0; k < 5; ++k)
       if (cudaMemcpyAsync(a[k].data(), d[k], bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
@@ -761,7 +912,9 @@ int pic_export_particles(pic_handle* h, int sim, double* r, double* z, double* v
 }
 
 int pic_set_efield(pic_handle* h, int sim, const double* er, const double* ez) {
-  if (!h || sim != 0 || !er || !ez) return PIC_EINVAL;
+  if (!h || sim < 0 || sim >= h->nsim || !er || !ez) return PIC_EINVAL;
+  const size_t eo = (size_t)sim * h->nnodes * (h->prec == 32 ? sizeof(float2) : sizeof(double2));
+  void* efield = (char*)h->efield + eo;
   const size_t bytes = (size_t)h->nnodes * sizeof(double);
   double* d0 = (double*)h_alloc(bytes, h);
   double* d1 = (double*)h_alloc(bytes, h);
@@ -771,8 +924,8 @@ int pic_set_efield(pic_handle* h, int sim, const double* er, const double* ez) {
       cudaMemcpyAsync(d1, ez, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     rc = PIC_ECUDA;
   if (!rc) {
-    if (h->prec == 32) launch_efield_set<float>(d0, d1, h->efield, h->nnodes, h->stream);
-    else launch_efield_set<double>(d0, d1, h->efield, h->nnodes, h->stream);
+    if (h->prec == 32) launch_efield_set<float>(d0, d1, efield, h->nnodes, h->stream);
+    else launch_efield_set<double>(d0, d1, efield, h->nnodes, h->stream);
   }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = PIC_ECUDA;
   for (double* p : {d0, d1}) {
@@ -784,14 +937,16 @@ int pic_set_efield(pic_handle* h, int sim, const double* er, const double* ez) {
 }
 
 int pic_get_grid(pic_handle* h, int sim, int which, double* out) {
-  if (!h || sim != 0 || !out) return PIC_EINVAL;
+  if (!h || sim < 0 || sim >= h->nsim || !out) return PIC_EINVAL;
   const size_t bytes = (size_t)h->nnodes * sizeof(double);
+  const size_t eo = (size_t)sim * h->nnodes * (h->prec == 32 ? sizeof(float2) : sizeof(double2));
+  const void* efield = (const char*)h->efield + eo;
   if (which == PIC_GRID_RHS) {
-    const int rr = read_rho(h, out);
+    const int rr = read_rho(h, sim, out);
     return rr ? rr : check_sticky(h);
   }
   if (which == PIC_GRID_PHI) {
-    launch_phi_out(h->T, h->phi, h->stream);
+    launch_phi_out(h->T, h->phi, h->stream, sim);
     CK(cudaMemcpyAsync(out, h->phi, bytes, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return check_sticky(h);
@@ -799,8 +954,8 @@ int pic_get_grid(pic_handle* h, int sim, int which, double* out) {
   if (which != PIC_GRID_ER && which != PIC_GRID_EZ) return PIC_EINVAL;
   double* d = (double*)h_alloc(bytes, h);
   if (!d) return PIC_ENOMEM;
-  if (h->prec == 32) launch_efield_get<float>(h->efield, d, which == PIC_GRID_ER ? 0 : 1, h->nnodes, h->stream);
-  else launch_efield_get<double>(h->efield, d, which == PIC_GRID_ER ? 0 : 1, h->nnodes, h->stream);
+  if (h->prec == 32) launch_efield_get<float>(efield, d, which == PIC_GRID_ER ? 0 : 1, h->nnodes, h->stream);
+  else launch_efield_get<double>(efield, d, which == PIC_GRID_ER ? 0 : 1, h->nnodes, h->stream);
   int rc = PIC_OK;
   if (cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -818,6 +973,7 @@ int pic_solve_field(pic_handle* h, const double* b, double* phi, double* relres)
   // the tables are shared; the work arrays are this call's own, so the
   // simulation's field is untouched
   FieldTables T = h->T;
+  T.nsim = 1;   // the first simulation's wall potentials
   double* d_b = (double*)h_alloc(nn * sizeof(double), h);
   double* d_phi = (double*)h_alloc(nn * sizeof(double), h);
   void* d_e = h_alloc(nn * sizeof(double2), h);
@@ -838,7 +994,7 @@ int pic_solve_field(pic_handle* h, const double* b, double* phi, double* relres)
               cudaMemsetAsync(T.phir, 0, nn * sizeof(float2), h->stream) != cudaSuccess))
     rc = PIC_ECUDA;
   if (!rc) {
-    launch_field_solve<double>(T, d_b, nullptr, 0.0, nullptr, d_e, d_st, h->stream);
+    launch_field_solve<double>(T, d_b, nullptr, 0.0, nullptr, nullptr, d_e, d_st, h->stream);
     launch_phi_out(T, d_phi, h->stream);
     if (cudaMemcpyAsync(phi, d_phi, nn * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
         cudaMemcpyAsync(&s0, d_st, sizeof(s0), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
@@ -864,7 +1020,7 @@ int pic_solve_field(pic_handle* h, const double* b, double* phi, double* relres)
 static const char kMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '2'};
 
 int pic_checkpoint(pic_handle* h, const char* path) {
-  if (!h || !path) return PIC_EINVAL;
+  if (!h || !path || h->nsim != 1) return PIC_EINVAL;
   DevState s;
   CK(cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -874,9 +1030,9 @@ int pic_checkpoint(pic_handle* h, const char* path) {
   const long long ns = s.n_slots;
   int64_t hdr[6] = {h->prec, h->cfg.nr, h->cfg.nz, h->capacity, (int64_t)h->cfg.seed, h->step};
   bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
-            std::fwrite(&h->ke_initial, sizeof(double), 1, f) == 1 &&
-            std::fwrite(h->last_abs, sizeof(double), 4, f) == 4 &&
-            std::fwrite(&h->last_diag_step, sizeof(long long), 1, f) == 1 &&
+            std::fwrite(&h->sims[0].ke_initial, sizeof(double), 1, f) == 1 &&
+            std::fwrite(h->sims[0].last_abs, sizeof(double), 4, f) == 4 &&
+            std::fwrite(&h->sims[0].last_diag_step, sizeof(long long), 1, f) == 1 &&
             std::fwrite(&s, sizeof(s), 1, f) == 1;
   std::vector<char> buf;
   void* arrays[7];
@@ -911,7 +1067,7 @@ int pic_checkpoint(pic_handle* h, const char* path) {
 }
 
 int pic_restore(pic_handle* h, const char* path) {
-  if (!h || !path) return PIC_EINVAL;
+  if (!h || !path || h->nsim != 1) return PIC_EINVAL;
   FILE* f = std::fopen(path, "rb");
   if (!f) return PIC_EINVAL;
   char magic[8];
@@ -963,9 +1119,9 @@ int pic_restore(pic_handle* h, const char* path) {
   h->last_buf = 0;
   h->dep_buf = h->cfg.fixed_efield ? 0 : 1;
   h->step = hdr[5];
-  h->ke_initial = ke0;
-  std::copy(labs, labs + 4, h->last_abs);
-  h->last_diag_step = lds;
+  h->sims[0].ke_initial = ke0;
+  std::copy(labs, labs + 4, h->sims[0].last_abs);
+  h->sims[0].last_diag_step = lds;
   h->sticky = s.err;
   return PIC_OK;
 }

@@ -77,36 +77,15 @@ float2 df_from(double x) {
 
 // ---------------------------------------------------------------- tables
 
-void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& H) {
-  const int nr = cfg.nr, nz = cfg.nz, M = nz, NI = nr - 1, M1 = M + 1;
-  T.nr = nr; T.nz = nz; T.M = M; T.NI = NI;
-  T.hr = (cfg.r_out - cfg.r_in) / nr;
-  T.hz = (cfg.z_max - cfg.z_min) / nz;
-  T.rtol = cfg.poisson_rtol;
-  T.maxit = cfg.poisson_maxit > 0 ? cfg.poisson_maxit : 4;
-  int l2 = 0;
-  while ((1 << l2) < 2 * M) ++l2;
-  // FFT path for M a power of two whose 2M-point complex line and its M
-  // twiddles fit the default 48 KB of dynamic shared memory; otherwise the
-  // direct transform
-  T.log2N = ((1 << l2) == 2 * M && 3 * M * (int)sizeof(float2) <= 48 * 1024) ? l2 : -1;
-  const double hr = T.hr, hz = T.hz;
-
-  double *kd = H.kd, *ko = H.ko, *md = H.md, *mo = H.mo;
-  for (int i = 0; i <= nr; ++i) kd[i] = ko[i] = md[i] = mo[i] = 0.0;
-  for (int e = 0; e < nr; ++e) {
-    const double r0 = cfg.r_in + e * hr, r1 = cfg.r_in + (e + 1) * hr;
-    const double k = (r0 + r1) / (2.0 * hr);
-    kd[e] += k; kd[e + 1] += k; ko[e] = -k;
-    md[e] += hr / 12.0 * (3.0 * r0 + r1);
-    md[e + 1] += hr / 12.0 * (r0 + 3.0 * r1);
-    mo[e] = hr / 12.0 * (r0 + r1);
-  }
-
-  // vacuum solution: K_r restricted to the interior lines with the wall
-  // potentials moved to the right-hand side (M_r and K_z drop out for a
-  // z-independent field); its radial node field by the same differences as
-  // the particle field (central, one-sided second order on the walls)
+// vacuum solution of the wall potentials of cfg (kd, ko: K_r) and its
+// radial node field, into H.vac, H.evac64, H.evac32
+static void vacuum_host(const pic_config& cfg, const HostTables& H, double hr) {
+  const int nr = cfg.nr, NI = nr - 1;
+  const double *kd = H.kd, *ko = H.ko;
+  // K_r restricted to the interior lines with the wall potentials moved to
+  // the right-hand side (M_r and K_z drop out for a z-independent field);
+  // its radial node field by the same differences as the particle field
+  // (central, one-sided second order on the walls)
   double* vac = H.vac;
   vac[0] = cfg.v_inner;
   vac[nr] = cfg.v_outer;
@@ -133,6 +112,35 @@ void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& 
     H.evac64[i] = -d;
     H.evac32[i] = (float)(-d);
   }
+}
+
+void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& H) {
+  const int nr = cfg.nr, nz = cfg.nz, M = nz, NI = nr - 1, M1 = M + 1;
+  T.nr = nr; T.nz = nz; T.M = M; T.NI = NI;
+  T.hr = (cfg.r_out - cfg.r_in) / nr;
+  T.hz = (cfg.z_max - cfg.z_min) / nz;
+  T.rtol = cfg.poisson_rtol;
+  T.maxit = cfg.poisson_maxit > 0 ? cfg.poisson_maxit : 4;
+  int l2 = 0;
+  while ((1 << l2) < 2 * M) ++l2;
+  // FFT path for M a power of two whose 2M-point complex line and its M
+  // twiddles fit the default 48 KB of dynamic shared memory; otherwise the
+  // direct transform
+  T.log2N = ((1 << l2) == 2 * M && 3 * M * (int)sizeof(float2) <= 48 * 1024) ? l2 : -1;
+  const double hr = T.hr, hz = T.hz;
+
+  double *kd = H.kd, *ko = H.ko, *md = H.md, *mo = H.mo;
+  for (int i = 0; i <= nr; ++i) kd[i] = ko[i] = md[i] = mo[i] = 0.0;
+  for (int e = 0; e < nr; ++e) {
+    const double r0 = cfg.r_in + e * hr, r1 = cfg.r_in + (e + 1) * hr;
+    const double k = (r0 + r1) / (2.0 * hr);
+    kd[e] += k; kd[e + 1] += k; ko[e] = -k;
+    md[e] += hr / 12.0 * (3.0 * r0 + r1);
+    md[e + 1] += hr / 12.0 * (r0 + 3.0 * r1);
+    mo[e] = hr / 12.0 * (r0 + r1);
+  }
+
+  vacuum_host(cfg, H, hr);
 
   // per-mode Thomas factors of g_k K_r + f_k M_r on the interior lines
   for (int k = 0; k <= M; ++k) {
@@ -173,8 +181,7 @@ void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& 
   T.kzd_end = df_from(1.0 / hz);
   T.kzd_in = df_from(2.0 / hz);
   T.kzo = df_from(-1.0 / hz);
-  T.lift_in = (float)(-ko[0] * cfg.v_inner);
-  T.lift_out = (float)(-ko[nr - 1] * cfg.v_outer);
+  T.nsim = 1;
 }
 
 int field_tables_upload(FieldTables& T, const HostTables& H, cudaStream_t stream) {
@@ -193,16 +200,19 @@ int field_tables_upload(FieldTables& T, const HostTables& H, cudaStream_t stream
        cp(T.evac32, H.evac32, rad * sizeof(float)) && cp(T.kr_d, H.kd2, rad * sizeof(float2)) &&
        cp(T.kr_o, H.ko2, rad * sizeof(float2)) && cp(T.mr_d, H.md2, rad * sizeof(float2)) &&
        cp(T.mr_o, H.mo2, rad * sizeof(float2));
-  ok = ok && cudaMemsetAsync(T.phir, 0, nn * sizeof(float2), stream) == cudaSuccess &&
-       cudaMemsetAsync(T.b2, 0, nn * sizeof(float2), stream) == cudaSuccess &&
-       cudaMemsetAsync(T.res, 0, nn * sizeof(float), stream) == cudaSuccess;
+  const size_t ns = (size_t)T.nsim;
+  ok = ok && cudaMemsetAsync(T.phir, 0, ns * nn * sizeof(float2), stream) == cudaSuccess &&
+       cudaMemsetAsync(T.b2, 0, ns * nn * sizeof(float2), stream) == cudaSuccess &&
+       cudaMemsetAsync(T.res, 0, ns * nn * sizeof(float), stream) == cudaSuccess;
   return ok ? PIC_OK : PIC_ECUDA;
 }
 
-int field_tables_build(const pic_config& cfg, FieldTables& T,
+int field_tables_build(const pic_config* cfgs, int nsim, FieldTables& T,
                        void* (*dev_alloc)(size_t, void*), void* ctx,
                        cudaStream_t stream) {
+  const pic_config& cfg = cfgs[0];
   const int nr = cfg.nr, M = cfg.nz, NI = nr - 1, M1 = M + 1;
+  const size_t S = (size_t)nsim;
   const size_t nn = (size_t)(nr + 1) * M1, tri = (size_t)NI * M1;
   std::vector<double> dbl(9 * (size_t)(nr + 1));
   std::vector<float> flt(3 * tri + M1 + 4 * (size_t)M + (nr + 1));
@@ -215,6 +225,7 @@ int field_tables_build(const pic_config& cfg, FieldTables& T,
   H.tw = H.scale + M1; H.cos = H.tw + 2 * (size_t)M; H.evac32 = H.cos + 2 * (size_t)M;
   H.kd2 = f2.data(); H.ko2 = H.kd2 + nr + 1; H.md2 = H.ko2 + nr + 1; H.mo2 = H.md2 + nr + 1;
   field_tables_host(cfg, T, H);
+  T.nsim = nsim;
 
   auto al = [&](size_t bytes, void** dst) -> bool {
     *dst = dev_alloc(std::max<size_t>(bytes, 16), ctx);
@@ -227,18 +238,32 @@ int field_tables_build(const pic_config& cfg, FieldTables& T,
   ok = ok && al(M1 * sizeof(float), (void**)&T.scale32) &&
        al(tri * sizeof(float), (void**)&T.tri_a) && al(tri * sizeof(float), (void**)&T.tri_inv) &&
        al(tri * sizeof(float), (void**)&T.tri_cp) &&
-       al((nr + 1) * sizeof(double), (void**)&T.phi_vac) &&
-       al((nr + 1) * sizeof(double), (void**)&T.evac64) &&
-       al((nr + 1) * sizeof(float), (void**)&T.evac32) &&
+       al(S * (nr + 1) * sizeof(double), (void**)&T.phi_vac) &&
+       al(S * (nr + 1) * sizeof(double), (void**)&T.evac64) &&
+       al(S * (nr + 1) * sizeof(float), (void**)&T.evac32) &&
        al((nr + 1) * sizeof(float2), (void**)&T.kr_d) &&
        al((nr + 1) * sizeof(float2), (void**)&T.kr_o) &&
        al((nr + 1) * sizeof(float2), (void**)&T.mr_d) &&
        al((nr + 1) * sizeof(float2), (void**)&T.mr_o) &&
-       al(nn * sizeof(float2), (void**)&T.b2) && al(nn * sizeof(float2), (void**)&T.phir) &&
-       al(nn * sizeof(float), (void**)&T.res) && al(tri * sizeof(float), (void**)&T.bhat) &&
-       al(tri * sizeof(float), (void**)&T.phihat);
+       al(S * nn * sizeof(float2), (void**)&T.b2) && al(S * nn * sizeof(float2), (void**)&T.phir) &&
+       al(S * nn * sizeof(float), (void**)&T.res) && al(S * tri * sizeof(float), (void**)&T.bhat) &&
+       al(S * tri * sizeof(float), (void**)&T.phihat);
   if (!ok) return PIC_ENOMEM;
   int rc = field_tables_upload(T, H, stream);
+  // the vacuum solution of every further simulation (its own wall
+  // potentials; the geometry is shared)
+  const size_t rad = (size_t)(nr + 1);
+  for (int k = 1; k < nsim && rc == PIC_OK; ++k) {
+    if (cudaStreamSynchronize(stream) != cudaSuccess) { rc = PIC_ECUDA; break; }
+    vacuum_host(cfgs[k], H, T.hr);
+    if (cudaMemcpyAsync(T.phi_vac + k * rad, H.vac, rad * sizeof(double), cudaMemcpyHostToDevice,
+                        stream) != cudaSuccess ||
+        cudaMemcpyAsync(T.evac64 + k * rad, H.evac64, rad * sizeof(double),
+                        cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(T.evac32 + k * rad, H.evac32, rad * sizeof(float), cudaMemcpyHostToDevice,
+                        stream) != cudaSuccess)
+      rc = PIC_ECUDA;
+  }
   if (rc == PIC_OK && cudaStreamSynchronize(stream) != cudaSuccess) rc = PIC_ECUDA;
   return rc;
 }
@@ -252,13 +277,17 @@ int field_tables_build(const pic_config& cfg, FieldTables& T,
 template <bool FIX>
 __global__ void __launch_bounds__(256)
 k_prep(const double* __restrict__ rhs, const unsigned long long* __restrict__ cnt, float2 unit2,
-       double unit64, unsigned long long* clear, FieldTables T, DevState* st) {
+       const float2* __restrict__ units, double unit64, unsigned long long* clear, FieldTables T,
+       DevState* st) {
   const int M1 = T.M + 1, nr = T.nr;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int sim = blockIdx.z;
+  st += sim;
+  if (units) unit2 = units[sim];
   float nb = 0.f, nl = 0.f;
   if (i <= nr && j < M1) {
-    const size_t o = (size_t)i * M1 + j;
+    const size_t o = (size_t)sim * (nr + 1) * M1 + (size_t)i * M1 + j;
     float2 b;
     if (FIX) {
       const unsigned long long c = cnt[o];
@@ -274,10 +303,13 @@ k_prep(const double* __restrict__ rhs, const unsigned long long* __restrict__ cn
     if (i > 0 && i < nr) {
       T.b2[o] = b;
       T.res[o] = b.x;
+      // the wall potentials moved to the right-hand side: -K_r(1,0) V_in
+      // and -K_r(nr-1,nr) V_out times the row sum of M_z
       const float zsum = (j == 0 || j == T.M) ? 0.5f * (float)T.hz : (float)T.hz;
+      const double* vac = T.phi_vac + (size_t)sim * (nr + 1);
       float lift = 0.f;
-      if (i == 1) lift += T.lift_in * zsum;
-      if (i == nr - 1) lift += T.lift_out * zsum;
+      if (i == 1) lift -= T.kr_o[0].x * (float)vac[0] * zsum;
+      if (i == nr - 1) lift -= T.kr_o[nr - 1].x * (float)vac[nr] * zsum;
       nb = b.x * b.x;
       nl = (b.x + lift) * (b.x + lift);
     }
@@ -313,9 +345,12 @@ k_prep(const double* __restrict__ rhs, const unsigned long long* __restrict__ cn
 template <bool FWD>
 __global__ void __launch_bounds__(512)
 k_dct32(FieldTables T, const DevState* st, int sweep) {
-  if (sweep > 0 && *(volatile const int*)&st->solve_done) return;
+  const int sim = blockIdx.y;
+  if (sweep > 0 && *(volatile const int*)&st[sim].solve_done) return;
   extern __shared__ float2 sh[];   // N line values, then N/2 twiddles
   const int M = T.M, N = 2 * M, M1 = M + 1, NI = T.NI, log2N = T.log2N;
+  const size_t nn = (size_t)(T.nr + 1) * M1, tri = (size_t)NI * M1;
+  T.res += sim * nn; T.phir += sim * nn; T.bhat += sim * tri; T.phihat += sim * tri;
   float2* tw = sh + N;
   const int line0 = blockIdx.x * 2;
   const bool two = line0 + 1 < NI;
@@ -364,9 +399,12 @@ k_dct32(FieldTables T, const DevState* st, int sweep) {
 // direct O(M^2) DCT-I for M that is not a power of two; one line per block
 template <bool FWD>
 __global__ void k_dct32_direct(FieldTables T, const DevState* st, int sweep) {
-  if (sweep > 0 && *(volatile const int*)&st->solve_done) return;
+  const int sim = blockIdx.y;
+  if (sweep > 0 && *(volatile const int*)&st[sim].solve_done) return;
   extern __shared__ float xs[];
   const int M = T.M, M1 = M + 1, line = blockIdx.x;
+  const size_t nn = (size_t)(T.nr + 1) * M1, tri = (size_t)T.NI * M1;
+  T.res += sim * nn; T.phir += sim * nn; T.bhat += sim * tri; T.phihat += sim * tri;
   const float* x = FWD ? T.res + (size_t)(line + 1) * M1 : T.phihat + (size_t)line * M1;
   for (int j = threadIdx.x; j <= M; j += blockDim.x) xs[j] = x[j];
   __syncthreads();
@@ -400,9 +438,12 @@ constexpr int kTriModes = 32;
 constexpr int kTriThreads = 256;
 __global__ void __launch_bounds__(kTriThreads) k_tridiag32(FieldTables T, const DevState* st,
                                                            int sweep) {
-  if (sweep > 0 && *(volatile const int*)&st->solve_done) return;
+  const int sim = blockIdx.y;
+  if (sweep > 0 && *(volatile const int*)&st[sim].solve_done) return;
   extern __shared__ float sm[];
   const int M1 = T.M + 1, NI = T.NI;
+  const size_t tri = (size_t)NI * M1;
+  T.bhat += sim * tri; T.phihat += sim * tri;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = blockIdx.x * kTriModes + lane;
   const bool in = k < M1;
@@ -456,8 +497,13 @@ __device__ __forceinline__ float df_diff(float2 a, float2 b) {   // a - b to flo
 template <typename Real>
 __global__ void __launch_bounds__(256)
 k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep, int last) {
+  const int sim = blockIdx.z;
+  st += sim;
   if (sweep > 0 && *(volatile const int*)&st->solve_done) return;
   const int nr = T.nr, M = T.M, M1 = M + 1;
+  const size_t nn = (size_t)(nr + 1) * M1;
+  T.phir += sim * nn; T.res += sim * nn; T.b2 += sim * nn; E += sim * nn;
+  T.evac32 += sim * (nr + 1); T.evac64 += sim * (nr + 1);
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   float rn = 0.f;
@@ -559,50 +605,54 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
 }
 
 // phi = phi_vac + phi_rho (FP64), on demand
-__global__ void k_phi_out(FieldTables T, double* phi) {
+__global__ void k_phi_out(FieldTables T, double* phi, int sim) {
   const int M1 = T.M + 1;
   const int n = (T.nr + 1) * M1;
+  const float2* ph = T.phir + (size_t)sim * n;
+  const double* vac = T.phi_vac + (size_t)sim * (T.nr + 1);
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
-    const float2 p = T.phir[o];
-    phi[o] = T.phi_vac[o / M1] + ((double)p.x + (double)p.y);
+    const float2 p = ph[o];
+    phi[o] = vac[o / M1] + ((double)p.x + (double)p.y);
   }
 }
 
-void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream) {
+void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream, int sim) {
   const int n = (T.nr + 1) * (T.M + 1);
-  k_phi_out<<<(n + 255) / 256, 256, 0, stream>>>(T, phi);
+  k_phi_out<<<(n + 255) / 256, 256, 0, stream>>>(T, phi, sim);
 }
 
 int field_solve_kernels(const FieldTables& T) { return 1 + 4 * T.maxit; }
 
 template <typename Real>
 void launch_field_solve(const FieldTables& T, const double* rhs, const unsigned long long* cnt,
-                        double cnt_unit, unsigned long long* cnt_clear, void* efield,
-                        DevState* st, cudaStream_t stream) {
-  const int M1 = T.M + 1;
-  dim3 blk(32, 8), grd((M1 + 31) / 32, (T.nr + 1 + 7) / 8);
+                        double cnt_unit, const float2* cnt_units, unsigned long long* cnt_clear,
+                        void* efield, DevState* st, cudaStream_t stream) {
+  const int M1 = T.M + 1, S = T.nsim;
+  dim3 blk(32, 8), grd((M1 + 31) / 32, (T.nr + 1 + 7) / 8, S);
   const double s0 = 1.0 / (2.0 * kPi * kEps0);
   if (tridiag_smem(T) > 48 * 1024)
     cudaFuncSetAttribute(k_tridiag32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tridiag_smem(T));
-  if (cnt) k_prep<true><<<grd, blk, 0, stream>>>(nullptr, cnt, df_from(cnt_unit * s0), 0.0,
-                                                  cnt_clear, T, st);
-  else k_prep<false><<<grd, blk, 0, stream>>>(rhs, nullptr, make_float2(0.f, 0.f), s0,
+  if (cnt) k_prep<true><<<grd, blk, 0, stream>>>(nullptr, cnt, df_from(cnt_unit * s0), cnt_units,
+                                                  0.0, cnt_clear, T, st);
+  else k_prep<false><<<grd, blk, 0, stream>>>(rhs, nullptr, make_float2(0.f, 0.f), nullptr, s0,
                                                cnt_clear, T, st);
   for (int s = 0; s < T.maxit; ++s) {
     if (T.log2N > 0) {
       const int N = 2 * T.M;
       const int threads = std::min(512, std::max(32, N / 2));
       const size_t smem = (size_t)(N + N / 2) * sizeof(float2);
-      const int blocks = (T.NI + 1) / 2;
+      const dim3 blocks((T.NI + 1) / 2, S);
       k_dct32<true><<<blocks, threads, smem, stream>>>(T, st, s);
-      k_tridiag32<<<(M1 + kTriModes - 1) / kTriModes, kTriThreads, tridiag_smem(T), stream>>>(T, st, s);
+      k_tridiag32<<<dim3((M1 + kTriModes - 1) / kTriModes, S), kTriThreads, tridiag_smem(T),
+                    stream>>>(T, st, s);
       k_dct32<false><<<blocks, threads, smem, stream>>>(T, st, s);
     } else {
       const size_t smem = (size_t)M1 * sizeof(float);
-      k_dct32_direct<true><<<T.NI, 256, smem, stream>>>(T, st, s);
-      k_tridiag32<<<(M1 + kTriModes - 1) / kTriModes, kTriThreads, tridiag_smem(T), stream>>>(T, st, s);
-      k_dct32_direct<false><<<T.NI, 256, smem, stream>>>(T, st, s);
+      k_dct32_direct<true><<<dim3(T.NI, S), 256, smem, stream>>>(T, st, s);
+      k_tridiag32<<<dim3((M1 + kTriModes - 1) / kTriModes, S), kTriThreads, tridiag_smem(T),
+                    stream>>>(T, st, s);
+      k_dct32_direct<false><<<dim3(T.NI, S), 256, smem, stream>>>(T, st, s);
     }
     k_residual<Real><<<grd, blk, 0, stream>>>(T, (typename Vec2<Real>::type*)efield, st, s,
                                              s == T.maxit - 1);
@@ -610,10 +660,10 @@ void launch_field_solve(const FieldTables& T, const double* rhs, const unsigned 
 }
 
 template void launch_field_solve<float>(const FieldTables&, const double*,
-                                        const unsigned long long*, double, unsigned long long*,
-                                        void*, DevState*, cudaStream_t);
+                                        const unsigned long long*, double, const float2*,
+                                        unsigned long long*, void*, DevState*, cudaStream_t);
 template void launch_field_solve<double>(const FieldTables&, const double*,
-                                         const unsigned long long*, double, unsigned long long*,
-                                         void*, DevState*, cudaStream_t);
+                                         const unsigned long long*, double, const float2*,
+                                         unsigned long long*, void*, DevState*, cudaStream_t);
 
 }  // namespace pic

@@ -132,7 +132,7 @@ extern "C" int pic_solve_field_static(const pic_config* cfg, const double* b, do
   if (field_tables_upload(T, H, stream) != PIC_OK ||
       cudaMemsetAsync(st, 0, sizeof(DevState), stream) != cudaSuccess)
     return PIC_ECUDA;
-  launch_field_solve<double>(T, b, nullptr, 0.0, nullptr, E, st, stream);
+  launch_field_solve<double>(T, b, nullptr, 0.0, nullptr, nullptr, E, st, stream);
   launch_phi_out(T, phi, stream);
   if (cudaGetLastError() != cudaSuccess) return PIC_ECUDA;
   if (!relres) return PIC_OK;

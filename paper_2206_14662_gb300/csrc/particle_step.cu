@@ -151,11 +151,12 @@ struct Part {
 // the move.  The draw-0 Philox block is recomputed here, so the common path
 // carries only the candidate flag.
 template <typename Real>
-__device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, const Soa<Real>& s,
+__device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, unsigned uid_hi,
+                                        const Soa<Real>& s,
                                      const DepGrid& g, DevState* st, unsigned* spawn_parent,
                                      int n_slots, unsigned step, const PushParams<Real>& P,
                                      BlockTally& bt) {
-  const uint4 xr = philox4x32_10_rk(make_uint4(uid, 0u, step, 0u), P.rk0, P.rk1);
+  const uint4 xr = philox4x32_10_rk(make_uint4(uid, uid_hi, step, 0u), P.rk0, P.rk1);
   atomicAdd(&bt.v[kNCandidate], 1.0);
   Real ur = q.vr, ut = q.vt, uz = q.vz;
   const Real v2 = ur * ur + ut * ut + uz * uz;
@@ -187,7 +188,7 @@ __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, const Soa<R
     atomicAdd(&bt.v[kNElastic], 1.0);
     return;
   }
-  const uint4 x2 = philox4x32_10_rk(make_uint4(uid, 0u, step, 1u), P.rk0, P.rk1);
+  const uint4 x2 = philox4x32_10_rk(make_uint4(uid, uid_hi, step, 1u), P.rk0, P.rk1);
   const Real E_rem = Ek - P.e_th;
   const Real E2 = P.opal_b * d_tan(u01<Real>(x2.x) * d_atan(E_rem / (2 * P.opal_b)));
   const Real E1 = E_rem - E2;
@@ -224,7 +225,7 @@ __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, const Soa<R
 // depend on the particle order the sort leaves).
 template <typename Real>
 __device__ __forceinline__ Dep<Real> advance(
-    Part<Real>& q, unsigned uid, const typename Vec2<Real>::type* __restrict__ E,
+    Part<Real>& q, unsigned uid, unsigned uid_hi, const typename Vec2<Real>::type* __restrict__ E,
     const Soa<Real>& s, const DepGrid& g, DevState* st, unsigned* spawn_parent, int n_slots,
     unsigned step, const PushParams<Real>& P, BlockTally& bt, Real& work) {
   using V2 = typename Vec2<Real>::type;
@@ -317,8 +318,9 @@ __device__ __forceinline__ Dep<Real> advance(
   q.vz = vnz;
 
   // null-collision candidate test: the integer form of u0 < P_null
-  const uint4 xr = philox4x32_10_rk(make_uint4(uid, 0u, step, 0u), P.rk0, P.rk1);
-  if ((xr.x >> 8) < P.thr_null) collide<Real>(q, uid, s, g, st, spawn_parent, n_slots, step, P, bt);
+  const uint4 xr = philox4x32_10_rk(make_uint4(uid, uid_hi, step, 0u), P.rk0, P.rk1);
+  if ((xr.x >> 8) < P.thr_null)
+    collide<Real>(q, uid, uid_hi, s, g, st, spawn_parent, n_slots, step, P, bt);
   dep.ir = ir1; dep.iz = iz1; dep.fr = fr1; dep.fz = fz1;
   return dep;
 }
@@ -560,7 +562,7 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, De
       live[k] = q[k].cell >= 0;
       if (live[k]) {
         ++pushed;
-        dep[k] = advance<Real>(q[k], uid[k], E, s, g, st, spawn_parent, n_slots, step, P, bt,
+        dep[k] = advance<Real>(q[k], uid[k], 0u, E, s, g, st, spawn_parent, n_slots, step, P, bt,
                                work);
       }
     }
@@ -580,13 +582,135 @@ void launch_particle_step(const Soa<Real>& s, const void* efield, double* rhs,
       s, (const typename Vec2<Real>::type*)efield, g, st, spawn_parent, P);
 }
 
+// ----------------------------------------------------------------- batch
+
+// The simulation a block is working on: its parameters and its views of
+// the store, the grids, the state and the spawn records.  Kept in shared
+// memory (the fields are read at a few points per chunk), so the per-
+// particle code keeps the register budget of the single-run kernel.
+template <typename Real>
+struct SimView {
+  PushParams<Real> P;
+  Soa<Real> s;
+  const typename Vec2<Real>::type* E;
+  DepGrid g;
+  DevState* st;
+  unsigned* spawn;
+  int n_slots;
+  unsigned step;
+};
+
+// One persistent launch over the chunks of every simulation of a batch
+// (chunk table: pic_internal.cuh).  A block takes global chunks
+// blockIdx.x, blockIdx.x + gridDim.x, ...; chunks of one simulation are
+// consecutive, so a block changes simulation rarely; when it does, it
+// flushes the tallies of the previous one and loads the new view.  The
+// per-particle work is that of k_particle_step.
+template <typename Real>
+__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 2)
+k_particle_step_batch(Soa<Real> s_all, const typename Vec2<Real>::type* __restrict__ E_all,
+                      double* rhs_all, unsigned long long* cnt_all, DevState* st_all,
+                      unsigned* spawn_all, long long spawn_stride,
+                      const PushParams<Real>* __restrict__ params, int nsim, int nnodes) {
+  using TT = typename TileT<Real>::type;
+  constexpr int kCap = TileT<Real>::cap;
+  __shared__ __align__(16) TT tile[kCap];
+  __shared__ int bbox[2][4];
+  __shared__ BlockTally bt;
+  __shared__ int first[kMaxSims + 1];
+  __shared__ long long nslots[kMaxSims];
+  __shared__ __align__(16) SimView<Real> V;
+
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < kTallyCount) bt.v[tid] = 0.0;
+  if (tid < 8) bbox[tid >> 2][tid & 3] = (tid & 1) ? INT_MIN : INT_MAX;
+  chunk_table(st_all, nsim, kChunk, first, nslots);   // ends with a barrier
+  const int total = first[nsim];
+  Real work = 0;
+  int pushed = 0;
+  int buf = 0;
+  int cur = -1;
+
+  for (int c = blockIdx.x; c < total; c += gridDim.x) {
+    const int sim = chunk_owner(first, nsim, c);
+    if (sim != cur) {
+      if (cur >= 0) {
+        flush_tallies<Real>(bt, work, pushed, V.st, V.P, tid, lane);
+        work = 0;
+        pushed = 0;
+        __syncthreads();   // V and bt are read by the flush
+      }
+      constexpr int kWords = sizeof(PushParams<Real>) / sizeof(unsigned);
+      static_assert(sizeof(PushParams<Real>) % sizeof(unsigned) == 0, "word copy");
+      const unsigned* src = reinterpret_cast<const unsigned*>(params + sim);
+      for (int w = tid; w < kWords; w += kThreads) reinterpret_cast<unsigned*>(&V.P)[w] = src[w];
+      if (tid < kTallyCount) bt.v[tid] = 0.0;
+      if (tid == 0) {
+        const long long base = params[sim].base;
+        const size_t go = (size_t)sim * nnodes;
+        V.s = soa_offset(s_all, base);
+        V.E = E_all + go;
+        V.g = DepGrid{rhs_all ? rhs_all + go : nullptr, cnt_all ? cnt_all + go : nullptr,
+                      params[sim].nz + 1, params[sim].qw};
+        V.st = st_all + sim;
+        V.spawn = spawn_all + (size_t)sim * spawn_stride;
+        V.n_slots = (int)nslots[sim];
+        V.step = *(volatile unsigned*)&st_all[sim].step;
+      }
+      __syncthreads();
+      cur = sim;
+    }
+    const int n_slots = V.n_slots;
+    const int p0 = (c - first[sim]) * kChunk + kPPT * tid;
+    Part<Real> q[kPPT];
+    unsigned uid[kPPT];
+    const bool vec = load_group<Real>(V.s, p0, n_slots, q, uid);
+    Dep<Real> dep[kPPT];
+    bool live[kPPT];
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+      dep[k].ir = -1;
+      live[k] = q[k].cell >= 0;
+      if (live[k]) {
+        ++pushed;
+        dep[k] = advance<Real>(q[k], uid[k], V.P.uid_hi, V.E, V.s, V.g, V.st, V.spawn, n_slots,
+                               V.step, V.P, bt, work);
+      }
+    }
+    store_group<Real>(V.s, p0, n_slots, q, live, vec);
+    deposit_chunk<Real, kCap>(dep, tile, bbox, buf, V.g, tid, lane);
+    buf ^= 1;
+  }
+  if (cur >= 0) flush_tallies<Real>(bt, work, pushed, V.st, V.P, tid, lane);
+}
+
+template <typename Real>
+void launch_particle_step_batch(const Soa<Real>& s, const void* efield, double* rhs,
+                                unsigned long long* cnt, DevState* st, unsigned* spawn_parent,
+                                long long spawn_stride, const PushParams<Real>* params, int nsim,
+                                int nnodes, int grid, cudaStream_t stream) {
+  k_particle_step_batch<Real><<<grid, kThreads, 0, stream>>>(
+      s, (const typename Vec2<Real>::type*)efield, rhs, cnt, st, spawn_parent, spawn_stride,
+      params, nsim, nnodes);
+}
+
 // ------------------------------------------------------------ child uids
 
 // Children of this step get uid_next + k, k the rank of the parent's uid
 // among this step's ionising parents; then the step counter advances.
+// In a batch (seg not null) block k serves simulation k.
 __global__ void k_spawn_finalize(DevState* st, unsigned* uid,
                                  const unsigned* __restrict__ parent,
-                                 long long spawn_cap, long long capacity) {
+                                 long long spawn_cap, long long capacity,
+                                 const SegInfo* __restrict__ seg, long long spawn_stride) {
+  if (seg) {
+    const int sim = blockIdx.x;
+    st += sim;
+    uid += seg[sim].base;
+    parent += (size_t)sim * spawn_stride;
+    spawn_cap = seg[sim].spawn_cap;
+    capacity = seg[sim].capacity;
+  }
   const long long ns_raw = st->n_spawn;
   const long long base = st->n_slots;
   long long ns = ns_raw < spawn_cap ? ns_raw : spawn_cap;
@@ -613,7 +737,13 @@ __global__ void k_spawn_finalize(DevState* st, unsigned* uid,
 void launch_spawn_finalize(DevState* st, unsigned* uid, const unsigned* parent,
                            long long spawn_cap, long long capacity,
                            cudaStream_t stream) {
-  k_spawn_finalize<<<1, 1024, 0, stream>>>(st, uid, parent, spawn_cap, capacity);
+  k_spawn_finalize<<<1, 1024, 0, stream>>>(st, uid, parent, spawn_cap, capacity, nullptr, 0);
+}
+
+void launch_spawn_finalize_batch(DevState* st, unsigned* uid, const unsigned* parent,
+                                 long long spawn_stride, const SegInfo* seg, int nsim,
+                                 cudaStream_t stream) {
+  k_spawn_finalize<<<nsim, 1024, 0, stream>>>(st, uid, parent, 0, 0, seg, spawn_stride);
 }
 
 // ------------------------------------------------------------------ load
@@ -777,6 +907,10 @@ void launch_efield_get(const void* efield, double* out, int component,
   template void launch_particle_step<R>(const Soa<R>&, const void*, double*,             \
                                         unsigned long long*, DevState*, unsigned*,      \
                                         const PushParams<R>&, int, cudaStream_t);       \
+  template void launch_particle_step_batch<R>(const Soa<R>&, const void*, double*,       \
+                                              unsigned long long*, DevState*, unsigned*, \
+                                              long long, const PushParams<R>*, int, int, \
+                                              int, cudaStream_t);                       \
   template void launch_load<R>(const double*, const double*, const double*,             \
                                const double*, const double*, const uint64_t*,           \
                                long long, Soa<R>, const PushParams<R>&, DevState*,      \
@@ -799,8 +933,15 @@ PIC_INSTANTIATE(double)
 
 namespace pic {
 // resident blocks of the fused kernel per SM (sizes its persistent grid)
-int particle_step_blocks_per_sm(int precision) {
+int particle_step_blocks_per_sm(int precision, bool batch) {
   int b = 0;
+  if (batch) {
+    if (precision == 32)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step_batch<float>, kThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step_batch<double>, kThreads, 0);
+    return b;
+  }
   if (precision == 32)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step<float>, kThreads, 0);
   else

@@ -100,13 +100,82 @@ struct PushParams {
   double weight;              // electrons per macro-electron
   double qw;                  // q weight, C
   unsigned seed_lo, seed_hi;
+  unsigned uid_hi;            // Philox counter word 1: the high word of the
+                              // particles' 64-bit identity, the index of the
+                              // simulation in a batch (0 for a single run)
   unsigned rk0[10], rk1[10];  // Philox round keys of the seed
   long long capacity;         // particle slots
   long long spawn_cap;        // children per step
+  long long base;             // first slot of the simulation's segment of the
+                              // store (0 for a single run)
   // grid geometry in FP64 for converting absolute positions to and from
   // (cell, offset) at load and export
   double r_in_d, hr_d, z_min_d, hz_d;
 };
+
+// ------------------------------------------------------------- batches
+// A batch holds nsim simulations on one grid geometry.  Simulation k owns
+// the slots [base_k, base_k + capacity_k) of the store (base_k a multiple
+// of the fused kernel's chunk), its own DevState, node grids at offset
+// k * nodes and spawn records at offset k * spawn_stride.  Kernels that walk
+// the particles of all simulations in one launch number the chunks of all
+// segments consecutively: chunk c belongs to the simulation k with
+// first[k] <= c < first[k + 1], first[] the prefix sum of each segment's
+// ceil(n_slots / chunk).
+constexpr int kMaxSims = 256;
+
+struct SegInfo {
+  long long base, capacity, spawn_cap;
+};
+
+// first[0..nsim] of the chunk table, built by one warp from the
+// device-resident slot counts (call from every thread of the block; ends
+// with a block barrier)
+__device__ __forceinline__ void chunk_table(const DevState* st, int nsim, int chunk,
+                                            int* first, long long* nslots) {
+  if (threadIdx.x < 32) {
+    int carry = 0;
+    for (int k0 = 0; k0 < nsim; k0 += 32) {
+      const int k = k0 + (int)threadIdx.x;
+      long long n = 0;
+      if (k < nsim) n = *(volatile const long long*)&st[k].n_slots;
+      int c = (int)((n + chunk - 1) / chunk);
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)threadIdx.x >= o) incl += v;
+      }
+      if (k < nsim) {
+        first[k] = carry + incl - c;
+        nslots[k] = n;
+      }
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (threadIdx.x == 0) first[nsim] = carry;
+  }
+  __syncthreads();
+}
+
+// simulation owning global chunk c (first[k] <= c < first[k + 1]; segments
+// with no chunk are skipped)
+__device__ __forceinline__ int chunk_owner(const int* first, int nsim, int c) {
+  int lo = 0, hi = nsim - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename Real>
+__host__ __device__ inline Soa<Real> soa_offset(const Soa<Real>& s, long long base) {
+  Soa<Real> o;
+  o.cell = s.cell + base; o.offr = s.offr + base; o.offz = s.offz + base;
+  o.vr = s.vr + base; o.vt = s.vt + base; o.vz = s.vz + base; o.uid = s.uid + base;
+  return o;
+}
 
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -180,7 +249,12 @@ struct FieldTables {
   float2* kr_d; float2* kr_o; // r-weighted stiffness: diagonal, (i, i+1)  [hi, lo]
   float2* mr_d; float2* mr_o; // r-weighted mass                            [hi, lo]
   float2 mzd_end, mzd_in, mzo, kzd_end, kzd_in, kzo;  // z matrices [hi, lo]
-  float lift_in, lift_out;    // -K_r(1,0) V_in and -K_r(nr-1,nr) V_out per unit z-row sum
+  // A batch of nsim simulations shares the geometry and so every table
+  // above except the vacuum solution; phi_vac, evac32 and evac64 hold
+  // nsim blocks of nr + 1 entries, the arrays below nsim blocks of one grid
+  // (nodes, or NI x (M+1) for bhat / phihat).  The kernels take the
+  // simulation from their last grid dimension.
+  int nsim;
   float2* b2;                 // right-hand side / (2 pi eps0), per node [hi, lo]
   float2* phir;               // phi_rho per node [hi, lo]; zero on the walls
   float* res;                 // FP32 input of the next sweep per node
@@ -196,32 +270,36 @@ struct HostTables {
   float *ta, *tinv, *tcp, *scale, *tw, *cos, *evac32;
   float2 *kd2, *ko2, *md2, *mo2;
 };
-// fills T's scalar fields and the host tables (FP64 arithmetic, no
-// allocation)
+// fills T's scalar fields (nsim = 1) and the host tables (FP64
+// arithmetic, no allocation)
 void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& H);
-// copies the host tables into T's device arrays (which must exist) and
-// clears the work arrays; queued on `stream`
+// copies the host tables into T's device arrays (which must exist; the
+// vacuum tables into the block of simulation 0) and clears the work arrays
+// of all T.nsim simulations; queued on `stream`
 int field_tables_upload(FieldTables& T, const HostTables& H, cudaStream_t stream);
-// allocates T's device arrays with `dev_alloc`, builds and uploads the
-// tables.  Returns PIC_OK or an error code.
-int field_tables_build(const pic_config& cfg, FieldTables& T,
+// allocates T's device arrays for nsim simulations with `dev_alloc`,
+// builds and uploads the tables (the shared ones from cfgs[0], the vacuum
+// solution of each simulation from its own wall potentials).  Returns
+// PIC_OK or an error code.
+int field_tables_build(const pic_config* cfgs, int nsim, FieldTables& T,
                        void* (*dev_alloc)(size_t, void*), void* ctx,
                        cudaStream_t stream);
 float2 df_from(double x);   // double -> double-float (hi, lo)
 constexpr double kFixUnit = 4194303.0;   // fixed-point deposit counts per particle charge
 // Solve for the node charge given either as FP64 charges (rhs) or as
-// fixed-point counts (cnt, charge = count * cnt_unit); `cnt_clear`, when
-// not null, is zeroed on the way (the next step's deposit buffer).  Writes
-// the node field E = E_vac - grad phi_rho in the particle precision and
-// latches PIC_ENOCONV in st if ||r|| / ||b_lifted|| > rtol after the last
-// sweep.
+// fixed-point counts (cnt, charge = count * cnt_unit, or cnt_units[k] for
+// simulation k when cnt_units is a device array); `cnt_clear`, when not
+// null, is zeroed on the way (the next step's deposit buffer).  Writes the
+// node field E = E_vac - grad phi_rho in the particle precision and latches
+// PIC_ENOCONV in st if ||r|| / ||b_lifted|| > rtol after the last sweep.
+// All T.nsim simulations are solved (grids at k * nodes, st + k).
 template <typename Real>
 void launch_field_solve(const FieldTables& T, const double* rhs,
                         const unsigned long long* cnt, double cnt_unit,
-                        unsigned long long* cnt_clear, void* efield,
-                        DevState* st, cudaStream_t stream);
-// phi = phi_vac + phi_rho on all nodes (FP64), on demand
-void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream);
+                        const float2* cnt_units, unsigned long long* cnt_clear,
+                        void* efield, DevState* st, cudaStream_t stream);
+// phi = phi_vac + phi_rho of simulation `sim` on all nodes (FP64)
+void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream, int sim = 0);
 int field_solve_kernels(const FieldTables& T);   // launches per solve
 
 // kernels launched from capi.cu (defined in particle_step.cu / sort.cu)
@@ -235,6 +313,22 @@ void launch_particle_step(const Soa<Real>& s, const void* efield,
 void launch_spawn_finalize(DevState* st, unsigned* uid, const unsigned* parent,
                            long long spawn_cap, long long capacity,
                            cudaStream_t stream);
+// a batch: the fused kernel over all simulations' chunks (params: device
+// array of nsim PushParams, each with its segment base), child uids per
+// simulation, and the counting sort of every segment
+template <typename Real>
+void launch_particle_step_batch(const Soa<Real>& s, const void* efield, double* rhs,
+                                unsigned long long* cnt, DevState* st,
+                                unsigned* spawn_parent, long long spawn_stride,
+                                const PushParams<Real>* params, int nsim, int nnodes,
+                                int grid, cudaStream_t stream);
+void launch_spawn_finalize_batch(DevState* st, unsigned* uid, const unsigned* parent,
+                                 long long spawn_stride, const SegInfo* seg, int nsim,
+                                 cudaStream_t stream);
+template <typename Real>
+void launch_sort_batch(const Soa<Real>& src, const Soa<Real>& dst, DevState* st,
+                       const SegInfo* seg, int nsim, int* cell_count, int ncells,
+                       int nz, int grid, cudaStream_t stream);
 template <typename Real>
 void launch_deposit_only(const Soa<Real>& s, long long n, double* rhs,
                          unsigned long long* cnt, int nz, double qw,

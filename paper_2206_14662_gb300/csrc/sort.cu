@@ -44,29 +44,56 @@ __device__ __forceinline__ Run lane_run(int key, int lane) {
 // histogram: each thread takes four consecutive slots (one 16-byte load;
 // the store is allocated in whole chunks of 1024 slots, so the vector never
 // leaves it), runs are found among the lanes for each of the four
+constexpr int kSortThreads = 256;
+constexpr int kSortChunk = 4 * kSortThreads;
+
+__device__ __forceinline__ void hist_group(const int* __restrict__ cell, int n, int p0,
+                                           int* count, int nz, int lane) {
+  const int4 c = *reinterpret_cast<const int4*>(cell + p0);
+  const int cs[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int key = p0 + k < n ? cell_key(cs[k], nz) : -1;
+    const Run r = lane_run(key, lane);
+    if (key >= 0 && r.head) atomicAdd(count + key, r.len);
+  }
+}
+
 template <typename Real>
-__global__ void k_sort_hist(const int* __restrict__ cell, const DevState* st,
-                            int* count, int nz) {
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_hist(const int* __restrict__ cell, const DevState* st, int* count, int nz) {
   const int n = (int)st->n_slots;
   const int lane = threadIdx.x & 31;
-  for (int base = blockIdx.x * blockDim.x * 4; base < n; base += gridDim.x * blockDim.x * 4) {
-    const int p0 = base + 4 * threadIdx.x;
-    const int4 c = *reinterpret_cast<const int4*>(cell + p0);
-    const int cs[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int key = p0 + k < n ? cell_key(cs[k], nz) : -1;
-      const Run r = lane_run(key, lane);
-      if (key >= 0 && r.head) atomicAdd(count + key, r.len);
-    }
+  for (int base = blockIdx.x * kSortChunk; base < n; base += gridDim.x * kSortChunk)
+    hist_group(cell, n, base + 4 * threadIdx.x, count, nz, lane);
+}
+
+// a batch: the chunks of all segments in one launch; simulation k counts
+// into count + k * count_stride
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_hist_batch(const int* __restrict__ cell, const DevState* st, const SegInfo* seg, int nsim,
+                  int* count, int count_stride, int nz) {
+  __shared__ int first[kMaxSims + 1];
+  __shared__ long long nslots[kMaxSims];
+  chunk_table(st, nsim, kSortChunk, first, nslots);
+  const int lane = threadIdx.x & 31;
+  for (int c = blockIdx.x; c < first[nsim]; c += gridDim.x) {
+    const int sim = chunk_owner(first, nsim, c);
+    const int p0 = (c - first[sim]) * kSortChunk + 4 * threadIdx.x;
+    hist_group(cell + seg[sim].base, (int)nslots[sim], p0, count + (size_t)sim * count_stride,
+               nz, lane);
   }
 }
 
 // exclusive scan of count[0..n) in place, one block of 1024 threads, each
 // owning a contiguous stretch of whole int4 vectors (count is allocated in
 // whole multiples of 4096 entries, the tail beyond n zero); the total goes
-// to st->n_live
-__global__ void __launch_bounds__(1024) k_sort_scan(int* count, int n, DevState* st) {
+// to st->n_live.  Block k scans simulation k's counts (count + k *
+// count_stride, st + k).
+__global__ void __launch_bounds__(1024) k_sort_scan(int* count, int n, DevState* st,
+                                                    int count_stride) {
+  count += (size_t)blockIdx.x * count_stride;
+  st += blockIdx.x;
   __shared__ int part[1024];
   const int n4 = (n + 4095) / 4096 * 1024;     // int4 vectors, whole per thread
   const int per = n4 / 1024;                   // vectors per thread
@@ -101,51 +128,94 @@ __global__ void __launch_bounds__(1024) k_sort_scan(int* count, int n, DevState*
 // scatter: four consecutive slots per thread as in the histogram; each
 // live particle goes to its cell's next free slot in the other buffer set
 template <typename Real>
-__global__ void k_sort_scatter(Soa<Real> src, Soa<Real> dst, const DevState* st,
-                               int* cursor, int nz) {
-  const int n = (int)st->n_slots;
-  const int lane = threadIdx.x & 31;
-  for (int base = blockIdx.x * blockDim.x * 4; base < n; base += gridDim.x * blockDim.x * 4) {
-    const int p0 = base + 4 * threadIdx.x;
+__device__ __forceinline__ void scatter_group(const Soa<Real>& src, const Soa<Real>& dst, int n,
+                                              int p0, int* cursor, int nz, int lane) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int p = p0 + k;
-      const int c = p < n ? src.cell[p] : -1;
-      const int key = cell_key(c, nz);
-      const Run r = lane_run(key, lane);
-      int slot = 0;
-      if (key >= 0 && r.head) slot = atomicAdd(cursor + key, r.len);
-      slot = __shfl_sync(0xffffffffu, slot, r.first);
-      if (key >= 0) {
-        const int q = slot + (lane - r.first);
-        dst.cell[q] = c;
-        dst.offr[q] = src.offr[p];
-        dst.offz[q] = src.offz[p];
-        dst.vr[q] = src.vr[p];
-        dst.vt[q] = src.vt[p];
-        dst.vz[q] = src.vz[p];
-        dst.uid[q] = src.uid[p];
-      }
+  for (int k = 0; k < 4; ++k) {
+    const int p = p0 + k;
+    const int c = p < n ? src.cell[p] : -1;
+    const int key = cell_key(c, nz);
+    const Run r = lane_run(key, lane);
+    int slot = 0;
+    if (key >= 0 && r.head) slot = atomicAdd(cursor + key, r.len);
+    slot = __shfl_sync(0xffffffffu, slot, r.first);
+    if (key >= 0) {
+      const int q = slot + (lane - r.first);
+      dst.cell[q] = c;
+      dst.offr[q] = src.offr[p];
+      dst.offz[q] = src.offz[p];
+      dst.vr[q] = src.vr[p];
+      dst.vt[q] = src.vt[p];
+      dst.vz[q] = src.vz[p];
+      dst.uid[q] = src.uid[p];
     }
   }
 }
 
-__global__ void k_sort_commit(DevState* st) { st->n_slots = st->n_live; }
+template <typename Real>
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_scatter(Soa<Real> src, Soa<Real> dst, const DevState* st, int* cursor, int nz) {
+  const int n = (int)st->n_slots;
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * kSortChunk; base < n; base += gridDim.x * kSortChunk)
+    scatter_group(src, dst, n, base + 4 * threadIdx.x, cursor, nz, lane);
+}
+
+// a batch: simulation k's particles stay in its segment (the same base in
+// both buffer sets)
+template <typename Real>
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_scatter_batch(Soa<Real> src, Soa<Real> dst, const DevState* st, const SegInfo* seg,
+                     int nsim, int* cursor, int count_stride, int nz) {
+  __shared__ int first[kMaxSims + 1];
+  __shared__ long long nslots[kMaxSims];
+  chunk_table(st, nsim, kSortChunk, first, nslots);
+  const int lane = threadIdx.x & 31;
+  for (int c = blockIdx.x; c < first[nsim]; c += gridDim.x) {
+    const int sim = chunk_owner(first, nsim, c);
+    const long long b = seg[sim].base;
+    const int p0 = (c - first[sim]) * kSortChunk + 4 * threadIdx.x;
+    scatter_group(soa_offset(src, b), soa_offset(dst, b), (int)nslots[sim], p0,
+                  cursor + (size_t)sim * count_stride, nz, lane);
+  }
+}
+
+__global__ void k_sort_commit(DevState* st, int nsim) {
+  for (int k = threadIdx.x; k < nsim; k += blockDim.x) st[k].n_slots = st[k].n_live;
+}
 
 template <typename Real>
 void launch_sort(const Soa<Real>& src, const Soa<Real>& dst, DevState* st,
                  int* cell_count, int ncells, int nz, int grid,
                  cudaStream_t stream) {
   cudaMemsetAsync(cell_count, 0, (size_t)(ncells + 4095) / 4096 * 4096 * sizeof(int), stream);
-  k_sort_hist<Real><<<grid, 256, 0, stream>>>(src.cell, st, cell_count, nz);
-  k_sort_scan<<<1, 1024, 0, stream>>>(cell_count, ncells, st);
-  k_sort_scatter<Real><<<grid, 256, 0, stream>>>(src, dst, st, cell_count, nz);
-  k_sort_commit<<<1, 1, 0, stream>>>(st);
+  k_sort_hist<Real><<<grid, kSortThreads, 0, stream>>>(src.cell, st, cell_count, nz);
+  k_sort_scan<<<1, 1024, 0, stream>>>(cell_count, ncells, st, 0);
+  k_sort_scatter<Real><<<grid, kSortThreads, 0, stream>>>(src, dst, st, cell_count, nz);
+  k_sort_commit<<<1, 1, 0, stream>>>(st, 1);
+}
+
+template <typename Real>
+void launch_sort_batch(const Soa<Real>& src, const Soa<Real>& dst, DevState* st,
+                       const SegInfo* seg, int nsim, int* cell_count, int ncells, int nz,
+                       int grid, cudaStream_t stream) {
+  const int stride = (ncells + 4095) / 4096 * 4096;
+  cudaMemsetAsync(cell_count, 0, (size_t)nsim * stride * sizeof(int), stream);
+  k_sort_hist_batch<<<grid, kSortThreads, 0, stream>>>(src.cell, st, seg, nsim, cell_count,
+                                                       stride, nz);
+  k_sort_scan<<<nsim, 1024, 0, stream>>>(cell_count, ncells, st, stride);
+  k_sort_scatter_batch<Real><<<grid, kSortThreads, 0, stream>>>(src, dst, st, seg, nsim,
+                                                                cell_count, stride, nz);
+  k_sort_commit<<<1, 256, 0, stream>>>(st, nsim);
 }
 
 template void launch_sort<float>(const Soa<float>&, const Soa<float>&, DevState*, int*, int,
                                  int, int, cudaStream_t);
 template void launch_sort<double>(const Soa<double>&, const Soa<double>&, DevState*, int*, int,
                                   int, int, cudaStream_t);
+template void launch_sort_batch<float>(const Soa<float>&, const Soa<float>&, DevState*,
+                                       const SegInfo*, int, int*, int, int, int, cudaStream_t);
+template void launch_sort_batch<double>(const Soa<double>&, const Soa<double>&, DevState*,
+                                        const SegInfo*, int, int*, int, int, int, cudaStream_t);
 
 }  // namespace pic

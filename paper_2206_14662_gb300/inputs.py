@@ -64,6 +64,37 @@ def workload(name: str, **overrides) -> dict:
     return cfg
 
 
+# The parametric scan (the paper's scans over pressure, applied voltage and
+# magnetic field, Sec. III-IV): a 4 x 4 x 4 grid of pressure, inner-electrode
+# voltage and mirror field B0, 64 x 256 cells each, run as one batch.
+SCAN_PRESSURES_MBAR = (1.0e-6, 1.0e-5, 1.0e-4, 1.0e-3)
+SCAN_VOLTAGES_V = (-5.0e3, -13.333e3, -21.667e3, -30.0e3)
+SCAN_B0_T = (0.1, 0.2333, 0.3667, 0.5)
+
+
+def scan_configs(n_sims: int = 64, nr: int = 64, nz: int = 256, n_min: int = 100_000,
+                 n_max: int = 5_000_000, **overrides) -> list[dict]:
+    """Configurations of the scan "scan_64x256_64sims".  Simulation k takes
+    pressure SCAN_PRESSURES_MBAR[(k // 16) % 4], voltage
+    SCAN_VOLTAGES_V[(k // 4) % 4] and field SCAN_B0_T[k % 4] (mirror field),
+    and N_k = round(n_min (n_max / n_min)^(k / (n_sims - 1))) macro-electrons
+    (log-spaced: a 50x spread of work between the smallest and the largest
+    simulation), with the macro weight n0 V_gap / N_k.  ``overrides`` apply
+    to every simulation."""
+    cfgs = []
+    for k in range(n_sims):
+        frac = k / (n_sims - 1) if n_sims > 1 else 0.0
+        n_k = int(round(n_min * (n_max / n_min) ** frac))
+        cfg = dict(_BASE, nr=nr, nz=nz, bfield_kind=1,
+                   p_mbar=SCAN_PRESSURES_MBAR[(k // 16) % 4],
+                   v_inner=SCAN_VOLTAGES_V[(k // 4) % 4],
+                   b0=SCAN_B0_T[k % 4],
+                   n_init=n_k, steps=20_000, precision=32)
+        cfg.update(overrides)
+        cfgs.append(cfg)
+    return cfgs
+
+
 ELECTRON_MASS = 9.1093837015e-31   # kg, CODATA 2018 (input recipe only)
 ELEMENTARY_CHARGE = 1.602176634e-19  # C
 

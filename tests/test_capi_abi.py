@@ -67,3 +67,30 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_capi, "_lib", None)
     with pytest.raises(RuntimeError):
         _capi.lib()
+
+
+def test_batch_configurations_validated_on_the_host():
+    """pic_init rejects, before touching a device, batches whose simulations
+    disagree in the shared geometry or settings, and batch sizes outside
+    1..256 (host logic; no GPU needed)."""
+    from paper_2206_14662_gb300 import _capi
+    from paper_2206_14662_gb300.inputs import scan_configs
+    L = _capi.lib()
+    h = ctypes.c_void_p()
+
+    def init(cfgs, n=None):
+        arr = (_capi.PicConfig * len(cfgs))(*[_capi.make_config(c) for c in cfgs])
+        return L.pic_init(arr, len(cfgs) if n is None else n, None, None, ctypes.byref(h))
+
+    base = scan_configs(n_sims=4, nr=32, nz=64, n_min=100, n_max=400)
+    for field, value in (("nr", 33), ("r_out", 11e-3), ("dt", 2e-12), ("sort_every", 10),
+                         ("precision", 64), ("seed", 2), ("poisson_rtol", 1e-9),
+                         ("fixed_efield", 1)):
+        bad = [dict(c) for c in base]
+        bad[2][field] = value
+        assert init(bad) == _capi.PIC_EINVAL, field
+    assert init(base, n=0) == _capi.PIC_EINVAL
+    assert init(base * 65, n=257) == _capi.PIC_EINVAL
+    bad = [dict(c) for c in base]
+    bad[3]["p_mbar"] = -1.0        # a per-simulation field is validated too
+    assert init(bad) == _capi.PIC_EINVAL
