@@ -139,11 +139,12 @@ class Clocks:
 def _inputs(args, rank):
     """(workload name, configurations, seeded particle arrays per
     simulation) of the run."""
+    over = {} if args.warm_start is None else {"warm_start": args.warm_start}
     if args.workload == SCAN:
-        cfgs = scan_configs(seed=1 + rank)
+        cfgs = scan_configs(seed=1 + rank, **over)
         parts = [seed_particles(c, seed=1000 * (rank + 1) + k) for k, c in enumerate(cfgs)]
         return SCAN, cfgs, parts
-    cfg = workload(WORKLOAD, seed=1 + rank)
+    cfg = workload(WORKLOAD, seed=1 + rank, **over)
     if args.particles:
         cfg["n_init"] = args.particles
     return WORKLOAD, [cfg], [seed_particles(cfg)]
@@ -280,7 +281,8 @@ def run_ours(args, ws, rank):
                               "note": "profiled pass after the timed region, kernels "
                                       "launched one by one"},
         "poisson": {"sweeps": d1["poisson_iters"], "relres": d1["poisson_relres"],
-                    "relres_charge": d1["poisson_relres_charge"]},
+                    "relres_charge": d1["poisson_relres_charge"],
+                    "warm_start": cfg.get("warm_start", 0)},
         "clocks": clk,
     }
     if args.cpu_baseline:
@@ -352,6 +354,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--workload", choices=[WORKLOAD, SCAN], default=WORKLOAD)
+    ap.add_argument("--warm-start", type=int, choices=[0, 1], default=None,
+                    help="override the field solve's initial guess (0 zero, 1 previous)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false",

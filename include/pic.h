@@ -92,6 +92,9 @@ typedef struct pic_config {
                               E_cap = 2 |v_inner - v_outer| eV */
   int32_t fixed_efield;    /* 1: skip the field solve; E stays as set by
                               pic_set_efield (particle-only stepping) */
+  int32_t warm_start;      /* initial guess of each field solve's
+                              refinement: 0 zero, 1 the previous solve's
+                              space-charge potential */
 } pic_config;
 
 /* Diagnostics of one simulation (Sec. III.A: peak density and boundary

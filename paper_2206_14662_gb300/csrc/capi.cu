@@ -157,6 +157,7 @@ int validate(const pic_config& c) {
   if (c.weight <= 0 && (c.n_init <= 0 || !(c.n0 > 0))) return PIC_EINVAL;
   if (c.sort_every < 0 || c.capacity < 0) return PIC_EINVAL;
   if (!(c.poisson_rtol > 0) || c.poisson_maxit < 0 || c.poisson_maxit > 64) return PIC_EINVAL;
+  if (c.warm_start != 0 && c.warm_start != 1) return PIC_EINVAL;
   // the Thomas sweep keeps four (nr - 1) x 32 float columns in shared memory
   if ((long long)4 * (c.nr - 1) * 32 * 4 > 200 * 1024) return PIC_EINVAL;
   if ((long long)(c.nr + 1) * (c.nz + 1) > (1ll << 30)) return PIC_EINVAL;
@@ -173,7 +174,8 @@ int validate_batch(const pic_config* c, int n) {
     if (b.r_in != a.r_in || b.r_out != a.r_out || b.z_min != a.z_min || b.z_max != a.z_max ||
         b.nr != a.nr || b.nz != a.nz || b.dt != a.dt || b.sort_every != a.sort_every ||
         b.poisson_rtol != a.poisson_rtol || b.poisson_maxit != a.poisson_maxit ||
-        b.precision != a.precision || b.seed != a.seed || b.fixed_efield != a.fixed_efield)
+        b.precision != a.precision || b.seed != a.seed || b.fixed_efield != a.fixed_efield ||
+        b.warm_start != a.warm_start)
       return PIC_EINVAL;
   }
   return PIC_OK;

@@ -35,6 +35,11 @@
 // the right-hand side with all wall potentials moved into it) is <= rtol;
 // if the last allowed sweep has not reached it, PIC_ENOCONV is latched.
 // ||r|| / ||b'_I|| (relative to the charge alone) is reported as well.
+//
+// Initial guess.  Cold (warm_start 0): phi_rho = 0, so the first sweep
+// sets phi_rho = S(b').  Warm (warm_start 1): the previous solve's phi_rho
+// is kept; one residual pass before the first sweep measures it (and ends
+// the solve at once if it already meets rtol), and every sweep adds.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -121,6 +126,7 @@ void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& 
   T.hz = (cfg.z_max - cfg.z_min) / nz;
   T.rtol = cfg.poisson_rtol;
   T.maxit = cfg.poisson_maxit > 0 ? cfg.poisson_maxit : 4;
+  T.warm = cfg.warm_start == 1 ? 1 : 0;
   int l2 = 0;
   while ((1 << l2) < 2 * M) ++l2;
   // FFT path for M a power of two whose 2M-point complex line and its M
@@ -346,7 +352,7 @@ template <bool FWD>
 __global__ void __launch_bounds__(512)
 k_dct32(FieldTables T, const DevState* st, int sweep) {
   const int sim = blockIdx.y;
-  if (sweep > 0 && *(volatile const int*)&st[sim].solve_done) return;
+  if ((sweep > 0 || T.warm) && *(volatile const int*)&st[sim].solve_done) return;
   extern __shared__ float2 sh[];   // N line values, then N/2 twiddles
   const int M = T.M, N = 2 * M, M1 = M + 1, NI = T.NI, log2N = T.log2N;
   const size_t nn = (size_t)(T.nr + 1) * M1, tri = (size_t)NI * M1;
@@ -386,11 +392,12 @@ k_dct32(FieldTables T, const DevState* st, int sweep) {
       T.bhat[(size_t)line0 * M1 + k] = vx * T.scale32[k];
       if (two) T.bhat[(size_t)(line0 + 1) * M1 + k] = vy * T.scale32[k];
     } else {
+      const bool set = sweep == 0 && !T.warm;
       float2* p = T.phir + (size_t)(line0 + 1) * M1 + k;
-      *p = sweep == 0 ? make_float2(vx, 0.f) : df_add(*p, make_float2(vx, 0.f));
+      *p = set ? make_float2(vx, 0.f) : df_add(*p, make_float2(vx, 0.f));
       if (two) {
         p += M1;
-        *p = sweep == 0 ? make_float2(vy, 0.f) : df_add(*p, make_float2(vy, 0.f));
+        *p = set ? make_float2(vy, 0.f) : df_add(*p, make_float2(vy, 0.f));
       }
     }
   }
@@ -400,7 +407,7 @@ k_dct32(FieldTables T, const DevState* st, int sweep) {
 template <bool FWD>
 __global__ void k_dct32_direct(FieldTables T, const DevState* st, int sweep) {
   const int sim = blockIdx.y;
-  if (sweep > 0 && *(volatile const int*)&st[sim].solve_done) return;
+  if ((sweep > 0 || T.warm) && *(volatile const int*)&st[sim].solve_done) return;
   extern __shared__ float xs[];
   const int M = T.M, M1 = M + 1, line = blockIdx.x;
   const size_t nn = (size_t)(T.nr + 1) * M1, tri = (size_t)T.NI * M1;
@@ -420,7 +427,7 @@ __global__ void k_dct32_direct(FieldTables T, const DevState* st, int sweep) {
       T.bhat[(size_t)line * M1 + k] = acc * T.scale32[k];
     } else {
       float2* p = T.phir + (size_t)(line + 1) * M1 + k;
-      *p = sweep == 0 ? make_float2(acc, 0.f) : df_add(*p, make_float2(acc, 0.f));
+      *p = sweep == 0 && !T.warm ? make_float2(acc, 0.f) : df_add(*p, make_float2(acc, 0.f));
     }
   }
 }
@@ -439,7 +446,7 @@ constexpr int kTriThreads = 256;
 __global__ void __launch_bounds__(kTriThreads) k_tridiag32(FieldTables T, const DevState* st,
                                                            int sweep) {
   const int sim = blockIdx.y;
-  if (sweep > 0 && *(volatile const int*)&st[sim].solve_done) return;
+  if ((sweep > 0 || T.warm) && *(volatile const int*)&st[sim].solve_done) return;
   extern __shared__ float sm[];
   const int M1 = T.M + 1, NI = T.NI;
   const size_t tri = (size_t)NI * M1;
@@ -499,7 +506,7 @@ __global__ void __launch_bounds__(256)
 k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep, int last) {
   const int sim = blockIdx.z;
   st += sim;
-  if (sweep > 0 && *(volatile const int*)&st->solve_done) return;
+  if (sweep >= 0 && (sweep > 0 || T.warm) && *(volatile const int*)&st->solve_done) return;
   const int nr = T.nr, M = T.M, M1 = M + 1;
   const size_t nn = (size_t)(nr + 1) * M1;
   T.phir += sim * nn; T.res += sim * nn; T.b2 += sim * nn; E += sim * nn;
@@ -621,7 +628,7 @@ void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream, int 
   k_phi_out<<<(n + 255) / 256, 256, 0, stream>>>(T, phi, sim);
 }
 
-int field_solve_kernels(const FieldTables& T) { return 1 + 4 * T.maxit; }
+int field_solve_kernels(const FieldTables& T) { return 1 + T.warm + 4 * T.maxit; }
 
 template <typename Real>
 void launch_field_solve(const FieldTables& T, const double* rhs, const unsigned long long* cnt,
@@ -637,6 +644,9 @@ void launch_field_solve(const FieldTables& T, const double* rhs, const unsigned 
                                                   0.0, cnt_clear, T, st);
   else k_prep<false><<<grd, blk, 0, stream>>>(rhs, nullptr, make_float2(0.f, 0.f), nullptr, s0,
                                                cnt_clear, T, st);
+  if (T.warm)   // residual of the previous solution, the refinement's start
+    k_residual<Real><<<grd, blk, 0, stream>>>(T, (typename Vec2<Real>::type*)efield, st, -1,
+                                             T.maxit == 0);
   for (int s = 0; s < T.maxit; ++s) {
     if (T.log2N > 0) {
       const int N = 2 * T.M;

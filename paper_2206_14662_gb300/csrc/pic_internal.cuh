@@ -236,6 +236,7 @@ struct FieldTables {
   int nr, nz, M, NI;          // cells, M = nz, NI = nr - 1 interior r-lines
   int log2N;                  // FFT length N = 2M = 2^log2N, or -1 (direct)
   int maxit;                  // refinement sweeps at most
+  int warm;                   // 1: refine from the previous phi_rho
   double hr, hz, rtol;
   float2* tw32;               // exp(-2 pi i m / N), m < N/2
   float* cos32;               // cos(pi m / M), m < 2M (direct transform)

@@ -31,7 +31,7 @@ _BASE = dict(
     n_init=10_000, n0=1.0e15, T0_eV=1.0,
     weight=0.0,
     dt=1.0e-12, sort_every=20,
-    poisson_rtol=1.0e-8, poisson_maxit=2,
+    poisson_rtol=1.0e-8, poisson_maxit=2, warm_start=1,
     capacity=0,
     seed=1,
     precision=32,

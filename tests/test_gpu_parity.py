@@ -154,16 +154,18 @@ def test_many_steps_with_sorting_fp64():
     assert d["n_absorbed"] == o.tally[oracle.T_N_ABSORBED]
 
 
+@pytest.mark.parametrize("warm", [0, 1])
 @pytest.mark.parametrize("precision", [64, 32])
-def test_self_consistent_steps(precision):
-    """Ten full steps of the workload "coax_32x64_1e4" (field solve on):
+def test_self_consistent_steps(precision, warm):
+    """Ten full steps of the workload "coax_32x64_1e4" (field solve on, each
+    solve refined from zero or from the previous step's potential):
     particles and the potential follow the oracle."""
     from paper_2206_14662_gb300._capi import PIC_GRID_PHI
     # FP64 path: the field solved to 1e-12 so that the particle comparison
     # measures the particle path; FP32 path: the default tolerance
     cfg = workload("coax_32x64_1e4", precision=precision, p_mbar=0.3, T0_eV=30.0,
                    poisson_rtol=1e-12 if precision == 64 else 1e-8,
-                   poisson_maxit=8 if precision == 64 else 2)
+                   poisson_maxit=8 if precision == 64 else 2, warm_start=warm)
     parts = seed_particles(cfg)
     o = oracle.OracleSim(cfg, *parts)
     sim = make_gpu(cfg, parts)
@@ -384,3 +386,28 @@ def test_graph_replay_matches_direct_launches():
     assert np.array_equal(pa, pb)
     assert da["n_pushed"] == db["n_pushed"] and da["step"] == db["step"] == 40
     assert db["kernels_launched"] == da["kernels_launched"]
+
+
+def test_warm_start_sweeps_and_residual():
+    """Warm-started solves (from the previous step's potential) on the
+    benchmark geometry meet the same residual bound in every step with no
+    more sweeps than cold-started ones, and give the same potential within
+    the solve's accuracy."""
+    from paper_2206_14662_gb300._capi import PIC_GRID_PHI, Simulation
+    res = {}
+    for warm in (0, 1):
+        cfg = workload("mirror_128x512_1e7", n_init=200_000, warm_start=warm)
+        parts = seed_particles(cfg)
+        with Simulation(cfg) as sim:
+            sim.load_particles(*parts)
+            sweeps, rel = [], []
+            for _ in range(12):
+                sim.step(1)
+                d = sim.diagnostics()
+                sweeps.append(d["poisson_iters"])
+                rel.append(d["poisson_relres"])
+            res[warm] = (np.array(sweeps), np.array(rel), sim.get_grid(PIC_GRID_PHI))
+    (s0, r0, p0), (s1, r1, p1) = res[0], res[1]
+    assert (r0 <= 1e-8).all() and (r1 <= 1e-8).all()
+    assert (s1 <= s0).all()
+    assert np.abs(p1 - p0).max() <= 1e-9 * np.abs(p0).max()
