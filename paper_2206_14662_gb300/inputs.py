@@ -150,3 +150,39 @@ def random_field_node_arrays(cfg: dict, scale: float, seed: int = 7):
         er += scale * rng.standard_normal() * np.sin(np.pi * kx * x + ph[0]) * np.cos(np.pi * ky * y + ph[1])
         ez += 0.3 * scale * rng.standard_normal() * np.cos(np.pi * kx * x + ph[1]) * np.sin(np.pi * ky * y + ph[0])
     return er.ravel(), ez.ravel()
+
+
+# Initial weights of the learned field-solve warm start (a U-Net of base
+# width c, see the library's pic_unet_* entry points for the layer order).
+# Each layer's weights are drawn N(0, 2 / fan_in) (fan_in = kernel taps x
+# input channels), biases are zero; the head starts at N(0, head_std^2).
+def unet_layer_shapes(c: int, cin: int = 2) -> list[tuple[str, tuple]]:
+    """(name, weight shape) in the flat parameter order: conv layers
+    (3, 3, in, out), transposed convolutions (2, 2, in, out), head (c,)."""
+    return [("enc1a", (3, 3, cin, c)), ("enc1b", (3, 3, c, c)),
+            ("enc2a", (3, 3, c, 2 * c)), ("enc2b", (3, 3, 2 * c, 2 * c)),
+            ("enc3a", (3, 3, 2 * c, 4 * c)), ("enc3b", (3, 3, 4 * c, 4 * c)),
+            ("enc4a", (3, 3, 4 * c, 8 * c)), ("enc4b", (3, 3, 8 * c, 8 * c)),
+            ("up3", (2, 2, 8 * c, 4 * c)), ("dec3a", (3, 3, 8 * c, 4 * c)),
+            ("dec3b", (3, 3, 4 * c, 4 * c)),
+            ("up2", (2, 2, 4 * c, 2 * c)), ("dec2a", (3, 3, 4 * c, 2 * c)),
+            ("dec2b", (3, 3, 2 * c, 2 * c)),
+            ("up1", (2, 2, 2 * c, c)), ("dec1a", (3, 3, 2 * c, c)), ("dec1b", (3, 3, c, c)),
+            ("head", (c,))]
+
+
+def unet_init_flat(c: int, seed: int = 0, cin: int = 2, head_std: float = 1e-2,
+                   bias_std: float = 0.0) -> np.ndarray:
+    """Flat float64 parameter vector: per layer its weights (C order), then
+    its bias (out channels; one value for the head)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for name, shp in unet_layer_shapes(c, cin):
+        if name == "head":
+            parts.append(rng.standard_normal(shp) * head_std)
+            parts.append(rng.standard_normal(1) * bias_std)
+        else:
+            fan_in = shp[0] * shp[1] * shp[2]
+            parts.append(rng.standard_normal(shp).ravel() * np.sqrt(2.0 / fan_in))
+            parts.append(rng.standard_normal(shp[3]) * bias_std)
+    return np.concatenate([np.ravel(p) for p in parts])
