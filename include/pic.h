@@ -94,7 +94,9 @@ typedef struct pic_config {
                               pic_set_efield (particle-only stepping) */
   int32_t warm_start;      /* initial guess of each field solve's
                               refinement: 0 zero, 1 the previous solve's
-                              space-charge potential */
+                              space-charge potential, 2 the learned guess
+                              of an attached net (pic_attach_unet; the
+                              previous potential until one is attached) */
 } pic_config;
 
 /* Diagnostics of one simulation (Sec. III.A: peak density and boundary
@@ -125,10 +127,13 @@ typedef struct pic_diag {
                                     side with the wall potentials moved into
                                     it (the convergence contract) */
   double poisson_relres_charge;  /* its residual relative to the charge
-                                    alone (the sweeps' stopping test) */
+                                    alone (reported beside the contract) */
   double nu_max;                 /* collision majorant in use, s^-1 */
   double weight;                 /* macro weight in use */
   int32_t error;                 /* sticky error code (0 none) */
+  double poisson_relres_init;    /* residual of the last solve's initial
+                                    guess (warm starts), measured as
+                                    poisson_relres; -1 after a cold start */
 } pic_diag;
 
 typedef struct pic_handle pic_handle;
@@ -281,6 +286,87 @@ void pic_free(pic_handle* h);
 
 /* Static string for a PIC_* code. */
 const char* pic_strerror(int code);
+
+/* ------------------------------------------------------------------------
+ * Learned initial guess of the field solve.  The paper has no counterpart:
+ * a four-level convolutional U-Net maps (charge, previous space-charge
+ * potential) on the H x W node grid to a guess of the new space-charge
+ * potential; the field solve then refines that guess to the same residual
+ * bound (poisson_rtol), so the solver stays the judge.
+ *
+ * Architecture (base width c, 1 <= c <= 32; H, W multiples of 8): per
+ * level k = 1..4 at width c 2^(k-1) two 3 x 3 convolutions with bias and
+ * ReLU, 2 x 2 average pooling between levels; back up through 2 x 2
+ * transposed convolutions (stride 2, with bias, no activation) whose output
+ * is concatenated before the level's skip activation and followed by two
+ * 3 x 3 convolutions with ReLU; a 1 x 1 head to one channel.  The 3 x 3
+ * layers are cross-correlations with zero padding:
+ * out[y][x] = b + sum in[y + ky - 1][x + kx - 1] W[ky][kx].
+ *
+ * Flat parameter layout (FP32, host): for the layers enc1a, enc1b, enc2a,
+ * enc2b, enc3a, enc3b, enc4a, enc4b, up3, dec3a, dec3b, up2, dec2a, dec2b,
+ * up1, dec1a, dec1b, head in this order, the weights then the bias:
+ * 3 x 3 layers W[ky][kx][in][out], transposed layers U[dy][dx][in][out]
+ * (out[2y + dy][2x + dx] += in[y][x] U[dy][dx]), the head w[c] and one
+ * bias.  Input channels of dec*a: the upsampled channels first, then the
+ * skip channels.
+ *
+ * Arrays passed to the net are DEVICE pointers, FP32, (batch, H, W,
+ * channels) with 2 input channels and 1 output channel.  Work is queued on
+ * the net's stream; calls synchronise only where stated.
+ * ---------------------------------------------------------------------- */
+typedef struct pic_unet pic_unet;
+
+/* Create a net for `batch` images of H x W.  precision 16: BF16
+ * activations and weight copies, convolutions on the tensor cores with FP32
+ * accumulation, FP32 master weights and Adam moments; precision 32: FP32
+ * throughout (test mode).  Parameters start at zero; set them with
+ * pic_unet_set_params.  PIC_EINVAL for unsupported sizes. */
+int pic_unet_create(int base_channels, int H, int W, int batch, int precision,
+                    void* cuda_stream, const pic_allocator* alloc,
+                    pic_unet** out);
+void pic_unet_free(pic_unet* net);
+/* number of FP32 values of the flat parameter vector */
+int64_t pic_unet_param_count(const pic_unet* net);
+/* host flat vector in / out (synchronise); set also clears the Adam
+ * moments */
+int pic_unet_set_params(pic_unet* net, const float* params);
+int pic_unet_get_params(pic_unet* net, float* params);
+/* y = net(x): x (batch, H, W, 2), y (batch, H, W) or NULL */
+int pic_unet_forward(pic_unet* net, const float* x, float* y);
+/* after pic_unet_forward: parameter gradients of sum(gy * y) (replacing
+ * the previous ones), and the input gradient into gx (batch, H, W, 2) when
+ * gx is not NULL */
+int pic_unet_backward(pic_unet* net, const float* gy, float* gx);
+/* host flat vector of the parameter gradients (synchronises) */
+int pic_unet_get_grads(pic_unet* net, float* grads);
+/* one Adam step (step number t >= 1) on the loss
+ * sum (y - target)^2 / (2 batch H W); *loss (device, may be NULL) receives
+ * the loss before the update */
+int pic_unet_train_step(pic_unet* net, const float* x, const float* target,
+                        float lr, float beta1, float beta2, float eps,
+                        int64_t t, float* loss);
+
+/* Use `net` (batch = n_sims, H = nr, W = nz) for the initial guess of the
+ * field solves of a handle made with warm_start = 2 (NULL detaches): before
+ * each solve the net reads, per simulation, the node charge of the step's
+ * deposit over rho_scale (C) and the previous space-charge potential
+ * phi_rho over phi_scale (V), node (i, j) as pixel (i - 1, j) for
+ * i = 1..nr, j < nz, and the interior potential becomes
+ * phi_rho + dphi_scale * output (node column nz takes pixel column
+ * nz - 1).  The solve then refines that guess to poisson_rtol as usual.
+ * The handle does not own the net; keep it alive while attached.
+ * Synchronises.  PIC_EINVAL for a net of other dimensions. */
+int pic_attach_unet(pic_handle* h, pic_unet* net, double rho_scale,
+                    double phi_scale, double dphi_scale);
+
+/* Images of the current field state of every simulation, FP32 DEVICE
+ * arrays of n_sims x nr x nz pixels in the net's layout (pixel (s, y, x) =
+ * node (y + 1, x) of simulation s): the last deposit's node charge (C) and
+ * the space-charge potential phi_rho = phi - phi_vac (V) of the last solve.
+ * Either pointer may be NULL.  Queued on the handle's stream; checks the
+ * sticky error (synchronises). */
+int pic_field_images(pic_handle* h, float* rho, float* phi_rho);
 
 #ifdef __cplusplus
 }

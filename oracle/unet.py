@@ -21,6 +21,12 @@ mean over 2 x 2 blocks; upconv2 the transposed 2 x 2 convolution of stride
 2, out[2y + dy, 2x + dx] = in[y, x] U[dy, dx] + b; concat puts the upsampled
 channels first.  Arrays are (batch, H, W, channels).  The loss is
 L = sum (y - t)^2 / (2 N), N the number of output values.
+
+``forward`` and ``backward`` take an optional rounding ``q`` applied where
+a reduced-precision implementation stores values (the input, every stored
+activation and activation gradient, the convolution weights): with
+q = round_bf16 the ReLU decisions are taken on the same BF16 values as a
+BF16 implementation takes them; q = None is the plain FP64 network.
 """
 from __future__ import annotations
 
@@ -70,6 +76,18 @@ def unflatten(vec: np.ndarray, c: int, cin: int = 2) -> dict:
 
 
 # ----------------------------------------------------------------- ops
+
+def round_bf16(a):
+    """Round to the nearest BF16 value (ties to even) through float32."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64).reshape(np.shape(a))
+
+
+def _ident(a):
+    return a
+
 
 def conv3(x, W, b):
     B, H, Wd, _ = x.shape
@@ -130,26 +148,31 @@ def relu(x):
 
 # ------------------------------------------------------------- network
 
-def forward(p: dict, x: np.ndarray):
+def forward(p: dict, x: np.ndarray, q=None):
     """Output y (batch, H, W) and the activations needed by backward."""
-    a = {"x": x}
-    a["e1a"] = relu(conv3(x, p["enc1a.w"], p["enc1a.b"]))
-    a["s1"] = relu(conv3(a["e1a"], p["enc1b.w"], p["enc1b.b"]))
-    a["p1"] = pool(a["s1"])
-    a["e2a"] = relu(conv3(a["p1"], p["enc2a.w"], p["enc2a.b"]))
-    a["s2"] = relu(conv3(a["e2a"], p["enc2b.w"], p["enc2b.b"]))
-    a["p2"] = pool(a["s2"])
-    a["e3a"] = relu(conv3(a["p2"], p["enc3a.w"], p["enc3a.b"]))
-    a["s3"] = relu(conv3(a["e3a"], p["enc3b.w"], p["enc3b.b"]))
-    a["p3"] = pool(a["s3"])
-    a["e4a"] = relu(conv3(a["p3"], p["enc4a.w"], p["enc4a.b"]))
-    a["e4b"] = relu(conv3(a["e4a"], p["enc4b.w"], p["enc4b.b"]))
+    q = q or _ident
+    a = {"x": q(x)}
+
+    def cv(inp, name):
+        return q(relu(conv3(inp, q(p[name + ".w"]), p[name + ".b"])))
+
+    a["e1a"] = cv(a["x"], "enc1a")
+    a["s1"] = cv(a["e1a"], "enc1b")
+    a["p1"] = q(pool(a["s1"]))
+    a["e2a"] = cv(a["p1"], "enc2a")
+    a["s2"] = cv(a["e2a"], "enc2b")
+    a["p2"] = q(pool(a["s2"]))
+    a["e3a"] = cv(a["p2"], "enc3a")
+    a["s3"] = cv(a["e3a"], "enc3b")
+    a["p3"] = q(pool(a["s3"]))
+    a["e4a"] = cv(a["p3"], "enc4a")
+    a["e4b"] = cv(a["e4a"], "enc4b")
     prev = a["e4b"]
     for k in (3, 2, 1):
-        u = upconv(prev, p[f"up{k}.w"], p[f"up{k}.b"])
+        u = q(upconv(prev, q(p[f"up{k}.w"]), p[f"up{k}.b"]))
         a[f"c{k}"] = np.concatenate([u, a[f"s{k}"]], axis=3)
-        a[f"d{k}a"] = relu(conv3(a[f"c{k}"], p[f"dec{k}a.w"], p[f"dec{k}a.b"]))
-        a[f"d{k}b"] = relu(conv3(a[f"d{k}a"], p[f"dec{k}b.w"], p[f"dec{k}b.b"]))
+        a[f"d{k}a"] = cv(a[f"c{k}"], f"dec{k}a")
+        a[f"d{k}b"] = cv(a[f"d{k}a"], f"dec{k}b")
         a[f"in_up{k}"] = prev
         prev = a[f"d{k}b"]
     y = a["d1b"] @ p["head.w"] + p["head.b"][0]
@@ -160,34 +183,35 @@ def loss(y, t):
     return 0.5 * np.sum((y - t) ** 2) / y.size
 
 
-def backward(p: dict, a: dict, gy: np.ndarray):
+def backward(p: dict, a: dict, gy: np.ndarray, q=None):
     """Gradients of every parameter and of the input for the output
     gradient gy (batch, H, W)."""
+    q = q or _ident
+    W = {k: (q(v) if k.endswith(".w") and not k.startswith("head") else v) for k, v in p.items()}
     g = {}
     g["head.w"] = np.einsum("bhwc,bhw->c", a["d1b"], gy)
     g["head.b"] = np.array([gy.sum()])
-    gpost = gy[..., None] * p["head.w"]            # wrt d1b
-    up_grad = None
+    gpre = q(gy[..., None] * p["head.w"] * (a["d1b"] > 0))   # wrt d1b, pre-activation
     for k in (1, 2, 3):
-        gpre = gpost * (a[f"d{k}b"] > 0)
-        gin, g[f"dec{k}b.w"], g[f"dec{k}b.b"] = conv3_backward(a[f"d{k}a"], p[f"dec{k}b.w"], gpre)
-        gpre = gin * (a[f"d{k}a"] > 0)
-        gc, g[f"dec{k}a.w"], g[f"dec{k}a.b"] = conv3_backward(a[f"c{k}"], p[f"dec{k}a.w"], gpre)
+        gin, g[f"dec{k}b.w"], g[f"dec{k}b.b"] = conv3_backward(a[f"d{k}a"], W[f"dec{k}b.w"], gpre)
+        gpre = q(gin * (a[f"d{k}a"] > 0))
+        gc, g[f"dec{k}a.w"], g[f"dec{k}a.b"] = conv3_backward(a[f"c{k}"], W[f"dec{k}a.w"], gpre)
+        gc = q(gc)
         nu = p[f"up{k}.w"].shape[3]
         g[f"skip{k}"] = gc[..., nu:]
-        gprev, g[f"up{k}.w"], g[f"up{k}.b"] = upconv_backward(a[f"in_up{k}"], p[f"up{k}.w"],
+        gprev, g[f"up{k}.w"], g[f"up{k}.b"] = upconv_backward(a[f"in_up{k}"], W[f"up{k}.w"],
                                                              gc[..., :nu])
-        gpost = gprev   # wrt d{k+1}b, or e4b after k = 3
-        up_grad = gprev
-    gpre = up_grad * (a["e4b"] > 0)
-    gin, g["enc4b.w"], g["enc4b.b"] = conv3_backward(a["e4a"], p["enc4b.w"], gpre)
-    gpre = gin * (a["e4a"] > 0)
-    gpool, g["enc4a.w"], g["enc4a.b"] = conv3_backward(a["p3"], p["enc4a.w"], gpre)
+        gpre = q(gprev * (a[f"in_up{k}"] > 0))   # pre-activation of d{k+1}b, or of e4b
+    gin, g["enc4b.w"], g["enc4b.b"] = conv3_backward(a["e4a"], W["enc4b.w"], gpre)
+    gpre = q(gin * (a["e4a"] > 0))
+    gpool, g["enc4a.w"], g["enc4a.b"] = conv3_backward(a["p3"], W["enc4a.w"], gpre)
+    gpool = q(gpool)
     for k in (3, 2, 1):
-        gs = (g.pop(f"skip{k}") + pool_backward(gpool)) * (a[f"s{k}"] > 0)
-        gin, g[f"enc{k}b.w"], g[f"enc{k}b.b"] = conv3_backward(a[f"e{k}a"], p[f"enc{k}b.w"], gs)
-        gpre = gin * (a[f"e{k}a"] > 0)
+        gs = q((g.pop(f"skip{k}") + pool_backward(gpool)) * (a[f"s{k}"] > 0))
+        gin, g[f"enc{k}b.w"], g[f"enc{k}b.b"] = conv3_backward(a[f"e{k}a"], W[f"enc{k}b.w"], gs)
+        gpre = q(gin * (a[f"e{k}a"] > 0))
         src = a["x"] if k == 1 else a[f"p{k - 1}"]
-        gpool, g[f"enc{k}a.w"], g[f"enc{k}a.b"] = conv3_backward(src, p[f"enc{k}a.w"], gpre)
+        gpool, g[f"enc{k}a.w"], g[f"enc{k}a.b"] = conv3_backward(src, W[f"enc{k}a.w"], gpre)
+        gpool = q(gpool)
     g["x"] = gpool
     return g

@@ -48,7 +48,7 @@ class PicDiag(ctypes.Structure):
         ("ion_loss_J", c_d), ("recoil_loss_J", c_d), ("ke_initial_J", c_d),
         ("ledger_residual_J", c_d), ("n_peak", c_d), ("poisson_iters", c_i32),
         ("poisson_relres", c_d), ("poisson_relres_charge", c_d), ("nu_max", c_d),
-        ("weight", c_d), ("error", c_i32),
+        ("weight", c_d), ("error", c_i32), ("poisson_relres_init", c_d),
     ]
 
 
@@ -262,6 +262,22 @@ class Simulation:
 
     def restore(self, path: str):
         _check(lib().pic_restore(self.h, path.encode()), "pic_restore")
+
+    def attach_unet(self, net, rho_scale: float, phi_scale: float, dphi_scale: float):
+        """Learned initial guess of the field solves (warm_start = 2)."""
+        L = lib()
+        L.pic_attach_unet.argtypes = [ctypes.c_void_p, ctypes.c_void_p, c_d, c_d, c_d]
+        _check(L.pic_attach_unet(self.h, net.h if net is not None else None, rho_scale,
+                                 phi_scale, dphi_scale), "pic_attach_unet")
+        self._net = net
+
+    def field_images(self, rho=None, phi_rho=None):
+        """Charge and space-charge potential images (n_sims, nr, nz) into
+        float32 CUDA tensors (either may be None)."""
+        L = lib()
+        L.pic_field_images.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        p = [ctypes.c_void_p(t.data_ptr()) if t is not None else None for t in (rho, phi_rho)]
+        _check(L.pic_field_images(self.h, *p), "pic_field_images")
 
     def profile_start(self):
         _check(lib().pic_profile(self.h, 1, None), "pic_profile")

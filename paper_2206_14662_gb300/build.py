@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpic.so")
-SOURCES = ["particle_step.cu", "field_solve.cu", "sort.cu", "capi.cu", "field_static.cu"]
+SOURCES = ["particle_step.cu", "field_solve.cu", "sort.cu", "capi.cu", "field_static.cu",
+           "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 # the particle step writes its multiply-adds out explicitly; no automatic
@@ -41,7 +42,8 @@ def _stale(target: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link libpic.so if any source or header changed."""
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(INCLUDE, "pic.h"), os.path.join(CSRC, "pic_internal.cuh")]
+    headers = [os.path.join(INCLUDE, "pic.h"), os.path.join(CSRC, "pic_internal.cuh"),
+               os.path.join(CSRC, "unet_kernels.cuh")]
     nvcc = _nvcc()
     procs, objs = [], []
     for src in SOURCES:

@@ -66,6 +66,12 @@ struct pic_handle {
   float2* cnt_units;              // nsim fixed-point charge units / (2 pi eps0)
   PushParams<float>* Pf_dev;      // nsim entries (batch kernel)
   PushParams<double>* Pd_dev;
+  double* q_units;                // nsim: charge (C) per fixed-point count
+
+  // learned initial guess of the field solve (warm_start 2)
+  pic_unet* net;
+  float ws_scale[3];              // rho, phi_rho, correction scales
+  float* ws_x;                    // network input, nsim x nr x nz x 2
   Soa<float> sf[2];
   Soa<double> sd[2];
   int cur;
@@ -157,7 +163,7 @@ int validate(const pic_config& c) {
   if (c.weight <= 0 && (c.n_init <= 0 || !(c.n0 > 0))) return PIC_EINVAL;
   if (c.sort_every < 0 || c.capacity < 0) return PIC_EINVAL;
   if (!(c.poisson_rtol > 0) || c.poisson_maxit < 0 || c.poisson_maxit > 64) return PIC_EINVAL;
-  if (c.warm_start != 0 && c.warm_start != 1) return PIC_EINVAL;
+  if (c.warm_start < 0 || c.warm_start > 2) return PIC_EINVAL;
   // the Thomas sweep keeps four (nr - 1) x 32 float columns in shared memory
   if ((long long)4 * (c.nr - 1) * 32 * 4 > 200 * 1024) return PIC_EINVAL;
   if ((long long)(c.nr + 1) * (c.nz + 1) > (1ll << 30)) return PIC_EINVAL;
@@ -323,6 +329,14 @@ int step_impl(pic_handle* h, long long nsteps) {
       mark(h, kTagSort);
     }
     if (fp32) h->last_buf = h->dep_buf;
+    if (solve && h->net && h->cfg.warm_start == 2) {
+      const int rc = warm_start_learned(h->net, h->T, fp32 ? h->cnt[h->dep_buf] : nullptr,
+                                        h->q_units, fp32 ? nullptr : h->rhs, h->ws_x,
+                                        h->ws_scale[0], h->ws_scale[1], h->ws_scale[2],
+                                        h->stream);
+      if (rc) return rc;
+      h->kernels += unet_kernels_per_forward(h->net) + 2;
+    }
     if (solve) {
       if (fp32)
         launch_field_solve<Real>(h->T, nullptr, h->cnt[h->dep_buf],
@@ -487,6 +501,7 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   h->cnt_units = (float2*)h_alloc(S * sizeof(float2), h);
   h->Pf_dev = (PushParams<float>*)h_alloc(S * sizeof(PushParams<float>), h);
   h->Pd_dev = (PushParams<double>*)h_alloc(S * sizeof(PushParams<double>), h);
+  h->q_units = (double*)h_alloc(S * sizeof(double), h);
   if (h->prec == 32) {
     rc = alloc_soa(h, h->sf[0]);
     if (!rc) rc = alloc_soa(h, h->sf[1]);
@@ -505,7 +520,7 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   h->phi = (double*)h_alloc((size_t)h->nnodes * sizeof(double), h);
   h->efield = h_alloc(gn * (h->prec == 32 ? sizeof(float2) : sizeof(double2)), h);
   h->scratch2 = (double*)h_alloc(2 * sizeof(double), h);
-  if (!rc && (!h->st || !h->seg || !h->cnt_units || !h->Pf_dev || !h->Pd_dev ||
+  if (!rc && (!h->st || !h->seg || !h->cnt_units || !h->Pf_dev || !h->Pd_dev || !h->q_units ||
               !h->spawn_parent || !h->cell_count || !h->rhs || !h->cnt[0] || !h->cnt[1] ||
               !h->phi || !h->efield || !h->scratch2))
     rc = PIC_ENOMEM;
@@ -515,12 +530,14 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
     h->Pd.resize(n_sims);
     std::vector<SegInfo> seg(n_sims);
     std::vector<float2> units(n_sims);
+    std::vector<double> qunits(n_sims);
     const double s0 = 1.0 / (2.0 * kPi * kEps0);
     for (int k = 0; k < n_sims; ++k) {
       fill_params<float>(h, k, h->Pf[k]);
       fill_params<double>(h, k, h->Pd[k]);
       seg[k] = SegInfo{h->sims[k].base, h->sims[k].capacity, h->sims[k].spawn_cap};
       units[k] = df_from(-kQe * h->sims[k].weight / kFixUnit * s0);
+      qunits[k] = -kQe * h->sims[k].weight / kFixUnit;
     }
     std::vector<DevState> s0v(n_sims);
     std::memset(s0v.data(), 0, S * sizeof(DevState));
@@ -529,6 +546,8 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
         cudaMemcpyAsync(h->seg, seg.data(), S * sizeof(SegInfo), cudaMemcpyHostToDevice,
                         h->stream) != cudaSuccess ||
         cudaMemcpyAsync(h->cnt_units, units.data(), S * sizeof(float2), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->q_units, qunits.data(), S * sizeof(double), cudaMemcpyHostToDevice,
                         h->stream) != cudaSuccess ||
         cudaMemcpyAsync(h->Pf_dev, h->Pf.data(), S * sizeof(PushParams<float>),
                         cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
@@ -834,6 +853,7 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
   out->nu_max = m.nu_max;
   out->weight = m.weight;
   out->error = h->sticky;
+  out->poisson_relres_init = s.relres_init;
   if (density) {
     // node volume of each hat function: 2 pi R_i Z_j
     const double hr = h->hr, hz = h->hz;
@@ -1126,6 +1146,39 @@ int pic_restore(pic_handle* h, const char* path) {
   h->sims[0].last_diag_step = lds;
   h->sticky = s.err;
   return PIC_OK;
+}
+
+int pic_attach_unet(pic_handle* h, pic_unet* net, double rho_scale, double phi_scale,
+                    double dphi_scale) {
+  if (!h) return PIC_EINVAL;
+  if (net && (!unet_fits(net, h->nsim, h->cfg.nr, h->cfg.nz) || !(rho_scale > 0) ||
+              !(phi_scale > 0) || !(dphi_scale > 0)))
+    return PIC_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  if (net && !h->ws_x) {
+    h->ws_x = (float*)h_alloc((size_t)h->nsim * h->cfg.nr * h->cfg.nz * 2 * sizeof(float), h);
+    if (!h->ws_x) return PIC_ENOMEM;
+  }
+  h->net = net;
+  h->ws_scale[0] = (float)rho_scale;
+  h->ws_scale[1] = (float)phi_scale;
+  h->ws_scale[2] = (float)dphi_scale;
+  // captured step blocks do not contain the net's launches: capture again
+  for (auto& row : h->graph)
+    for (auto& x : row)
+      if (x) {
+        cudaGraphExecDestroy(x);
+        x = nullptr;
+      }
+  return PIC_OK;
+}
+
+int pic_field_images(pic_handle* h, float* rho, float* phi_rho) {
+  if (!h) return PIC_EINVAL;
+  const bool fp32 = h->prec == 32;
+  const int rc = field_images(h->T, fp32 ? h->cnt[h->last_buf] : nullptr, h->q_units,
+                              fp32 ? nullptr : h->rhs, rho, phi_rho, h->stream);
+  return rc ? rc : check_sticky(h);
 }
 
 int pic_profile(pic_handle* h, int enable, pic_kernel_times* out) {

@@ -126,7 +126,7 @@ void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& 
   T.hz = (cfg.z_max - cfg.z_min) / nz;
   T.rtol = cfg.poisson_rtol;
   T.maxit = cfg.poisson_maxit > 0 ? cfg.poisson_maxit : 4;
-  T.warm = cfg.warm_start == 1 ? 1 : 0;
+  T.warm = cfg.warm_start >= 1 ? 1 : 0;
   int l2 = 0;
   while ((1 << l2) < 2 * M) ++l2;
   // FFT path for M a power of two whose 2M-point complex line and its M
@@ -599,6 +599,8 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
       st->relres_last = rel;
       st->relres_strict = strict;
       st->poisson_iters = sweep + 1;
+      if (sweep < 0) st->relres_init = rel;
+      else if (!T.warm) st->relres_init = -1.0;
       if (rel <= T.rtol || last) {
         st->solve_done = 1;
         if (!(rel <= T.rtol)) atomicCAS(&st->err, 0, PIC_ENOCONV);

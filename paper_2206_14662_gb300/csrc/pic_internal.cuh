@@ -59,6 +59,8 @@ struct DevState {
   int solve_done;             // set when the solve has converged
   int pad1;
   long long n_live;           // live count after the last sort / load
+  double relres_init;         // ||r|| / ||b_lifted|| of the last solve's
+                              // initial guess (warm start), -1 if cold
 };
 
 template <typename Real>
@@ -357,5 +359,17 @@ void launch_efield_set(const double* er, const double* ez, void* efield,
 template <typename Real>
 void launch_efield_get(const void* efield, double* out, int component,
                        int nnodes, cudaStream_t stream);
+
+// learned initial guess (unet.cu): network input from the deposit (cnt with
+// per-simulation charge units, or FP64 charges rhs) and phi_rho, forward
+// pass on `stream`, phi_rho += dphi_scale * output on the interior lines
+int warm_start_learned(pic_unet* net, const FieldTables& T, const unsigned long long* cnt,
+                       const double* units, const double* rhs, float* xbuf, float rho_scale,
+                       float phi_scale, float dphi_scale, cudaStream_t stream);
+// (nsim, nr, nz) FP32 images of the deposit's charge and of phi_rho
+int field_images(const FieldTables& T, const unsigned long long* cnt, const double* units,
+                 const double* rhs, float* rho, float* phi, cudaStream_t stream);
+bool unet_fits(const pic_unet* net, int nsim, int nr, int nz);
+int unet_kernels_per_forward(const pic_unet* net);
 
 }  // namespace pic

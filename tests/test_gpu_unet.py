@@ -1,0 +1,191 @@
+"""The U-Net of the learned field-solve warm start, forward and backward
+through the C ABI, against the CPU FP64 oracle (oracle/unet.py): FP32 test
+mode to 1e-5, BF16 tensor-core mode to the BF16 tolerance, on a 16 x 32 grid
+with base width 4 (every layer padded) and on 16 x 64 with base width 32
+(the production widths, full tensor-core tiles)."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+from paper_2206_14662_gb300.inputs import unet_init_flat, unet_layer_shapes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2206_14662_gb300 import build
+    build.build()
+    return torch
+
+
+def _layer_slices(c):
+    out, o = {}, 0
+    for name, shp in unet_layer_shapes(c):
+        k = int(np.prod(shp)) + (1 if name == "head" else shp[-1])
+        out[name] = slice(o, o + k)
+        o += k
+    return out
+
+
+def _case(torch, c, B, H, W, precision, seed=0, q=None, coherent=False):
+    """GPU and oracle outputs, parameter gradients and input gradients for
+    one forward / backward; q the oracle's storage rounding; coherent: the
+    output gradient of the loss against a smooth target instead of noise."""
+    from paper_2206_14662_gb300.unet import UNet
+    flat = unet_init_flat(c, seed=seed, head_std=0.3, bias_std=0.1).astype(np.float32)
+    rng = np.random.default_rng(seed + 7)
+    x = rng.standard_normal((B, H, W, 2)).astype(np.float32)
+    gy = (rng.standard_normal((B, H, W)) / (B * H * W)).astype(np.float32)
+    if coherent:
+        yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+        t = np.sin(2 * np.pi * yy / H) * np.cos(2 * np.pi * xx / W)
+        y0, _ = U.forward(U.unflatten(flat.astype(np.float64), c), x.astype(np.float64))
+        gy = ((y0 - t) / (B * H * W)).astype(np.float32)
+    net = UNet(c, H, W, B, precision=precision)
+    net.set_params(flat)
+    assert np.array_equal(net.get_params(), flat)
+    xd = torch.from_numpy(x).cuda()
+    y = net.forward(xd).cpu().numpy()
+    gx = torch.zeros((B, H, W, 2), dtype=torch.float32, device="cuda")
+    net.backward(torch.from_numpy(gy).cuda(), gx)
+    grads = net.get_grads()
+    net.close()
+    p = U.unflatten(flat.astype(np.float64), c)
+    yo, a = U.forward(p, x.astype(np.float64), q=q)
+    go = U.backward(p, a, gy.astype(np.float64), q=q)
+    return y, yo, grads, U.flatten({k: v for k, v in go.items() if k != "x"}), gx.cpu().numpy(), go["x"]
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("c,H,W", [(4, 16, 32), (32, 16, 64)])
+def test_fp32_mode_matches_oracle(torch, c, H, W):
+    y, yo, g, go, gx, gxo = _case(torch, c, 2, H, W, precision=32)
+    assert np.abs(y - yo).max() <= 1e-5 * np.abs(yo).max()
+    for name, sl in _layer_slices(c).items():
+        assert _rel(g[sl], go[sl]) <= 1e-5, name
+    assert _rel(gx, gxo) <= 1e-5
+
+
+def test_bf16_tensor_core_mode_matches_bf16_rounding_oracle(torch):
+    """Base width 4 (every layer padded to 32 channels, all tensor-core
+    GEMM forms: 3 x 3 forward, data and weight gradients, transposed
+    convolutions, masks): the BF16 path equals the oracle that rounds to
+    BF16 where the GPU stores BF16, up to FP32 accumulation order."""
+    y, yo, g, go, gx, gxo = _case(torch, 4, 2, 16, 32, precision=16, q=U.round_bf16)
+    assert _rel(y, yo) <= 1e-5
+    for name, sl in _layer_slices(4).items():
+        assert _rel(g[sl], go[sl]) <= 1e-5, name
+    assert _rel(gx, gxo) <= 1e-5
+
+
+@pytest.mark.parametrize("H,W", [(16, 64), (32, 64)])
+def test_bf16_tensor_core_mode_production_width(torch, H, W):
+    """Base width 32 (the production widths, full 64-channel tiles, K up to
+    9 x 256): against the FP64 oracle the output agrees to 1e-2 and the
+    gradients of a loss against a smooth target to the BF16 storage
+    tolerance.  The remaining differences are BF16 values one unit apart
+    where the FP32 sum of several thousand products falls on the other side
+    of a rounding boundary than the exact sum; they accumulate through the
+    18 layers (the width-4 case above shows the kernels themselves exact)."""
+    y, yo, g, go, gx, gxo = _case(torch, 32, 2, H, W, precision=16, coherent=True)
+    assert _rel(y, yo) <= 1e-2
+    assert _rel(g, go) <= 2.5e-2
+    y, yo, g, go, gx, gxo = _case(torch, 32, 2, H, W, precision=16, q=U.round_bf16, coherent=True)
+    assert _rel(y, yo) <= 1e-2
+    assert _rel(g, go) <= 1.5e-2
+    assert max(_rel(g[sl], go[sl]) for sl in _layer_slices(32).values()) <= 8e-2
+
+
+def test_training_reduces_the_loss(torch):
+    """Adam on a fixed smooth mapping (the target is a blurred copy of the
+    first input channel): the loss falls by an order of magnitude."""
+    from paper_2206_14662_gb300.unet import UNet
+    B, H, W, c = 4, 32, 64, 8
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((B, H, W, 2)).astype(np.float32)
+    k = np.ones(5) / 5.0
+    t = x[..., 0].copy()
+    for axis in (1, 2):
+        t = np.apply_along_axis(lambda v: np.convolve(v, k, mode="same"), axis, t)
+    net = UNet(c, H, W, B, precision=16)
+    net.set_params(unet_init_flat(c, seed=1).astype(np.float32))
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t.astype(np.float32)).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    for _ in range(300):
+        net.train_step(xd, td, lr=2e-3, loss=loss)
+        hist.append(float(loss.item()))
+    net.close()
+    assert hist[-1] < 0.1 * hist[0], (hist[0], hist[-1])
+
+
+def test_learned_warm_start_with_a_zero_net_is_the_previous_potential(torch):
+    """warm_start = 2 with a net whose output is zero gives, bit for bit,
+    the run refined from the previous potential (graph blocks included)."""
+    from paper_2206_14662_gb300._capi import PIC_GRID_PHI, Simulation
+    from paper_2206_14662_gb300.inputs import seed_particles, workload
+    from paper_2206_14662_gb300.unet import UNet
+    from parity import by_uid
+    out = []
+    for ws in (1, 2):
+        cfg = workload("mirror_128x512_1e7", n_init=30_000, warm_start=ws, sort_every=4)
+        with Simulation(cfg) as sim:
+            sim.load_particles(*seed_particles(cfg))
+            net = None
+            if ws == 2:
+                net = UNet(32, cfg["nr"], cfg["nz"], 1, precision=16)
+                net.set_params(np.zeros(net.n_params, dtype=np.float32))
+                sim.attach_unet(net, 1e-12, 1.0, 1e-3)
+            sim.step(3)
+            sim.step(16)
+            d = sim.diagnostics()
+            out.append((by_uid(sim.export_particles()), sim.get_grid(PIC_GRID_PHI), d))
+            if net is not None:
+                sim.attach_unet(None, 1.0, 1.0, 1.0)
+                net.close()
+    (ga, pa, da), (gb, pb, db) = out
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k]), k
+    assert np.array_equal(pa, pb)
+    # the norms are sums of block partials in arrival order
+    assert db["poisson_relres_init"] == pytest.approx(da["poisson_relres_init"], rel=1e-12)
+    assert da["poisson_relres_init"] > 0
+    assert db["kernels_launched"] > da["kernels_launched"]
+
+
+def test_learned_warm_start_trained_in_the_loop(torch):
+    """Snapshots from a batch of eight randomised simulations of the small
+    workload's physics, a few hundred Adam steps, then the trained net as the
+    initial guess inside the loop: every solve still meets poisson_rtol, and
+    the initial residuals with and without the net are reported."""
+    from paper_2206_14662_gb300 import warmstart
+    from paper_2206_14662_gb300.unet import UNet
+    cfgs = warmstart.snapshot_configs(8, nr=32, nz=64, n_particles=3000, seed=1)
+    rho, phi, dphi = warmstart.collect(cfgs, steps=64, warmup=4)
+    sc = warmstart.scales(rho, phi, dphi)
+    net = UNet(8, 32, 64, 16, precision=16)
+    net.set_params(unet_init_flat(8, seed=2).astype(np.float32))
+    losses, base = warmstart.train(net, rho, phi, dphi, sc, epochs=16, lr=1e-3)
+    losses, base = losses.cpu().numpy(), base.cpu().numpy()
+    # against predicting no change on the same batches, the trained net
+    # explains part of the potential's change
+    assert losses[-64:].mean() < 0.8 * base[-64:].mean()
+    inf = UNet(8, 32, 64, 1, precision=16)
+    inf.set_params(net.get_params())
+    cfg = warmstart.snapshot_configs(1, nr=32, nz=64, n_particles=3000, seed=9)[0]
+    prv = warmstart.evaluate(cfg, 24, warmup=4)
+    lrn = warmstart.evaluate(cfg, 24, inf, sc, warmup=4)
+    net.close()
+    inf.close()
+    for r in (prv, lrn):
+        assert (r["relres"] <= cfg["poisson_rtol"]).all()
+    print(f"initial residual: previous potential {np.median(prv['relres_init']):.3e}, "
+          f"learned {np.median(lrn['relres_init']):.3e}; sweeps {prv['sweeps'].mean():.2f} / "
+          f"{lrn['sweeps'].mean():.2f}; loss / no-change loss {losses[-64:].mean() / base[-64:].mean():.3f}")
