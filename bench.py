@@ -9,6 +9,11 @@ macro-electrons (FP32 particle path, FP64 field), mirror field B0 = 0.3 T,
 ``--workload scan_64x256_64sims`` times the parametric scan instead: 64
 simulations of 64 x 256 cells (pressure x voltage x mirror field, 1e5 to 5e6
 macro-electrons each, 8.15e7 in all) stepped as one batch.
+``--workload unet_warmstart_128x512`` measures the learned field-solve warm
+start: snapshots from 64 randomised simulations of the small workload's
+physics on 128 x 512 cells, the U-Net's training throughput (TFLOP/s on the
+BF16 tensor cores; K timed training steps after W warm-up steps), then the
+trained net inside the loop against the previous-potential initial guess.
 
 Prints one JSON line.  ``value`` is particle-steps/s with the particles
 resident in HBM; ``e2e`` is the same metric through the C ABI from host
@@ -40,6 +45,8 @@ from paper_2206_14662_gb300.inputs import scan_configs, seed_particles, workload
 
 WORKLOAD = "mirror_128x512_1e7"
 SCAN = "scan_64x256_64sims"
+UNET = "unet_warmstart_128x512"
+FALLBACK_BF16_TFLOPS = 1900.0
 METRIC = "particle-steps/s (gather+push+MCC+deposit+field solve)"
 # algorithmic bytes per particle-step of the fused particle kernel (FP32):
 # read cell 4 + offsets 8 + velocity 12 + uid 4, write cell + offsets +
@@ -65,6 +72,19 @@ def _peak_hbm():
     except Exception:
         pass
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def _peak_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("bf16_tflops", "bf16_TFLOPs", "bf16"):
+            if k in d:
+                return float(d[k]), "measured"
+    except Exception:
+        pass
+    return FALLBACK_BF16_TFLOPS, "fallback"
 
 
 def _traffic_record():
@@ -295,6 +315,101 @@ def run_ours(args, ws, rank):
     return out
 
 
+def run_unet(args, ws, rank):
+    """Training throughput of the warm-start U-Net and its effect in the
+    loop (rank 0; other ranks exit)."""
+    if rank != 0:
+        return None
+    import torch
+    from paper_2206_14662_gb300 import warmstart
+    from paper_2206_14662_gb300.inputs import unet_init_flat
+    from paper_2206_14662_gb300.unet import UNet
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    c, H, W, B = 32, 128, 512, 16
+    cfgs = warmstart.snapshot_configs(64, nr=H, nz=W, n_particles=10_000, seed=1)
+    rho, phi, dphi = warmstart.collect(cfgs, steps=64, warmup=20)
+    sc = warmstart.scales(rho, phi, dphi)
+    net = UNet(c, H, W, B, precision=16)
+    net.set_params(unet_init_flat(c, seed=3).astype(np.float32))
+    # fixed mini-batches for the timed steps
+    nb = 8
+    xs = torch.empty((nb, B, H, W, 2), dtype=torch.float32, device="cuda")
+    ts = torch.empty((nb, B, H, W), dtype=torch.float32, device="cuda")
+    for i in range(nb):
+        sl = slice(i * B, (i + 1) * B)
+        xs[i, ..., 0] = rho[sl] / sc[0]
+        xs[i, ..., 1] = phi[sl] / sc[1]
+        ts[i] = dphi[sl] / sc[2]
+    for i in range(args.warmup):
+        net.train_step(xs[i % nb], ts[i % nb], lr=1e-3)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks()
+    clocks.start()
+    ev0.record()
+    for i in range(args.steps):
+        net.train_step(xs[i % nb], ts[i % nb], lr=1e-3)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    tflops = warmstart.train_step_flops(c, H, W, B) / (ms * 1e-3) / 1e12
+    # inference forward alone (batch 1, the in-loop size)
+    inf = UNet(c, H, W, 1, precision=16)
+    x1 = xs[0, :1].contiguous()
+    for _ in range(5):
+        inf.forward(x1)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(50):
+        inf.forward(x1)
+    ev1.record()
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / 50
+    # train on all snapshots, then the A/B inside the loop
+    net.set_params(unet_init_flat(c, seed=3).astype(np.float32))
+    losses, base = warmstart.train(net, rho, phi, dphi, sc, epochs=2, lr=1e-3)
+    losses, base = losses.cpu().numpy(), base.cpu().numpy()
+    inf.set_params(net.get_params())
+    ab = {}
+    for n_part in (10_000, 1_000_000):
+        cfg = warmstart.snapshot_configs(1, nr=H, nz=W, n_particles=n_part, seed=77)[0]
+        prv = warmstart.evaluate(cfg, 50, warmup=20)
+        lrn = warmstart.evaluate(cfg, 50, inf, sc, warmup=20)
+        ab[f"particles_{n_part}"] = {
+            "relres_init_median": {"previous": float(np.median(prv["relres_init"])),
+                                   "learned": float(np.median(lrn["relres_init"]))},
+            "sweeps_mean": {"previous": float(prv["sweeps"].mean()),
+                            "learned": float(lrn["sweeps"].mean())},
+            "relres_max": {"previous": float(prv["relres"].max()),
+                           "learned": float(lrn["relres"].max())}}
+    net.close()
+    inf.close()
+    peak, src = _peak_bf16()
+    return {
+        "metric": "U-Net training throughput (forward + data and weight gradients + Adam)",
+        "value": tflops, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (fp32 accumulation and master weights)",
+        "data": "synthetic (snapshots of seeded simulations)",
+        "config": {"workload": UNET, "base_channels": c, "grid": f"{H}x{W}", "batch": B,
+                   "snapshots": int(rho.shape[0]),
+                   "flop_per_step": warmstart.train_step_flops(c, H, W, B),
+                   "l2": "activations and gradients of a batch exceed L2"},
+        "e2e": None, "gpu_launches": None,
+        "roofline": {"bound": "tensor", "kernel": "k_gemm_fwd / k_gemm_wgrad (mma.sync bf16)",
+                     "achieved": tflops, "peak": peak, "peak_source": src, "unit": "TFLOP/s",
+                     "frac": tflops / peak, "traffic": None},
+        "inference_forward_ms": fwd_ms,
+        "inference_tflops": warmstart.forward_flops(c, H, W) / (fwd_ms * 1e-3) / 1e12,
+        "training": {"epochs": 2, "loss_over_no_change_last64":
+                     float(losses[-64:].mean() / base[-64:].mean())},
+        "warm_start_ab": ab,
+        "clocks": clk,
+    }
+
+
 def cpu_baseline(cfg, parts, n_sample=None, steps=2, name=WORKLOAD):
     """The oracle as it stands (single thread) on a bounded sample: the full
     1e7-particle load and field, ``steps`` steps."""
@@ -319,6 +434,8 @@ def run_reference(args, ws, rank):
     field solve."""
     if rank != 0:
         return None
+    if args.workload == UNET:
+        return run_reference_unet(args, ws)
     import oracle
     oracle.build()
     name = args.workload
@@ -348,12 +465,40 @@ def run_reference(args, ws, rank):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_reference_unet(args, ws):
+    """The FP64 U-Net oracle (numpy) on a bounded sample: forward and
+    backward of one 128 x 512 image per step."""
+    from oracle import unet as U
+    from paper_2206_14662_gb300 import warmstart
+    from paper_2206_14662_gb300.inputs import unet_init_flat
+    c, H, W = 32, 128, 512
+    p = U.unflatten(unet_init_flat(c, seed=3), c)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((1, H, W, 2))
+    steps = max(1, min(args.steps, 2))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        y, a = U.forward(p, x)
+        U.backward(p, a, y / y.size)
+    sec = (time.perf_counter() - t0) / steps
+    v = warmstart.train_step_flops(c, H, W, 1) / sec / 1e12
+    return {"impl": "reference", "metric": "U-Net training throughput (forward + data and "
+            "weight gradients + Adam)", "value": v, "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": steps, "warmup": 0, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": UNET, "batch": 1, "grid": f"{H}x{W}"},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": f"{steps} forward+backward of one image"},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
-    ap.add_argument("--workload", choices=[WORKLOAD, SCAN], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, SCAN, UNET], default=WORKLOAD)
     ap.add_argument("--warm-start", type=int, choices=[0, 1], default=None,
                     help="override the field solve's initial guess (0 zero, 1 previous)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -371,7 +516,12 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
         args.cpu_baseline = args.cpu_baseline and rank == 0 and False
-    out = run_ours(args, ws, rank) if args.impl == "ours" else run_reference(args, ws, rank)
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    elif args.workload == UNET:
+        out = run_unet(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank)
     if out is not None:
         print(json.dumps(out), flush=True)
     if ws > 1 and args.impl == "ours":

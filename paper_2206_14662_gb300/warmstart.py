@@ -114,3 +114,25 @@ def evaluate(cfg: dict, steps: int, net=None, sc=None, seed: int = 0, warmup: in
         if net is not None:
             sim.attach_unet(None, 1.0, 1.0, 1.0)
     return {k: np.array(v) for k, v in out.items()}
+
+
+def forward_flops(c: int, H: int, W: int) -> float:
+    """Multiply-adds x 2 of one forward pass on an H x W image (real
+    channel counts): 3 x 3 layers 18 in out pixels, transposed layers
+    8 in out coarse pixels, the head 2 c pixels."""
+    P = [H * W, H * W // 4, H * W // 16, H * W // 64]
+    w = [c, 2 * c, 4 * c, 8 * c]
+    f = 18.0 * P[0] * (2 * c + c * c)                     # level 1 encoder
+    for k in (1, 2, 3):
+        f += 18.0 * P[k] * (w[k - 1] * w[k] + w[k] * w[k])   # levels 2..4 encoder
+    for k in (2, 1, 0):                                   # decoder levels 3, 2, 1
+        f += 8.0 * P[k + 1] * w[k + 1] * w[k]             # transposed 2 x 2
+        f += 18.0 * P[k] * (2 * w[k] * w[k] + w[k] * w[k])
+    f += 2.0 * P[0] * c
+    return f
+
+
+def train_step_flops(c: int, H: int, W: int, batch: int) -> float:
+    """Forward, data gradients and weight gradients: three times the forward
+    (the first layer's data gradient is not formed; ignored)."""
+    return 3.0 * batch * forward_flops(c, H, W)
