@@ -73,7 +73,7 @@ class _Params(ctypes.Structure):
         ("opal_B_eV", ctypes.c_double), ("xi", ctypes.c_double),
         ("gas_mass_kg", ctypes.c_double), ("weight", ctypes.c_double),
         ("dt", ctypes.c_double), ("nu_max", ctypes.c_double),
-        ("seed", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64), ("T0_eV", ctypes.c_double),
     ]
 
 
@@ -104,6 +104,8 @@ def lib():
         L.or_step.restype = i64
         L.or_kinetic_energy.argtypes = [P, i64, vp, vp, vp]
         L.or_kinetic_energy.restype = d
+        L.or_source.argtypes = [P, i64, u64, u32, vp, vp, vp, vp, vp]
+        L.or_source.restype = None
         _lib = L
     return _lib
 
@@ -138,12 +140,21 @@ def params(cfg: dict) -> _Params:
         ion_sigma_pk=cfg["ion_sigma_pk"], ion_E_pk_eV=cfg["ion_E_pk_eV"],
         opal_B_eV=cfg["opal_B_eV"], xi=cfg["xi_param"],
         gas_mass_kg=d["gas_mass_kg"], weight=d["weight"], dt=cfg["dt"],
-        nu_max=0.0, seed=cfg["seed"])
+        nu_max=0.0, seed=cfg["seed"], T0_eV=cfg.get("T0_eV", 1.0))
     if cfg.get("nu_max", 0.0) > 0:
         p.nu_max = cfg["nu_max"]
     else:
         p.nu_max = lib().or_nu_max(ctypes.byref(p), d["E_cap_eV"])
     return p
+
+
+def source(cfg: dict, k: int, uid0: int, step: int):
+    """k electrons of the volumetric seed source (Sec. II.A) born in step
+    `step` with uids uid0.. (see or_source): arrays r, z, vr, vt, vz."""
+    P = params(cfg)
+    out = [np.zeros(max(k, 1)) for _ in range(5)]
+    lib().or_source(ctypes.byref(P), k, uid0, step & 0xFFFFFFFF, *[_ptr(a) for a in out])
+    return [a[:k] for a in out]
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
@@ -337,6 +348,9 @@ class OracleSim:
         self.step_index = step0
         self.uid_next = int(self.uid.max()) + 1 if uid_next is None and len(self.uid) else (uid_next or 0)
         self.tally = np.zeros(T_COUNT)
+        self.n_source = 0
+        self.ke_source = 0.0  # kinetic energy brought in by the seed source, J
+        self.src_acc = 0.0    # fractional seed-source count carried between steps
         self.solve_field = solve_field
         self.b = deposit(self.cfg, self.r, self.z)
         if efield_nodes is not None:
@@ -385,6 +399,24 @@ class OracleSim:
         self.vz = np.concatenate([self.vz[keep], ch[4][:nc]])
         self.uid = np.concatenate([self.uid[keep], cu[:nc]])
         self.uid_next += int(nc)
+        # volumetric seed source (Sec. II.A): source_rate macro-electrons per
+        # second, whole ones injected, the fraction carried over (FP64)
+        rate = self.cfg.get("source_rate", 0.0)
+        if rate > 0:
+            self.src_acc += rate * self.cfg["dt"]
+            k = int(np.floor(self.src_acc))
+            self.src_acc -= k
+            if k > 0:
+                new = source(self.cfg, k, self.uid_next, self.step_index)
+                b = b + deposit(self.cfg, new[0], new[1])
+                for name, arr in zip(("r", "z", "vr", "vt", "vz"), new):
+                    setattr(self, name, np.concatenate([getattr(self, name), arr]))
+                self.uid = np.concatenate([self.uid, np.arange(self.uid_next, self.uid_next + k,
+                                                               dtype=np.uint64)])
+                self.uid_next += k
+                self.n_source += k
+                self.ke_source += lib().or_kinetic_energy(ctypes.byref(self.P), k, _ptr(new[2]),
+                                                          _ptr(new[3]), _ptr(new[4]))
         self.step_index += 1
         self.tally += tally
         self.b = b
@@ -394,7 +426,8 @@ class OracleSim:
         return StepResult(int(nc), event, margin, b, tally)
 
     def ledger_residual(self) -> float:
-        """KE_now - KE_0 - (W_E - KE_absorbed - ionisation loss - recoil loss)."""
+        """KE_now - KE_0 - (W_E - KE_absorbed - ionisation loss - recoil loss
+        + KE brought in by the seed source)."""
         t = self.tally
         return (self.kinetic_energy() - self.ke0) - (
-            t[T_WORK_E] - t[T_KE_ABSORBED] - t[T_ION_LOSS] - t[T_RECOIL_LOSS])
+            t[T_WORK_E] - t[T_KE_ABSORBED] - t[T_ION_LOSS] - t[T_RECOIL_LOSS] + self.ke_source)

@@ -62,6 +62,7 @@ typedef struct {
   double dt;                        /* s */
   double nu_max;                    /* null-collision majorant, s^-1 */
   uint64_t seed;
+  double T0_eV;                     /* temperature of the seed source, eV */
 } or_params;
 
 /* tally slots (accumulated, doubles) */
@@ -408,6 +409,33 @@ int64_t or_step(const or_params* P, int64_t n, double* r, double* z,
     b[n10 + 1] += qw * fr * fz;
   }
   return nchild;
+}
+
+/* Volumetric seed source (Sec. II.A: electrons created uniformly in space
+ * with a Maxwellian velocity distribution): k new electrons with uids
+ * uid0 .. uid0 + k - 1, born in step `step`.  Each draws from its own
+ * stream: draw 2 gives (u_r, u_z, u_a, u_b), draw 3 gives (u_c, u_d, ., .);
+ *   r = sqrt(a^2 + u_r (b^2 - a^2))      (uniform in the annulus' volume)
+ *   z = z_min + u_z (z_max - z_min)
+ *   vr, vt = vth sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b)
+ *   vz     = vth sqrt(-2 ln u_c) cos 2 pi u_d        (Box-Muller)
+ * with vth = sqrt(e T0 / m_e).  The velocity is that of half step n + 1/2:
+ * the particles first move in step n + 1. */
+void or_source(const or_params* P, int64_t k, uint64_t uid0, uint32_t step,
+               double* r, double* z, double* vr, double* vt, double* vz) {
+  const double a2 = P->r_in * P->r_in, b2 = P->r_out * P->r_out;
+  const double vth = sqrt(OR_E * P->T0_eV / OR_ME);
+  for (int64_t j = 0; j < k; ++j) {
+    double u[4], w[4];
+    or_draw4(P, uid0 + (uint64_t)j, step, 2u, u);
+    or_draw4(P, uid0 + (uint64_t)j, step, 3u, w);
+    r[j] = sqrt(a2 + u[0] * (b2 - a2));
+    z[j] = P->z_min + u[1] * (P->z_max - P->z_min);
+    const double m1 = vth * sqrt(-2.0 * log(u[2]));
+    vr[j] = m1 * cos(2.0 * OR_PI * u[3]);
+    vt[j] = m1 * sin(2.0 * OR_PI * u[3]);
+    vz[j] = vth * sqrt(-2.0 * log(w[0])) * cos(2.0 * OR_PI * w[1]);
+  }
 }
 
 /* total kinetic energy of n macro-electrons, J */

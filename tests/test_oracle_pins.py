@@ -460,3 +460,50 @@ def test_seed_load_statistics():
     for v in (vr, vt, vz):
         assert stats.kstest(v / sig, "norm").pvalue > 1e-3
     assert np.all(uid == np.arange(100_000))
+
+
+# ------------------------------------------------------ seed source (II.A)
+
+def test_seed_source_distribution(oracle_mod):
+    """The volumetric seed source: r^2 uniform on [a^2, b^2] (uniform in
+    volume), z uniform, each velocity component normal with variance
+    e T0 / m_e, components uncorrelated."""
+    oracle = oracle_mod
+    import scipy.stats as ss
+    cfg = workload("coax_32x64_1e4", T0_eV=4.0)
+    k = 20000
+    r, z, vr, vt, vz = oracle.source(cfg, k, uid0=123, step=7)
+    a, b = cfg["r_in"], cfg["r_out"]
+    assert (r > a).all() and (r < b).all()
+    assert (z > cfg["z_min"]).all() and (z < cfg["z_max"]).all()
+    assert ss.kstest((r * r - a * a) / (b * b - a * a), "uniform").pvalue > 1e-3
+    assert ss.kstest((z - cfg["z_min"]) / (cfg["z_max"] - cfg["z_min"]), "uniform").pvalue > 1e-3
+    vth = np.sqrt(oracle.QE * 4.0 / oracle.ME)
+    for v in (vr, vt, vz):
+        assert ss.kstest(v / vth, "norm").pvalue > 1e-3
+    c = np.corrcoef(np.vstack([vr, vt, vz, r, z]))
+    assert np.abs(c - np.eye(5)).max() < 4.0 / np.sqrt(k)
+
+
+def test_seed_source_streams_and_counts(oracle_mod):
+    """Source particles depend only on (seed, uid, step): the same call
+    repeats, another step or uid differs; OracleSim injects
+    floor(rate dt steps) particles (the fraction carried in FP64) with
+    consecutive uids after the loaded ones, and the energy ledger accounts
+    for the energy they bring."""
+    oracle = oracle_mod
+    cfg = workload("coax_32x64_1e4", fixed_efield=1, p_mbar=0.0)
+    x1 = oracle.source(cfg, 5, 40, 3)
+    assert all(np.array_equal(p, q) for p, q in zip(x1, oracle.source(cfg, 5, 40, 3)))
+    assert not np.array_equal(x1[0], oracle.source(cfg, 5, 40, 4)[0])
+    assert np.array_equal(x1[0][1:], oracle.source(cfg, 4, 41, 3)[0])
+    cfg["source_rate"] = 0.37 / cfg["dt"]
+    parts = seed_particles(cfg, n=50, margin_cells=4)
+    nn = (cfg["nr"] + 1) * (cfg["nz"] + 1)
+    o = oracle.OracleSim(cfg, *parts, efield_nodes=(np.zeros(nn), np.zeros(nn)), solve_field=False)
+    for _ in range(100):
+        o.step()
+    assert abs(o.n_source - 37) <= 1
+    assert np.array_equal(np.sort(o.uid)[-o.n_source:] if o.n_source else [],
+                          np.arange(50, 50 + o.n_source, dtype=np.uint64))
+    assert abs(o.ledger_residual()) <= 1e-12 * max(o.kinetic_energy(), 1e-30) + 1e-25
