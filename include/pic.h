@@ -75,7 +75,7 @@ typedef struct pic_config {
   double gas_mass_amu;     /* neutral mass M, u */
   int64_t n_init;          /* macro-electrons of the seed load */
   double n0;               /* seed density, m^-3 (macro weight source) */
-  double T0_eV;            /* seed temperature (informational), eV */
+  double T0_eV;            /* temperature of the seed source, eV */
   double weight;           /* electrons per macro-electron; 0 derives
                               n0 pi (b^2 - a^2) L / n_init */
   double dt;               /* s */
@@ -97,6 +97,9 @@ typedef struct pic_config {
                               space-charge potential, 2 the learned guess
                               of an attached net (pic_attach_unet; the
                               previous potential until one is attached) */
+  double source_rate;      /* volumetric seed source (Sec. II.A): macro-
+                              electrons created per second, uniform in the
+                              gap's volume, Maxwellian at T0_eV; 0 off */
 } pic_config;
 
 /* Diagnostics of one simulation (Sec. III.A: peak density and boundary
@@ -134,6 +137,12 @@ typedef struct pic_diag {
   double poisson_relres_init;    /* residual of the last solve's initial
                                     guess (warm starts), measured as
                                     poisson_relres; -1 after a cold start */
+  int64_t n_source;              /* cumulative seed-source particles */
+  double ke_source_J;            /* cumulative kinetic energy they brought
+                                    (in the ledger: ledger_residual_J =
+                                    ke_total - ke_initial - (work_E -
+                                    ke_absorbed - ion_loss - recoil_loss +
+                                    ke_source)) */
 } pic_diag;
 
 typedef struct pic_handle pic_handle;

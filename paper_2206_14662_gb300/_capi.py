@@ -32,7 +32,7 @@ class PicConfig(ctypes.Structure):
         ("n0", c_d), ("T0_eV", c_d), ("weight", c_d), ("dt", c_d),
         ("sort_every", c_i32), ("poisson_rtol", c_d), ("poisson_maxit", c_i32),
         ("capacity", c_i64), ("seed", c_u64), ("precision", c_i32),
-        ("nu_max", c_d), ("fixed_efield", c_i32), ("warm_start", c_i32),
+        ("nu_max", c_d), ("fixed_efield", c_i32), ("warm_start", c_i32), ("source_rate", c_d),
     ]
 
 
@@ -49,6 +49,7 @@ class PicDiag(ctypes.Structure):
         ("ledger_residual_J", c_d), ("n_peak", c_d), ("poisson_iters", c_i32),
         ("poisson_relres", c_d), ("poisson_relres_charge", c_d), ("nu_max", c_d),
         ("weight", c_d), ("error", c_i32), ("poisson_relres_init", c_d),
+        ("n_source", c_i64), ("ke_source_J", c_d),
     ]
 
 

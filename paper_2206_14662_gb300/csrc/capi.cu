@@ -59,6 +59,7 @@ struct pic_handle {
   long long capacity;             // slots of all segments
   long long spawn_stride;         // spawn records per simulation
   int nnodes, ncells, grid_particle, grid_sort;
+  bool any_source;                // some simulation has a seed source
 
   // device memory
   DevState* st;                   // nsim entries
@@ -164,6 +165,8 @@ int validate(const pic_config& c) {
   if (c.sort_every < 0 || c.capacity < 0) return PIC_EINVAL;
   if (!(c.poisson_rtol > 0) || c.poisson_maxit < 0 || c.poisson_maxit > 64) return PIC_EINVAL;
   if (c.warm_start < 0 || c.warm_start > 2) return PIC_EINVAL;
+  if (!(c.source_rate >= 0) || !std::isfinite(c.source_rate)) return PIC_EINVAL;
+  if (c.source_rate > 0 && !(c.T0_eV > 0)) return PIC_EINVAL;
   // the Thomas sweep keeps four (nr - 1) x 32 float columns in shared memory
   if ((long long)4 * (c.nr - 1) * 32 * 4 > 200 * 1024) return PIC_EINVAL;
   if ((long long)(c.nr + 1) * (c.nz + 1) > (1ll << 30)) return PIC_EINVAL;
@@ -224,6 +227,10 @@ void fill_params(pic_handle* h, int k, PushParams<Real>& P) {
   P.capacity = m.capacity;
   P.spawn_cap = m.spawn_cap;
   P.base = m.base;
+  P.src_per_step = c.source_rate > 0 ? c.source_rate * c.dt : 0.0;
+  P.vth_src = std::sqrt(kQe * c.T0_eV / kMe);
+  P.r_out_d = c.r_out;
+  P.z_max_d = c.z_max;
   P.r_in_d = c.r_in;
   P.hr_d = h->hr;
   P.z_min_d = c.z_min;
@@ -314,6 +321,12 @@ int step_impl(pic_handle* h, long long nsteps) {
       launch_spawn_finalize(h->st, soa<Real>(h, h->cur).uid, h->spawn_parent,
                             h->sims[0].spawn_cap, h->sims[0].capacity, h->stream);
     h->kernels += 2;
+    if (h->any_source) {
+      launch_source<Real>(soa<Real>(h, h->cur), h->st, params_dev<Real>(h), h->nsim,
+                          fp32 ? nullptr : h->rhs, fp32 ? h->cnt[h->dep_buf] : nullptr,
+                          h->nnodes, h->stream);
+      h->kernels += 1;
+    }
     mark(h, kTagFinalize);
     ++h->step;
     if (h->cfg.sort_every > 0 && h->step % h->cfg.sort_every == 0) {
@@ -477,6 +490,8 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   }
   h->capacity = base;
   h->spawn_stride = spawn_stride;
+  h->any_source = false;
+  for (const pic_config& ck : h->cfgs) h->any_source = h->any_source || ck.source_rate > 0;
   if (h->capacity > (1ll << 31) - 1) { delete h; return PIC_EINVAL; }
   h->nnodes = (c.nr + 1) * (c.nz + 1);
   h->ncells = c.nr * c.nz;
@@ -845,8 +860,11 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
   out->ion_loss_J = s.tally[kIonLoss];
   out->recoil_loss_J = s.tally[kRecoilLoss];
   out->ke_initial_J = m.ke_initial;
+  out->n_source = (int64_t)s.tally[kNSource];
+  out->ke_source_J = s.tally[kKeSource];
   out->ledger_residual_J = (out->ke_total_J - m.ke_initial) -
-                           (out->work_E_J - out->ke_absorbed_J - out->ion_loss_J - out->recoil_loss_J);
+                           (out->work_E_J - out->ke_absorbed_J - out->ion_loss_J -
+                            out->recoil_loss_J + out->ke_source_J);
   out->poisson_iters = s.poisson_iters;
   out->poisson_relres = s.relres_last;
   out->poisson_relres_charge = s.relres_strict;

@@ -746,6 +746,103 @@ void launch_spawn_finalize_batch(DevState* st, unsigned* uid, const unsigned* pa
   k_spawn_finalize<<<nsim, 1024, 0, stream>>>(st, uid, parent, 0, 0, seg, spawn_stride);
 }
 
+// ---------------------------------------------------------- seed source
+
+// Volumetric seed source (Sec. II.A: electrons created uniformly in space
+// with a Maxwellian velocity distribution), one block per simulation, after
+// the child uids of step n: src_acc += src_per_step, k = floor(src_acc)
+// whole particles are appended with uids uid_next .. uid_next + k - 1.
+// Each draws from its own stream (uid, uid_hi, n, draw): draw 2 gives
+// (u_r, u_z, u_a, u_b), draw 3 (u_c, u_d, ., .);
+//   r = sqrt(a^2 + u_r (b^2 - a^2)), z = z_min + u_z L,
+//   (vr, vt) = vth sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b),
+//   vz = vth sqrt(-2 ln u_c) cos 2 pi u_d,
+// evaluated in FP64 (a handful of particles per step), stored in the
+// particle precision and deposited in this step's charge.
+template <typename Real>
+__global__ void k_source(Soa<Real> s_all, DevState* st_all, const PushParams<Real>* params,
+                         double* rhs_all, unsigned long long* cnt_all, int nnodes) {
+  const int sim = blockIdx.x;
+  const PushParams<Real>& P = params[sim];
+  if (!(P.src_per_step > 0.0)) return;
+  DevState* st = st_all + sim;
+  __shared__ long long s_k, s_base;
+  __shared__ unsigned s_uid0, s_step;
+  __shared__ double s_ke[32];
+  if (threadIdx.x == 0) {
+    double acc = st->src_acc + P.src_per_step;
+    long long k = (long long)floor(acc);
+    acc -= (double)k;
+    const long long n = st->n_slots;
+    if (n + k > P.capacity || st->uid_next + (unsigned long long)k > 0xFFFFFFFFull) {
+      atomicCAS(&st->err, 0, PIC_ECAPACITY);
+      k = 0;
+    }
+    st->src_acc = acc;
+    s_k = k;
+    s_base = n;
+    s_uid0 = (unsigned)st->uid_next;
+    s_step = st->step - 1u;   // the step whose child uids were just fixed
+    st->n_slots = n + k;
+    st->uid_next += (unsigned long long)k;
+    if (k > 0) st->tally[kNSource] += (double)k;
+  }
+  if (threadIdx.x < 32) s_ke[threadIdx.x] = 0.0;
+  __syncthreads();
+  const long long k = s_k;
+  const Soa<Real> s = soa_offset(s_all, P.base);
+  const size_t go = (size_t)sim * nnodes;
+  const DepGrid g{rhs_all ? rhs_all + go : nullptr, cnt_all ? cnt_all + go : nullptr, P.nz + 1,
+                  P.qw};
+  const double a2 = P.r_in_d * P.r_in_d, b2 = P.r_out_d * P.r_out_d;
+  double ke = 0.0;
+  for (long long j = threadIdx.x; j < k; j += blockDim.x) {
+    const unsigned uid = s_uid0 + (unsigned)j;
+    const uint4 x = philox4x32_10_rk(make_uint4(uid, P.uid_hi, s_step, 2u), P.rk0, P.rk1);
+    const uint4 w = philox4x32_10_rk(make_uint4(uid, P.uid_hi, s_step, 3u), P.rk0, P.rk1);
+    const double r = sqrt(a2 + u01<double>(x.x) * (b2 - a2));
+    const double z = P.z_min_d + u01<double>(x.y) * (P.z_max_d - P.z_min_d);
+    const double m1 = P.vth_src * sqrt(-2.0 * log(u01<double>(x.z)));
+    double sn, cs;
+    sincospi(2.0 * u01<double>(x.w), &sn, &cs);
+    const double vz = P.vth_src * sqrt(-2.0 * log(u01<double>(w.x))) * cospi(2.0 * u01<double>(w.y));
+    const double sr = (r - P.r_in_d) / P.hr_d, sz = (z - P.z_min_d) / P.hz_d;
+    int ir = (int)floor(sr), iz = (int)floor(sz);
+    ir = min(max(ir, 0), P.nr - 1);
+    iz = min(max(iz, 0), P.nz - 1);
+    Real fr = (Real)(sr - ir), fz = (Real)(sz - iz);
+    if (fr >= Real(1)) fr = nextafter(Real(1), Real(0));
+    if (fz >= Real(1)) fz = nextafter(Real(1), Real(0));
+    if (fr < Real(0)) fr = 0;
+    if (fz < Real(0)) fz = 0;
+    const long long slot = s_base + j;
+    const Real vr = (Real)(m1 * cs), vt = (Real)(m1 * sn), vzr = (Real)vz;
+    s.cell[slot] = (ir << 16) | iz;
+    s.offr[slot] = fr;
+    s.offz[slot] = fz;
+    s.vr[slot] = vr;
+    s.vt[slot] = vt;
+    s.vz[slot] = vzr;
+    s.uid[slot] = uid;
+    deposit_global(g, ir, iz, fr, fz);
+    ke += (double)vr * vr + (double)vt * vt + (double)vzr * vzr;
+  }
+  for (int o = 16; o > 0; o >>= 1) ke += __shfl_xor_sync(0xffffffffu, ke, o);
+  if ((threadIdx.x & 31) == 0) s_ke[threadIdx.x >> 5] = ke;
+  __syncthreads();
+  if (threadIdx.x == 0 && k > 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_ke[i];
+    st->tally[kKeSource] += 0.5 * kMe * t * P.weight;
+  }
+}
+
+template <typename Real>
+void launch_source(const Soa<Real>& s, DevState* st, const PushParams<Real>* params, int nsim,
+                   double* rhs, unsigned long long* cnt, int nnodes, cudaStream_t stream) {
+  k_source<Real><<<nsim, 256, 0, stream>>>(s, st, params, rhs, cnt, nnodes);
+}
+
 // ------------------------------------------------------------------ load
 
 template <typename Real>
@@ -924,7 +1021,9 @@ void launch_efield_get(const void* efield, double* out, int component,
                                          cudaStream_t);                                 \
   template void launch_efield_set<R>(const double*, const double*, void*, int,          \
                                      cudaStream_t);                                     \
-  template void launch_efield_get<R>(const void*, double*, int, int, cudaStream_t);
+  template void launch_efield_get<R>(const void*, double*, int, int, cudaStream_t);       \
+  template void launch_source<R>(const Soa<R>&, DevState*, const PushParams<R>*, int,    \
+                                 double*, unsigned long long*, int, cudaStream_t);
 
 PIC_INSTANTIATE(float)
 PIC_INSTANTIATE(double)

@@ -36,6 +36,8 @@ enum Tally {
   kRecoilLoss,     // elastic recoil loss, J
   kNElastic, kNIonise, kNAbsorbed, kNOver, kNCandidate,
   kNPushed,        // particle-steps taken (live particles advanced)
+  kNSource,        // particles created by the seed source
+  kKeSource,       // their kinetic energy, J
   kTallyCount
 };
 
@@ -61,6 +63,7 @@ struct DevState {
   long long n_live;           // live count after the last sort / load
   double relres_init;         // ||r|| / ||b_lifted|| of the last solve's
                               // initial guess (warm start), -1 if cold
+  double src_acc;             // fractional seed-source count carried over
 };
 
 template <typename Real>
@@ -110,6 +113,9 @@ struct PushParams {
   long long spawn_cap;        // children per step
   long long base;             // first slot of the simulation's segment of the
                               // store (0 for a single run)
+  double src_per_step;        // seed source: macro-electrons per step
+  double vth_src;             // sqrt(e T0 / m_e), m/s
+  double r_out_d, z_max_d;
   // grid geometry in FP64 for converting absolute positions to and from
   // (cell, offset) at load and export
   double r_in_d, hr_d, z_min_d, hz_d;
@@ -325,6 +331,11 @@ void launch_particle_step_batch(const Soa<Real>& s, const void* efield, double* 
                                 unsigned* spawn_parent, long long spawn_stride,
                                 const PushParams<Real>* params, int nsim, int nnodes,
                                 int grid, cudaStream_t stream);
+// seed source of every simulation with src_per_step > 0 (after the child
+// uids, before the sort and the field solve)
+template <typename Real>
+void launch_source(const Soa<Real>& s, DevState* st, const PushParams<Real>* params, int nsim,
+                   double* rhs, unsigned long long* cnt, int nnodes, cudaStream_t stream);
 void launch_spawn_finalize_batch(DevState* st, unsigned* uid, const unsigned* parent,
                                  long long spawn_stride, const SegInfo* seg, int nsim,
                                  cudaStream_t stream);

@@ -36,6 +36,7 @@ _BASE = dict(
     seed=1,
     precision=32,
     nu_max=0.0,
+    source_rate=0.0,
 )
 
 #: The synthetic workloads.  ``steps`` is the length of the run the workload

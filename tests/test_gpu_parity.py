@@ -411,3 +411,44 @@ def test_warm_start_sweeps_and_residual():
     assert (r0 <= 1e-8).all() and (r1 <= 1e-8).all()
     assert (s1 <= s0).all()
     assert np.abs(p1 - p0).max() <= 1e-9 * np.abs(p0).max()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_seed_source_matches_oracle(precision):
+    """The volumetric seed source (Sec. II.A) in a fixed field with
+    collisions and a sort every two steps: the created particles (uids after
+    the children), their motion, the charge and the energy ledger follow the
+    oracle."""
+    from paper_2206_14662_gb300._capi import PIC_GRID_RHS
+    cfg = _collision_cfg(precision, n_init=3000, sort_every=2, T0_eV=20.0,
+                         source_rate=37.3 / 1e-12)
+    parts = seed_particles(cfg, n=3000, seed=5)
+    er, ez = random_field_node_arrays(cfg, 2e5, seed=6)
+    o = oracle.OracleSim(cfg, *parts, efield_nodes=(er, ez), solve_field=False)
+    sim = make_gpu(cfg, parts, efield=(er, ez))
+    for _ in range(6):
+        o.step()
+    sim.step(6)
+    g = by_uid(sim.export_particles())
+    b = sim.get_grid(PIC_GRID_RHS)
+    d = sim.diagnostics()
+    sim.close()
+    assert d["n_source"] == o.n_source == 6 * 37 + 1
+    if precision == 64:
+        compare_states(cfg, 64, g, o, tol=1e-10)
+        assert np.abs(b - o.b).max() <= 1e-10 * np.abs(o.b).max()
+    else:
+        # FP32: a wall or collision decision within rounding of its threshold
+        # may go the other way in six steps; compare the common particles
+        keep = np.isin(o.uid, g["uid"])
+        assert keep.mean() > 0.998 and np.isin(g["uid"], o.uid).mean() > 0.998
+        gi = np.searchsorted(g["uid"], o.uid[keep])
+        hr = (cfg["r_out"] - cfg["r_in"]) / cfg["nr"]
+        vmax = np.abs(o.vr).max()
+        assert np.abs(g["r"][gi] - o.r[keep]).max() / hr <= 2e-5
+        assert np.abs(g["vz"][gi] - o.vz[keep]).max() / vmax <= 2e-5
+        src = o.uid >= 3000 + 0   # created particles and children
+        assert np.isin(o.uid[src], g["uid"]).mean() > 0.99
+    assert d["ke_source_J"] == pytest.approx(o.ke_source, rel=1e-12 if precision == 64 else 1e-6)
+    scale = max(d["ke_total_J"], d["ke_source_J"])
+    assert abs(d["ledger_residual_J"]) <= (1e-10 if precision == 64 else 1e-4) * scale
