@@ -14,6 +14,10 @@ start: snapshots from 64 randomised simulations of the small workload's
 physics on 128 x 512 cells, the U-Net's training throughput (TFLOP/s on the
 BF16 tensor cores; K timed training steps after W warm-up steps), then the
 trained net inside the loop against the previous-potential initial guess.
+``--workload time_to_steady_64sims`` measures the wall time to steady state
+of the 64-simulation scan at up-scaled pressure with a seed source, in the
+batched FP32 form and in the plain FP64 form (one simulation after another,
+cold-started solves); --steps is the step cap per simulation.
 
 Prints one JSON line.  ``value`` is particle-steps/s with the particles
 resident in HBM; ``e2e`` is the same metric through the C ABI from host
@@ -46,6 +50,7 @@ from paper_2206_14662_gb300.inputs import scan_configs, seed_particles, workload
 WORKLOAD = "mirror_128x512_1e7"
 SCAN = "scan_64x256_64sims"
 UNET = "unet_warmstart_128x512"
+STEADY = "time_to_steady_64sims"
 FALLBACK_BF16_TFLOPS = 1900.0
 METRIC = "particle-steps/s (gather+push+MCC+deposit+field solve)"
 # algorithmic bytes per particle-step of the fused particle kernel (FP32):
@@ -410,6 +415,56 @@ def run_unet(args, ws, rank):
     }
 
 
+def steady_configs():
+    """The scan's 4 x 4 x 4 grid of voltage and field with the pressures
+    scaled up to 1e-2 .. 1e-1 mbar (collision times of 30 to 700 steps),
+    2e3 to 1e5 macro-electrons per simulation, room for 40 times the load,
+    and a seed source of 1% of the initial load per collision time."""
+    cfgs = scan_configs(n_sims=64, n_min=2_000, n_max=100_000)
+    P = (1e-2, 2.15e-2, 4.64e-2, 1e-1)
+    for k, c in enumerate(cfgs):
+        c["p_mbar"] = P[(k // 16) % 4]
+        c["capacity"] = 40 * c["n_init"] + 4096
+    return cfgs
+
+
+def run_steady(args, ws, rank):
+    if rank != 0:
+        return None
+    import torch
+    from paper_2206_14662_gb300 import steady
+    from paper_2206_14662_gb300._capi import Simulation
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfgs = steady_configs()
+    with Simulation(cfgs) as sim:
+        nus = [sim.diagnostics(sim=k)["nu_max"] for k in range(len(cfgs))]
+    for c, nu in zip(cfgs, nus):
+        c["source_rate"] = 0.01 * c["n_init"] * nu
+    res = {}
+    for form in ("batched", "plain"):
+        sec, st, pushed = steady.time_to_steady(cfgs, form, cap_steps=args.steps)
+        done = [x for x in st if x is not None]
+        res[form] = {"seconds": sec, "steady": len(done), "of": len(cfgs),
+                     "median_steady_step": float(np.median(done)) if done else None,
+                     "particle_steps": int(pushed),
+                     "particle_steps_per_s": pushed / sec}
+    b, p = res["batched"], res["plain"]
+    return {
+        "metric": "time to steady state, 64-simulation scan (batched FP32 vs plain FP64)",
+        "value": b["seconds"], "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": 0,
+        "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 particles / f64 field (batched); f64 (plain)",
+        "data": "synthetic (seeded loads, seed source)",
+        "config": {"workload": STEADY, "simulations": len(cfgs), "grid": "64 x 64x256",
+                   "pressures_mbar": [1e-2, 2.15e-2, 4.64e-2, 1e-1],
+                   "particles_min_max": [2000, 100000], "cap_steps": args.steps,
+                   "detector": "window means of N, n_max, I_outer; two consecutive windows "
+                               "within 2%; window max(2000 steps, 5/nu_max)"},
+        "forms": res, "speedup": p["seconds"] / b["seconds"],
+        "note": "simulations not steady by the cap count with the cap",
+    }
+
+
 def cpu_baseline(cfg, parts, n_sample=None, steps=2, name=WORKLOAD):
     """The oracle as it stands (single thread) on a bounded sample: the full
     1e7-particle load and field, ``steps`` steps."""
@@ -498,7 +553,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
-    ap.add_argument("--workload", choices=[WORKLOAD, SCAN, UNET], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, SCAN, UNET, STEADY], default=WORKLOAD)
     ap.add_argument("--warm-start", type=int, choices=[0, 1], default=None,
                     help="override the field solve's initial guess (0 zero, 1 previous)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -520,6 +575,8 @@ def main():
         out = run_reference(args, ws, rank)
     elif args.workload == UNET:
         out = run_unet(args, ws, rank)
+    elif args.workload == STEADY:
+        out = run_steady(args, ws, rank)
     else:
         out = run_ours(args, ws, rank)
     if out is not None:
