@@ -197,6 +197,7 @@ def run_ours(args, ws, rank):
     for k in range(S):
         sim.load_particles(*pinned[k], sim=k)
     sim.step(args.warmup)
+    tune = sim.autotune(80) if args.autotune else None   # schedule, untimed
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -263,14 +264,16 @@ def run_ours(args, ws, rank):
     nnodes = (cfg["nr"] + 1) * (cfg["nz"] + 1)
     if S == 1:
         config = {"workload": name if not args.particles else f"{name} (particles={n0})",
-                  "particles": n0, "grid": grid, "sort_every": cfg["sort_every"],
+                  "particles": n0, "grid": grid,
+                  "sort_every": tune["sort_every"] if tune else cfg["sort_every"],
                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                   "l2": "inputs larger than L2 (particle store 520 MB per step)"}
     else:
         config = {"workload": name, "simulations": S, "particles": n0,
                   "particles_min_max": [min(len(p[0]) for p in parts),
                                         max(len(p[0]) for p in parts)],
-                  "grid": f"{S} x {grid}", "sort_every": cfg["sort_every"],
+                  "grid": f"{S} x {grid}",
+                  "sort_every": tune["sort_every"] if tune else cfg["sort_every"],
                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU, one batch",
                   "l2": f"inputs larger than L2 (particle store {n0 * 52 / 1e9:.1f} GB per step)"}
     out = {
@@ -309,6 +312,7 @@ def run_ours(args, ws, rank):
                     "relres_charge": d1["poisson_relres_charge"],
                     "warm_start": cfg.get("warm_start", 0)},
         "clocks": clk,
+        "schedule": tune,
     }
     if args.cpu_baseline:
         if S == 1:
@@ -554,6 +558,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--workload", choices=[WORKLOAD, SCAN, UNET, STEADY], default=WORKLOAD)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the workload's sort period and the default kernel grid")
     ap.add_argument("--warm-start", type=int, choices=[0, 1], default=None,
                     help="override the field solve's initial guess (0 zero, 1 previous)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")

@@ -369,6 +369,24 @@ int pic_unet_train_step(pic_unet* net, const float* x, const float* target,
 int pic_attach_unet(pic_handle* h, pic_unet* net, double rho_scale,
                     double phi_scale, double dphi_scale);
 
+/* Schedule autotuner: tries sort periods {5, 10, 20, 40, 80} x fused-
+ * kernel grids {1 .. resident blocks per SM} x SMs on the running
+ * simulation, each over steps_per_trial steps (rounded up to a multiple of
+ * 80) after an untimed graph block, times them with CUDA events on the
+ * handle's stream and keeps the fastest (it replaces cfg.sort_every).  The
+ * trials are ordinary steps: the simulation advances by all of them, and
+ * its particles do not depend on the schedule (bit for bit in the FP32
+ * path; in the FP64 path up to the order of the FP64 deposit sums).
+ * Synchronises.  This library's addition; the paper has no counterpart. */
+typedef struct pic_tune_result {
+  int32_t sort_every;            /* chosen sort period, steps */
+  int32_t particle_blocks;       /* chosen persistent grid of the fused
+                                    kernel, blocks */
+  double ms_per_step;            /* its measured time per step */
+  int32_t trials;                /* candidates timed */
+} pic_tune_result;
+int pic_autotune(pic_handle* h, int64_t steps_per_trial, pic_tune_result* out);
+
 /* Images of the current field state of every simulation, FP32 DEVICE
  * arrays of n_sims x nr x nz pixels in the net's layout (pixel (s, y, x) =
  * node (y + 1, x) of simulation s): the last deposit's node charge (C) and

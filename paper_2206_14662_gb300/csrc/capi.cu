@@ -59,6 +59,7 @@ struct pic_handle {
   long long capacity;             // slots of all segments
   long long spawn_stride;         // spawn records per simulation
   int nnodes, ncells, grid_particle, grid_sort;
+  int sms, blocks_per_sm;         // device SMs, resident fused-kernel blocks
   bool any_source;                // some simulation has a seed source
 
   // device memory
@@ -252,6 +253,23 @@ int alloc_soa(pic_handle* h, Soa<Real>& s) {
   s.uid = (unsigned*)al(n * sizeof(unsigned));
   if (!s.cell || !s.offr || !s.offz || !s.vr || !s.vt || !s.vz || !s.uid) return PIC_ENOMEM;
   return PIC_OK;
+}
+
+// A graph block returns the alternating buffers (sort ping-pong, FP32
+// deposit buffers) to a fixed pattern: lcm(sort_every, 2) steps, at least 8.
+void set_graph_len(pic_handle* h) {
+  const int se = h->cfg.sort_every;
+  h->graph_len = se > 0 ? (se % 2 == 0 ? se : 2 * se) : 2;
+  while (h->graph_len < 8) h->graph_len *= 2;
+}
+
+void drop_graphs(pic_handle* h) {
+  for (auto& row : h->graph)
+    for (auto& x : row)
+      if (x) {
+        cudaGraphExecDestroy(x);
+        x = nullptr;
+      }
 }
 
 // profiling: an event on the stream tagged with the stage that just ended
@@ -505,6 +523,8 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   }
   const bool batch = n_sims > 1;
   const int bps = std::max(1, particle_step_blocks_per_sm(h->prec, batch));
+  h->sms = sms;
+  h->blocks_per_sm = bps;
   const long long chunks = (h->capacity + 1023) / 1024;
   h->grid_particle = (int)std::max<long long>(1, std::min<long long>((long long)sms * bps, chunks));
   h->grid_sort = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8,
@@ -591,13 +611,7 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   // the last deposit is in cnt[last_buf], the next goes to cnt[dep_buf]
   h->last_buf = 0;
   h->dep_buf = c.fixed_efield ? 0 : 1;
-  {
-    // a graph block returns the alternating buffers (sort ping-pong, FP32
-    // deposit buffers) to a fixed pattern: lcm(sort_every, 2) steps
-    const int se = c.sort_every;
-    h->graph_len = se > 0 ? (se % 2 == 0 ? se : 2 * se) : 2;
-    while (h->graph_len < 8) h->graph_len *= 2;
-  }
+  set_graph_len(h);
   *out = h;
   return PIC_OK;
 }
@@ -1182,13 +1196,66 @@ int pic_attach_unet(pic_handle* h, pic_unet* net, double rho_scale, double phi_s
   h->ws_scale[1] = (float)phi_scale;
   h->ws_scale[2] = (float)dphi_scale;
   // captured step blocks do not contain the net's launches: capture again
-  for (auto& row : h->graph)
-    for (auto& x : row)
-      if (x) {
-        cudaGraphExecDestroy(x);
-        x = nullptr;
-      }
+  drop_graphs(h);
   return PIC_OK;
+}
+
+// Schedule autotuner: the sort period and the fused kernel's persistent
+// grid are tried on the running simulation (particle states do not depend
+// on either: every particle's arithmetic is fixed, the FP32 deposit is an
+// integer sum, child uids go by parent rank), each candidate timed with
+// events over whole graph blocks; the fastest is kept.
+int pic_autotune(pic_handle* h, int64_t steps_per_trial, pic_tune_result* out) {
+  if (!h || !out || steps_per_trial < 1) return PIC_EINVAL;
+  if (h->sticky) return h->sticky;
+  std::memset(out, 0, sizeof(*out));
+  const int sort_cand[] = {5, 10, 20, 40, 80};
+  std::vector<int> grid_cand;
+  for (int b = 1; b <= h->blocks_per_sm; ++b) grid_cand.push_back(h->sms * b);
+  const long long trial = (steps_per_trial + 79) / 80 * 80;   // whole periods of every candidate
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int best_se = h->cfg.sort_every, best_grid = h->grid_particle;
+  int rc = PIC_OK;
+  for (int se : sort_cand) {
+    for (int grid : grid_cand) {
+      h->cfg.sort_every = se;
+      for (pic_config& c : h->cfgs) c.sort_every = se;
+      h->grid_particle = grid;
+      set_graph_len(h);
+      drop_graphs(h);
+      // align to a graph block and capture, untimed
+      rc = pic_step(h, h->graph_len + (h->graph_len - h->step % h->graph_len) % h->graph_len);
+      if (rc) break;
+      if (cudaEventRecord(e0, h->stream) != cudaSuccess) { rc = PIC_ECUDA; break; }
+      rc = pic_step(h, trial);
+      if (rc) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, h->stream) != cudaSuccess ||
+          cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = PIC_ECUDA;
+        break;
+      }
+      ++out->trials;
+      const double per = ms / (double)trial;
+      if (per < best) { best = per; best_se = se; best_grid = grid; }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->cfg.sort_every = best_se;
+  for (pic_config& c : h->cfgs) c.sort_every = best_se;
+  h->grid_particle = best_grid;
+  set_graph_len(h);
+  drop_graphs(h);
+  out->sort_every = best_se;
+  out->particle_blocks = best_grid;
+  out->ms_per_step = best;
+  return rc ? rc : check_sticky(h);
 }
 
 int pic_field_images(pic_handle* h, float* rho, float* phi_rho) {

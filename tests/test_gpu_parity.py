@@ -452,3 +452,27 @@ def test_seed_source_matches_oracle(precision):
     assert d["ke_source_J"] == pytest.approx(o.ke_source, rel=1e-12 if precision == 64 else 1e-6)
     scale = max(d["ke_total_J"], d["ke_source_J"])
     assert abs(d["ledger_residual_J"]) <= (1e-10 if precision == 64 else 1e-4) * scale
+
+
+def test_autotuner_keeps_the_particles_bit_for_bit():
+    """pic_autotune times sort periods and kernel grids on the running FP32
+    simulation; the particles after it are bit for bit those of the same
+    number of steps with the default schedule."""
+    from paper_2206_14662_gb300._capi import Simulation
+    cfg = workload("mirror_128x512_1e7", n_init=40_000, p_mbar=0.3, T0_eV=20.0)
+    parts = seed_particles(cfg)
+    with Simulation(cfg) as sim:
+        sim.load_particles(*parts)
+        sim.step(5)
+        res = sim.autotune(8)
+        sim.step(7)
+        d = sim.diagnostics()
+        ga = by_uid(sim.export_particles())
+    assert res["trials"] >= 5 and res["sort_every"] in (5, 10, 20, 40, 80)
+    assert res["ms_per_step"] > 0
+    with Simulation(cfg) as sim:
+        sim.load_particles(*parts)
+        sim.step(d["step"])
+        gb = by_uid(sim.export_particles())
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k]), k
