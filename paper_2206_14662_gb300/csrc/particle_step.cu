@@ -394,8 +394,9 @@ __device__ __forceinline__ void store_group(const Soa<Real>& s, int p0, int n, c
 // Deposit of one chunk: the chunk's node bounding box is reduced over the
 // block; if it fits the shared tile the block accumulates there and flushes
 // one global atomic per touched node, otherwise every particle deposits
-// with global atomics.  Contains two block barriers; every thread of the
-// block must call it.
+// with global atomics.  The tile is all zero between chunks (zeroed once at
+// kernel start, and the flush zeroes every word it reads), so a chunk needs
+// two block barriers; every thread of the block must call it.
 //
 // FP32 tile: unsigned fixed-point weights, native integer shared atomics.
 // Cell-sorted particles put whole warps on the same four nodes, and
@@ -441,13 +442,6 @@ __device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename Til
   const bool use_tile = any && rows * cols <= cap;
   const int warp = tid >> 5;
   if (use_tile) {
-    for (int t = tid; t < rows * cols; t += kThreads) {
-      if constexpr (f32) reinterpret_cast<uint4*>(tile)[t] = make_uint4(0u, 0u, 0u, 0u);
-      else tile[t] = TT(0);
-    }
-  }
-  __syncthreads();
-  if (use_tile) {
 #pragma unroll
     for (int k = 0; k < kPPT; ++k) {
       if (dep[k].ir < 0) continue;
@@ -487,10 +481,16 @@ __device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename Til
         if constexpr (f32) {
           const uint4 q = reinterpret_cast<const uint4*>(tile)[t];
           const unsigned v = q.x + q.y + q.z + q.w;
-          if (v) atomicAdd(g.cnt + node, (unsigned long long)v);
+          if (v) {
+            atomicAdd(g.cnt + node, (unsigned long long)v);
+            reinterpret_cast<uint4*>(tile)[t] = make_uint4(0u, 0u, 0u, 0u);
+          }
         } else {
           const TT v = tile[t];
-          if (v != TT(0)) atomicAdd(g.rhs + node, g.qw * (double)v);
+          if (v != TT(0)) {
+            atomicAdd(g.rhs + node, g.qw * (double)v);
+            tile[t] = TT(0);
+          }
         }
       }
     }
@@ -543,6 +543,7 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, De
   const unsigned step = *(volatile unsigned*)&st->step;
   if (tid < kTallyCount) bt.v[tid] = 0.0;
   if (tid < 8) bbox[tid >> 2][tid & 3] = (tid & 1) ? INT_MIN : INT_MAX;
+  for (int t = tid; t < kCap; t += kThreads) tile[t] = TT(0);
   __syncthreads();
   Real work = 0;
   int pushed = 0;
@@ -624,6 +625,7 @@ k_particle_step_batch(Soa<Real> s_all, const typename Vec2<Real>::type* __restri
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid < kTallyCount) bt.v[tid] = 0.0;
   if (tid < 8) bbox[tid >> 2][tid & 3] = (tid & 1) ? INT_MIN : INT_MAX;
+  for (int t = tid; t < kCap; t += kThreads) tile[t] = TT(0);
   chunk_table(st_all, nsim, kChunk, first, nslots);   // ends with a barrier
   const int total = first[nsim];
   Real work = 0;
