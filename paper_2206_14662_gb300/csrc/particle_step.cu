@@ -28,20 +28,21 @@
 
 namespace pic {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 constexpr int kPPT = 4;                 // particles per thread per chunk
 constexpr int kChunk = kThreads * kPPT;
 
 // Shared-memory deposit tile.  The FP32 path accumulates hat weights as
 // unsigned fixed-point numbers (native integer shared atomics, sums that do
-// not depend on the order of the adds): a chunk holds at most kChunk
-// particles of weight <= 1 per node, so kFix = floor((2^32 - 1) / kChunk)
-// cannot overflow even when the private copies are added; the rounding is
-// 2^-23 of a particle's charge per contribution.  The FP64 path accumulates
+// not depend on the order of the adds): a chunk holds at most 1024 (>=
+// kChunk) particles of weight <= 1 per node, so kFix = floor((2^32 - 1) /
+// 1024) cannot overflow even when the private copies are added; the
+// rounding is 2^-23 of a particle's charge per contribution.  The FP64 path accumulates
 // doubles.  cap is the tile's size in words (FP32: four copies of 1024).
 template <typename Real> struct TileT { using type = unsigned; static constexpr int cap = 4096; };
 template <> struct TileT<double> { using type = double; static constexpr int cap = 2048; };
-constexpr float kFix = (float)(4294967295u / kChunk);   // 4194303
+static_assert(kChunk <= 1024, "fixed-point tile sums");
+constexpr float kFix = (float)(4294967295u / 1024);   // 4194303
 static_assert((double)kFix == kFixUnit, "fixed-point unit shared with the field solve");
 
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
@@ -522,14 +523,14 @@ __device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pus
 
 // resident blocks per SM the FP32 kernel is compiled for (register cap)
 #ifndef PIC_MIN_BLOCKS
-#define PIC_MIN_BLOCKS 3
+#define PIC_MIN_BLOCKS 7
 #endif
 
 // Each thread loads its kPPT consecutive particles directly (16-byte vector
 // loads with streaming hints in the FP32 path), advances them, stores them
 // back and joins the block's tile deposit.
 template <typename Real>
-__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 2)
+__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 4)
 k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, DepGrid g,
                 DevState* st, unsigned* __restrict__ spawn_parent, PushParams<Real> P) {
   using TT = typename TileT<Real>::type;
@@ -608,7 +609,7 @@ struct SimView {
 // flushes the tallies of the previous one and loads the new view.  The
 // per-particle work is that of k_particle_step.
 template <typename Real>
-__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 2)
+__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 4)
 k_particle_step_batch(Soa<Real> s_all, const typename Vec2<Real>::type* __restrict__ E_all,
                       double* rhs_all, unsigned long long* cnt_all, DevState* st_all,
                       unsigned* spawn_all, long long spawn_stride,
@@ -1049,5 +1050,7 @@ int particle_step_blocks_per_sm(int precision, bool batch) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step<double>, kThreads, 0);
   return b;
 }
-int particle_chunk() { return kChunk; }
+// slots of the store are allocated in whole multiples of this (the sort
+// kernels read 1024-slot chunks)
+int particle_chunk() { return kChunk < 1024 ? 1024 : kChunk; }
 }  // namespace pic
