@@ -525,6 +525,11 @@ __device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pus
 #ifndef PIC_MIN_BLOCKS
 #define PIC_MIN_BLOCKS 7
 #endif
+// the batch kernel keeps its simulation's view in shared memory and
+// addresses it through registers; it is given a few more of them
+#ifndef PIC_MIN_BLOCKS_BATCH
+#define PIC_MIN_BLOCKS_BATCH 6
+#endif
 
 // Each thread loads its kPPT consecutive particles directly (16-byte vector
 // loads with streaming hints in the FP32 path), advances them, stores them
@@ -609,7 +614,7 @@ struct SimView {
 // flushes the tallies of the previous one and loads the new view.  The
 // per-particle work is that of k_particle_step.
 template <typename Real>
-__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 4)
+__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS_BATCH : 4)
 k_particle_step_batch(Soa<Real> s_all, const typename Vec2<Real>::type* __restrict__ E_all,
                       double* rhs_all, unsigned long long* cnt_all, DevState* st_all,
                       unsigned* spawn_all, long long spawn_stride,
