@@ -125,14 +125,16 @@ __global__ void __launch_bounds__(1024) k_sort_scan(int* count, int n, DevState*
   if (threadIdx.x == 1023) st->n_live = part[1023];
 }
 
-// scatter: four consecutive slots per thread as in the histogram; each
+// scatter: a block takes 1024 consecutive slots in four passes of 256
+// lane-consecutive slots (coalesced loads; runs of equal cells fall on
+// consecutive lanes, which then write consecutive destination slots); each
 // live particle goes to its cell's next free slot in the other buffer set
 template <typename Real>
 __device__ __forceinline__ void scatter_group(const Soa<Real>& src, const Soa<Real>& dst, int n,
-                                              int p0, int* cursor, int nz, int lane) {
+                                              int base, int* cursor, int nz, int lane) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int p = p0 + k;
+    const int p = base + k * kSortThreads + (int)threadIdx.x;
     const int c = p < n ? src.cell[p] : -1;
     const int key = cell_key(c, nz);
     const Run r = lane_run(key, lane);
@@ -158,7 +160,7 @@ k_sort_scatter(Soa<Real> src, Soa<Real> dst, const DevState* st, int* cursor, in
   const int n = (int)st->n_slots;
   const int lane = threadIdx.x & 31;
   for (int base = blockIdx.x * kSortChunk; base < n; base += gridDim.x * kSortChunk)
-    scatter_group(src, dst, n, base + 4 * threadIdx.x, cursor, nz, lane);
+    scatter_group(src, dst, n, base, cursor, nz, lane);
 }
 
 // a batch: simulation k's particles stay in its segment (the same base in
@@ -174,9 +176,8 @@ k_sort_scatter_batch(Soa<Real> src, Soa<Real> dst, const DevState* st, const Seg
   for (int c = blockIdx.x; c < first[nsim]; c += gridDim.x) {
     const int sim = chunk_owner(first, nsim, c);
     const long long b = seg[sim].base;
-    const int p0 = (c - first[sim]) * kSortChunk + 4 * threadIdx.x;
-    scatter_group(soa_offset(src, b), soa_offset(dst, b), (int)nslots[sim], p0,
-                  cursor + (size_t)sim * count_stride, nz, lane);
+    scatter_group(soa_offset(src, b), soa_offset(dst, b), (int)nslots[sim],
+                  (c - first[sim]) * kSortChunk, cursor + (size_t)sim * count_stride, nz, lane);
   }
 }
 
