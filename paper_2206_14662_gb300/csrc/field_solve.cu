@@ -126,6 +126,11 @@ void field_tables_host(const pic_config& cfg, FieldTables& T, const HostTables& 
   T.hz = (cfg.z_max - cfg.z_min) / nz;
   T.rtol = cfg.poisson_rtol;
   T.maxit = cfg.poisson_maxit > 0 ? cfg.poisson_maxit : 4;
+  T.inv2hr_d = 0.5 / T.hr;
+  T.inv2hz_d = 0.5 / T.hz;
+  T.inv2hr = (float)T.inv2hr_d;
+  T.inv2hz = (float)T.inv2hz_d;
+  T.hz32 = (float)T.hz;
   T.warm = cfg.warm_start >= 1 ? 1 : 0;
   int l2 = 0;
   while ((1 << l2) < 2 * M) ++l2;
@@ -311,7 +316,7 @@ k_prep(const double* __restrict__ rhs, const unsigned long long* __restrict__ cn
       T.res[o] = b.x;
       // the wall potentials moved to the right-hand side: -K_r(1,0) V_in
       // and -K_r(nr-1,nr) V_out times the row sum of M_z
-      const float zsum = (j == 0 || j == T.M) ? 0.5f * (float)T.hz : (float)T.hz;
+      const float zsum = (j == 0 || j == T.M) ? 0.5f * T.hz32 : T.hz32;
       const double* vac = T.phi_vac + (size_t)sim * (nr + 1);
       float lift = 0.f;
       if (i == 1) lift -= T.kr_o[0].x * (float)vac[0] * zsum;
@@ -435,14 +440,16 @@ __global__ void k_dct32_direct(FieldTables T, const DevState* st, int sweep) {
 // ------------------------------------------------------------- tridiag
 
 // One thread per z-mode: forward and back substitution of the pre-factored
-// Thomas recurrence along the interior r-lines (FP32).  A block holds 32
-// consecutive modes; its eight warps first copy the columns it needs into
-// shared memory (independent 128-byte line loads spread over the warps), so
-// the recurrence, run by the first warp, then waits only on shared memory.
-// Right-hand side, sub-diagonal and pivot serve the forward pass; the
-// super-diagonal, loaded during the forward pass, serves the backward pass.
-constexpr int kTriModes = 32;
+// Thomas recurrence along the interior r-lines (FP32).  A block holds 16
+// consecutive modes (33 blocks on the 512-cell grid); its 256 threads first
+// copy the columns it needs into shared memory, 16 rows at a time with four
+// rows' loads in flight per thread, so the recurrence, run by the first
+// half-warp, then waits only on shared memory.  Right-hand side,
+// sub-diagonal and pivot serve the forward pass; the super-diagonal serves
+// the backward pass.
+constexpr int kTriModes = 16;
 constexpr int kTriThreads = 256;
+constexpr int kTriRows = kTriThreads / kTriModes;   // rows staged per pass
 __global__ void __launch_bounds__(kTriThreads) k_tridiag32(FieldTables T, const DevState* st,
                                                            int sweep) {
   const int sim = blockIdx.y;
@@ -451,45 +458,48 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag32(FieldTables T, const 
   const int M1 = T.M + 1, NI = T.NI;
   const size_t tri = (size_t)NI * M1;
   T.bhat += sim * tri; T.phihat += sim * tri;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int k = blockIdx.x * kTriModes + lane;
+  const int col = threadIdx.x % kTriModes, row0 = threadIdx.x / kTriModes;
+  const int k = blockIdx.x * kTriModes + col;
   const bool in = k < M1;
-  float* sb = sm;                    // NI x 32: right-hand side, then solution
-  float* sa = sm + NI * kTriModes;   // NI x 32: sub-diagonal
-  float* sd = sa + NI * kTriModes;   // NI x 32: 1 / pivot
-  float* sc = sd + NI * kTriModes;   // NI x 32: super-diagonal / pivot
-  for (int i = warp; i < NI; i += kTriThreads / 32) {
+  float* sb = sm;                    // NI x 16: right-hand side, then solution
+  float* sa = sm + NI * kTriModes;   // NI x 16: sub-diagonal
+  float* sd = sa + NI * kTriModes;   // NI x 16: 1 / pivot
+  float* sc = sd + NI * kTriModes;   // NI x 16: super-diagonal / pivot
+#pragma unroll 4
+  for (int i = row0; i < NI; i += kTriRows) {
     const size_t o = (size_t)i * M1 + k;
-    const int q = i * kTriModes + lane;
+    const int q = i * kTriModes + col;
     sb[q] = in ? T.bhat[o] : 0.f;
     sa[q] = in ? T.tri_a[o] : 0.f;
     sd[q] = in ? T.tri_inv[o] : 0.f;
     sc[q] = in ? T.tri_cp[o] : 0.f;
   }
   __syncthreads();
-  if (warp == 0) {
+  if (threadIdx.x < kTriModes) {
     float y = 0.f;
 #pragma unroll 8
     for (int i = 0; i < NI; ++i) {
-      const int o = i * kTriModes + lane;
+      const int o = i * kTriModes + col;
       y = (sb[o] - sa[o] * y) * sd[o];
       sb[o] = y;
     }
     float xn = 0.f;
 #pragma unroll 8
     for (int i = NI - 1; i >= 0; --i) {
-      const int o = i * kTriModes + lane;
+      const int o = i * kTriModes + col;
       xn = sb[o] - sc[o] * xn;
       sb[o] = xn;
     }
   }
   __syncthreads();
-  if (in)
-    for (int i = warp; i < NI; i += kTriThreads / 32)
-      T.phihat[(size_t)i * M1 + k] = sb[i * kTriModes + lane];
+  if (in) {
+#pragma unroll 4
+    for (int i = row0; i < NI; i += kTriRows)
+      T.phihat[(size_t)i * M1 + k] = sb[i * kTriModes + col];
+  }
 }
 
-// shared memory of k_tridiag32 (four NI x 32 float arrays); above the
+// shared memory of k_tridiag32 (four NI x 16 float arrays); above the
 // default 48 KB the kernel is opted in once
 static size_t tridiag_smem(const FieldTables& T) {
   return (size_t)4 * T.NI * kTriModes * sizeof(float);
@@ -520,7 +530,7 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
     // E = E_vac - grad phi_rho: central differences, one-sided second order
     // on the boundary lines (phi_rho is zero on the walls)
     float dr, dz;
-    const float inv2hr = (float)(0.5 / T.hr), inv2hz = (float)(0.5 / T.hz);
+    const float inv2hr = T.inv2hr, inv2hz = T.inv2hz;
     if (i == 0) dr = (-3.f * ph[o].x + 4.f * ph[o + M1].x - ph[o + 2 * M1].x +
                       (-3.f * ph[o].y + 4.f * ph[o + M1].y - ph[o + 2 * M1].y)) * inv2hr;
     else if (i == nr) dr = (3.f * ph[o].x - 4.f * ph[o - M1].x + ph[o - 2 * M1].x +
@@ -538,7 +548,7 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
     } else {
       // FP64 particle path: the same differences of hi + lo in double
       auto p = [&](size_t q) { return (double)ph[q].x + (double)ph[q].y; };
-      const double i2r = 0.5 / T.hr, i2z = 0.5 / T.hz;
+      const double i2r = T.inv2hr_d, i2z = T.inv2hz_d;
       double ddr, ddz;
       if (i == 0) ddr = (-3.0 * p(o) + 4.0 * p(o + M1) - p(o + 2 * M1)) * i2r;
       else if (i == nr) ddr = (3.0 * p(o) - 4.0 * p(o - M1) + p(o - 2 * M1)) * i2r;

@@ -246,6 +246,9 @@ struct FieldTables {
   int maxit;                  // refinement sweeps at most
   int warm;                   // 1: refine from the previous phi_rho
   double hr, hz, rtol;
+  float inv2hr, inv2hz;       // 1 / (2 h) for the node-field differences
+  double inv2hr_d, inv2hz_d;
+  float hz32;                 // h_z
   float2* tw32;               // exp(-2 pi i m / N), m < N/2
   float* cos32;               // cos(pi m / M), m < 2M (direct transform)
   float* scale32;             // 2 eps_k / M, k = 0..M
