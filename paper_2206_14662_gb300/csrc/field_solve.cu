@@ -285,45 +285,63 @@ int field_tables_build(const pic_config* cfgs, int nsim, FieldTables& T,
 // interior right-hand side and of the lifted one; clears the next deposit
 // buffer.  FIX: b' = count * unit2 (fixed-point counts); else b' = rhs *
 // unit64 (FP64 charges).
+// the deposit's charge source of a solve
+struct ChargeIn {
+  const double* rhs;                  // FP64 charges (C), or
+  const unsigned long long* cnt;      // fixed-point counts
+  float2 unit2;                       // count -> b' (double-float), or
+  const float2* units;                //   per simulation (batch)
+  double unit64;                      // charge -> b'
+  unsigned long long* clear;          // buffer zeroed on the way, or null
+};
+
+// b' at node o (global index) of simulation sim, node (i, j): stored in T.b2
+// on the interior lines, with the squares of it and of the lifted value
+// added to nb, nl; the node of `clear` is zeroed
 template <bool FIX>
-__global__ void __launch_bounds__(256)
-k_prep(const double* __restrict__ rhs, const unsigned long long* __restrict__ cnt, float2 unit2,
-       const float2* __restrict__ units, double unit64, unsigned long long* clear, FieldTables T,
-       DevState* st) {
+__device__ __forceinline__ float2 prep_node(const ChargeIn& in, const FieldTables& T, int sim,
+                                            size_t o, int i, int j, float& nb, float& nl) {
+  const int nr = T.nr;
+  float2 b;
+  if (FIX) {
+    const float2 unit2 = in.units ? in.units[sim] : in.unit2;
+    const unsigned long long c = in.cnt[o];
+    const float hi = __ull2float_rn(c);
+    const long long rem = (long long)(c - __float2ull_rn(hi));
+    b = df_mul(qts(hi, __ll2float_rn(rem)), unit2);
+  } else {
+    const double x = in.rhs[o] * in.unit64;
+    const float hi = (float)x;
+    b = make_float2(hi, (float)(x - (double)hi));
+  }
+  if (in.clear) in.clear[o] = 0ull;
+  if (i > 0 && i < nr) {
+    T.b2[o] = b;
+    // the wall potentials moved to the right-hand side: -K_r(1,0) V_in
+    // and -K_r(nr-1,nr) V_out times the row sum of M_z
+    const float zsum = (j == 0 || j == T.M) ? 0.5f * T.hz32 : T.hz32;
+    const double* vac = T.phi_vac + (size_t)sim * (nr + 1);
+    float lift = 0.f;
+    if (i == 1) lift -= T.kr_o[0].x * (float)vac[0] * zsum;
+    if (i == nr - 1) lift -= T.kr_o[nr - 1].x * (float)vac[nr] * zsum;
+    nb = b.x * b.x;
+    nl = (b.x + lift) * (b.x + lift);
+  }
+  return b;
+}
+
+template <bool FIX>
+__global__ void __launch_bounds__(256) k_prep(ChargeIn in, FieldTables T, DevState* st) {
   const int M1 = T.M + 1, nr = T.nr;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int sim = blockIdx.z;
   st += sim;
-  if (units) unit2 = units[sim];
   float nb = 0.f, nl = 0.f;
   if (i <= nr && j < M1) {
     const size_t o = (size_t)sim * (nr + 1) * M1 + (size_t)i * M1 + j;
-    float2 b;
-    if (FIX) {
-      const unsigned long long c = cnt[o];
-      const float hi = __ull2float_rn(c);
-      const long long rem = (long long)(c - __float2ull_rn(hi));
-      b = df_mul(qts(hi, __ll2float_rn(rem)), unit2);
-    } else {
-      const double x = rhs[o] * unit64;
-      const float hi = (float)x;
-      b = make_float2(hi, (float)(x - (double)hi));
-    }
-    if (clear) clear[o] = 0ull;
-    if (i > 0 && i < nr) {
-      T.b2[o] = b;
-      T.res[o] = b.x;
-      // the wall potentials moved to the right-hand side: -K_r(1,0) V_in
-      // and -K_r(nr-1,nr) V_out times the row sum of M_z
-      const float zsum = (j == 0 || j == T.M) ? 0.5f * T.hz32 : T.hz32;
-      const double* vac = T.phi_vac + (size_t)sim * (nr + 1);
-      float lift = 0.f;
-      if (i == 1) lift -= T.kr_o[0].x * (float)vac[0] * zsum;
-      if (i == nr - 1) lift -= T.kr_o[nr - 1].x * (float)vac[nr] * zsum;
-      nb = b.x * b.x;
-      nl = (b.x + lift) * (b.x + lift);
-    }
+    const float2 b = prep_node<FIX>(in, T, sim, o, i, j, nb, nl);
+    if (i > 0 && i < nr) T.res[o] = b.x;
   }
   __shared__ float red[2][8];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -511,18 +529,30 @@ __device__ __forceinline__ float df_diff(float2 a, float2 b) {   // a - b to flo
   return (a.x - b.x) + (a.y - b.y);
 }
 
-template <typename Real>
+// PREP (the warm start's first pass): b' is formed here as in k_prep before
+// the residual of the previous solution, so one pass replaces two.
+template <typename Real, int PREP>
 __global__ void __launch_bounds__(256)
-k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep, int last) {
+k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep, int last,
+           ChargeIn in) {
   const int sim = blockIdx.z;
   st += sim;
   if (sweep >= 0 && (sweep > 0 || T.warm) && *(volatile const int*)&st->solve_done) return;
   const int nr = T.nr, M = T.M, M1 = M + 1;
   const size_t nn = (size_t)(nr + 1) * M1;
-  T.phir += sim * nn; T.res += sim * nn; T.b2 += sim * nn; E += sim * nn;
-  T.evac32 += sim * (nr + 1); T.evac64 += sim * (nr + 1);
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  float nb = 0.f, nl = 0.f;
+  // the solve's first kernel resets the stopping state (before this
+  // block's completion is counted, so before the last block's test)
+  if (PREP && threadIdx.x == 0 && threadIdx.y == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
+    st->solve_done = 0;
+    st->poisson_iters = 0;
+  }
+  if (PREP && i <= nr && j <= M)
+    prep_node<PREP == 1>(in, T, sim, (size_t)sim * nn + (size_t)i * M1 + j, i, j, nb, nl);
+  T.phir += sim * nn; T.res += sim * nn; T.b2 += sim * nn; E += sim * nn;
+  T.evac32 += sim * (nr + 1); T.evac64 += sim * (nr + 1);
   float rn = 0.f;
   if (i <= nr && j <= M) {
     const size_t o = (size_t)i * M1 + j;
@@ -587,16 +617,28 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
     }
   }
   // block reduction, then the last block evaluates the stopping test
-  __shared__ float red[8];
+  __shared__ float red[3][8];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, w = tid >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) rn += __shfl_xor_sync(0xffffffffu, rn, o);
-  if (lane == 0) red[w] = rn;
+  for (int o = 16; o > 0; o >>= 1) {
+    rn += __shfl_xor_sync(0xffffffffu, rn, o);
+    if (PREP) {
+      nb += __shfl_xor_sync(0xffffffffu, nb, o);
+      nl += __shfl_xor_sync(0xffffffffu, nl, o);
+    }
+  }
+  if (lane == 0) { red[0][w] = rn; red[1][w] = nb; red[2][w] = nl; }
   __syncthreads();
   if (tid == 0) {
-    double a = 0.0;
-    for (int k = 0; k < (int)(blockDim.x * blockDim.y) / 32; ++k) a += red[k];
+    double a = 0.0, bsum = 0.0, lsum = 0.0;
+    for (int k = 0; k < (int)(blockDim.x * blockDim.y) / 32; ++k) {
+      a += red[0][k];
+      bsum += red[1][k];
+      lsum += red[2][k];
+    }
     if (a != 0.0) atomicAdd(&st->r2sum, a);
+    if (PREP && bsum != 0.0) atomicAdd(&st->b2sum, bsum);
+    if (PREP && lsum != 0.0) atomicAdd(&st->bl2sum, lsum);
     __threadfence();
     const unsigned nb = gridDim.x * gridDim.y;
     if (atomicAdd(&st->solve_blocks_done, 1u) == nb - 1) {
@@ -640,7 +682,7 @@ void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream, int 
   k_phi_out<<<(n + 255) / 256, 256, 0, stream>>>(T, phi, sim);
 }
 
-int field_solve_kernels(const FieldTables& T) { return 1 + T.warm + 4 * T.maxit; }
+int field_solve_kernels(const FieldTables& T) { return 1 + 4 * T.maxit; }
 
 template <typename Real>
 void launch_field_solve(const FieldTables& T, const double* rhs, const unsigned long long* cnt,
@@ -652,13 +694,18 @@ void launch_field_solve(const FieldTables& T, const double* rhs, const unsigned 
   if (tridiag_smem(T) > 48 * 1024)
     cudaFuncSetAttribute(k_tridiag32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tridiag_smem(T));
-  if (cnt) k_prep<true><<<grd, blk, 0, stream>>>(nullptr, cnt, df_from(cnt_unit * s0), cnt_units,
-                                                  0.0, cnt_clear, T, st);
-  else k_prep<false><<<grd, blk, 0, stream>>>(rhs, nullptr, make_float2(0.f, 0.f), nullptr, s0,
-                                               cnt_clear, T, st);
-  if (T.warm)   // residual of the previous solution, the refinement's start
-    k_residual<Real><<<grd, blk, 0, stream>>>(T, (typename Vec2<Real>::type*)efield, st, -1,
-                                             T.maxit == 0);
+  const ChargeIn in{rhs, cnt, cnt ? df_from(cnt_unit * s0) : make_float2(0.f, 0.f), cnt_units,
+                    s0, cnt_clear};
+  using V2 = typename Vec2<Real>::type;
+  if (T.warm) {
+    // b' and the residual of the previous solution (the refinement's start)
+    // in one pass; the stopping state is reset by the solve's first kernel
+    if (cnt) k_residual<Real, 1><<<grd, blk, 0, stream>>>(T, (V2*)efield, st, -1, T.maxit == 0, in);
+    else k_residual<Real, 2><<<grd, blk, 0, stream>>>(T, (V2*)efield, st, -1, T.maxit == 0, in);
+  } else {
+    if (cnt) k_prep<true><<<grd, blk, 0, stream>>>(in, T, st);
+    else k_prep<false><<<grd, blk, 0, stream>>>(in, T, st);
+  }
   for (int s = 0; s < T.maxit; ++s) {
     if (T.log2N > 0) {
       const int N = 2 * T.M;
@@ -676,8 +723,8 @@ void launch_field_solve(const FieldTables& T, const double* rhs, const unsigned 
                     stream>>>(T, st, s);
       k_dct32_direct<false><<<dim3(T.NI, S), 256, smem, stream>>>(T, st, s);
     }
-    k_residual<Real><<<grd, blk, 0, stream>>>(T, (typename Vec2<Real>::type*)efield, st, s,
-                                             s == T.maxit - 1);
+    k_residual<Real, 0><<<grd, blk, 0, stream>>>(T, (V2*)efield, st, s, s == T.maxit - 1,
+                                                ChargeIn{});
   }
 }
 
