@@ -377,7 +377,18 @@ void gemm_fwd(pic_unet* n, const void* X, int ldx, int K, const void* w, int ldw
 void gemm_wgrad(pic_unet* n, const void* G, int ldg, const void* X, int ldx, int K, int N,
                 int map, Grid3 g, float* dW, int taps) {
   const long long P = (long long)g.B * g.H * g.W;
-  if (n->prec == 16) {
+  if (n->prec == 16 && (K == 32 || N == 32)) {
+    // 32 x 32 tiles; pixels split so that the grid fills the machine about
+    // four times
+    const long long tiles = (long long)(K / 32) * (N / 32) * taps;
+    long long splits = std::max<long long>(1, (4LL * n->sms + tiles - 1) / tiles);
+    long long per = (P + splits - 1) / splits;
+    per = std::max<long long>(kW2K * 4, (per + kW2K - 1) / kW2K * kW2K);
+    splits = (P + per - 1) / per;
+    const dim3 grid(K / 32, N / 32, (unsigned)(splits * taps));
+    k_gemm_wgrad32<<<grid, 128, 0, n->stream>>>((const bf16*)G, ldg, (const bf16*)X, ldx, K, N,
+                                                map, g, per, dW, taps);
+  } else if (n->prec == 16) {
     // split the pixels so that the grid fills the machine about four times
     const long long tiles = (long long)((K + kWN - 1) / kWN) * ((N + kWM - 1) / kWM) * taps;
     long long splits = std::max<long long>(1, (4LL * n->sms + tiles - 1) / tiles);

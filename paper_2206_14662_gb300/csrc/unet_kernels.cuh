@@ -348,5 +348,120 @@ k_gemm_wgrad(const bf16* __restrict__ G, int ldg, const bf16* __restrict__ X, in
     }
 }
 
+// Weight gradient of a 32 x 32 tile (layers with 32 input or output
+// channels, where a 64 x 64 tile would idle half or more of its MMAs):
+// stages of 64 pixels, each warp takes one 16-pixel slice of every stage
+// and accumulates the whole tile, and the four partial tiles are summed in
+// shared memory before the FP32 atomics.
+constexpr int kW2K = 64, kW2Lds = 40;
+
+__global__ void __launch_bounds__(128)
+k_gemm_wgrad32(const bf16* __restrict__ G, int ldg, const bf16* __restrict__ X, int ldx, int K,
+               int N, int map, Grid3 g, long long pix_per_block, float* __restrict__ dW,
+               int taps) {
+  __shared__ __align__(16) bf16 sm[2 * 2 * kW2K * kW2Lds];   // sG[2], sX[2]; partials after
+  bf16* sG = sm;
+  bf16* sX = sm + 2 * kW2K * kW2Lds;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t = blockIdx.z % taps;
+  const long long P = (long long)g.B * g.H * g.W;
+  const long long pa = (long long)(blockIdx.z / taps) * pix_per_block;
+  const long long pb = pa + pix_per_block < P ? pa + pix_per_block : P;
+  const int m0 = blockIdx.y * 32;                // output channels n
+  const int k0 = blockIdx.x * 32;                // input channels k
+  const int steps = (int)((pb - pa + kW2K - 1) / kW2K);
+  if (steps <= 0) return;
+
+  auto load = [&](int stage, int st) {
+    // 64 pixel rows x 32 channels for each operand: 256 chunks each
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int ch = tid + i * 128;
+      const int row = ch >> 2, part = ch & 3;
+      const long long p = pa + (long long)st * kW2K + row;
+      long long gp = -1, xp = -1;
+      if (p < pb) {
+        if (map == kConv3) {
+          gp = p;
+          xp = src_pixel(kConv3, p, t, g);
+        } else {
+          gp = dst_pixel(kUpFwd, p, t, g);
+          xp = p;
+        }
+      }
+      const bool vg = gp >= 0 && m0 + part * 8 < N, vx = xp >= 0 && k0 + part * 8 < K;
+      cp_async16(&sG[(stage * kW2K + row) * kW2Lds + part * 8],
+                 G + (vg ? gp * ldg + m0 + part * 8 : 0), vg);
+      cp_async16(&sX[(stage * kW2K + row) * kW2Lds + part * 8],
+                 X + (vx ? xp * ldx + k0 + part * 8 : 0), vx);
+    }
+  };
+
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+
+  load(0, 0);
+  cp_async_commit();
+  for (int st = 0; st < steps; ++st) {
+    const int cur = st & 1;
+    if (st + 1 < steps) load(cur ^ 1, st + 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const bf16* gs = sG + cur * kW2K * kW2Lds;
+    const bf16* xs = sX + cur * kW2K * kW2Lds;
+    const int kk = warp * 16;                    // this warp's pixel slice
+    unsigned af[2][4], bfr[4][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int kr = kk + (lane & 7) + ((lane >> 4) << 3);
+      const int mc = mt * 16 + ((lane >> 3) & 1) * 8;
+      ldsm_x4_t(af[mt][0], af[mt][1], af[mt][2], af[mt][3], gs + kr * kW2Lds + mc);
+    }
+#pragma unroll
+    for (int np = 0; np < 2; ++np) {
+      const int kr = kk + (lane & 7) + (((lane >> 3) & 1) << 3);
+      const int nc = np * 16 + (lane >> 4) * 8;
+      unsigned r0, r1, r2, r3;
+      ldsm_x4_t(r0, r1, r2, r3, xs + kr * kW2Lds + nc);
+      bfr[2 * np][0] = r0; bfr[2 * np][1] = r1;
+      bfr[2 * np + 1][0] = r2; bfr[2 * np + 1][1] = r3;
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+        mma_bf16(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], bfr[nt][0], bfr[nt][1]);
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  // sum the four warps' tiles in shared memory (the staging area is free)
+  float* part = reinterpret_cast<float*>(sm);    // [4][32][33]
+  const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int m = mt * 16 + gq + 8 * h, k = nt * 8 + 2 * tq;
+        part[(warp * 32 + m) * 33 + k] = acc[mt][nt][2 * h];
+        part[(warp * 32 + m) * 33 + k + 1] = acc[mt][nt][2 * h + 1];
+      }
+  __syncthreads();
+  const int ldw = taps * K;
+  for (int e = tid; e < 32 * 32; e += 128) {
+    const int m = e >> 5, k = e & 31;
+    const float v = part[m * 33 + k] + part[(32 + m) * 33 + k] + part[(64 + m) * 33 + k] +
+                    part[(96 + m) * 33 + k];
+    if (m0 + m < N && k0 + k < K) atomicAdd(dW + (size_t)(m0 + m) * ldw + t * K + k0 + k, v);
+  }
+}
+
 }  // namespace unet
 }  // namespace pic
