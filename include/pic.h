@@ -301,7 +301,7 @@ const char* pic_strerror(int code);
  * a four-level convolutional U-Net maps (charge, previous space-charge
  * potential) on the H x W node grid to a guess of the new space-charge
  * potential; the field solve then refines that guess to the same residual
- * bound (poisson_rtol), so the solver stays the judge.
+ * bound (poisson_rtol), so the solver still decides convergence.
  *
  * Architecture (base width c, 1 <= c <= 32; H, W multiples of 8): per
  * level k = 1..4 at width c 2^(k-1) two 3 x 3 convolutions with bias and

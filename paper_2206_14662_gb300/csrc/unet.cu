@@ -5,7 +5,7 @@
 // channels, a 1 x 1 head to one channel), trained on the GPU by this file's
 // forward and backward kernels with Adam.  The paper has no counterpart: it
 // only warm-starts the field solve, which still iterates to the same
-// residual bound (the solver stays the judge).
+// residual bound (the solver still decides convergence).
 //
 // Precision: precision 16 keeps activations and weight copies in BF16 and
 // runs every convolution on the tensor cores with FP32 accumulation (FP32
