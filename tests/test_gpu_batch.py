@@ -188,3 +188,33 @@ def test_batch_edge_cases():
         with pytest.raises(PicError) as ei:
             sim.diagnostics(sim=1)
         assert ei.value.code == PIC_ECAPACITY
+
+
+def test_batch_with_seed_sources_matches_oracle():
+    """Seed sources of different rates in the simulations of a batch (FP64,
+    fixed per-simulation fields, collisions, a sort every two steps): the
+    created particles of simulation k carry uids after its children and draw
+    from its own streams (counter word 1 = k), as in the oracle."""
+    from paper_2206_14662_gb300._capi import Simulation
+    cfgs = _batch_cfgs(64, ns=(800, 1500, 300), fixed_efield=1, sort_every=2, T0_eV=20.0)
+    rates = (11.4, 0.0, 3.7)
+    for c, r in zip(cfgs, rates):
+        c["source_rate"] = r / c["dt"]
+    parts = [_parts(c, k) for k, c in enumerate(cfgs)]
+    fields = [random_field_node_arrays(c, 2e5, seed=30 + k) for k, c in enumerate(cfgs)]
+    oracles = [_oracle(c, k, p, efield_nodes=f, solve_field=False)
+               for k, (c, p, f) in enumerate(zip(cfgs, parts, fields))]
+    with Simulation(cfgs) as sim:
+        for k, (p, f) in enumerate(zip(parts, fields)):
+            sim.load_particles(*p, sim=k)
+            sim.set_efield(*f, sim=k)
+        sim.step(5)
+        got = [(_export(sim, k), sim.diagnostics(sim=k)) for k in range(len(cfgs))]
+    for o in oracles:
+        for _ in range(5):
+            o.step()
+    for k, (cfg, o, (g, d)) in enumerate(zip(cfgs, oracles, got)):
+        assert d["n_source"] == o.n_source, k
+        compare_states(cfg, 64, g, o, tol=1e-10)
+        assert d["ke_source_J"] == pytest.approx(o.ke_source, rel=1e-12, abs=1e-30), k
+    assert oracles[0].n_source in (56, 57) and oracles[1].n_source == 0
