@@ -218,3 +218,55 @@ def test_batch_with_seed_sources_matches_oracle():
         compare_states(cfg, 64, g, o, tol=1e-10)
         assert d["ke_source_J"] == pytest.approx(o.ke_source, rel=1e-12, abs=1e-30), k
     assert oracles[0].n_source in (56, 57) and oracles[1].n_source == 0
+
+
+def test_batch_self_consistent_fp32_follows_oracle():
+    """Ten self-consistent FP32 steps of a batch (field solve on, sorts):
+    each simulation's potential and particle positions follow its FP64
+    oracle run within the FP32 tolerance."""
+    from paper_2206_14662_gb300._capi import PIC_GRID_PHI, Simulation
+    cfgs = _batch_cfgs(32, sort_every=3)
+    parts = [_parts(c, k) for k, c in enumerate(cfgs)]
+    oracles = [_oracle(c, k, p) for k, (c, p) in enumerate(zip(cfgs, parts))]
+    with Simulation(cfgs) as sim:
+        for k, p in enumerate(parts):
+            sim.load_particles(*p, sim=k)
+        sim.step(10)
+        got = [(_export(sim, k), sim.get_grid(PIC_GRID_PHI, sim=k)) for k in range(len(cfgs))]
+    for o in oracles:
+        for _ in range(10):
+            o.step()
+    for k, (cfg, o, (g, phi)) in enumerate(zip(cfgs, oracles, got)):
+        assert np.abs(phi - o.phi).max() <= 1e-5 * np.abs(o.phi).max(), k
+        keep = np.isin(o.uid, g["uid"])
+        assert keep.mean() > 0.995, k
+        gi = np.searchsorted(g["uid"], o.uid[keep])
+        hr = (cfg["r_out"] - cfg["r_in"]) / cfg["nr"]
+        assert np.abs(g["r"][gi] - o.r[keep]).max() / hr <= 2e-5, k
+
+
+def test_batch_autotuner_keeps_the_particles_bit_for_bit():
+    """pic_autotune on a batch: the particles of every simulation equal
+    those of the same number of steps with the default schedule."""
+    from paper_2206_14662_gb300._capi import Simulation
+    # the trials run thousands of steps: a low pressure and room to grow
+    cfgs = _batch_cfgs(32, ns=(3000, 9000, 500), sort_every=20, p_mbar=0.01)
+    for c in cfgs:
+        c["capacity"] = 4 * c["n_init"] + 4096
+    parts = [_parts(c, k) for k, c in enumerate(cfgs)]
+    out = []
+    for tune in (True, False):
+        with Simulation(cfgs) as sim:
+            for k, p in enumerate(parts):
+                sim.load_particles(*p, sim=k)
+            if tune:
+                sim.step(3)
+                sim.autotune(8)
+                sim.step(5)
+                steps = sim.diagnostics(sim=0)["step"]
+            else:
+                sim.step(steps)
+            out.append([by_uid(sim.export_particles(sim=k)) for k in range(len(cfgs))])
+    for a, b in zip(*out):
+        for key in a:
+            assert np.array_equal(a[key], b[key]), key
