@@ -48,6 +48,7 @@ sys.path.insert(0, ROOT)
 from paper_2206_14662_gb300.inputs import scan_configs, seed_particles, workload  # noqa: E402
 
 WORKLOAD = "mirror_128x512_1e7"
+LARGE = "mirror_256x1024_2e8"
 SCAN = "scan_64x256_64sims"
 UNET = "unet_warmstart_128x512"
 STEADY = "time_to_steady_64sims"
@@ -182,10 +183,11 @@ def _inputs(args, rank):
         cfgs = scan_configs(seed=1 + rank, **over)
         parts = [seed_particles(c, seed=1000 * (rank + 1) + k) for k, c in enumerate(cfgs)]
         return SCAN, cfgs, parts
-    cfg = workload(WORKLOAD, seed=1 + rank, **over)
+    name = LARGE if args.workload == LARGE else WORKLOAD
+    cfg = workload(name, seed=1 + rank, **over)
     if args.particles:
         cfg["n_init"] = args.particles
-    return WORKLOAD, [cfg], [seed_particles(cfg)]
+    return name, [cfg], [seed_particles(cfg)]
 
 
 def run_ours(args, ws, rank):
@@ -277,7 +279,7 @@ def run_ours(args, ws, rank):
                   "particles": n0, "grid": grid,
                   "sort_every": tune["sort_every"] if tune else cfg["sort_every"],
                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                  "l2": "inputs larger than L2 (particle store 520 MB per step)"}
+                  "l2": f"inputs larger than L2 (particle store {n0 * 52 / 1e9:.2f} GB per step)"}
     else:
         config = {"workload": name, "simulations": S, "particles": n0,
                   "particles_min_max": [min(len(p[0]) for p in parts),
@@ -326,7 +328,9 @@ def run_ours(args, ws, rank):
     }
     if args.cpu_baseline:
         if S == 1:
-            out["cpu_baseline"] = cpu_baseline(cfg, parts[0])
+            # the oracle on at most 2e7 of the particles (a bounded sample)
+            out["cpu_baseline"] = cpu_baseline(cfg, parts[0], name=name,
+                                               n_sample=min(len(parts[0][0]), 20_000_000))
         else:
             # the oracle on the largest simulation of the scan, 4 steps
             k = int(np.argmax([len(p[0]) for p in parts]))
@@ -480,8 +484,9 @@ def run_steady(args, ws, rank):
 
 
 def cpu_baseline(cfg, parts, n_sample=None, steps=2, name=WORKLOAD):
-    """The oracle as it stands (single thread) on a bounded sample: the full
-    1e7-particle load and field, ``steps`` steps."""
+    """The oracle as it stands (single thread) on a bounded sample: the
+    first n_sample particles of the load (all by default) with the full grid
+    and field solve, ``steps`` steps."""
     import oracle
     oracle.build()
     sel = slice(None) if n_sample is None else slice(0, n_sample)
@@ -509,7 +514,7 @@ def run_reference(args, ws, rank):
     oracle.build()
     name = args.workload
     # the scan: its largest simulation (the oracle runs one simulation)
-    cfg = workload(WORKLOAD) if name == WORKLOAD else scan_configs()[-1]
+    cfg = workload(name) if name in (WORKLOAD, LARGE) else scan_configs()[-1]
     n = 20_000
     parts = seed_particles(cfg, n=n)
     o = oracle.OracleSim(cfg, *parts)
@@ -567,7 +572,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
-    ap.add_argument("--workload", choices=[WORKLOAD, SCAN, UNET, STEADY], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, LARGE, SCAN, UNET, STEADY], default=WORKLOAD)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the workload's sort period and the default kernel grid")
     ap.add_argument("--warm-start", type=int, choices=[0, 1], default=None,
