@@ -45,35 +45,11 @@
 #include <type_traits>
 #include <vector>
 
-#include "pic_internal.cuh"
+#include "field_common.cuh"
 
 namespace pic {
 
 // ------------------------------------------------------- double-float
-// Error-free transformations (Knuth's two-sum, Dekker's product via FMA)
-// and the usual double-float add / multiply built on them.
-
-__device__ __forceinline__ float2 qts(float a, float b) {   // |a| >= |b|
-  const float s = a + b;
-  return make_float2(s, b - (s - a));
-}
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-  const float s = a + b;
-  const float v = s - a;
-  return make_float2(s, (a - (s - v)) + (b - v));
-}
-__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-  const float2 s = two_sum(a.x, b.x);
-  return qts(s.x, s.y + a.y + b.y);
-}
-__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-  const float p = a.x * b.x;
-  float e = fmaf(a.x, b.x, -p);
-  e = fmaf(a.x, b.y, e);
-  e = fmaf(a.y, b.x, e);
-  return qts(p, e);
-}
 
 float2 df_from(double x) {
   const float hi = (float)x;
@@ -281,55 +257,6 @@ int field_tables_build(const pic_config* cfgs, int nsim, FieldTables& T,
 
 // ---------------------------------------------------------------- prep
 
-// b' per node in double-float, the sweep-0 input, and the norms of the
-// interior right-hand side and of the lifted one; clears the next deposit
-// buffer.  FIX: b' = count * unit2 (fixed-point counts); else b' = rhs *
-// unit64 (FP64 charges).
-// the deposit's charge source of a solve
-struct ChargeIn {
-  const double* rhs;                  // FP64 charges (C), or
-  const unsigned long long* cnt;      // fixed-point counts
-  float2 unit2;                       // count -> b' (double-float), or
-  const float2* units;                //   per simulation (batch)
-  double unit64;                      // charge -> b'
-  unsigned long long* clear;          // buffer zeroed on the way, or null
-};
-
-// b' at node o (global index) of simulation sim, node (i, j): stored in T.b2
-// on the interior lines, with the squares of it and of the lifted value
-// added to nb, nl; the node of `clear` is zeroed
-template <bool FIX>
-__device__ __forceinline__ float2 prep_node(const ChargeIn& in, const FieldTables& T, int sim,
-                                            size_t o, int i, int j, float& nb, float& nl) {
-  const int nr = T.nr;
-  float2 b;
-  if (FIX) {
-    const float2 unit2 = in.units ? in.units[sim] : in.unit2;
-    const unsigned long long c = in.cnt[o];
-    const float hi = __ull2float_rn(c);
-    const long long rem = (long long)(c - __float2ull_rn(hi));
-    b = df_mul(qts(hi, __ll2float_rn(rem)), unit2);
-  } else {
-    const double x = in.rhs[o] * in.unit64;
-    const float hi = (float)x;
-    b = make_float2(hi, (float)(x - (double)hi));
-  }
-  if (in.clear) in.clear[o] = 0ull;
-  if (i > 0 && i < nr) {
-    T.b2[o] = b;
-    // the wall potentials moved to the right-hand side: -K_r(1,0) V_in
-    // and -K_r(nr-1,nr) V_out times the row sum of M_z
-    const float zsum = (j == 0 || j == T.M) ? 0.5f * T.hz32 : T.hz32;
-    const double* vac = T.phi_vac + (size_t)sim * (nr + 1);
-    float lift = 0.f;
-    if (i == 1) lift -= T.kr_o[0].x * (float)vac[0] * zsum;
-    if (i == nr - 1) lift -= T.kr_o[nr - 1].x * (float)vac[nr] * zsum;
-    nb = b.x * b.x;
-    nl = (b.x + lift) * (b.x + lift);
-  }
-  return b;
-}
-
 template <bool FIX>
 __global__ void __launch_bounds__(256) k_prep(ChargeIn in, FieldTables T, DevState* st) {
   const int M1 = T.M + 1, nr = T.nr;
@@ -392,25 +319,14 @@ k_dct32(FieldTables T, const DevState* st, int sweep) {
   }
   __syncthreads();
   for (int s = 1; s <= log2N; ++s) {
-    const int half = 1 << (s - 1), stride = N >> s;
-    for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      const float2 w = tw[pos * stride];
-      const float2 a = sh[i0], b = sh[i1];
-      const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
-      sh[i0] = make_float2(a.x + bw.x, a.y + bw.y);
-      sh[i1] = make_float2(a.x - bw.x, a.y - bw.y);
-    }
+    for (int t = threadIdx.x; t < N / 2; t += blockDim.x) fft_butterfly(sh, tw, N, s, t);
     __syncthreads();
   }
   const float x0 = x[0], xM = x[M];
   const float y0 = two ? y[0] : 0.f, yM = two ? y[M] : 0.f;
   for (int k = threadIdx.x; k <= M; k += blockDim.x) {
-    const float sg = (k & 1) ? -1.f : 1.f;
-    const float2 C = sh[k];
-    const float vx = 0.5f * (C.x + x0 + sg * xM);
-    const float vy = 0.5f * (C.y + y0 + sg * yM);
+    const float2 v = dct_out(sh[k], k, x0, xM, y0, yM);
+    const float vx = v.x, vy = v.y;
     if (FWD) {
       T.bhat[(size_t)line0 * M1 + k] = vx * T.scale32[k];
       if (two) T.bhat[(size_t)(line0 + 1) * M1 + k] = vy * T.scale32[k];
@@ -498,14 +414,14 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag32(FieldTables T, const 
 #pragma unroll 8
     for (int i = 0; i < NI; ++i) {
       const int o = i * kTriModes + col;
-      y = (sb[o] - sa[o] * y) * sd[o];
+      y = thomas_fwd(sb[o], sa[o], sd[o], y);
       sb[o] = y;
     }
     float xn = 0.f;
 #pragma unroll 8
     for (int i = NI - 1; i >= 0; --i) {
       const int o = i * kTriModes + col;
-      xn = sb[o] - sc[o] * xn;
+      xn = thomas_bwd(sb[o], sc[o], xn);
       sb[o] = xn;
     }
   }
@@ -524,10 +440,6 @@ static size_t tridiag_smem(const FieldTables& T) {
 }
 
 // ------------------------------------ residual, convergence test, E field
-
-__device__ __forceinline__ float df_diff(float2 a, float2 b) {   // a - b to float
-  return (a.x - b.x) + (a.y - b.y);
-}
 
 // PREP (the warm start's first pass): b' is formed here as in k_prep before
 // the residual of the previous solution, so one pass replaces two.
@@ -557,59 +469,16 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
   if (i <= nr && j <= M) {
     const size_t o = (size_t)i * M1 + j;
     const float2* ph = T.phir;
-    // E = E_vac - grad phi_rho: central differences, one-sided second order
-    // on the boundary lines (phi_rho is zero on the walls)
-    float dr, dz;
-    const float inv2hr = T.inv2hr, inv2hz = T.inv2hz;
-    if (i == 0) dr = (-3.f * ph[o].x + 4.f * ph[o + M1].x - ph[o + 2 * M1].x +
-                      (-3.f * ph[o].y + 4.f * ph[o + M1].y - ph[o + 2 * M1].y)) * inv2hr;
-    else if (i == nr) dr = (3.f * ph[o].x - 4.f * ph[o - M1].x + ph[o - 2 * M1].x +
-                            (3.f * ph[o].y - 4.f * ph[o - M1].y + ph[o - 2 * M1].y)) * inv2hr;
-    else dr = df_diff(ph[o + M1], ph[o - M1]) * inv2hr;
-    if (j == 0) dz = (-3.f * ph[o].x + 4.f * ph[o + 1].x - ph[o + 2].x +
-                      (-3.f * ph[o].y + 4.f * ph[o + 1].y - ph[o + 2].y)) * inv2hz;
-    else if (j == M) dz = (3.f * ph[o].x - 4.f * ph[o - 1].x + ph[o - 2].x +
-                           (3.f * ph[o].y - 4.f * ph[o - 1].y + ph[o - 2].y)) * inv2hz;
-    else dz = df_diff(ph[o + 1], ph[o - 1]) * inv2hz;
-    typename Vec2<Real>::type e;
-    if constexpr (std::is_same<Real, float>::value) {
-      e.x = T.evac32[i] - dr;
-      e.y = -dz;
-    } else {
-      // FP64 particle path: the same differences of hi + lo in double
-      auto p = [&](size_t q) { return (double)ph[q].x + (double)ph[q].y; };
-      const double i2r = T.inv2hr_d, i2z = T.inv2hz_d;
-      double ddr, ddz;
-      if (i == 0) ddr = (-3.0 * p(o) + 4.0 * p(o + M1) - p(o + 2 * M1)) * i2r;
-      else if (i == nr) ddr = (3.0 * p(o) - 4.0 * p(o - M1) + p(o - 2 * M1)) * i2r;
-      else ddr = (p(o + M1) - p(o - M1)) * i2r;
-      if (j == 0) ddz = (-3.0 * p(o) + 4.0 * p(o + 1) - p(o + 2)) * i2z;
-      else if (j == M) ddz = (3.0 * p(o) - 4.0 * p(o - 1) + p(o - 2)) * i2z;
-      else ddz = (p(o + 1) - p(o - 1)) * i2z;
-      e.x = T.evac64[i] - ddr;
-      e.y = -ddz;
-    }
-    E[o] = e;
+    E[o] = node_field<Real>(T, ph, T.evac32, T.evac64, o, i, j, LdPlain());
 
     if (i > 0 && i < nr) {
       // r = b' - A' phi_rho in double-float
-      const bool end = (j == 0 || j == M);
-      const float2 mzd = end ? T.mzd_end : T.mzd_in, kzd = end ? T.kzd_end : T.kzd_in;
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
       for (int di = -1; di <= 1; ++di) {
-        const size_t q = o + (ptrdiff_t)di * M1;
-        const float2 c = ph[q];
-        float2 nb = make_float2(0.f, 0.f);
-        if (j > 0) nb = ph[q - 1];
-        if (j < M) nb = df_add(nb, ph[q + 1]);
-        const float2 mz = df_add(df_mul(mzd, c), df_mul(T.mzo, nb));
-        const float2 kz = df_add(df_mul(kzd, c), df_mul(T.kzo, nb));
-        float2 kr, mr;
-        if (di == 0) { kr = T.kr_d[i]; mr = T.mr_d[i]; }
-        else if (di < 0) { kr = T.kr_o[i - 1]; mr = T.mr_o[i - 1]; }
-        else { kr = T.kr_o[i]; mr = T.mr_o[i]; }
-        acc = df_add(acc, df_add(df_mul(kr, mz), df_mul(mr, kz)));
+        float2 mz, kz;
+        node_mzkz(T, ph, o + (ptrdiff_t)di * M1, j, mz, kz, LdPlain());
+        acc = df_add(acc, row_term(T, i, di, mz, kz));
       }
       const float2 r = df_add(T.b2[o], df_neg(acc));
       T.res[o] = r.x;
@@ -646,16 +515,9 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
       const double r2 = *(volatile double*)&st->r2sum;
       const double b2 = *(volatile double*)&st->b2sum;
       const double bl2 = *(volatile double*)&st->bl2sum;
-      const double strict = b2 > 0.0 ? sqrt(r2 / b2) : (r2 > 0.0 ? 1.0 : 0.0);
-      const double rel = bl2 > 0.0 ? sqrt(r2 / bl2) : strict;
-      st->relres_last = rel;
-      st->relres_strict = strict;
-      st->poisson_iters = sweep + 1;
-      if (sweep < 0) st->relres_init = rel;
-      else if (!T.warm) st->relres_init = -1.0;
-      if (rel <= T.rtol || last) {
-        st->solve_done = 1;
-        if (!(rel <= T.rtol)) atomicCAS(&st->err, 0, PIC_ENOCONV);
+      double rel, strict;
+      solve_norms(r2, b2, bl2, rel, strict);
+      if (solve_record(st, T, rel, strict, sweep, last)) {
         st->b2sum = 0.0;
         st->bl2sum = 0.0;
       }
