@@ -97,6 +97,12 @@ struct pic_handle {
   // of the block; captured on a private stream, replayed on the caller's
   cudaStream_t cap_stream;
   int graph_len;                        // steps per graph
+  // The child-uid kernel and the sort run on a second stream beside the
+  // field solve (forked after the particle kernel, joined at the end of
+  // the step) unless a seed source needs the child uids before the solve
+  // or the stages are being timed; null: everything on one stream.
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
   cudaGraphExec_t graph[2][2];
   long long graph_kernels[2][2];
   bool graph_failed;
@@ -312,6 +318,9 @@ int step_impl(pic_handle* h, long long nsteps) {
   const bool solve = h->cfg.fixed_efield == 0;
   const bool batch = h->nsim > 1;
   const size_t grid_nodes = (size_t)h->nsim * h->nnodes;
+  // child uids and the sort beside the field solve (neither reads the
+  // other's data; the source, when on, needs the uids before the solve)
+  const bool fork = solve && h->side && !h->any_source && !h->profiling;
   for (long long s = 0; s < nsteps; ++s) {
     mark(h, kTagStart);
     const bool fp32 = std::is_same<Real, float>::value;
@@ -332,12 +341,18 @@ int step_impl(pic_handle* h, long long nsteps) {
                                  fp32 ? h->cnt[h->dep_buf] : nullptr, h->st, h->spawn_parent, P,
                                  h->grid_particle, h->stream);
     mark(h, kTagParticle);
+    cudaStream_t aux = h->stream;
+    if (fork) {
+      CK(cudaEventRecord(h->ev_fork, h->stream));
+      CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+      aux = h->side;
+    }
     if (batch)
       launch_spawn_finalize_batch(h->st, soa<Real>(h, h->cur).uid, h->spawn_parent,
-                                  h->spawn_stride, h->seg, h->nsim, h->stream);
+                                  h->spawn_stride, h->seg, h->nsim, aux);
     else
       launch_spawn_finalize(h->st, soa<Real>(h, h->cur).uid, h->spawn_parent,
-                            h->sims[0].spawn_cap, h->sims[0].capacity, h->stream);
+                            h->sims[0].spawn_cap, h->sims[0].capacity, aux);
     h->kernels += 2;
     if (h->any_source) {
       launch_source<Real>(soa<Real>(h, h->cur), h->st, params_dev<Real>(h), h->nsim,
@@ -350,11 +365,10 @@ int step_impl(pic_handle* h, long long nsteps) {
     if (h->cfg.sort_every > 0 && h->step % h->cfg.sort_every == 0) {
       if (batch)
         launch_sort_batch<Real>(soa<Real>(h, h->cur), soa<Real>(h, h->cur ^ 1), h->st, h->seg,
-                                h->nsim, h->cell_count, h->ncells, h->cfg.nz, h->grid_sort,
-                                h->stream);
+                                h->nsim, h->cell_count, h->ncells, h->cfg.nz, h->grid_sort, aux);
       else
         launch_sort<Real>(soa<Real>(h, h->cur), soa<Real>(h, h->cur ^ 1), h->st, h->cell_count,
-                          h->ncells, h->cfg.nz, h->grid_sort, h->stream);
+                          h->ncells, h->cfg.nz, h->grid_sort, aux);
       h->cur ^= 1;
       h->kernels += 4;
       mark(h, kTagSort);
@@ -380,6 +394,10 @@ int step_impl(pic_handle* h, long long nsteps) {
       if (fp32) h->dep_buf ^= 1;
       h->kernels += field_solve_kernels(h->T);
       mark(h, kTagField);
+    }
+    if (fork) {
+      CK(cudaEventRecord(h->ev_join, h->side));
+      CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     }
   }
   CK(cudaGetLastError());
@@ -612,6 +630,15 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   h->last_buf = 0;
   h->dep_buf = c.fixed_efield ? 0 : 1;
   set_graph_len(h);
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    h->side = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
+  }
   *out = h;
   return PIC_OK;
 }
@@ -623,6 +650,12 @@ void pic_free(pic_handle* h) {
     for (auto& x : row)
       if (x) cudaGraphExecDestroy(x);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (void* p : h->owned) h_free_one(p, h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
