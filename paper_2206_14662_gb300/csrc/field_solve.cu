@@ -312,10 +312,14 @@ k_dct32(FieldTables T, const DevState* st, int sweep) {
   const bool two = line0 + 1 < NI;
   const float* x = FWD ? T.res + (size_t)(line0 + 1) * M1 : T.phihat + (size_t)line0 * M1;
   const float* y = x + M1;
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+  // bit-reversed input order, gathered from global memory so that the
+  // shared-memory writes are consecutive (a bit-reversed scatter puts a
+  // warp's writes N/2 apart, all in one bank)
+  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    const int n = __brev(p) >> (32 - log2N);
     const int m = n <= M ? n : N - n;
-    sh[__brev(n) >> (32 - log2N)] = make_float2(x[m], two ? y[m] : 0.f);
-    if (n < N / 2) tw[n] = T.tw32[n];
+    sh[p] = make_float2(x[m], two ? y[m] : 0.f);
+    if (p < N / 2) tw[p] = T.tw32[p];
   }
   __syncthreads();
   for (int s = 1; s <= log2N; ++s) {
@@ -378,12 +382,13 @@ __global__ void k_dct32_direct(FieldTables T, const DevState* st, int sweep) {
 // consecutive modes (33 blocks on the 512-cell grid); its 256 threads first
 // copy the columns it needs into shared memory, 16 rows at a time with four
 // rows' loads in flight per thread, so the recurrence, run by the first
-// half-warp, then waits only on shared memory.  Right-hand side,
-// sub-diagonal and pivot serve the forward pass; the super-diagonal serves
-// the backward pass.
+// half-warp, then reads only shared memory, eight rows' operands at a time
+// ahead of their dependent chain.  Right-hand side, sub-diagonal and pivot
+// serve the forward pass; the super-diagonal serves the backward pass.
 constexpr int kTriModes = 16;
 constexpr int kTriThreads = 256;
 constexpr int kTriRows = kTriThreads / kTriModes;   // rows staged per pass
+constexpr int kTriBatch = 8;                        // rows per register batch of the recurrence
 __global__ void __launch_bounds__(kTriThreads) k_tridiag32(FieldTables T, const DevState* st,
                                                            int sweep) {
   const int sim = blockIdx.y;
@@ -410,19 +415,42 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag32(FieldTables T, const 
   }
   __syncthreads();
   if (threadIdx.x < kTriModes) {
+    // the recurrence in batches of kTriBatch rows: the batch's operands
+    // are loaded into registers before its dependent chain starts
     float y = 0.f;
-#pragma unroll 8
-    for (int i = 0; i < NI; ++i) {
-      const int o = i * kTriModes + col;
-      y = thomas_fwd(sb[o], sa[o], sd[o], y);
-      sb[o] = y;
+    for (int i0 = 0; i0 < NI; i0 += kTriBatch) {
+      float b[kTriBatch], a[kTriBatch], d[kTriBatch];
+#pragma unroll
+      for (int k = 0; k < kTriBatch; ++k) {
+        const int o = min(i0 + k, NI - 1) * kTriModes + col;
+        b[k] = sb[o];
+        a[k] = sa[o];
+        d[k] = sd[o];
+      }
+#pragma unroll
+      for (int k = 0; k < kTriBatch; ++k) {
+        if (i0 + k < NI) {
+          y = thomas_fwd(b[k], a[k], d[k], y);
+          sb[(i0 + k) * kTriModes + col] = y;
+        }
+      }
     }
     float xn = 0.f;
-#pragma unroll 8
-    for (int i = NI - 1; i >= 0; --i) {
-      const int o = i * kTriModes + col;
-      xn = thomas_bwd(sb[o], sc[o], xn);
-      sb[o] = xn;
+    for (int i0 = NI - 1; i0 >= 0; i0 -= kTriBatch) {
+      float b[kTriBatch], c[kTriBatch];
+#pragma unroll
+      for (int k = 0; k < kTriBatch; ++k) {
+        const int o = max(i0 - k, 0) * kTriModes + col;
+        b[k] = sb[o];
+        c[k] = sc[o];
+      }
+#pragma unroll
+      for (int k = 0; k < kTriBatch; ++k) {
+        if (i0 - k >= 0) {
+          xn = thomas_bwd(b[k], c[k], xn);
+          sb[(i0 - k) * kTriModes + col] = xn;
+        }
+      }
     }
   }
   __syncthreads();
