@@ -202,13 +202,20 @@ void fill_params(pic_handle* h, int k, PushParams<Real>& P) {
   const pic_config& c = h->cfgs[k];
   const SimHost& m = h->sims[k];
   const double L = c.z_max - c.z_min;
-  P.r_in = (Real)c.r_in; P.hr = (Real)h->hr; P.inv_hr = (Real)(1.0 / h->hr);
-  P.z_min = (Real)c.z_min; P.hz = (Real)h->hz; P.inv_hz = (Real)(1.0 / h->hz);
-  P.z_mid = (Real)(0.5 * (c.z_min + c.z_max)); P.inv_L2 = (Real)(1.0 / (L * L));
-  P.b0 = (Real)c.b0;
+  P.r_in = (Real)c.r_in; P.hr = (Real)h->hr;
+  P.z_min = (Real)c.z_min; P.hz = (Real)h->hz;
   P.nr = c.nr; P.nz = c.nz; P.bkind = c.bfield_kind;
   P.qmdt2 = (Real)(-kQe * c.dt / (2.0 * kMe));
   P.dt = (Real)c.dt;
+  P.dt_hr = (Real)(c.dt / h->hr);
+  P.dt_hz = (Real)(c.dt / h->hz);
+  P.zoff = (Real)(c.z_min - 0.5 * (c.z_min + c.z_max));
+  {
+    const double q = -kQe * c.dt / (2.0 * kMe), il2 = 1.0 / (L * L);
+    P.tz0 = (Real)(q * c.b0);
+    P.tzc = (Real)(c.bfield_kind == 1 ? 2.0 * q * c.b0 * il2 : 0.0);
+    P.trc = (Real)(c.bfield_kind == 1 ? -2.0 * q * c.b0 * il2 : 0.0);
+  }
   P.thr_null = m.thr_null;
   P.nsig_el = (Real)(m.n_gas * c.sigma_el);
   P.n_gas = (Real)m.n_gas;

@@ -113,13 +113,17 @@ struct DepGrid {
   double qw;
 };
 
+// FP32: the fixed-point count of a corner is rn((w_r kFix) w_z), the same
+// rounding sequence as the shared-tile path of deposit_chunk, so a node's
+// sum does not depend on which path a particle takes
 __device__ __forceinline__ void deposit_global(const DepGrid& g, int ir, int iz, float fr,
                                                float fz) {
   const int n00 = ir * g.nzp + iz;
-  atomicAdd(g.cnt + n00, (unsigned long long)__float2uint_rn((1.f - fr) * (1.f - fz) * kFix));
-  atomicAdd(g.cnt + n00 + g.nzp, (unsigned long long)__float2uint_rn(fr * (1.f - fz) * kFix));
-  atomicAdd(g.cnt + n00 + 1, (unsigned long long)__float2uint_rn((1.f - fr) * fz * kFix));
-  atomicAdd(g.cnt + n00 + g.nzp + 1, (unsigned long long)__float2uint_rn(fr * fz * kFix));
+  const float ra = (1.f - fr) * kFix, rb = fr * kFix, za = 1.f - fz;
+  atomicAdd(g.cnt + n00, (unsigned long long)__float2uint_rn(ra * za));
+  atomicAdd(g.cnt + n00 + g.nzp, (unsigned long long)__float2uint_rn(rb * za));
+  atomicAdd(g.cnt + n00 + 1, (unsigned long long)__float2uint_rn(ra * fz));
+  atomicAdd(g.cnt + n00 + g.nzp + 1, (unsigned long long)__float2uint_rn(rb * fz));
 }
 __device__ __forceinline__ void deposit_global(const DepGrid& g, int ir, int iz, double fr,
                                                double fz) {
@@ -244,16 +248,17 @@ __device__ __forceinline__ Dep<Real> advance(
   const Real w00 = gr * gz, w10 = fr * gz, w01 = gr * fz, w11 = fr * fz;
   const Real Er = mad(w11, e11.x, mad(w01, e01.x, mad(w10, e10.x, w00 * e00.x)));
   const Real Ez = mad(w11, e11.y, mad(w01, e01.y, mad(w10, e10.y, w00 * e00.y)));
-  Real Br = 0, Bz = P.b0;
+  // t = (q dt / 2m) B: mirror Bz = b0 (1 + 2 zeta^2 / L^2),
+  // Br = -2 b0 r zeta / L^2 (constants folded on the host)
+  Real tr = 0, tz = P.tz0;
   if (P.bkind == 1) {
-    const Real zeta = mad((Real)iz + fz, P.hz, P.z_min) - P.z_mid;
-    Bz = P.b0 * mad(2 * zeta * zeta, P.inv_L2, Real(1));
-    Br = -2 * P.b0 * r * zeta * P.inv_L2;
+    const Real zeta = mad((Real)iz + fz, P.hz, P.zoff);
+    tz = mad(P.tzc * zeta, zeta, P.tz0);
+    tr = P.trc * r * zeta;
   }
 
   // Boris: half kick, rotation about B, half kick (components r, theta, z)
   const Real vmr = mad(P.qmdt2, Er, vr), vmt = vt, vmz = mad(P.qmdt2, Ez, vz);
-  const Real tr = P.qmdt2 * Br, tz = P.qmdt2 * Bz;
   const Real sf = q_div(Real(2), mad(tz, tz, mad(tr, tr, Real(1))));
   const Real sr = sf * tr, sz = sf * tz;
   const Real qr = mad(vmt, tz, vmr);
@@ -273,8 +278,8 @@ __device__ __forceinline__ Dep<Real> advance(
   const Real inv_r1 = q_rsqrt(rr);
   const Real r1 = rr * inv_r1;
   const Real v2p = mad(vnt, vnt, vnr * vnr);
-  const Real dr_cells = q_div(P.dt * mad(v2p, P.dt, 2 * r * vnr), r + r1) * P.inv_hr;
-  const Real dz_cells = vnz * P.dt * P.inv_hz;
+  const Real dr_cells = q_div(mad(v2p, P.dt, 2 * r * vnr), r + r1) * P.dt_hr;
+  const Real dz_cells = vnz * P.dt_hz;
   Real fr1 = fr + dr_cells, fz1 = fz + dz_cells;
   // cell jumps beyond +-2^20 cells (non-physical speeds) are clamped before
   // the integer conversion; they end outside the grid and are absorbed
@@ -443,6 +448,12 @@ __device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename Til
   const bool use_tile = any && rows * cols <= cap;
   const int warp = tid >> 5;
   if (use_tile) {
+    // FP32: the m-th update of a lane goes to corner m ^ rot (bit 0 along
+    // r, bit 1 along z), rot = (lane >> 2) & 3; its weight and word offset
+    // per corner parity are chosen once per chunk and particle
+    const int rot = (lane >> 2) & 3;
+    const int cr0 = kCopies * ((rot & 1) ? cols : 0), cr1 = kCopies * ((rot & 1) ? 0 : cols);
+    const int cz0 = kCopies * (rot >> 1), cz1 = kCopies * ((rot >> 1) ^ 1);
 #pragma unroll
     for (int k = 0; k < kPPT; ++k) {
       if (dep[k].ir < 0) continue;
@@ -450,15 +461,12 @@ __device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename Til
       if constexpr (f32) {
         const float a = dep[k].fr, c = dep[k].fz;
         unsigned* tc = tile + kCopies * t + (lane & 3);
-        const int rot = (lane >> 2) & 3;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int j = (m + rot) & 3;   // corner: bit 0 along r, bit 1 along z
-          const float wr = (j & 1) ? a : 1.f - a;
-          const float wz = (j & 2) ? c : 1.f - c;
-          atomicAdd(tc + kCopies * (((j & 1) ? cols : 0) + (j >> 1)),
-                    __float2uint_rn(wr * wz * kFix));
-        }
+        const float ra = ((rot & 1) ? a : 1.f - a) * kFix, rb = ((rot & 1) ? 1.f - a : a) * kFix;
+        const float za = (rot & 2) ? c : 1.f - c, zb = (rot & 2) ? 1.f - c : c;
+        atomicAdd(tc + cr0 + cz0, __float2uint_rn(ra * za));
+        atomicAdd(tc + cr1 + cz0, __float2uint_rn(rb * za));
+        atomicAdd(tc + cr0 + cz1, __float2uint_rn(ra * zb));
+        atomicAdd(tc + cr1 + cz1, __float2uint_rn(rb * zb));
       } else {
         const TT a = (TT)dep[k].fr, c = (TT)dep[k].fz;
         atomicAdd(&tile[t], (TT(1) - a) * (TT(1) - c));

@@ -84,12 +84,16 @@ template <> struct Vec2<double> { using type = double2; };
 // Parameters of the fused particle kernel, in the particle precision.
 template <typename Real>
 struct PushParams {
-  Real r_in, hr, inv_hr;      // radial grid
-  Real z_min, hz, inv_hz;     // axial grid
-  Real z_mid, inv_L2, b0;     // magnetic field: mirror centre, 1/L^2
+  Real r_in, hr;              // radial grid
+  Real z_min, hz;             // axial grid
   int nr, nz, bkind;          // cells, field kind
   Real qmdt2;                 // q dt / (2 m)
   Real dt;
+  Real dt_hr, dt_hz;          // dt / h_r, dt / h_z
+  Real zoff;                  // z_min - z_mid
+  // the Boris rotation vector t = (q dt / 2m) B: t_z = tz0 + tzc zeta^2,
+  // t_r = trc r zeta (mirror field; uniform: t_z = tz0, t_r = 0)
+  Real tz0, tzc, trc;
   unsigned thr_null;          // candidate iff (x0 >> 8) < thr_null
   Real nsig_el;               // n_gas sigma_el, 1/m
   Real n_gas;
