@@ -262,10 +262,10 @@ __device__ __forceinline__ Dep<Real> advance(
   const Real sf = q_div(Real(2), mad(tz, tz, mad(tr, tr, Real(1))));
   const Real sr = sf * tr, sz = sf * tz;
   const Real qr = mad(vmt, tz, vmr);
-  const Real qt = vmt + (vmz * tr - vmr * tz);
+  const Real qt = vmt + mad(vmz, tr, -vmr * tz);
   const Real qz = mad(-vmt, tr, vmz);
   const Real vpr = mad(qt, sz, vmr);
-  const Real vpt = vmt + (qz * sr - qr * sz);
+  const Real vpt = vmt + mad(qz, sr, -qr * sz);
   const Real vpz = mad(-qt, sr, vmz);
   const Real vnr = mad(P.qmdt2, Er, vpr), vnt = vpt, vnz = mad(P.qmdt2, Ez, vpz);
   // work of the two half kicks, (q dt / 4) E . (v + v- + v+ + v_new)
