@@ -240,14 +240,15 @@ __device__ __forceinline__ Dep<Real> advance(
   const Real fr = q.fr, fz = q.fz, vr = q.vr, vt = q.vt, vz = q.vz;
   const Real r = mad((Real)ir + fr, P.hr, P.r_in);
 
-  // gather: bilinear weights of the four nodes of the cell
+  // gather: bilinear interpolation of the cell's four nodes, as linear
+  // interpolation along r on both z-edges, then along z
   const int n00 = ir * nzp + iz;
   const V2 e00 = __ldg(E + n00), e01 = __ldg(E + n00 + 1);
   const V2 e10 = __ldg(E + n00 + nzp), e11 = __ldg(E + n00 + nzp + 1);
-  const Real gr = 1 - fr, gz = 1 - fz;
-  const Real w00 = gr * gz, w10 = fr * gz, w01 = gr * fz, w11 = fr * fz;
-  const Real Er = mad(w11, e11.x, mad(w01, e01.x, mad(w10, e10.x, w00 * e00.x)));
-  const Real Ez = mad(w11, e11.y, mad(w01, e01.y, mad(w10, e10.y, w00 * e00.y)));
+  const Real ar0 = mad(fr, e10.x - e00.x, e00.x), ar1 = mad(fr, e11.x - e01.x, e01.x);
+  const Real az0 = mad(fr, e10.y - e00.y, e00.y), az1 = mad(fr, e11.y - e01.y, e01.y);
+  const Real Er = mad(fz, ar1 - ar0, ar0);
+  const Real Ez = mad(fz, az1 - az0, az0);
   // t = (q dt / 2m) B: mirror Bz = b0 (1 + 2 zeta^2 / L^2),
   // Br = -2 b0 r zeta / L^2 (constants folded on the host)
   Real tr = 0, tz = P.tz0;
@@ -286,11 +287,13 @@ __device__ __forceinline__ Dep<Real> advance(
   const Real jmax = Real(1048576);
   const Real flr = fmin(fmax(d_floor(fr1), -jmax), jmax);
   const Real flz = fmin(fmax(d_floor(fz1), -jmax), jmax);
-  int ir1 = ir + (int)flr, iz1 = iz + (int)flz;
-  fr1 -= flr;
-  fz1 -= flz;
-  if (fr1 >= 1) { fr1 = 0; ++ir1; }
-  if (fz1 >= 1) { fz1 = 0; ++iz1; }
+  const int ir1 = ir + (int)flr, iz1 = iz + (int)flz;
+  // an offset that rounds up to 1 (a tiny negative sum) stays in its cell
+  // at the largest offset below 1
+  const Real below1 = std::is_same<Real, float>::value ? Real(0x1.fffffep-1f)
+                                                       : Real(0x1.fffffffffffffp-1);
+  fr1 = fmin(fr1 - flr, below1);
+  fz1 = fmin(fz1 - flz, below1);
 
   // absorbing walls: r1 <= a, r1 >= b, z1 <= z_min, z1 >= z_max
   const bool out_in = ir1 < 0 || (ir1 == 0 && fr1 == 0);
