@@ -360,13 +360,16 @@ def test_full_size_mirror_128x512_1e7_one_step():
     del next0
 
 
-def test_graph_replay_matches_direct_launches():
+@pytest.mark.parametrize("warm", [1, 0])
+def test_graph_replay_matches_direct_launches(warm):
     """Blocks of steps replayed as CUDA graphs give bit-identical particles
     and potential to the same steps launched one by one (the deposit is
     integer fixed-point and every particle's arithmetic is fixed, so the
-    FP32 run is deterministic)."""
+    FP32 run is deterministic).  Warm-started solves converge in one sweep,
+    cold-started ones take two."""
     from paper_2206_14662_gb300._capi import PIC_GRID_PHI, Simulation
-    cfg = workload("mirror_128x512_1e7", n_init=50_000, p_mbar=0.3, T0_eV=20.0, sort_every=4)
+    cfg = workload("mirror_128x512_1e7", n_init=50_000, p_mbar=0.3, T0_eV=20.0, sort_every=4,
+                   warm_start=warm)
     parts = seed_particles(cfg)
     out = []
     for profiled in (True, False):
@@ -385,6 +388,8 @@ def test_graph_replay_matches_direct_launches():
         assert np.array_equal(ga[k], gb[k]), k
     assert np.array_equal(pa, pb)
     assert da["n_pushed"] == db["n_pushed"] and da["step"] == db["step"] == 40
+    assert da["poisson_iters"] == db["poisson_iters"] == (1 if warm else 2)
+    assert da["poisson_relres"] == pytest.approx(db["poisson_relres"], rel=1e-12)
     assert db["kernels_launched"] == da["kernels_launched"]
 
 
