@@ -257,8 +257,12 @@ int field_tables_build(const pic_config* cfgs, int nsim, FieldTables& T,
 
 // ---------------------------------------------------------------- prep
 
+// node-pass blocks: up to 32 x 16 threads (launch_field_solve picks the shape)
+constexpr int kNodeThreads = 512;
+constexpr int kNodeWarps = kNodeThreads / 32;
+
 template <bool FIX>
-__global__ void __launch_bounds__(256) k_prep(ChargeIn in, FieldTables T, DevState* st) {
+__global__ void __launch_bounds__(kNodeThreads) k_prep(ChargeIn in, FieldTables T, DevState* st) {
   const int M1 = T.M + 1, nr = T.nr;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(256) k_prep(ChargeIn in, FieldTables T, DevSta
     const float2 b = prep_node<FIX>(in, T, sim, o, i, j, nb, nl);
     if (i > 0 && i < nr) T.res[o] = b.x;
   }
-  __shared__ float red[2][8];
+  __shared__ float red[2][kNodeWarps];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, w = tid >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -472,7 +476,7 @@ static size_t tridiag_smem(const FieldTables& T) {
 // PREP (the warm start's first pass): b' is formed here as in k_prep before
 // the residual of the previous solution, so one pass replaces two.
 template <typename Real, int PREP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kNodeThreads)
 k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep, int last,
            ChargeIn in) {
   const int sim = blockIdx.z;
@@ -514,7 +518,7 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
     }
   }
   // block reduction, then the last block evaluates the stopping test
-  __shared__ float red[3][8];
+  __shared__ float red[3][kNodeWarps];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, w = tid >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -579,7 +583,12 @@ void launch_field_solve(const FieldTables& T, const double* rhs, const unsigned 
                         double cnt_unit, const float2* cnt_units, unsigned long long* cnt_clear,
                         void* efield, DevState* st, cudaStream_t stream) {
   const int M1 = T.M + 1, S = T.nsim;
-  dim3 blk(32, 8), grd((M1 + 31) / 32, (T.nr + 1 + 7) / 8, S);
+  // node passes: 32 x 16 blocks for one simulation (half the blocks, so
+  // half the same-address norm atomics of the 32 x 8 shape: 37 against 40
+  // us per solve in the graph-replayed 128 x 512 step); 32 x 8 for a
+  // batch, whose many blocks fill the GPU better in the smaller shape
+  const int by = S == 1 ? 16 : 8;
+  dim3 blk(32, by), grd((M1 + 31) / 32, (T.nr + 1 + by - 1) / by, S);
   const double s0 = 1.0 / (2.0 * kPi * kEps0);
   if (tridiag_smem(T) > 48 * 1024)
     cudaFuncSetAttribute(k_tridiag32, cudaFuncAttributeMaxDynamicSharedMemorySize,
