@@ -40,11 +40,6 @@ __device__ __forceinline__ float df_diff(float2 a, float2 b) {   // a - b to flo
   return (a.x - b.x) + (a.y - b.y);
 }
 
-// loads of the solve's work arrays (written by earlier launches)
-struct LdPlain {
-  template <typename T> __device__ __forceinline__ T operator()(const T* p) const { return *p; }
-};
-
 // ---------------------------------------------------------------- prep
 
 // the deposit's charge source of a solve
@@ -102,38 +97,38 @@ __device__ __forceinline__ float2 prep_node(const ChargeIn& in, const FieldTable
 // simulation's grid: central differences, one-sided second order on the
 // boundary lines (phi_rho is zero on the walls).  FP32 particle path: the
 // differences of hi and lo pairs in float; FP64: of hi + lo in double.
-template <typename Real, class Ld>
+template <typename Real>
 __device__ __forceinline__ typename Vec2<Real>::type node_field(
     const FieldTables& T, const float2* ph, const float* evac32, const double* evac64, size_t o,
-    int i, int j, Ld ld) {
+    int i, int j) {
   const int nr = T.nr, M = T.M, M1 = M + 1;
   typename Vec2<Real>::type e;
   if constexpr (std::is_same<Real, float>::value) {
     float dr, dz;
     const float inv2hr = T.inv2hr, inv2hz = T.inv2hz;
     if (i == 0) {
-      const float2 a = ld(ph + o), b = ld(ph + o + M1), c = ld(ph + o + 2 * M1);
+      const float2 a = ph[o], b = ph[o + M1], c = ph[o + 2 * M1];
       dr = (-3.f * a.x + 4.f * b.x - c.x + (-3.f * a.y + 4.f * b.y - c.y)) * inv2hr;
     } else if (i == nr) {
-      const float2 a = ld(ph + o), b = ld(ph + o - M1), c = ld(ph + o - 2 * M1);
+      const float2 a = ph[o], b = ph[o - M1], c = ph[o - 2 * M1];
       dr = (3.f * a.x - 4.f * b.x + c.x + (3.f * a.y - 4.f * b.y + c.y)) * inv2hr;
     } else {
-      dr = df_diff(ld(ph + o + M1), ld(ph + o - M1)) * inv2hr;
+      dr = df_diff(ph[o + M1], ph[o - M1]) * inv2hr;
     }
     if (j == 0) {
-      const float2 a = ld(ph + o), b = ld(ph + o + 1), c = ld(ph + o + 2);
+      const float2 a = ph[o], b = ph[o + 1], c = ph[o + 2];
       dz = (-3.f * a.x + 4.f * b.x - c.x + (-3.f * a.y + 4.f * b.y - c.y)) * inv2hz;
     } else if (j == M) {
-      const float2 a = ld(ph + o), b = ld(ph + o - 1), c = ld(ph + o - 2);
+      const float2 a = ph[o], b = ph[o - 1], c = ph[o - 2];
       dz = (3.f * a.x - 4.f * b.x + c.x + (3.f * a.y - 4.f * b.y + c.y)) * inv2hz;
     } else {
-      dz = df_diff(ld(ph + o + 1), ld(ph + o - 1)) * inv2hz;
+      dz = df_diff(ph[o + 1], ph[o - 1]) * inv2hz;
     }
     e.x = evac32[i] - dr;
     e.y = -dz;
   } else {
     auto p = [&](size_t q) {
-      const float2 v = ld(ph + q);
+      const float2 v = ph[q];
       return (double)v.x + (double)v.y;
     };
     const double i2r = T.inv2hr_d, i2z = T.inv2hz_d;
@@ -151,16 +146,15 @@ __device__ __forceinline__ typename Vec2<Real>::type node_field(
 }
 
 // M_z phi and K_z phi of the r-line holding node q (column j), double-float
-template <class Ld>
 __device__ __forceinline__ void node_mzkz(const FieldTables& T, const float2* ph, size_t q, int j,
-                                          float2& mz, float2& kz, Ld ld) {
+                                          float2& mz, float2& kz) {
   const int M = T.M;
   const bool end = (j == 0 || j == M);
   const float2 mzd = end ? T.mzd_end : T.mzd_in, kzd = end ? T.kzd_end : T.kzd_in;
-  const float2 c = ld(ph + q);
+  const float2 c = ph[q];
   float2 nb = make_float2(0.f, 0.f);
-  if (j > 0) nb = ld(ph + q - 1);
-  if (j < M) nb = df_add(nb, ld(ph + q + 1));
+  if (j > 0) nb = ph[q - 1];
+  if (j < M) nb = df_add(nb, ph[q + 1]);
   mz = df_add(df_mul(mzd, c), df_mul(T.mzo, nb));
   kz = df_add(df_mul(kzd, c), df_mul(T.kzo, nb));
 }

@@ -501,7 +501,7 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
   if (i <= nr && j <= M) {
     const size_t o = (size_t)i * M1 + j;
     const float2* ph = T.phir;
-    E[o] = node_field<Real>(T, ph, T.evac32, T.evac64, o, i, j, LdPlain());
+    E[o] = node_field<Real>(T, ph, T.evac32, T.evac64, o, i, j);
 
     if (i > 0 && i < nr) {
       // r = b' - A' phi_rho in double-float
@@ -509,7 +509,7 @@ k_residual(FieldTables T, typename Vec2<Real>::type* E, DevState* st, int sweep,
 #pragma unroll
       for (int di = -1; di <= 1; ++di) {
         float2 mz, kz;
-        node_mzkz(T, ph, o + (ptrdiff_t)di * M1, j, mz, kz, LdPlain());
+        node_mzkz(T, ph, o + (ptrdiff_t)di * M1, j, mz, kz);
         acc = df_add(acc, row_term(T, i, di, mz, kz));
       }
       const float2 r = df_add(T.b2[o], df_neg(acc));
