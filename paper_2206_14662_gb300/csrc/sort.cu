@@ -128,28 +128,50 @@ __global__ void __launch_bounds__(1024) k_sort_scan(int* count, int n, DevState*
 // scatter: a block takes 1024 consecutive slots in four passes of 256
 // lane-consecutive slots (coalesced loads; runs of equal cells fall on
 // consecutive lanes, which then write consecutive destination slots); each
-// live particle goes to its cell's next free slot in the other buffer set
+// live particle goes to its cell's next free slot in the other buffer set.
+// A thread first loads its four particles, then claims the four runs'
+// slots (independent atomics in flight together), then stores, so the
+// loads and the atomics' round trips overlap instead of alternating.
 template <typename Real>
 __device__ __forceinline__ void scatter_group(const Soa<Real>& src, const Soa<Real>& dst, int n,
                                               int base, int* cursor, int nz, int lane) {
+  int c[4], key[4];
+  Real fr[4], fz[4], vr[4], vt[4], vz[4];
+  unsigned id[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int p = base + k * kSortThreads + (int)threadIdx.x;
-    const int c = p < n ? src.cell[p] : -1;
-    const int key = cell_key(c, nz);
-    const Run r = lane_run(key, lane);
-    int slot = 0;
-    if (key >= 0 && r.head) slot = atomicAdd(cursor + key, r.len);
-    slot = __shfl_sync(0xffffffffu, slot, r.first);
-    if (key >= 0) {
-      const int q = slot + (lane - r.first);
-      dst.cell[q] = c;
-      dst.offr[q] = src.offr[p];
-      dst.offz[q] = src.offz[p];
-      dst.vr[q] = src.vr[p];
-      dst.vt[q] = src.vt[p];
-      dst.vz[q] = src.vz[p];
-      dst.uid[q] = src.uid[p];
+    c[k] = p < n ? src.cell[p] : -1;
+    key[k] = cell_key(c[k], nz);
+    if (key[k] >= 0) {
+      fr[k] = src.offr[p];
+      fz[k] = src.offz[p];
+      vr[k] = src.vr[p];
+      vt[k] = src.vt[p];
+      vz[k] = src.vz[p];
+      id[k] = src.uid[p];
+    }
+  }
+  Run r[4];
+  int slot[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    r[k] = lane_run(key[k], lane);
+    slot[k] = 0;
+    if (key[k] >= 0 && r[k].head) slot[k] = atomicAdd(cursor + key[k], r[k].len);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int s0 = __shfl_sync(0xffffffffu, slot[k], r[k].first);
+    if (key[k] >= 0) {
+      const int q = s0 + (lane - r[k].first);
+      dst.cell[q] = c[k];
+      dst.offr[q] = fr[k];
+      dst.offz[q] = fz[k];
+      dst.vr[q] = vr[k];
+      dst.vt[q] = vt[k];
+      dst.vz[q] = vz[k];
+      dst.uid[q] = id[k];
     }
   }
 }
