@@ -410,9 +410,9 @@ __device__ __forceinline__ void store_group(const Soa<Real>& s, int p0, int n, c
 // FP32 tile: unsigned fixed-point weights, native integer shared atomics.
 // Cell-sorted particles put whole warps on the same four nodes, and
 // same-address atomics of one instruction serialise; so the tile is kept in
-// kCopies private copies (lane & 3 picks the copy) and each lane issues its
-// four corner updates in an order rotated by (lane >> 2) & 3.  Lanes of one
-// cell then hit 16 different words per instruction.  The copies of a node
+// kCopies private copies (lane & 3 picks the copy) and the m-th of a
+// lane's four corner updates goes to corner m ^ ((lane >> 2) & 3).  Lanes
+// of one cell then hit 16 different words per instruction.  The copies of a node
 // are interleaved word by word (word 4 t + c), which spreads those 16 words
 // over different banks and lets the flush read a node's copies as one
 // 16-byte vector.
