@@ -89,7 +89,8 @@ typedef struct pic_config {
   double nu_max;           /* collision majorant, s^-1; 0 derives
                               (1 + 1e-6) max_E n (sigma_el + sigma_io(E)) v
                               over E = E_cap k / 1e5, k = 0..1e5,
-                              E_cap = 2 |v_inner - v_outer| eV */
+                              E_cap = 2 |v_inner - v_outer| eV (with the
+                              tables of pic_set_cross_sections once set) */
   int32_t fixed_efield;    /* 1: skip the field solve; E stays as set by
                               pic_set_efield (particle-only stepping) */
   int32_t warm_start;      /* initial guess of each field solve's
@@ -220,6 +221,26 @@ int pic_export_particles(pic_handle* h, int sim, double* r, double* z,
  * Synchronises. */
 int pic_set_efield(pic_handle* h, int sim, const double* er,
                    const double* ez);
+
+/* Tabulated cross sections of simulation `sim` (Sec. II.A takes the
+ * elastic momentum-transfer and the total ionisation cross sections from
+ * tabulated data, and the scattering angle from an analytic law whose
+ * anisotropy depends on the energy).  E_eV: n strictly increasing energies
+ * >= 0 (eV), 2 <= n <= PIC_XS_MAX_POINTS; sigma_el_m2, sigma_io_m2: n
+ * values >= 0 (m^2); xi: n anisotropies in [0, 1) of the angle law, or
+ * NULL to keep the config's constant xi_param.  At energy E the values are
+ * f_k + w (f_{k+1} - f_k), E_k <= E < E_{k+1}, w = (E - E_k) / (E_{k+1} -
+ * E_k); the first (last) value holds at or below E_0 (at or above
+ * E_{n-1}); sigma_io counts as 0 at or below ion_E_th_eV whatever the
+ * table says.  The collision majorant is derived again from the tables as
+ * at pic_init (unless the config set nu_max) and the step graphs are
+ * rebuilt.  n = 0 (arrays ignored) returns to the config's analytic cross
+ * sections.  The arrays are copied; the caller keeps them.  PIC_EINVAL on
+ * a bad argument. */
+#define PIC_XS_MAX_POINTS 1024
+int pic_set_cross_sections(pic_handle* h, int sim, int n, const double* E_eV,
+                           const double* sigma_el_m2, const double* sigma_io_m2,
+                           const double* xi);
 
 enum {
   PIC_GRID_PHI = 0,   /* potential phi, V */

@@ -74,6 +74,9 @@ class _Params(ctypes.Structure):
         ("gas_mass_kg", ctypes.c_double), ("weight", ctypes.c_double),
         ("dt", ctypes.c_double), ("nu_max", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("T0_eV", ctypes.c_double),
+        ("xs_n", ctypes.c_int32), ("xs_E_eV", ctypes.c_void_p),
+        ("xs_sigma_el", ctypes.c_void_p), ("xs_sigma_io", ctypes.c_void_p),
+        ("xs_xi", ctypes.c_void_p),
     ]
 
 
@@ -93,6 +96,8 @@ def lib():
         L.or_nu_max.restype = d
         L.or_sigma_ion.argtypes = [P, d]
         L.or_sigma_ion.restype = d
+        L.or_xs_lookup.argtypes = [P, d, vp, vp, vp]
+        L.or_xs_lookup.restype = None
         L.or_scatter_dir.argtypes = [vp, d, d, d, vp]
         L.or_scatter_dir.restype = None
         L.or_opal_secondary.argtypes = [d, d, d]
@@ -141,6 +146,17 @@ def params(cfg: dict) -> _Params:
         opal_B_eV=cfg["opal_B_eV"], xi=cfg["xi_param"],
         gas_mass_kg=d["gas_mass_kg"], weight=d["weight"], dt=cfg["dt"],
         nu_max=0.0, seed=cfg["seed"], T0_eV=cfg.get("T0_eV", 1.0))
+    xs = cfg.get("xs")
+    if xs is not None:
+        # tabulated cross sections: cfg["xs"] = dict(E_eV, sigma_el, sigma_io,
+        # xi or None), kept alive on the structure
+        arrs = [np.ascontiguousarray(xs[k], dtype=np.float64) for k in ("E_eV", "sigma_el", "sigma_io")]
+        xi = xs.get("xi")
+        arrs.append(None if xi is None else np.ascontiguousarray(xi, dtype=np.float64))
+        p._xs_keep = arrs
+        p.xs_n = len(arrs[0])
+        p.xs_E_eV, p.xs_sigma_el, p.xs_sigma_io = (_ptr(a) for a in arrs[:3])
+        p.xs_xi = None if arrs[3] is None else _ptr(arrs[3])
     if cfg.get("nu_max", 0.0) > 0:
         p.nu_max = cfg["nu_max"]
     else:
@@ -177,8 +193,22 @@ def opal_secondary(E_rem, B, u) -> float:
 
 
 def sigma_ion(cfg: dict, E_eV: float) -> float:
-    p = params(cfg)
+    p = params(dict(cfg, nu_max=1.0))   # (the majorant is not needed here)
     return lib().or_sigma_ion(ctypes.byref(p), float(E_eV))
+
+
+def xs_lookup(cfg: dict, E_eV: float):
+    """(sigma_el, sigma_io, xi) of cfg["xs"] at energy E_eV (see
+    or_xs_lookup)."""
+    p = params(dict(cfg, nu_max=1.0))   # (the majorant is not needed here)
+    out = [ctypes.c_double() for _ in range(3)]
+    lib().or_xs_lookup(ctypes.byref(p), float(E_eV), *[ctypes.byref(o) for o in out])
+    return tuple(o.value for o in out)
+
+
+def nu_max(cfg: dict) -> float:
+    """The collision majorant the oracle derives for cfg (or cfg's own)."""
+    return params(cfg).nu_max
 
 
 # ------------------------------------------------------------------ grid

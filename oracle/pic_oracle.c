@@ -63,6 +63,14 @@ typedef struct {
   double nu_max;                    /* null-collision majorant, s^-1 */
   uint64_t seed;
   double T0_eV;                     /* temperature of the seed source, eV */
+  /* tabulated cross sections (Sec. II.A: momentum-transfer elastic and
+   * total ionisation cross sections from tabulated data, and the angle
+   * law's anisotropy): xs_n points (0: the analytic ones above) */
+  int32_t xs_n;
+  const double* xs_E_eV;            /* strictly increasing */
+  const double* xs_sigma_el;        /* m^2 */
+  const double* xs_sigma_io;        /* m^2 */
+  const double* xs_xi;              /* NULL: the constant xi */
 } or_params;
 
 /* tally slots (accumulated, doubles) */
@@ -131,11 +139,56 @@ double or_sigma_ion(const or_params* P, double E_eV) {
   return P->ion_sigma_pk * 2.0 * s / (1.0 + s * s);
 }
 
-/* collision frequencies at speed v */
-static void or_nu(const or_params* P, double v, double* nu_el, double* nu_io) {
+/* Tabulated values at energy E (eV): the table point k with E_k <= E <
+ * E_{k+1} found by bisection and f = f_k + w (f_{k+1} - f_k), w = (E -
+ * E_k) / (E_{k+1} - E_k); at or below E_0 the first value (w = 0 on the
+ * first segment), at or above E_{n-1} the last (w = 1 on the last). */
+void or_xs_lookup(const or_params* P, double E_eV, double* sig_el, double* sig_io,
+                  double* xi) {
+  const int n = P->xs_n;
+  const double* E = P->xs_E_eV;
+  int k;
+  double w;
+  if (!(E_eV > E[0])) {
+    k = 0;
+    w = 0.0;
+  } else if (!(E_eV < E[n - 1])) {
+    k = n - 2;
+    w = 1.0;
+  } else {
+    int lo = 0, hi = n - 1;   /* E[lo] <= E_eV < E[hi] */
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) / 2;
+      if (E[mid] <= E_eV) lo = mid;
+      else hi = mid;
+    }
+    k = lo;
+    w = (E_eV - E[k]) / (E[k + 1] - E[k]);
+  }
+  *sig_el = P->xs_sigma_el[k] + w * (P->xs_sigma_el[k + 1] - P->xs_sigma_el[k]);
+  *sig_io = P->xs_sigma_io[k] + w * (P->xs_sigma_io[k + 1] - P->xs_sigma_io[k]);
+  *xi = P->xs_xi ? P->xs_xi[k] + w * (P->xs_xi[k + 1] - P->xs_xi[k]) : P->xi;
+}
+
+/* collision frequencies at speed v, and the angle law's anisotropy there;
+ * ionisation needs more energy than the binding energy whatever a table
+ * says */
+static void or_nu_xi(const or_params* P, double v, double* nu_el, double* nu_io, double* xi) {
   double E_eV = 0.5 * OR_ME * v * v / OR_E;
-  *nu_el = P->n_gas * P->sigma_el * v;
-  *nu_io = P->n_gas * or_sigma_ion(P, E_eV) * v;
+  if (P->xs_n > 0) {
+    double se, si;
+    or_xs_lookup(P, E_eV, &se, &si, xi);
+    *nu_el = P->n_gas * se * v;
+    *nu_io = E_eV > P->ion_E_th_eV ? P->n_gas * si * v : 0.0;
+  } else {
+    *nu_el = P->n_gas * P->sigma_el * v;
+    *nu_io = P->n_gas * or_sigma_ion(P, E_eV) * v;
+    *xi = P->xi;
+  }
+}
+static void or_nu(const or_params* P, double v, double* nu_el, double* nu_io) {
+  double xi;
+  or_nu_xi(P, v, nu_el, nu_io, &xi);
 }
 
 /* Majorant: (1 + 1e-6) * max of nu_el + nu_io over E_k = E_cap k / 1e5,
@@ -342,15 +395,15 @@ int64_t or_step(const or_params* P, int64_t n, double* r, double* z,
       double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
       double speed = sqrt(v2);
       double E = 0.5 * m * v2;
-      double nu_el, nu_io;
-      or_nu(P, speed, &nu_el, &nu_io);
+      double nu_el, nu_io, xi;
+      or_nu_xi(P, speed, &nu_el, &nu_io, &xi);
       if (nu_el + nu_io > P->nu_max) tally[T_N_OVER] += 1.0;
       double x1 = u[1] * P->nu_max;
       mg = fmin(mg, fmin(fabs(x1 - nu_el), fabs(x1 - nu_el - nu_io)) / P->nu_max);
       double vhat[3] = {v[0] / speed, v[1] / speed, v[2] / speed};
       if (x1 < nu_el) {
         double d[3];
-        or_scatter_dir(vhat, u[2], u[3], P->xi, d);
+        or_scatter_dir(vhat, u[2], u[3], xi, d);
         double E1 = E;
         if (P->elastic_recoil) {
           double mu = d[0] * vhat[0] + d[1] * vhat[1] + d[2] * vhat[2];
@@ -368,8 +421,8 @@ int64_t or_step(const or_params* P, int64_t n, double* r, double* z,
         double E2 = or_opal_secondary(E_rem, B_share, u2[0]);
         double E1 = E_rem - E2;
         double d1[3], d2[3];
-        or_scatter_dir(vhat, u[2], u[3], P->xi, d1);
-        or_scatter_dir(vhat, u2[1], u2[2], P->xi, d2);
+        or_scatter_dir(vhat, u[2], u[3], xi, d1);
+        or_scatter_dir(vhat, u2[1], u2[2], xi, d2);
         double s1 = sqrt(2.0 * E1 / m), s2 = sqrt(2.0 * E2 / m);
         for (int k = 0; k < 3; ++k) v[k] = s1 * d1[k];
         if (nchild >= child_cap) return -1;

@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
         L.pic_diagnostics.argtypes = [vp, ctypes.c_int, P(PicDiag), vp]
         L.pic_export_particles.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, c_i64, P(c_i64)]
         L.pic_set_efield.argtypes = [vp, ctypes.c_int, vp, vp]
+        L.pic_set_cross_sections.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.pic_get_grid.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
         L.pic_solve_field.argtypes = [vp, vp, vp, P(c_d)]
         L.pic_checkpoint.argtypes = [vp, ctypes.c_char_p]
@@ -103,7 +104,8 @@ def lib() -> ctypes.CDLL:
         L.pic_free.argtypes = [vp]
         L.pic_free.restype = None
         for name in ("pic_init", "pic_load_particles", "pic_step", "pic_diagnostics",
-                     "pic_export_particles", "pic_set_efield", "pic_get_grid", "pic_solve_field",
+                     "pic_export_particles", "pic_set_efield", "pic_set_cross_sections",
+                     "pic_get_grid", "pic_solve_field",
                      "pic_checkpoint", "pic_restore", "pic_profile"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -243,6 +245,20 @@ class Simulation:
     def set_efield(self, er, ez, sim: int = 0):
         pe, pz = _f64(er), _f64(ez)
         _check(lib().pic_set_efield(self.h, sim, pe[0], pz[0]), "pic_set_efield")
+
+    def set_cross_sections(self, E_eV=None, sigma_el=None, sigma_io=None, xi=None, sim: int = 0):
+        """Tabulated cross sections of simulation `sim` (pic_set_cross_sections);
+        no arguments return to the config's analytic ones."""
+        if E_eV is None:
+            _check(lib().pic_set_cross_sections(self.h, sim, 0, None, None, None, None),
+                   "pic_set_cross_sections")
+            return
+        pe, ps, pi = _f64(E_eV), _f64(sigma_el), _f64(sigma_io)
+        px = _f64(xi) if xi is not None else (None, None)
+        n = len(pe[1])
+        assert len(ps[1]) == n and len(pi[1]) == n and (xi is None or len(px[1]) == n)
+        _check(lib().pic_set_cross_sections(self.h, sim, n, pe[0], ps[0], pi[0], px[0]),
+               "pic_set_cross_sections")
 
     def get_grid(self, which: int, sim: int = 0) -> np.ndarray:
         out = np.zeros(self.nnodes)

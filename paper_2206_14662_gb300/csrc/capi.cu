@@ -44,6 +44,15 @@ struct SimHost {
   long long last_diag_step;
 };
 
+// tabulated cross sections of one simulation (pic_set_cross_sections):
+// the caller's tables and their device copy in the particle precision
+// (energies in J, n_gas sigma in 1/m, xi), 4 x PIC_XS_MAX_POINTS values
+struct XsHost {
+  int n = 0;
+  std::vector<double> E_eV, sigma_el, sigma_io, xi;
+  void* dev = nullptr;
+};
+
 struct pic_handle {
   pic_config cfg;                 // simulation 0 (the shared geometry)
   std::vector<pic_config> cfgs;   // every simulation
@@ -55,6 +64,8 @@ struct pic_handle {
   std::vector<void*> owned;
 
   std::vector<SimHost> sims;
+  std::vector<XsHost> xs;         // per simulation
+  bool any_xs;                    // some simulation has tables
   double hr, hz;
   long long capacity;             // slots of all segments
   long long spawn_stride;         // spawn records per simulation
@@ -156,6 +167,54 @@ double sigma_ion_host(const pic_config& c, double E_eV) {
   return c.ion_sigma_pk * 2.0 * s / (1.0 + s * s);
 }
 
+// sigma_el, sigma_io at E (eV): the config's analytic cross sections, or
+// the tables by the rule of pic_set_cross_sections
+void sigmas_host(const pic_config& c, const XsHost& X, double E_eV, double& sel, double& sio) {
+  if (X.n == 0) {
+    sel = c.sigma_el;
+    sio = sigma_ion_host(c, E_eV);
+    return;
+  }
+  const int n = X.n;
+  const double* E = X.E_eV.data();
+  int k = 0;
+  double w = 0.0;
+  if (!(E_eV > E[0])) {
+    k = 0;
+    w = 0.0;
+  } else if (!(E_eV < E[n - 1])) {
+    k = n - 2;
+    w = 1.0;
+  } else {
+    k = (int)(std::upper_bound(E, E + n, E_eV) - E) - 1;
+    w = (E_eV - E[k]) / (E[k + 1] - E[k]);
+  }
+  sel = X.sigma_el[k] + w * (X.sigma_el[k + 1] - X.sigma_el[k]);
+  sio = E_eV > c.ion_E_th_eV ? X.sigma_io[k] + w * (X.sigma_io[k + 1] - X.sigma_io[k]) : 0.0;
+}
+
+// the collision majorant of simulation k and its null-collision threshold
+void derive_nu_max(const pic_config& ck, const XsHost& X, SimHost& m) {
+  if (ck.nu_max > 0) {
+    m.nu_max = ck.nu_max;
+  } else {
+    const double E_cap = 2.0 * std::fabs(ck.v_inner - ck.v_outer);
+    double best = 0.0;
+    for (int q = 0; q <= 100000; ++q) {
+      const double E_eV = E_cap * (double)q / 100000.0;
+      const double v = std::sqrt(2.0 * E_eV * kQe / kMe);
+      double sel, sio;
+      sigmas_host(ck, X, E_eV, sel, sio);
+      const double nu = m.n_gas * sel * v + m.n_gas * sio * v;
+      if (nu > best) best = nu;
+    }
+    m.nu_max = best * (1.0 + 1e-6);
+  }
+  m.p_null = 1.0 - std::exp(-m.nu_max * ck.dt);
+  const double cthr = m.p_null * 16777216.0 - 0.5;
+  m.thr_null = cthr <= 0 ? 0u : (unsigned)std::min(16777216.0, std::ceil(cthr));
+}
+
 int validate(const pic_config& c) {
   if (!(c.r_in > 0 && c.r_out > c.r_in && c.z_max > c.z_min)) return PIC_EINVAL;
   // nz + 1 doubles of one z-line must fit the direct transform's 48 KB of
@@ -227,6 +286,14 @@ void fill_params(pic_handle* h, int k, PushParams<Real>& P) {
   P.recoil = c.elastic_recoil ? (Real)(2.0 * kMe / m.gas_mass) : (Real)0;
   P.nu_max = (Real)m.nu_max;
   P.half_m = (Real)(0.5 * kMe);
+  const XsHost& X = h->xs[k];
+  const bool tab = X.n > 0 && X.dev && h->prec == (int)(8 * sizeof(Real));
+  const Real* xd = (const Real*)X.dev;
+  P.xs_n = tab ? X.n : 0;
+  P.xs_E = tab ? xd : nullptr;
+  P.xs_nel = tab ? xd + PIC_XS_MAX_POINTS : nullptr;
+  P.xs_nio = tab ? xd + 2 * PIC_XS_MAX_POINTS : nullptr;
+  P.xs_xi = tab && !X.xi.empty() ? xd + 3 * PIC_XS_MAX_POINTS : nullptr;
   P.two_over_m = (Real)(2.0 / kMe);
   P.work_scale = (Real)(-kQe * c.dt / 4.0);
   P.weight = m.weight;
@@ -342,7 +409,8 @@ int step_impl(pic_handle* h, long long nsteps) {
       launch_particle_step_batch<Real>(soa<Real>(h, h->cur), h->efield, fp32 ? nullptr : h->rhs,
                                        fp32 ? h->cnt[h->dep_buf] : nullptr, h->st,
                                        h->spawn_parent, h->spawn_stride, params_dev<Real>(h),
-                                       h->nsim, h->nnodes, h->grid_particle, h->stream);
+                                       h->nsim, h->nnodes, h->any_xs, h->grid_particle,
+                                       h->stream);
     else
       launch_particle_step<Real>(soa<Real>(h, h->cur), h->efield, h->rhs,
                                  fp32 ? h->cnt[h->dep_buf] : nullptr, h->st, h->spawn_parent, P,
@@ -498,6 +566,7 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   h->hz = L / c.nz;
   const long long ch = particle_chunk();
   h->sims.resize(n_sims);
+  h->xs.resize(n_sims);
   long long base = 0, spawn_stride = 0;
   for (int k = 0; k < n_sims; ++k) {
     const pic_config& ck = h->cfgs[k];
@@ -508,22 +577,7 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
                              : ck.n0 * kPi * (ck.r_out * ck.r_out - ck.r_in * ck.r_in) * L /
                                    (double)ck.n_init;
     m.gas_mass = ck.gas_mass_amu * kAmu;
-    if (ck.nu_max > 0) {
-      m.nu_max = ck.nu_max;
-    } else {
-      const double E_cap = 2.0 * std::fabs(ck.v_inner - ck.v_outer);
-      double best = 0.0;
-      for (int q = 0; q <= 100000; ++q) {
-        const double E_eV = E_cap * (double)q / 100000.0;
-        const double v = std::sqrt(2.0 * E_eV * kQe / kMe);
-        const double nu = m.n_gas * ck.sigma_el * v + m.n_gas * sigma_ion_host(ck, E_eV) * v;
-        if (nu > best) best = nu;
-      }
-      m.nu_max = best * (1.0 + 1e-6);
-    }
-    m.p_null = 1.0 - std::exp(-m.nu_max * ck.dt);
-    const double cthr = m.p_null * 16777216.0 - 0.5;
-    m.thr_null = cthr <= 0 ? 0u : (unsigned)std::min(16777216.0, std::ceil(cthr));
+    derive_nu_max(ck, h->xs[k], m);
     m.capacity = ck.capacity > 0 ? ck.capacity
                                  : (long long)(1.25 * (double)std::max<int64_t>(ck.n_init, 0)) + 4096;
     m.spawn_cap = std::min<long long>(m.capacity, 1 << 20);
@@ -1028,6 +1082,79 @@ int pic_set_efield(pic_handle* h, int sim, const double* er, const double* ez) {
     h_free_one(p, h);
   }
   return rc;
+}
+
+int pic_set_cross_sections(pic_handle* h, int sim, int n, const double* E_eV,
+                           const double* sigma_el_m2, const double* sigma_io_m2,
+                           const double* xi) {
+  if (!h || sim < 0 || sim >= h->nsim || n < 0 || n == 1 || n > PIC_XS_MAX_POINTS)
+    return PIC_EINVAL;
+  if (n > 0) {
+    if (!E_eV || !sigma_el_m2 || !sigma_io_m2) return PIC_EINVAL;
+    for (int k = 0; k < n; ++k) {
+      if (!std::isfinite(E_eV[k]) || !(E_eV[k] >= 0) || (k > 0 && !(E_eV[k] > E_eV[k - 1])))
+        return PIC_EINVAL;
+      if (!std::isfinite(sigma_el_m2[k]) || !(sigma_el_m2[k] >= 0) ||
+          !std::isfinite(sigma_io_m2[k]) || !(sigma_io_m2[k] >= 0))
+        return PIC_EINVAL;
+      if (xi && !(xi[k] >= 0 && xi[k] < 1)) return PIC_EINVAL;
+    }
+  }
+  if (h->sticky) return h->sticky;
+  // kernels in flight may read the current tables
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PIC_ECUDA;
+  XsHost& X = h->xs[sim];
+  SimHost& m = h->sims[sim];
+  X.n = n;
+  X.E_eV.clear();
+  X.sigma_el.clear();
+  X.sigma_io.clear();
+  X.xi.clear();
+  if (n > 0) {
+    X.E_eV.assign(E_eV, E_eV + n);
+    X.sigma_el.assign(sigma_el_m2, sigma_el_m2 + n);
+    X.sigma_io.assign(sigma_io_m2, sigma_io_m2 + n);
+    if (xi) X.xi.assign(xi, xi + n);
+  }
+  if (n > 0) {
+    const size_t rs = h->prec == 32 ? sizeof(float) : sizeof(double);
+    if (!X.dev) {
+      X.dev = h_alloc(4 * (size_t)PIC_XS_MAX_POINTS * rs, h);
+      if (!X.dev) {
+        X.n = 0;
+        return PIC_ENOMEM;
+      }
+    }
+    // device copy in the particle precision: E in J, n_gas sigma in 1/m
+    std::vector<double> v(4 * (size_t)PIC_XS_MAX_POINTS, 0.0);
+    for (int k = 0; k < n; ++k) {
+      v[k] = E_eV[k] * kQe;
+      v[PIC_XS_MAX_POINTS + k] = m.n_gas * sigma_el_m2[k];
+      v[2 * PIC_XS_MAX_POINTS + k] = m.n_gas * sigma_io_m2[k];
+      v[3 * PIC_XS_MAX_POINTS + k] = xi ? xi[k] : 0.0;
+    }
+    cudaError_t e;
+    if (h->prec == 32) {
+      std::vector<float> f(v.begin(), v.end());
+      e = cudaMemcpy(X.dev, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+    } else {
+      e = cudaMemcpy(X.dev, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return PIC_ECUDA;
+  }
+  derive_nu_max(h->cfgs[sim], X, m);
+  fill_params<float>(h, sim, h->Pf[sim]);
+  fill_params<double>(h, sim, h->Pd[sim]);
+  if (cudaMemcpy(h->Pf_dev + sim, &h->Pf[sim], sizeof(PushParams<float>), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(h->Pd_dev + sim, &h->Pd[sim], sizeof(PushParams<double>), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return PIC_ECUDA;
+  h->any_xs = false;
+  for (const XsHost& x : h->xs) h->any_xs = h->any_xs || x.n > 0;
+  // the captured steps hold the old parameters (and kernel variant)
+  drop_graphs(h);
+  return PIC_OK;
 }
 
 int pic_get_grid(pic_handle* h, int sim, int which, double* out) {

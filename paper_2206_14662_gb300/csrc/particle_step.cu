@@ -20,6 +20,7 @@
 //
 // Memory traffic per particle-step: 28 B read (cell, two offsets, three
 // velocity components, uid) and 24 B written (all but the uid) in FP32.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <type_traits>
@@ -150,12 +151,52 @@ struct Part {
   Real fr, fz, vr, vt, vz;
 };
 
+// Tabulated n_gas sigma_el, n_gas sigma_io and xi at energy E (J): the
+// point k with E_k <= E < E_{k+1} by bisection, f = f_k + w (f_{k+1} -
+// f_k); the first (last) value at or below E_0 (at or above E_{n-1}); xi0
+// when there is no xi table.  Compiled only into the kernels launched
+// while some simulation has tables (TAB), so the analytic kernels keep
+// their registers.
+template <typename Real>
+struct Xs3 {
+  Real nel, nio, xi;
+};
+template <typename Real>
+__device__ __forceinline__ Xs3<Real> xs_eval(int n, const Real* __restrict__ Et,
+                                          const Real* __restrict__ el,
+                                          const Real* __restrict__ io,
+                                          const Real* __restrict__ xt, Real xi0, Real E) {
+  int k;
+  Real w;
+  if (!(E > Et[0])) {
+    k = 0;
+    w = 0;
+  } else if (!(E < Et[n - 1])) {
+    k = n - 2;
+    w = 1;
+  } else {
+    int lo = 0, hi = n - 1;   // Et[lo] <= E < Et[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (Et[mid] <= E) lo = mid;
+      else hi = mid;
+    }
+    k = lo;
+    w = (E - Et[k]) / (Et[k + 1] - Et[k]);
+  }
+  Xs3<Real> r;
+  r.nel = mad(w, el[k + 1] - el[k], el[k]);
+  r.nio = mad(w, io[k + 1] - io[k], io[k]);
+  r.xi = xt ? mad(w, xt[k + 1] - xt[k], xt[k]) : xi0;
+  return r;
+}
+
 // Collision of a particle that passed the null-collision candidate test
 // (rare): type from u1 against the cumulative frequencies, then elastic
 // scattering or ionisation with a child appended.  q holds the state after
 // the move.  The draw-0 Philox block is recomputed here, so the common path
 // carries only the candidate flag.
-template <typename Real>
+template <typename Real, bool TAB>
 __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, unsigned uid_hi,
                                         const Soa<Real>& s,
                                      const DepGrid& g, DevState* st, unsigned* spawn_parent,
@@ -167,13 +208,22 @@ __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, unsigned ui
   const Real v2 = ur * ur + ut * ut + uz * uz;
   const Real speed = d_sqrt(v2);
   const Real Ek = P.half_m * v2;
-  const Real nu_el = P.nsig_el * speed;
+  const Real nu_el0 = P.nsig_el * speed;
   Real sig_io = 0;
   if (Ek > P.e_th) {
     const Real qq = (Ek - P.e_th) * P.e_span_inv;
     sig_io = P.sig_pk * 2 * qq / (1 + qq * qq);
   }
-  const Real nu_io = P.n_gas * sig_io * speed;
+  const Real nu_io0 = P.n_gas * sig_io * speed;
+  // tabulated (TAB kernels with tables); ionisation needs more than the
+  // binding energy.  The analytic kernels keep the expressions above.
+  const bool tab = TAB && P.xs_n > 0;
+  Xs3<Real> xt = {};
+  if constexpr (TAB) {
+    if (tab) xt = xs_eval<Real>(P.xs_n, P.xs_E, P.xs_nel, P.xs_nio, P.xs_xi, P.xi, Ek);
+  }
+  const Real nu_el = tab ? xt.nel * speed : nu_el0;
+  const Real nu_io = tab ? (Ek > P.e_th ? xt.nio * speed : Real(0)) : nu_io0;
   if (nu_el + nu_io > P.nu_max) atomicAdd(&bt.v[kNOver], 1.0);
   const Real x1 = u01<Real>(xr.y) * P.nu_max;
   if (!(x1 < nu_el + nu_io)) return;   // null collision
@@ -181,7 +231,7 @@ __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, unsigned ui
   const Real hr_ = ur * inv_s, ht_ = ut * inv_s, hz_ = uz * inv_s;
   if (x1 < nu_el) {
     Real dr, dt, dz;
-    scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), P.xi, dr, dt, dz);
+    scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), tab ? xt.xi : P.xi, dr, dt, dz);
     Real E1 = Ek;
     if (P.recoil != 0) {
       const Real mu = dr * hr_ + dt * ht_ + dz * hz_;
@@ -198,8 +248,8 @@ __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, unsigned ui
   const Real E2 = P.opal_b * d_tan(u01<Real>(x2.x) * d_atan(E_rem / (2 * P.opal_b)));
   const Real E1 = E_rem - E2;
   Real d1r, d1t, d1z, d2r, d2t, d2z;
-  scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), P.xi, d1r, d1t, d1z);
-  scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(x2.y), u01<Real>(x2.z), P.xi, d2r, d2t, d2z);
+  scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(xr.z), u01<Real>(xr.w), tab ? xt.xi : P.xi, d1r, d1t, d1z);
+  scatter_dir<Real>(hr_, ht_, hz_, u01<Real>(x2.y), u01<Real>(x2.z), tab ? xt.xi : P.xi, d2r, d2t, d2z);
   const Real s1 = d_sqrt(P.two_over_m * E1), s2 = d_sqrt(P.two_over_m * E2);
   q.vr = s1 * d1r; q.vt = s1 * d1t; q.vz = s1 * d1z;
   atomicAdd(&bt.v[kIonLoss], (double)P.e_th);
@@ -228,7 +278,7 @@ __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, unsigned ui
 // automatic contraction, so each particle is computed by the same sequence
 // of roundings whichever slot of its thread it occupies (results do not
 // depend on the particle order the sort leaves).
-template <typename Real>
+template <typename Real, bool TAB>
 __device__ __forceinline__ Dep<Real> advance(
     Part<Real>& q, unsigned uid, unsigned uid_hi, const typename Vec2<Real>::type* __restrict__ E,
     const Soa<Real>& s, const DepGrid& g, DevState* st, unsigned* spawn_parent, int n_slots,
@@ -329,7 +379,7 @@ __device__ __forceinline__ Dep<Real> advance(
   // null-collision candidate test: the integer form of u0 < P_null
   const uint4 xr = philox4x32_10_rk(make_uint4(uid, uid_hi, step, 0u), P.rk0, P.rk1);
   if ((xr.x >> 8) < P.thr_null)
-    collide<Real>(q, uid, uid_hi, s, g, st, spawn_parent, n_slots, step, P, bt);
+    collide<Real, TAB>(q, uid, uid_hi, s, g, st, spawn_parent, n_slots, step, P, bt);
   dep.ir = ir1; dep.iz = iz1; dep.fr = fr1; dep.fz = fz1;
   return dep;
 }
@@ -544,8 +594,9 @@ __device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pus
 
 // Each thread loads its kPPT consecutive particles directly (16-byte vector
 // loads with streaming hints in the FP32 path), advances them, stores them
-// back and joins the block's tile deposit.
-template <typename Real>
+// back and joins the block's tile deposit.  TAB: some simulation has
+// tabulated cross sections.
+template <typename Real, bool TAB>
 __global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 4)
 k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, DepGrid g,
                 DevState* st, unsigned* __restrict__ spawn_parent, PushParams<Real> P) {
@@ -580,7 +631,7 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, De
       live[k] = q[k].cell >= 0;
       if (live[k]) {
         ++pushed;
-        dep[k] = advance<Real>(q[k], uid[k], 0u, E, s, g, st, spawn_parent, n_slots, step, P, bt,
+        dep[k] = advance<Real, TAB>(q[k], uid[k], 0u, E, s, g, st, spawn_parent, n_slots, step, P, bt,
                                work);
       }
     }
@@ -596,8 +647,12 @@ void launch_particle_step(const Soa<Real>& s, const void* efield, double* rhs,
                           unsigned long long* cnt, DevState* st, unsigned* spawn_parent,
                           const PushParams<Real>& P, int grid, cudaStream_t stream) {
   DepGrid g{rhs, cnt, P.nz + 1, P.qw};
-  k_particle_step<Real><<<grid, kThreads, 0, stream>>>(
-      s, (const typename Vec2<Real>::type*)efield, g, st, spawn_parent, P);
+  if (P.xs_n > 0)
+    k_particle_step<Real, true><<<grid, kThreads, 0, stream>>>(
+        s, (const typename Vec2<Real>::type*)efield, g, st, spawn_parent, P);
+  else
+    k_particle_step<Real, false><<<grid, kThreads, 0, stream>>>(
+        s, (const typename Vec2<Real>::type*)efield, g, st, spawn_parent, P);
 }
 
 // ----------------------------------------------------------------- batch
@@ -624,7 +679,7 @@ struct SimView {
 // consecutive, so a block changes simulation rarely; when it does, it
 // flushes the tallies of the previous one and loads the new view.  The
 // per-particle work is that of k_particle_step.
-template <typename Real>
+template <typename Real, bool TAB>
 __global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS_BATCH : 4)
 k_particle_step_batch(Soa<Real> s_all, const typename Vec2<Real>::type* __restrict__ E_all,
                       double* rhs_all, unsigned long long* cnt_all, DevState* st_all,
@@ -692,7 +747,7 @@ k_particle_step_batch(Soa<Real> s_all, const typename Vec2<Real>::type* __restri
       live[k] = q[k].cell >= 0;
       if (live[k]) {
         ++pushed;
-        dep[k] = advance<Real>(q[k], uid[k], V.P.uid_hi, V.E, V.s, V.g, V.st, V.spawn, n_slots,
+        dep[k] = advance<Real, TAB>(q[k], uid[k], V.P.uid_hi, V.E, V.s, V.g, V.st, V.spawn, n_slots,
                                V.step, V.P, bt, work);
       }
     }
@@ -707,10 +762,15 @@ template <typename Real>
 void launch_particle_step_batch(const Soa<Real>& s, const void* efield, double* rhs,
                                 unsigned long long* cnt, DevState* st, unsigned* spawn_parent,
                                 long long spawn_stride, const PushParams<Real>* params, int nsim,
-                                int nnodes, int grid, cudaStream_t stream) {
-  k_particle_step_batch<Real><<<grid, kThreads, 0, stream>>>(
-      s, (const typename Vec2<Real>::type*)efield, rhs, cnt, st, spawn_parent, spawn_stride,
-      params, nsim, nnodes);
+                                int nnodes, bool tables, int grid, cudaStream_t stream) {
+  if (tables)
+    k_particle_step_batch<Real, true><<<grid, kThreads, 0, stream>>>(
+        s, (const typename Vec2<Real>::type*)efield, rhs, cnt, st, spawn_parent, spawn_stride,
+        params, nsim, nnodes);
+  else
+    k_particle_step_batch<Real, false><<<grid, kThreads, 0, stream>>>(
+        s, (const typename Vec2<Real>::type*)efield, rhs, cnt, st, spawn_parent, spawn_stride,
+        params, nsim, nnodes);
 }
 
 // ------------------------------------------------------------ child uids
@@ -1026,7 +1086,7 @@ void launch_efield_get(const void* efield, double* out, int component,
   template void launch_particle_step_batch<R>(const Soa<R>&, const void*, double*,       \
                                               unsigned long long*, DevState*, unsigned*, \
                                               long long, const PushParams<R>*, int, int, \
-                                              int, cudaStream_t);                       \
+                                              bool, int, cudaStream_t);                 \
   template void launch_load<R>(const double*, const double*, const double*,             \
                                const double*, const double*, const uint64_t*,           \
                                long long, Soa<R>, const PushParams<R>&, DevState*,      \
@@ -1050,21 +1110,25 @@ PIC_INSTANTIATE(double)
 }  // namespace pic
 
 namespace pic {
-// resident blocks of the fused kernel per SM (sizes its persistent grid)
-int particle_step_blocks_per_sm(int precision, bool batch) {
+// resident blocks of the fused kernel per SM (sizes its persistent grid;
+// the lesser of the analytic and the tabulated variant)
+template <typename K>
+static int blocks_of(K kernel) {
   int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, 0);
+  return b;
+}
+int particle_step_blocks_per_sm(int precision, bool batch) {
   if (batch) {
     if (precision == 32)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step_batch<float>, kThreads, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step_batch<double>, kThreads, 0);
-    return b;
+      return std::min(blocks_of(k_particle_step_batch<float, false>),
+                      blocks_of(k_particle_step_batch<float, true>));
+    return std::min(blocks_of(k_particle_step_batch<double, false>),
+                    blocks_of(k_particle_step_batch<double, true>));
   }
   if (precision == 32)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step<float>, kThreads, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particle_step<double>, kThreads, 0);
-  return b;
+    return std::min(blocks_of(k_particle_step<float, false>), blocks_of(k_particle_step<float, true>));
+  return std::min(blocks_of(k_particle_step<double, false>), blocks_of(k_particle_step<double, true>));
 }
 // slots of the store are allocated in whole multiples of this (the sort
 // kernels read 1024-slot chunks)

@@ -123,6 +123,14 @@ struct PushParams {
   // grid geometry in FP64 for converting absolute positions to and from
   // (cell, offset) at load and export
   double r_in_d, hr_d, z_min_d, hz_d;
+  // tabulated cross sections (pic_set_cross_sections): xs_n points, 0 for
+  // the analytic ones; energies in J, n_gas sigma in 1/m, anisotropy xi
+  // (xs_xi null: the constant xi)
+  int xs_n;
+  const Real* xs_E;
+  const Real* xs_nel;
+  const Real* xs_nio;
+  const Real* xs_xi;
 };
 
 // ------------------------------------------------------------- batches
@@ -330,14 +338,15 @@ void launch_spawn_finalize(DevState* st, unsigned* uid, const unsigned* parent,
                            long long spawn_cap, long long capacity,
                            cudaStream_t stream);
 // a batch: the fused kernel over all simulations' chunks (params: device
-// array of nsim PushParams, each with its segment base), child uids per
+// array of nsim PushParams, each with its segment base; tables: some
+// simulation has tabulated cross sections), child uids per
 // simulation, and the counting sort of every segment
 template <typename Real>
 void launch_particle_step_batch(const Soa<Real>& s, const void* efield, double* rhs,
                                 unsigned long long* cnt, DevState* st,
                                 unsigned* spawn_parent, long long spawn_stride,
                                 const PushParams<Real>* params, int nsim, int nnodes,
-                                int grid, cudaStream_t stream);
+                                bool tables, int grid, cudaStream_t stream);
 // seed source of every simulation with src_per_step > 0 (after the child
 // uids, before the sort and the field solve)
 template <typename Real>

@@ -157,6 +157,28 @@ def random_field_node_arrays(cfg: dict, scale: float, seed: int = 7):
 # width c, see the library's pic_unet_* entry points for the layer order).
 # Each layer's weights are drawn N(0, 2 / fan_in) (fan_in = kernel taps x
 # input channels), biases are zero; the head starts at N(0, head_std^2).
+def cross_section_tables(E_th_eV: float = 21.56, n: int = 64, E_max_eV: float = 3.0e4,
+                         sigma_el_scale: float = 1.0e-19, sigma_io_scale: float = 2.0e-20,
+                         with_xi: bool = True):
+    """Synthetic tables for pic_set_cross_sections (the LXCat data the paper
+    uses are not available): n energies, 0 then log-spaced from 0.1 eV to
+    E_max_eV, with the ionisation threshold among them; an elastic
+    momentum-transfer cross-section falling as (1 + E / 10 eV)^-1/2, an
+    ionisation cross-section zero up to the threshold, rising to its peak
+    at e E_th and falling as log(E) / E; an angle-law anisotropy rising
+    from 0 to 0.6 with energy (None when with_xi is false).  Returns
+    (E_eV, sigma_el, sigma_io, xi)."""
+    E = np.concatenate([[0.0], np.geomspace(0.1, E_max_eV, n - 2)])
+    E = np.unique(np.concatenate([E, [E_th_eV]]))
+    while len(E) < n:   # keep n points when the threshold was already there
+        E = np.unique(np.concatenate([E, [0.5 * (E[-1] + E[-2])]]))
+    sigma_el = sigma_el_scale / np.sqrt(1.0 + E / 10.0)
+    x = np.maximum(E / E_th_eV, 1.0)
+    sigma_io = np.where(E > E_th_eV, sigma_io_scale * 5.0 * np.log(x) / x, 0.0)
+    xi = 0.6 * E / (E + 100.0) if with_xi else None
+    return E, sigma_el, sigma_io, xi
+
+
 def unet_layer_shapes(c: int, cin: int = 2) -> list[tuple[str, tuple]]:
     """(name, weight shape) in the flat parameter order: conv layers
     (3, 3, in, out), transposed convolutions (2, 2, in, out), head (c,)."""

@@ -507,3 +507,68 @@ def test_seed_source_streams_and_counts(oracle_mod):
     assert np.array_equal(np.sort(o.uid)[-o.n_source:] if o.n_source else [],
                           np.arange(50, 50 + o.n_source, dtype=np.uint64))
     assert abs(o.ledger_residual()) <= 1e-12 * max(o.kinetic_energy(), 1e-30) + 1e-25
+
+
+def test_cross_section_table_rule(oracle_mod):
+    """Tabulated cross sections: the table's own values at its energies,
+    the mean of two neighbours half-way between them, the end values held
+    outside the table, and the constant xi when the table has none."""
+    oracle = oracle_mod
+    cfg = workload("coax_32x64_1e4")
+    E = np.array([0.0, 10.0, 30.0, 100.0])
+    sel = np.array([4e-20, 2e-20, 1e-20, 5e-21])
+    sio = np.array([0.0, 0.0, 3e-21, 1e-21])
+    xi = np.array([0.0, 0.2, 0.4, 0.5])
+    cfg["xs"] = dict(E_eV=E, sigma_el=sel, sigma_io=sio, xi=xi)
+    for k in range(4):
+        assert oracle.xs_lookup(cfg, E[k]) == pytest.approx((sel[k], sio[k], xi[k]), rel=1e-15)
+    for k in range(3):
+        mid = 0.5 * (E[k] + E[k + 1])
+        want = (0.5 * (sel[k] + sel[k + 1]), 0.5 * (sio[k] + sio[k + 1]), 0.5 * (xi[k] + xi[k + 1]))
+        assert oracle.xs_lookup(cfg, mid) == pytest.approx(want, rel=1e-14)
+    assert oracle.xs_lookup(cfg, -5.0) == pytest.approx((sel[0], sio[0], xi[0]))
+    assert oracle.xs_lookup(cfg, 1e6) == pytest.approx((sel[-1], sio[-1], xi[-1]))
+    cfg["xs"] = dict(E_eV=E, sigma_el=sel, sigma_io=sio, xi=None)
+    assert oracle.xs_lookup(cfg, 20.0)[2] == cfg["xi_param"]
+
+
+def test_dense_table_of_the_analytic_fit_gives_its_majorant(oracle_mod):
+    """A table sampled finely from the config's analytic cross sections
+    (constant elastic, the ionisation fit) interpolates them to within the
+    linear-interpolation error h^2 max|f''| / 8 and gives the same
+    collision majorant to 1e-5."""
+    oracle = oracle_mod
+    cfg = workload("coax_32x64_1e4", p_mbar=1.0)
+    # up to the majorant's energy cap 2 |V_in - V_out|, beyond which the
+    # table's last value would hold
+    E_cap = 2.0 * abs(cfg["v_inner"] - cfg["v_outer"])
+    E = np.unique(np.concatenate([np.linspace(0.0, E_cap, 40001), [cfg["ion_E_th_eV"]]]))
+    sio = np.array([oracle.sigma_ion(cfg, e) for e in E])
+    tab = dict(cfg, xs=dict(E_eV=E, sigma_el=np.full_like(E, cfg["sigma_el"]), sigma_io=sio))
+    rng = np.random.default_rng(5)
+    h = np.diff(E).max()
+    for e in rng.uniform(0.0, E_cap, 200):
+        se, si, _ = oracle.xs_lookup(tab, e)
+        assert se == pytest.approx(cfg["sigma_el"], rel=1e-15)
+        # second derivative of the fit is at most 2 sigma_pk / (E_pk - E_th)^2 in size
+        bound = h * h / 8.0 * 2.0 * cfg["ion_sigma_pk"] / (cfg["ion_E_pk_eV"] - cfg["ion_E_th_eV"]) ** 2
+        assert abs(si - oracle.sigma_ion(cfg, e)) <= bound + 1e-35
+    assert oracle.nu_max(tab) == pytest.approx(oracle.nu_max(cfg), rel=1e-5)
+
+
+def test_table_ionisation_needs_the_binding_energy(oracle_mod):
+    """Ionisation counts only above the binding energy, whatever the table
+    says: a table whose ionisation cross-section is large only below the
+    threshold gives the elastic majorant."""
+    oracle = oracle_mod
+    cfg = workload("coax_32x64_1e4", p_mbar=1.0)
+    Eth = cfg["ion_E_th_eV"]
+    E = np.array([0.0, 0.5 * Eth, Eth, 2 * Eth, 1e5])
+    sel = np.full(5, 1e-20)
+    sio_low = np.array([1e-18, 1e-18, 0.0, 0.0, 0.0])
+    a = oracle.nu_max(dict(cfg, xs=dict(E_eV=E, sigma_el=sel, sigma_io=sio_low)))
+    b = oracle.nu_max(dict(cfg, xs=dict(E_eV=E, sigma_el=sel, sigma_io=np.zeros(5))))
+    assert a == b
+    # and above it the table counts
+    c = oracle.nu_max(dict(cfg, xs=dict(E_eV=E, sigma_el=sel, sigma_io=sio_low[::-1])))
+    assert c > 10 * a
