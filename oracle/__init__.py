@@ -98,6 +98,8 @@ def lib():
         L.or_sigma_ion.restype = d
         L.or_xs_lookup.argtypes = [P, d, vp, vp, vp]
         L.or_xs_lookup.restype = None
+        L.or_nu_drag.argtypes = [P, d]
+        L.or_nu_drag.restype = d
         L.or_scatter_dir.argtypes = [vp, d, d, d, vp]
         L.or_scatter_dir.restype = None
         L.or_opal_secondary.argtypes = [d, d, d]
@@ -204,6 +206,13 @@ def xs_lookup(cfg: dict, E_eV: float):
     out = [ctypes.c_double() for _ in range(3)]
     lib().or_xs_lookup(ctypes.byref(p), float(E_eV), *[ctypes.byref(o) for o in out])
     return tuple(o.value for o in out)
+
+
+def nu_drag(cfg: dict, speed) -> np.ndarray:
+    """Electron-neutral momentum-exchange frequency at each speed (m/s)."""
+    p = params(dict(cfg, nu_max=1.0))   # (the majorant is not needed here)
+    L = lib()
+    return np.array([L.or_nu_drag(ctypes.byref(p), float(v)) for v in np.ravel(speed)])
 
 
 def nu_max(cfg: dict) -> float:
