@@ -238,6 +238,34 @@ int pic_set_efield(pic_handle* h, int sim, const double* er,
  * sections.  The arrays are copied; the caller keeps them.  PIC_EINVAL on
  * a bad argument. */
 #define PIC_XS_MAX_POINTS 1024
+
+/* Fluid moments of simulation `sim`'s particles on the nodes (Sec. IV.A
+ * evaluates the electron fluid's forces from moments of the distribution
+ * function).  out: PIC_MOMENTS grids of (nr + 1) (nz + 1) FP64 (node i * (nz
+ * + 1) + j), in the order n, n u_r, n u_theta, n u_z, n <v_r v_r>,
+ * n <v_r v_theta>, n <v_r v_z>, n <v_theta v_theta>, n <v_theta v_z>,
+ * n <v_z v_z>, n <nu_d>, each (w / V_i) sum_p Lambda_i(r_p, z_p) g(v_p)
+ * with the hat functions and volumes of the density diagnostic, the
+ * particles' stored velocities (the leapfrog's v^{n-1/2}) and nu_d =
+ * n_gas (sigma_el + sigma_io) |v| (the collision path's cross sections;
+ * ionisation above its threshold).  Synchronises. */
+#define PIC_MOMENTS 11
+int pic_moments(pic_handle* h, int sim, double* out);
+
+/* The terms of the electron fluid's force balance (Sec. IV.A) at every
+ * node from moments in the layout of pic_moments (host arrays: one
+ * call's, or averages over several): out holds PIC_FORCE_TERMS x 3 grids
+ * (components r, theta, z) of FP64 in N m^-3, in the order F_E = q n E
+ * (the simulation's current node field), F_B = q n u x B (B analytic),
+ * F_i = -m n (u . grad) u, F_p = -div P with P = m (n <v v> - n u u),
+ * F_d = -m n <nu_d> u, F_a = m n (u - u_prev) / dt_prev (zero when
+ * moments_prev is NULL), and the sum F_i + F_E + F_B + F_p + F_d - F_a
+ * (q = -e, m = m_e).  Cylindrical operators; derivatives by central
+ * differences, one-sided second order on the boundary lines; u = 0 and
+ * P = 0 where n = 0. */
+#define PIC_FORCE_TERMS 7
+int pic_force_balance(pic_handle* h, int sim, const double* moments,
+                      const double* moments_prev, double dt_prev, double* out);
 int pic_set_cross_sections(pic_handle* h, int sim, int n, const double* E_eV,
                            const double* sigma_el_m2, const double* sigma_io_m2,
                            const double* xi);

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpic.so")
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECAPACITY = 0, -1, -2, -3
 PIC_ENOCONV, PIC_ETIMEOUT, PIC_ENONFINITE, PIC_ECUDA = -4, -5, -6, -7
 PIC_GRID_PHI, PIC_GRID_RHS, PIC_GRID_ER, PIC_GRID_EZ = 0, 1, 2, 3
+MOMENTS, FORCE_TERMS = 11, 7   # PIC_MOMENTS, PIC_FORCE_TERMS
 
 c_d, c_i32, c_i64, c_u64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
 
@@ -96,6 +97,8 @@ def lib() -> ctypes.CDLL:
         L.pic_export_particles.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, c_i64, P(c_i64)]
         L.pic_set_efield.argtypes = [vp, ctypes.c_int, vp, vp]
         L.pic_set_cross_sections.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+        L.pic_moments.argtypes = [vp, ctypes.c_int, vp]
+        L.pic_force_balance.argtypes = [vp, ctypes.c_int, vp, vp, c_d, vp]
         L.pic_get_grid.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
         L.pic_solve_field.argtypes = [vp, vp, vp, P(c_d)]
         L.pic_checkpoint.argtypes = [vp, ctypes.c_char_p]
@@ -105,6 +108,7 @@ def lib() -> ctypes.CDLL:
         L.pic_free.restype = None
         for name in ("pic_init", "pic_load_particles", "pic_step", "pic_diagnostics",
                      "pic_export_particles", "pic_set_efield", "pic_set_cross_sections",
+                     "pic_moments", "pic_force_balance",
                      "pic_get_grid", "pic_solve_field",
                      "pic_checkpoint", "pic_restore", "pic_profile"):
             getattr(L, name).restype = ctypes.c_int
@@ -259,6 +263,27 @@ class Simulation:
         assert len(ps[1]) == n and len(pi[1]) == n and (xi is None or len(px[1]) == n)
         _check(lib().pic_set_cross_sections(self.h, sim, n, pe[0], ps[0], pi[0], px[0]),
                "pic_set_cross_sections")
+
+    def moments(self, sim: int = 0) -> np.ndarray:
+        """Fluid moments on the nodes (pic_moments): shape (11, nr + 1, nz + 1)."""
+        out = np.zeros((MOMENTS, self.cfg["nr"] + 1, self.cfg["nz"] + 1))
+        _check(lib().pic_moments(self.h, sim, out.ctypes.data_as(ctypes.c_void_p)), "pic_moments")
+        return out
+
+    def force_balance(self, moments, moments_prev=None, dt_prev: float = 0.0, sim: int = 0):
+        """Force-balance terms (pic_force_balance) from moments of shape
+        (11, nr + 1, nz + 1): shape (7, 3, nr + 1, nz + 1), terms F_E, F_B,
+        F_i, F_p, F_d, F_a and their sum; components r, theta, z."""
+        shape = (MOMENTS, self.cfg["nr"] + 1, self.cfg["nz"] + 1)
+        for m in (moments, moments_prev):
+            if m is not None and np.shape(m) != shape:
+                raise ValueError(f"moments must have shape {shape}, got {np.shape(m)}")
+        pm = _f64(np.ascontiguousarray(moments).ravel())
+        pp = _f64(np.ascontiguousarray(moments_prev).ravel()) if moments_prev is not None else (None, None)
+        out = np.zeros((FORCE_TERMS, 3, self.cfg["nr"] + 1, self.cfg["nz"] + 1))
+        _check(lib().pic_force_balance(self.h, sim, pm[0], pp[0], float(dt_prev),
+                                       out.ctypes.data_as(ctypes.c_void_p)), "pic_force_balance")
+        return out
 
     def get_grid(self, which: int, sim: int = 0) -> np.ndarray:
         out = np.zeros(self.nnodes)

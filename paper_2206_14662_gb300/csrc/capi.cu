@@ -1157,6 +1157,90 @@ int pic_set_cross_sections(pic_handle* h, int sim, int n, const double* E_eV,
   return PIC_OK;
 }
 
+namespace {
+ForceParams force_params(const pic_handle* h, int sim, double dt_prev) {
+  const pic_config& c = h->cfgs[sim];
+  ForceParams F;
+  F.nr = c.nr;
+  F.nz = c.nz;
+  F.bkind = c.bfield_kind;
+  F.r_in = c.r_in;
+  F.hr = h->hr;
+  F.z_min = c.z_min;
+  F.hz = h->hz;
+  F.b0 = c.b0;
+  F.L = c.z_max - c.z_min;
+  F.z_mid = 0.5 * (c.z_min + c.z_max);
+  F.weight = h->sims[sim].weight;
+  F.dt_prev = dt_prev;
+  return F;
+}
+
+// device buffer of `bytes` owned by this call (freed by drop_tmp)
+void* tmp_alloc(pic_handle* h, size_t bytes) { return h_alloc(bytes, h); }
+void drop_tmp(pic_handle* h, void* p) {
+  if (!p) return;
+  auto it = std::find(h->owned.begin(), h->owned.end(), p);
+  if (it != h->owned.end()) h->owned.erase(it);
+  h_free_one(p, h);
+}
+}  // namespace
+
+static_assert(kMoments == PIC_MOMENTS, "moment count of the ABI");
+
+int pic_moments(pic_handle* h, int sim, double* out) {
+  if (!h || sim < 0 || sim >= h->nsim || !out) return PIC_EINVAL;
+  if (h->sticky) return h->sticky;
+  const size_t bytes = (size_t)kMoments * h->nnodes * sizeof(double);
+  double* M = (double*)tmp_alloc(h, bytes);
+  if (!M) return PIC_ENOMEM;
+  const ForceParams F = force_params(h, sim, 0.0);
+  if (h->prec == 32)
+    launch_moments<float>(sim_soa<float>(h, sim, h->cur), h->st + sim, h->Pf[sim], F, M,
+                          h->sims[sim].capacity, h->stream);
+  else
+    launch_moments<double>(sim_soa<double>(h, sim, h->cur), h->st + sim, h->Pd[sim], F, M,
+                           h->sims[sim].capacity, h->stream);
+  int rc = PIC_OK;
+  if (cudaMemcpyAsync(out, M, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    rc = PIC_ECUDA;
+  drop_tmp(h, M);
+  return rc;
+}
+
+int pic_force_balance(pic_handle* h, int sim, const double* moments, const double* moments_prev,
+                      double dt_prev, double* out) {
+  if (!h || sim < 0 || sim >= h->nsim || !moments || !out) return PIC_EINVAL;
+  if (moments_prev && !(dt_prev > 0)) return PIC_EINVAL;
+  if (h->sticky) return h->sticky;
+  const size_t nn = (size_t)h->nnodes;
+  const size_t mb = (size_t)kMoments * nn * sizeof(double);
+  const size_t ob = (size_t)PIC_FORCE_TERMS * 3 * nn * sizeof(double);
+  double* M = (double*)tmp_alloc(h, mb);
+  double* Mp = moments_prev ? (double*)tmp_alloc(h, mb) : nullptr;
+  double* O = (double*)tmp_alloc(h, ob);
+  int rc = (!M || !O || (moments_prev && !Mp)) ? PIC_ENOMEM : PIC_OK;
+  if (!rc && (cudaMemcpyAsync(M, moments, mb, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+              (Mp && cudaMemcpyAsync(Mp, moments_prev, mb, cudaMemcpyHostToDevice, h->stream) !=
+                         cudaSuccess)))
+    rc = PIC_ECUDA;
+  if (!rc) {
+    const ForceParams F = force_params(h, sim, moments_prev ? dt_prev : 0.0);
+    const size_t eo = (size_t)sim * nn * (h->prec == 32 ? sizeof(float2) : sizeof(double2));
+    const void* E = (const char*)h->efield + eo;
+    if (h->prec == 32) launch_force_terms<float>(M, Mp, E, F, O, h->stream);
+    else launch_force_terms<double>(M, Mp, E, F, O, h->stream);
+    if (cudaMemcpyAsync(out, O, ob, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      rc = PIC_ECUDA;
+  }
+  drop_tmp(h, M);
+  drop_tmp(h, Mp);
+  drop_tmp(h, O);
+  return rc;
+}
+
 int pic_get_grid(pic_handle* h, int sim, int which, double* out) {
   if (!h || sim < 0 || sim >= h->nsim || !out) return PIC_EINVAL;
   const size_t bytes = (size_t)h->nnodes * sizeof(double);

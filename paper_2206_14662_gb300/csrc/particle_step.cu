@@ -151,46 +151,6 @@ struct Part {
   Real fr, fz, vr, vt, vz;
 };
 
-// Tabulated n_gas sigma_el, n_gas sigma_io and xi at energy E (J): the
-// point k with E_k <= E < E_{k+1} by bisection, f = f_k + w (f_{k+1} -
-// f_k); the first (last) value at or below E_0 (at or above E_{n-1}); xi0
-// when there is no xi table.  Compiled only into the kernels launched
-// while some simulation has tables (TAB), so the analytic kernels keep
-// their registers.
-template <typename Real>
-struct Xs3 {
-  Real nel, nio, xi;
-};
-template <typename Real>
-__device__ __forceinline__ Xs3<Real> xs_eval(int n, const Real* __restrict__ Et,
-                                          const Real* __restrict__ el,
-                                          const Real* __restrict__ io,
-                                          const Real* __restrict__ xt, Real xi0, Real E) {
-  int k;
-  Real w;
-  if (!(E > Et[0])) {
-    k = 0;
-    w = 0;
-  } else if (!(E < Et[n - 1])) {
-    k = n - 2;
-    w = 1;
-  } else {
-    int lo = 0, hi = n - 1;   // Et[lo] <= E < Et[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (Et[mid] <= E) lo = mid;
-      else hi = mid;
-    }
-    k = lo;
-    w = (E - Et[k]) / (Et[k + 1] - Et[k]);
-  }
-  Xs3<Real> r;
-  r.nel = mad(w, el[k + 1] - el[k], el[k]);
-  r.nio = mad(w, io[k + 1] - io[k], io[k]);
-  r.xi = xt ? mad(w, xt[k + 1] - xt[k], xt[k]) : xi0;
-  return r;
-}
-
 // Collision of a particle that passed the null-collision candidate test
 // (rare): type from u1 against the cumulative frequencies, then elastic
 // scattering or ionisation with a child appended.  q holds the state after

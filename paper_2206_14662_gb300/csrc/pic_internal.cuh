@@ -244,6 +244,45 @@ __device__ __forceinline__ double u01<double>(unsigned x) {
   return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0);
 }
 
+// Tabulated n_gas sigma_el, n_gas sigma_io and xi at energy E (J): the
+// point k with E_k <= E < E_{k+1} by bisection, f = f_k + w (f_{k+1} -
+// f_k); the first (last) value at or below E_0 (at or above E_{n-1}); xi0
+// when there is no xi table.  (The particle step compiles it only into the
+// kernels launched while some simulation has tables.)
+template <typename Real>
+struct Xs3 {
+  Real nel, nio, xi;
+};
+template <typename Real>
+__device__ __forceinline__ Xs3<Real> xs_eval(int n, const Real* __restrict__ Et,
+                                          const Real* __restrict__ el,
+                                          const Real* __restrict__ io,
+                                          const Real* __restrict__ xt, Real xi0, Real E) {
+  int k;
+  Real w;
+  if (!(E > Et[0])) {
+    k = 0;
+    w = 0;
+  } else if (!(E < Et[n - 1])) {
+    k = n - 2;
+    w = 1;
+  } else {
+    int lo = 0, hi = n - 1;   // Et[lo] <= E < Et[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (Et[mid] <= E) lo = mid;
+      else hi = mid;
+    }
+    k = lo;
+    w = (E - Et[k]) / (Et[k + 1] - Et[k]);
+  }
+  Xs3<Real> r;
+  r.nel = fma(w, el[k + 1] - el[k], el[k]);
+  r.nio = fma(w, io[k + 1] - io[k], io[k]);
+  r.xi = xt ? fma(w, xt[k + 1] - xt[k], xt[k]) : xi0;
+  return r;
+}
+
 // ------------------------------------------------------------ host side
 
 // Tables and work arrays of the field solver (field_solve.cu), all in
@@ -325,6 +364,26 @@ void launch_field_solve(const FieldTables& T, const double* rhs,
 // phi = phi_vac + phi_rho of simulation `sim` on all nodes (FP64)
 void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream, int sim = 0);
 int field_solve_kernels(const FieldTables& T);   // launches per solve
+
+// fluid moments and force-balance terms (moments.cu)
+constexpr int kMoments = 11;   // n, n u (3), n <v v> (6), n <nu_d>
+struct ForceParams {
+  int nr, nz, bkind;
+  double r_in, hr, z_min, hz;
+  double b0, L, z_mid;          // field: uniform b0, or the mirror about z_mid
+  double weight;                // electrons per macro-electron
+  double dt_prev;               // time since the previous moments (F_a), 0: none
+};
+// moments of simulation `sim`'s particles (its views s, st, P) on the
+// nodes, scaled to per-volume: kMoments x nnodes FP64 at M
+template <typename Real>
+void launch_moments(const Soa<Real>& s, const DevState* st, const PushParams<Real>& P,
+                    const ForceParams& F, double* M, long long max_slots, cudaStream_t stream);
+// the 7 x 3 force-term grids (F_E, F_B, F_i, F_p, F_d, F_a, sum; r, theta,
+// z) from moments M (and Mprev for F_a, or null) and the node field
+template <typename Real>
+void launch_force_terms(const double* M, const double* Mprev, const void* efield,
+                        const ForceParams& F, double* out, cudaStream_t stream);
 
 // kernels launched from capi.cu (defined in particle_step.cu / sort.cu)
 // rhs: FP64 deposit grid (FP64 path); cnt: fixed-point deposit grid (FP32
