@@ -93,14 +93,23 @@ def _peak_bf16():
     return FALLBACK_BF16_TFLOPS, "fallback"
 
 
+def particle_kernel_sha() -> str:
+    """SHA-256 over the sources the fused particle kernel is compiled from."""
+    h = hashlib.sha256()
+    for name in ("particle_step.cu", "pic_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2206_14662_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def _traffic_record():
     """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+    summary, valid only while the kernel source (particle_step.cu and the
+    header it includes) is unchanged."""
     try:
         with open(os.path.join(ROOT, "profiles", "particle_step_traffic.json")) as f:
             rec = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2206_14662_gb300", "csrc", "particle_step.cu"), "rb").read()
-        if rec.get("source_sha256") == hashlib.sha256(src).hexdigest():
+        if rec.get("source_sha256") == particle_kernel_sha():
             return rec
     except Exception:
         pass
