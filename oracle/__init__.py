@@ -98,8 +98,8 @@ def lib():
         L.or_sigma_ion.restype = d
         L.or_xs_lookup.argtypes = [P, d, vp, vp, vp]
         L.or_xs_lookup.restype = None
-        L.or_nu_drag.argtypes = [P, d]
-        L.or_nu_drag.restype = d
+        L.or_nu_parts.argtypes = [P, d, vp, vp]
+        L.or_nu_parts.restype = None
         L.or_scatter_dir.argtypes = [vp, d, d, d, vp]
         L.or_scatter_dir.restype = None
         L.or_opal_secondary.argtypes = [d, d, d]
@@ -208,11 +208,25 @@ def xs_lookup(cfg: dict, E_eV: float):
     return tuple(o.value for o in out)
 
 
-def nu_drag(cfg: dict, speed) -> np.ndarray:
-    """Electron-neutral momentum-exchange frequency at each speed (m/s)."""
+def nu_parts(cfg: dict, speed):
+    """(nu_el, nu_io) at each speed (m/s): elastic and ionisation
+    frequencies of the collision path."""
     p = params(dict(cfg, nu_max=1.0))   # (the majorant is not needed here)
     L = lib()
-    return np.array([L.or_nu_drag(ctypes.byref(p), float(v)) for v in np.ravel(speed)])
+    speed = np.ravel(np.asarray(speed, dtype=float))
+    el, io = np.zeros(speed.size), np.zeros(speed.size)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    for k, v in enumerate(speed):
+        L.or_nu_parts(ctypes.byref(p), float(v), ctypes.byref(a), ctypes.byref(b))
+        el[k], io[k] = a.value, b.value
+    return el, io
+
+
+def nu_drag(cfg: dict, speed) -> np.ndarray:
+    """Electron-neutral momentum-exchange frequency nu_el + nu_io at each
+    speed (m/s)."""
+    el, io = nu_parts(cfg, speed)
+    return el + io
 
 
 def nu_max(cfg: dict) -> float:

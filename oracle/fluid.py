@@ -10,8 +10,9 @@ moments(): for node i with hat function Lambda_i (bilinear on the (r, z)
 cell) and volume V_i,
     M_c(i) = (w / V_i) sum_p Lambda_i(r_p, z_p) g_c(v_p),
     g = (1, v_r, v_t, v_z, v_r v_r, v_r v_t, v_r v_z, v_t v_t, v_t v_z,
-         v_z v_z, nu_d(|v|)),
-so M_0 = n, M_1..3 = n u, M_4..9 = n <v v>, M_10 = n <nu_d>.
+         v_z v_z, nu_d(|v|), nu_io(|v|)),
+so M_0 = n, M_1..3 = n u, M_4..9 = n <v v>, M_10 = n <nu_d> (momentum
+exchange: elastic + ionisation), M_11 = n <nu_io>.
 
 force_terms(): with u = (n u) / n, P = m (n <v v> - n u u) (u = 0, P = 0
 where n = 0), q = -e, m = m_e, components (r, theta, z):
@@ -26,14 +27,30 @@ where n = 0), q = -e, m = m_e, components (r, theta, z):
     S   = F_i + F_E + F_B + F_p + F_d - F_a
 with derivatives by central differences and one-sided second-order ones on
 the boundary lines.
+
+fluid_model(): the fluid-Poisson model of Sec. V.A (force balance without
+pressure, continuity, Gauss's law) evaluated per node, with
+Omega_c = e B_z / m and omega_p^2 = e^2 n / (eps0 m):
+    u_theta = -E_r / B_z                                 (radial balance)
+    <nu_d>, <nu_io> = M_10 / n, M_11 / n
+    u_r = -(q <nu_d> / m) E_r / (omega_p^2 - Omega_c^2)  (azimuthal balance)
+    omega_p,max^2 = Omega_c^2 <nu_io> / (<nu_io> + <nu_d>)  (peak density)
+    n_max = eps0 m omega_p,max^2 / e^2
+    nu_d, nu_io at the drift speed |E x B| / |B|^2         (Sec. V.B)
+    j = -eps0 E_r <nu_io>     (peak current 2 pi L r_+ j, L and r_+ the
+                               cloud's length and outer radius)
+zero where n = 0 or a denominator vanishes.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import ME, QE, grid, node_volumes, nu_drag
+from . import ME, QE, grid, node_volumes, nu_parts
 
-MOMENTS = 11
+EPS0 = 8.8541878128e-12
+MOMENTS = 12
+FLUID_MODEL = ("u_theta", "nu_d", "nu_io", "u_r", "omega_p2_max", "n_max",
+               "nu_d_drift", "nu_io_drift", "j")
 TERMS = ("F_E", "F_B", "F_i", "F_p", "F_d", "F_a", "sum")
 
 
@@ -48,8 +65,9 @@ def moments(cfg: dict, r, z, vr, vt, vz, weight: float) -> np.ndarray:
     iz = np.clip(np.floor(sz).astype(int), 0, nz - 1)
     fr, fz = sr - ir, sz - iz
     vr, vt, vz = (np.asarray(a, float) for a in (vr, vt, vz))
+    nu_el, nu_io = nu_parts(cfg, np.sqrt(vr * vr + vt * vt + vz * vz))
     g = [np.ones_like(vr), vr, vt, vz, vr * vr, vr * vt, vr * vz, vt * vt, vt * vz, vz * vz,
-         nu_drag(cfg, np.sqrt(vr * vr + vt * vt + vz * vz))]
+         nu_el + nu_io, nu_io]
     corners = [(0, 0, (1 - fr) * (1 - fz)), (1, 0, fr * (1 - fz)), (0, 1, (1 - fr) * fz),
                (1, 1, fr * fz)]
     M = np.zeros((MOMENTS, nr + 1, nz + 1))
@@ -124,3 +142,37 @@ def force_terms(cfg: dict, M: np.ndarray, Er: np.ndarray, Ez: np.ndarray,
         T[5] = m * n * (u - u_prev) / dt_prev
     T[6] = T[2] + T[0] + T[1] + T[3] + T[4] - T[5]
     return T
+
+
+def fluid_model(cfg: dict, M: np.ndarray, Er: np.ndarray, Ez: np.ndarray) -> np.ndarray:
+    """(9, nr + 1, nz + 1) fluid-model grids in the order of FLUID_MODEL."""
+    shp = (cfg["nr"] + 1, cfg["nz"] + 1)
+    Er = np.asarray(Er, float).reshape(shp)
+    Ez = np.asarray(Ez, float).reshape(shp)
+    Br, Bz = magnetic_field(cfg)
+    q, m = -QE, ME
+    n = M[0]
+    has = n > 0
+    safe = np.where(has, n, 1.0)
+    nu_d = np.where(has, M[10] / safe, 0.0)
+    nu_io = np.where(has, M[11] / safe, 0.0)
+    Oc2 = (QE * Bz / m) ** 2
+    wp2 = QE ** 2 * n / (EPS0 * m)
+    den = wp2 - Oc2
+    u_r = np.where(den != 0, -(q * nu_d / m) * Er / np.where(den != 0, den, 1.0), 0.0)
+    tot = nu_io + nu_d
+    w2 = np.where(tot > 0, Oc2 * nu_io / np.where(tot > 0, tot, 1.0), 0.0)
+    # drift speed |E x B| / |B|^2 with E = (E_r, 0, E_z), B = (B_r, 0, B_z)
+    E3 = np.stack([Er, np.zeros_like(Er), Ez], axis=-1)
+    B3 = np.stack([Br, np.zeros_like(Br), Bz], axis=-1)
+    B2 = (B3 ** 2).sum(-1)
+    vd = np.linalg.norm(np.cross(E3, B3), axis=-1) / B2
+    d_el, d_io = nu_parts(cfg, vd.ravel())
+    out = np.zeros((len(FLUID_MODEL),) + shp)
+    out[0] = np.where(Bz != 0, -Er / np.where(Bz != 0, Bz, 1.0), 0.0)
+    out[1], out[2], out[3], out[4] = nu_d, nu_io, u_r, w2
+    out[5] = EPS0 * m * w2 / QE ** 2
+    out[6] = (d_el + d_io).reshape(shp)
+    out[7] = d_io.reshape(shp)
+    out[8] = -EPS0 * Er * nu_io
+    return out

@@ -191,12 +191,11 @@ static void or_nu(const or_params* P, double v, double* nu_el, double* nu_io) {
   or_nu_xi(P, v, nu_el, nu_io, &xi);
 }
 
-/* electron-neutral momentum-exchange frequency nu_d = nu_el + nu_io at
- * speed v (the drag of the fluid force balance, Sec. IV.A) */
-double or_nu_drag(const or_params* P, double v) {
-  double a, b;
-  or_nu(P, v, &a, &b);
-  return a + b;
+/* elastic and ionisation frequencies at speed v; their sum is the
+ * electron-neutral momentum-exchange frequency nu_d of the fluid force
+ * balance (Sec. IV.A) */
+void or_nu_parts(const or_params* P, double v, double* nu_el, double* nu_io) {
+  or_nu(P, v, nu_el, nu_io);
 }
 
 /* Majorant: (1 + 1e-6) * max of nu_el + nu_io over E_k = E_cap k / 1e5,

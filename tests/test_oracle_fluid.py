@@ -6,7 +6,8 @@ pressure, rigid rotation, radial expansion, pressure fields whose
 divergence is known, the Lorentz force against a plain cross product, the
 drag of mono-energetic electrons, the inertia of two snapshots, the mirror
 field's vanishing divergence and the isothermal Boltzmann equilibrium,
-where the force balance sums to zero."""
+where the force balance sums to zero.  The fluid-Poisson model's
+predictions (Sec. V) against the balance equations they solve."""
 import numpy as np
 import pytest
 
@@ -73,8 +74,9 @@ def test_partition_of_unity(cfg):
     vr, vt, vz = rng.normal(0, 1e6, (3, n))
     M = fluid.moments(cfg, r, z, vr, vt, vz, w)
     V = _vol(cfg)
-    nu = oracle.nu_drag(cfg, np.sqrt(vr ** 2 + vt ** 2 + vz ** 2))
-    g = [np.ones(n), vr, vt, vz, vr * vr, vr * vt, vr * vz, vt * vt, vt * vz, vz * vz, nu]
+    el, io = oracle.nu_parts(cfg, np.sqrt(vr ** 2 + vt ** 2 + vz ** 2))
+    assert io.sum() > 0
+    g = [np.ones(n), vr, vt, vz, vr * vr, vr * vt, vr * vz, vt * vt, vt * vz, vz * vz, el + io, io]
     for c in range(fluid.MOMENTS):
         assert (M[c] * V).sum() == pytest.approx(w * g[c].sum(), rel=1e-10, abs=1e-9 * w * np.abs(g[c]).sum())
 
@@ -254,3 +256,92 @@ def test_empty_nodes_have_no_flow(cfg):
     M = np.zeros((fluid.MOMENTS,) + shp)
     T = fluid.force_terms(cfg, M, np.ones(shp), np.ones(shp))
     assert not T.any()
+
+
+def _fm_moments(cfg, n, nu_d, nu_io):
+    shp = _shape(cfg)
+    M = np.zeros((fluid.MOMENTS,) + shp)
+    M[0] = n
+    M[10] = n * nu_d
+    M[11] = n * nu_io
+    return M
+
+
+def test_fluid_model_solves_the_azimuthal_balance(cfg):
+    """u_r of the model satisfies the azimuthal balance it came from,
+    m u_r (1/r) d(r u_theta)/dr = -q u_r B_z - m nu_d u_theta, with the left
+    side replaced through Gauss's law by -m u_r q n / (eps0 B_z) and
+    u_theta = -E_r / B_z; below and above the Brillouin density."""
+    c = dict(cfg, b0=0.2, bfield_kind=0)
+    rng = np.random.default_rng(3)
+    shp = _shape(c)
+    q, m = -QE, ME
+    n_brillouin = fluid.EPS0 * c["b0"] ** 2 / ME
+    n = rng.uniform(0.05, 3.0, shp) * n_brillouin
+    nu_d = rng.uniform(1e6, 1e8, shp)
+    Er = rng.normal(0, 1e5, shp)
+    out = fluid.fluid_model(c, _fm_moments(c, n, nu_d, 0.3 * nu_d), Er, np.zeros(shp))
+    u_t, u_r = out[0], out[3]
+    assert np.allclose(u_t, -Er / c["b0"], rtol=1e-14)
+    lhs = -m * u_r * q * n / (fluid.EPS0 * c["b0"])
+    rhs = -q * u_r * c["b0"] - m * nu_d * u_t
+    assert np.abs(lhs - rhs).max() <= 1e-9 * np.abs(rhs).max()
+
+
+def test_fluid_model_peak_density(cfg):
+    """omega_p,max^2 = Omega_c^2 nu_io / (nu_io + nu_d): half Omega_c^2 when
+    the two frequencies are equal, zero without ionisation; n_max gives
+    back omega_p,max through omega_p^2 = e^2 n / (eps0 m)."""
+    c = dict(cfg, b0=0.25, bfield_kind=0)
+    shp = _shape(c)
+    n = np.full(shp, 1e15)
+    nu = np.full(shp, 3e7)
+    Oc2 = (QE * c["b0"] / ME) ** 2
+    out = fluid.fluid_model(c, _fm_moments(c, n, nu, nu), np.zeros(shp), np.zeros(shp))
+    assert np.allclose(out[4], Oc2 / 2, rtol=1e-14)
+    assert np.allclose(QE ** 2 * out[5] / (fluid.EPS0 * ME), out[4], rtol=1e-14)
+    assert np.allclose(out[1], nu, rtol=1e-15) and np.allclose(out[2], nu, rtol=1e-15)
+    out0 = fluid.fluid_model(c, _fm_moments(c, n, nu, 0 * nu), np.zeros(shp), np.zeros(shp))
+    assert not out0[4].any() and not out0[5].any()
+    # empty nodes: no ratios
+    empty = fluid.fluid_model(c, _fm_moments(c, 0 * n, nu, nu), np.ones(shp), np.ones(shp))
+    assert not empty[1:6].any() and not empty[8].any()
+
+
+def test_fluid_model_drift_frequencies(cfg):
+    """Collision frequencies at the E x B drift speed: with a uniform B_z
+    and a radial field the drift is |E_r| / B_z; below the ionisation
+    threshold nu_d = n_gas sigma_el v, above it the fit
+    sigma_pk 2 s / (1 + s^2), s = (E - E_th) / (E_pk - E_th), adds."""
+    c = dict(cfg, b0=0.1, bfield_kind=0)
+    shp = _shape(c)
+    n_gas = oracle.derived(c)["n_gas"]
+    # a speed below and one above threshold
+    E_lo, E_hi = 0.4 * c["ion_E_th_eV"], 4.0 * c["ion_E_th_eV"]
+    v_lo, v_hi = np.sqrt(2 * E_lo * QE / ME), np.sqrt(2 * E_hi * QE / ME)
+    Er = np.where(np.arange(shp[1])[None, :] % 2 == 0, v_lo, -v_hi) * c["b0"] * np.ones(shp)
+    out = fluid.fluid_model(c, _fm_moments(c, np.ones(shp), np.ones(shp), np.ones(shp)), Er,
+                            np.zeros(shp))
+    lo, hi = out[:, :, 0], out[:, :, 1]
+    assert np.allclose(lo[6], n_gas * c["sigma_el"] * v_lo, rtol=1e-12)
+    assert not lo[7].any()
+    s = (E_hi - c["ion_E_th_eV"]) / (c["ion_E_pk_eV"] - c["ion_E_th_eV"])
+    sig_io = c["ion_sigma_pk"] * 2 * s / (1 + s * s)
+    assert np.allclose(hi[7], n_gas * sig_io * v_hi, rtol=1e-12)
+    assert np.allclose(hi[6], n_gas * (c["sigma_el"] + sig_io) * v_hi, rtol=1e-12)
+
+
+def test_fluid_model_drift_speed_in_the_mirror(cfg):
+    """|E x B| / |B|^2 with B_r != 0: against the component formula
+    |E_z B_r - E_r B_z| / (B_r^2 + B_z^2), below threshold (pure elastic)."""
+    c = dict(cfg, b0=0.5, bfield_kind=1, sigma_el=1e-20)
+    shp = _shape(c)
+    rng = np.random.default_rng(4)
+    Er, Ez = rng.normal(0, 3e4, (2,) + shp)
+    Br, Bz = fluid.magnetic_field(c)
+    vd = np.abs(Ez * Br - Er * Bz) / (Br ** 2 + Bz ** 2)
+    assert (0.5 * ME * vd ** 2 / QE < c["ion_E_th_eV"]).all()
+    n_gas = oracle.derived(c)["n_gas"]
+    out = fluid.fluid_model(c, _fm_moments(c, np.ones(shp), np.ones(shp), np.ones(shp)), Er, Ez)
+    assert np.allclose(out[6], n_gas * 1e-20 * vd, rtol=1e-12)
+    assert np.allclose(out[8], -fluid.EPS0 * Er * 1.0, rtol=1e-15)
