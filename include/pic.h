@@ -241,31 +241,59 @@ int pic_set_efield(pic_handle* h, int sim, const double* er,
 
 /* Fluid moments of simulation `sim`'s particles on the nodes (Sec. IV.A
  * evaluates the electron fluid's forces from moments of the distribution
- * function).  out: PIC_MOMENTS grids of (nr + 1) (nz + 1) FP64 (node i * (nz
- * + 1) + j), in the order n, n u_r, n u_theta, n u_z, n <v_r v_r>,
- * n <v_r v_theta>, n <v_r v_z>, n <v_theta v_theta>, n <v_theta v_z>,
- * n <v_z v_z>, n <nu_d>, each (w / V_i) sum_p Lambda_i(r_p, z_p) g(v_p)
- * with the hat functions and volumes of the density diagnostic, the
- * particles' stored velocities (the leapfrog's v^{n-1/2}) and nu_d =
- * n_gas (sigma_el + sigma_io) |v| (the collision path's cross sections;
- * ionisation above its threshold).  Synchronises. */
-#define PIC_MOMENTS 11
+ * function).  out: host array of PIC_MOMENTS grids of (nr + 1) (nz + 1)
+ * FP64 (node i * (nz + 1) + j), in the order n, n u_r, n u_theta, n u_z,
+ * n <v_r v_r>, n <v_r v_theta>, n <v_r v_z>, n <v_theta v_theta>,
+ * n <v_theta v_z>, n <v_z v_z>, n <nu_d>, n <nu_io>, each
+ * (w / V_i) sum_p Lambda_i(r_p, z_p) g(v_p) with the hat functions and
+ * volumes of the density diagnostic, the particles' stored velocities (the
+ * leapfrog's v^{n-1/2}), nu_d = n_gas (sigma_el + sigma_io) |v| (momentum
+ * exchange) and nu_io = n_gas sigma_io |v| (ionisation), with the
+ * collision path's cross sections (ionisation above its threshold).  Uses
+ * a temporary device buffer; synchronises.  PIC_EINVAL on a bad handle,
+ * index or NULL out; PIC_ENOMEM, PIC_ECUDA. */
+#define PIC_MOMENTS 12
 int pic_moments(pic_handle* h, int sim, double* out);
 
 /* The terms of the electron fluid's force balance (Sec. IV.A) at every
- * node from moments in the layout of pic_moments (host arrays: one
- * call's, or averages over several): out holds PIC_FORCE_TERMS x 3 grids
- * (components r, theta, z) of FP64 in N m^-3, in the order F_E = q n E
- * (the simulation's current node field), F_B = q n u x B (B analytic),
- * F_i = -m n (u . grad) u, F_p = -div P with P = m (n <v v> - n u u),
- * F_d = -m n <nu_d> u, F_a = m n (u - u_prev) / dt_prev (zero when
- * moments_prev is NULL), and the sum F_i + F_E + F_B + F_p + F_d - F_a
- * (q = -e, m = m_e).  Cylindrical operators; derivatives by central
- * differences, one-sided second order on the boundary lines; u = 0 and
- * P = 0 where n = 0. */
+ * node from moments in the layout of pic_moments (host arrays, read only:
+ * one call's moments, or averages over several steps): out (host) holds
+ * PIC_FORCE_TERMS x 3 grids (components r, theta, z) of FP64 in N m^-3, in
+ * the order F_E = q n E (the simulation's current node field), F_B =
+ * q n u x B (B analytic), F_i = -m n (u . grad) u, F_p = -div P with
+ * P = m (n <v v> - n u u), F_d = -m n <nu_d> u, F_a = m n (u - u_prev) /
+ * dt_prev (zero when moments_prev is NULL), and the sum
+ * F_i + F_E + F_B + F_p + F_d - F_a (q = -e, m = m_e).  Cylindrical
+ * operators; derivatives by central differences, one-sided second order on
+ * the boundary lines; u = 0 and P = 0 where n = 0.  Synchronises.
+ * PIC_EINVAL on a bad handle or index, NULL moments or out, or
+ * moments_prev with dt_prev <= 0; PIC_ENOMEM, PIC_ECUDA. */
 #define PIC_FORCE_TERMS 7
 int pic_force_balance(pic_handle* h, int sim, const double* moments,
                       const double* moments_prev, double dt_prev, double* out);
+
+/* Predictions of the fluid-Poisson model (Sec. V.A: the force balance
+ * without pressure, the continuity equation and Gauss's law) at every node
+ * from moments in the layout of pic_moments (host, read only) and the
+ * simulation's current node field.  out (host): PIC_FLUID_MODEL grids of
+ * FP64, in the order
+ *   u_theta = -E_r / B_z (m/s),
+ *   <nu_d> = M_10 / n, <nu_io> = M_11 / n (1/s),
+ *   u_r = -(q <nu_d> / m) E_r / (omega_p^2 - Omega_c^2) (m/s),
+ *   omega_p,max^2 = Omega_c^2 <nu_io> / (<nu_io> + <nu_d>) (1/s^2),
+ *   n_max = eps0 m omega_p,max^2 / e^2 (m^-3),
+ *   nu_d and nu_io at the E x B drift speed |E x B| / |B|^2 (1/s, Sec. V.B's
+ *   approximation),
+ *   j = -eps0 E_r <nu_io> (A/m^2; the peak current is 2 pi L r_+ j at the
+ *   cloud edge r_+),
+ * with q = -e, m = m_e, Omega_c = e B_z / m, omega_p^2 = e^2 n / (eps0 m);
+ * a value whose moment ratio has n = 0, or whose denominator is 0, is 0.
+ * Averaging over time (the paper's <>_T) is the caller's: average the
+ * moments, or the outputs.  Synchronises.  PIC_EINVAL on a bad handle or
+ * index or NULL pointers; PIC_ENOMEM, PIC_ECUDA. */
+#define PIC_FLUID_MODEL 9
+int pic_fluid_model(pic_handle* h, int sim, const double* moments, double* out);
+
 int pic_set_cross_sections(pic_handle* h, int sim, int n, const double* E_eV,
                            const double* sigma_el_m2, const double* sigma_io_m2,
                            const double* xi);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpic.so")
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECAPACITY = 0, -1, -2, -3
 PIC_ENOCONV, PIC_ETIMEOUT, PIC_ENONFINITE, PIC_ECUDA = -4, -5, -6, -7
 PIC_GRID_PHI, PIC_GRID_RHS, PIC_GRID_ER, PIC_GRID_EZ = 0, 1, 2, 3
-MOMENTS, FORCE_TERMS = 11, 7   # PIC_MOMENTS, PIC_FORCE_TERMS
+MOMENTS, FORCE_TERMS, FLUID_MODEL = 12, 7, 9   # PIC_MOMENTS, PIC_FORCE_TERMS, PIC_FLUID_MODEL
 
 c_d, c_i32, c_i64, c_u64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
 
@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
         L.pic_set_cross_sections.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.pic_moments.argtypes = [vp, ctypes.c_int, vp]
         L.pic_force_balance.argtypes = [vp, ctypes.c_int, vp, vp, c_d, vp]
+        L.pic_fluid_model.argtypes = [vp, ctypes.c_int, vp, vp]
         L.pic_get_grid.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
         L.pic_solve_field.argtypes = [vp, vp, vp, P(c_d)]
         L.pic_checkpoint.argtypes = [vp, ctypes.c_char_p]
@@ -108,7 +109,7 @@ def lib() -> ctypes.CDLL:
         L.pic_free.restype = None
         for name in ("pic_init", "pic_load_particles", "pic_step", "pic_diagnostics",
                      "pic_export_particles", "pic_set_efield", "pic_set_cross_sections",
-                     "pic_moments", "pic_force_balance",
+                     "pic_moments", "pic_force_balance", "pic_fluid_model",
                      "pic_get_grid", "pic_solve_field",
                      "pic_checkpoint", "pic_restore", "pic_profile"):
             getattr(L, name).restype = ctypes.c_int
@@ -283,6 +284,20 @@ class Simulation:
         out = np.zeros((FORCE_TERMS, 3, self.cfg["nr"] + 1, self.cfg["nz"] + 1))
         _check(lib().pic_force_balance(self.h, sim, pm[0], pp[0], float(dt_prev),
                                        out.ctypes.data_as(ctypes.c_void_p)), "pic_force_balance")
+        return out
+
+    def fluid_model(self, moments, sim: int = 0) -> np.ndarray:
+        """Fluid-Poisson model predictions (pic_fluid_model) from moments of
+        shape (12, nr + 1, nz + 1): shape (9, nr + 1, nz + 1), in the order
+        u_theta, <nu_d>, <nu_io>, u_r, omega_p,max^2, n_max, nu_d and nu_io
+        at the E x B drift speed, j."""
+        shape = (MOMENTS, self.cfg["nr"] + 1, self.cfg["nz"] + 1)
+        if np.shape(moments) != shape:
+            raise ValueError(f"moments must have shape {shape}, got {np.shape(moments)}")
+        pm = _f64(np.ascontiguousarray(moments).ravel())
+        out = np.zeros((FLUID_MODEL, self.cfg["nr"] + 1, self.cfg["nz"] + 1))
+        _check(lib().pic_fluid_model(self.h, sim, pm[0], out.ctypes.data_as(ctypes.c_void_p)),
+               "pic_fluid_model")
         return out
 
     def get_grid(self, which: int, sim: int = 0) -> np.ndarray:

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "pic_internal.cuh"
+#include "fluid.cuh"
 
 using namespace pic;
 
@@ -1187,6 +1188,7 @@ void drop_tmp(pic_handle* h, void* p) {
 }  // namespace
 
 static_assert(kMoments == PIC_MOMENTS, "moment count of the ABI");
+static_assert(kFluidModel == PIC_FLUID_MODEL, "fluid-model grid count of the ABI");
 
 int pic_moments(pic_handle* h, int sim, double* out) {
   if (!h || sim < 0 || sim >= h->nsim || !out) return PIC_EINVAL;
@@ -1237,6 +1239,32 @@ int pic_force_balance(pic_handle* h, int sim, const double* moments, const doubl
   }
   drop_tmp(h, M);
   drop_tmp(h, Mp);
+  drop_tmp(h, O);
+  return rc;
+}
+
+int pic_fluid_model(pic_handle* h, int sim, const double* moments, double* out) {
+  if (!h || sim < 0 || sim >= h->nsim || !moments || !out) return PIC_EINVAL;
+  if (h->sticky) return h->sticky;
+  const size_t nn = (size_t)h->nnodes;
+  const size_t mb = (size_t)kMoments * nn * sizeof(double);
+  const size_t ob = (size_t)kFluidModel * nn * sizeof(double);
+  double* M = (double*)tmp_alloc(h, mb);
+  double* O = (double*)tmp_alloc(h, ob);
+  int rc = (!M || !O) ? PIC_ENOMEM : PIC_OK;
+  if (!rc && cudaMemcpyAsync(M, moments, mb, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    rc = PIC_ECUDA;
+  if (!rc) {
+    const ForceParams F = force_params(h, sim, 0.0);
+    const size_t eo = (size_t)sim * nn * (h->prec == 32 ? sizeof(float2) : sizeof(double2));
+    const void* E = (const char*)h->efield + eo;
+    if (h->prec == 32) launch_fluid_model<float>(M, E, F, h->Pf[sim], O, h->stream);
+    else launch_fluid_model<double>(M, E, F, h->Pd[sim], O, h->stream);
+    if (cudaMemcpyAsync(out, O, ob, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      rc = PIC_ECUDA;
+  }
+  drop_tmp(h, M);
   drop_tmp(h, O);
   return rc;
 }

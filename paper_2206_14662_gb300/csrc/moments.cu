@@ -6,11 +6,12 @@
 // Moments.  For node i with hat function Lambda_i and volume V_i,
 //   M_c(i) = (w / V_i) sum_p Lambda_i(r_p, z_p) g_c(v_p),
 //   g = (1, v_r, v_theta, v_z, v_r v_r, v_r v_theta, v_r v_z,
-//        v_theta v_theta, v_theta v_z, v_z v_z, nu_d(|v|)),
-// w the macro weight and nu_d = n_gas (sigma_el + sigma_io) |v| the
-// electron-neutral momentum-exchange frequency (the collision path's
-// cross sections: analytic or tabulated, ionisation only above its
-// threshold).  So M_0 = n, M_1..3 = n u, M_4..9 = n <v v>, M_10 = n <nu_d>.
+//        v_theta v_theta, v_theta v_z, v_z v_z, nu_d(|v|), nu_io(|v|)),
+// w the macro weight, nu_d = n_gas (sigma_el + sigma_io) |v| the
+// electron-neutral momentum-exchange frequency and nu_io = n_gas sigma_io
+// |v| the ionisation frequency (the collision path's cross sections:
+// analytic or tabulated, ionisation only above its threshold).  So M_0 =
+// n, M_1..3 = n u, M_4..9 = n <v v>, M_10 = n <nu_d>, M_11 = n <nu_io>.
 // The weights Lambda_i are the deposit's bilinear ones; accumulation is in
 // FP64 global atomics, a warp whose particles share one cell adding its
 // sums once.
@@ -27,28 +28,46 @@
 //   S   = F_i + F_E + F_B + F_p + F_d - F_a
 // Derivatives: central differences, one-sided second order on the boundary
 // lines (as the node field); where n = 0, u = 0 and P = 0.
+//
+// Fluid-Poisson model (Sec. V.A, pressure neglected), per node from the
+// moments and the node field, with Omega_c = e B_z / m_e and
+// omega_p^2 = e^2 n / (eps0 m_e):
+//   u_theta = -E_r / B_z                               (Eq. uthet)
+//   <nu_d>, <nu_io> = M_10 / n, M_11 / n
+//   u_r = -(q <nu_d> / m) E_r / (omega_p^2 - Omega_c^2)   (Eq. ur)
+//   omega_p,max^2 = Omega_c^2 <nu_io> / (<nu_io> + <nu_d>)   (Eq. omegape_pred)
+//   n_max = eps0 m omega_p,max^2 / e^2
+//   nu_d, nu_io at the E x B drift speed v = |E x B| / |B|^2 (Sec. V.B's
+//   approximation of the collision frequencies)
+//   j = -eps0 E_r <nu_io>   (I = 2 pi L r_+ j at the cloud edge, Eq. current)
+// Zero where n = 0 (the moment ratios) or where a denominator vanishes.
 #include <algorithm>
 
-#include "pic_internal.cuh"
+#include "fluid.cuh"
 
 namespace pic {
 
 constexpr int kMomThreads = 256;
 
+// elastic and ionisation frequencies at speed^2 v2
 template <typename Real>
-__device__ __forceinline__ double nu_drag(const PushParams<Real>& P, double v2) {
+__device__ __forceinline__ void nu_parts(const PushParams<Real>& P, double v2, double& nu_el,
+                                         double& nu_io) {
   const double speed = sqrt(v2);
   const double Ek = 0.5 * kMe * v2;
   if (P.xs_n > 0) {
     const Xs3<Real> x = xs_eval<Real>(P.xs_n, P.xs_E, P.xs_nel, P.xs_nio, P.xs_xi, P.xi, (Real)Ek);
-    return ((double)x.nel + (Ek > (double)P.e_th ? (double)x.nio : 0.0)) * speed;
+    nu_el = (double)x.nel * speed;
+    nu_io = Ek > (double)P.e_th ? (double)x.nio * speed : 0.0;
+    return;
   }
   double sio = 0.0;
   if (Ek > (double)P.e_th) {
     const double qq = (Ek - (double)P.e_th) * (double)P.e_span_inv;
     sio = (double)P.sig_pk * 2.0 * qq / (1.0 + qq * qq);
   }
-  return ((double)P.nsig_el + (double)P.n_gas * sio) * speed;
+  nu_el = (double)P.nsig_el * speed;
+  nu_io = (double)P.n_gas * sio * speed;
 }
 
 template <typename Real>
@@ -75,7 +94,10 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, double* M, int nn
       g[0] = 1.0; g[1] = vr; g[2] = vt; g[3] = vz;
       g[4] = vr * vr; g[5] = vr * vt; g[6] = vr * vz;
       g[7] = vt * vt; g[8] = vt * vz; g[9] = vz * vz;
-      g[10] = nu_drag<Real>(P, vr * vr + vt * vt + vz * vz);
+      double nel, nio;
+      nu_parts<Real>(P, vr * vr + vt * vt + vz * vz, nel, nio);
+      g[10] = nel + nio;
+      g[11] = nio;
     } else {
 #pragma unroll
       for (int k = 0; k < kMoments; ++k) g[k] = 0.0;
@@ -119,6 +141,19 @@ __global__ void k_moment_scale(double* M, ForceParams F) {
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nnodes; o += gridDim.x * blockDim.x) {
     const double s = F.weight / node_volume(F, o / (F.nz + 1), o % (F.nz + 1));
     for (int k = 0; k < kMoments; ++k) M[(size_t)k * nnodes + o] *= s;
+  }
+}
+
+// magnetic field (B_r, B_z) at node (i, j)
+__device__ __forceinline__ void node_b(const ForceParams& F, int i, int j, double& Br,
+                                       double& Bz) {
+  Br = 0.0;
+  Bz = F.b0;
+  if (F.bkind == 1) {
+    const double r = F.r_in + i * F.hr;
+    const double zeta = F.z_min + j * F.hz - F.z_mid;
+    Bz = F.b0 * (1.0 + 2.0 * zeta * zeta / (F.L * F.L));
+    Br = -2.0 * F.b0 * r * zeta / (F.L * F.L);
   }
 }
 
@@ -179,13 +214,8 @@ __global__ void k_force_terms(const double* __restrict__ M, const double* __rest
       du_r[a] = dr(rm2.u[a], rm1.u[a], c.u[a], rp1.u[a], rp2.u[a]);
       du_z[a] = dz(zm2.u[a], zm1.u[a], c.u[a], zp1.u[a], zp2.u[a]);
     }
-    // B at the node
-    double Br = 0.0, Bz = F.b0;
-    if (F.bkind == 1) {
-      const double zeta = F.z_min + j * F.hz - F.z_mid;
-      Bz = F.b0 * (1.0 + 2.0 * zeta * zeta / (F.L * F.L));
-      Br = -2.0 * F.b0 * r * zeta / (F.L * F.L);
-    }
+    double Br, Bz;
+    node_b(F, i, j, Br, Bz);
     const double n = c.n, ur = c.u[0], ut = c.u[1], uz = c.u[2];
     double T[7][3];
     T[0][0] = q * n * (double)E[o].x;
@@ -230,6 +260,51 @@ __global__ void k_force_terms(const double* __restrict__ M, const double* __rest
 }
 
 template <typename Real>
+__global__ void k_fluid_model(const double* __restrict__ M,
+                              const typename Vec2<Real>::type* __restrict__ E, ForceParams F,
+                              PushParams<Real> P, double* __restrict__ out) {
+  const int nzp = F.nz + 1, nnodes = (F.nr + 1) * nzp;
+  const double m = kMe, q = -kQe;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nnodes; o += gridDim.x * blockDim.x) {
+    const int i = o / nzp, j = o % nzp;
+    double Br, Bz;
+    node_b(F, i, j, Br, Bz);
+    const double Er = (double)E[o].x, Ez = (double)E[o].y;
+    const double n = M[o];
+    const double nud = n > 0 ? M[(size_t)10 * nnodes + o] / n : 0.0;
+    const double nuio = n > 0 ? M[(size_t)11 * nnodes + o] / n : 0.0;
+    const double Oc2 = (q * Bz / m) * (q * Bz / m);
+    const double wp2 = q * q * n / (kEps0 * m);
+    const double den = wp2 - Oc2;
+    const double wmax2 = nuio + nud > 0 ? Oc2 * nuio / (nuio + nud) : 0.0;
+    // E x B drift speed: |E x B| = |E_z B_r - E_r B_z| (E and B in the r-z plane)
+    const double B2 = Br * Br + Bz * Bz;
+    const double vd = B2 > 0 ? fabs(Ez * Br - Er * Bz) / B2 : 0.0;
+    double dnel, dnio;
+    nu_parts<Real>(P, vd * vd, dnel, dnio);
+    double g[kFluidModel];
+    g[0] = Bz != 0 ? -Er / Bz : 0.0;
+    g[1] = nud;
+    g[2] = nuio;
+    g[3] = den != 0 ? -(q * nud / m) * Er / den : 0.0;
+    g[4] = wmax2;
+    g[5] = kEps0 * m * wmax2 / (q * q);
+    g[6] = dnel + dnio;
+    g[7] = dnio;
+    g[8] = -kEps0 * Er * nuio;
+    for (int k = 0; k < kFluidModel; ++k) out[(size_t)k * nnodes + o] = g[k];
+  }
+}
+
+template <typename Real>
+void launch_fluid_model(const double* M, const void* efield, const ForceParams& F,
+                        const PushParams<Real>& P, double* out, cudaStream_t stream) {
+  const int nnodes = (F.nr + 1) * (F.nz + 1);
+  k_fluid_model<Real><<<std::min(152 * 4, (nnodes + 127) / 128), 128, 0, stream>>>(
+      M, (const typename Vec2<Real>::type*)efield, F, P, out);
+}
+
+template <typename Real>
 void launch_moments(const Soa<Real>& s, const DevState* st, const PushParams<Real>& P,
                     const ForceParams& F, double* M, long long max_slots, cudaStream_t stream) {
   const int nnodes = (F.nr + 1) * (F.nz + 1);
@@ -257,5 +332,9 @@ template void launch_force_terms<float>(const double*, const double*, const void
                                         const ForceParams&, double*, cudaStream_t);
 template void launch_force_terms<double>(const double*, const double*, const void*,
                                          const ForceParams&, double*, cudaStream_t);
+template void launch_fluid_model<float>(const double*, const void*, const ForceParams&,
+                                        const PushParams<float>&, double*, cudaStream_t);
+template void launch_fluid_model<double>(const double*, const void*, const ForceParams&,
+                                         const PushParams<double>&, double*, cudaStream_t);
 
 }  // namespace pic

@@ -365,26 +365,6 @@ void launch_field_solve(const FieldTables& T, const double* rhs,
 void launch_phi_out(const FieldTables& T, double* phi, cudaStream_t stream, int sim = 0);
 int field_solve_kernels(const FieldTables& T);   // launches per solve
 
-// fluid moments and force-balance terms (moments.cu)
-constexpr int kMoments = 11;   // n, n u (3), n <v v> (6), n <nu_d>
-struct ForceParams {
-  int nr, nz, bkind;
-  double r_in, hr, z_min, hz;
-  double b0, L, z_mid;          // field: uniform b0, or the mirror about z_mid
-  double weight;                // electrons per macro-electron
-  double dt_prev;               // time since the previous moments (F_a), 0: none
-};
-// moments of simulation `sim`'s particles (its views s, st, P) on the
-// nodes, scaled to per-volume: kMoments x nnodes FP64 at M
-template <typename Real>
-void launch_moments(const Soa<Real>& s, const DevState* st, const PushParams<Real>& P,
-                    const ForceParams& F, double* M, long long max_slots, cudaStream_t stream);
-// the 7 x 3 force-term grids (F_E, F_B, F_i, F_p, F_d, F_a, sum; r, theta,
-// z) from moments M (and Mprev for F_a, or null) and the node field
-template <typename Real>
-void launch_force_terms(const double* M, const double* Mprev, const void* efield,
-                        const ForceParams& F, double* out, cudaStream_t stream);
-
 // kernels launched from capi.cu (defined in particle_step.cu / sort.cu)
 // rhs: FP64 deposit grid (FP64 path); cnt: fixed-point deposit grid (FP32
 // path, kFix counts per particle charge)

@@ -4,7 +4,8 @@ pic_force_balance, against the oracle (oracle.fluid) on the same seeded
 inputs: loaded states (scattered and clustered, so that both the per-lane
 and the warp-summed accumulation run), a stepped state with absorbed
 particles, tabulated cross sections, a batch member, FP64 and FP32; the
-force terms from the oracle's moments; at the full mirror workload
+force terms and the fluid-model predictions (Sec. V) from the oracle's
+moments; at the full mirror workload
 (128 x 512 cells, 1e7 electrons) the partition-of-unity sums."""
 import numpy as np
 import pytest
@@ -206,6 +207,7 @@ def test_full_size_partition_of_unity():
         got = (M[c] * V).sum()
         assert got == pytest.approx(want, rel=1e-9, abs=1e-9 * w * np.abs(s).sum()), c
     assert (M[10] >= 0).all() and M[10].sum() > 0
+    assert (M[11] >= 0).all() and (M[11] <= M[10] * (1 + 1e-12)).all()
 
 
 def test_force_balance_refuses_a_wrong_shape():
@@ -217,3 +219,28 @@ def test_force_balance_refuses_a_wrong_shape():
     with pytest.raises(ValueError):
         sim.force_balance(M, M[:10], 1e-12)
     sim.close()
+
+
+@pytest.mark.parametrize("precision,bkind", [(64, 0), (64, 1), (32, 1)])
+def test_fluid_model_matches_oracle(precision, bkind):
+    """Fluid-Poisson model grids (pic_fluid_model) from the oracle's moments
+    of a hot load (ionising speeds present) and a random node field."""
+    cfg = _cfg(precision, bfield_kind=bkind, b0=0.05, T0_eV=120.0)
+    w = oracle.derived(cfg)["weight"]
+    parts = seed_particles(cfg, n=30_000, seed=71)
+    M = fluid.moments(cfg, *parts[:5], w)
+    assert M[11].sum() > 0
+    er, ez = random_field_node_arrays(cfg, 3e5, seed=72)
+    sim = make_gpu(cfg, seed_particles(cfg, n=100, seed=73), efield=(er, ez))
+    got = sim.fluid_model(M)
+    sim.close()
+    want = fluid.fluid_model(cfg, M, er, ez)
+    assert got.shape == want.shape == (9, cfg["nr"] + 1, cfg["nz"] + 1)
+    tol = 1e-12 if precision == 64 else 1e-5
+    for k, name in enumerate(fluid.FLUID_MODEL):
+        scale = np.abs(want[k]).max()
+        assert scale > 0, name
+        err = np.abs(got[k] - want[k]).max() / scale
+        assert err <= tol, (name, err)
+    # the drift speeds reach the ionising range somewhere
+    assert want[7].max() > 0
