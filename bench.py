@@ -14,6 +14,12 @@ start: snapshots from 64 randomised simulations of the small workload's
 physics on 128 x 512 cells, the U-Net's training throughput (TFLOP/s on the
 BF16 tensor cores; K timed training steps after W warm-up steps), then the
 trained net inside the loop against the previous-potential initial guess.
+``--workload mirror_128x512_1e7_tables`` is the benchmark step with
+tabulated cross sections (synthetic tables of 64 points: elastic,
+ionisation and an energy-dependent anisotropy) instead of the analytic fits.
+``--workload fluid_moments_128x512_1e7`` times the fluid-moment pass
+(pic_moments_accumulate: twelve node moments of the 1e7 electrons after the
+warm-up steps, accumulated on the GPU) in particles/s.
 ``--workload time_to_steady_64sims`` measures the wall time to steady state
 of the 64-simulation scan at up-scaled pressure with a seed source, in the
 batched FP32 form and in the plain FP64 form (one simulation after another,
@@ -45,13 +51,19 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2206_14662_gb300.inputs import scan_configs, seed_particles, workload  # noqa: E402
+from paper_2206_14662_gb300.inputs import (cross_section_tables, scan_configs,  # noqa: E402
+                                           seed_particles, workload)
 
 WORKLOAD = "mirror_128x512_1e7"
 LARGE = "mirror_256x1024_2e8"
 SCAN = "scan_64x256_64sims"
 UNET = "unet_warmstart_128x512"
 STEADY = "time_to_steady_64sims"
+TABLES = "mirror_128x512_1e7_tables"
+MOMENTS = "fluid_moments_128x512_1e7"
+# algorithmic bytes per particle of the moment pass: cell 4 + offsets 8 +
+# velocity 12 read (the node grids stay in L2)
+BYTES_PER_PARTICLE_MOMENTS = 24
 FALLBACK_BF16_TFLOPS = 1900.0
 METRIC = "particle-steps/s (gather+push+MCC+deposit+field solve)"
 # algorithmic bytes per particle-step of the fused particle kernel (FP32):
@@ -196,6 +208,10 @@ def _inputs(args, rank):
     cfg = workload(name, seed=1 + rank, **over)
     if args.particles:
         cfg["n_init"] = args.particles
+    if args.workload == TABLES:
+        E, sel, sio, xi = cross_section_tables(cfg["ion_E_th_eV"])
+        cfg["xs"] = dict(E_eV=E, sigma_el=sel, sigma_io=sio, xi=xi)
+        name = TABLES
     return name, [cfg], [seed_particles(cfg)]
 
 
@@ -220,6 +236,9 @@ def run_ours(args, ws, rank):
     sim = Simulation(cfgs if S > 1 else cfgs[0])
     for k in range(S):
         sim.load_particles(*pinned[k], sim=k)
+        xs = cfgs[k].get("xs")
+        if xs is not None:   # tables stay with the simulation across loads
+            sim.set_cross_sections(xs["E_eV"], xs["sigma_el"], xs["sigma_io"], xs["xi"], sim=k)
     sim.step(args.warmup)
     tune = None
     if args.autotune:
@@ -279,7 +298,7 @@ def run_ours(args, ws, rank):
     kern_ms = prof["particle_ms"] / max(1, prof["particle_launches"])
     per_launch_units = prof_units / max(1, prof["particle_launches"])
     achieved = BYTES_PER_PARTICLE_STEP * per_launch_units / (kern_ms * 1e-3) / 1e9
-    traffic = _traffic_record() if S == 1 else None
+    traffic = _traffic_record() if S == 1 and name != TABLES else None
     cfg = cfgs[0]
     grid = f"{cfg['nr']}x{cfg['nz']}"
     nnodes = (cfg["nr"] + 1) * (cfg["nz"] + 1)
@@ -309,14 +328,17 @@ def run_ours(args, ws, rank):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32 particles / f64 field",
-        "data": "synthetic (seeded volume-uniform 1 eV Maxwellian load)",
+        "data": "synthetic (seeded volume-uniform 1 eV Maxwellian load)" + (
+            "; synthetic 64-point cross-section tables" if name == TABLES else ""),
         "config": config,
         "e2e": None if not args.e2e else {"value": e2e_units * ws / esec, "unit": "particle-steps/s",
                 "h2d_bytes_per_step": int(n0 * 48 / args.steps),
                 "d2h_bytes_per_step": int(S * (nnodes * 8 + 512) / args.steps)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm",
-                     "kernel": "k_particle_step<float>" if S == 1 else "k_particle_step_batch<float>",
+                     "kernel": ("k_particle_step_batch<float>" if S > 1 else
+                                "k_particle_step<float, 1> (tables)" if name == TABLES else
+                                "k_particle_step<float, 0>"),
                      "achieved": achieved,
                      "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (traffic["dram_bytes_per_particle"] * per_launch_units) if traffic else None,
@@ -345,6 +367,123 @@ def run_ours(args, ws, rank):
             k = int(np.argmax([len(p[0]) for p in parts]))
             out["cpu_baseline"] = cpu_baseline(cfgs[k], parts[k], steps=4, name=f"{name} (simulation {k})")
     return out
+
+
+def run_moments(args, ws, rank):
+    """The fluid-moment pass (Sec. IV.A): after the warm-up steps of the
+    benchmark workload, K calls of pic_moments_accumulate over the resident
+    particle store, each adding 1/K of the twelve node moments into one
+    device array.  e2e: the exported state loaded from pinned host memory
+    and K calls of pic_moments, each returning the grids to the host."""
+    import torch
+    from paper_2206_14662_gb300._capi import MOMENTS as NMOM
+    from paper_2206_14662_gb300._capi import Simulation
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg = workload(WORKLOAD, seed=1 + rank)
+    if args.particles:
+        cfg["n_init"] = args.particles
+    parts = seed_particles(cfg)
+    shape = (NMOM, cfg["nr"] + 1, cfg["nz"] + 1)
+    sim = Simulation(cfg)
+    sim.load_particles(*parts)
+    sim.step(args.warmup)
+    n_live = int(sim.diagnostics()["n_particles"])
+    acc = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        sim.moments_accumulate(acc, 1.0)
+    acc.zero_()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks()
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.moments_accumulate(acc, 1.0 / args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    units = n_live * args.steps
+
+    # end to end: the current state, in the simulation's cell order (export
+    # returns uid order), from pinned host memory, then K calls returning
+    # the moments to the host
+    g = sim.export_particles()
+    hr = (cfg["r_out"] - cfg["r_in"]) / cfg["nr"]
+    hz = (cfg["z_max"] - cfg["z_min"]) / cfg["nz"]
+    ir = np.clip(((g["r"] - cfg["r_in"]) / hr).astype(np.int64), 0, cfg["nr"] - 1)
+    iz = np.clip(((g["z"] - cfg["z_min"]) / hz).astype(np.int64), 0, cfg["nz"] - 1)
+    order = np.argsort(ir * (cfg["nz"] + 1) + iz, kind="stable")
+    g = {k: v[order] for k, v in g.items()}
+    host = [torch.from_numpy(np.ascontiguousarray(g[k])).pin_memory()
+            for k in ("r", "z", "vr", "vt", "vz")]
+    host.append(torch.from_numpy(np.ascontiguousarray(g["uid"]).view(np.int64)).pin_memory())
+    n_e2e = len(g["uid"])
+    e2e_units = 0
+    esec = 0.0
+    if args.e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.load_particles(*host)
+        for _ in range(args.steps):
+            sim.moments()
+            e2e_units += n_e2e
+        esec = time.perf_counter() - t0
+    sim.close()
+
+    if ws > 1:
+        sec, units, esec, e2e_units = combine_ranks(ms / 1e3, units, esec, e2e_units, "cuda")
+    else:
+        sec = ms / 1e3
+    if rank != 0:
+        return None
+    peak, src = _peak_hbm()
+    kern_s = sec / args.steps
+    achieved = BYTES_PER_PARTICLE_MOMENTS * n_live / kern_s / 1e9
+    nnodes = shape[1] * shape[2]
+    out = {
+        "metric": "particles/s (fluid moments: n, n u, n <v v>, n <nu_d>, n <nu_io> on the nodes)",
+        "value": units / sec, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 particles / f64 moments",
+        "data": "synthetic (the benchmark workload after the warm-up steps)",
+        "config": {"workload": MOMENTS if not args.particles else f"{MOMENTS} (particles={n_live})",
+                   "particles": n_live, "grid": f"{cfg['nr']}x{cfg['nz']}",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": f"inputs larger than L2 (particle store read {n_live * 24 / 1e9:.2f} GB per pass)"},
+        "e2e": None if not args.e2e else {
+            "value": e2e_units / esec, "unit": "particles/s",
+            "h2d_bytes_per_step": int(n_e2e * 48 / args.steps),
+            "d2h_bytes_per_step": int(NMOM * nnodes * 8)},
+        "gpu_launches": int(args.steps),
+        "roofline": {"bound": "hbm", "kernel": "k_moments<float>", "achieved": achieved,
+                     "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel_ms_per_launch": kern_s * 1e3,
+                     "bytes_per_particle": BYTES_PER_PARTICLE_MOMENTS},
+        "clocks": clk,
+    }
+    if args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_moments(cfg, g, n_sample=min(n_e2e, 1_000_000))
+    return out
+
+
+def cpu_baseline_moments(cfg, g, n_sample):
+    """The oracle's moments (numpy, one thread) of the first n_sample
+    particles of the state."""
+    import oracle
+    from oracle import fluid
+    oracle.build()
+    w = oracle.derived(cfg)["weight"]
+    t0 = time.perf_counter()
+    fluid.moments(cfg, *(g[k][:n_sample] for k in ("r", "z", "vr", "vt", "vz")), w)
+    sec = time.perf_counter() - t0
+    return {"value": n_sample / sec, "unit": "particles/s", "cores": 1, "kind": "oracle",
+            "sample": f"moments of {n_sample} particles of {MOMENTS}", "seconds": sec}
 
 
 def run_unet(args, ws, rank):
@@ -519,11 +658,17 @@ def run_reference(args, ws, rank):
         return None
     if args.workload == UNET:
         return run_reference_unet(args, ws)
+    if args.workload == MOMENTS:
+        return run_reference_moments(args, ws)
     import oracle
     oracle.build()
     name = args.workload
     # the scan: its largest simulation (the oracle runs one simulation)
-    cfg = workload(name) if name in (WORKLOAD, LARGE) else scan_configs()[-1]
+    cfg = workload(name) if name in (WORKLOAD, LARGE) else (
+        workload(WORKLOAD) if name == TABLES else scan_configs()[-1])
+    if name == TABLES:
+        E, sel, sio, xi = cross_section_tables(cfg["ion_E_th_eV"])
+        cfg["xs"] = dict(E_eV=E, sigma_el=sel, sigma_io=sio, xi=xi)
     n = 20_000
     parts = seed_particles(cfg, n=n)
     o = oracle.OracleSim(cfg, *parts)
@@ -545,6 +690,35 @@ def run_reference(args, ws, rank):
             "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"{n} particles of {name} per step, full grid and field solve"},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def run_reference_moments(args, ws):
+    """The oracle's moments (numpy) on a bounded sample: each step the
+    moments of 200 000 seeded particles of the benchmark workload."""
+    import oracle
+    from oracle import fluid
+    oracle.build()
+    cfg = workload(WORKLOAD)
+    n = 200_000
+    r, z, vr, vt, vz, _ = seed_particles(cfg, n=n)
+    w = oracle.derived(cfg)["weight"]
+    steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fluid.moments(cfg, r, z, vr, vt, vz, w)
+    sec = time.perf_counter() - t0
+    v = n * steps / sec
+    return {"impl": "reference", "metric": "particles/s (fluid moments: n, n u, n <v v>, "
+            "n <nu_d>, n <nu_io> on the nodes)", "value": v, "unit": "particles/s",
+            "n_gpus": ws, "steps": steps, "warmup": 0, "ms_per_step": sec * 1e3 / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": MOMENTS, "particles": n,
+                                            "grid": f"{cfg['nr']}x{cfg['nz']}",
+                                            "parallelism": "cpu oracle, rank 0 only"},
+            "cpu_baseline": {"value": v, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                             "sample": f"moments of {n} particles of {MOMENTS} per step"},
+            "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
@@ -581,7 +755,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
-    ap.add_argument("--workload", choices=[WORKLOAD, LARGE, SCAN, UNET, STEADY], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, LARGE, SCAN, UNET, STEADY, TABLES, MOMENTS],
+                    default=WORKLOAD)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the workload's sort period and the default kernel grid")
     ap.add_argument("--warm-start", type=int, choices=[0, 1], default=None,
@@ -607,6 +782,8 @@ def main():
         out = run_unet(args, ws, rank)
     elif args.workload == STEADY:
         out = run_steady(args, ws, rank)
+    elif args.workload == MOMENTS:
+        out = run_moments(args, ws, rank)
     else:
         out = run_ours(args, ws, rank)
     if out is not None:

@@ -255,6 +255,16 @@ int pic_set_efield(pic_handle* h, int sim, const double* er,
 #define PIC_MOMENTS 12
 int pic_moments(pic_handle* h, int sim, double* out);
 
+/* Adds scale x the moments of pic_moments (same layout and definitions) to
+ * acc, a caller-owned DEVICE array of PIC_MOMENTS x (nr + 1) (nz + 1) FP64
+ * (zeroed by the caller before the first call): the average over several
+ * steps (Sec. IV.A averages over several cyclotron periods) accumulates on
+ * the GPU with scale = 1 / (number of snapshots).  Asynchronous on the
+ * handle's stream, no allocation, no host copy; acc must not be in use by
+ * other work meanwhile.  PIC_EINVAL on a bad handle or index, NULL acc or a
+ * non-finite scale; launch errors as PIC_ECUDA. */
+int pic_moments_accumulate(pic_handle* h, int sim, double* acc, double scale);
+
 /* The terms of the electron fluid's force balance (Sec. IV.A) at every
  * node from moments in the layout of pic_moments (host arrays, read only:
  * one call's moments, or averages over several steps): out (host) holds

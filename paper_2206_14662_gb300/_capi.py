@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.pic_set_efield.argtypes = [vp, ctypes.c_int, vp, vp]
         L.pic_set_cross_sections.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.pic_moments.argtypes = [vp, ctypes.c_int, vp]
+        L.pic_moments_accumulate.argtypes = [vp, ctypes.c_int, vp, c_d]
         L.pic_force_balance.argtypes = [vp, ctypes.c_int, vp, vp, c_d, vp]
         L.pic_fluid_model.argtypes = [vp, ctypes.c_int, vp, vp]
         L.pic_get_grid.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
@@ -109,7 +110,7 @@ def lib() -> ctypes.CDLL:
         L.pic_free.restype = None
         for name in ("pic_init", "pic_load_particles", "pic_step", "pic_diagnostics",
                      "pic_export_particles", "pic_set_efield", "pic_set_cross_sections",
-                     "pic_moments", "pic_force_balance", "pic_fluid_model",
+                     "pic_moments", "pic_moments_accumulate", "pic_force_balance", "pic_fluid_model",
                      "pic_get_grid", "pic_solve_field",
                      "pic_checkpoint", "pic_restore", "pic_profile"):
             getattr(L, name).restype = ctypes.c_int
@@ -270,6 +271,17 @@ class Simulation:
         out = np.zeros((MOMENTS, self.cfg["nr"] + 1, self.cfg["nz"] + 1))
         _check(lib().pic_moments(self.h, sim, out.ctypes.data_as(ctypes.c_void_p)), "pic_moments")
         return out
+
+    def moments_accumulate(self, acc, scale: float = 1.0, sim: int = 0):
+        """Add scale x the moments to acc (pic_moments_accumulate), a CUDA
+        float64 tensor of shape (12, nr + 1, nz + 1), asynchronously on the
+        simulation's stream."""
+        shape = (MOMENTS, self.cfg["nr"] + 1, self.cfg["nz"] + 1)
+        if not (getattr(acc, "is_cuda", False) and str(acc.dtype) == "torch.float64"
+                and acc.is_contiguous() and tuple(acc.shape) == shape):
+            raise ValueError(f"acc must be a contiguous CUDA float64 tensor of shape {shape}")
+        _check(lib().pic_moments_accumulate(self.h, sim, ctypes.c_void_p(acc.data_ptr()),
+                                            float(scale)), "pic_moments_accumulate")
 
     def force_balance(self, moments, moments_prev=None, dt_prev: float = 0.0, sim: int = 0):
         """Force-balance terms (pic_force_balance) from moments of shape

@@ -1190,25 +1190,39 @@ void drop_tmp(pic_handle* h, void* p) {
 static_assert(kMoments == PIC_MOMENTS, "moment count of the ABI");
 static_assert(kFluidModel == PIC_FLUID_MODEL, "fluid-model grid count of the ABI");
 
+namespace {
+void moments_into(pic_handle* h, int sim, double scale, double* M) {
+  const ForceParams F = force_params(h, sim, 0.0);
+  if (h->prec == 32)
+    launch_moments<float>(sim_soa<float>(h, sim, h->cur), h->st + sim, h->Pf[sim], F, scale, M,
+                          h->sims[sim].capacity, h->stream);
+  else
+    launch_moments<double>(sim_soa<double>(h, sim, h->cur), h->st + sim, h->Pd[sim], F, scale,
+                           M, h->sims[sim].capacity, h->stream);
+}
+}  // namespace
+
 int pic_moments(pic_handle* h, int sim, double* out) {
   if (!h || sim < 0 || sim >= h->nsim || !out) return PIC_EINVAL;
   if (h->sticky) return h->sticky;
   const size_t bytes = (size_t)kMoments * h->nnodes * sizeof(double);
   double* M = (double*)tmp_alloc(h, bytes);
   if (!M) return PIC_ENOMEM;
-  const ForceParams F = force_params(h, sim, 0.0);
-  if (h->prec == 32)
-    launch_moments<float>(sim_soa<float>(h, sim, h->cur), h->st + sim, h->Pf[sim], F, M,
-                          h->sims[sim].capacity, h->stream);
-  else
-    launch_moments<double>(sim_soa<double>(h, sim, h->cur), h->st + sim, h->Pd[sim], F, M,
-                           h->sims[sim].capacity, h->stream);
   int rc = PIC_OK;
-  if (cudaMemcpyAsync(out, M, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-      cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+  if (cudaMemsetAsync(M, 0, bytes, h->stream) != cudaSuccess) rc = PIC_ECUDA;
+  if (!rc) moments_into(h, sim, 1.0, M);
+  if (!rc && (cudaMemcpyAsync(out, M, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+              cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess))
     rc = PIC_ECUDA;
   drop_tmp(h, M);
   return rc;
+}
+
+int pic_moments_accumulate(pic_handle* h, int sim, double* acc, double scale) {
+  if (!h || sim < 0 || sim >= h->nsim || !acc || !std::isfinite(scale)) return PIC_EINVAL;
+  if (h->sticky) return h->sticky;
+  moments_into(h, sim, scale, acc);
+  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
 int pic_force_balance(pic_handle* h, int sim, const double* moments, const double* moments_prev,

@@ -15,11 +15,12 @@ struct ForceParams {
   double weight;                // electrons per macro-electron
   double dt_prev;               // time since the previous moments (F_a), 0: none
 };
-// moments of simulation `sim`'s particles (its views s, st, P) on the
-// nodes, scaled to per-volume: kMoments x nnodes FP64 at M
+// adds scale x the moments of simulation `sim`'s particles (its views s,
+// st, P) on the nodes, per volume, to the kMoments x nnodes FP64 grids at M
 template <typename Real>
 void launch_moments(const Soa<Real>& s, const DevState* st, const PushParams<Real>& P,
-                    const ForceParams& F, double* M, long long max_slots, cudaStream_t stream);
+                    const ForceParams& F, double scale, double* M, long long max_slots,
+                    cudaStream_t stream);
 // the 7 x 3 force-term grids (F_E, F_B, F_i, F_p, F_d, F_a, sum; r, theta,
 // z) from moments M (and Mprev for F_a, or null) and the node field
 template <typename Real>

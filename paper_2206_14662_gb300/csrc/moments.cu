@@ -12,9 +12,10 @@
 // |v| the ionisation frequency (the collision path's cross sections:
 // analytic or tabulated, ionisation only above its threshold).  So M_0 =
 // n, M_1..3 = n u, M_4..9 = n <v v>, M_10 = n <nu_d>, M_11 = n <nu_io>.
-// The weights Lambda_i are the deposit's bilinear ones; accumulation is in
-// FP64 global atomics, a warp whose particles share one cell adding its
-// sums once.
+// The weights Lambda_i are the deposit's bilinear ones.  Products and
+// short sums are in the particles' precision, running sums and the grids
+// in FP64 (global atomics, each already multiplied by w / V_i, so a call
+// can add a scaled set into a running average).
 //
 // Force terms at each node (per unit volume, components r, theta, z), with
 // u = M_1..3 / n, P = m (n <v v> - n u u), q = -e, m = m_e:
@@ -47,83 +48,25 @@
 
 namespace pic {
 
-constexpr int kMomThreads = 256;
 
-// elastic and ionisation frequencies at speed^2 v2
-template <typename Real>
-__device__ __forceinline__ void nu_parts(const PushParams<Real>& P, double v2, double& nu_el,
-                                         double& nu_io) {
-  const double speed = sqrt(v2);
-  const double Ek = 0.5 * kMe * v2;
+// elastic and ionisation frequencies at speed^2 v2, in arithmetic type T
+template <typename Real, typename T>
+__device__ __forceinline__ void nu_parts(const PushParams<Real>& P, T v2, T& nu_el, T& nu_io) {
+  const T speed = sqrt(v2);
+  const T Ek = (T)(0.5 * kMe) * v2;
   if (P.xs_n > 0) {
     const Xs3<Real> x = xs_eval<Real>(P.xs_n, P.xs_E, P.xs_nel, P.xs_nio, P.xs_xi, P.xi, (Real)Ek);
-    nu_el = (double)x.nel * speed;
-    nu_io = Ek > (double)P.e_th ? (double)x.nio * speed : 0.0;
+    nu_el = (T)x.nel * speed;
+    nu_io = Ek > (T)P.e_th ? (T)x.nio * speed : T(0);
     return;
   }
-  double sio = 0.0;
-  if (Ek > (double)P.e_th) {
-    const double qq = (Ek - (double)P.e_th) * (double)P.e_span_inv;
-    sio = (double)P.sig_pk * 2.0 * qq / (1.0 + qq * qq);
+  T sio = T(0);
+  if (Ek > (T)P.e_th) {
+    const T qq = (Ek - (T)P.e_th) * (T)P.e_span_inv;
+    sio = (T)P.sig_pk * T(2) * qq / (T(1) + qq * qq);
   }
-  nu_el = (double)P.nsig_el * speed;
-  nu_io = (double)P.n_gas * sio * speed;
-}
-
-template <typename Real>
-__global__ void __launch_bounds__(kMomThreads)
-k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, double* M, int nnodes) {
-  const long long n = st->n_slots;
-  const int lane = threadIdx.x & 31, nzp = P.nz + 1;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
-       base += (long long)gridDim.x * blockDim.x) {
-    const long long p = base + threadIdx.x;
-    const int cell = p < n ? s.cell[p] : -1;
-    double c[4] = {0.0, 0.0, 0.0, 0.0};
-    double g[kMoments];
-    int n00 = 0;
-    if (cell >= 0) {
-      const int ir = cell >> 16, iz = cell & 0xFFFF;
-      n00 = ir * nzp + iz;
-      const double fr = (double)s.offr[p], fz = (double)s.offz[p];
-      c[0] = (1.0 - fr) * (1.0 - fz);
-      c[1] = fr * (1.0 - fz);
-      c[2] = (1.0 - fr) * fz;
-      c[3] = fr * fz;
-      const double vr = (double)s.vr[p], vt = (double)s.vt[p], vz = (double)s.vz[p];
-      g[0] = 1.0; g[1] = vr; g[2] = vt; g[3] = vz;
-      g[4] = vr * vr; g[5] = vr * vt; g[6] = vr * vz;
-      g[7] = vt * vt; g[8] = vt * vz; g[9] = vz * vz;
-      double nel, nio;
-      nu_parts<Real>(P, vr * vr + vt * vt + vz * vz, nel, nio);
-      g[10] = nel + nio;
-      g[11] = nio;
-    } else {
-#pragma unroll
-      for (int k = 0; k < kMoments; ++k) g[k] = 0.0;
-    }
-    const int off[4] = {0, nzp, 1, nzp + 1};
-    // one cell for the whole warp (sorted stores): sum in the warp first
-    int same = 0;
-    __match_all_sync(0xffffffffu, cell, &same);
-    if (same && cell >= 0) {
-#pragma unroll
-      for (int k = 0; k < kMoments; ++k) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          double v = g[k] * c[j];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) atomicAdd(M + (size_t)k * nnodes + n00 + off[j], v);
-        }
-      }
-    } else if (cell >= 0) {
-#pragma unroll
-      for (int k = 0; k < kMoments; ++k)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) atomicAdd(M + (size_t)k * nnodes + n00 + off[j], g[k] * c[j]);
-    }
-  }
+  nu_el = (T)P.nsig_el * speed;
+  nu_io = (T)P.n_gas * sio * speed;
 }
 
 // hat-function volume of node (i, j): 2 pi R_i Z_j
@@ -136,11 +79,108 @@ __device__ __forceinline__ double node_volume(const ForceParams& F, int i, int j
   return 2.0 * kPi * R * Z;
 }
 
-__global__ void k_moment_scale(double* M, ForceParams F) {
-  const int nnodes = (F.nr + 1) * (F.nz + 1);
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nnodes; o += gridDim.x * blockDim.x) {
-    const double s = F.weight / node_volume(F, o / (F.nz + 1), o % (F.nz + 1));
-    for (int k = 0; k < kMoments; ++k) M[(size_t)k * nnodes + o] *= s;
+// Moment pass.  A warp takes chunks of kMomIters x 32 consecutive slots;
+// per 32-slot row each lane writes its particle's 48 products
+// g_k Lambda_j (moment k, corner j) to a padded shared-memory row, then
+// lane l sums columns l and l + 32 down the rows (in the particle's
+// precision), carrying an FP64 running sum while the rows' cell stays the
+// same and adding it, times w / V of the node, to M with one atomic per
+// column when the cell changes.  In a cell-sorted store a cell change is
+// rare, so the atomics per particle are few; any order stays correct.
+constexpr int kMomCols = 4 * kMoments;   // column 4 k + j
+constexpr int kMomRow = kMomCols + 1;    // padded: rows start in different banks
+constexpr int kMomIters = 32;
+template <typename Real>
+struct MomShape {
+  static constexpr int warps = sizeof(Real) == 4 ? 4 : 2;   // 25 KB of rows per block
+};
+
+// w / V of node (i, j) in the particles' precision (an FP64 division costs
+// dozens of FP64 operations; FP32 simulations are held to 1e-5 anyway)
+template <typename Real>
+__device__ __forceinline__ double weight_per_volume(const ForceParams& F, double ws, int i, int j) {
+  if (sizeof(Real) == 8) return ws / node_volume(F, i, j);
+  const float hr = (float)F.hr, hz = (float)F.hz, r_in = (float)F.r_in;
+  const float R = i == 0 ? hr * (0.5f * r_in + hr / 6.0f)
+                         : (i == F.nr ? hr * (0.5f * (r_in + F.nr * hr) - hr / 6.0f)
+                                      : (r_in + i * hr) * hr);
+  const float Z = (j == 0 || j == F.nz) ? 0.5f * hz : hz;
+  return (double)((float)ws / ((float)(2.0 * kPi) * R * Z));
+}
+
+template <typename Real>
+__device__ __forceinline__ void moment_flush(const ForceParams& F, double ws, int cell, int col,
+                                             double v, double* M, int nzp, int nnodes) {
+  const int k = col >> 2, j = col & 3;
+  const int i = (cell >> 16) + (j & 1), jz = (cell & 0xFFFF) + (j >> 1);
+  atomicAdd(M + (size_t)k * nnodes + i * nzp + jz, v * weight_per_volume<Real>(F, ws, i, jz));
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(MomShape<Real>::warps * 32)
+k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, double scale,
+          double* M) {
+  constexpr int W = MomShape<Real>::warps;
+  __shared__ Real rows[W][32][kMomRow];
+  __shared__ int rcell[W][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long n = st->n_slots;
+  const int nzp = F.nz + 1, nnodes = (F.nr + 1) * nzp;
+  const double ws = scale * F.weight;
+  const long long chunk = 32LL * kMomIters;
+  const long long nchunks = (n + chunk - 1) / chunk;
+  const int col0 = lane, col1 = lane + 32;
+  const bool has1 = col1 < kMomCols;
+  Real(*row)[kMomRow] = rows[wib];
+  int* rc = rcell[wib];
+  for (long long ch = (long long)blockIdx.x * W + wib; ch < nchunks;
+       ch += (long long)gridDim.x * W) {
+    int run_cell = -1;
+    double run0 = 0.0, run1 = 0.0;
+    for (int it = 0; it < kMomIters; ++it) {
+      const long long p = ch * chunk + (long long)it * 32 + lane;
+      const int cell = p < n ? s.cell[p] : -1;
+      if (cell >= 0) {
+        const Real fr = s.offr[p], fz = s.offz[p];
+        const Real c[4] = {(Real(1) - fr) * (Real(1) - fz), fr * (Real(1) - fz),
+                           (Real(1) - fr) * fz, fr * fz};
+        const Real vr = s.vr[p], vt = s.vt[p], vz = s.vz[p];
+        Real nel, nio;
+        nu_parts<Real, Real>(P, vr * vr + vt * vt + vz * vz, nel, nio);
+        const Real g[kMoments] = {Real(1), vr, vt, vz, vr * vr, vr * vt, vr * vz,
+                                  vt * vt, vt * vz, vz * vz, nel + nio, nio};
+#pragma unroll
+        for (int k = 0; k < kMoments; ++k)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) row[lane][4 * k + j] = g[k] * c[j];
+      }
+      rc[lane] = cell;
+      __syncwarp();
+      Real part0 = Real(0), part1 = Real(0);
+      for (int r = 0; r < 32; ++r) {
+        const int cr = rc[r];   // the same for every lane: uniform branches
+        if (cr < 0) continue;
+        if (cr != run_cell) {
+          if (run_cell >= 0) {
+            moment_flush<Real>(F, ws, run_cell, col0, run0 + (double)part0, M, nzp, nnodes);
+            if (has1)
+              moment_flush<Real>(F, ws, run_cell, col1, run1 + (double)part1, M, nzp, nnodes);
+          }
+          run_cell = cr;
+          run0 = run1 = 0.0;
+          part0 = part1 = Real(0);
+        }
+        part0 += row[r][col0];
+        if (has1) part1 += row[r][col1];
+      }
+      run0 += (double)part0;
+      run1 += (double)part1;
+      __syncwarp();   // the rows are rewritten by the next iteration
+    }
+    if (run_cell >= 0) {
+      moment_flush<Real>(F, ws, run_cell, col0, run0, M, nzp, nnodes);
+      if (has1) moment_flush<Real>(F, ws, run_cell, col1, run1, M, nzp, nnodes);
+    }
   }
 }
 
@@ -281,7 +321,7 @@ __global__ void k_fluid_model(const double* __restrict__ M,
     const double B2 = Br * Br + Bz * Bz;
     const double vd = B2 > 0 ? fabs(Ez * Br - Er * Bz) / B2 : 0.0;
     double dnel, dnio;
-    nu_parts<Real>(P, vd * vd, dnel, dnio);
+    nu_parts<Real, double>(P, vd * vd, dnel, dnio);
     double g[kFluidModel];
     g[0] = Bz != 0 ? -Er / Bz : 0.0;
     g[1] = nud;
@@ -306,13 +346,13 @@ void launch_fluid_model(const double* M, const void* efield, const ForceParams& 
 
 template <typename Real>
 void launch_moments(const Soa<Real>& s, const DevState* st, const PushParams<Real>& P,
-                    const ForceParams& F, double* M, long long max_slots, cudaStream_t stream) {
-  const int nnodes = (F.nr + 1) * (F.nz + 1);
-  cudaMemsetAsync(M, 0, (size_t)kMoments * nnodes * sizeof(double), stream);
-  const long long blocks = std::min<long long>((max_slots + kMomThreads - 1) / kMomThreads, 152 * 16);
-  k_moments<Real><<<(int)std::max<long long>(blocks, 1), kMomThreads, 0, stream>>>(s, st, P, M,
-                                                                                    nnodes);
-  k_moment_scale<<<std::min(152 * 4, (nnodes + 255) / 256), 256, 0, stream>>>(M, F);
+                    const ForceParams& F, double scale, double* M, long long max_slots,
+                    cudaStream_t stream) {
+  constexpr int W = MomShape<Real>::warps;
+  const long long chunks = (max_slots + 32LL * kMomIters - 1) / (32LL * kMomIters);
+  const long long blocks = std::min<long long>((chunks + W - 1) / W, 152 * 8);
+  k_moments<Real><<<(int)std::max<long long>(blocks, 1), W * 32, 0, stream>>>(s, st, P, F, scale,
+                                                                             M);
 }
 
 template <typename Real>
@@ -324,10 +364,10 @@ void launch_force_terms(const double* M, const double* Mprev, const void* efield
 }
 
 template void launch_moments<float>(const Soa<float>&, const DevState*, const PushParams<float>&,
-                                    const ForceParams&, double*, long long, cudaStream_t);
+                                    const ForceParams&, double, double*, long long, cudaStream_t);
 template void launch_moments<double>(const Soa<double>&, const DevState*,
-                                     const PushParams<double>&, const ForceParams&, double*,
-                                     long long, cudaStream_t);
+                                     const PushParams<double>&, const ForceParams&, double,
+                                     double*, long long, cudaStream_t);
 template void launch_force_terms<float>(const double*, const double*, const void*,
                                         const ForceParams&, double*, cudaStream_t);
 template void launch_force_terms<double>(const double*, const double*, const void*,

@@ -188,7 +188,8 @@ def test_force_balance_argument_checks():
 
 def test_full_size_partition_of_unity():
     """Mirror workload, 128 x 512 cells, 1e7 electrons, FP32, three solved
-    steps: sum_i V_i M_c(i) = w sum_p g_c(v_p) over the live particles."""
+    steps: sum_i V_i M_c(i) = w sum_p g_c(v_p) over the live particles, to
+    the FP32 arithmetic of the FP32 path."""
     cfg = workload("mirror_128x512_1e7")
     parts = seed_particles(cfg)
     sim = make_gpu(cfg, parts)
@@ -205,7 +206,8 @@ def test_full_size_partition_of_unity():
     for c, s in enumerate(sums):
         want = w * s.sum()
         got = (M[c] * V).sum()
-        assert got == pytest.approx(want, rel=1e-9, abs=1e-9 * w * np.abs(s).sum()), c
+        # FP32 simulation: products, short sums and w / V in FP32
+        assert got == pytest.approx(want, rel=1e-6, abs=1e-6 * w * np.abs(s).sum()), c
     assert (M[10] >= 0).all() and M[10].sum() > 0
     assert (M[11] >= 0).all() and (M[11] <= M[10] * (1 + 1e-12)).all()
 
@@ -244,3 +246,33 @@ def test_fluid_model_matches_oracle(precision, bkind):
         assert err <= tol, (name, err)
     # the drift speeds reach the ionising range somewhere
     assert want[7].max() > 0
+
+
+def test_accumulated_moments_average_snapshots():
+    """pic_moments_accumulate adds scale x the moments into a device array:
+    halves of a loaded state's moments sum to the oracle's; a time average
+    of three snapshots equals the mean of three pic_moments calls."""
+    import torch
+    cfg = _cfg(64, fixed_efield=0, sort_every=2)
+    parts = seed_particles(cfg, n=15_000, seed=81)
+    sim = make_gpu(cfg, parts)
+    shape = (fluid.MOMENTS, cfg["nr"] + 1, cfg["nz"] + 1)
+    acc = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    sim.moments_accumulate(acc, 0.5)
+    sim.moments_accumulate(acc, 0.5)
+    got = acc.cpu().numpy()
+    want = fluid.moments(cfg, *parts[:5], oracle.derived(cfg)["weight"])
+    _compare_moments(got, want, MOM_TOL[64])
+    acc.zero_()
+    snaps = []
+    for _ in range(3):
+        sim.step(3)
+        sim.moments_accumulate(acc, 1.0 / 3.0)
+        snaps.append(sim.moments())
+    avg = acc.cpu().numpy()
+    _compare_moments(avg, sum(snaps) / 3.0, 1e-13)
+    with pytest.raises(ValueError):
+        sim.moments_accumulate(acc.float(), 1.0)
+    with pytest.raises(ValueError):
+        sim.moments_accumulate(acc.cpu(), 1.0)
+    sim.close()
