@@ -76,7 +76,7 @@ class _Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("T0_eV", ctypes.c_double),
         ("xs_n", ctypes.c_int32), ("xs_E_eV", ctypes.c_void_p),
         ("xs_sigma_el", ctypes.c_void_p), ("xs_sigma_io", ctypes.c_void_p),
-        ("xs_xi", ctypes.c_void_p),
+        ("xs_xi", ctypes.c_void_p), ("e_per_particle", ctypes.c_int32),
     ]
 
 
@@ -385,6 +385,11 @@ class OracleSim:
     Particles are kept sorted by uid; children are appended (their uids are
     above every existing uid, so the order is kept).  Step n: particle step
     with E^n, removal of absorbed particles, then field solve for E^{n+1}.
+
+    With cfg["bspline_degree"] = n >= 1 the field is the weighted B-spline
+    field of degree n (oracle.bspline): particles deposit with its basis
+    and are pushed with its exact gradient at their position; self.coef
+    holds its coefficients (self.phi, self.er, self.ez are then None).
     """
 
     def __init__(self, cfg: dict, r, z, vr, vt, vz, uid, efield_nodes=None,
@@ -405,6 +410,17 @@ class OracleSim:
         self.ke_source = 0.0  # kinetic energy brought in by the seed source, J
         self.src_acc = 0.0    # fractional seed-source count carried between steps
         self.solve_field = solve_field
+        self.spline = None
+        if self.cfg.get("bspline_degree", 0) > 0:
+            from .bspline import SplineField
+            self.spline = SplineField(self.cfg)
+            self.P.e_per_particle = 1
+            self.qw = -QE * derived(self.cfg)["weight"]
+            self.b = self.spline.deposit(self.r, self.z, self.qw)
+            self.coef = self.spline.solve(self.b)
+            self.phi = self.er = self.ez = None
+            self.ke0 = self.kinetic_energy()
+            return
         self.b = deposit(self.cfg, self.r, self.z)
         if efield_nodes is not None:
             self.er, self.ez = (np.array(efield_nodes[0], dtype=np.float64),
@@ -436,9 +452,14 @@ class OracleSim:
         cu = np.zeros(cap, dtype=np.uint64)
         b = np.zeros((self.cfg["nr"] + 1) * (self.cfg["nz"] + 1))
         tally = np.zeros(T_COUNT)
+        if self.spline is not None:   # E at each particle from the spline field
+            er, ez = self.spline.efield(self.coef, self.r, self.z)
+            er, ez = np.ascontiguousarray(er), np.ascontiguousarray(ez)
+        else:
+            er, ez = self.er, self.ez
         nc = lib().or_step(ctypes.byref(self.P), n, _ptr(self.r), _ptr(self.z), _ptr(self.vr),
                            _ptr(self.vt), _ptr(self.vz), _ptr(self.uid), _ptr(event),
-                           _ptr(margin), _ptr(self.er), _ptr(self.ez),
+                           _ptr(margin), _ptr(er), _ptr(ez),
                            self.step_index & 0xFFFFFFFF, self.uid_next, cap,
                            _ptr(ch[0]), _ptr(ch[1]), _ptr(ch[2]), _ptr(ch[3]), _ptr(ch[4]),
                            _ptr(cu), _ptr(b), _ptr(tally))
@@ -472,6 +493,13 @@ class OracleSim:
                                                           _ptr(new[3]), _ptr(new[4]))
         self.step_index += 1
         self.tally += tally
+        if self.spline is not None:
+            # every particle after the step (survivors, children, source)
+            # deposits with the spline basis
+            self.b = self.spline.deposit(self.r, self.z, self.qw)
+            if self.solve_field:
+                self.coef = self.spline.solve(self.b)
+            return StepResult(int(nc), event, margin, self.b, tally)
         self.b = b
         if self.solve_field:
             self.phi = poisson_solve(self.cfg, b)

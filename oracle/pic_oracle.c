@@ -71,6 +71,9 @@ typedef struct {
   const double* xs_sigma_el;        /* m^2 */
   const double* xs_sigma_io;        /* m^2 */
   const double* xs_xi;              /* NULL: the constant xi */
+  /* 1: or_step's er/ez hold E at each particle (length n, e.g. the exact
+   * gradient of a B-spline field) instead of node grids */
+  int32_t e_per_particle;
 } or_params;
 
 /* tally slots (accumulated, doubles) */
@@ -317,7 +320,8 @@ void or_deposit(const or_params* P, int64_t n, const double* r,
  * rank of the parent among this step's ionising parents (array order is uid
  * order).  margin[p] is the smallest distance of a discrete decision from
  * its threshold: walls in cells, collision-type tests relative to nu_max.
- * The surviving particles and the children are deposited into b.
+ * The surviving particles and the children are deposited into b.  er, ez
+ * are node grids, or E at each particle when P->e_per_particle is set.
  * Returns the number of children, or -1 if child_cap was too small. */
 int64_t or_step(const or_params* P, int64_t n, double* r, double* z,
                 double* vr, double* vt, double* vz, const uint64_t* uid,
@@ -339,7 +343,12 @@ int64_t or_step(const or_params* P, int64_t n, double* r, double* z,
     double r0 = r[p], z0 = z[p];
     double v0[3] = {vr[p], vt[p], vz[p]};
     double Er, Ez, Br, Bz;
-    or_gather(P, er, ez, r0, z0, &Er, &Ez);
+    if (P->e_per_particle) {
+      Er = er[p];
+      Ez = ez[p];
+    } else {
+      or_gather(P, er, ez, r0, z0, &Er, &Ez);
+    }
     or_bfield(P, r0, z0, &Br, &Bz);
 
     /* Boris: half kick, rotation about B, half kick; components (r,theta,z) */
