@@ -482,6 +482,69 @@ int pic_autotune(pic_handle* h, int64_t steps_per_trial, pic_tune_result* out);
  * sticky error (synchronises). */
 int pic_field_images(pic_handle* h, float* rho, float* phi_rho);
 
+/* ------------------------------------------------------------------
+ * Weighted B-spline field of degree n (Sec. II.A: finite elements on
+ * weighted B-splines of any order, with the Dirichlet electrodes carried
+ * by a weight function on a rectangular grid), with particle shapes from
+ * the same basis.  Uniform B-splines b_i of degree n on knots extending n
+ * cells past each end: mr = nr + n functions in r, mz = nz + n in z; the
+ * coaxial walls carry the weight w(r) = (r - a)(b - r) / (b - a) and the
+ * lift phi_D(r) = V_in + (V_out - V_in)(r - a) / (b - a):
+ *   phi(r, z) = phi_D(r) + sum_ij c_ij w(r) b_i(r) b_j(z),
+ * coefficient c_ij at i * mz + j.  Galerkin system (volume 2 pi r dr dz):
+ *   (K_r (x) M_z + M_r (x) K_z) c = f / (2 pi eps0) - g_r (x) m_z
+ * with K_r = int (w b_i)'(w b_k)' r dr, M_r = int w^2 b_i b_k r dr,
+ * g_r = int phi_D' (w b_i)' r dr, K_z = int b_j' b_l' dz, M_z = int b_j b_l
+ * dz, m_z = int b_j dz over [a, b] and [z_min, z_max]; the z ends are
+ * natural (Neumann).  Geometry, grid and wall voltages come from a
+ * pic_config (the other fields are ignored); 1 <= degree <=
+ * PIC_SPLINE_MAX_DEGREE, nr + degree <= 1024 (the host eigen solve at
+ * creation grows as (nr + degree)^3: under a second at 256 cells, about a
+ * minute at 1024).
+ * ------------------------------------------------------------------ */
+#define PIC_SPLINE_MAX_DEGREE 5
+typedef struct pic_spline pic_spline;
+
+/* The 1D matrices (host only, no GPU): dense row-major K_r, M_r (mr x mr),
+ * g_r (mr), K_z, M_z (mz x mz), m_z (mz); any pointer may be NULL.
+ * PIC_EINVAL on a bad config or degree. */
+int pic_spline_matrices(const pic_config* cfg, int degree, double* K_r, double* M_r,
+                        double* g_r, double* K_z, double* M_z, double* m_z);
+
+/* The generalised eigenpairs of (K_r, M_r) the solver uses (host only):
+ * V (mr x mr, row-major, column k the k-th eigenvector) with V^T M_r V = I
+ * and V^T K_r V = diag(lambda), lambda ascending.  PIC_ENOCONV if the
+ * eigen solver did not converge. */
+int pic_spline_eigen(const pic_config* cfg, int degree, double* V, double* lambda);
+
+/* A solver on the current CUDA device: builds the tables on the host
+ * (eigenpairs of (K_r, M_r), band Cholesky factors of lambda_k M_z + K_z
+ * for every r-mode k) and copies them to device memory it owns (cudaMalloc,
+ * freed by pic_spline_free).  Work is queued on cuda_stream (NULL: the
+ * default stream).  PIC_EINVAL, PIC_ENOCONV, PIC_ENOMEM. */
+int pic_spline_create(const pic_config* cfg, int degree, void* cuda_stream, pic_spline** out);
+void pic_spline_free(pic_spline* s);
+int pic_spline_sizes(const pic_spline* s, int* mr, int* mz);
+
+/* c = the Galerkin solution for the load f (DEVICE arrays of mr x mz
+ * FP64; f is the charge term sum_p q w_p w(r_p) b_i(r_p) b_j(z_p), in C);
+ * dirichlet = 0 solves with both walls at 0 V.  A direct FP64 solve: per
+ * r-mode band solves between two dense transforms.  Asynchronous on the
+ * solver's stream; f and c must not alias. */
+int pic_spline_solve(pic_spline* s, const double* f, double* c, int dirichlet);
+
+/* f += qw w(r_p) b_i(r_p) b_j(z_p) for n particles at (r_p, z_p) (DEVICE
+ * FP64 arrays; positions inside the gap are expected, others are charged
+ * to the nearest cell's functions); FP64 atomics, asynchronous. */
+int pic_spline_deposit(pic_spline* s, const double* r, const double* z, int64_t n, double qw,
+                       double* f);
+
+/* phi, E_r = -d phi/dr, E_z = -d phi/dz of coefficients c at n points
+ * (DEVICE FP64 arrays; any of phi, er, ez may be NULL); dirichlet = 0
+ * leaves out the lift phi_D.  Asynchronous. */
+int pic_spline_eval(pic_spline* s, const double* c, const double* r, const double* z, int64_t n,
+                    int dirichlet, double* phi, double* er, double* ez);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,19 @@ def lib() -> ctypes.CDLL:
         L.pic_profile.argtypes = [vp, ctypes.c_int, P(PicKernelTimes)]
         L.pic_free.argtypes = [vp]
         L.pic_free.restype = None
+        L.pic_spline_matrices.argtypes = [P(PicConfig), ctypes.c_int, vp, vp, vp, vp, vp, vp]
+        L.pic_spline_eigen.argtypes = [P(PicConfig), ctypes.c_int, vp, vp]
+        L.pic_spline_create.argtypes = [P(PicConfig), ctypes.c_int, vp, P(vp)]
+        L.pic_spline_free.argtypes = [vp]
+        L.pic_spline_free.restype = None
+        L.pic_spline_sizes.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int)]
+        L.pic_spline_solve.argtypes = [vp, vp, vp, ctypes.c_int]
+        L.pic_spline_deposit.argtypes = [vp, vp, vp, c_i64, c_d, vp]
+        L.pic_spline_eval.argtypes = [vp, vp, vp, vp, c_i64, ctypes.c_int, vp, vp, vp]
+        for name in ("pic_spline_matrices", "pic_spline_eigen", "pic_spline_create",
+                     "pic_spline_sizes", "pic_spline_solve", "pic_spline_deposit",
+                     "pic_spline_eval"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("pic_init", "pic_load_particles", "pic_step", "pic_diagnostics",
                      "pic_export_particles", "pic_set_efield", "pic_set_cross_sections",
                      "pic_moments", "pic_moments_accumulate", "pic_force_balance", "pic_fluid_model",
@@ -386,3 +399,106 @@ def solve_field_static(cfg: dict, b_dev_ptr: int, phi_dev_ptr: int, stream: int 
             ctypes.byref(rel) if check else None, ctypes.c_void_p(stream))
     _check(rc, "pic_solve_field_static")
     return rel.value if check else None
+
+
+# ------------------------------------------------------- weighted B-splines
+
+def _ptr_np(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def spline_matrices(cfg: dict, degree: int) -> dict:
+    """The weighted B-spline field's 1D matrices (pic_spline_matrices,
+    host only): K_r, M_r (mr x mr), g_r (mr), K_z, M_z (mz x mz), m_z (mz)."""
+    mr, mz = cfg["nr"] + degree, cfg["nz"] + degree
+    out = dict(K_r=np.zeros((mr, mr)), M_r=np.zeros((mr, mr)), g_r=np.zeros(mr),
+               K_z=np.zeros((mz, mz)), M_z=np.zeros((mz, mz)), m_z=np.zeros(mz))
+    c = make_config(cfg)
+    _check(lib().pic_spline_matrices(ctypes.byref(c), int(degree),
+                                     *[_ptr_np(out[k]) for k in ("K_r", "M_r", "g_r", "K_z",
+                                                                "M_z", "m_z")]),
+           "pic_spline_matrices")
+    return out
+
+
+def spline_eigen(cfg: dict, degree: int):
+    """(V, lambda) of pic_spline_eigen (host only)."""
+    mr = cfg["nr"] + degree
+    V, lam = np.zeros((mr, mr)), np.zeros(mr)
+    c = make_config(cfg)
+    _check(lib().pic_spline_eigen(ctypes.byref(c), int(degree), _ptr_np(V), _ptr_np(lam)),
+           "pic_spline_eigen")
+    return V, lam
+
+
+def _dev_f64(t, n=None, name="array"):
+    if not (getattr(t, "is_cuda", False) and str(t.dtype) == "torch.float64" and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA float64 tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class SplineSolver:
+    """pic_spline_create ... pic_spline_free: the degree-n weighted B-spline
+    field on the current CUDA device; arrays are torch CUDA float64
+    tensors, coefficients of shape (mr, mz)."""
+
+    def __init__(self, cfg: dict, degree: int, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.cfg, self.degree = dict(cfg), int(degree)
+        h = ctypes.c_void_p()
+        c = make_config(cfg)
+        _check(lib().pic_spline_create(ctypes.byref(c), self.degree, ctypes.c_void_p(int(stream)),
+                                       ctypes.byref(h)), "pic_spline_create")
+        self.h = h
+        mr, mz = ctypes.c_int(), ctypes.c_int()
+        _check(lib().pic_spline_sizes(self.h, ctypes.byref(mr), ctypes.byref(mz)), "pic_spline_sizes")
+        self.mr, self.mz = mr.value, mz.value
+
+    def close(self):
+        if self.h:
+            lib().pic_spline_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, f, dirichlet: bool = True):
+        import torch
+        c = torch.empty((self.mr, self.mz), dtype=torch.float64, device=f.device)
+        _check(lib().pic_spline_solve(self.h, _dev_f64(f, self.mr * self.mz, "f"),
+                                      _dev_f64(c), int(bool(dirichlet))), "pic_spline_solve")
+        return c
+
+    def deposit(self, r, z, qw: float, f=None):
+        import torch
+        if f is None:
+            f = torch.zeros((self.mr, self.mz), dtype=torch.float64, device=r.device)
+        n = r.numel()
+        _check(lib().pic_spline_deposit(self.h, _dev_f64(r, n, "r"), _dev_f64(z, n, "z"), n,
+                                        float(qw), _dev_f64(f, self.mr * self.mz, "f")),
+               "pic_spline_deposit")
+        return f
+
+    def eval(self, c, r, z, dirichlet: bool = True):
+        """(phi, E_r, E_z) at the points."""
+        import torch
+        n = r.numel()
+        out = [torch.empty(n, dtype=torch.float64, device=r.device) for _ in range(3)]
+        _check(lib().pic_spline_eval(self.h, _dev_f64(c, self.mr * self.mz, "c"),
+                                     _dev_f64(r, n, "r"), _dev_f64(z, n, "z"), n,
+                                     int(bool(dirichlet)), *[_dev_f64(o) for o in out]),
+               "pic_spline_eval")
+        return tuple(out)
