@@ -484,7 +484,7 @@ int pic_field_images(pic_handle* h, float* rho, float* phi_rho);
 
 /* ------------------------------------------------------------------
  * Weighted B-spline field of degree n (Sec. II.A: finite elements on
- * weighted B-splines of any order, with the Dirichlet electrodes carried
+ * weighted B-splines of arbitrary degree, with the Dirichlet electrodes carried
  * by a weight function on a rectangular grid), with particle shapes from
  * the same basis.  Uniform B-splines b_i of degree n on knots extending n
  * cells past each end: mr = nr + n functions in r, mz = nz + n in z; the

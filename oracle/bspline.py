@@ -1,6 +1,6 @@
 """Weighted B-spline finite elements of degree n for the r-z Poisson
 problem, with particle shapes taken from the same basis (arXiv 2206.14662,
-Sec. II.A: the field solve uses weighted extended B-splines of any order,
+Sec. II.A: the field solve uses weighted extended B-splines of arbitrary degree,
 which put Dirichlet electrodes on a rectangular grid) -- plain numpy and
 scipy, FP64.
 

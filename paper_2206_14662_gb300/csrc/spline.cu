@@ -1,5 +1,5 @@
 // spline.cu -- the weighted B-spline field of degree n (arXiv 2206.14662,
-// Sec. II.A: finite elements on weighted B-splines of any order, which put
+// Sec. II.A: finite elements on weighted B-splines of arbitrary degree, which put
 // the Dirichlet electrodes on a rectangular grid) with particle shapes from
 // the same basis.
 //

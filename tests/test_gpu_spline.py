@@ -1,5 +1,5 @@
 """The weighted B-spline field on the GPU (pic_spline_*: Sec. II.A's
-finite elements on weighted B-splines of any order, with particle shapes
+finite elements on weighted B-splines of arbitrary degree, with particle shapes
 from the same basis) against oracle.bspline on the same seeded inputs:
 the deposit, the fast-diagonalisation solve against the oracle's sparse
 LU (residual of the assembled system and the field at the particles), and

@@ -1,5 +1,5 @@
 """Pins of the oracle's weighted B-spline field of degree n (Sec. II.A:
-finite elements on weighted B-splines of any order; particles deposit with
+finite elements on weighted B-splines of arbitrary degree; particles deposit with
 and feel the same basis): Cox-de Boor values against the closed forms of
 low degrees, partition of unity and Marsden's identity, derivatives
 against differences, the 1D mass and stiffness matrices against the
