@@ -545,6 +545,42 @@ int pic_spline_deposit(pic_spline* s, const double* r, const double* z, int64_t 
 int pic_spline_eval(pic_spline* s, const double* c, const double* r, const double* z, int64_t n,
                     int dirichlet, double* phi, double* er, double* ez);
 
+/* ------------------------------------------------------------------
+ * Web-spline system for curved electrodes (Sec. II.A: weighted extended
+ * B-splines carry curved Dirichlet surfaces on a rectangular grid; Sec.
+ * II.B: the coaxial gap with a filled ellipse on the outer cylinder).
+ * Host assembly, no GPU.  Domain: r_in < r < r_out, z_min < z < z_max of
+ * cfg, minus the filled ellipse ((r - e0)/e2)^2 + ((z - e1)/e3)^2 <= 1 of
+ * ellipse = {e0 (r centre), e1 (z centre), e2 (r semi-axis), e3 (z
+ * semi-axis)} (NULL: none); V = v_inner on r_in, v_outer on r_out and on
+ * the ellipse; natural ends in z.  B-spline grid: nr cells on [r_lo, r_hi]
+ * (r_lo <= r_in, r_hi >= r_out: walls may lie between grid lines) and
+ * cfg->nz cells on [z_min, z_max]; degree 1..PIC_SPLINE_MAX_DEGREE.
+ * Weight: the R-function conjunction x + y - sqrt(x^2 + y^2) of
+ * (r - r_in)(r_out - r)/(r_out - r_in) and min(e2, e3)/2 times the
+ * ellipse's quadratic minus 1; lift V_in + dV (r - r_in)/(r - r_in + w_o),
+ * w_o the conjunction of (r_out - r) and the ellipse weight.  Inner
+ * B-splines (a whole grid cell of the support in the domain) carry the
+ * outer ones (support meeting the domain only in cut cells) through
+ * Lagrange coefficients on the nearest (n+1)^2 array of inner indices.
+ * Output: A (n_inner x n_inner, CSR with sorted columns, row pointers of
+ * n_inner + 1 ints) = T^T A_full T with A_full = eps0 int grad(w b_k) .
+ * grad(w b_l) 2 pi r dr dz over the domain; g = T^T eps0 int grad(w b_k) .
+ * grad(phi_D) dV (the load of the lift: solve A u = f_inner - g); the
+ * full index (i * mz + j, mz = nz + degree) of each inner function; the
+ * extension T (rows: mr * mz full functions, CSR).  Full coefficients of
+ * phi - phi_D are c = T u.  PIC_EINVAL on bad arguments or a grid too
+ * coarse for the geometry (an outer B-spline without an inner array). */
+typedef struct pic_web pic_web;
+int pic_web_create(const pic_config* cfg, const double* ellipse, double r_lo, double r_hi,
+                   int nr, int degree, pic_web** out);
+void pic_web_free(pic_web* w);
+int pic_web_sizes(const pic_web* w, int* n_inner, int64_t* nnz, int64_t* t_nnz, int* mr,
+                  int* mz);
+/* Copies out the arrays sized by pic_web_sizes; any pointer may be NULL. */
+int pic_web_export(const pic_web* w, int* a_ptr, int* a_col, double* a_val, double* g,
+                   int* inner_full, int* t_ptr, int* t_col, double* t_val);
+
 #ifdef __cplusplus
 }
 #endif

@@ -117,6 +117,14 @@ def lib() -> ctypes.CDLL:
         L.pic_spline_solve.argtypes = [vp, vp, vp, ctypes.c_int]
         L.pic_spline_deposit.argtypes = [vp, vp, vp, c_i64, c_d, vp]
         L.pic_spline_eval.argtypes = [vp, vp, vp, vp, c_i64, ctypes.c_int, vp, vp, vp]
+        L.pic_web_create.argtypes = [P(PicConfig), vp, c_d, c_d, ctypes.c_int, ctypes.c_int, P(vp)]
+        L.pic_web_free.argtypes = [vp]
+        L.pic_web_free.restype = None
+        L.pic_web_sizes.argtypes = [vp, P(ctypes.c_int), P(c_i64), P(c_i64), P(ctypes.c_int),
+                                    P(ctypes.c_int)]
+        L.pic_web_export.argtypes = [vp] * 9
+        for name in ("pic_web_create", "pic_web_sizes", "pic_web_export"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("pic_spline_matrices", "pic_spline_eigen", "pic_spline_create",
                      "pic_spline_sizes", "pic_spline_solve", "pic_spline_deposit",
                      "pic_spline_eval"):
@@ -502,3 +510,33 @@ class SplineSolver:
                                      int(bool(dirichlet)), *[_dev_f64(o) for o in out]),
                "pic_spline_eval")
         return tuple(out)
+
+
+def web_system(cfg: dict, ellipse, r_lo: float, r_hi: float, nr: int, degree: int) -> dict:
+    """The web-spline system of pic_web_create (host only): CSR arrays
+    a_ptr, a_col, a_val (n_inner x n_inner), the lift load g, the full
+    index of each inner function, and the extension T (t_ptr, t_col,
+    t_val; mr * mz rows)."""
+    c = make_config(cfg)
+    e = None if ellipse is None else np.ascontiguousarray(ellipse, dtype=np.float64)
+    h = ctypes.c_void_p()
+    L = lib()
+    _check(L.pic_web_create(ctypes.byref(c), _ptr_np(e), float(r_lo), float(r_hi), int(nr),
+                            int(degree), ctypes.byref(h)), "pic_web_create")
+    try:
+        ni, nnz, tn = ctypes.c_int(), c_i64(), c_i64()
+        mr, mz = ctypes.c_int(), ctypes.c_int()
+        _check(L.pic_web_sizes(h, ctypes.byref(ni), ctypes.byref(nnz), ctypes.byref(tn),
+                               ctypes.byref(mr), ctypes.byref(mz)), "pic_web_sizes")
+        out = dict(a_ptr=np.zeros(ni.value + 1, np.int32), a_col=np.zeros(nnz.value, np.int32),
+                   a_val=np.zeros(nnz.value), g=np.zeros(ni.value),
+                   inner_full=np.zeros(ni.value, np.int32),
+                   t_ptr=np.zeros(mr.value * mz.value + 1, np.int32),
+                   t_col=np.zeros(tn.value, np.int32), t_val=np.zeros(tn.value))
+        _check(L.pic_web_export(h, *[_ptr_np(out[k]) for k in ("a_ptr", "a_col", "a_val", "g",
+                                                               "inner_full", "t_ptr", "t_col",
+                                                               "t_val")]), "pic_web_export")
+        out["mr"], out["mz"] = mr.value, mz.value
+        return out
+    finally:
+        L.pic_web_free(h)

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpic.so")
 SOURCES = ["particle_step.cu", "field_solve.cu", "sort.cu", "capi.cu", "field_static.cu",
-           "unet.cu", "moments.cu", "spline.cu"]
+           "unet.cu", "moments.cu", "spline.cu", "webspline.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 # the particle step writes its multiply-adds out explicitly; no automatic
