@@ -44,10 +44,11 @@ AMU = 1.66053906660e-27
 T_ABS_INNER, T_ABS_OUTER, T_ABS_ZMIN, T_ABS_ZMAX = 0, 1, 2, 3
 T_WORK_E, T_KE_ABSORBED, T_ION_LOSS, T_RECOIL_LOSS = 4, 5, 6, 7
 T_N_ELASTIC, T_N_IONISE, T_N_ABSORBED, T_N_OVER, T_N_CANDIDATE = 8, 9, 10, 11, 12
-T_COUNT = 13
+T_ABS_ELLIPSE = 13
+T_COUNT = 14
 
 EV_NONE, EV_ELASTIC, EV_IONISE, EV_NULL = 0, 1, 2, 3
-EV_WALL = 10  # 10 inner, 11 outer, 12 z_min, 13 z_max
+EV_WALL = 10  # 10 inner, 11 outer, 12 z_min, 13 z_max, 14 ellipse
 
 
 def build(force: bool = False) -> str:
@@ -77,6 +78,8 @@ class _Params(ctypes.Structure):
         ("xs_n", ctypes.c_int32), ("xs_E_eV", ctypes.c_void_p),
         ("xs_sigma_el", ctypes.c_void_p), ("xs_sigma_io", ctypes.c_void_p),
         ("xs_xi", ctypes.c_void_p), ("e_per_particle", ctypes.c_int32),
+        ("has_ellipse", ctypes.c_int32), ("e_r0", ctypes.c_double), ("e_z0", ctypes.c_double),
+        ("e_dr", ctypes.c_double), ("e_dz", ctypes.c_double),
     ]
 
 
@@ -159,6 +162,10 @@ def params(cfg: dict) -> _Params:
         p.xs_n = len(arrs[0])
         p.xs_E_eV, p.xs_sigma_el, p.xs_sigma_io = (_ptr(a) for a in arrs[:3])
         p.xs_xi = None if arrs[3] is None else _ptr(arrs[3])
+    ell = cfg.get("ellipse")
+    if ell is not None:   # (r0, z0, dr, dz) of a filled metal ellipse
+        p.has_ellipse = 1
+        p.e_r0, p.e_z0, p.e_dr, p.e_dz = (float(v) for v in ell)
     if cfg.get("nu_max", 0.0) > 0:
         p.nu_max = cfg["nu_max"]
     else:
@@ -387,9 +394,12 @@ class OracleSim:
     with E^n, removal of absorbed particles, then field solve for E^{n+1}.
 
     With cfg["bspline_degree"] = n >= 1 the field is the weighted B-spline
-    field of degree n (oracle.bspline): particles deposit with its basis
-    and are pushed with its exact gradient at their position; self.coef
-    holds its coefficients (self.phi, self.er, self.ez are then None).
+    field of degree n (oracle.bspline), or with cfg["ellipse"] = (r0, z0,
+    dr, dz) as well the web-spline field of the gap minus that metal
+    ellipse (oracle.webspline; particles entering the ellipse are absorbed
+    and tallied in T_ABS_ELLIPSE): particles deposit with its basis and
+    are pushed with its exact gradient at their position; self.coef holds
+    its coefficients (self.phi, self.er, self.ez are then None).
     """
 
     def __init__(self, cfg: dict, r, z, vr, vt, vz, uid, efield_nodes=None,
@@ -412,8 +422,16 @@ class OracleSim:
         self.solve_field = solve_field
         self.spline = None
         if self.cfg.get("bspline_degree", 0) > 0:
-            from .bspline import SplineField
-            self.spline = SplineField(self.cfg)
+            if self.cfg.get("ellipse") is not None:
+                from .webspline import Geometry, WebSplineField
+                c = self.cfg
+                geo = Geometry(c["r_in"], c["r_out"], c["z_min"], c["z_max"], c["v_inner"],
+                               c["v_outer"], ellipse=tuple(c["ellipse"]))
+                self.spline = WebSplineField(geo, int(c["bspline_degree"]), c["r_in"],
+                                             c["r_out"], c["nr"], c["nz"])
+            else:
+                from .bspline import SplineField
+                self.spline = SplineField(self.cfg)
             self.P.e_per_particle = 1
             self.qw = -QE * derived(self.cfg)["weight"]
             self.b = self.spline.deposit(self.r, self.z, self.qw)

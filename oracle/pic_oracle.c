@@ -74,6 +74,10 @@ typedef struct {
   /* 1: or_step's er/ez hold E at each particle (length n, e.g. the exact
    * gradient of a B-spline field) instead of node grids */
   int32_t e_per_particle;
+  /* optional filled ellipse ((r - e_r0)/e_dr)^2 + ((z - e_z0)/e_dz)^2 <= 1
+   * of metal (Sec. II.B's trap): particles entering it are absorbed */
+  int32_t has_ellipse;
+  double e_r0, e_z0, e_dr, e_dz;
 } or_params;
 
 /* tally slots (accumulated, doubles) */
@@ -84,13 +88,14 @@ enum {
   T_ION_LOSS,        /* binding energy removed by ionisation, J */
   T_RECOIL_LOSS,     /* elastic recoil loss, J */
   T_N_ELASTIC, T_N_IONISE, T_N_ABSORBED, T_N_OVER, T_N_CANDIDATE,
+  T_ABS_ELLIPSE,     /* weight absorbed by the ellipse */
   T_COUNT
 };
 
 /* per-particle event codes */
 enum { EV_NONE = 0, EV_ELASTIC = 1, EV_IONISE = 2, EV_NULL = 3,
        EV_WALL_INNER = 10, EV_WALL_OUTER = 11, EV_WALL_ZMIN = 12,
-       EV_WALL_ZMAX = 13 };
+       EV_WALL_ZMAX = 13, EV_WALL_ELLIPSE = 14 };
 
 /* ---------------------------------------------------------------- Philox */
 
@@ -312,6 +317,26 @@ void or_deposit(const or_params* P, int64_t n, const double* r,
   }
 }
 
+/* First entry of the straight (r,z) segment (r0,z0) -> (r1,z1) into the
+ * filled ellipse: f(t) = X(t)^2 + Y(t)^2 - 1 with X, Y the normalised
+ * offsets is a quadratic a t^2 + b t + c; a start inside (c <= 0) enters
+ * at t = 0, otherwise at the smaller root if it lies in [0, 1].  Returns 1
+ * and *t on entry; *f_least is the least f on the segment (the decision's
+ * distance from its threshold). */
+static int or_ellipse_entry(const or_params* P, double r0, double z0, double r1, double z1,
+                            double* t, double* f_least) {
+  double x0 = (r0 - P->e_r0) / P->e_dr, y0 = (z0 - P->e_z0) / P->e_dz;
+  double dx = (r1 - r0) / P->e_dr, dy = (z1 - z0) / P->e_dz;
+  double a = dx * dx + dy * dy, b = 2.0 * (x0 * dx + y0 * dy), c = x0 * x0 + y0 * y0 - 1.0;
+  double tm = a > 0 ? fmin(fmax(-b / (2.0 * a), 0.0), 1.0) : 0.0;
+  *f_least = (a * tm + b) * tm + c;
+  if (c <= 0.0) { *t = 0.0; return 1; }
+  if (*f_least > 0.0) return 0;
+  double disc = b * b - 4.0 * a * c;
+  *t = (-b - sqrt(fmax(disc, 0.0))) / (2.0 * a);
+  return *t >= 0.0 && *t <= 1.0;
+}
+
 /* ----------------------------------------------------------------- step */
 
 /* One step for particles sorted by ascending uid.  Arrays are updated in
@@ -385,9 +410,15 @@ int64_t or_step(const or_params* P, int64_t n, double* r, double* z,
     if (z1 >= P->z_max) tw[3] = (P->z_max - z0) / (z1 - z0);
     for (int w = 0; w < 4; ++w)
       if (tw[w] < 3.0 && tw[w] < tbest) { tbest = tw[w]; wall = w; }
+    if (P->has_ellipse) {
+      double te, fm;
+      int hit = or_ellipse_entry(P, r0, z0, r1, z1, &te, &fm);
+      mg = fmin(mg, fabs(fm) * 0.5 * fmin(P->e_dr, P->e_dz) / fmin(hr, hz));
+      if (hit && te < tbest) { tbest = te; wall = 4; }
+    }
     if (wall >= 0) {
       double v2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
-      tally[T_ABS_INNER + wall] += P->weight;
+      tally[wall == 4 ? T_ABS_ELLIPSE : T_ABS_INNER + wall] += P->weight;
       tally[T_KE_ABSORBED] += P->weight * 0.5 * m * v2;
       tally[T_N_ABSORBED] += 1.0;
       event[p] = (int8_t)(EV_WALL_INNER + wall);
