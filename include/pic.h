@@ -581,6 +581,33 @@ int pic_web_sizes(const pic_web* w, int* n_inner, int64_t* nnz, int64_t* t_nnz, 
 int pic_web_export(const pic_web* w, int* a_ptr, int* a_col, double* a_val, double* g,
                    int* inner_full, int* t_ptr, int* t_col, double* t_val);
 
+/* Device side of a web-spline system on the current CUDA device: copies
+ * the system, its extension and T^T to device memory owned by w (freed by
+ * pic_web_free), and builds the preconditioner, the weighted B-spline
+ * solver of the grid's box (pic_spline_create with walls at the grid's
+ * ends).  Work is queued on cuda_stream.  PIC_ENOMEM, PIC_ENOCONV. */
+int pic_web_device(pic_web* w, void* cuda_stream);
+
+/* Solves A u = T^T f - [dirichlet] g by conjugate gradients preconditioned
+ * with D P^T S^-1 P D (P: inner functions into the full basis, S: the box
+ * solver, D = sqrt(diag(P^T S P) / diag A): the web functions near a
+ * curved electrode carry a small weight), from u = 0, until ||r|| <= rtol ||b|| or maxit iterations; then
+ * c = T u.  f (the particle load in the full basis, pic_web_deposit) and
+ * c are DEVICE arrays of mr * mz FP64.  *iters, *relres (may be NULL) get
+ * the count and the final relative residual.  Synchronises each
+ * iteration.  PIC_ENOCONV if rtol was not met. */
+int pic_web_solve(pic_web* w, const double* f, double* c, int dirichlet, double rtol, int maxit,
+                  int* iters, double* relres);
+
+/* f_k += qw w(r_p, z_p) b_k(r_p, z_p) with the web weight (DEVICE arrays;
+ * FP64 atomics), and phi, E = -grad phi of full coefficients c at points
+ * (any output may be NULL; dirichlet = 0 leaves out the lift).
+ * Asynchronous. */
+int pic_web_deposit(pic_web* w, const double* r, const double* z, int64_t n, double qw,
+                    double* f);
+int pic_web_eval(pic_web* w, const double* c, const double* r, const double* z, int64_t n,
+                 int dirichlet, double* phi, double* er, double* ez);
+
 #ifdef __cplusplus
 }
 #endif

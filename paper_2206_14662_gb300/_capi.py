@@ -123,7 +123,13 @@ def lib() -> ctypes.CDLL:
         L.pic_web_sizes.argtypes = [vp, P(ctypes.c_int), P(c_i64), P(c_i64), P(ctypes.c_int),
                                     P(ctypes.c_int)]
         L.pic_web_export.argtypes = [vp] * 9
-        for name in ("pic_web_create", "pic_web_sizes", "pic_web_export"):
+        L.pic_web_device.argtypes = [vp, vp]
+        L.pic_web_solve.argtypes = [vp, vp, vp, ctypes.c_int, c_d, ctypes.c_int,
+                                    P(ctypes.c_int), P(c_d)]
+        L.pic_web_deposit.argtypes = [vp, vp, vp, c_i64, c_d, vp]
+        L.pic_web_eval.argtypes = [vp, vp, vp, vp, c_i64, ctypes.c_int, vp, vp, vp]
+        for name in ("pic_web_create", "pic_web_sizes", "pic_web_export", "pic_web_device",
+                     "pic_web_solve", "pic_web_deposit", "pic_web_eval"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("pic_spline_matrices", "pic_spline_eigen", "pic_spline_create",
                      "pic_spline_sizes", "pic_spline_solve", "pic_spline_deposit",
@@ -540,3 +546,73 @@ def web_system(cfg: dict, ellipse, r_lo: float, r_hi: float, nr: int, degree: in
         return out
     finally:
         L.pic_web_free(h)
+
+
+class WebSolver:
+    """pic_web_create + pic_web_device ... pic_web_free: the web-spline
+    field on the current CUDA device; arrays are torch CUDA float64
+    tensors, full coefficients of shape (mr, mz)."""
+
+    def __init__(self, cfg: dict, ellipse, r_lo: float, r_hi: float, nr: int, degree: int,
+                 stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        c = make_config(cfg)
+        e = None if ellipse is None else np.ascontiguousarray(ellipse, dtype=np.float64)
+        h = ctypes.c_void_p()
+        L = lib()
+        _check(L.pic_web_create(ctypes.byref(c), _ptr_np(e), float(r_lo), float(r_hi), int(nr),
+                                int(degree), ctypes.byref(h)), "pic_web_create")
+        self.h = h
+        mr, mz = ctypes.c_int(), ctypes.c_int()
+        _check(L.pic_web_sizes(h, None, None, None, ctypes.byref(mr), ctypes.byref(mz)),
+               "pic_web_sizes")
+        self.mr, self.mz = mr.value, mz.value
+        _check(L.pic_web_device(h, ctypes.c_void_p(int(stream))), "pic_web_device")
+
+    def close(self):
+        if self.h:
+            lib().pic_web_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def deposit(self, r, z, qw: float, f=None):
+        import torch
+        if f is None:
+            f = torch.zeros((self.mr, self.mz), dtype=torch.float64, device=r.device)
+        n = r.numel()
+        _check(lib().pic_web_deposit(self.h, _dev_f64(r, n, "r"), _dev_f64(z, n, "z"), n,
+                                     float(qw), _dev_f64(f, self.mr * self.mz, "f")),
+               "pic_web_deposit")
+        return f
+
+    def solve(self, f, dirichlet: bool = True, rtol: float = 1e-12, maxit: int = 500):
+        """(c, iterations, relative residual)."""
+        import torch
+        c = torch.empty((self.mr, self.mz), dtype=torch.float64, device=f.device)
+        it, rel = ctypes.c_int(), c_d()
+        _check(lib().pic_web_solve(self.h, _dev_f64(f, self.mr * self.mz, "f"), _dev_f64(c),
+                                   int(bool(dirichlet)), float(rtol), int(maxit),
+                                   ctypes.byref(it), ctypes.byref(rel)), "pic_web_solve")
+        return c, it.value, rel.value
+
+    def eval(self, c, r, z, dirichlet: bool = True):
+        import torch
+        n = r.numel()
+        out = [torch.empty(n, dtype=torch.float64, device=r.device) for _ in range(3)]
+        _check(lib().pic_web_eval(self.h, _dev_f64(c, self.mr * self.mz, "c"), _dev_f64(r, n, "r"),
+                                  _dev_f64(z, n, "z"), n, int(bool(dirichlet)),
+                                  *[_dev_f64(o) for o in out]), "pic_web_eval")
+        return tuple(out)

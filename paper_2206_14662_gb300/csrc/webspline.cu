@@ -39,7 +39,7 @@ constexpr int kMaxDeg = PIC_SPLINE_MAX_DEGREE;
 // the p + 1 non-zero uniform B-splines of degree p on a knot span at local
 // coordinate u (triangular Cox-de Boor scheme, distances in units of the
 // spacing) and their derivatives for spacing h
-void span_basis_d(int p, double u, double h, double* N, double* dN) {
+__host__ __device__ inline void span_basis_d(int p, double u, double h, double* N, double* dN) {
   double M[kMaxDeg + 1];
   auto basis = [](int q, double x, double* B) {
     B[0] = 1.0;
@@ -87,20 +87,20 @@ struct Geo {
   bool ell;
   double er, ez, edr, edz;
 
-  void w_e(double r, double z, double& v, double& gr, double& gz) const {
-    const double s = 0.5 * std::min(edr, edz);
+  __host__ __device__ void w_e(double r, double z, double& v, double& gr, double& gz) const {
+    const double s = 0.5 * fmin(edr, edz);
     v = s * (((r - er) / edr) * ((r - er) / edr) + ((z - ez) / edz) * ((z - ez) / edz) - 1.0);
     gr = s * 2.0 * (r - er) / (edr * edr);
     gz = s * 2.0 * (z - ez) / (edz * edz);
   }
-  static void conj(double x, double gx0, double gx1, double y, double gy0, double gy1, double& v,
+  __host__ __device__ static void conj(double x, double gx0, double gx1, double y, double gy0, double gy1, double& v,
                    double& g0, double& g1) {
-    const double q = std::sqrt(x * x + y * y), qs = q > 0 ? q : 1.0;
+    const double q = sqrt(x * x + y * y), qs = q > 0 ? q : 1.0;
     v = x + y - q;
     g0 = gx0 + gy0 - (x * gx0 + y * gy0) / qs;
     g1 = gx1 + gy1 - (x * gx1 + y * gy1) / qs;
   }
-  void weight(double r, double z, double& w, double& wr, double& wz) const {
+  __host__ __device__ void weight(double r, double z, double& w, double& wr, double& wz) const {
     const double ab = b - a;
     const double wc = (r - a) * (b - r) / ab, gc = (a + b - 2.0 * r) / ab;
     if (!ell) {
@@ -113,7 +113,7 @@ struct Geo {
     w_e(r, z, v, gr, gz);
     conj(wc, gc, 0.0, v, gr, gz, w, wr, wz);
   }
-  void lift(double r, double z, double& p, double& pr, double& pz) const {
+  __host__ __device__ void lift(double r, double z, double& p, double& pr, double& pz) const {
     const double dv = v_out - v_in;
     if (!ell) {
       p = v_in + dv * (r - a) / (b - a);
@@ -165,7 +165,25 @@ struct Geo {
 
 using namespace pic;
 
+namespace pic {
+namespace web {
+// device copies and work vectors of a web-spline system (pic_web_device)
+struct Dev {
+  cudaStream_t stream = nullptr;
+  int *a_ptr = nullptr, *a_col = nullptr, *inner_full = nullptr;
+  int *t_ptr = nullptr, *t_col = nullptr, *tt_ptr = nullptr, *tt_col = nullptr;
+  double *a_val = nullptr, *g = nullptr, *t_val = nullptr, *tt_val = nullptr;
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *full = nullptr, *full2 = nullptr, *dots = nullptr;
+  double* scale = nullptr;     // sqrt(diag S / diag A) on the inner functions
+  pic_spline* pre = nullptr;   // the enclosing box's solver: the preconditioner
+};
+}  // namespace web
+}  // namespace pic
+
 struct pic_web {
+  pic_config box;            // the grid box as a config (walls at the grid's ends)
+  pic::web::Dev* dev = nullptr;
   web::Geo G;
   int n, nr, nz, mr, mz;
   double r_lo, hr, hz;
@@ -354,6 +372,10 @@ int pic_web_create(const pic_config* cfg, const double* ellipse, double r_lo, do
     return PIC_EINVAL;
   if (ellipse && !(ellipse[2] > 0 && ellipse[3] > 0)) return PIC_EINVAL;
   pic_web* W = new pic_web();
+  W->box = *cfg;
+  W->box.r_in = r_lo;
+  W->box.r_out = r_hi;
+  W->box.nr = nr;
   const int rc = build(W, cfg, ellipse, r_lo, r_hi, nr, degree);
   if (rc) {
     delete W;
@@ -363,7 +385,21 @@ int pic_web_create(const pic_config* cfg, const double* ellipse, double r_lo, do
   return PIC_OK;
 }
 
-void pic_web_free(pic_web* w) { delete w; }
+void pic_web_free(pic_web* w) {
+  if (!w) return;
+  if (w->dev) {
+    pic::web::Dev* d = w->dev;
+    for (void* ptr : {(void*)d->a_ptr, (void*)d->a_col, (void*)d->inner_full, (void*)d->t_ptr,
+                      (void*)d->t_col, (void*)d->tt_ptr, (void*)d->tt_col, (void*)d->a_val,
+                      (void*)d->g, (void*)d->t_val, (void*)d->tt_val, (void*)d->x, (void*)d->r,
+                      (void*)d->z, (void*)d->p, (void*)d->q, (void*)d->full, (void*)d->full2,
+                      (void*)d->dots, (void*)d->scale})
+      if (ptr) cudaFree(ptr);
+    pic_spline_free(d->pre);
+    delete d;
+  }
+  delete w;
+}
 
 int pic_web_sizes(const pic_web* w, int* n_inner, int64_t* nnz, int64_t* t_nnz, int* mr, int* mz) {
   if (!w) return PIC_EINVAL;
@@ -390,6 +426,314 @@ int pic_web_export(const pic_web* w, int* a_ptr, int* a_col, double* a_val, doub
   put(t_col, w->t_col);
   put(t_val, w->t_val);
   return PIC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ device
+
+namespace pic {
+namespace web {
+
+// y = A x, one warp per row (rows hold a few dozen entries)
+__global__ void k_spmv(int rows, const int* __restrict__ ptr, const int* __restrict__ col,
+                       const double* __restrict__ val, const double* __restrict__ x,
+                       double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < rows;
+       row += ((long long)gridDim.x * blockDim.x) >> 5) {
+    double s = 0.0;
+    for (int e = ptr[row] + lane; e < ptr[row + 1]; e += 32) s = fma(val[e], x[col[e]], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = s;
+  }
+}
+
+// out[0] += a . b, out[1] += b . b (block sums, one atomic each)
+__global__ void k_dots(int n, const double* __restrict__ a, const double* __restrict__ b,
+                       double* out) {
+  __shared__ double sa[32], sb[32];
+  double ab = 0.0, bb = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    ab = fma(a[i], b[i], ab);
+    bb = fma(b[i], b[i], bb);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ab += __shfl_xor_sync(0xffffffffu, ab, o);
+    bb += __shfl_xor_sync(0xffffffffu, bb, o);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sa[w] = ab; sb[w] = bb; }
+  __syncthreads();
+  if (w == 0) {
+    ab = lane < (int)(blockDim.x >> 5) ? sa[lane] : 0.0;
+    bb = lane < (int)(blockDim.x >> 5) ? sb[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      ab += __shfl_xor_sync(0xffffffffu, ab, o);
+      bb += __shfl_xor_sync(0xffffffffu, bb, o);
+    }
+    if (lane == 0) {
+      atomicAdd(out, ab);
+      atomicAdd(out + 1, bb);
+    }
+  }
+}
+
+// y = alpha x + beta y
+__global__ void k_axpby(int n, double alpha, const double* __restrict__ x, double beta,
+                        double* __restrict__ y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i] = alpha * x[i] + beta * y[i];
+}
+
+// dst[idx[i]] = s[i] src[i] and dst[i] = s[i] src[idx[i]]
+__global__ void k_scatter(int n, const int* __restrict__ idx, const double* __restrict__ s,
+                          const double* __restrict__ src, double* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[idx[i]] = s[i] * src[i];
+}
+
+__global__ void k_gather(int n, const int* __restrict__ idx, const double* __restrict__ s,
+                         const double* __restrict__ src, double* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = s[i] * src[idx[i]];
+}
+
+struct Grid {
+  int n, nr, nz, mz;
+  double r_lo, z0, hr, hz;
+};
+
+__device__ __forceinline__ int span(double x, double lo, double h, int cells, double& u) {
+  int c = (int)floor((x - lo) / h);
+  c = min(max(c, 0), cells - 1);
+  u = (x - lo) / h - c;
+  return c;
+}
+
+__global__ void k_web_deposit(Geo G, Grid D, const double* __restrict__ r,
+                              const double* __restrict__ z, long long np, double qw,
+                              double* __restrict__ f) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    double ur, uz, Nr[kMaxDeg + 1], dNr[kMaxDeg + 1], Nz[kMaxDeg + 1], dNz[kMaxDeg + 1];
+    const int cr = span(r[p], D.r_lo, D.hr, D.nr, ur), cz = span(z[p], D.z0, D.hz, D.nz, uz);
+    span_basis_d(D.n, ur, D.hr, Nr, dNr);
+    span_basis_d(D.n, uz, D.hz, Nz, dNz);
+    double w, wr, wz;
+    G.weight(r[p], z[p], w, wr, wz);
+    for (int k = 0; k <= D.n; ++k)
+      for (int l = 0; l <= D.n; ++l)
+        atomicAdd(f + (size_t)(cr + k) * D.mz + cz + l, qw * w * Nr[k] * Nz[l]);
+  }
+}
+
+__global__ void k_web_eval(Geo G, Grid D, const double* __restrict__ c,
+                           const double* __restrict__ r, const double* __restrict__ z,
+                           long long np, int dirichlet, double* __restrict__ phi,
+                           double* __restrict__ er, double* __restrict__ ez) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    double ur, uz, Nr[kMaxDeg + 1], dNr[kMaxDeg + 1], Nz[kMaxDeg + 1], dNz[kMaxDeg + 1];
+    const int cr = span(r[p], D.r_lo, D.hr, D.nr, ur), cz = span(z[p], D.z0, D.hz, D.nz, uz);
+    span_basis_d(D.n, ur, D.hr, Nr, dNr);
+    span_basis_d(D.n, uz, D.hz, Nz, dNz);
+    double w, wr, wz;
+    G.weight(r[p], z[p], w, wr, wz);
+    double s = 0.0, sr = 0.0, sz = 0.0;   // sum c b, d/dr, d/dz (without the weight)
+    for (int k = 0; k <= D.n; ++k) {
+      const double* row = c + (size_t)(cr + k) * D.mz + cz;
+      for (int l = 0; l <= D.n; ++l) {
+        s = fma(row[l], Nr[k] * Nz[l], s);
+        sr = fma(row[l], dNr[k] * Nz[l], sr);
+        sz = fma(row[l], Nr[k] * dNz[l], sz);
+      }
+    }
+    double v = w * s, gr = wr * s + w * sr, gz = wz * s + w * sz;
+    if (dirichlet) {
+      double pl, pr, pz;
+      G.lift(r[p], z[p], pl, pr, pz);
+      v += pl;
+      gr += pr;
+      gz += pz;
+    }
+    if (phi) phi[p] = v;
+    if (er) er[p] = -gr;
+    if (ez) ez[p] = -gz;
+  }
+}
+
+inline int blocks_for(long long n, int threads) {
+  return (int)std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, 152 * 8));
+}
+
+}  // namespace web
+}  // namespace pic
+
+extern "C" {
+
+int pic_web_device(pic_web* w, void* cuda_stream) {
+  using namespace pic::web;
+  if (!w) return PIC_EINVAL;
+  if (w->dev) return PIC_OK;
+  Dev* d = new Dev();
+  d->stream = (cudaStream_t)cuda_stream;
+  w->dev = d;
+  const int ni = (int)w->inner_full.size(), nf = w->mr * w->mz;
+  // T^T (inner rows) from T (full rows)
+  std::vector<int> tt_ptr(ni + 1, 0), tt_col(w->t_col.size());
+  std::vector<double> tt_val(w->t_val.size());
+  for (int c : w->t_col) ++tt_ptr[c + 1];
+  for (int i = 0; i < ni; ++i) tt_ptr[i + 1] += tt_ptr[i];
+  std::vector<int> fill(tt_ptr.begin(), tt_ptr.end() - 1);
+  for (int row = 0; row < nf; ++row)
+    for (int e = w->t_ptr[row]; e < w->t_ptr[row + 1]; ++e) {
+      const int k = fill[w->t_col[e]]++;
+      tt_col[k] = row;
+      tt_val[k] = w->t_val[e];
+    }
+  bool ok = true;
+  auto up = [&](auto*& dst, const auto& v) {
+    using T = std::remove_reference_t<decltype(v[0])>;
+    if (!ok) return;
+    ok = cudaMalloc((void**)&dst, std::max<size_t>(v.size(), 1) * sizeof(T)) == cudaSuccess &&
+         (v.empty() || cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) ==
+                           cudaSuccess);
+  };
+  auto zeros = [&](double*& dst, size_t n) {
+    if (!ok) return;
+    ok = cudaMalloc((void**)&dst, std::max<size_t>(n, 1) * sizeof(double)) == cudaSuccess;
+  };
+  up(d->a_ptr, w->a_ptr);
+  up(d->a_col, w->a_col);
+  up(d->a_val, w->a_val);
+  up(d->g, w->g);
+  up(d->inner_full, w->inner_full);
+  up(d->t_ptr, w->t_ptr);
+  up(d->t_col, w->t_col);
+  up(d->t_val, w->t_val);
+  up(d->tt_ptr, tt_ptr);
+  up(d->tt_col, tt_col);
+  up(d->tt_val, tt_val);
+  // preconditioner scale: sqrt(diag S / diag A), S the box system
+  // 2 pi eps0 (K_r (x) M_z + M_r (x) K_z) on the inner functions; the web
+  // functions near the ellipse carry a small weight, so without it the
+  // box operator is far from A there
+  {
+    const int mr = w->mr, mz = w->mz;
+    std::vector<double> Kr((size_t)mr * mr), Mr((size_t)mr * mr), Kz((size_t)mz * mz),
+        Mz((size_t)mz * mz);
+    if (pic_spline_matrices(&w->box, w->n, Kr.data(), Mr.data(), nullptr, Kz.data(), Mz.data(),
+                            nullptr) != PIC_OK)
+      return PIC_EINVAL;
+    std::vector<double> sc(ni);
+    for (int i = 0; i < ni; ++i) {
+      const int f = w->inner_full[i], ir = f / mz, jz = f % mz;
+      const double dS = 2.0 * kPi * kEps0 *
+                        (Kr[(size_t)ir * mr + ir] * Mz[(size_t)jz * mz + jz] +
+                         Mr[(size_t)ir * mr + ir] * Kz[(size_t)jz * mz + jz]);
+      double dA = 0.0;
+      for (int e = w->a_ptr[i]; e < w->a_ptr[i + 1]; ++e)
+        if (w->a_col[e] == i) dA = w->a_val[e];
+      sc[i] = dA > 0 ? std::sqrt(dS / dA) : 1.0;
+    }
+    up(d->scale, sc);
+  }
+  for (double** v : {&d->x, &d->r, &d->z, &d->p, &d->q}) zeros(*v, ni);
+  zeros(d->full, nf);
+  zeros(d->full2, nf);
+  zeros(d->dots, 2);
+  if (!ok) {
+    cudaGetLastError();
+    return PIC_ENOMEM;
+  }
+  return pic_spline_create(&w->box, w->n, cuda_stream, &d->pre);
+}
+
+int pic_web_solve(pic_web* w, const double* f_full, double* c_full, int dirichlet, double rtol,
+                  int maxit, int* iters, double* relres) {
+  using namespace pic::web;
+  if (!w || !w->dev || !f_full || !c_full || !(rtol > 0) || maxit < 1) return PIC_EINVAL;
+  Dev* d = w->dev;
+  cudaStream_t st = d->stream;
+  const int ni = (int)w->inner_full.size(), nf = w->mr * w->mz;
+  const int bi = blocks_for(ni, 256);
+  const int bw = blocks_for((long long)ni * 32, 256), bwf = blocks_for((long long)nf * 32, 256);
+  double h[2];
+  auto dots = [&](const double* a, const double* b) -> bool {
+    cudaMemsetAsync(d->dots, 0, 2 * sizeof(double), st);
+    k_dots<<<bi, 256, 0, st>>>(ni, a, b, d->dots);
+    return cudaMemcpyAsync(h, d->dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, st) ==
+               cudaSuccess &&
+           cudaStreamSynchronize(st) == cudaSuccess;
+  };
+  // preconditioner z = D P^T S^-1 P D r (S: the box's weighted B-spline
+  // system, D the diagonal rescaling)
+  auto precond = [&](const double* r, double* z) -> int {
+    cudaMemsetAsync(d->full, 0, (size_t)nf * sizeof(double), st);
+    k_scatter<<<bi, 256, 0, st>>>(ni, d->inner_full, d->scale, r, d->full);
+    const int rc = pic_spline_solve(d->pre, d->full, d->full2, 0);
+    k_gather<<<bi, 256, 0, st>>>(ni, d->inner_full, d->scale, d->full2, z);
+    return rc;
+  };
+  // right-hand side b = T^T f - [dirichlet] g, held in r; x = 0
+  k_spmv<<<bw, 256, 0, st>>>(ni, d->tt_ptr, d->tt_col, d->tt_val, f_full, d->r);
+  if (dirichlet) k_axpby<<<bi, 256, 0, st>>>(ni, -1.0, d->g, 1.0, d->r);
+  cudaMemsetAsync(d->x, 0, (size_t)ni * sizeof(double), st);
+  if (!dots(d->r, d->r)) return PIC_ECUDA;
+  const double bnorm = std::sqrt(h[1]);
+  int it = 0;
+  double res = bnorm > 0 ? 1.0 : 0.0;
+  if (bnorm > 0) {
+    if (int rc = precond(d->r, d->z)) return rc;
+    cudaMemcpyAsync(d->p, d->z, (size_t)ni * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (!dots(d->r, d->z)) return PIC_ECUDA;
+    double rz = h[0];
+    for (it = 1; it <= maxit; ++it) {
+      k_spmv<<<bw, 256, 0, st>>>(ni, d->a_ptr, d->a_col, d->a_val, d->p, d->q);
+      if (!dots(d->q, d->p)) return PIC_ECUDA;
+      const double alpha = rz / h[0];
+      k_axpby<<<bi, 256, 0, st>>>(ni, alpha, d->p, 1.0, d->x);
+      k_axpby<<<bi, 256, 0, st>>>(ni, -alpha, d->q, 1.0, d->r);
+      if (!dots(d->r, d->r)) return PIC_ECUDA;
+      res = std::sqrt(h[1]) / bnorm;
+      if (res <= rtol) break;
+      if (int rc = precond(d->r, d->z)) return rc;
+      if (!dots(d->z, d->r)) return PIC_ECUDA;
+      const double beta = h[0] / rz;
+      rz = h[0];
+      k_axpby<<<bi, 256, 0, st>>>(ni, 1.0, d->z, beta, d->p);
+    }
+    it = std::min(it, maxit);
+  }
+  // c = T x
+  k_spmv<<<bwf, 256, 0, st>>>(nf, d->t_ptr, d->t_col, d->t_val, d->x, c_full);
+  if (iters) *iters = it;
+  if (relres) *relres = res;
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return PIC_ECUDA;
+  return res <= rtol ? PIC_OK : PIC_ENOCONV;
+}
+
+int pic_web_deposit(pic_web* w, const double* r, const double* z, int64_t n, double qw,
+                    double* f_full) {
+  using namespace pic::web;
+  if (!w || !w->dev || n < 0 || (n > 0 && (!r || !z || !f_full))) return PIC_EINVAL;
+  if (n == 0) return PIC_OK;
+  const Grid D{w->n, w->nr, w->nz, w->mz, w->r_lo, w->G.z0, w->hr, w->hz};
+  k_web_deposit<<<blocks_for(n, 256), 256, 0, w->dev->stream>>>(w->G, D, r, z, n, qw, f_full);
+  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+int pic_web_eval(pic_web* w, const double* c_full, const double* r, const double* z, int64_t n,
+                 int dirichlet, double* phi, double* er, double* ez) {
+  using namespace pic::web;
+  if (!w || !w->dev || n < 0 || (n > 0 && (!c_full || !r || !z))) return PIC_EINVAL;
+  if (n == 0) return PIC_OK;
+  const Grid D{w->n, w->nr, w->nz, w->mz, w->r_lo, w->G.z0, w->hr, w->hz};
+  k_web_eval<<<blocks_for(n, 256), 256, 0, w->dev->stream>>>(w->G, D, c_full, r, z, n,
+                                                             dirichlet, phi, er, ez);
+  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
 }  // extern "C"
