@@ -517,7 +517,7 @@ int pic_spline_create(const pic_config* cfg, int degree, void* cuda_stream, pic_
 }
 
 int pic_spline_solve(pic_spline* s, const double* f, double* c, int dirichlet) {
-  if (!s || !f || !c) return PIC_EINVAL;
+  if (!s || !f || !c || (const double*)c == f) return PIC_EINVAL;
   const spl::Geo& G = s->G;
   const int mr = G.mr, mz = G.mz;
   const long long cells = (long long)mr * mz;
