@@ -608,6 +608,20 @@ int pic_web_deposit(pic_web* w, const double* r, const double* z, int64_t n, dou
 int pic_web_eval(pic_web* w, const double* c, const double* r, const double* z, int64_t n,
                  int dirichlet, double* phi, double* er, double* ez);
 
+/* Potential-well depth (Sec. II.B: a well is a local maximum U_max of the
+ * potential energy along a magnetic field line; its depth is U_max minus
+ * the higher of the lowest values on either side) on the field lines
+ * through (r_start[i], z1), i < lines (host array): each line is sampled
+ * at `samples` equally spaced z over [z_min, z_max] with r^2 B_z(z) kept
+ * (B_z = b0, or b0 (1 + 2 (z - z_mid)^2 / L^2) for bfield_kind 1), cut to
+ * the stretch around z1 inside the domain, U = e phi in eV from the full
+ * coefficients c (DEVICE, mr * mz FP64, with the lift).  depth[i] (eV)
+ * and z_at[i] (z of the deepest well's maximum, NaN if none) are host
+ * arrays.  Synchronises.  PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA. */
+int pic_web_well_depth(pic_web* w, const double* c, const double* r_start, int lines, double z1,
+                       int samples, int bfield_kind, double b0, double z_mid, double L,
+                       double* depth, double* z_at);
+
 #ifdef __cplusplus
 }
 #endif

@@ -128,8 +128,10 @@ def lib() -> ctypes.CDLL:
                                     P(ctypes.c_int), P(c_d)]
         L.pic_web_deposit.argtypes = [vp, vp, vp, c_i64, c_d, vp]
         L.pic_web_eval.argtypes = [vp, vp, vp, vp, c_i64, ctypes.c_int, vp, vp, vp]
+        L.pic_web_well_depth.argtypes = [vp, vp, vp, ctypes.c_int, c_d, ctypes.c_int,
+                                         ctypes.c_int, c_d, c_d, c_d, vp, vp]
         for name in ("pic_web_create", "pic_web_sizes", "pic_web_export", "pic_web_device",
-                     "pic_web_solve", "pic_web_deposit", "pic_web_eval"):
+                     "pic_web_solve", "pic_web_deposit", "pic_web_eval", "pic_web_well_depth"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("pic_spline_matrices", "pic_spline_eigen", "pic_spline_create",
                      "pic_spline_sizes", "pic_spline_solve", "pic_spline_deposit",
@@ -607,6 +609,18 @@ class WebSolver:
                                    int(bool(dirichlet)), float(rtol), int(maxit),
                                    ctypes.byref(it), ctypes.byref(rel)), "pic_web_solve")
         return c, it.value, rel.value
+
+    def well_depth(self, c, r_start, z1: float, samples: int = 2001, bfield_kind: int = 0,
+                   b0: float = 0.28, z_mid: float = 0.0, L: float = 1.0):
+        """(U_d in eV, z of the well's maximum) on the field lines through
+        (r, z1), r in r_start (pic_web_well_depth)."""
+        rs = np.ascontiguousarray(r_start, dtype=np.float64)
+        depth, z_at = np.zeros(len(rs)), np.zeros(len(rs))
+        _check(lib().pic_web_well_depth(self.h, _dev_f64(c, self.mr * self.mz, "c"), _ptr_np(rs),
+                                        len(rs), float(z1), int(samples), int(bfield_kind),
+                                        float(b0), float(z_mid), float(L), _ptr_np(depth),
+                                        _ptr_np(z_at)), "pic_web_well_depth")
+        return depth, z_at
 
     def eval(self, c, r, z, dirichlet: bool = True):
         import torch

@@ -563,6 +563,108 @@ __global__ void k_web_eval(Geo G, Grid D, const double* __restrict__ c,
   }
 }
 
+// the magnetic field of the step on the axis-parallel coordinate: B_z(z)
+// uniform b0, or the mirror b0 (1 + 2 (z - z_mid)^2 / L^2); field lines
+// keep r^2 B_z(z)
+struct BzModel {
+  int kind;
+  double b0, z_mid, L;
+  __device__ double operator()(double z) const {
+    if (kind != 1) return b0;
+    const double s = (z - z_mid) / L;
+    return b0 * (1.0 + 2.0 * s * s);
+  }
+};
+
+__device__ __forceinline__ bool geo_inside(const Geo& G, double r, double z) {
+  bool ok = r > G.a && r < G.b && z > G.z0 && z < G.z1;
+  if (G.ell) {
+    const double x = (r - G.er) / G.edr, y = (z - G.ez) / G.edz;
+    ok = ok && x * x + y * y > 1.0;
+  }
+  return ok;
+}
+
+__device__ __forceinline__ double web_phi(const Geo& G, const Grid& D, const double* c, double r,
+                                          double z) {
+  double ur, uz, Nr[kMaxDeg + 1], dNr[kMaxDeg + 1], Nz[kMaxDeg + 1], dNz[kMaxDeg + 1];
+  const int cr = span(r, D.r_lo, D.hr, D.nr, ur), cz = span(z, D.z0, D.hz, D.nz, uz);
+  span_basis_d(D.n, ur, D.hr, Nr, dNr);
+  span_basis_d(D.n, uz, D.hz, Nz, dNz);
+  double w, wr, wz, pl, pr, pz;
+  G.weight(r, z, w, wr, wz);
+  G.lift(r, z, pl, pr, pz);
+  double s = 0.0;
+  for (int k = 0; k <= D.n; ++k) {
+    const double* row = c + (size_t)(cr + k) * D.mz + cz;
+    for (int l = 0; l <= D.n; ++l) s = fma(row[l], Nr[k] * Nz[l], s);
+  }
+  return pl + w * s;
+}
+
+// Potential-well depth along field lines (one thread per line): samples
+// z_k = z_min + k (z_max - z_min)/(S - 1), r_k = r1 sqrt(B_z(z1)/B_z(z_k));
+// U = e phi (eV) on the stretch around the sample nearest z1 that stays
+// in the domain; the deepest interior local maximum, its depth measured to
+// the higher of the lowest values on either side.  scratch holds S doubles
+// per line (the suffix minima).
+__global__ void k_well_depth(Geo G, Grid D, BzModel B, const double* __restrict__ c,
+                             const double* __restrict__ r_start, int lines, double z1, int S,
+                             double* __restrict__ U, double* __restrict__ smin,
+                             double* __restrict__ depth, double* __restrict__ z_at) {
+  const int line = blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= lines) return;
+  double* u = U + (size_t)line * S;
+  double* sm = smin + (size_t)line * S;
+  const double dz = (G.z1 - G.z0) / (S - 1);
+  const double r1 = r_start[line], b1 = B(z1);
+  int k1 = (int)floor((z1 - G.z0) / dz + 0.5);
+  k1 = min(max(k1, 0), S - 1);
+  depth[line] = 0.0;
+  z_at[line] = nan("");
+  auto rz = [&](int k, double& r, double& z) {
+    z = G.z0 + k * dz;
+    r = r1 * sqrt(b1 / B(z));
+  };
+  double r, z;
+  rz(k1, r, z);
+  if (!geo_inside(G, r, z)) return;
+  int lo = k1, hi = k1;
+  while (lo > 0) {
+    rz(lo - 1, r, z);
+    if (!geo_inside(G, r, z)) break;
+    --lo;
+  }
+  while (hi < S - 1) {
+    rz(hi + 1, r, z);
+    if (!geo_inside(G, r, z)) break;
+    ++hi;
+  }
+  for (int k = lo; k <= hi; ++k) {
+    rz(k, r, z);
+    u[k] = web_phi(G, D, c, r, z);   // U in eV for phi in V
+  }
+  double m = INFINITY;   // suffix minima: sm[k] = min U[k + 1 .. hi]
+  for (int k = hi; k >= lo; --k) {
+    sm[k] = m;
+    m = fmin(m, u[k]);
+  }
+  double left = u[lo], best = 0.0;
+  int arg = -1;
+  for (int k = lo + 1; k < hi; ++k) {
+    if (u[k] >= u[k - 1] && u[k] > u[k + 1]) {
+      const double d = u[k] - fmax(left, sm[k]);
+      if (d > best) {
+        best = d;
+        arg = k;
+      }
+    }
+    left = fmin(left, u[k]);
+  }
+  depth[line] = best;
+  if (arg >= 0) z_at[line] = G.z0 + arg * dz;
+}
+
 inline int blocks_for(long long n, int threads) {
   return (int)std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, 152 * 8));
 }
@@ -713,6 +815,44 @@ int pic_web_solve(pic_web* w, const double* f_full, double* c_full, int dirichle
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return PIC_ECUDA;
   return res <= rtol ? PIC_OK : PIC_ENOCONV;
+}
+
+int pic_web_well_depth(pic_web* w, const double* c, const double* r_start, int lines, double z1,
+                       int samples, int bfield_kind, double b0, double z_mid, double L,
+                       double* depth, double* z_at) {
+  using namespace pic::web;
+  if (!w || !w->dev || !c || !r_start || lines < 1 || samples < 3 || !depth || !z_at ||
+      !(b0 > 0) || (bfield_kind == 1 && !(L > 0)))
+    return PIC_EINVAL;
+  cudaStream_t st = w->dev->stream;
+  const size_t cells = (size_t)lines * samples;
+  double *dr = nullptr, *dU = nullptr, *dS = nullptr, *dd = nullptr, *dza = nullptr;
+  int rc = PIC_OK;
+  if (cudaMalloc(&dr, lines * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dU, cells * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dS, cells * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dd, lines * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dza, lines * sizeof(double)) != cudaSuccess)
+    rc = PIC_ENOMEM;
+  if (!rc && cudaMemcpyAsync(dr, r_start, lines * sizeof(double), cudaMemcpyHostToDevice, st) !=
+                 cudaSuccess)
+    rc = PIC_ECUDA;
+  if (!rc) {
+    const Grid D{w->n, w->nr, w->nz, w->mz, w->r_lo, w->G.z0, w->hr, w->hz};
+    const BzModel B{bfield_kind, b0, z_mid, L};
+    k_well_depth<<<(lines + 127) / 128, 128, 0, st>>>(w->G, D, B, c, dr, lines, z1, samples, dU,
+                                                      dS, dd, dza);
+    if (cudaMemcpyAsync(depth, dd, lines * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(z_at, dza, lines * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      rc = PIC_ECUDA;
+  }
+  for (double* p : {dr, dU, dS, dd, dza})
+    if (p) cudaFree(p);
+  cudaGetLastError();
+  return rc;
 }
 
 int pic_web_deposit(pic_web* w, const double* r, const double* z, int64_t n, double qw,
