@@ -345,3 +345,34 @@ def test_fluid_model_drift_speed_in_the_mirror(cfg):
     out = fluid.fluid_model(c, _fm_moments(c, np.ones(shp), np.ones(shp), np.ones(shp)), Er, Ez)
     assert np.allclose(out[6], n_gas * 1e-20 * vd, rtol=1e-12)
     assert np.allclose(out[8], -fluid.EPS0 * Er * 1.0, rtol=1e-15)
+
+
+def test_rigid_rotor_equilibrium_balances():
+    """Electrons on the circular orbits of the coaxial vacuum field and a
+    uniform B (each with the slow root of m v^2/r + q v B + q E_r = 0): the
+    force terms evaluated from their moments sum to nearly zero (the
+    verification of Sec. IV.A), while F_E and F_B are each far larger."""
+    c = dict(workload("coax_32x64_1e4", precision=64), nr=24, nz=6, b0=0.3, bfield_kind=0,
+             v_inner=-2e3, v_outer=0.0, p_mbar=1e-12)   # inside the Brillouin limit
+    a, b = c["r_in"], c["r_out"]
+    rng = np.random.default_rng(12)
+    npart = 200_000
+    r = np.sqrt(a * a + rng.uniform(0, 1, npart) * (b * b - a * a))
+    z = rng.uniform(c["z_min"], c["z_max"], npart)
+    Er_of = lambda rr: (c["v_inner"] - c["v_outer"]) / (rr * np.log(b / a))
+    q, B = -QE, c["b0"]
+    E = Er_of(r)
+    v = (-q * B - np.sqrt((q * B) ** 2 - 4 * (ME / r) * q * E)) / (2 * ME / r)
+    assert np.all(np.abs(ME * v * v / r + q * v * B + q * E) <= 1e-9 * np.abs(q * E))
+    M = fluid.moments(c, r, z, np.zeros(npart), v, np.zeros(npart), 1e3)
+    R, _ = _RZ(c)
+    T = fluid.force_terms(c, M, Er_of(R), np.zeros_like(R))
+    inner = (slice(2, -2), slice(1, -1))   # away from the walls and the z ends
+    FE, FB, S = T[0, 0][inner], T[1, 0][inner], T[6, 0][inner]
+    scale = np.abs(FE).max()
+    assert np.abs(FB).max() > 0.9 * scale
+    # the centrifugal term is ~2% of F_E here, the sum (discretisation and
+    # sampling) ~0.3%: a dropped or mis-signed term cannot pass
+    assert np.abs(T[2, 0][inner]).max() > 1e-2 * scale
+    assert np.abs(S).max() <= 6e-3 * scale
+    assert np.abs(T[6, 1][inner]).max() <= 1e-6 * scale   # no azimuthal force
