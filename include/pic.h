@@ -101,6 +101,12 @@ typedef struct pic_config {
   double source_rate;      /* volumetric seed source (Sec. II.A): macro-
                               electrons created per second, uniform in the
                               gap's volume, Maxwellian at T0_eV; 0 off */
+  int32_t bspline_degree;  /* 0: bilinear node field; 1..3: the weighted
+                              B-spline field of that degree (pic_spline_*)
+                              with particle shapes from its basis: deposit
+                              w(r) b_i(r) b_j(z), gather the exact -grad
+                              phi.  Single simulations without a seed
+                              source or a fixed field */
 } pic_config;
 
 /* Diagnostics of one simulation (Sec. III.A: peak density and boundary
@@ -525,6 +531,8 @@ int pic_spline_eigen(const pic_config* cfg, int degree, double* V, double* lambd
 int pic_spline_create(const pic_config* cfg, int degree, void* cuda_stream, pic_spline** out);
 void pic_spline_free(pic_spline* s);
 int pic_spline_sizes(const pic_spline* s, int* mr, int* mz);
+/* The stream later calls queue on (NULL: the default stream). */
+int pic_spline_set_stream(pic_spline* s, void* cuda_stream);
 
 /* c = the Galerkin solution for the load f (DEVICE arrays of mr x mz
  * FP64; f is the charge term sum_p q w_p w(r_p) b_i(r_p) b_j(z_p), in C);

@@ -34,6 +34,7 @@ class PicConfig(ctypes.Structure):
         ("sort_every", c_i32), ("poisson_rtol", c_d), ("poisson_maxit", c_i32),
         ("capacity", c_i64), ("seed", c_u64), ("precision", c_i32),
         ("nu_max", c_d), ("fixed_efield", c_i32), ("warm_start", c_i32), ("source_rate", c_d),
+        ("bspline_degree", c_i32),
     ]
 
 
@@ -114,6 +115,7 @@ def lib() -> ctypes.CDLL:
         L.pic_spline_free.argtypes = [vp]
         L.pic_spline_free.restype = None
         L.pic_spline_sizes.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int)]
+        L.pic_spline_set_stream.argtypes = [vp, vp]
         L.pic_spline_solve.argtypes = [vp, vp, vp, ctypes.c_int]
         L.pic_spline_deposit.argtypes = [vp, vp, vp, c_i64, c_d, vp]
         L.pic_spline_eval.argtypes = [vp, vp, vp, vp, c_i64, ctypes.c_int, vp, vp, vp]
@@ -135,7 +137,7 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).restype = ctypes.c_int
         for name in ("pic_spline_matrices", "pic_spline_eigen", "pic_spline_create",
                      "pic_spline_sizes", "pic_spline_solve", "pic_spline_deposit",
-                     "pic_spline_eval"):
+                     "pic_spline_eval", "pic_spline_set_stream"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("pic_init", "pic_load_particles", "pic_step", "pic_diagnostics",
                      "pic_export_particles", "pic_set_efield", "pic_set_cross_sections",
