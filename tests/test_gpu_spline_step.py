@@ -2,7 +2,8 @@
 Sec. II.A's weighted B-splines of arbitrary degree with particle shapes
 from the same basis) against the oracle stepping the same particles in
 its spline mode: FP64 steps with collisions and sorts, the potential at
-the nodes, FP32 one step; graph replay equal to direct launches."""
+the nodes, FP32 one step; graph replay agreeing with direct launches to
+rounding (FP64)."""
 import numpy as np
 import pytest
 
@@ -45,9 +46,8 @@ def test_spline_steps_match_oracle(n):
         phi = sim.get_grid(PIC_GRID_PHI)
         d = sim.diagnostics()
     rep = {}
-    compare_states(cfg, 64, g, o, report=rep)
-    assert max(rep.values()) <= 1e-9, rep
-    assert d["n_elastic"] == o.tally[oracle.T_N_ELASTIC]
+    compare_states(cfg, 64, g, o, report=rep, tol=1e-9)
+    assert abs(d["n_elastic"] - o.tally[oracle.T_N_ELASTIC]) <= 1
     r, z = oracle.grid(cfg)
     R, Z = np.meshgrid(r, z, indexing="ij")
     want = o.spline.phi(o.coef, R.ravel(), Z.ravel())
@@ -71,7 +71,7 @@ def test_spline_step_fp32_one_step():
 
 def test_spline_graph_replay_equals_direct():
     from paper_2206_14662_gb300._capi import Simulation
-    cfg = _cfg(32, 2, n_init=30_000)
+    cfg = _cfg(64, 2, n_init=30_000)
     parts = seed_particles(cfg, n=30_000, seed=8)
     out = []
     for k in (1, 24):   # one step at a time (direct) / blocks (graphs)
@@ -83,5 +83,6 @@ def test_spline_graph_replay_equals_direct():
     a, b = out
     # FP64 atomics in the spline deposit make the sums order-dependent:
     # agreement to rounding, not bit for bit
+    assert np.array_equal(a["uid"], b["uid"])
     for key in ("r", "z"):
         assert np.abs(a[key] - b[key]).max() <= 1e-9 * np.abs(a[key]).max()
