@@ -589,6 +589,11 @@ int pic_web_sizes(const pic_web* w, int* n_inner, int64_t* nnz, int64_t* t_nnz, 
 int pic_web_export(const pic_web* w, int* a_ptr, int* a_col, double* a_val, double* g,
                    int* inner_full, int* t_ptr, int* t_col, double* t_val);
 
+/* A^-1 of the web-spline system (host only; n_inner^2 FP64, row-major,
+ * by dense Cholesky: O(n_inner^3), seconds for a few thousand inner
+ * functions).  PIC_ENOCONV if A is not positive definite. */
+int pic_web_inverse(const pic_web* w, double* out);
+
 /* Device side of a web-spline system on the current CUDA device: copies
  * the system, its extension and T^T to device memory owned by w (freed by
  * pic_web_free), and builds the preconditioner, the weighted B-spline
@@ -606,6 +611,14 @@ int pic_web_device(pic_web* w, void* cuda_stream);
  * iteration.  PIC_ENOCONV if rtol was not met. */
 int pic_web_solve(pic_web* w, const double* f, double* c, int dirichlet, double rtol, int maxit,
                   int* iters, double* relres);
+
+/* Direct solve for time stepping: pic_web_direct (after pic_web_device)
+ * makes A^-1 on the host and keeps it in device memory (n_inner^2 FP64:
+ * 85 MB for 3260 inner functions, inside the L2); pic_web_solve_direct
+ * then queues b = T^T f - [dirichlet] g, u = A^-1 b, c = T u with no host
+ * synchronisation, so the solve can be captured in a CUDA graph. */
+int pic_web_direct(pic_web* w);
+int pic_web_solve_direct(pic_web* w, const double* f, double* c, int dirichlet);
 
 /* f_k += qw w(r_p, z_p) b_k(r_p, z_p) with the web weight (DEVICE arrays;
  * FP64 atomics), and phi, E = -grad phi of full coefficients c at points
