@@ -175,16 +175,57 @@ __device__ __forceinline__ void spl_span_d(Real u, Real* B, Real* dB) {
   for (int r = 0; r <= N; ++r) dB[r] = (r >= 1 ? M[r - 1] : Real(0)) - (r <= N - 1 ? M[r] : Real(0));
 }
 
+// R-function conjunction x + y - sqrt(x^2 + y^2) and its gradient
+template <typename Real>
+__device__ __forceinline__ void r_conj(Real x, Real x0, Real x1, Real y, Real y0, Real y1, Real& v,
+                                       Real& g0, Real& g1) {
+  const Real q = d_sqrt(x * x + y * y), qs = q > Real(0) ? q : Real(1);
+  v = x + y - q;
+  g0 = x0 + y0 - (x * x0 + y * y0) / qs;
+  g1 = x1 + y1 - (x * x1 + y * y1) / qs;
+}
+
+// weight w of the spline field and its gradient, and the gradient of the
+// lift, at (r, z): the walls' w = (r - r_in)(r_out - r)/(r_out - r_in) and
+// the linear lift; with the trap's ellipse the conjunction of that w and
+// w_e = s (x^2 + y^2 - 1) (x, y the normalised offsets), and the lift
+// V_in + dV t, t = (r - r_in)/(r - r_in + w_o), w_o the conjunction of
+// (r_out - r) and w_e
+template <typename Real>
+__device__ __forceinline__ void spl_wl(const PushParams<Real>& P, Real r, Real z, Real& w, Real& wr,
+                                       Real& wz, Real& pr, Real& pz) {
+  const Real wc = (r - P.r_in) * (P.spl_r_out - r) * P.spl_inv_ab;
+  const Real gc = (P.r_in + P.spl_r_out - Real(2) * r) * P.spl_inv_ab;
+  if (!P.spl_ell) {
+    w = wc;
+    wr = gc;
+    wz = Real(0);
+    pr = P.spl_dphi;
+    pz = Real(0);
+    return;
+  }
+  const Real x = (r - P.e_r0) * P.e_idr, y = (z - P.e_z0) * P.e_idz;
+  const Real we = P.e_s * (x * x + y * y - Real(1));
+  const Real ger = P.e_s * Real(2) * x * P.e_idr, gez = P.e_s * Real(2) * y * P.e_idz;
+  r_conj<Real>(wc, gc, Real(0), we, ger, gez, w, wr, wz);
+  Real wo, go0, go1;
+  r_conj<Real>(P.spl_r_out - r, Real(-1), Real(0), we, ger, gez, wo, go0, go1);
+  const Real xa = r - P.r_in, den = xa + wo;
+  pr = P.spl_dv * (den - xa * (Real(1) + go0)) / (den * den);
+  pz = P.spl_dv * (-xa * go1) / (den * den);
+}
+
 // E at a particle from the spline coefficients: E = -grad(phi_D + w sum c
-// b_i b_j), w = (r - r_in)(r_out - r)/(r_out - r_in)
+// b_i b_j)
 template <typename Real, int N>
 __device__ __forceinline__ void spline_gather(const PushParams<Real>& P, int ir, int iz, Real fr,
                                               Real fz, Real r, Real& Er, Real& Ez) {
   Real Br[N + 1], dBr[N + 1], Bz[N + 1], dBz[N + 1];
   spl_span_d<Real, N>(fr, Br, dBr);
   spl_span_d<Real, N>(fz, Bz, dBz);
-  const Real w = (r - P.r_in) * (P.spl_r_out - r) * P.spl_inv_ab;
-  const Real dw = (P.r_in + P.spl_r_out - Real(2) * r) * P.spl_inv_ab;
+  const Real z = mad((Real)iz + fz, P.hz, P.z_min);
+  Real w, wr, wz, pr, pz;
+  spl_wl<Real>(P, r, z, w, wr, wz, pr, pz);
   const Real ihr = P.dt_hr / P.dt, ihz = P.dt_hz / P.dt;   // 1 / h_r, 1 / h_z
   Real sr = 0, sz = 0;
 #pragma unroll
@@ -197,11 +238,11 @@ __device__ __forceinline__ void spline_gather(const PushParams<Real>& P, int ir,
       s0 = mad(c, Bz[l], s0);
       s1 = mad(c, dBz[l], s1);
     }
-    sr = mad(mad(dw, Br[k], w * dBr[k] * ihr), s0, sr);
-    sz = mad(w * Br[k] * ihz, s1, sz);
+    sr = mad(mad(wr, Br[k], w * dBr[k] * ihr), s0, sr);
+    sz = mad(wz * Br[k], s0, mad(w * Br[k] * ihz, s1, sz));
   }
-  Er = -(P.spl_dphi + sr);
-  Ez = -sz;
+  Er = -(pr + sr);
+  Ez = -(pz + sz);
 }
 
 // load of one particle: f_ij += q w w(r) b_i b_j (FP64 atomics)
@@ -212,7 +253,9 @@ __device__ __forceinline__ void spline_deposit(const PushParams<Real>& P, int ir
   spl_span<Real, N>(fr, Br);
   spl_span<Real, N>(fz, Bz);
   const Real r = mad((Real)ir + fr, P.hr, P.r_in);
-  const Real w = (r - P.r_in) * (P.spl_r_out - r) * P.spl_inv_ab;
+  const Real z = mad((Real)iz + fz, P.hz, P.z_min);
+  Real w, wr, wz, pr, pz;
+  spl_wl<Real>(P, r, z, w, wr, wz, pr, pz);
 #pragma unroll
   for (int k = 0; k <= N; ++k) {
     const double wk = P.qw * (double)(w * Br[k]);
@@ -395,7 +438,33 @@ __device__ __forceinline__ Dep<Real> advance(
   const bool out_out = ir1 >= P.nr;
   const bool out_zl = iz1 < 0 || (iz1 == 0 && fz1 == 0);
   const bool out_zh = iz1 >= P.nz;
-  if (out_in || out_out || out_zl || out_zh) {
+  // the trap's ellipse: first entry of the straight (r, z) segment (the
+  // smaller root of the quadratic along it; a start inside enters at 0)
+  bool ell_hit = false;
+  Real te = Real(3);
+  if constexpr (SPL > 0) {
+    if (P.spl_ell) {
+      const Real z0a = mad((Real)iz + fz, P.hz, P.z_min), z1a = mad(vnz, P.dt, z0a);
+      const Real x0 = (r - P.e_r0) * P.e_idr, y0 = (z0a - P.e_z0) * P.e_idz;
+      const Real dx = (r1 - r) * P.e_idr, dy = (z1a - z0a) * P.e_idz;
+      const Real qa = dx * dx + dy * dy, qb = Real(2) * (x0 * dx + y0 * dy);
+      const Real qc = x0 * x0 + y0 * y0 - Real(1);
+      if (qc <= Real(0)) {
+        ell_hit = true;
+        te = Real(0);
+      } else if (qa > Real(0)) {
+        const Real disc = qb * qb - Real(4) * qa * qc;
+        if (disc >= Real(0)) {
+          const Real t = (-qb - d_sqrt(disc)) / (Real(2) * qa);
+          if (t >= Real(0) && t <= Real(1)) {
+            ell_hit = true;
+            te = t;
+          }
+        }
+      }
+    }
+  }
+  if (out_in || out_out || out_zl || out_zh || ell_hit) {
     // first crossing along the straight (r,z) segment, ties in the order
     // inner, outer, z_min, z_max
     const Real s0r = (Real)ir + fr, s0z = (Real)iz + fz;
@@ -405,7 +474,8 @@ __device__ __forceinline__ Dep<Real> advance(
     if (out_out) { const Real t = ((Real)P.nr - s0r) / dr_cells; if (t < tb) { tb = t; wall = 1; } }
     if (out_zl) { const Real t = -s0z / dz_cells; if (t < tb) { tb = t; wall = 2; } }
     if (out_zh) { const Real t = ((Real)P.nz - s0z) / dz_cells; if (t < tb) { tb = t; wall = 3; } }
-    atomicAdd(&bt.v[kAbsInner + wall], 1.0);
+    if (ell_hit && te < tb) wall = 4;
+    atomicAdd(&bt.v[wall == 4 ? (int)kAbsEllipse : kAbsInner + wall], 1.0);
     atomicAdd(&bt.v[kKeAbsorbed], (double)(P.half_m * mad(vnz, vnz, v2p)));
     atomicAdd(&bt.v[kNAbsorbed], 1.0);
     q.cell = -1;
@@ -619,7 +689,7 @@ __device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pus
   if (tid < kTallyCount) {
     double v = bt.v[tid];
     if (v != 0.0) {
-      if (tid <= kAbsZmax) v *= P.weight;
+      if (tid <= kAbsZmax || tid == kAbsEllipse) v *= P.weight;
       else if (tid == kWorkE) v *= (double)P.work_scale * P.weight;
       else if (tid <= kRecoilLoss) v *= P.weight;
       atomicAdd(&st->tally[tid], v);

@@ -38,6 +38,7 @@ enum Tally {
   kNPushed,        // particle-steps taken (live particles advanced)
   kNSource,        // particles created by the seed source
   kKeSource,       // their kinetic energy, J
+  kAbsEllipse,     // absorbed weight on the trap's ellipse
   kTallyCount
 };
 
@@ -139,6 +140,12 @@ struct PushParams {
   const Real* spl_c;
   double* spl_f;
   Real spl_r_out, spl_inv_ab, spl_dphi;
+  // the trap's metal ellipse (spl_ell): centre, inverse semi-axes, the
+  // weight's scale min(dr, dz)/2 and the wall potential difference; the
+  // weight and lift become the web-spline field's and electrons entering
+  // the ellipse are absorbed
+  int spl_ell;
+  Real e_r0, e_z0, e_idr, e_idz, e_s, spl_dv;
 };
 
 // ------------------------------------------------------------- batches
