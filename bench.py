@@ -60,6 +60,7 @@ SCAN = "scan_64x256_64sims"
 UNET = "unet_warmstart_128x512"
 STEADY = "time_to_steady_64sims"
 TABLES = "mirror_128x512_1e7_tables"
+SPLINE = "mirror_128x512_1e7_spline2"
 MOMENTS = "fluid_moments_128x512_1e7"
 # algorithmic bytes per particle of the moment pass: cell 4 + offsets 8 +
 # velocity 12 read (the node grids stay in L2)
@@ -212,6 +213,9 @@ def _inputs(args, rank):
         E, sel, sio, xi = cross_section_tables(cfg["ion_E_th_eV"])
         cfg["xs"] = dict(E_eV=E, sigma_el=sel, sigma_io=sio, xi=xi)
         name = TABLES
+    if args.workload == SPLINE:   # the weighted B-spline field of degree 2
+        cfg["bspline_degree"] = 2
+        name = SPLINE
     return name, [cfg], [seed_particles(cfg)]
 
 
@@ -298,7 +302,7 @@ def run_ours(args, ws, rank):
     kern_ms = prof["particle_ms"] / max(1, prof["particle_launches"])
     per_launch_units = prof_units / max(1, prof["particle_launches"])
     achieved = BYTES_PER_PARTICLE_STEP * per_launch_units / (kern_ms * 1e-3) / 1e9
-    traffic = _traffic_record() if S == 1 and name != TABLES else None
+    traffic = _traffic_record() if S == 1 and name not in (TABLES, SPLINE) else None
     cfg = cfgs[0]
     grid = f"{cfg['nr']}x{cfg['nz']}"
     nnodes = (cfg["nr"] + 1) * (cfg["nz"] + 1)
@@ -338,6 +342,7 @@ def run_ours(args, ws, rank):
         "roofline": {"bound": "hbm",
                      "kernel": ("k_particle_step_batch<float>" if S > 1 else
                                 "k_particle_step<float, 1> (tables)" if name == TABLES else
+                                "k_particle_step<float, 0, 2> (spline field)" if name == SPLINE else
                                 "k_particle_step<float, 0>"),
                      "achieved": achieved,
                      "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
@@ -360,8 +365,10 @@ def run_ours(args, ws, rank):
     if args.cpu_baseline:
         if S == 1:
             # the oracle on at most 2e7 of the particles (a bounded sample)
+            # (the spline oracle evaluates dense basis rows: a small sample)
+            cap = 20_000 if name == SPLINE else 20_000_000
             out["cpu_baseline"] = cpu_baseline(cfg, parts[0], name=name,
-                                               n_sample=min(len(parts[0][0]), 20_000_000))
+                                               n_sample=min(len(parts[0][0]), cap))
         else:
             # the oracle on the largest simulation of the scan, 4 steps
             k = int(np.argmax([len(p[0]) for p in parts]))
@@ -665,7 +672,9 @@ def run_reference(args, ws, rank):
     name = args.workload
     # the scan: its largest simulation (the oracle runs one simulation)
     cfg = workload(name) if name in (WORKLOAD, LARGE) else (
-        workload(WORKLOAD) if name == TABLES else scan_configs()[-1])
+        workload(WORKLOAD) if name in (TABLES, SPLINE) else scan_configs()[-1])
+    if name == SPLINE:
+        cfg["bspline_degree"] = 2
     if name == TABLES:
         E, sel, sio, xi = cross_section_tables(cfg["ion_E_th_eV"])
         cfg["xs"] = dict(E_eV=E, sigma_el=sel, sigma_io=sio, xi=xi)
@@ -755,7 +764,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
-    ap.add_argument("--workload", choices=[WORKLOAD, LARGE, SCAN, UNET, STEADY, TABLES, MOMENTS],
+    ap.add_argument("--workload", choices=[WORKLOAD, LARGE, SCAN, UNET, STEADY, TABLES, MOMENTS,
+                                           SPLINE],
                     default=WORKLOAD)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the workload's sort period and the default kernel grid")
