@@ -60,6 +60,29 @@ SCAN = "scan_64x256_64sims"
 UNET = "unet_warmstart_128x512"
 STEADY = "time_to_steady_64sims"
 TABLES = "mirror_128x512_1e7_tables"
+SPLINE = "mirror_128x512_1e7_spline2"
+TRAP = "trap_36x92_2e6"
+ELLIPSE = (81e-3, 12e-3, 3e-3, 14e-3)
+
+
+def trap_config(**kw):
+    """The trap of Sec. II.B on a 36 x 92 grid: inner conductor 63.75 mm,
+    outer cylinder 81 mm, z from -10 to 34 mm, the metal ellipse centred on
+    the outer cylinder at z = 12 mm (semi-axes 3 mm in r, 14 mm in z),
+    -30 kV bias, a uniform 0.28 T field (the paper's field map is not
+    available), 0.1 mbar, degree-2 web splines."""
+    base = dict(r_in=63.75e-3, r_out=81e-3, z_min=-10e-3, z_max=34e-3, nr=36, nz=92,
+                v_inner=-30e3, v_outer=0.0, bfield_kind=0, b0=0.28, p_mbar=0.1,
+                bspline_degree=2, ellipse=ELLIPSE, n_init=2_000_000, sort_every=20,
+                source_rate=0.0)
+    base.update(kw)
+    return workload(WORKLOAD, **base)
+
+
+def outside_ellipse(parts):
+    r, z = parts[0], parts[1]
+    keep = ((r - ELLIPSE[0]) / ELLIPSE[2]) ** 2 + ((z - ELLIPSE[1]) / ELLIPSE[3]) ** 2 > 1.0
+    return [a[keep] for a in parts]
 MOMENTS = "fluid_moments_128x512_1e7"
 # algorithmic bytes per particle of the moment pass: cell 4 + offsets 8 +
 # velocity 12 read (the node grids stay in L2)
@@ -204,6 +227,11 @@ def _inputs(args, rank):
         cfgs = scan_configs(seed=1 + rank, **over)
         parts = [seed_particles(c, seed=1000 * (rank + 1) + k) for k, c in enumerate(cfgs)]
         return SCAN, cfgs, parts
+    if args.workload == TRAP:
+        cfg = trap_config(seed=1 + rank, **over)
+        if args.particles:
+            cfg["n_init"] = args.particles
+        return TRAP, [cfg], [outside_ellipse(seed_particles(cfg))]
     name = LARGE if args.workload == LARGE else WORKLOAD
     cfg = workload(name, seed=1 + rank, **over)
     if args.particles:
@@ -212,6 +240,9 @@ def _inputs(args, rank):
         E, sel, sio, xi = cross_section_tables(cfg["ion_E_th_eV"])
         cfg["xs"] = dict(E_eV=E, sigma_el=sel, sigma_io=sio, xi=xi)
         name = TABLES
+    if args.workload == SPLINE:   # the weighted B-spline field of degree 2
+        cfg["bspline_degree"] = 2
+        name = SPLINE
     return name, [cfg], [seed_particles(cfg)]
 
 
@@ -298,7 +329,7 @@ def run_ours(args, ws, rank):
     kern_ms = prof["particle_ms"] / max(1, prof["particle_launches"])
     per_launch_units = prof_units / max(1, prof["particle_launches"])
     achieved = BYTES_PER_PARTICLE_STEP * per_launch_units / (kern_ms * 1e-3) / 1e9
-    traffic = _traffic_record() if S == 1 and name != TABLES else None
+    traffic = _traffic_record() if S == 1 and name not in (TABLES, SPLINE, TRAP) else None
     cfg = cfgs[0]
     grid = f"{cfg['nr']}x{cfg['nz']}"
     nnodes = (cfg["nr"] + 1) * (cfg["nz"] + 1)
@@ -338,6 +369,8 @@ def run_ours(args, ws, rank):
         "roofline": {"bound": "hbm",
                      "kernel": ("k_particle_step_batch<float>" if S > 1 else
                                 "k_particle_step<float, 1> (tables)" if name == TABLES else
+                                "k_particle_step<float, 0, 2> (spline field)" if name == SPLINE else
+                                "k_particle_step<float, 0, 2> (trap, web-spline field)" if name == TRAP else
                                 "k_particle_step<float, 0>"),
                      "achieved": achieved,
                      "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
@@ -360,8 +393,10 @@ def run_ours(args, ws, rank):
     if args.cpu_baseline:
         if S == 1:
             # the oracle on at most 2e7 of the particles (a bounded sample)
+            # (the spline oracle evaluates dense basis rows: a small sample)
+            cap = 20_000 if name in (SPLINE, TRAP) else 20_000_000
             out["cpu_baseline"] = cpu_baseline(cfg, parts[0], name=name,
-                                               n_sample=min(len(parts[0][0]), 20_000_000))
+                                               n_sample=min(len(parts[0][0]), cap))
         else:
             # the oracle on the largest simulation of the scan, 4 steps
             k = int(np.argmax([len(p[0]) for p in parts]))
@@ -665,12 +700,19 @@ def run_reference(args, ws, rank):
     name = args.workload
     # the scan: its largest simulation (the oracle runs one simulation)
     cfg = workload(name) if name in (WORKLOAD, LARGE) else (
-        workload(WORKLOAD) if name == TABLES else scan_configs()[-1])
+        workload(WORKLOAD) if name in (TABLES, SPLINE) else scan_configs()[-1])
+    if name == SPLINE:
+        cfg["bspline_degree"] = 2
+    if name == TRAP:
+        cfg = trap_config()
     if name == TABLES:
         E, sel, sio, xi = cross_section_tables(cfg["ion_E_th_eV"])
         cfg["xs"] = dict(E_eV=E, sigma_el=sel, sigma_io=sio, xi=xi)
     n = 20_000
     parts = seed_particles(cfg, n=n)
+    if name == TRAP:
+        parts = outside_ellipse(parts)
+        n = len(parts[0])
     o = oracle.OracleSim(cfg, *parts)
     for _ in range(args.warmup):
         o.step()
@@ -755,7 +797,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
-    ap.add_argument("--workload", choices=[WORKLOAD, LARGE, SCAN, UNET, STEADY, TABLES, MOMENTS],
+    ap.add_argument("--workload", choices=[WORKLOAD, LARGE, SCAN, UNET, STEADY, TABLES, MOMENTS,
+                                           SPLINE, TRAP],
                     default=WORKLOAD)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the workload's sort period and the default kernel grid")

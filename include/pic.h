@@ -101,6 +101,18 @@ typedef struct pic_config {
   double source_rate;      /* volumetric seed source (Sec. II.A): macro-
                               electrons created per second, uniform in the
                               gap's volume, Maxwellian at T0_eV; 0 off */
+  int32_t bspline_degree;  /* 0: bilinear node field; 1..3: the weighted
+                              B-spline field of that degree (pic_spline_*)
+                              with particle shapes from its basis: deposit
+                              w(r) b_i(r) b_j(z), gather the exact -grad
+                              phi.  Single simulations without a seed
+                              source or a fixed field */
+  int32_t has_ellipse;     /* 1: a filled metal ellipse at the outer
+                              wall's potential (Sec. II.B's trap), needs
+                              bspline_degree > 0: the field is the
+                              web-spline field (pic_web_*, direct solve)
+                              and electrons entering it are absorbed */
+  double ellipse[4];       /* r centre, z centre, r semi-axis, z semi-axis, m */
 } pic_config;
 
 /* Diagnostics of one simulation (Sec. III.A: peak density and boundary
@@ -144,6 +156,9 @@ typedef struct pic_diag {
                                     ke_total - ke_initial - (work_E -
                                     ke_absorbed - ion_loss - recoil_loss +
                                     ke_source)) */
+  double I_ellipse;              /* electron current into the ellipse, A
+                                    (averaged as the wall currents) */
+  double absorbed_ellipse;       /* cumulative electrons absorbed by it */
 } pic_diag;
 
 typedef struct pic_handle pic_handle;
@@ -529,6 +544,8 @@ void pic_spline_free(pic_spline* s);
 /* mr = nr + degree and mz = nz + degree (either pointer may be NULL).
  * PIC_EINVAL on a NULL solver. */
 int pic_spline_sizes(const pic_spline* s, int* mr, int* mz);
+/* The stream later calls queue on (NULL: the default stream). */
+int pic_spline_set_stream(pic_spline* s, void* cuda_stream);
 
 /* c = the Galerkin solution for the load f (DEVICE arrays of mr x mz
  * FP64; f is the charge term sum_p q w_p w(r_p) b_i(r_p) b_j(z_p), in C);
@@ -619,6 +636,8 @@ int pic_web_solve(pic_web* w, const double* f, double* c, int dirichlet, double 
  * then queues b = T^T f - [dirichlet] g, u = A^-1 b, c = T u with no host
  * synchronisation, so the solve can be captured in a CUDA graph. */
 int pic_web_direct(pic_web* w);
+/* The stream later device calls queue on (after pic_web_device). */
+int pic_web_set_stream(pic_web* w, void* cuda_stream);
 int pic_web_solve_direct(pic_web* w, const double* f, double* c, int dirichlet);
 
 /* f_k += qw w(r_p, z_p) b_k(r_p, z_p) with the web weight (DEVICE arrays;

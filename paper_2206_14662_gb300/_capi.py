@@ -34,6 +34,7 @@ class PicConfig(ctypes.Structure):
         ("sort_every", c_i32), ("poisson_rtol", c_d), ("poisson_maxit", c_i32),
         ("capacity", c_i64), ("seed", c_u64), ("precision", c_i32),
         ("nu_max", c_d), ("fixed_efield", c_i32), ("warm_start", c_i32), ("source_rate", c_d),
+        ("bspline_degree", c_i32), ("has_ellipse", c_i32), ("ellipse", c_d * 4),
     ]
 
 
@@ -50,7 +51,8 @@ class PicDiag(ctypes.Structure):
         ("ledger_residual_J", c_d), ("n_peak", c_d), ("poisson_iters", c_i32),
         ("poisson_relres", c_d), ("poisson_relres_charge", c_d), ("nu_max", c_d),
         ("weight", c_d), ("error", c_i32), ("poisson_relres_init", c_d),
-        ("n_source", c_i64), ("ke_source_J", c_d),
+        ("n_source", c_i64), ("ke_source_J", c_d), ("I_ellipse", c_d),
+        ("absorbed_ellipse", c_d),
     ]
 
 
@@ -114,6 +116,7 @@ def lib() -> ctypes.CDLL:
         L.pic_spline_free.argtypes = [vp]
         L.pic_spline_free.restype = None
         L.pic_spline_sizes.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int)]
+        L.pic_spline_set_stream.argtypes = [vp, vp]
         L.pic_spline_solve.argtypes = [vp, vp, vp, ctypes.c_int]
         L.pic_spline_deposit.argtypes = [vp, vp, vp, c_i64, c_d, vp]
         L.pic_spline_eval.argtypes = [vp, vp, vp, vp, c_i64, ctypes.c_int, vp, vp, vp]
@@ -132,14 +135,16 @@ def lib() -> ctypes.CDLL:
                                          ctypes.c_int, c_d, c_d, c_d, vp, vp]
         L.pic_web_inverse.argtypes = [vp, vp]
         L.pic_web_direct.argtypes = [vp]
+        L.pic_web_set_stream.argtypes = [vp, vp]
         L.pic_web_solve_direct.argtypes = [vp, vp, vp, ctypes.c_int]
         for name in ("pic_web_create", "pic_web_sizes", "pic_web_export", "pic_web_device",
                      "pic_web_solve", "pic_web_deposit", "pic_web_eval", "pic_web_well_depth",
-                     "pic_web_inverse", "pic_web_direct", "pic_web_solve_direct"):
+                     "pic_web_inverse", "pic_web_direct", "pic_web_solve_direct",
+                     "pic_web_set_stream"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("pic_spline_matrices", "pic_spline_eigen", "pic_spline_create",
                      "pic_spline_sizes", "pic_spline_solve", "pic_spline_deposit",
-                     "pic_spline_eval"):
+                     "pic_spline_eval", "pic_spline_set_stream"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("pic_init", "pic_load_particles", "pic_step", "pic_diagnostics",
                      "pic_export_particles", "pic_set_efield", "pic_set_cross_sections",
@@ -160,7 +165,12 @@ def make_config(cfg: dict) -> PicConfig:
     """pic_config from a workload dict (keys are the struct's field names;
     other keys are ignored)."""
     c = PicConfig()
+    if cfg.get("ellipse") is not None:   # (r0, z0, dr, dz) of the trap's ellipse
+        c.has_ellipse = 1
+        c.ellipse = (c_d * 4)(*[float(v) for v in cfg["ellipse"]])
     for name, ctype in PicConfig._fields_:
+        if name in ("ellipse", "has_ellipse"):
+            continue
         if name in cfg:
             setattr(c, name, ctype(cfg[name]).value if ctype in (c_i32, c_i64, c_u64) else float(cfg[name]))
     return c

@@ -42,6 +42,7 @@ struct SimHost {
   long long capacity, spawn_cap, base;
   double ke_initial;
   double last_abs[4];
+  double last_abs_ell = 0.0;
   long long last_diag_step;
 };
 
@@ -129,6 +130,16 @@ struct pic_handle {
 
   std::vector<PushParams<float>> Pf;   // per simulation
   std::vector<PushParams<double>> Pd;
+
+  // weighted B-spline field (bspline_degree > 0, single simulation): the
+  // solver, the FP64 load grid and coefficients (mr x mz), and the
+  // coefficients in the particle precision for the gather
+  pic_spline* spl = nullptr;
+  pic_web* web = nullptr;           // has_ellipse: the web-spline field instead
+  double* spl_f = nullptr;
+  double* spl_c = nullptr;
+  void* spl_cr = nullptr;
+  int spl_cells = 0;
 };
 
 namespace {
@@ -233,6 +244,10 @@ int validate(const pic_config& c) {
   if (!(c.poisson_rtol > 0) || c.poisson_maxit < 0 || c.poisson_maxit > 64) return PIC_EINVAL;
   if (c.warm_start < 0 || c.warm_start > 2) return PIC_EINVAL;
   if (!(c.source_rate >= 0) || !std::isfinite(c.source_rate)) return PIC_EINVAL;
+  if (c.bspline_degree < 0 || c.bspline_degree > 3) return PIC_EINVAL;
+  if (c.bspline_degree > 0 && (c.source_rate > 0 || c.fixed_efield)) return PIC_EINVAL;
+  if (c.has_ellipse && (c.bspline_degree <= 0 || !(c.ellipse[2] > 0) || !(c.ellipse[3] > 0)))
+    return PIC_EINVAL;
   if (c.source_rate > 0 && !(c.T0_eV > 0)) return PIC_EINVAL;
   // the Thomas sweep keeps four (nr - 1) x 32 float columns in shared memory
   if ((long long)4 * (c.nr - 1) * 32 * 4 > 200 * 1024) return PIC_EINVAL;
@@ -317,6 +332,68 @@ void fill_params(pic_handle* h, int k, PushParams<Real>& P) {
   P.hr_d = h->hr;
   P.z_min_d = c.z_min;
   P.hz_d = h->hz;
+  const bool spl = (h->spl || h->web) && h->prec == (int)(8 * sizeof(Real));
+  P.spl_n = spl ? c.bspline_degree : 0;
+  P.spl_mz = c.nz + c.bspline_degree;
+  P.spl_c = spl ? (const Real*)h->spl_cr : nullptr;
+  P.spl_f = spl ? h->spl_f : nullptr;
+  P.spl_r_out = (Real)c.r_out;
+  P.spl_inv_ab = (Real)(1.0 / (c.r_out - c.r_in));
+  P.spl_dphi = (Real)((c.v_outer - c.v_inner) / (c.r_out - c.r_in));
+  P.spl_ell = spl && h->web ? 1 : 0;
+  P.e_r0 = (Real)c.ellipse[0];
+  P.e_z0 = (Real)c.ellipse[1];
+  P.e_idr = (Real)(c.ellipse[2] > 0 ? 1.0 / c.ellipse[2] : 0.0);
+  P.e_idz = (Real)(c.ellipse[3] > 0 ? 1.0 / c.ellipse[3] : 0.0);
+  P.e_s = (Real)(0.5 * std::min(c.ellipse[2], c.ellipse[3]));
+  P.spl_dv = (Real)(c.v_outer - c.v_inner);
+}
+
+// spline mode: the solver on the handle's geometry and its grids
+int spline_setup(pic_handle* h) {
+  const pic_config& c = h->cfg;
+  int mr = 0, mz = 0;
+  if (c.has_ellipse) {
+    // the trap: web-spline system on the gap's grid, solved through its
+    // dense inverse kept on the device (graph-capturable)
+    int rc = pic_web_create(&c, c.ellipse, c.r_in, c.r_out, c.nr, c.bspline_degree, &h->web);
+    if (!rc) rc = pic_web_device(h->web, h->stream);
+    if (!rc) rc = pic_web_direct(h->web);
+    if (rc) return rc;
+    pic_web_sizes(h->web, nullptr, nullptr, nullptr, &mr, &mz);
+  } else {
+    const int rc = pic_spline_create(&c, c.bspline_degree, h->stream, &h->spl);
+    if (rc) return rc;
+    pic_spline_sizes(h->spl, &mr, &mz);
+  }
+  h->spl_cells = mr * mz;
+  const size_t cells = (size_t)h->spl_cells;
+  h->spl_f = (double*)h_alloc(cells * sizeof(double), h);
+  h->spl_c = (double*)h_alloc(cells * sizeof(double), h);
+  h->spl_cr = h_alloc(cells * (h->prec == 32 ? sizeof(float) : sizeof(double)), h);
+  if (!h->spl_f || !h->spl_c || !h->spl_cr) return PIC_ENOMEM;
+  return cudaMemsetAsync(h->spl_f, 0, cells * sizeof(double), h->stream) == cudaSuccess
+             ? PIC_OK
+             : PIC_ECUDA;
+}
+
+// spline mode: coefficients of the load in spl_f (solve on the handle's
+// current stream) and their copy in the particle precision
+int spline_solve_into(pic_handle* h) {
+  int rc;
+  if (h->web) {
+    pic_web_set_stream(h->web, h->stream);
+    rc = pic_web_solve_direct(h->web, h->spl_f, h->spl_c, 1);
+  } else {
+    pic_spline_set_stream(h->spl, h->stream);
+    rc = pic_spline_solve(h->spl, h->spl_f, h->spl_c, 1);
+  }
+  if (rc) return rc;
+  if (h->prec == 32)
+    launch_spline_coef<float>(h->spl_c, (float*)h->spl_cr, h->spl_cells, h->stream);
+  else
+    launch_spline_coef<double>(h->spl_c, (double*)h->spl_cr, h->spl_cells, h->stream);
+  return PIC_OK;
 }
 
 template <typename Real>
@@ -406,6 +483,8 @@ int step_impl(pic_handle* h, long long nsteps) {
     if (!fp32) {
       CK(cudaMemsetAsync(h->rhs, 0, grid_nodes * sizeof(double), h->stream));
     }
+    if (h->spl || h->web)
+      CK(cudaMemsetAsync(h->spl_f, 0, (size_t)h->spl_cells * sizeof(double), h->stream));
     if (batch)
       launch_particle_step_batch<Real>(soa<Real>(h, h->cur), h->efield, fp32 ? nullptr : h->rhs,
                                        fp32 ? h->cnt[h->dep_buf] : nullptr, h->st,
@@ -458,7 +537,14 @@ int step_impl(pic_handle* h, long long nsteps) {
       if (rc) return rc;
       h->kernels += unet_kernels_per_forward(h->net) + 2;
     }
-    if (solve) {
+    if (solve && (h->spl || h->web)) {
+      const int rc = spline_solve_into(h);
+      if (rc) return rc;
+      // spline: lift, two transforms, band solves; web: T^T f - g, A^-1 b,
+      // T u; and the precision copy
+      h->kernels += h->web ? 4 : 5;
+      mark(h, kTagField);
+    } else if (solve) {
       if (fp32)
         launch_field_solve<Real>(h->T, nullptr, h->cnt[h->dep_buf],
                                  -kQe * h->sims[0].weight / kFixUnit,
@@ -538,6 +624,29 @@ const char* pic_strerror(int code) {
   }
 }
 
+namespace {
+// spline mode: load the stored particles (deposit = true) or none, solve,
+// and wait
+int spline_refresh(pic_handle* h, bool deposit) {
+  const size_t cells = (size_t)h->spl_cells;
+  if (cudaMemsetAsync(h->spl_f, 0, cells * sizeof(double), h->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  if (deposit) {
+    if (h->prec == 32)
+      launch_spline_deposit_store<float>(sim_soa<float>(h, 0, h->cur), h->st, h->Pf[0],
+                                         h->sims[0].capacity, h->stream);
+    else
+      launch_spline_deposit_store<double>(sim_soa<double>(h, 0, h->cur), h->st, h->Pd[0],
+                                          h->sims[0].capacity, h->stream);
+  }
+  const int rc = spline_solve_into(h);
+  if (rc) return rc;
+  return cudaStreamSynchronize(h->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess
+             ? PIC_OK
+             : PIC_ECUDA;
+}
+}  // namespace
+
 int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
              const pic_allocator* alloc, pic_handle** out) {
   if (!cfg || !out) return PIC_EINVAL;
@@ -549,6 +658,7 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
   }
   int rc = validate_batch(cfg, n_sims);
   if (rc) return rc;
+  if (cfg[0].bspline_degree > 0 && n_sims > 1) return PIC_EINVAL;
   pic_handle* h = new (std::nothrow) pic_handle();
   if (!h) return PIC_ENOMEM;
   h->cfg = cfg[0];
@@ -640,6 +750,7 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
               !h->phi || !h->efield || !h->scratch2))
     rc = PIC_ENOMEM;
   if (!rc) rc = field_tables_build(h->cfgs.data(), n_sims, h->T, h_alloc, h, h->stream);
+  if (!rc && c.bspline_degree > 0) rc = spline_setup(h);
   if (!rc) {
     h->Pf.resize(n_sims);
     h->Pd.resize(n_sims);
@@ -684,6 +795,7 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
                                  h->stream);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = PIC_ECUDA;
   }
+  if (!rc && (h->spl || h->web)) rc = spline_refresh(h, false);   // vacuum spline field
   if (rc) {
     pic_free(h);
     return rc;
@@ -718,6 +830,8 @@ void pic_free(pic_handle* h) {
   }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  pic_spline_free(h->spl);
+  pic_web_free(h->web);
   for (void* p : h->owned) h_free_one(p, h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -826,6 +940,7 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
         cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
       rc = PIC_ECUDA;
     m.ke_initial = 0.5 * kMe * ke[0] * m.weight;
+    if (!rc && (h->spl || h->web)) rc = spline_refresh(h, true);
   } else {
     cudaStreamSynchronize(h->stream);
   }
@@ -838,6 +953,7 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
   }
   m.last_diag_step = h->step;
   for (double& a : m.last_abs) a = 0.0;
+  m.last_abs_ell = 0.0;
   return rc;
 }
 
@@ -922,6 +1038,7 @@ int pic_step(pic_handle* h, int64_t nsteps) {
 
 int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
   if (!h || sim < 0 || sim >= h->nsim || !out) return PIC_EINVAL;
+  if (density && (h->spl || h->web)) return PIC_EINVAL;   // no node deposit in spline mode
   const pic_config& c = h->cfgs[sim];
   SimHost& m = h->sims[sim];
   DevState s;
@@ -955,6 +1072,9 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
     *I[w] = dtw > 0 ? (s.tally[kAbsInner + w] - m.last_abs[w]) * kQe / dtw : 0.0;
     m.last_abs[w] = s.tally[kAbsInner + w];
   }
+  out->absorbed_ellipse = s.tally[kAbsEllipse];
+  out->I_ellipse = dtw > 0 ? (s.tally[kAbsEllipse] - m.last_abs_ell) * kQe / dtw : 0.0;
+  m.last_abs_ell = s.tally[kAbsEllipse];
   m.last_diag_step = h->step;
   out->n_elastic = (int64_t)s.tally[kNElastic];
   out->n_ionise = (int64_t)s.tally[kNIonise];
@@ -1288,6 +1408,39 @@ int pic_get_grid(pic_handle* h, int sim, int which, double* out) {
   const size_t bytes = (size_t)h->nnodes * sizeof(double);
   const size_t eo = (size_t)sim * h->nnodes * (h->prec == 32 ? sizeof(float2) : sizeof(double2));
   const void* efield = (const char*)h->efield + eo;
+  if (h->spl || h->web) {
+    // spline mode: phi or E at the nodes from the coefficients
+    if (which != PIC_GRID_PHI && which != PIC_GRID_ER && which != PIC_GRID_EZ) return PIC_EINVAL;
+    double* d = (double*)h_alloc(3 * bytes, h);
+    if (!d) return PIC_ENOMEM;
+    std::vector<double> nr_(h->nnodes), nz_(h->nnodes);
+    for (int i = 0; i <= h->cfg.nr; ++i)
+      for (int j = 0; j <= h->cfg.nz; ++j) {
+        nr_[(size_t)i * (h->cfg.nz + 1) + j] = std::min(h->cfg.r_in + i * h->hr, h->cfg.r_out);
+        nz_[(size_t)i * (h->cfg.nz + 1) + j] = std::min(h->cfg.z_min + j * h->hz, h->cfg.z_max);
+      }
+    double* dr = d + h->nnodes;
+    double* dz = d + 2 * (size_t)h->nnodes;
+    int rc = PIC_OK;
+    if (h->web) pic_web_set_stream(h->web, h->stream);
+    else pic_spline_set_stream(h->spl, h->stream);
+    if (cudaMemcpyAsync(dr, nr_.data(), bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dz, nz_.data(), bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      rc = PIC_ECUDA;
+    double* o_phi = which == PIC_GRID_PHI ? d : nullptr;
+    double* o_er = which == PIC_GRID_ER ? d : nullptr;
+    double* o_ez = which == PIC_GRID_EZ ? d : nullptr;
+    if (!rc)
+      rc = h->web ? pic_web_eval(h->web, h->spl_c, dr, dz, h->nnodes, 1, o_phi, o_er, o_ez)
+                  : pic_spline_eval(h->spl, h->spl_c, dr, dz, h->nnodes, 1, o_phi, o_er, o_ez);
+    if (!rc && (cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess))
+      rc = PIC_ECUDA;
+    auto it = std::find(h->owned.begin(), h->owned.end(), (void*)d);
+    if (it != h->owned.end()) h->owned.erase(it);
+    h_free_one(d, h);
+    return rc ? rc : check_sticky(h);
+  }
   if (which == PIC_GRID_RHS) {
     const int rr = read_rho(h, sim, out);
     return rr ? rr : check_sticky(h);
@@ -1470,6 +1623,9 @@ int pic_restore(pic_handle* h, const char* path) {
   std::copy(labs, labs + 4, h->sims[0].last_abs);
   h->sims[0].last_diag_step = lds;
   h->sticky = s.err;
+  // spline mode: the field of the restored particles (the checkpoint holds
+  // the node grids only)
+  if (h->spl || h->web) return spline_refresh(h, true);
   return PIC_OK;
 }
 

@@ -145,6 +145,126 @@ __device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a,
 __device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ double q_rsqrt(double a) { return 1.0 / sqrt(a); }
 
+// Weighted B-spline field of degree N (the step's spline mode): the span
+// of a particle is its cell and the local coordinate its offset, so the N
+// + 1 non-zero B-splines per direction come from the triangular Cox-de
+// Boor scheme at the offset (distances in cells, denominators j).
+template <typename Real, int N>
+__device__ __forceinline__ void spl_span(Real u, Real* B) {
+  B[0] = Real(1);
+#pragma unroll
+  for (int j = 1; j <= N; ++j) {
+    Real saved = Real(0);
+#pragma unroll
+    for (int r = 0; r < j; ++r) {
+      const Real tmp = B[r] * (Real(1) / Real(j));
+      B[r] = saved + (Real(r + 1) - u) * tmp;
+      saved = (u + Real(j - r - 1)) * tmp;
+    }
+    B[j] = saved;
+  }
+}
+
+// values and derivatives per cell width (d/du) of the span's functions
+template <typename Real, int N>
+__device__ __forceinline__ void spl_span_d(Real u, Real* B, Real* dB) {
+  Real M[N > 0 ? N : 1];
+  spl_span<Real, N>(u, B);
+  spl_span<Real, N - 1>(u, M);
+#pragma unroll
+  for (int r = 0; r <= N; ++r) dB[r] = (r >= 1 ? M[r - 1] : Real(0)) - (r <= N - 1 ? M[r] : Real(0));
+}
+
+// R-function conjunction x + y - sqrt(x^2 + y^2) and its gradient
+template <typename Real>
+__device__ __forceinline__ void r_conj(Real x, Real x0, Real x1, Real y, Real y0, Real y1, Real& v,
+                                       Real& g0, Real& g1) {
+  const Real q = d_sqrt(x * x + y * y), qs = q > Real(0) ? q : Real(1);
+  v = x + y - q;
+  g0 = x0 + y0 - (x * x0 + y * y0) / qs;
+  g1 = x1 + y1 - (x * x1 + y * y1) / qs;
+}
+
+// weight w of the spline field and its gradient, and the gradient of the
+// lift, at (r, z): the walls' w = (r - r_in)(r_out - r)/(r_out - r_in) and
+// the linear lift; with the trap's ellipse the conjunction of that w and
+// w_e = s (x^2 + y^2 - 1) (x, y the normalised offsets), and the lift
+// V_in + dV t, t = (r - r_in)/(r - r_in + w_o), w_o the conjunction of
+// (r_out - r) and w_e
+template <typename Real>
+__device__ __forceinline__ void spl_wl(const PushParams<Real>& P, Real r, Real z, Real& w, Real& wr,
+                                       Real& wz, Real& pr, Real& pz) {
+  const Real wc = (r - P.r_in) * (P.spl_r_out - r) * P.spl_inv_ab;
+  const Real gc = (P.r_in + P.spl_r_out - Real(2) * r) * P.spl_inv_ab;
+  if (!P.spl_ell) {
+    w = wc;
+    wr = gc;
+    wz = Real(0);
+    pr = P.spl_dphi;
+    pz = Real(0);
+    return;
+  }
+  const Real x = (r - P.e_r0) * P.e_idr, y = (z - P.e_z0) * P.e_idz;
+  const Real we = P.e_s * (x * x + y * y - Real(1));
+  const Real ger = P.e_s * Real(2) * x * P.e_idr, gez = P.e_s * Real(2) * y * P.e_idz;
+  r_conj<Real>(wc, gc, Real(0), we, ger, gez, w, wr, wz);
+  Real wo, go0, go1;
+  r_conj<Real>(P.spl_r_out - r, Real(-1), Real(0), we, ger, gez, wo, go0, go1);
+  const Real xa = r - P.r_in, den = xa + wo;
+  pr = P.spl_dv * (den - xa * (Real(1) + go0)) / (den * den);
+  pz = P.spl_dv * (-xa * go1) / (den * den);
+}
+
+// E at a particle from the spline coefficients: E = -grad(phi_D + w sum c
+// b_i b_j)
+template <typename Real, int N>
+__device__ __forceinline__ void spline_gather(const PushParams<Real>& P, int ir, int iz, Real fr,
+                                              Real fz, Real r, Real& Er, Real& Ez) {
+  Real Br[N + 1], dBr[N + 1], Bz[N + 1], dBz[N + 1];
+  spl_span_d<Real, N>(fr, Br, dBr);
+  spl_span_d<Real, N>(fz, Bz, dBz);
+  const Real z = mad((Real)iz + fz, P.hz, P.z_min);
+  Real w, wr, wz, pr, pz;
+  spl_wl<Real>(P, r, z, w, wr, wz, pr, pz);
+  const Real ihr = P.dt_hr / P.dt, ihz = P.dt_hz / P.dt;   // 1 / h_r, 1 / h_z
+  Real sr = 0, sz = 0;
+#pragma unroll
+  for (int k = 0; k <= N; ++k) {
+    const Real* row = P.spl_c + (size_t)(ir + k) * P.spl_mz + iz;
+    Real s0 = 0, s1 = 0;
+#pragma unroll
+    for (int l = 0; l <= N; ++l) {
+      const Real c = __ldg(row + l);
+      s0 = mad(c, Bz[l], s0);
+      s1 = mad(c, dBz[l], s1);
+    }
+    sr = mad(mad(wr, Br[k], w * dBr[k] * ihr), s0, sr);
+    sz = mad(wz * Br[k], s0, mad(w * Br[k] * ihz, s1, sz));
+  }
+  Er = -(pr + sr);
+  Ez = -(pz + sz);
+}
+
+// load of one particle: f_ij += q w w(r) b_i b_j (FP64 atomics)
+template <typename Real, int N>
+__device__ __forceinline__ void spline_deposit(const PushParams<Real>& P, int ir, int iz, Real fr,
+                                               Real fz) {
+  Real Br[N + 1], Bz[N + 1];
+  spl_span<Real, N>(fr, Br);
+  spl_span<Real, N>(fz, Bz);
+  const Real r = mad((Real)ir + fr, P.hr, P.r_in);
+  const Real z = mad((Real)iz + fz, P.hz, P.z_min);
+  Real w, wr, wz, pr, pz;
+  spl_wl<Real>(P, r, z, w, wr, wz, pr, pz);
+#pragma unroll
+  for (int k = 0; k <= N; ++k) {
+    const double wk = P.qw * (double)(w * Br[k]);
+    double* row = P.spl_f + (size_t)(ir + k) * P.spl_mz + iz;
+#pragma unroll
+    for (int l = 0; l <= N; ++l) atomicAdd(row + l, wk * (double)Bz[l]);
+  }
+}
+
 template <typename Real>
 struct Part {
   int cell;
@@ -156,7 +276,7 @@ struct Part {
 // scattering or ionisation with a child appended.  q holds the state after
 // the move.  The draw-0 Philox block is recomputed here, so the common path
 // carries only the candidate flag.
-template <typename Real, bool TAB>
+template <typename Real, bool TAB, int SPL>
 __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, unsigned uid_hi,
                                         const Soa<Real>& s,
                                      const DepGrid& g, DevState* st, unsigned* spawn_parent,
@@ -225,7 +345,10 @@ __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, unsigned ui
     s.vz[slot] = s2 * d2z;
     s.uid[slot] = 0u;   // fixed by the child-uid kernel
     spawn_parent[k] = uid;
-    deposit_global(g, q.cell >> 16, q.cell & 0xFFFF, q.fr, q.fz);
+    if constexpr (SPL == 0)
+      deposit_global(g, q.cell >> 16, q.cell & 0xFFFF, q.fr, q.fz);
+    else
+      spline_deposit<Real, SPL>(P, q.cell >> 16, q.cell & 0xFFFF, q.fr, q.fz);
   } else {
     set_error(st, PIC_ECAPACITY);
   }
@@ -238,7 +361,7 @@ __device__ __forceinline__ void collide(Part<Real>& q, unsigned uid, unsigned ui
 // automatic contraction, so each particle is computed by the same sequence
 // of roundings whichever slot of its thread it occupies (results do not
 // depend on the particle order the sort leaves).
-template <typename Real, bool TAB>
+template <typename Real, bool TAB, int SPL>
 __device__ __forceinline__ Dep<Real> advance(
     Part<Real>& q, unsigned uid, unsigned uid_hi, const typename Vec2<Real>::type* __restrict__ E,
     const Soa<Real>& s, const DepGrid& g, DevState* st, unsigned* spawn_parent, int n_slots,
@@ -250,15 +373,20 @@ __device__ __forceinline__ Dep<Real> advance(
   const Real fr = q.fr, fz = q.fz, vr = q.vr, vt = q.vt, vz = q.vz;
   const Real r = mad((Real)ir + fr, P.hr, P.r_in);
 
-  // gather: bilinear interpolation of the cell's four nodes, as linear
-  // interpolation along r on both z-edges, then along z
-  const int n00 = ir * nzp + iz;
-  const V2 e00 = __ldg(E + n00), e01 = __ldg(E + n00 + 1);
-  const V2 e10 = __ldg(E + n00 + nzp), e11 = __ldg(E + n00 + nzp + 1);
-  const Real ar0 = mad(fr, e10.x - e00.x, e00.x), ar1 = mad(fr, e11.x - e01.x, e01.x);
-  const Real az0 = mad(fr, e10.y - e00.y, e00.y), az1 = mad(fr, e11.y - e01.y, e01.y);
-  const Real Er = mad(fz, ar1 - ar0, ar0);
-  const Real Ez = mad(fz, az1 - az0, az0);
+  Real Er, Ez;
+  if constexpr (SPL == 0) {
+    // gather: bilinear interpolation of the cell's four nodes, as linear
+    // interpolation along r on both z-edges, then along z
+    const int n00 = ir * nzp + iz;
+    const V2 e00 = __ldg(E + n00), e01 = __ldg(E + n00 + 1);
+    const V2 e10 = __ldg(E + n00 + nzp), e11 = __ldg(E + n00 + nzp + 1);
+    const Real ar0 = mad(fr, e10.x - e00.x, e00.x), ar1 = mad(fr, e11.x - e01.x, e01.x);
+    const Real az0 = mad(fr, e10.y - e00.y, e00.y), az1 = mad(fr, e11.y - e01.y, e01.y);
+    Er = mad(fz, ar1 - ar0, ar0);
+    Ez = mad(fz, az1 - az0, az0);
+  } else {
+    spline_gather<Real, SPL>(P, ir, iz, fr, fz, r, Er, Ez);
+  }
   // t = (q dt / 2m) B: mirror Bz = b0 (1 + 2 zeta^2 / L^2),
   // Br = -2 b0 r zeta / L^2 (constants folded on the host)
   Real tr = 0, tz = P.tz0;
@@ -310,7 +438,33 @@ __device__ __forceinline__ Dep<Real> advance(
   const bool out_out = ir1 >= P.nr;
   const bool out_zl = iz1 < 0 || (iz1 == 0 && fz1 == 0);
   const bool out_zh = iz1 >= P.nz;
-  if (out_in || out_out || out_zl || out_zh) {
+  // the trap's ellipse: first entry of the straight (r, z) segment (the
+  // smaller root of the quadratic along it; a start inside enters at 0)
+  bool ell_hit = false;
+  Real te = Real(3);
+  if constexpr (SPL > 0) {
+    if (P.spl_ell) {
+      const Real z0a = mad((Real)iz + fz, P.hz, P.z_min), z1a = mad(vnz, P.dt, z0a);
+      const Real x0 = (r - P.e_r0) * P.e_idr, y0 = (z0a - P.e_z0) * P.e_idz;
+      const Real dx = (r1 - r) * P.e_idr, dy = (z1a - z0a) * P.e_idz;
+      const Real qa = dx * dx + dy * dy, qb = Real(2) * (x0 * dx + y0 * dy);
+      const Real qc = x0 * x0 + y0 * y0 - Real(1);
+      if (qc <= Real(0)) {
+        ell_hit = true;
+        te = Real(0);
+      } else if (qa > Real(0)) {
+        const Real disc = qb * qb - Real(4) * qa * qc;
+        if (disc >= Real(0)) {
+          const Real t = (-qb - d_sqrt(disc)) / (Real(2) * qa);
+          if (t >= Real(0) && t <= Real(1)) {
+            ell_hit = true;
+            te = t;
+          }
+        }
+      }
+    }
+  }
+  if (out_in || out_out || out_zl || out_zh || ell_hit) {
     // first crossing along the straight (r,z) segment, ties in the order
     // inner, outer, z_min, z_max
     const Real s0r = (Real)ir + fr, s0z = (Real)iz + fz;
@@ -320,7 +474,8 @@ __device__ __forceinline__ Dep<Real> advance(
     if (out_out) { const Real t = ((Real)P.nr - s0r) / dr_cells; if (t < tb) { tb = t; wall = 1; } }
     if (out_zl) { const Real t = -s0z / dz_cells; if (t < tb) { tb = t; wall = 2; } }
     if (out_zh) { const Real t = ((Real)P.nz - s0z) / dz_cells; if (t < tb) { tb = t; wall = 3; } }
-    atomicAdd(&bt.v[kAbsInner + wall], 1.0);
+    if (ell_hit && te < tb) wall = 4;
+    atomicAdd(&bt.v[wall == 4 ? (int)kAbsEllipse : kAbsInner + wall], 1.0);
     atomicAdd(&bt.v[kKeAbsorbed], (double)(P.half_m * mad(vnz, vnz, v2p)));
     atomicAdd(&bt.v[kNAbsorbed], 1.0);
     q.cell = -1;
@@ -339,7 +494,7 @@ __device__ __forceinline__ Dep<Real> advance(
   // null-collision candidate test: the integer form of u0 < P_null
   const uint4 xr = philox4x32_10_rk(make_uint4(uid, uid_hi, step, 0u), P.rk0, P.rk1);
   if ((xr.x >> 8) < P.thr_null)
-    collide<Real, TAB>(q, uid, uid_hi, s, g, st, spawn_parent, n_slots, step, P, bt);
+    collide<Real, TAB, SPL>(q, uid, uid_hi, s, g, st, spawn_parent, n_slots, step, P, bt);
   dep.ir = ir1; dep.iz = iz1; dep.fr = fr1; dep.fz = fz1;
   return dep;
 }
@@ -534,7 +689,7 @@ __device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pus
   if (tid < kTallyCount) {
     double v = bt.v[tid];
     if (v != 0.0) {
-      if (tid <= kAbsZmax) v *= P.weight;
+      if (tid <= kAbsZmax || tid == kAbsEllipse) v *= P.weight;
       else if (tid == kWorkE) v *= (double)P.work_scale * P.weight;
       else if (tid <= kRecoilLoss) v *= P.weight;
       atomicAdd(&st->tally[tid], v);
@@ -555,8 +710,10 @@ __device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pus
 // Each thread loads its kPPT consecutive particles directly (16-byte vector
 // loads with streaming hints in the FP32 path), advances them, stores them
 // back and joins the block's tile deposit.  TAB: some simulation has
-// tabulated cross sections.
-template <typename Real, bool TAB>
+// tabulated cross sections.  SPL > 0: the weighted B-spline field of that
+// degree (gather from its coefficients, deposit into its load grid with
+// FP64 atomics; the tile is not used).
+template <typename Real, bool TAB, int SPL>
 __global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 4)
 k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, DepGrid g,
                 DevState* st, unsigned* __restrict__ spawn_parent, PushParams<Real> P) {
@@ -591,13 +748,18 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, De
       live[k] = q[k].cell >= 0;
       if (live[k]) {
         ++pushed;
-        dep[k] = advance<Real, TAB>(q[k], uid[k], 0u, E, s, g, st, spawn_parent, n_slots, step, P, bt,
-                               work);
+        dep[k] = advance<Real, TAB, SPL>(q[k], uid[k], 0u, E, s, g, st, spawn_parent, n_slots, step,
+                                         P, bt, work);
+        if constexpr (SPL > 0) {
+          if (dep[k].ir >= 0) spline_deposit<Real, SPL>(P, dep[k].ir, dep[k].iz, dep[k].fr, dep[k].fz);
+        }
       }
     }
     store_group<Real>(s, p0, n_slots, q, live, vec);
-    deposit_chunk<Real, kCap>(dep, tile, bbox, buf, g, tid, lane);
-    buf ^= 1;
+    if constexpr (SPL == 0) {
+      deposit_chunk<Real, kCap>(dep, tile, bbox, buf, g, tid, lane);
+      buf ^= 1;
+    }
   }
   flush_tallies<Real>(bt, work, pushed, st, P, tid, lane);
 }
@@ -607,12 +769,23 @@ void launch_particle_step(const Soa<Real>& s, const void* efield, double* rhs,
                           unsigned long long* cnt, DevState* st, unsigned* spawn_parent,
                           const PushParams<Real>& P, int grid, cudaStream_t stream) {
   DepGrid g{rhs, cnt, P.nz + 1, P.qw};
-  if (P.xs_n > 0)
-    k_particle_step<Real, true><<<grid, kThreads, 0, stream>>>(
-        s, (const typename Vec2<Real>::type*)efield, g, st, spawn_parent, P);
-  else
-    k_particle_step<Real, false><<<grid, kThreads, 0, stream>>>(
-        s, (const typename Vec2<Real>::type*)efield, g, st, spawn_parent, P);
+  const auto* E = (const typename Vec2<Real>::type*)efield;
+  auto run = [&](auto tab, auto spl) {
+    k_particle_step<Real, decltype(tab)::value, decltype(spl)::value>
+        <<<grid, kThreads, 0, stream>>>(s, E, g, st, spawn_parent, P);
+  };
+  using T0 = std::false_type;
+  using T1 = std::true_type;
+  auto by_spl = [&](auto tab) {
+    switch (P.spl_n) {
+      case 1: run(tab, std::integral_constant<int, 1>()); break;
+      case 2: run(tab, std::integral_constant<int, 2>()); break;
+      case 3: run(tab, std::integral_constant<int, 3>()); break;
+      default: run(tab, std::integral_constant<int, 0>()); break;
+    }
+  };
+  if (P.xs_n > 0) by_spl(T1());
+  else by_spl(T0());
 }
 
 // ----------------------------------------------------------------- batch
@@ -707,7 +880,7 @@ k_particle_step_batch(Soa<Real> s_all, const typename Vec2<Real>::type* __restri
       live[k] = q[k].cell >= 0;
       if (live[k]) {
         ++pushed;
-        dep[k] = advance<Real, TAB>(q[k], uid[k], V.P.uid_hi, V.E, V.s, V.g, V.st, V.spawn, n_slots,
+        dep[k] = advance<Real, TAB, 0>(q[k], uid[k], V.P.uid_hi, V.E, V.s, V.g, V.st, V.spawn, n_slots,
                                V.step, V.P, bt, work);
       }
     }
@@ -921,6 +1094,48 @@ __global__ void k_deposit_only(Soa<Real> s, int n, DepGrid g) {
   }
 }
 
+// spline load of the stored particles at their positions (no push)
+template <typename Real, int N>
+__global__ void k_spline_deposit_store(Soa<Real> s, const DevState* st, PushParams<Real> P) {
+  const long long n = st->n_slots;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int c = s.cell[p];
+    if (c >= 0) spline_deposit<Real, N>(P, c >> 16, c & 0xFFFF, s.offr[p], s.offz[p]);
+  }
+}
+
+template <typename Real>
+void launch_spline_deposit_store(const Soa<Real>& s, const DevState* st,
+                                 const PushParams<Real>& P, long long max_slots,
+                                 cudaStream_t stream) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((max_slots + 255) / 256, 152 * 16));
+  switch (P.spl_n) {
+    case 1: k_spline_deposit_store<Real, 1><<<grid, 256, 0, stream>>>(s, st, P); break;
+    case 2: k_spline_deposit_store<Real, 2><<<grid, 256, 0, stream>>>(s, st, P); break;
+    case 3: k_spline_deposit_store<Real, 3><<<grid, 256, 0, stream>>>(s, st, P); break;
+    default: break;
+  }
+}
+template void launch_spline_deposit_store<float>(const Soa<float>&, const DevState*,
+                                                 const PushParams<float>&, long long, cudaStream_t);
+template void launch_spline_deposit_store<double>(const Soa<double>&, const DevState*,
+                                                  const PushParams<double>&, long long,
+                                                  cudaStream_t);
+
+// spline coefficients in the particle precision (gather copy)
+template <typename Real>
+__global__ void k_spline_coef(const double* __restrict__ c, Real* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = (Real)c[i];
+}
+template <typename Real>
+void launch_spline_coef(const double* c, Real* out, int n, cudaStream_t stream) {
+  k_spline_coef<Real><<<std::min(152 * 4, (n + 255) / 256), 256, 0, stream>>>(c, out, n);
+}
+template void launch_spline_coef<float>(const double*, float*, int, cudaStream_t);
+template void launch_spline_coef<double>(const double*, double*, int, cudaStream_t);
+
 template <typename Real>
 void launch_load(const double* r, const double* z, const double* vr,
                  const double* vt, const double* vz, const uint64_t* uid,
@@ -1087,8 +1302,10 @@ int particle_step_blocks_per_sm(int precision, bool batch) {
                     blocks_of(k_particle_step_batch<double, true>));
   }
   if (precision == 32)
-    return std::min(blocks_of(k_particle_step<float, false>), blocks_of(k_particle_step<float, true>));
-  return std::min(blocks_of(k_particle_step<double, false>), blocks_of(k_particle_step<double, true>));
+    return std::min(blocks_of(k_particle_step<float, false, 0>),
+                    blocks_of(k_particle_step<float, true, 0>));
+  return std::min(blocks_of(k_particle_step<double, false, 0>),
+                  blocks_of(k_particle_step<double, true, 0>));
 }
 // slots of the store are allocated in whole multiples of this (the sort
 // kernels read 1024-slot chunks)

@@ -38,6 +38,7 @@ enum Tally {
   kNPushed,        // particle-steps taken (live particles advanced)
   kNSource,        // particles created by the seed source
   kKeSource,       // their kinetic energy, J
+  kAbsEllipse,     // absorbed weight on the trap's ellipse
   kTallyCount
 };
 
@@ -131,6 +132,20 @@ struct PushParams {
   const Real* xs_nel;
   const Real* xs_nio;
   const Real* xs_xi;
+  // weighted B-spline field of degree spl_n (0: the bilinear node field):
+  // its coefficients in the particle precision (mr x mz, row i at i spl_mz)
+  // for the gather, the FP64 load grid for the deposit, the walls' weight
+  // w = (r - r_in)(r_out - r) spl_inv_ab and the lift's slope spl_dphi
+  int spl_n, spl_mz;
+  const Real* spl_c;
+  double* spl_f;
+  Real spl_r_out, spl_inv_ab, spl_dphi;
+  // the trap's metal ellipse (spl_ell): centre, inverse semi-axes, the
+  // weight's scale min(dr, dz)/2 and the wall potential difference; the
+  // weight and lift become the web-spline field's and electrons entering
+  // the ellipse are absorbed
+  int spl_ell;
+  Real e_r0, e_z0, e_idr, e_idz, e_s, spl_dv;
 };
 
 // ------------------------------------------------------------- batches
@@ -373,6 +388,14 @@ void launch_particle_step(const Soa<Real>& s, const void* efield,
                           double* rhs, unsigned long long* cnt, DevState* st,
                           unsigned* spawn_parent, const PushParams<Real>& P,
                           int grid, cudaStream_t stream);
+// spline mode: load of every stored particle into P.spl_f, and the gather
+// copy of the coefficients
+template <typename Real>
+void launch_spline_deposit_store(const Soa<Real>& s, const DevState* st,
+                                 const PushParams<Real>& P, long long max_slots,
+                                 cudaStream_t stream);
+template <typename Real>
+void launch_spline_coef(const double* c, Real* out, int n, cudaStream_t stream);
 void launch_spawn_finalize(DevState* st, unsigned* uid, const unsigned* parent,
                            long long spawn_cap, long long capacity,
                            cudaStream_t stream);

@@ -553,6 +553,12 @@ int pic_spline_eval(pic_spline* s, const double* c, const double* r, const doubl
   return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
+int pic_spline_set_stream(pic_spline* s, void* cuda_stream) {
+  if (!s) return PIC_EINVAL;
+  s->stream = (cudaStream_t)cuda_stream;
+  return PIC_OK;
+}
+
 int pic_spline_sizes(const pic_spline* s, int* mr, int* mz) {
   if (!s) return PIC_EINVAL;
   if (mr) *mr = s->G.mr;

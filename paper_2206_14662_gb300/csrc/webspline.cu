@@ -892,6 +892,12 @@ int pic_web_solve(pic_web* w, const double* f_full, double* c_full, int dirichle
   return res <= rtol ? PIC_OK : PIC_ENOCONV;
 }
 
+int pic_web_set_stream(pic_web* w, void* cuda_stream) {
+  if (!w || !w->dev) return PIC_EINVAL;
+  w->dev->stream = (cudaStream_t)cuda_stream;
+  return w->dev->pre ? pic_spline_set_stream(w->dev->pre, cuda_stream) : PIC_OK;
+}
+
 int pic_web_direct(pic_web* w) {
   using namespace pic::web;
   if (!w || !w->dev) return PIC_EINVAL;

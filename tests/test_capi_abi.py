@@ -94,3 +94,30 @@ def test_batch_configurations_validated_on_the_host():
     bad = [dict(c) for c in base]
     bad[3]["p_mbar"] = -1.0        # a per-simulation field is validated too
     assert init(bad) == _capi.PIC_EINVAL
+
+
+def test_spline_and_trap_configurations_validated_on_the_host():
+    """pic_init refuses, before touching a device, spline degrees outside
+    0..3, a spline field with a seed source, a fixed field or a batch, and
+    an ellipse without a spline degree or with a non-positive semi-axis."""
+    from paper_2206_14662_gb300 import _capi
+    from paper_2206_14662_gb300.inputs import workload
+    L = _capi.lib()
+    h = ctypes.c_void_p()
+
+    def init(cfgs):
+        arr = (_capi.PicConfig * len(cfgs))(*[_capi.make_config(c) for c in cfgs])
+        return L.pic_init(arr, len(cfgs), None, None, ctypes.byref(h))
+
+    base = workload("coax_32x64_1e4", precision=64)
+    for deg in (-1, 4):
+        assert init([dict(base, bspline_degree=deg)]) == _capi.PIC_EINVAL
+    assert init([dict(base, bspline_degree=2, source_rate=1e9)]) == _capi.PIC_EINVAL
+    assert init([dict(base, bspline_degree=2, fixed_efield=1)]) == _capi.PIC_EINVAL
+    assert init([dict(base, bspline_degree=2)] * 2) == _capi.PIC_EINVAL
+    ell = (9e-3, 0.0, 1e-3, 3e-3)
+    assert init([dict(base, ellipse=ell)]) == _capi.PIC_EINVAL
+    assert init([dict(base, bspline_degree=2, ellipse=(9e-3, 0.0, 0.0, 3e-3))]) == _capi.PIC_EINVAL
+    # the binding sets the ellipse flag and axes
+    c = _capi.make_config(dict(base, bspline_degree=2, ellipse=ell))
+    assert c.has_ellipse == 1 and tuple(c.ellipse) == ell
