@@ -523,7 +523,11 @@ int pic_spline_eigen(const pic_config* cfg, int degree, double* V, double* lambd
  * freed by pic_spline_free).  Work is queued on cuda_stream (NULL: the
  * default stream).  PIC_EINVAL, PIC_ENOCONV, PIC_ENOMEM. */
 int pic_spline_create(const pic_config* cfg, int degree, void* cuda_stream, pic_spline** out);
+/* Frees the solver and its device memory (NULL is ignored); waits for
+ * nothing: the caller makes sure no queued work still uses it. */
 void pic_spline_free(pic_spline* s);
+/* mr = nr + degree and mz = nz + degree (either pointer may be NULL).
+ * PIC_EINVAL on a NULL solver. */
 int pic_spline_sizes(const pic_spline* s, int* mr, int* mz);
 
 /* c = the Galerkin solution for the load f (DEVICE arrays of mr x mz
@@ -574,7 +578,12 @@ int pic_spline_eval(pic_spline* s, const double* c, const double* r, const doubl
 typedef struct pic_web pic_web;
 int pic_web_create(const pic_config* cfg, const double* ellipse, double r_lo, double r_hi,
                    int nr, int degree, pic_web** out);
+/* Frees the system and any device memory of pic_web_device (NULL is
+ * ignored); the caller makes sure no queued work still uses it. */
 void pic_web_free(pic_web* w);
+/* The sizes of the exported arrays: inner functions, entries of A and of
+ * T, and mr = nr + degree, mz = nz + degree (any pointer may be NULL).
+ * PIC_EINVAL on a NULL system. */
 int pic_web_sizes(const pic_web* w, int* n_inner, int64_t* nnz, int64_t* t_nnz, int* mr,
                   int* mz);
 /* Copies out the arrays sized by pic_web_sizes; any pointer may be NULL. */
