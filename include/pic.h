@@ -523,7 +523,11 @@ int pic_spline_eigen(const pic_config* cfg, int degree, double* V, double* lambd
  * freed by pic_spline_free).  Work is queued on cuda_stream (NULL: the
  * default stream).  PIC_EINVAL, PIC_ENOCONV, PIC_ENOMEM. */
 int pic_spline_create(const pic_config* cfg, int degree, void* cuda_stream, pic_spline** out);
+/* Frees the solver and its device memory (NULL is ignored); waits for
+ * nothing: the caller makes sure no queued work still uses it. */
 void pic_spline_free(pic_spline* s);
+/* mr = nr + degree and mz = nz + degree (either pointer may be NULL).
+ * PIC_EINVAL on a NULL solver. */
 int pic_spline_sizes(const pic_spline* s, int* mr, int* mz);
 
 /* c = the Galerkin solution for the load f (DEVICE arrays of mr x mz
@@ -574,12 +578,22 @@ int pic_spline_eval(pic_spline* s, const double* c, const double* r, const doubl
 typedef struct pic_web pic_web;
 int pic_web_create(const pic_config* cfg, const double* ellipse, double r_lo, double r_hi,
                    int nr, int degree, pic_web** out);
+/* Frees the system and any device memory of pic_web_device (NULL is
+ * ignored); the caller makes sure no queued work still uses it. */
 void pic_web_free(pic_web* w);
+/* The sizes of the exported arrays: inner functions, entries of A and of
+ * T, and mr = nr + degree, mz = nz + degree (any pointer may be NULL).
+ * PIC_EINVAL on a NULL system. */
 int pic_web_sizes(const pic_web* w, int* n_inner, int64_t* nnz, int64_t* t_nnz, int* mr,
                   int* mz);
 /* Copies out the arrays sized by pic_web_sizes; any pointer may be NULL. */
 int pic_web_export(const pic_web* w, int* a_ptr, int* a_col, double* a_val, double* g,
                    int* inner_full, int* t_ptr, int* t_col, double* t_val);
+
+/* A^-1 of the web-spline system (host only; n_inner^2 FP64, row-major,
+ * by dense Cholesky: O(n_inner^3), seconds for a few thousand inner
+ * functions).  PIC_ENOCONV if A is not positive definite. */
+int pic_web_inverse(const pic_web* w, double* out);
 
 /* Device side of a web-spline system on the current CUDA device: copies
  * the system, its extension and T^T to device memory owned by w (freed by
@@ -598,6 +612,14 @@ int pic_web_device(pic_web* w, void* cuda_stream);
  * iteration.  PIC_ENOCONV if rtol was not met. */
 int pic_web_solve(pic_web* w, const double* f, double* c, int dirichlet, double rtol, int maxit,
                   int* iters, double* relres);
+
+/* Direct solve for time stepping: pic_web_direct (after pic_web_device)
+ * makes A^-1 on the host and keeps it in device memory (n_inner^2 FP64:
+ * 85 MB for 3260 inner functions, inside the L2); pic_web_solve_direct
+ * then queues b = T^T f - [dirichlet] g, u = A^-1 b, c = T u with no host
+ * synchronisation, so the solve can be captured in a CUDA graph. */
+int pic_web_direct(pic_web* w);
+int pic_web_solve_direct(pic_web* w, const double* f, double* c, int dirichlet);
 
 /* f_k += qw w(r_p, z_p) b_k(r_p, z_p) with the web weight (DEVICE arrays;
  * FP64 atomics), and phi, E = -grad phi of full coefficients c at points

@@ -130,8 +130,12 @@ def lib() -> ctypes.CDLL:
         L.pic_web_eval.argtypes = [vp, vp, vp, vp, c_i64, ctypes.c_int, vp, vp, vp]
         L.pic_web_well_depth.argtypes = [vp, vp, vp, ctypes.c_int, c_d, ctypes.c_int,
                                          ctypes.c_int, c_d, c_d, c_d, vp, vp]
+        L.pic_web_inverse.argtypes = [vp, vp]
+        L.pic_web_direct.argtypes = [vp]
+        L.pic_web_solve_direct.argtypes = [vp, vp, vp, ctypes.c_int]
         for name in ("pic_web_create", "pic_web_sizes", "pic_web_export", "pic_web_device",
-                     "pic_web_solve", "pic_web_deposit", "pic_web_eval", "pic_web_well_depth"):
+                     "pic_web_solve", "pic_web_deposit", "pic_web_eval", "pic_web_well_depth",
+                     "pic_web_inverse", "pic_web_direct", "pic_web_solve_direct"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("pic_spline_matrices", "pic_spline_eigen", "pic_spline_create",
                      "pic_spline_sizes", "pic_spline_solve", "pic_spline_deposit",
@@ -520,6 +524,24 @@ class SplineSolver:
         return tuple(out)
 
 
+def web_inverse(cfg: dict, ellipse, r_lo: float, r_hi: float, nr: int, degree: int) -> np.ndarray:
+    """A^-1 of the web-spline system (pic_web_inverse, host only)."""
+    c = make_config(cfg)
+    e = None if ellipse is None else np.ascontiguousarray(ellipse, dtype=np.float64)
+    h = ctypes.c_void_p()
+    L = lib()
+    _check(L.pic_web_create(ctypes.byref(c), _ptr_np(e), float(r_lo), float(r_hi), int(nr),
+                            int(degree), ctypes.byref(h)), "pic_web_create")
+    try:
+        ni = ctypes.c_int()
+        _check(L.pic_web_sizes(h, ctypes.byref(ni), None, None, None, None), "pic_web_sizes")
+        out = np.zeros((ni.value, ni.value))
+        _check(L.pic_web_inverse(h, _ptr_np(out)), "pic_web_inverse")
+        return out
+    finally:
+        L.pic_web_free(h)
+
+
 def web_system(cfg: dict, ellipse, r_lo: float, r_hi: float, nr: int, degree: int) -> dict:
     """The web-spline system of pic_web_create (host only): CSR arrays
     a_ptr, a_col, a_val (n_inner x n_inner), the lift load g, the full
@@ -599,6 +621,17 @@ class WebSolver:
                                      float(qw), _dev_f64(f, self.mr * self.mz, "f")),
                "pic_web_deposit")
         return f
+
+    def solve_direct(self, f, dirichlet: bool = True):
+        """c by the dense inverse (pic_web_direct once, then
+        pic_web_solve_direct; asynchronous)."""
+        import torch
+        _check(lib().pic_web_direct(self.h), "pic_web_direct")
+        c = torch.empty((self.mr, self.mz), dtype=torch.float64, device=f.device)
+        _check(lib().pic_web_solve_direct(self.h, _dev_f64(f, self.mr * self.mz, "f"),
+                                          _dev_f64(c), int(bool(dirichlet))),
+               "pic_web_solve_direct")
+        return c
 
     def solve(self, f, dirichlet: bool = True, rtol: float = 1e-12, maxit: int = 500):
         """(c, iterations, relative residual)."""

@@ -176,6 +176,7 @@ struct Dev {
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *full = nullptr, *full2 = nullptr, *dots = nullptr;
   double* scale = nullptr;     // sqrt(diag S / diag A) on the inner functions
+  double* inv = nullptr;       // A^-1 (n_inner x n_inner), pic_web_direct
   pic_spline* pre = nullptr;   // the enclosing box's solver: the preconditioner
 };
 }  // namespace web
@@ -358,9 +359,69 @@ int build(pic_web* W, const pic_config* c, const double* ellipse, double r_lo, d
   return PIC_OK;
 }
 
+// A^-1 of the SPD system: Cholesky A = L L^T, L^-1 by forward substitution,
+// A^-1 = L^-T L^-1 (dense, row-major; false if A is not positive definite)
+bool dense_inverse(const pic_web* W, std::vector<double>& inv) {
+  const int n = (int)W->inner_full.size();
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int e = W->a_ptr[i]; e < W->a_ptr[i + 1]; ++e)
+      if (W->a_col[e] <= i) L[(size_t)i * n + W->a_col[e]] = W->a_val[e];
+  for (int j = 0; j < n; ++j) {   // right-looking Cholesky, column j
+    double* Lj = &L[(size_t)j * n];
+    double d = Lj[j];
+    for (int k = 0; k < j; ++k) d -= Lj[k] * Lj[k];
+    if (!(d > 0)) return false;
+    d = std::sqrt(d);
+    Lj[j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double* Li = &L[(size_t)i * n];
+      double s = Li[j];
+      for (int k = 0; k < j; ++k) s -= Li[k] * Lj[k];
+      Li[j] = s / d;
+    }
+  }
+  // X = L^-1 (lower), row by row: X[i][j] = (delta_ij - sum_{j<=k<i} L[i][k] X[k][j]) / L[i][i]
+  std::vector<double> X((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const double* Li = &L[(size_t)i * n];
+    double* Xi = &X[(size_t)i * n];
+    for (int k = 0; k < i; ++k) {
+      const double lik = Li[k];
+      if (lik == 0.0) continue;
+      const double* Xk = &X[(size_t)k * n];
+      for (int j = 0; j <= k; ++j) Xi[j] -= lik * Xk[j];
+    }
+    Xi[i] += 1.0;
+    for (int j = 0; j <= i; ++j) Xi[j] /= Li[i];
+  }
+  // A^-1 = X^T X: entry (a, b) = sum_{k >= max(a, b)} X[k][a] X[k][b]
+  inv.assign((size_t)n * n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const double* Xk = &X[(size_t)k * n];
+    for (int a = 0; a <= k; ++a) {
+      const double xa = Xk[a];
+      if (xa == 0.0) continue;
+      double* row = &inv[(size_t)a * n];
+      for (int b = 0; b <= a; ++b) row[b] += xa * Xk[b];
+    }
+  }
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < a; ++b) inv[(size_t)b * n + a] = inv[(size_t)a * n + b];
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
+
+int pic_web_inverse(const pic_web* w, double* out) {
+  if (!w || !out) return PIC_EINVAL;
+  std::vector<double> inv;
+  if (!dense_inverse(w, inv)) return PIC_ENOCONV;
+  std::memcpy(out, inv.data(), inv.size() * sizeof(double));
+  return PIC_OK;
+}
 
 int pic_web_create(const pic_config* cfg, const double* ellipse, double r_lo, double r_hi,
                    int nr, int degree, pic_web** out) {
@@ -393,7 +454,7 @@ void pic_web_free(pic_web* w) {
                       (void*)d->t_col, (void*)d->tt_ptr, (void*)d->tt_col, (void*)d->a_val,
                       (void*)d->g, (void*)d->t_val, (void*)d->tt_val, (void*)d->x, (void*)d->r,
                       (void*)d->z, (void*)d->p, (void*)d->q, (void*)d->full, (void*)d->full2,
-                      (void*)d->dots, (void*)d->scale})
+                      (void*)d->dots, (void*)d->scale, (void*)d->inv})
       if (ptr) cudaFree(ptr);
     pic_spline_free(d->pre);
     delete d;
@@ -444,6 +505,20 @@ __global__ void k_spmv(int rows, const int* __restrict__ ptr, const int* __restr
        row += ((long long)gridDim.x * blockDim.x) >> 5) {
     double s = 0.0;
     for (int e = ptr[row] + lane; e < ptr[row + 1]; e += 32) s = fma(val[e], x[col[e]], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = s;
+  }
+}
+
+// y = M x for a dense row-major n x n matrix, one warp per row
+__global__ void k_gemv(int n, const double* __restrict__ M, const double* __restrict__ x,
+                       double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < n;
+       row += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const double* m = M + row * (long long)n;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s = fma(m[j], x[j], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) y[row] = s;
   }
@@ -815,6 +890,39 @@ int pic_web_solve(pic_web* w, const double* f_full, double* c_full, int dirichle
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return PIC_ECUDA;
   return res <= rtol ? PIC_OK : PIC_ENOCONV;
+}
+
+int pic_web_direct(pic_web* w) {
+  using namespace pic::web;
+  if (!w || !w->dev) return PIC_EINVAL;
+  if (w->dev->inv) return PIC_OK;
+  std::vector<double> inv;
+  if (!dense_inverse(w, inv)) return PIC_ENOCONV;
+  if (cudaMalloc(&w->dev->inv, inv.size() * sizeof(double)) != cudaSuccess ||
+      cudaMemcpy(w->dev->inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return PIC_ENOMEM;
+  }
+  return PIC_OK;
+}
+
+int pic_web_solve_direct(pic_web* w, const double* f, double* c, int dirichlet) {
+  using namespace pic::web;
+  if (!w || !w->dev || !w->dev->inv || !f || !c) return PIC_EINVAL;
+  Dev* d = w->dev;
+  cudaStream_t st = d->stream;
+  const int ni = (int)w->inner_full.size(), nf = w->mr * w->mz;
+  const int bi = blocks_for(ni, 256);
+  // b = T^T f - [dirichlet] g;  u = A^-1 b (one warp per row of the dense
+  // inverse, kept in L2 across steps);  c = T u
+  k_spmv<<<blocks_for((long long)ni * 32, 256), 256, 0, st>>>(ni, d->tt_ptr, d->tt_col, d->tt_val,
+                                                              f, d->r);
+  if (dirichlet) k_axpby<<<bi, 256, 0, st>>>(ni, -1.0, d->g, 1.0, d->r);
+  k_gemv<<<blocks_for((long long)ni * 32, 256), 256, 0, st>>>(ni, d->inv, d->r, d->x);
+  k_spmv<<<blocks_for((long long)nf * 32, 256), 256, 0, st>>>(nf, d->t_ptr, d->t_col, d->t_val,
+                                                              d->x, c);
+  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
 int pic_web_well_depth(pic_web* w, const double* c, const double* r_start, int lines, double z1,

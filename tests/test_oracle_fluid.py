@@ -376,3 +376,12 @@ def test_rigid_rotor_equilibrium_balances():
     assert np.abs(T[2, 0][inner]).max() > 1e-2 * scale
     assert np.abs(S).max() <= 6e-3 * scale
     assert np.abs(T[6, 1][inner]).max() <= 1e-6 * scale   # no azimuthal force
+    # the fluid-Poisson model's drift u_theta = -E_r / B_z (Sec. V.A) is the
+    # electrons' mean azimuthal velocity up to the centrifugal correction
+    # (m u^2 / r against q E_r: about 2 % here); with next to no gas the
+    # predicted radial drift is negligible
+    F = fluid.fluid_model(c, M, Er_of(R), np.zeros_like(R))
+    u_t = M[2][inner] / M[0][inner]
+    rel = np.abs(F[0][inner] - u_t) / np.abs(u_t)
+    assert rel.max() <= 4e-2 and rel.max() >= 2e-3
+    assert np.abs(F[3][inner]).max() <= 1e-9 * np.abs(u_t).max()

@@ -59,3 +59,21 @@ def test_bad_arguments_are_refused():
         web_system(cfg, (0.081, 0.012, 0.0, 0.014), geo.a, geo.b, 14, 2)
     with pytest.raises(PicError):
         web_system(cfg, geo.ellipse, geo.a, geo.b, 14, 0)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_web_inverse_matches_numpy(n):
+    """The dense inverse the direct solve keeps on the device, against
+    numpy's inverse of the oracle's matrix."""
+    from paper_2206_14662_gb300._capi import web_inverse
+    geo = paper_trap()
+    nr, nz = 10, 24
+    W = WebSplineField(geo, n, geo.a, geo.b, nr, nz)
+    cfg = workload("coax_32x64_1e4", r_in=geo.a, r_out=geo.b, z_min=geo.z_min,
+                   z_max=geo.z_max, nz=nz, v_inner=geo.v_in, v_outer=geo.v_out)
+    got = web_inverse(cfg, geo.ellipse, geo.a, geo.b, nr, n)
+    A = W.A.toarray()
+    want = np.linalg.inv(A)
+    assert np.abs(got - got.T).max() == 0.0
+    assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
+    assert np.abs(got @ A - np.eye(len(A))).max() <= 1e-8
