@@ -43,6 +43,7 @@
 //   j = -eps0 E_r <nu_io>   (I = 2 pi L r_+ j at the cloud edge, Eq. current)
 // Zero where n = 0 (the moment ratios) or where a denominator vanishes.
 #include <algorithm>
+#include <climits>
 
 #include "fluid.cuh"
 
@@ -80,13 +81,14 @@ __device__ __forceinline__ double node_volume(const ForceParams& F, int i, int j
 }
 
 // Moment pass.  A warp takes chunks of kMomIters x 32 consecutive slots;
-// per 32-slot row each lane writes its particle's 48 products
-// g_k Lambda_j (moment k, corner j) to a padded shared-memory row, then
-// lane l sums columns l and l + 32 down the rows (in the particle's
-// precision), carrying an FP64 running sum while the rows' cell stays the
-// same and adding it, times w / V of the node, to M with one atomic per
-// column when the cell changes.  In a cell-sorted store a cell change is
-// rare, so the atomics per particle are few; any order stays correct.
+// per 32-slot tile each lane writes its particle's 48 products
+// g_k Lambda_j (moment k, corner j) to a padded shared-memory row, the
+// tile's rows are ordered by cell (a bitonic sort of (cell, lane) across
+// the warp, holes last), then lane l sums columns l and l + 32 down the
+// ordered rows (in the particle's precision), carrying an FP64 running sum
+// while the cell stays the same and adding it, times w / V of the node, to
+// M with one atomic per column when the cell changes: a tile flushes once
+// per distinct cell whatever the order of its slots.
 constexpr int kMomCols = 4 * kMoments;   // column 4 k + j
 constexpr int kMomRow = kMomCols + 1;    // padded: rows start in different banks
 constexpr int kMomIters = 32;
@@ -123,6 +125,7 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
   constexpr int W = MomShape<Real>::warps;
   __shared__ Real rows[W][32][kMomRow];
   __shared__ int rcell[W][32];
+  __shared__ int rperm[W][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long n = st->n_slots;
   const int nzp = F.nz + 1, nnodes = (F.nr + 1) * nzp;
@@ -133,6 +136,7 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
   const bool has1 = col1 < kMomCols;
   Real(*row)[kMomRow] = rows[wib];
   int* rc = rcell[wib];
+  int* rp = rperm[wib];
   for (long long ch = (long long)blockIdx.x * W + wib; ch < nchunks;
        ch += (long long)gridDim.x * W) {
     int run_cell = -1;
@@ -154,12 +158,30 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
 #pragma unroll
           for (int j = 0; j < 4; ++j) row[lane][4 * k + j] = g[k] * c[j];
       }
-      rc[lane] = cell;
+      // order the tile's rows by cell (bitonic sort of (cell, lane) across
+      // the warp; holes last) so that equal cells are walked together
+      int key = cell < 0 ? INT_MAX : cell, idx = lane;
+#pragma unroll
+      for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const int ok = __shfl_xor_sync(0xffffffffu, key, j);
+          const int oi = __shfl_xor_sync(0xffffffffu, idx, j);
+          const bool ascending = (lane & k) == 0, lower = (lane & j) == 0;
+          const bool other_less = ok < key || (ok == key && oi < idx);
+          if (lower == ascending ? other_less : !other_less) {
+            key = ok;
+            idx = oi;
+          }
+        }
+      }
+      rc[lane] = key == INT_MAX ? -1 : key;
+      rp[lane] = idx;
       __syncwarp();
       Real part0 = Real(0), part1 = Real(0);
       for (int r = 0; r < 32; ++r) {
         const int cr = rc[r];   // the same for every lane: uniform branches
-        if (cr < 0) continue;
+        if (cr < 0) break;      // holes are sorted last
         if (cr != run_cell) {
           if (run_cell >= 0) {
             moment_flush<Real>(F, ws, run_cell, col0, run0 + (double)part0, M, nzp, nnodes);
@@ -170,8 +192,8 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
           run0 = run1 = 0.0;
           part0 = part1 = Real(0);
         }
-        part0 += row[r][col0];
-        if (has1) part1 += row[r][col1];
+        part0 += row[rp[r]][col0];
+        if (has1) part1 += row[rp[r]][col1];
       }
       run0 += (double)part0;
       run1 += (double)part1;
