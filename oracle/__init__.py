@@ -55,7 +55,7 @@ def build(force: bool = False) -> str:
     """Compile the C part of the oracle with the host compiler."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
                                "-fno-fast-math", "-ffp-contract=off",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
@@ -116,12 +116,26 @@ def lib():
         L.or_kinetic_energy.restype = d
         L.or_source.argtypes = [P, i64, u64, u32, vp, vp, vp, vp, vp]
         L.or_source.restype = None
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_set_threads.restype = None
+        L.or_get_threads.argtypes = []
+        L.or_get_threads.restype = ctypes.c_int
         _lib = L
     return _lib
 
 
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    """Threads of the particle loop of a step (OpenMP); the results do not
+    depend on it."""
+    lib().or_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().or_get_threads())
 
 
 # ----------------------------------------------------------------- params

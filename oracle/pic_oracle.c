@@ -8,7 +8,10 @@
  * cpu_baseline / reference legs of bench.py may load this library.  It shares
  * no code, header, table or constant generator with the CUDA path; it follows
  * the method's steps in the order the paper states them, one particle at a
- * time, in double precision, with no blocking, fusion or reordering.
+ * time, in double precision, with no blocking, fusion or reordering.  (With
+ * OpenMP the particles' own steps run on several threads; every sum and the
+ * list of children are still formed one particle after another in particle
+ * order, so the results are bitwise those of one thread.)
  *
  * Steps of one particle step (leapfrog: position at n, velocity at n-1/2):
  *   1. gather  : bilinear interpolation of node E (Sec. II.A, standard PIC);
@@ -40,6 +43,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* CODATA 2018 / exact SI values. */
 #define OR_E    1.602176634e-19  /* elementary charge, C */
@@ -339,6 +345,164 @@ static int or_ellipse_entry(const or_params* P, double r0, double z0, double r1,
 
 /* ----------------------------------------------------------------- step */
 
+/* What one particle's step contributes to the step's sums and lists, kept
+ * so that the sums can be formed afterwards in particle order. */
+typedef struct {
+  double work;       /* W_E of the two half kicks (macro-weighted), J */
+  double ke_abs;     /* kinetic energy carried into a wall, J */
+  double recoil;     /* elastic recoil loss, J */
+  int wall;          /* -1, or 0..3 the walls, 4 the ellipse */
+  int candidate;     /* passed the null-collision candidate test */
+  int over;          /* nu_el + nu_io above the majorant */
+  int kind;          /* EV_ELASTIC, EV_IONISE or 0 */
+  double child[5];   /* r, z, vr, vt, vz of an ionisation's secondary */
+} or_rec;
+
+/* Gather, push, absorb and collide particle p: its new state, event and
+ * margin are written in place, its contributions to the sums into *rec. */
+static void or_advance(const or_params* P, int64_t p, double* r, double* z, double* vr,
+                       double* vt, double* vz, const uint64_t* uid, int8_t* event,
+                       double* margin, const double* er, const double* ez, uint32_t step,
+                       or_rec* rec) {
+  const double q = -OR_E, m = OR_ME;
+  const double qmdt2 = q * P->dt / (2.0 * m);
+  const double hr = (P->r_out - P->r_in) / P->nr;
+  const double hz = (P->z_max - P->z_min) / P->nz;
+  const double p_null = 1.0 - exp(-P->nu_max * P->dt);
+  const double E_ion = P->ion_E_th_eV * OR_E;
+  const double B_share = P->opal_B_eV * OR_E;
+  rec->wall = -1;
+  rec->candidate = rec->over = rec->kind = 0;
+  double r0 = r[p], z0 = z[p];
+  double v0[3] = {vr[p], vt[p], vz[p]};
+  double Er, Ez, Br, Bz;
+  if (P->e_per_particle) {
+    Er = er[p];
+    Ez = ez[p];
+  } else {
+    or_gather(P, er, ez, r0, z0, &Er, &Ez);
+  }
+  or_bfield(P, r0, z0, &Br, &Bz);
+  /* Boris: half kick, rotation about B, half kick; components (r,theta,z) */
+  double vm[3] = {v0[0] + qmdt2 * Er, v0[1], v0[2] + qmdt2 * Ez};
+  double t[3] = {qmdt2 * Br, 0.0, qmdt2 * Bz};
+  double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  double s[3] = {2 * t[0] / (1 + t2), 2 * t[1] / (1 + t2), 2 * t[2] / (1 + t2)};
+  double vpr[3] = {vm[0] + (vm[1] * t[2] - vm[2] * t[1]),
+                   vm[1] + (vm[2] * t[0] - vm[0] * t[2]),
+                   vm[2] + (vm[0] * t[1] - vm[1] * t[0])};
+  double vp[3] = {vm[0] + (vpr[1] * s[2] - vpr[2] * s[1]),
+                  vm[1] + (vpr[2] * s[0] - vpr[0] * s[2]),
+                  vm[2] + (vpr[0] * s[1] - vpr[1] * s[0])};
+  double vn[3] = {vp[0] + qmdt2 * Er, vp[1], vp[2] + qmdt2 * Ez};
+  /* exact work of the two half kicks: (q dt / 4) E . (v0 + vm + vp + vn) */
+  rec->work = P->weight * (q * P->dt / 4.0) *
+              (Er * (v0[0] + vm[0] + vp[0] + vn[0]) + Ez * (v0[2] + vm[2] + vp[2] + vn[2]));
+  /* move in the local Cartesian frame (x along rhat, y along thetahat) */
+  double x = r0 + vn[0] * P->dt, y = vn[1] * P->dt;
+  double r1 = sqrt(x * x + y * y);
+  double z1 = z0 + vn[2] * P->dt;
+  /* absorbing walls: first crossing along the straight (r,z) segment */
+  double mg = fmin(fmin(fabs(r1 - P->r_in), fabs(r1 - P->r_out)) / hr,
+                   fmin(fabs(z1 - P->z_min), fabs(z1 - P->z_max)) / hz);
+  int wall = -1;
+  double tbest = 2.0;
+  double tw[4] = {3.0, 3.0, 3.0, 3.0};
+  if (r1 <= P->r_in) tw[0] = (P->r_in - r0) / (r1 - r0);
+  if (r1 >= P->r_out) tw[1] = (P->r_out - r0) / (r1 - r0);
+  if (z1 <= P->z_min) tw[2] = (P->z_min - z0) / (z1 - z0);
+  if (z1 >= P->z_max) tw[3] = (P->z_max - z0) / (z1 - z0);
+  for (int w = 0; w < 4; ++w)
+    if (tw[w] < 3.0 && tw[w] < tbest) { tbest = tw[w]; wall = w; }
+  if (P->has_ellipse) {
+    double te, fm;
+    int hit = or_ellipse_entry(P, r0, z0, r1, z1, &te, &fm);
+    mg = fmin(mg, fabs(fm) * 0.5 * fmin(P->e_dr, P->e_dz) / fmin(hr, hz));
+    if (hit && te < tbest) { tbest = te; wall = 4; }
+  }
+  if (wall >= 0) {
+    double v2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
+    rec->wall = wall;
+    rec->ke_abs = P->weight * 0.5 * m * v2;
+    event[p] = (int8_t)(EV_WALL_INNER + wall);
+    margin[p] = mg;
+    r[p] = r1; z[p] = z1;
+    vr[p] = vn[0]; vt[p] = vn[1]; vz[p] = vn[2];
+    return;
+  }
+  /* rotate (vr, vtheta) into the basis at the new position */
+  double c = x / r1, sn = y / r1;
+  double v[3] = {c * vn[0] + sn * vn[1], -sn * vn[0] + c * vn[1], vn[2]};
+  r[p] = r1; z[p] = z1;
+  event[p] = EV_NONE;
+  /* null-collision Monte Carlo */
+  double u[4];
+  or_draw4(P, uid[p], step, 0u, u);
+  if (u[0] < p_null) {
+    rec->candidate = 1;
+    double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    double speed = sqrt(v2);
+    double E = 0.5 * m * v2;
+    double nu_el, nu_io, xi;
+    or_nu_xi(P, speed, &nu_el, &nu_io, &xi);
+    if (nu_el + nu_io > P->nu_max) rec->over = 1;
+    double x1 = u[1] * P->nu_max;
+    mg = fmin(mg, fmin(fabs(x1 - nu_el), fabs(x1 - nu_el - nu_io)) / P->nu_max);
+    double vhat[3] = {v[0] / speed, v[1] / speed, v[2] / speed};
+    if (x1 < nu_el) {
+      double d[3];
+      or_scatter_dir(vhat, u[2], u[3], xi, d);
+      double E1 = E;
+      if (P->elastic_recoil) {
+        double mu = d[0] * vhat[0] + d[1] * vhat[1] + d[2] * vhat[2];
+        E1 = E * (1.0 - (2.0 * m / P->gas_mass_kg) * (1.0 - mu));
+        rec->recoil = P->weight * (E - E1);
+      }
+      double s1 = sqrt(2.0 * E1 / m);
+      for (int k = 0; k < 3; ++k) v[k] = s1 * d[k];
+      rec->kind = EV_ELASTIC;
+      event[p] = EV_ELASTIC;
+    } else if (x1 < nu_el + nu_io) {
+      double u2[4];
+      or_draw4(P, uid[p], step, 1u, u2);
+      double E_rem = E - E_ion;
+      double E2 = or_opal_secondary(E_rem, B_share, u2[0]);
+      double E1 = E_rem - E2;
+      double d1[3], d2[3];
+      or_scatter_dir(vhat, u[2], u[3], xi, d1);
+      or_scatter_dir(vhat, u2[1], u2[2], xi, d2);
+      double s1 = sqrt(2.0 * E1 / m), s2 = sqrt(2.0 * E2 / m);
+      for (int k = 0; k < 3; ++k) v[k] = s1 * d1[k];
+      rec->child[0] = r1; rec->child[1] = z1;
+      rec->child[2] = s2 * d2[0]; rec->child[3] = s2 * d2[1]; rec->child[4] = s2 * d2[2];
+      rec->kind = EV_IONISE;
+      event[p] = EV_IONISE;
+    } else {
+      event[p] = EV_NULL;
+    }
+  }
+  margin[p] = mg;
+  vr[p] = v[0]; vt[p] = v[1]; vz[p] = v[2];
+}
+
+/* Threads or_step may use (OpenMP builds; 1 otherwise).  The particles'
+ * own work runs in parallel, every sum and list is formed afterwards in
+ * particle order, so the results do not depend on the thread count. */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
+int or_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* One step for particles sorted by ascending uid.  Arrays are updated in
  * place; event[p] >= 10 marks an absorbed particle (the caller removes it).
  * Children are written to the c* arrays and get uids uid_next + k, k the
@@ -347,7 +511,11 @@ static int or_ellipse_entry(const or_params* P, double r0, double z0, double r1,
  * its threshold: walls in cells, collision-type tests relative to nu_max.
  * The surviving particles and the children are deposited into b.  er, ez
  * are node grids, or E at each particle when P->e_per_particle is set.
- * Returns the number of children, or -1 if child_cap was too small. */
+ * Each particle is advanced on its own (or_advance); its contributions to
+ * the tallies and its child are then added in particle order, as a loop
+ * over the particles one after another would add them.
+ * Returns the number of children, or -1 if child_cap was too small (or
+ * the record buffer could not be allocated). */
 int64_t or_step(const or_params* P, int64_t n, double* r, double* z,
                 double* vr, double* vt, double* vz, const uint64_t* uid,
                 int8_t* event, double* margin, const double* er,
@@ -355,140 +523,49 @@ int64_t or_step(const or_params* P, int64_t n, double* r, double* z,
                 int64_t child_cap, double* cr, double* cz, double* cvr,
                 double* cvt, double* cvz, uint64_t* cuid, double* b,
                 double* tally) {
-  const double q = -OR_E, m = OR_ME;
-  const double qmdt2 = q * P->dt / (2.0 * m);
-  const double hr = (P->r_out - P->r_in) / P->nr;
-  const double hz = (P->z_max - P->z_min) / P->nz;
-  const double p_null = 1.0 - exp(-P->nu_max * P->dt);
+  const double q = -OR_E;
   const double E_ion = P->ion_E_th_eV * OR_E;
-  const double B_share = P->opal_B_eV * OR_E;
+  const int64_t block = 32768;
+  or_rec* rec = (or_rec*)malloc((size_t)(n < block ? (n > 0 ? n : 1) : block) * sizeof(or_rec));
+  if (!rec) return -1;
   int64_t nchild = 0;
-
-  for (int64_t p = 0; p < n; ++p) {
-    double r0 = r[p], z0 = z[p];
-    double v0[3] = {vr[p], vt[p], vz[p]};
-    double Er, Ez, Br, Bz;
-    if (P->e_per_particle) {
-      Er = er[p];
-      Ez = ez[p];
-    } else {
-      or_gather(P, er, ez, r0, z0, &Er, &Ez);
-    }
-    or_bfield(P, r0, z0, &Br, &Bz);
-
-    /* Boris: half kick, rotation about B, half kick; components (r,theta,z) */
-    double vm[3] = {v0[0] + qmdt2 * Er, v0[1], v0[2] + qmdt2 * Ez};
-    double t[3] = {qmdt2 * Br, 0.0, qmdt2 * Bz};
-    double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-    double s[3] = {2 * t[0] / (1 + t2), 2 * t[1] / (1 + t2), 2 * t[2] / (1 + t2)};
-    double vpr[3] = {vm[0] + (vm[1] * t[2] - vm[2] * t[1]),
-                     vm[1] + (vm[2] * t[0] - vm[0] * t[2]),
-                     vm[2] + (vm[0] * t[1] - vm[1] * t[0])};
-    double vp[3] = {vm[0] + (vpr[1] * s[2] - vpr[2] * s[1]),
-                    vm[1] + (vpr[2] * s[0] - vpr[0] * s[2]),
-                    vm[2] + (vpr[0] * s[1] - vpr[1] * s[0])};
-    double vn[3] = {vp[0] + qmdt2 * Er, vp[1], vp[2] + qmdt2 * Ez};
-    /* exact work of the two half kicks: (q dt / 4) E . (v0 + vm + vp + vn) */
-    tally[T_WORK_E] += P->weight * (q * P->dt / 4.0) *
-                       (Er * (v0[0] + vm[0] + vp[0] + vn[0]) +
-                        Ez * (v0[2] + vm[2] + vp[2] + vn[2]));
-
-    /* move in the local Cartesian frame (x along rhat, y along thetahat) */
-    double x = r0 + vn[0] * P->dt, y = vn[1] * P->dt;
-    double r1 = sqrt(x * x + y * y);
-    double z1 = z0 + vn[2] * P->dt;
-
-    /* absorbing walls: first crossing along the straight (r,z) segment */
-    double mg = fmin(fmin(fabs(r1 - P->r_in), fabs(r1 - P->r_out)) / hr,
-                     fmin(fabs(z1 - P->z_min), fabs(z1 - P->z_max)) / hz);
-    int wall = -1;
-    double tbest = 2.0;
-    double tw[4] = {3.0, 3.0, 3.0, 3.0};
-    if (r1 <= P->r_in) tw[0] = (P->r_in - r0) / (r1 - r0);
-    if (r1 >= P->r_out) tw[1] = (P->r_out - r0) / (r1 - r0);
-    if (z1 <= P->z_min) tw[2] = (P->z_min - z0) / (z1 - z0);
-    if (z1 >= P->z_max) tw[3] = (P->z_max - z0) / (z1 - z0);
-    for (int w = 0; w < 4; ++w)
-      if (tw[w] < 3.0 && tw[w] < tbest) { tbest = tw[w]; wall = w; }
-    if (P->has_ellipse) {
-      double te, fm;
-      int hit = or_ellipse_entry(P, r0, z0, r1, z1, &te, &fm);
-      mg = fmin(mg, fabs(fm) * 0.5 * fmin(P->e_dr, P->e_dz) / fmin(hr, hz));
-      if (hit && te < tbest) { tbest = te; wall = 4; }
-    }
-    if (wall >= 0) {
-      double v2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
-      tally[wall == 4 ? T_ABS_ELLIPSE : T_ABS_INNER + wall] += P->weight;
-      tally[T_KE_ABSORBED] += P->weight * 0.5 * m * v2;
-      tally[T_N_ABSORBED] += 1.0;
-      event[p] = (int8_t)(EV_WALL_INNER + wall);
-      margin[p] = mg;
-      r[p] = r1; z[p] = z1;
-      vr[p] = vn[0]; vt[p] = vn[1]; vz[p] = vn[2];
-      continue;
-    }
-
-    /* rotate (vr, vtheta) into the basis at the new position */
-    double c = x / r1, sn = y / r1;
-    double v[3] = {c * vn[0] + sn * vn[1], -sn * vn[0] + c * vn[1], vn[2]};
-    r[p] = r1; z[p] = z1;
-    event[p] = EV_NONE;
-
-    /* null-collision Monte Carlo */
-    double u[4];
-    or_draw4(P, uid[p], step, 0u, u);
-    if (u[0] < p_null) {
+  for (int64_t p0 = 0; p0 < n; p0 += block) {
+    const int64_t m = n - p0 < block ? n - p0 : block;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t k = 0; k < m; ++k)
+      or_advance(P, p0 + k, r, z, vr, vt, vz, uid, event, margin, er, ez, step, &rec[k]);
+    for (int64_t k = 0; k < m; ++k) {
+      const or_rec* e = &rec[k];
+      tally[T_WORK_E] += e->work;
+      if (e->wall >= 0) {
+        tally[e->wall == 4 ? T_ABS_ELLIPSE : T_ABS_INNER + e->wall] += P->weight;
+        tally[T_KE_ABSORBED] += e->ke_abs;
+        tally[T_N_ABSORBED] += 1.0;
+        continue;
+      }
+      if (!e->candidate) continue;
       tally[T_N_CANDIDATE] += 1.0;
-      double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-      double speed = sqrt(v2);
-      double E = 0.5 * m * v2;
-      double nu_el, nu_io, xi;
-      or_nu_xi(P, speed, &nu_el, &nu_io, &xi);
-      if (nu_el + nu_io > P->nu_max) tally[T_N_OVER] += 1.0;
-      double x1 = u[1] * P->nu_max;
-      mg = fmin(mg, fmin(fabs(x1 - nu_el), fabs(x1 - nu_el - nu_io)) / P->nu_max);
-      double vhat[3] = {v[0] / speed, v[1] / speed, v[2] / speed};
-      if (x1 < nu_el) {
-        double d[3];
-        or_scatter_dir(vhat, u[2], u[3], xi, d);
-        double E1 = E;
-        if (P->elastic_recoil) {
-          double mu = d[0] * vhat[0] + d[1] * vhat[1] + d[2] * vhat[2];
-          E1 = E * (1.0 - (2.0 * m / P->gas_mass_kg) * (1.0 - mu));
-          tally[T_RECOIL_LOSS] += P->weight * (E - E1);
-        }
-        double s1 = sqrt(2.0 * E1 / m);
-        for (int k = 0; k < 3; ++k) v[k] = s1 * d[k];
+      if (e->over) tally[T_N_OVER] += 1.0;
+      if (e->kind == EV_ELASTIC) {
+        if (P->elastic_recoil) tally[T_RECOIL_LOSS] += e->recoil;
         tally[T_N_ELASTIC] += 1.0;
-        event[p] = EV_ELASTIC;
-      } else if (x1 < nu_el + nu_io) {
-        double u2[4];
-        or_draw4(P, uid[p], step, 1u, u2);
-        double E_rem = E - E_ion;
-        double E2 = or_opal_secondary(E_rem, B_share, u2[0]);
-        double E1 = E_rem - E2;
-        double d1[3], d2[3];
-        or_scatter_dir(vhat, u[2], u[3], xi, d1);
-        or_scatter_dir(vhat, u2[1], u2[2], xi, d2);
-        double s1 = sqrt(2.0 * E1 / m), s2 = sqrt(2.0 * E2 / m);
-        for (int k = 0; k < 3; ++k) v[k] = s1 * d1[k];
-        if (nchild >= child_cap) return -1;
-        cr[nchild] = r1; cz[nchild] = z1;
-        cvr[nchild] = s2 * d2[0]; cvt[nchild] = s2 * d2[1];
-        cvz[nchild] = s2 * d2[2];
+      } else if (e->kind == EV_IONISE) {
+        if (nchild >= child_cap) {
+          free(rec);
+          return -1;
+        }
+        cr[nchild] = e->child[0]; cz[nchild] = e->child[1];
+        cvr[nchild] = e->child[2]; cvt[nchild] = e->child[3]; cvz[nchild] = e->child[4];
         cuid[nchild] = uid_next + (uint64_t)nchild;
         ++nchild;
         tally[T_ION_LOSS] += P->weight * E_ion;
         tally[T_N_IONISE] += 1.0;
-        event[p] = EV_IONISE;
-      } else {
-        event[p] = EV_NULL;
       }
     }
-    margin[p] = mg;
-    vr[p] = v[0]; vt[p] = v[1]; vz[p] = v[2];
   }
-
+  free(rec);
   /* deposit survivors and children at their new positions */
   double qw = q * P->weight;
   int nzp = P->nz + 1;
