@@ -249,10 +249,14 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const unsigned* rk0,
   return c;
 }
 
-// ((x >> 8) + 0.5) 2^-24: exact in float and double, strictly in (0, 1)
+// Uniform (k + 0.5) 2^-24 of k = x >> 8.  FP64: exact.  FP32: the value
+// needs 25 significant bits once k >= 2^23, so it is rounded once (an FMA of
+// the exact k) and held below 1: exact for k < 2^23, otherwise within
+// 2^-25 of the exact value, and always strictly inside (0, 1).  The
+// collision candidate test does not use it (it compares k itself).
 template <typename Real>
 __device__ __forceinline__ Real u01(unsigned x) {
-  return (Real)((x >> 8) + 0.5f) * (Real)(1.0 / 16777216.0);
+  return fminf(__fmaf_rn((float)(x >> 8), 0x1p-24f, 0x1p-25f), 0x1.fffffep-1f);
 }
 template <>
 __device__ __forceinline__ double u01<double>(unsigned x) {
