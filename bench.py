@@ -96,6 +96,15 @@ BYTES_PER_PARTICLE_STEP = 52
 FALLBACK_HBM_GBS = 6800.0
 
 
+def graph_len(sort_every: int) -> int:
+    """Steps per captured CUDA graph of pic_step for a sort period: lcm of
+    the period and 2 (the two deposit buffers), doubled up to at least 8."""
+    n = sort_every if sort_every % 2 == 0 else 2 * sort_every
+    while n < 8:
+        n *= 2
+    return n
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -273,8 +282,16 @@ def run_ours(args, ws, rank):
     sim.step(args.warmup)
     tune = None
     if args.autotune:
-        tune = sim.autotune(80)   # schedule, untimed
-        sim.step(160)             # capture the chosen schedule's graphs, untimed
+        # schedule, untimed: the sort periods that divide the timed step
+        # count, so that the timed steps hold whole sort periods
+        periods = [p for p in (5, 10, 20, 40, 80) if args.steps % graph_len(p) == 0]
+        tune = sim.autotune(80, periods=periods or None)
+    # start the timed region on a graph block (the steps are then replayed
+    # graphs), after capturing the schedule's graphs untimed
+    se = tune["sort_every"] if tune else cfgs[0]["sort_every"]
+    gl = graph_len(se)
+    at = sim.diagnostics()["step"]
+    sim.step((gl - at % gl) % gl + 2 * gl)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -333,14 +350,15 @@ def run_ours(args, ws, rank):
     cfg = cfgs[0]
     grid = f"{cfg['nr']}x{cfg['nz']}"
     nnodes = (cfg["nr"] + 1) * (cfg["nz"] + 1)
+    live = int(round(units / args.steps))   # live particles per timed step
     if S == 1:
         config = {"workload": name if not args.particles else f"{name} (particles={n0})",
-                  "particles": n0, "grid": grid,
+                  "particles": live, "particles_loaded": n0, "grid": grid,
                   "sort_every": tune["sort_every"] if tune else cfg["sort_every"],
                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                  "l2": f"inputs larger than L2 (particle store {n0 * 52 / 1e9:.2f} GB per step)"}
+                  "l2": f"inputs larger than L2 (particle store {live * 52 / 1e9:.2f} GB per step)"}
     else:
-        config = {"workload": name, "simulations": S, "particles": n0,
+        config = {"workload": name, "simulations": S, "particles": live, "particles_loaded": n0,
                   "particles_min_max": [min(len(p[0]) for p in parts),
                                         max(len(p[0]) for p in parts)],
                   "grid": f"{S} x {grid}",
@@ -666,23 +684,42 @@ def run_steady(args, ws, rank):
     }
 
 
+def host_cores() -> int:
+    """Cores this process may run on (nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(cfg, parts, n_sample=None, steps=2, name=WORKLOAD):
-    """The oracle as it stands (single thread) on a bounded sample: the
-    first n_sample particles of the load (all by default) with the full grid
-    and field solve, ``steps`` steps."""
+    """The oracle as it stands on a bounded sample: the first n_sample
+    particles of the load (all by default) with the full grid and field
+    solve, ``steps`` steps, on all host cores (OpenMP over the particles'
+    own steps; sums in particle order) and on one core.  The main figure is
+    the all-core one; both give bitwise the same states."""
     import oracle
     oracle.build()
     sel = slice(None) if n_sample is None else slice(0, n_sample)
-    o = oracle.OracleSim(cfg, *[a[sel] for a in parts])
-    t0 = time.perf_counter()
-    units = 0
-    for _ in range(steps):
-        units += o.n
-        o.step()
-    sec = time.perf_counter() - t0
-    return {"value": units / sec, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of {len(parts[0][sel])} particles of {name} "
-                      "(full grid, field solve included)", "seconds": sec}
+    res = {}
+    for cores in (host_cores(), 1):
+        oracle.set_threads(cores)
+        o = oracle.OracleSim(cfg, *[a[sel] for a in parts])
+        t0 = time.perf_counter()
+        units = 0
+        for _ in range(steps):
+            units += o.n
+            o.step()
+        sec = time.perf_counter() - t0
+        res[cores] = (units / sec, sec, oracle.threads())
+    oracle.set_threads(host_cores())
+    many, one = res[host_cores()], res[1]
+    sample = (f"{steps} steps of {len(parts[0][sel])} particles of {name} "
+              "(full grid, field solve included)")
+    return {"value": many[0], "unit": "particle-steps/s", "cores": many[2], "kind": "oracle",
+            "sample": sample, "seconds": many[1], "nproc": host_cores(),
+            "single_core": {"value": one[0], "unit": "particle-steps/s", "cores": 1,
+                            "seconds": one[1]}}
 
 
 def run_reference(args, ws, rank):
@@ -708,7 +745,14 @@ def run_reference(args, ws, rank):
     if name == TABLES:
         E, sel, sio, xi = cross_section_tables(cfg["ion_E_th_eV"])
         cfg["xs"] = dict(E_eV=E, sigma_el=sel, sigma_io=sio, xi=xi)
-    n = 20_000
+    # the spline and trap oracles evaluate dense basis rows per particle:
+    # a small sample there
+    # elsewhere at most 2e7 particle-steps over the whole run, at least
+    # 20 000 particles per step
+    n = 20_000 if name in (SPLINE, TRAP) else int(
+        min(1_000_000, max(20_000, 2e7 // (args.steps + args.warmup))))
+    oracle.set_threads(host_cores())
+    cores = oracle.threads()
     parts = seed_particles(cfg, n=n)
     if name == TRAP:
         parts = outside_ellipse(parts)
@@ -729,8 +773,10 @@ def run_reference(args, ws, rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "particles": n, "grid": f"{cfg['nr']}x{cfg['nz']}",
                        "parallelism": "cpu oracle, rank 0 only"},
-            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n} particles of {name} per step, full grid and field solve"},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": cores,
+                             "kind": "oracle", "nproc": host_cores(),
+                             "sample": f"{n} particles of {name} per step, full grid and field "
+                                       "solve (OpenMP over the particles' own steps)"},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

@@ -488,6 +488,13 @@ typedef struct pic_tune_result {
   int32_t trials;                /* candidates timed */
 } pic_tune_result;
 int pic_autotune(pic_handle* h, int64_t steps_per_trial, pic_tune_result* out);
+/* The same with the caller's candidate sort periods (n_periods of them,
+ * 1 .. 64, each 1 .. 100000): for instance only the periods that divide a
+ * planned run's step count, so that the run holds whole sort periods.
+ * Trials last a multiple of every candidate's graph block.  PIC_EINVAL on
+ * a bad list.  This library's addition; the paper has no counterpart. */
+int pic_autotune_periods(pic_handle* h, int64_t steps_per_trial, const int32_t* periods,
+                         int n_periods, pic_tune_result* out);
 
 /* Images of the current field state of every simulation, FP32 DEVICE
  * arrays of n_sims x nr x nz pixels in the net's layout (pixel (s, y, x) =

@@ -391,16 +391,25 @@ class Simulation:
         p = [ctypes.c_void_p(t.data_ptr()) if t is not None else None for t in (rho, phi_rho)]
         _check(L.pic_field_images(self.h, *p), "pic_field_images")
 
-    def autotune(self, steps_per_trial: int = 80) -> dict:
+    def autotune(self, steps_per_trial: int = 80, periods=None) -> dict:
         """pic_autotune: time sort periods and fused-kernel grids on the
-        running simulation (which advances) and keep the fastest."""
+        running simulation (which advances) and keep the fastest.  periods:
+        the candidate sort periods (pic_autotune_periods), default {5, 10,
+        20, 40, 80}."""
         class R(ctypes.Structure):
             _fields_ = [("sort_every", c_i32), ("particle_blocks", c_i32),
                         ("ms_per_step", c_d), ("trials", c_i32)]
         L = lib()
-        L.pic_autotune.argtypes = [ctypes.c_void_p, c_i64, ctypes.c_void_p]
         r = R()
-        _check(L.pic_autotune(self.h, int(steps_per_trial), ctypes.byref(r)), "pic_autotune")
+        if periods is None:
+            L.pic_autotune.argtypes = [ctypes.c_void_p, c_i64, ctypes.c_void_p]
+            _check(L.pic_autotune(self.h, int(steps_per_trial), ctypes.byref(r)), "pic_autotune")
+        else:
+            arr = (c_i32 * len(periods))(*[int(p) for p in periods])
+            L.pic_autotune_periods.argtypes = [ctypes.c_void_p, c_i64, ctypes.c_void_p,
+                                               ctypes.c_int, ctypes.c_void_p]
+            _check(L.pic_autotune_periods(self.h, int(steps_per_trial), arr, len(periods),
+                                          ctypes.byref(r)), "pic_autotune_periods")
         return {name: getattr(r, name) for name, _ in R._fields_}
 
     def profile_start(self):

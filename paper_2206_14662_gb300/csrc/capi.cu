@@ -415,11 +415,13 @@ int alloc_soa(pic_handle* h, Soa<Real>& s) {
 
 // A graph block returns the alternating buffers (sort ping-pong, FP32
 // deposit buffers) to a fixed pattern: lcm(sort_every, 2) steps, at least 8.
-void set_graph_len(pic_handle* h) {
-  const int se = h->cfg.sort_every;
-  h->graph_len = se > 0 ? (se % 2 == 0 ? se : 2 * se) : 2;
-  while (h->graph_len < 8) h->graph_len *= 2;
+int graph_len_of(int se) {
+  int len = se > 0 ? (se % 2 == 0 ? se : 2 * se) : 2;
+  while (len < 8) len *= 2;
+  return len;
 }
+
+void set_graph_len(pic_handle* h) { h->graph_len = graph_len_of(h->cfg.sort_every); }
 
 void drop_graphs(pic_handle* h) {
   for (auto& row : h->graph)
@@ -1655,13 +1657,30 @@ int pic_attach_unet(pic_handle* h, pic_unet* net, double rho_scale, double phi_s
 // integer sum, child uids go by parent rank), each candidate timed with
 // events over whole graph blocks; the fastest is kept.
 int pic_autotune(pic_handle* h, int64_t steps_per_trial, pic_tune_result* out) {
-  if (!h || !out || steps_per_trial < 1) return PIC_EINVAL;
+  const int32_t sort_cand[] = {5, 10, 20, 40, 80};
+  return pic_autotune_periods(h, steps_per_trial, sort_cand, 5, out);
+}
+
+int pic_autotune_periods(pic_handle* h, int64_t steps_per_trial, const int32_t* periods,
+                         int n_periods, pic_tune_result* out) {
+  if (!h || !out || steps_per_trial < 1 || !periods || n_periods < 1 || n_periods > 64)
+    return PIC_EINVAL;
+  for (int k = 0; k < n_periods; ++k)
+    if (periods[k] < 1 || periods[k] > 100000) return PIC_EINVAL;
   if (h->sticky) return h->sticky;
   std::memset(out, 0, sizeof(*out));
-  const int sort_cand[] = {5, 10, 20, 40, 80};
+  const std::vector<int> sort_cand(periods, periods + n_periods);
   std::vector<int> grid_cand;
   for (int b = 1; b <= h->blocks_per_sm; ++b) grid_cand.push_back(h->sms * b);
-  const long long trial = (steps_per_trial + 79) / 80 * 80;   // whole periods of every candidate
+  // whole graph blocks of every candidate: a multiple of the lcm of their
+  // block lengths
+  long long unit = 1;
+  for (int se : sort_cand) {
+    const long long g = graph_len_of(se);
+    unit = unit / std::gcd(unit, g) * g;
+    if (unit > 1000000) return PIC_EINVAL;
+  }
+  const long long trial = (steps_per_trial + unit - 1) / unit * unit;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
