@@ -22,6 +22,10 @@ mean over 2 x 2 blocks; upconv2 the transposed 2 x 2 convolution of stride
 channels first.  Arrays are (batch, H, W, channels).  The loss is
 L = sum (y - t)^2 / (2 N), N the number of output values.
 
+Every operation keeps the dtype of its inputs: FP64 arrays (the oracle)
+give an FP64 network; FP32 arrays give the same network in plain FP32
+arithmetic, which tells how far FP32 rounding alone moves a result.
+
 ``forward`` and ``backward`` take an optional rounding ``q`` applied where
 a reduced-precision implementation stores values (the input, every stored
 activation and activation gradient, the convolution weights): with
@@ -92,7 +96,7 @@ def _ident(a):
 def conv3(x, W, b):
     B, H, Wd, _ = x.shape
     xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0)))
-    out = np.zeros((B, H, Wd, W.shape[3])) + b
+    out = np.zeros((B, H, Wd, W.shape[3]), dtype=x.dtype) + b
     for ky in range(3):
         for kx in range(3):
             out += xp[:, ky:ky + H, kx:kx + Wd, :] @ W[ky, kx]
@@ -124,7 +128,7 @@ def pool_backward(g):
 
 def upconv(x, U, b):
     B, H, W, _ = x.shape
-    out = np.zeros((B, 2 * H, 2 * W, U.shape[3])) + b
+    out = np.zeros((B, 2 * H, 2 * W, U.shape[3]), dtype=x.dtype) + b
     for dy in range(2):
         for dx in range(2):
             out[:, dy::2, dx::2, :] += x @ U[dy, dx]
@@ -215,3 +219,20 @@ def backward(p: dict, a: dict, gy: np.ndarray, q=None):
         gpool = q(gpool)
     g["x"] = gpool
     return g
+
+
+# ------------------------------------------------------------ optimiser
+
+def adam_step(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One step of Adam (Kingma and Ba, 2015, Algorithm 1) in FP64 at step
+    number t >= 1: the moment estimates m <- beta1 m + (1 - beta1) g and
+    v <- beta2 v + (1 - beta2) g^2, their bias-corrected values
+    m / (1 - beta1^t) and v / (1 - beta2^t), and the update
+    w <- w - lr mhat / (sqrt(vhat) + eps).  Returns the new (w, m, v)."""
+    w, g, m, v = (np.asarray(a, dtype=np.float64) for a in (w, g, m, v))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return w - lr * mhat / (np.sqrt(vhat) + eps), m, v
+

@@ -103,6 +103,90 @@ def test_bf16_tensor_core_mode_production_width(torch, H, W):
     assert max(_rel(g[sl], go[sl]) for sl in _layer_slices(32).values()) <= 8e-2
 
 
+def test_production_grid_128x512(torch):
+    """The size the net runs at inside the loop: base width 32 on the
+    128 x 512 grid, batch 1, the output gradient of a loss against a smooth
+    target.  One FP64 oracle forward and backward is the reference for both
+    modes: the FP32 test mode to 1e-5 (output, every layer's gradients, the
+    input gradient), the BF16 tensor-core mode to the BF16 tolerances of the
+    narrower production-width case."""
+    from paper_2206_14662_gb300.unet import UNet
+    c, B, H, W = 32, 1, 128, 512
+    flat = unet_init_flat(c, seed=11, head_std=0.3, bias_std=0.1).astype(np.float32)
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal((B, H, W, 2)).astype(np.float32)
+    p = U.unflatten(flat.astype(np.float64), c)
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    t = np.sin(2 * np.pi * yy / H) * np.cos(2 * np.pi * xx / W)
+    yo, a = U.forward(p, x.astype(np.float64))
+    gy = ((yo - t) / (B * H * W)).astype(np.float32)
+    go = U.backward(p, a, gy.astype(np.float64))
+    go_flat = U.flatten({k: v for k, v in go.items() if k != "x"})
+    # the same network in plain FP32 arithmetic (numpy, blocked sums): how
+    # far FP32 rounding alone moves each result from the FP64 oracle.  The
+    # weight gradients sum over up to 65 536 pixels and the input gradient
+    # comes through 18 layers, so at this size that is well above 1e-5.
+    p32 = {k: v.astype(np.float32) for k, v in p.items()}
+    y32, a32 = U.forward(p32, x)
+    g32 = U.backward(p32, a32, gy)
+    g32_flat = U.flatten({k: v for k, v in g32.items() if k != "x"})
+    res = {}
+    for prec in (32, 16):
+        net = UNet(c, H, W, B, precision=prec)
+        net.set_params(flat)
+        y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+        gx = torch.zeros((B, H, W, 2), dtype=torch.float32, device="cuda")
+        net.backward(torch.from_numpy(gy).cuda(), gx)
+        res[prec] = (y, net.get_grads(), gx.cpu().numpy())
+        net.close()
+    # FP32 test mode: within 10x of plain FP32's own distance from the FP64
+    # oracle (the kernels sum in other orders: tiles, pixel splits, FP32
+    # atomics), and never worse than 1e-5 where FP32 is that close.  A
+    # tiling or index mistake gives errors of order one.
+    y, g, gx = res[32]
+    bar = lambda e32: max(1e-5, 10.0 * e32)
+    assert _rel(y, yo) <= bar(_rel(y32, yo))
+    for name, sl in _layer_slices(c).items():
+        assert _rel(g[sl], go_flat[sl]) <= bar(_rel(g32_flat[sl], go_flat[sl])), name
+    assert _rel(gx, go["x"]) <= bar(_rel(g32["x"], go["x"]))
+    y, g, gx = res[16]
+    assert _rel(y, yo) <= 1e-2
+    assert _rel(g, go_flat) <= 2.5e-2
+
+
+def test_adam_matches_oracle(torch):
+    """Three training steps on the GPU (forward, loss gradient, backward,
+    Adam); after each, the parameters equal the oracle's FP64 Adam step
+    (Kingma and Ba, Algorithm 1) applied to the GPU's own gradients of that
+    step, element by element, within FP32 rounding of the weights plus
+    1e-5 of the step size per step."""
+    from paper_2206_14662_gb300.unet import UNet
+    c, B, H, W = 8, 2, 16, 32
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    flat = unet_init_flat(c, seed=4).astype(np.float32)
+    rng = np.random.default_rng(5)
+    x = torch.from_numpy(rng.standard_normal((B, H, W, 2)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((B, H, W)).astype(np.float32)).cuda()
+    net = UNet(c, H, W, B, precision=32)
+    net.set_params(flat)
+    w = flat.astype(np.float64)
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    moved = 0.0
+    for step in (1, 2, 3):
+        net.train_step(x, t, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        g = net.get_grads().astype(np.float64)
+        # (weights feeding inactive ReLUs get exactly zero gradient)
+        assert np.count_nonzero(g) > 0.5 * g.size
+        w, m, v = U.adam_step(w, g, m, v, step, lr, b1, b2, eps)
+        got = net.get_params().astype(np.float64)
+        ulp = np.spacing(np.abs(w).astype(np.float32)).astype(np.float64)
+        assert (np.abs(got - w) <= step * (ulp + 1e-5 * lr)).all(), step
+        moved = np.abs(got - flat).max()
+    net.close()
+    assert moved > 2 * lr
+
+
 def test_training_reduces_the_loss(torch):
     """Adam on a fixed smooth mapping (the target is a blurred copy of the
     first input channel): the loss falls by an order of magnitude."""

@@ -80,3 +80,27 @@ def test_gradients_match_central_differences(seed):
         fd = (L(h) - L(-h)) / (2 * h)
         an = float(np.sum(g[key] * d))
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-8) + 1e-12, (key, fd, an)
+
+
+def test_adam_first_steps_closed_forms():
+    """Adam's first steps worked out by hand: at t = 1 the bias-corrected
+    moments are g and g^2, so with eps = 0 every weight moves by exactly
+    lr sign(g) whatever |g|; a constant gradient keeps that step at t = 2;
+    two different gradients g1, g2 give mhat = (beta1 g1 + g2)/(1 + beta1)
+    and vhat = (beta2 g1^2 + g2^2)/(1 + beta2) at t = 2."""
+    lr, b1, b2 = 1e-3, 0.9, 0.999
+    w0 = np.array([0.5, -0.25, 2.0, 0.0, 1e-3])
+    g1 = np.array([3.0, -1e-4, 2.5e5, -7.0, 0.5])
+    w1, m1, v1 = U.adam_step(w0, g1, np.zeros(5), np.zeros(5), 1, lr, b1, b2, eps=0.0)
+    assert np.allclose(w1, w0 - lr * np.sign(g1), rtol=0, atol=1e-15)
+    assert np.allclose(m1, 0.1 * g1, rtol=1e-15) and np.allclose(v1, 0.001 * g1 ** 2, rtol=1e-12)
+    w2, _, _ = U.adam_step(w1, g1, m1, v1, 2, lr, b1, b2, eps=0.0)
+    assert np.allclose(w2, w0 - 2 * lr * np.sign(g1), rtol=0, atol=1e-15)
+    g2 = np.array([-1.0, 2e-4, 1e5, -7.0, 0.25])
+    w2, m2, v2 = U.adam_step(w1, g2, m1, v1, 2, lr, b1, b2, eps=1e-8)
+    mhat = (b1 * g1 + g2) / (1 + b1)
+    vhat = (b2 * g1 ** 2 + g2 ** 2) / (1 + b2)
+    assert np.allclose(w2, w1 - lr * mhat / (np.sqrt(vhat) + 1e-8), rtol=0, atol=1e-15)
+    # a zero gradient from zero moments leaves the weight where it is
+    w, m, v = U.adam_step(np.ones(2), np.zeros(2), np.zeros(2), np.zeros(2), 1, lr)
+    assert np.array_equal(w, np.ones(2)) and not m.any() and not v.any()
