@@ -39,7 +39,7 @@ def _collision_cfg(precision, **kw):
 
 # ------------------------------------------------------------ field solve
 
-@pytest.mark.parametrize("nr,nz", [(32, 64), (128, 512), (20, 48), (7, 6), (2, 2)])
+@pytest.mark.parametrize("nr,nz", [(32, 64), (128, 512), (256, 1024), (20, 48), (7, 6), (2, 2)])
 def test_field_solve_matches_oracle(nr, nz):
     """Same right-hand side: the separable DCT/Thomas solve against the
     sparse direct solve of the assembled finite-element system."""
@@ -196,6 +196,53 @@ def test_self_consistent_steps(precision, warm):
         assert np.abs(g["r"][gi] - o.r[keep]).max() / hr <= tol
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_large_grid_steps(precision):
+    """The large workload's grid, 256 x 1024 cells (the field solve's
+    transforms are 2048-point FFTs there), with 2e5 of its particles at a
+    pressure and temperature that make collisions, ionisation and wall
+    losses happen: three self-consistent steps against the oracle's
+    (particles, event counts, deposit and potential)."""
+    from paper_2206_14662_gb300._capi import PIC_GRID_PHI, PIC_GRID_RHS
+    cfg = workload("mirror_256x1024_2e8", n_init=200_000, capacity=400_000, p_mbar=0.3,
+                   T0_eV=30.0, precision=precision,
+                   poisson_rtol=1e-12 if precision == 64 else 1e-8,
+                   poisson_maxit=8 if precision == 64 else 2)
+    parts = seed_particles(cfg)
+    o = oracle.OracleSim(cfg, *parts)
+    sim = make_gpu(cfg, parts)
+    for _ in range(3):
+        o.step()
+    sim.step(3)
+    g = by_uid(sim.export_particles())
+    phi = sim.get_grid(PIC_GRID_PHI)
+    b = sim.get_grid(PIC_GRID_RHS)
+    d = sim.diagnostics()
+    sim.close()
+    assert o.tally[oracle.T_N_ELASTIC] > 100 and o.tally[oracle.T_N_IONISE] > 0
+    assert o.tally[oracle.T_N_ABSORBED] > 0
+    assert d["poisson_relres"] <= cfg["poisson_rtol"]
+    vac = oracle.poisson_solve(cfg, np.zeros_like(o.b))
+    if precision == 64:
+        compare_states(cfg, 64, g, o, tol=1e-9)
+        assert d["n_elastic"] == o.tally[oracle.T_N_ELASTIC]
+        assert d["n_ionise"] == o.tally[oracle.T_N_IONISE]
+        assert np.abs(b - o.b).max() <= 1e-10 * np.abs(o.b).max()
+        assert np.abs(phi - o.phi).max() <= 1e-10 * np.abs(o.phi).max()
+        assert np.abs((phi - vac) - (o.phi - vac)).max() <= 1e-8 * np.abs(o.phi - vac).max()
+    else:
+        keep = np.isin(o.uid, g["uid"])
+        assert keep.mean() > 0.999
+        gi = np.searchsorted(g["uid"], o.uid[keep])
+        hr = (cfg["r_out"] - cfg["r_in"]) / cfg["nr"]
+        hz = (cfg["z_max"] - cfg["z_min"]) / cfg["nz"]
+        assert np.abs(g["r"][gi] - o.r[keep]).max() / hr <= 2e-5
+        assert np.abs(g["z"][gi] - o.z[keep]).max() / hz <= 2e-5
+        assert abs(d["n_elastic"] - o.tally[oracle.T_N_ELASTIC]) <= 3
+        assert np.abs(phi - o.phi).max() <= 1e-5 * np.abs(o.phi).max()
+        assert np.abs(b - o.b).max() <= 1e-5 * np.abs(o.b).max() + 3 * oracle.QE * o.P.weight
+
+
 def test_brute_force_tiny():
     """N = 1..4 particles over 100 steps, fixed field, FP64: particle by
     particle."""
@@ -252,6 +299,30 @@ def test_capacity_overflow_is_reported():
         assert ei.value.code == PIC_ECAPACITY
         with pytest.raises(PicError):
             sim.step(1)
+
+
+def test_unconverged_field_solve_latches_enoconv():
+    """A field solve that cannot reach its tolerance (one refinement sweep
+    towards a relative residual of 1e-30) latches PIC_ENOCONV on the
+    device: the next synchronising call reports it and pic_step keeps
+    returning it until particles are loaded again."""
+    from paper_2206_14662_gb300._capi import PIC_ENOCONV, PicError, Simulation
+    cfg = workload("coax_32x64_1e4", precision=32, poisson_rtol=1e-30, poisson_maxit=1)
+    parts = seed_particles(cfg, n=2000)
+    with Simulation(cfg) as sim:
+        code = None
+        try:
+            sim.load_particles(*parts)
+            sim.step(2)
+            sim.diagnostics()
+        except PicError as e:
+            code = e.code
+        assert code == PIC_ENOCONV
+        with pytest.raises(PicError) as ei:
+            sim.step(1)
+        assert ei.value.code == PIC_ENOCONV
+        d = sim.diagnostics(raise_on_error=False)
+        assert d["poisson_relres"] > 1e-30
 
 
 def test_invalid_inputs_rejected():
