@@ -194,15 +194,17 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
 /* Load n macro-electrons into simulation `sim` (0 <= sim < n_sims) from
  * host FP64 arrays (structure of arrays): positions r, z (strictly inside
  * the gap), velocity components vr, vtheta, vz (the velocity at half step
- * -1/2 of the leapfrog) and unique uids (< 2^32).  Replaces the
+ * -1/2 of the leapfrog) and unique uids (< 2^32 - 1, so that the uid
+ * counter, max uid + 1, fits in 32 bits).  Replaces the
  * simulation's particles, resets its tallies and uid counter (max uid + 1),
  * deposits the charge and, unless fixed_efield, solves the field (Sec. II.A
  * seed load and first field; in a batch every simulation is solved again
  * from its last deposit, which leaves the others' fields as they were).  A
  * single simulation restarts at step 0; a simulation of a batch joins at the
  * batch's current step.  Synchronises (page-locked host arrays make the
- * copies faster).  PIC_EINVAL for out-of-domain or non-finite values, uids
- * at or above 2^32, or n above the simulation's capacity. */
+ * copies faster).  PIC_EINVAL for out-of-domain positions, uids at or
+ * above 2^32 - 1, or n above the simulation's capacity; PIC_ENONFINITE for
+ * a non-finite velocity. */
 int pic_load_particles(pic_handle* h, int sim, const double* r,
                        const double* z, const double* vr, const double* vt,
                        const double* vz, const uint64_t* uid, int64_t n);
@@ -355,10 +357,11 @@ int pic_solve_field(pic_handle* h, const double* b, double* phi,
  *   phi     DEVICE pointer, receives the potential on all nodes (V)
  *   relres  host pointer or NULL.  Non-NULL: the call synchronises the
  *           stream, stores the relative residual and returns PIC_ENOCONV if
- *           it exceeds poisson_rtol.  NULL: the work is only queued.
+ *           it exceeds poisson_rtol.  NULL: the work is only queued,
+ *           and a solve that misses poisson_rtol is not reported.
  *   cuda_stream  cudaStream_t of the caller (NULL = legacy default stream)
  * Allocates nothing: its working memory is one fixed device array of about
- * 5.5 MB inside the library, which every GPU that loads the library keeps
+ * 4 MB inside the library, which every GPU that loads the library keeps
  * until the process exits.  Grids above PIC_STATIC_MAX_NODES nodes, or with
  * nz > 4096 or nr > 401, return PIC_EINVAL before any device work.  All calls share that
  * array: calls whose GPU work overlaps (other streams, other host threads)

@@ -10,7 +10,7 @@
 // right-hand side, per-mode Thomas factors, FFT twiddles, space-charge
 // potential, node field, residual accumulators) lives in one file-scope
 // device array, g_field_scratch, of fixed size.  Every GPU that loads the
-// library holds that array (about 5.5 MB) until the process exits.
+// library holds that array (about 4 MB) until the process exits.
 //
 // The array is shared by all calls: each call clears what must start at
 // zero (the residual accumulators, the space-charge potential) and
@@ -31,7 +31,13 @@ namespace {
 
 constexpr int kMaxNodes = PIC_STATIC_MAX_NODES;
 constexpr int kMaxM = 4096;                 // nz limit of the library
-constexpr int kMaxRadial = kMaxNodes / 3;   // nr + 1 when nz = 2
+// radial node lines nr + 1: the Thomas sweep's shared-memory columns
+// (four (nr - 1) x 32 floats, at most 200 KB, the check at entry) admit
+// nr <= 401
+constexpr int kMaxRadial = 402;
+static_assert(4LL * (kMaxRadial - 2) * 32 * 4 <= 200 * 1024 &&
+                  4LL * (kMaxRadial - 1) * 32 * 4 > 200 * 1024,
+              "kMaxRadial is the largest nr + 1 the Thomas limit admits");
 
 // scratch layout: byte offsets, each region 256-byte aligned
 constexpr size_t al256(size_t x) { return (x + 255) / 256 * 256; }
@@ -86,6 +92,7 @@ extern "C" int pic_solve_field_static(const pic_config* cfg, const double* b, do
   const long long nodes = (long long)(c.nr + 1) * (c.nz + 1);
   if (nodes > kMaxNodes) return PIC_EINVAL;   // beyond the static scratch
   if ((long long)4 * (c.nr - 1) * 32 * 4 > 200 * 1024) return PIC_EINVAL;   // Thomas columns
+  if (c.nr + 1 > kMaxRadial) return PIC_EINVAL;   // (implied by the line above)
   cudaStream_t stream = (cudaStream_t)cuda_stream;
 
   int dev = 0;

@@ -170,6 +170,7 @@ namespace web {
 // device copies and work vectors of a web-spline system (pic_web_device)
 struct Dev {
   cudaStream_t stream = nullptr;
+  int device = 0;              // the device the arrays live on
   int *a_ptr = nullptr, *a_col = nullptr, *inner_full = nullptr;
   int *t_ptr = nullptr, *t_col = nullptr, *tt_ptr = nullptr, *tt_col = nullptr;
   double *a_val = nullptr, *g = nullptr, *t_val = nullptr, *tt_val = nullptr;
@@ -755,6 +756,10 @@ int pic_web_device(pic_web* w, void* cuda_stream) {
   if (w->dev) return PIC_OK;
   Dev* d = new Dev();
   d->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&d->device) != cudaSuccess) {
+    delete d;
+    return PIC_ECUDA;
+  }
   w->dev = d;
   const int ni = (int)w->inner_full.size(), nf = w->mr * w->mz;
   // T^T (inner rows) from T (full rows)
@@ -901,16 +906,34 @@ int pic_web_set_stream(pic_web* w, void* cuda_stream) {
 int pic_web_direct(pic_web* w) {
   using namespace pic::web;
   if (!w || !w->dev) return PIC_EINVAL;
-  if (w->dev->inv) return PIC_OK;
+  Dev* d = w->dev;
+  if (d->inv) return PIC_OK;
   std::vector<double> inv;
   if (!dense_inverse(w, inv)) return PIC_ENOCONV;
-  if (cudaMalloc(&w->dev->inv, inv.size() * sizeof(double)) != cudaSuccess ||
-      cudaMemcpy(w->dev->inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    return PIC_ENOMEM;
+  // on the device the system was built on, queued on its stream; the
+  // inverse is published only once its copy has completed
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(d->device) != cudaSuccess)
+    return PIC_ECUDA;
+  const size_t bytes = inv.size() * sizeof(double);
+  double* p = nullptr;
+  int rc = PIC_OK;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+    rc = PIC_ENOMEM;
+  } else if (cudaMemcpyAsync(p, inv.data(), bytes, cudaMemcpyHostToDevice, d->stream) !=
+                 cudaSuccess ||
+             cudaStreamSynchronize(d->stream) != cudaSuccess) {
+    rc = PIC_ECUDA;
   }
-  return PIC_OK;
+  if (rc) {
+    if (p) cudaFree(p);
+    cudaGetLastError();
+  } else {
+    d->inv = p;
+  }
+  cudaSetDevice(prev);
+  return rc;
 }
 
 int pic_web_solve_direct(pic_web* w, const double* f, double* c, int dirichlet) {

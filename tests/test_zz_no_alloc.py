@@ -2,9 +2,10 @@
 device memory (their framework owns the device pool, or they may only touch
 the buffers they are handed): called through the C ABI with device buffers
 the test owns, twice in a row with different right-hand sides, it must give
-the potential of the handle-based pic_solve_field within the field-solve
-tolerance of the other tests (1e-10 of the potential's scale), and it must
-refuse grids beyond its fixed working array.
+the potential of the handle-based pic_solve_field and of the oracle's
+sparse direct solve within the field-solve tolerance of the other tests
+(1e-10 of the potential's scale), its calls must not take device memory,
+and it must refuse grids beyond its fixed working array.
 
 This file is collected last so that a failure here, with -x, stops the run
 only after every other test has run.
@@ -29,6 +30,7 @@ def torch_cuda():
 
 def test_static_solve_matches_handle_solve(torch_cuda):
     torch = torch_cuda
+    import oracle
     from paper_2206_14662_gb300._capi import Simulation, solve_field_static
     cfg = workload("mirror_128x512_1e7", precision=64)
     nn = (cfg["nr"] + 1) * (cfg["nz"] + 1)
@@ -38,7 +40,7 @@ def test_static_solve_matches_handle_solve(torch_cuda):
         ref = [sim.solve_field(b)[0] for b in rhs]
     stream = torch.cuda.current_stream().cuda_stream
     phi = torch.empty(nn, dtype=torch.float64, device="cuda")
-    for b, phi_ref in zip(rhs, ref):     # two calls in a row share the scratch
+    for k, (b, phi_ref) in enumerate(zip(rhs, ref)):   # two calls in a row share the scratch
         b_dev = torch.from_numpy(b).to("cuda")
         phi.fill_(float("nan"))
         rel = solve_field_static(cfg, b_dev.data_ptr(), phi.data_ptr(), stream)
@@ -46,6 +48,28 @@ def test_static_solve_matches_handle_solve(torch_cuda):
         assert np.isfinite(got).all()
         assert np.abs(got - phi_ref).max() <= 1e-10 * np.abs(phi_ref).max()
         assert rel <= cfg["poisson_rtol"]
+        if k == 0:   # the plain definition: the oracle's sparse direct solve
+            phi_o = oracle.poisson_solve(cfg, b)
+            assert np.abs(got - phi_o).max() <= 1e-10 * np.abs(phi_o).max()
+
+
+def test_static_solve_takes_no_device_memory(torch_cuda):
+    """After a first call (which loads the library's kernels and the array
+    with them), further calls leave the device's free memory unchanged."""
+    torch = torch_cuda
+    from paper_2206_14662_gb300._capi import solve_field_static
+    cfg = workload("coax_32x64_1e4", precision=64)
+    nn = (cfg["nr"] + 1) * (cfg["nz"] + 1)
+    b = torch.from_numpy(-np.random.default_rng(3).random(nn) * 1e-13).to("cuda")
+    phi = torch.empty(nn, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    solve_field_static(cfg, b.data_ptr(), phi.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        solve_field_static(cfg, b.data_ptr(), phi.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0
 
 
 def test_static_solve_rejects_grids_beyond_its_array(torch_cuda):
