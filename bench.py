@@ -329,8 +329,11 @@ def run_ours(args, ws, rank):
         for k in range(S):
             sim.load_particles(*pinned[k], sim=k)
         sim.step(args.steps)
+        # the spline fields have no node deposit: their result is the
+        # diagnostics record alone
+        dens = name not in (SPLINE, TRAP)
         for k in range(S):   # a load resets the simulation's counters
-            e2e_units += sim.diagnostics(density=True, sim=k)["n_pushed"]
+            e2e_units += sim.diagnostics(density=dens, sim=k)["n_pushed"]
     t1 = time.perf_counter()
     sim.close()
 
@@ -382,7 +385,8 @@ def run_ours(args, ws, rank):
         "config": config,
         "e2e": None if not args.e2e else {"value": e2e_units * ws / esec, "unit": "particle-steps/s",
                 "h2d_bytes_per_step": int(n0 * 48 / args.steps),
-                "d2h_bytes_per_step": int(S * (nnodes * 8 + 512) / args.steps)},
+                "d2h_bytes_per_step": int(S * (nnodes * 8 * (name not in (SPLINE, TRAP)) + 512)
+                                          / args.steps)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm",
                      "kernel": ("k_particle_step_batch<float>" if S > 1 else
@@ -393,6 +397,10 @@ def run_ours(args, ws, rank):
                      "achieved": achieved,
                      "peak": peak, "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (traffic["dram_bytes_per_particle"] * per_launch_units) if traffic else None,
+                     "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                                        f"{traffic['workload']}: {traffic['dram_bytes_per_particle']} "
+                                        "B per particle-step, times this launch's particles")
+                                       if traffic else None,
                      "kernel_ms_per_launch": kern_ms,
                      "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
         "stage_ms_per_step": {"particle": prof["particle_ms"] / prof_steps,
@@ -441,6 +449,11 @@ def run_moments(args, ws, rank):
     sim = Simulation(cfg)
     sim.load_particles(*parts)
     sim.step(args.warmup)
+    # the walk's speed depends on how far the store has drifted from cell
+    # order since the last sort (the store is cell-sorted every sort_every
+    # steps; the seeded load itself is in random order)
+    se = cfg["sort_every"]
+    since_sort = args.warmup % se if args.warmup >= se else None
     n_live = int(sim.diagnostics()["n_particles"])
     acc = torch.zeros(shape, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
@@ -507,6 +520,7 @@ def run_moments(args, ws, rank):
         "data": "synthetic (the benchmark workload after the warm-up steps)",
         "config": {"workload": MOMENTS if not args.particles else f"{MOMENTS} (particles={n_live})",
                    "particles": n_live, "grid": f"{cfg['nr']}x{cfg['nz']}",
+                   "steps_since_sort": since_sort,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": f"inputs larger than L2 (particle store read {n_live * 24 / 1e9:.2f} GB per pass)"},
         "e2e": None if not args.e2e else {
