@@ -442,6 +442,14 @@ int pic_unet_create(int base_channels, int H, int W, int batch, int precision,
 void pic_unet_free(pic_unet* net);
 /* number of FP32 values of the flat parameter vector */
 int64_t pic_unet_param_count(const pic_unet* net);
+/* Which kernels the BF16 3 x 3 convolution GEMMs use: -1 (default) the
+ * tcgen05 tensor-core kernel where its grid fills the GPU (at least two
+ * CTAs of 8 x 16 pixels per SM), else the mma.sync kernel; 0 always
+ * mma.sync; 1 tcgen05 wherever the shape allows (image height and width
+ * multiples of 8 and 16, 32 to 256 output channels).  Results agree to
+ * FP32 summation order.  This library's addition; the paper has no
+ * counterpart.  PIC_EINVAL for another mode. */
+int pic_unet_set_tensor_path(pic_unet* net, int mode);
 /* host flat vector in / out (synchronise); set also clears the Adam
  * moments */
 int pic_unet_set_params(pic_unet* net, const float* params);

@@ -43,7 +43,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link libpic.so if any source or header changed."""
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(INCLUDE, "pic.h"), os.path.join(CSRC, "pic_internal.cuh"),
-               os.path.join(CSRC, "unet_kernels.cuh"), os.path.join(CSRC, "field_common.cuh"),
+               os.path.join(CSRC, "unet_kernels.cuh"), os.path.join(CSRC, "unet_tc.cuh"),
+               os.path.join(CSRC, "field_common.cuh"),
                os.path.join(CSRC, "fluid.cuh")]
     nvcc = _nvcc()
     procs, objs = [], []

@@ -15,10 +15,12 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "pic_internal.cuh"
 #include "unet_kernels.cuh"
+#include "unet_tc.cuh"
 
 namespace pic {
 namespace unet {
@@ -282,6 +284,9 @@ struct pic_unet {
   void *g1b, *g1a, *gc1, *g2b, *g2a, *gc2, *g3b, *g3a, *gc3, *g4b, *g4a, *gp3, *gs3, *ge3a,
       *gp2, *gs2, *ge2a, *gp1, *gs1, *ge1a, *gx0;
   float *y, *gy, *loss;
+  int* dev_err;           // set by a tensor-core GEMM whose bounded wait ran out
+  int tc_mode = -1;       // 3 x 3 GEMMs on tcgen05: -1 where the grid fills the GPU, 0 never,
+                          // 1 wherever the shape allows
   int sms;
 };
 
@@ -351,13 +356,58 @@ int derive_all(pic_unet* n) {
   return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
+// dynamic shared memory of the tensor-core GEMMs (once per process)
+int tc_prepare() {
+  static int rc = -1;
+  if (rc < 0) {
+    auto set = [](auto kern, int bytes) {
+      return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess;
+    };
+    const bool ok = set(k_conv3_tc<32>, TcShape<32>::kSmemBytes) &&
+                    set(k_conv3_tc<64>, TcShape<64>::kSmemBytes) &&
+                    set(k_conv3_tc<128>, TcShape<128>::kSmemBytes) &&
+                    set(k_conv3_tc<256>, TcShape<256>::kSmemBytes);
+    rc = ok ? PIC_OK : PIC_ECUDA;
+  }
+  return rc;
+}
+
+// a tensor-core GEMM's bounded wait that ran out (synchronises)
+int tc_status(pic_unet* n) {
+  int e = 0;
+  if (cudaMemcpyAsync(&e, n->dev_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(n->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  return e ? PIC_ETIMEOUT : PIC_OK;
+}
+
 // out[p, n] (+ epilogue) = GEMM over the taps of `map`; weights `w` with
 // row stride ldw (taps * K, or 4 * K for one sub-grid of a transposed layer)
 void gemm_fwd(pic_unet* n, const void* X, int ldx, int K, const void* w, int ldw, int taps,
               int map, int tap0, Grid3 g, const float* bias, void* Y, int ldy, int N, int epi,
               const void* act, int lda, int mask_from) {
   const long long P = (long long)g.B * g.H * g.W;
-  if (n->prec == 16) {
+  const long long tc_ctas = P / kTcM;
+  if (n->prec == 16 && map == kConv3 && taps == 9 && tap0 == 0 && K % kTcK == 0 &&
+      g.H % kTcTileH == 0 && g.W % kTcTileW == 0 &&
+      (N == 32 || N == 64 || N == 128 || N == 256) && n->tc_mode != 0 &&
+      (n->tc_mode == 1 || tc_ctas >= 2LL * n->sms)) {
+    // tcgen05: one CTA per 8 x 16 pixel block computes every output channel
+    // (grids of fewer than two CTAs per SM stay on the smaller mma.sync tiles)
+    const unsigned grid = (unsigned)tc_ctas;
+    auto run = [&](auto nn) {
+      constexpr int NN = decltype(nn)::value;
+      k_conv3_tc<NN><<<grid, kTcThreads, TcShape<NN>::kSmemBytes, n->stream>>>(
+          (const bf16*)X, ldx, K, (const bf16*)w, ldw, g, bias, (bf16*)Y, ldy, epi,
+          (const bf16*)act, lda, mask_from, n->dev_err);
+    };
+    if (N == 32) run(std::integral_constant<int, 32>());
+    else if (N == 64) run(std::integral_constant<int, 64>());
+    else if (N == 128) run(std::integral_constant<int, 128>());
+    else run(std::integral_constant<int, 256>());
+  } else if (n->prec == 16) {
     const dim3 grid((unsigned)((P + kBM - 1) / kBM), N % 64 == 0 ? N / 64 : N / 32);
     if (N % 64 == 0)
       k_gemm_fwd<64><<<grid, 128, 0, n->stream>>>((const bf16*)X, ldx, K, (const bf16*)w, ldw,
@@ -603,6 +653,7 @@ void unpack_layer(const Layer& l, const std::vector<float>& w, const std::vector
 long long layer_params(const Layer& l) { return (long long)l.cout * l.taps * l.cin + l.cout; }
 
 int copy_out(pic_unet* n, bool grads, float* host) {
+  if (const int st = tc_status(n)) return st;
   std::vector<float> w, b;
   long long o = 0;
   for (Layer& l : n->L) {
@@ -686,12 +737,16 @@ int pic_unet_create(int base_channels, int H, int W, int batch, int precision, v
   n->y = (float*)u_alloc(n, (size_t)P1 * 4);
   n->gy = (float*)u_alloc(n, (size_t)P1 * 4);
   n->loss = (float*)u_alloc(n, 16);
+  n->dev_err = (int*)u_alloc(n, 16);
   for (void* p : {n->x0, n->e1a, n->cat1, n->p1, n->e2a, n->cat2, n->p2, n->e3a, n->cat3, n->p3,
                   n->e4a, n->e4b, n->d3a, n->d3b, n->d2a, n->d2b, n->d1a, n->d1b, n->g1b, n->g1a,
                   n->gc1, n->g2b, n->g2a, n->gc2, n->g3b, n->g3a, n->gc3, n->g4b, n->g4a, n->gp3,
                   n->gs3, n->ge3a, n->gp2, n->gs2, n->ge2a, n->gp1, n->gs1, n->ge1a, n->gx0,
-                  (void*)n->y, (void*)n->gy, (void*)n->loss})
+                  (void*)n->y, (void*)n->gy, (void*)n->loss, (void*)n->dev_err})
     ok = ok && p;
+  if (ok) ok = cudaMemsetAsync(n->dev_err, 0, 16, n->stream) == cudaSuccess;
+  // the tensor-core GEMMs stage four operand tiles in dynamic shared memory
+  if (ok) ok = tc_prepare() == PIC_OK;
   // the concatenation buffers' padded channels must read as zero
   if (ok) {
     ok = cudaMemsetAsync(n->cat1, 0, (size_t)P1 * 2 * C1 * n->es, n->stream) == cudaSuccess &&
@@ -737,6 +792,12 @@ int pic_unet_set_params(pic_unet* n, const float* params) {
   }
   const int rc = derive_all(n);
   return rc ? rc : (cudaStreamSynchronize(n->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA);
+}
+
+int pic_unet_set_tensor_path(pic_unet* n, int mode) {
+  if (!n || mode < -1 || mode > 1) return PIC_EINVAL;
+  n->tc_mode = mode;
+  return PIC_OK;
 }
 
 int pic_unet_get_params(pic_unet* n, float* params) {

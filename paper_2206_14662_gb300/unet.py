@@ -78,6 +78,13 @@ class UNet:
         _check(_sig().pic_unet_set_params(self.h, a.ctypes.data_as(vp)), "pic_unet_set_params")
         self.t = 0
 
+    def set_tensor_path(self, mode: int):
+        """pic_unet_set_tensor_path: -1 automatic, 0 mma.sync only, 1 the
+        tcgen05 kernel wherever the shape allows."""
+        L = lib()
+        L.pic_unet_set_tensor_path.argtypes = [vp, ctypes.c_int]
+        _check(L.pic_unet_set_tensor_path(self.h, int(mode)), "pic_unet_set_tensor_path")
+
     def get_params(self) -> np.ndarray:
         a = np.zeros(self.n_params, dtype=np.float32)
         _check(_sig().pic_unet_get_params(self.h, a.ctypes.data_as(vp)), "pic_unet_get_params")
