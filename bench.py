@@ -565,8 +565,9 @@ def run_unet(args, ws, rank):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     c, H, W, B = 32, 128, 512, 16
+    # 2e4 snapshots: 64 randomised simulations x 313 steps
     cfgs = warmstart.snapshot_configs(64, nr=H, nz=W, n_particles=10_000, seed=1)
-    rho, phi, dphi = warmstart.collect(cfgs, steps=64, warmup=20)
+    rho, phi, dphi = warmstart.collect(cfgs, steps=313, warmup=20)
     sc = warmstart.scales(rho, phi, dphi)
     net = UNet(c, H, W, B, precision=16)
     net.set_params(unet_init_flat(c, seed=3).astype(np.float32))
@@ -613,15 +614,19 @@ def run_unet(args, ws, rank):
     ab = {}
     for n_part in (10_000, 1_000_000):
         cfg = warmstart.snapshot_configs(1, nr=H, nz=W, n_particles=n_part, seed=77)[0]
+        t0 = time.perf_counter()
         prv = warmstart.evaluate(cfg, 50, warmup=20)
+        t1 = time.perf_counter()
         lrn = warmstart.evaluate(cfg, 50, inf, sc, warmup=20)
+        t2 = time.perf_counter()
         ab[f"particles_{n_part}"] = {
             "relres_init_median": {"previous": float(np.median(prv["relres_init"])),
                                    "learned": float(np.median(lrn["relres_init"]))},
             "sweeps_mean": {"previous": float(prv["sweeps"].mean()),
                             "learned": float(lrn["sweeps"].mean())},
             "relres_max": {"previous": float(prv["relres"].max()),
-                           "learned": float(lrn["relres"].max())}}
+                           "learned": float(lrn["relres"].max())},
+            "wall_s_70_steps": {"previous": t1 - t0, "learned": t2 - t1}}
     net.close()
     inf.close()
     peak, src = _peak_bf16()
@@ -636,7 +641,8 @@ def run_unet(args, ws, rank):
                    "flop_per_step": warmstart.train_step_flops(c, H, W, B),
                    "l2": "activations and gradients of a batch exceed L2"},
         "e2e": None, "gpu_launches": None,
-        "roofline": {"bound": "tensor", "kernel": "k_gemm_fwd / k_gemm_wgrad (mma.sync bf16)",
+        "roofline": {"bound": "tensor",
+                     "kernel": "k_conv3_tc (tcgen05) / k_gemm_fwd / k_gemm_wgrad (mma.sync) bf16",
                      "achieved": tflops, "peak": peak, "peak_source": src, "unit": "TFLOP/s",
                      "frac": tflops / peak, "traffic": None},
         "inference_forward_ms": fwd_ms,
@@ -673,14 +679,39 @@ def run_steady(args, ws, rank):
         nus = [sim.diagnostics(sim=k)["nu_max"] for k in range(len(cfgs))]
     for c, nu in zip(cfgs, nus):
         c["source_rate"] = 0.01 * c["n_init"] * nu
+    # the learned form's net: base width 8 (the scan's 64 x 256 grids), trained
+    # on snapshots of the same 64 simulations (100 steps each after 20), not
+    # counted in the time to steady
+    from paper_2206_14662_gb300 import warmstart
+    from paper_2206_14662_gb300.inputs import unet_init_flat
+    from paper_2206_14662_gb300.unet import UNet
+    t0 = time.perf_counter()
+    nr, nz = cfgs[0]["nr"], cfgs[0]["nz"]
+    rho, phi, dphi = warmstart.collect(cfgs, steps=100, warmup=20)
+    sc = warmstart.scales(rho, phi, dphi)
+    trainer = UNet(8, nr, nz, 16, precision=16)
+    trainer.set_params(unet_init_flat(8, seed=5).astype(np.float32))
+    losses, base = warmstart.train(trainer, rho, phi, dphi, sc, epochs=4, lr=1e-3)
+    loss_ratio = float(losses[-64:].mean().item() / base[-64:].mean().item())
+    net = UNet(8, nr, nz, len(cfgs), precision=16)
+    net.set_params(trainer.get_params())
+    trainer.close()
+    del rho, phi, dphi
+    train_s = time.perf_counter() - t0
     res = {}
-    for form in ("batched", "plain"):
-        sec, st, pushed = steady.time_to_steady(cfgs, form, cap_steps=args.steps)
+    for form in ("batched", "learned", "plain"):
+        stats = {}
+        sec, st, pushed = steady.time_to_steady(cfgs, form, cap_steps=args.steps, net=net,
+                                                scales=sc, stats=stats)
         done = [x for x in st if x is not None]
         res[form] = {"seconds": sec, "steady": len(done), "of": len(cfgs),
                      "median_steady_step": float(np.median(done)) if done else None,
                      "particle_steps": int(pushed),
-                     "particle_steps_per_s": pushed / sec}
+                     "particle_steps_per_s": pushed / sec, "field_solve": stats}
+    net.close()
+    res["learned"]["net"] = {"base_channels": 8, "snapshots": 6400, "epochs": 4,
+                             "train_seconds": train_s,
+                             "loss_over_no_change_last64": loss_ratio}
     b, p = res["batched"], res["plain"]
     return {
         "metric": "time to steady state, 64-simulation scan (batched FP32 vs plain FP64)",
@@ -694,6 +725,7 @@ def run_steady(args, ws, rank):
                    "detector": "window means of N, n_max, I_outer; two consecutive windows "
                                "within 2%; window max(2000 steps, 5/nu_max)"},
         "forms": res, "speedup": p["seconds"] / b["seconds"],
+        "speedup_learned": p["seconds"] / res["learned"]["seconds"],
         "note": "simulations not steady by the cap count with the cap",
     }
 

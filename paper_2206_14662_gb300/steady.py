@@ -69,15 +69,24 @@ def _sample(sim, k):
 
 
 def time_to_steady(cfgs: list[dict], form: str, cap_steps: int, samples_per_window: int = 10,
-                   seed: int = 0):
+                   seed: int = 0, net=None, scales=None, stats: dict | None = None):
     """Run `cfgs` in the given form until every simulation is steady or has
     taken cap_steps; returns wall seconds, the per-simulation steady step
-    (None if not reached) and the particle-steps advanced."""
+    (None if not reached) and the particle-steps advanced.  Form "learned"
+    is "batched" with the net (batch = the simulations, H x W = nr x nz)
+    supplying every solve's initial guess (warm_start = 2, `scales` the
+    rho / phi / dphi scales of its training data).  `stats`, if given,
+    receives the median initial relative residual and the mean sweeps of
+    the field solves at the samples."""
     import torch
     from ._capi import Simulation
     S = len(cfgs)
     if form == "batched":
         cf = [dict(c, precision=32, warm_start=1) for c in cfgs]
+    elif form == "learned":
+        if net is None or scales is None:
+            raise ValueError("the learned form needs a net and its scales")
+        cf = [dict(c, precision=32, warm_start=2) for c in cfgs]
     elif form == "plain":
         cf = [dict(c, precision=64, warm_start=0) for c in cfgs]
     else:
@@ -87,10 +96,17 @@ def time_to_steady(cfgs: list[dict], form: str, cap_steps: int, samples_per_wind
     t0 = time.perf_counter()
     steady = [None] * S
     pushed = 0
-    if form == "batched":
+    solve = {"relres_init": [], "sweeps": []}   # the field solves at the samples
+
+    def note(d):
+        solve["relres_init"].append(d["poisson_relres_init"])
+        solve["sweeps"].append(d["poisson_iters"])
+    if form in ("batched", "learned"):
         with Simulation(cf) as sim:
             for k, p in enumerate(parts):
                 sim.load_particles(*p, sim=k)
+            if form == "learned":
+                sim.attach_unet(net, *scales)
             W = [window_steps(c, sim.diagnostics(sim=k)["nu_max"]) for k, c in enumerate(cf)]
             every = max(1, min(W) // samples_per_window)
             det = [SteadyDetector(w) for w in W]
@@ -101,9 +117,12 @@ def time_to_steady(cfgs: list[dict], form: str, cap_steps: int, samples_per_wind
                 for k in range(S):
                     if steady[k] is None:
                         vals, d = _sample(sim, k)
+                        note(d)
                         if det[k].add(step, **vals):
                             steady[k] = det[k].steady_step
             pushed = sum(sim.diagnostics(sim=k)["n_pushed"] for k in range(S))
+            if form == "learned":
+                sim.attach_unet(None, 1.0, 1.0, 1.0)
     else:
         for k in range(S):
             with Simulation(cf[k]) as sim:
@@ -116,9 +135,14 @@ def time_to_steady(cfgs: list[dict], form: str, cap_steps: int, samples_per_wind
                     sim.step(every)
                     step += every
                     vals, d = _sample(sim, 0)
+                    note(d)
                     if det.add(step, **vals):
                         steady[k] = det.steady_step
                         break
                 pushed += sim.diagnostics()["n_pushed"]
     torch.cuda.synchronize()
-    return time.perf_counter() - t0, steady, pushed
+    sec = time.perf_counter() - t0
+    if stats is not None:
+        stats["relres_init_median"] = float(np.median(solve["relres_init"])) if solve["sweeps"] else None
+        stats["sweeps_mean"] = float(np.mean(solve["sweeps"])) if solve["sweeps"] else None
+    return sec, steady, pushed
