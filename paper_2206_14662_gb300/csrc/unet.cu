@@ -364,10 +364,14 @@ int tc_prepare() {
       return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
              cudaSuccess;
     };
-    const bool ok = set(k_conv3_tc<32>, TcShape<32>::kSmemBytes) &&
-                    set(k_conv3_tc<64>, TcShape<64>::kSmemBytes) &&
-                    set(k_conv3_tc<128>, TcShape<128>::kSmemBytes) &&
-                    set(k_conv3_tc<256>, TcShape<256>::kSmemBytes);
+    const bool ok = set(k_conv3_tc<32, 1>, TcShape<32, 1>::kSmemBytes) &&
+                    set(k_conv3_tc<64, 1>, TcShape<64, 1>::kSmemBytes) &&
+                    set(k_conv3_tc<128, 1>, TcShape<128, 1>::kSmemBytes) &&
+                    set(k_conv3_tc<256, 1>, TcShape<256, 1>::kSmemBytes) &&
+                    set(k_conv3_tc<32, 2>, TcShape<32, 2>::kSmemBytes) &&
+                    set(k_conv3_tc<64, 2>, TcShape<64, 2>::kSmemBytes) &&
+                    set(k_conv3_tc<128, 2>, TcShape<128, 2>::kSmemBytes) &&
+                    set(k_conv3_tc<256, 2>, TcShape<256, 2>::kSmemBytes);
     rc = ok ? PIC_OK : PIC_ECUDA;
   }
   return rc;
@@ -399,9 +403,14 @@ void gemm_fwd(pic_unet* n, const void* X, int ldx, int K, const void* w, int ldw
     const unsigned grid = (unsigned)tc_ctas;
     auto run = [&](auto nn) {
       constexpr int NN = decltype(nn)::value;
-      k_conv3_tc<NN><<<grid, kTcThreads, TcShape<NN>::kSmemBytes, n->stream>>>(
-          (const bf16*)X, ldx, K, (const bf16*)w, ldw, g, bias, (bf16*)Y, ldy, epi,
-          (const bf16*)act, lda, mask_from, n->dev_err);
+      if (K == kTcK)
+        k_conv3_tc<NN, 1><<<grid, kTcThreads, TcShape<NN, 1>::kSmemBytes, n->stream>>>(
+            (const bf16*)X, ldx, K, (const bf16*)w, ldw, g, bias, (bf16*)Y, ldy, epi,
+            (const bf16*)act, lda, mask_from, n->dev_err);
+      else
+        k_conv3_tc<NN, 2><<<grid, kTcThreads, TcShape<NN, 2>::kSmemBytes, n->stream>>>(
+            (const bf16*)X, ldx, K, (const bf16*)w, ldw, g, bias, (bf16*)Y, ldy, epi,
+            (const bf16*)act, lda, mask_from, n->dev_err);
     };
     if (N == 32) run(std::integral_constant<int, 32>());
     else if (N == 64) run(std::integral_constant<int, 64>());

@@ -51,17 +51,18 @@ constexpr int kTcTileH = 8, kTcTileW = 16;
 constexpr int kTcHaloRows = (kTcTileH + 2) * kTcTileW;     // 160 staged pixel rows
 constexpr int kTcHaloBytes = kTcHaloRows * kTcK * 2;       // one shifted copy, 10 KB
 constexpr int kTcABytes = 3 * kTcHaloBytes;                 // the three copies, 30 KB
-constexpr int kTcAStages = 2;
 
-template <int N>
+// SA halo stages: 2 when there are several 32-channel chunks to overlap, 1
+// for a single chunk (K = 32), which leaves room for more CTAs per SM
+template <int N, int SA>
 struct TcShape {
   static_assert(N == 32 || N == 64 || N == 128 || N == 256, "tensor-memory columns");
   static constexpr int kBBytes = N * kTcK * 2;   // one tap's weights for one chunk
   static constexpr int kBStages = N <= 64 ? 8 : 4;
   // A ring, B ring, then the barriers (A full/empty, B full/empty, done)
   // and the tensor-memory address
-  static constexpr int kBarOff = kTcAStages * kTcABytes + kBStages * kBBytes;
-  static constexpr int kSmemBytes = kBarOff + 16 * (kTcAStages + kBStages) + 8 + 16;
+  static constexpr int kBarOff = SA * kTcABytes + kBStages * kBBytes;
+  static constexpr int kSmemBytes = kBarOff + 16 * (SA + kBStages) + 8 + 16;
   // instruction descriptor: FP32 accumulator (bits 4-5 = 1), BF16 A and B
   // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 (bits
   // 17-22), M >> 4 (bits 24-28)
@@ -151,13 +152,13 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-template <int N>
+template <int N, int SA>
 __global__ void __launch_bounds__(kTcThreads)
 k_conv3_tc(const bf16* __restrict__ X, int ldx, int K, const bf16* __restrict__ Wk, int ldw,
            Grid3 g, const float* __restrict__ bias, bf16* __restrict__ Y, int ldy, int epi,
            const bf16* __restrict__ act, int lda, int mask_from, int* __restrict__ err) {
-  using Sh = TcShape<N>;
-  constexpr int SA = kTcAStages, SB = Sh::kBStages;
+  using Sh = TcShape<N, SA>;
+  constexpr int SB = Sh::kBStages;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   const uint32_t s0 = smem_u32(tc_smem);
   const uint32_t sB0 = s0 + SA * kTcABytes;
