@@ -223,7 +223,9 @@ int pic_step(pic_handle* h, int64_t nsteps);
 /* Synchronise and fill *out; if density is not NULL, also write the node
  * density (b_i / q) / V_i of the last deposit ((nr + 1) * (nz + 1) FP64,
  * V_i the volume of the hat function).  Currents are averaged since the
- * previous call. */
+ * previous call.  Returns the sticky error; a non-finite velocity among the
+ * live particles, or a non-finite tally (a particle with non-finite values
+ * reached a wall), latches PIC_ENONFINITE. */
 int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density);
 
 /* Synchronise and copy the live particles, sorted by uid, to host FP64

@@ -1063,6 +1063,13 @@ int pic_diagnostics(pic_handle* h, int sim, pic_diag* out, double* density) {
   }
   CK(cudaGetLastError());
   if (s.err && !h->sticky) h->sticky = s.err;
+  if (!h->sticky) {
+    // a non-finite velocity among the live particles, or one that reached a
+    // tally before its particle was removed (an unphysical field, say)
+    bool finite = std::isfinite(ke[0]);
+    for (double v : s.tally) finite = finite && std::isfinite(v);
+    if (!finite) h->sticky = PIC_ENONFINITE;
+  }
   std::memset(out, 0, sizeof(*out));
   out->step = h->step;
   out->t = (double)h->step * c.dt;

@@ -325,6 +325,34 @@ def test_unconverged_field_solve_latches_enoconv():
         assert d["poisson_relres"] > 1e-30
 
 
+def test_non_finite_field_latches_enonfinite():
+    """A field with a NaN node (set from the host) gives the particles of
+    the neighbouring cells non-finite velocities: the next diagnostics
+    latch PIC_ENONFINITE, pic_step keeps returning it, and a reload with a
+    finite field clears it."""
+    from paper_2206_14662_gb300._capi import PIC_ENONFINITE, PicError
+    cfg = _collision_cfg(32, n_init=5000)
+    parts = seed_particles(cfg, n=5000, seed=9)
+    er, ez = random_field_node_arrays(cfg, 1e5, seed=10)
+    bad = er.copy()
+    bad[len(bad) // 2] = np.nan
+    sim = make_gpu(cfg, parts, efield=(bad, ez))
+    try:
+        sim.step(2)
+        with pytest.raises(PicError) as ei:
+            sim.diagnostics()
+        assert ei.value.code == PIC_ENONFINITE
+        with pytest.raises(PicError) as ei:
+            sim.step(1)
+        assert ei.value.code == PIC_ENONFINITE
+        sim.load_particles(*parts)
+        sim.set_efield(er, ez)
+        sim.step(2)
+        assert sim.diagnostics()["n_particles"] > 0
+    finally:
+        sim.close()
+
+
 def test_invalid_inputs_rejected():
     from paper_2206_14662_gb300._capi import PIC_EINVAL, PicError, Simulation
     with pytest.raises(PicError) as ei:
