@@ -80,18 +80,24 @@ __device__ __forceinline__ double node_volume(const ForceParams& F, int i, int j
   return 2.0 * kPi * R * Z;
 }
 
-// Moment pass.  A warp takes chunks of kMomIters x 32 consecutive slots;
-// per 32-slot tile each lane writes its particle's 48 products
-// g_k Lambda_j (moment k, corner j) to a padded shared-memory row, the
-// tile's rows are ordered by cell (a bitonic sort of (cell, lane) across
-// the warp, holes last), then lane l sums columns l and l + 32 down the
-// ordered rows (in the particle's precision), carrying an FP64 running sum
-// while the cell stays the same and adding it, times w / V of the node, to
-// M with one atomic per column when the cell changes: a tile flushes once
-// per distinct cell whatever the order of its slots.
+// Moment pass.  A warp takes chunks of kMomIters x 32 consecutive slots.
+// A 32-slot tile whose slots hold one or two cells (in a cell-sorted store
+// all tiles but those where three cells meet) is added by each lane into 48
+// per-lane registers (its particle's products g_k Lambda_j, moment k,
+// corner j), one cell after the other; a run of additions on one cell,
+// kRegTiles at most, is folded once it ends: the lanes write their
+// registers to a padded shared-memory row each and lane l sums columns l
+// and l + 32 down the rows.  Any other tile writes its particles'
+// products to the rows, the rows are ordered by cell (a bitonic sort of
+// (cell, lane) across the warp, holes last) and lane l sums its columns
+// down the ordered rows.  Both carry an FP64 running sum per column while
+// the cell stays the same and add it, times w / V of the node, to M with
+// one atomic per column when the cell changes: a tile flushes once per
+// distinct cell whatever the order of its slots.
 constexpr int kMomCols = 4 * kMoments;   // column 4 k + j
 constexpr int kMomRow = kMomCols + 1;    // padded: rows start in different banks
 constexpr int kMomIters = 32;
+constexpr int kRegTiles = 8;   // additions summed in registers before a fold
 template <typename Real>
 struct MomShape {
   static constexpr int warps = sizeof(Real) == 4 ? 4 : 2;   // 25 KB of rows per block
@@ -137,22 +143,122 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
   Real(*row)[kMomRow] = rows[wib];
   int* rc = rcell[wib];
   int* rp = rperm[wib];
+  // register runs: FP32 only (48 FP64 registers a lane would halve the
+  // resident warps; FP64 simulations are the small validation cases)
+  constexpr bool kReg = sizeof(Real) == 4;
   for (long long ch = (long long)blockIdx.x * W + wib; ch < nchunks;
        ch += (long long)gridDim.x * W) {
     int run_cell = -1;
     double run0 = 0.0, run1 = 0.0;
+    // adds a tile's column sums of cell cr to the running sums, flushing
+    // them first if the cell changes
+    auto merge = [&](int cr, Real part0, Real part1) {
+      if (cr != run_cell) {
+        if (run_cell >= 0) {
+          moment_flush<Real>(F, ws, run_cell, col0, run0, M, nzp, nnodes);
+          if (has1) moment_flush<Real>(F, ws, run_cell, col1, run1, M, nzp, nnodes);
+        }
+        run_cell = cr;
+        run0 = run1 = 0.0;
+      }
+      run0 += (double)part0;
+      run1 += (double)part1;
+    };
+    Real acc[kMomCols];
+#pragma unroll
+    for (int q = 0; q < kMomCols; ++q) acc[q] = Real(0);
+    int reg_cell = -1, reg_tiles = 0;
+    // folds the register run into the running sums through the rows
+    auto fold = [&]() {
+#pragma unroll
+      for (int q = 0; q < kMomCols; ++q) {
+        row[lane][q] = acc[q];
+        acc[q] = Real(0);
+      }
+      __syncwarp();
+      Real part0 = Real(0), part1 = Real(0);
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) {
+        part0 += row[r][col0];
+        if (has1) part1 += row[r][col1];
+      }
+      __syncwarp();   // the rows are rewritten next
+      merge(reg_cell, part0, part1);
+      reg_tiles = 0;
+    };
+    // the next tile's loads are issued before this tile is processed
+    const long long base = ch * chunk + lane;
+    int ncell = -1;
+    Real nfr = Real(0), nfz = Real(0), nvr = Real(0), nvt = Real(0), nvz = Real(0);
+    if (base < n) {
+      ncell = s.cell[base];
+      nfr = s.offr[base]; nfz = s.offz[base];
+      nvr = s.vr[base]; nvt = s.vt[base]; nvz = s.vz[base];
+    }
     for (int it = 0; it < kMomIters; ++it) {
-      const long long p = ch * chunk + (long long)it * 32 + lane;
-      const int cell = p < n ? s.cell[p] : -1;
+      const int cell = ncell;
+      const Real fr = nfr, fz = nfz, vr = nvr, vt = nvt, vz = nvz;
+      {
+        const long long q = base + (long long)(it + 1) * 32;
+        ncell = -1;
+        if (it + 1 < kMomIters && q < n) {
+          ncell = s.cell[q];
+          nfr = s.offr[q]; nfz = s.offz[q];
+          nvr = s.vr[q]; nvt = s.vt[q]; nvz = s.vz[q];
+        }
+      }
+      Real c[4] = {Real(0), Real(0), Real(0), Real(0)};
+      Real g[kMoments];
+#pragma unroll
+      for (int k = 0; k < kMoments; ++k) g[k] = Real(0);
       if (cell >= 0) {
-        const Real fr = s.offr[p], fz = s.offz[p];
-        const Real c[4] = {(Real(1) - fr) * (Real(1) - fz), fr * (Real(1) - fz),
-                           (Real(1) - fr) * fz, fr * fz};
-        const Real vr = s.vr[p], vt = s.vt[p], vz = s.vz[p];
+        c[0] = (Real(1) - fr) * (Real(1) - fz);
+        c[1] = fr * (Real(1) - fz);
+        c[2] = (Real(1) - fr) * fz;
+        c[3] = fr * fz;
         Real nel, nio;
         nu_parts<Real, Real>(P, vr * vr + vt * vt + vz * vz, nel, nio);
-        const Real g[kMoments] = {Real(1), vr, vt, vz, vr * vr, vr * vt, vr * vz,
-                                  vt * vt, vt * vz, vz * vz, nel + nio, nio};
+        g[0] = Real(1);
+        g[1] = vr;
+        g[2] = vt;
+        g[3] = vz;
+        g[4] = vr * vr;
+        g[5] = vr * vt;
+        g[6] = vr * vz;
+        g[7] = vt * vt;
+        g[8] = vt * vz;
+        g[9] = vz * vz;
+        g[10] = nel + nio;
+        g[11] = nio;
+      }
+      if (kReg) {
+        // a tile of at most two cells (all of a sorted store's but those
+        // where several cells meet) is added to the registers cell by
+        // cell, in ascending order; the warp's reductions are uniform
+        const int cmin = __reduce_min_sync(0xffffffffu, cell >= 0 ? cell : INT_MAX);
+        const int cmax = __reduce_max_sync(0xffffffffu, cell);
+        if (cmin != INT_MAX && __all_sync(0xffffffffu, cell < 0 || cell == cmin || cell == cmax)) {
+#pragma unroll
+          for (int pass = 0; pass < 2; ++pass) {
+            const int cc = pass == 0 ? cmin : cmax;
+            if (pass == 1 && cmax == cmin) break;
+            if (reg_tiles > 0 && (cc != reg_cell || reg_tiles == kRegTiles)) fold();
+            reg_cell = cc;
+            ++reg_tiles;
+            const bool mine = cell == cc;
+            Real cm[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cm[j] = mine ? c[j] : Real(0);
+#pragma unroll
+            for (int k = 0; k < kMoments; ++k)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[4 * k + j] += g[k] * cm[j];
+          }
+          continue;
+        }
+        if (reg_tiles > 0) fold();
+      }
+      if (cell >= 0) {
 #pragma unroll
         for (int k = 0; k < kMoments; ++k)
 #pragma unroll
@@ -178,27 +284,23 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
       rc[lane] = key == INT_MAX ? -1 : key;
       rp[lane] = idx;
       __syncwarp();
+      int walk_cell = -1;
       Real part0 = Real(0), part1 = Real(0);
       for (int r = 0; r < 32; ++r) {
         const int cr = rc[r];   // the same for every lane: uniform branches
         if (cr < 0) break;      // holes are sorted last
-        if (cr != run_cell) {
-          if (run_cell >= 0) {
-            moment_flush<Real>(F, ws, run_cell, col0, run0 + (double)part0, M, nzp, nnodes);
-            if (has1)
-              moment_flush<Real>(F, ws, run_cell, col1, run1 + (double)part1, M, nzp, nnodes);
-          }
-          run_cell = cr;
-          run0 = run1 = 0.0;
+        if (cr != walk_cell) {
+          if (walk_cell >= 0) merge(walk_cell, part0, part1);
+          walk_cell = cr;
           part0 = part1 = Real(0);
         }
         part0 += row[rp[r]][col0];
         if (has1) part1 += row[rp[r]][col1];
       }
-      run0 += (double)part0;
-      run1 += (double)part1;
+      if (walk_cell >= 0) merge(walk_cell, part0, part1);
       __syncwarp();   // the rows are rewritten by the next iteration
     }
+    if (kReg && reg_tiles > 0) fold();
     if (run_cell >= 0) {
       moment_flush<Real>(F, ws, run_cell, col0, run0, M, nzp, nnodes);
       if (has1) moment_flush<Real>(F, ws, run_cell, col1, run1, M, nzp, nnodes);
