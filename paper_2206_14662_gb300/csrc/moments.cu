@@ -80,28 +80,55 @@ __device__ __forceinline__ double node_volume(const ForceParams& F, int i, int j
   return 2.0 * kPi * R * Z;
 }
 
-// Moment pass.  A warp takes chunks of kMomIters x 32 consecutive slots.
-// A 32-slot tile whose slots hold one or two cells (in a cell-sorted store
-// all tiles but those where three cells meet) is added by each lane into 48
-// per-lane registers (its particle's products g_k Lambda_j, moment k,
-// corner j), one cell after the other; a run of additions on one cell,
-// kRegTiles at most, is folded once it ends: the lanes write their
-// registers to a padded shared-memory row each and lane l sums columns l
-// and l + 32 down the rows.  Any other tile writes its particles'
-// products to the rows, the rows are ordered by cell (a bitonic sort of
-// (cell, lane) across the warp, holes last) and lane l sums its columns
-// down the ordered rows.  Both carry an FP64 running sum per column while
-// the cell stays the same and add it, times w / V of the node, to M with
-// one atomic per column when the cell changes: a tile flushes once per
-// distinct cell whatever the order of its slots.
+// Moment pass.  A warp takes chunks of kMomIters x 32 consecutive slots,
+// with the next 32-slot tile's loads issued before the current one is
+// processed.  Each particle contributes the 48 products g_k Lambda_j
+// (moment k, corner j: column 4 k + j).  The cross-lane sums go through a
+// padded shared-memory row per lane: lane l < 24 owns the column pair
+// (2 l, 2 l + 1) and sums it down the rows.
+//  * FP32, a tile of one or two cells (in a cell-sorted store all tiles but
+//    those where three cells meet): each lane adds its products into 48
+//    registers, one cell after the other in ascending order; a run of
+//    additions on one cell, kRegTiles at most, is folded once it ends (the
+//    registers written to the rows and summed down them).
+//  * Otherwise the tile is sorted by cell across the warp (bitonic, on a
+//    32-bit key packing the cell and the lane, holes last), each lane writes
+//    its products to the row of its rank, and the lanes sum their columns
+//    down the runs of equal cells.
+// Both carry an FP64 running sum per column while the cell stays the same
+// and add it, times w / V of the node, to M with one atomic per column
+// when the cell changes: a tile flushes once per distinct cell whatever
+// the order of its slots.
 constexpr int kMomCols = 4 * kMoments;   // column 4 k + j
-constexpr int kMomRow = kMomCols + 1;    // padded: rows start in different banks
+constexpr int kMomPairs = kMomCols / 2;  // lanes owning a column pair
 constexpr int kMomIters = 32;
 constexpr int kRegTiles = 8;   // additions summed in registers before a fold
 template <typename Real>
-struct MomShape {
-  static constexpr int warps = sizeof(Real) == 4 ? 4 : 2;   // 25 KB of rows per block
+struct MomShape;
+template <>
+struct MomShape<float> {
+  static constexpr int warps = 4;
+  static constexpr int row = 52;   // 208 B: 16-byte stores of 8 lanes in distinct banks
+  using Store = float4;            // 4 columns (one moment)
+  using Pair = float2;
 };
+template <>
+struct MomShape<double> {
+  static constexpr int warps = 2;
+  static constexpr int row = 50;   // 400 B
+  using Store = double2;           // 2 columns
+  using Pair = double2;
+};
+
+// 32-bit sort key: ((ir << 12 | iz) << 5 | lane), iz < 4096 and ir < 32768;
+// holes 0xFFFFFFE0 | lane, above every cell's key
+__device__ __forceinline__ unsigned mom_key(int cell, int lane) {
+  if (cell < 0) return 0xFFFFFFE0u | (unsigned)lane;
+  return ((((unsigned)cell >> 16) << 12 | ((unsigned)cell & 0xFFFu)) << 5) | (unsigned)lane;
+}
+__device__ __forceinline__ int key_cell(unsigned key) {
+  return (int)(((key >> 17) << 16) | ((key >> 5) & 0xFFFu));
+}
 
 // w / V of node (i, j) in the particles' precision (an FP64 division costs
 // dozens of FP64 operations; FP32 simulations are held to 1e-5 anyway)
@@ -128,21 +155,21 @@ template <typename Real>
 __global__ void __launch_bounds__(MomShape<Real>::warps * 32)
 k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, double scale,
           double* M) {
-  constexpr int W = MomShape<Real>::warps;
-  __shared__ Real rows[W][32][kMomRow];
-  __shared__ int rcell[W][32];
-  __shared__ int rperm[W][32];
+  using Sh = MomShape<Real>;
+  constexpr int W = Sh::warps, RW = Sh::row;
+  constexpr int kPerStore = (int)(sizeof(typename Sh::Store) / sizeof(Real));
+  __shared__ __align__(16) Real rows[W][32][RW];
+  __shared__ int rrank[W][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long n = st->n_slots;
   const int nzp = F.nz + 1, nnodes = (F.nr + 1) * nzp;
   const double ws = scale * F.weight;
   const long long chunk = 32LL * kMomIters;
   const long long nchunks = (n + chunk - 1) / chunk;
-  const int col0 = lane, col1 = lane + 32;
-  const bool has1 = col1 < kMomCols;
-  Real(*row)[kMomRow] = rows[wib];
-  int* rc = rcell[wib];
-  int* rp = rperm[wib];
+  const bool owner = lane < kMomPairs;   // owns columns 2 lane, 2 lane + 1
+  const int col0 = 2 * lane;
+  Real(*row)[RW] = rows[wib];
+  int* rk = rrank[wib];
   // register runs: FP32 only (48 FP64 registers a lane would halve the
   // resident warps; FP64 simulations are the small validation cases)
   constexpr bool kReg = sizeof(Real) == 4;
@@ -150,19 +177,29 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
        ch += (long long)gridDim.x * W) {
     int run_cell = -1;
     double run0 = 0.0, run1 = 0.0;
-    // adds a tile's column sums of cell cr to the running sums, flushing
+    // adds a column pair's sums over cell cr to the running sums, flushing
     // them first if the cell changes
     auto merge = [&](int cr, Real part0, Real part1) {
       if (cr != run_cell) {
-        if (run_cell >= 0) {
+        if (run_cell >= 0 && owner) {
           moment_flush<Real>(F, ws, run_cell, col0, run0, M, nzp, nnodes);
-          if (has1) moment_flush<Real>(F, ws, run_cell, col1, run1, M, nzp, nnodes);
+          moment_flush<Real>(F, ws, run_cell, col0 + 1, run1, M, nzp, nnodes);
         }
         run_cell = cr;
         run0 = run1 = 0.0;
       }
       run0 += (double)part0;
       run1 += (double)part1;
+    };
+    // sums of the column pair down rows [r0, r1)
+    auto column_sums = [&](int r0, int r1, Real& part0, Real& part1) {
+      part0 = part1 = Real(0);
+      if (owner)
+        for (int r = r0; r < r1; ++r) {
+          const typename Sh::Pair v = *reinterpret_cast<const typename Sh::Pair*>(&row[r][col0]);
+          part0 += v.x;
+          part1 += v.y;
+        }
     };
     Real acc[kMomCols];
 #pragma unroll
@@ -171,29 +208,33 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
     // folds the register run into the running sums through the rows
     auto fold = [&]() {
 #pragma unroll
-      for (int q = 0; q < kMomCols; ++q) {
-        row[lane][q] = acc[q];
-        acc[q] = Real(0);
+      for (int q = 0; q < kMomCols; q += kPerStore) {
+        typename Sh::Store v;
+        Real* e = reinterpret_cast<Real*>(&v);
+#pragma unroll
+        for (int t = 0; t < kPerStore; ++t) {
+          e[t] = acc[q + t];
+          acc[q + t] = Real(0);
+        }
+        *reinterpret_cast<typename Sh::Store*>(&row[lane][q]) = v;
       }
       __syncwarp();
-      Real part0 = Real(0), part1 = Real(0);
-#pragma unroll 8
-      for (int r = 0; r < 32; ++r) {
-        part0 += row[r][col0];
-        if (has1) part1 += row[r][col1];
-      }
+      Real part0, part1;
+      column_sums(0, 32, part0, part1);
       __syncwarp();   // the rows are rewritten next
       merge(reg_cell, part0, part1);
       reg_tiles = 0;
     };
-    // the next tile's loads are issued before this tile is processed
     const long long base = ch * chunk + lane;
     int ncell = -1;
     Real nfr = Real(0), nfz = Real(0), nvr = Real(0), nvt = Real(0), nvz = Real(0);
     if (base < n) {
       ncell = s.cell[base];
-      nfr = s.offr[base]; nfz = s.offz[base];
-      nvr = s.vr[base]; nvt = s.vt[base]; nvz = s.vz[base];
+      nfr = s.offr[base];
+      nfz = s.offz[base];
+      nvr = s.vr[base];
+      nvt = s.vt[base];
+      nvz = s.vz[base];
     }
     for (int it = 0; it < kMomIters; ++it) {
       const int cell = ncell;
@@ -203,8 +244,11 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
         ncell = -1;
         if (it + 1 < kMomIters && q < n) {
           ncell = s.cell[q];
-          nfr = s.offr[q]; nfz = s.offz[q];
-          nvr = s.vr[q]; nvt = s.vt[q]; nvz = s.vz[q];
+          nfr = s.offr[q];
+          nfz = s.offz[q];
+          nvr = s.vr[q];
+          nvt = s.vt[q];
+          nvz = s.vz[q];
         }
       }
       Real c[4] = {Real(0), Real(0), Real(0), Real(0)};
@@ -232,8 +276,7 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
         g[11] = nio;
       }
       if (kReg) {
-        // a tile of at most two cells (all of a sorted store's but those
-        // where several cells meet) is added to the registers cell by
+        // a tile of at most two cells is added to the registers cell by
         // cell, in ascending order; the warp's reductions are uniform
         const int cmin = __reduce_min_sync(0xffffffffu, cell >= 0 ? cell : INT_MAX);
         const int cmax = __reduce_max_sync(0xffffffffu, cell);
@@ -258,52 +301,58 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
         }
         if (reg_tiles > 0) fold();
       }
-      if (cell >= 0) {
-#pragma unroll
-        for (int k = 0; k < kMoments; ++k)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) row[lane][4 * k + j] = g[k] * c[j];
-      }
-      // order the tile's rows by cell (bitonic sort of (cell, lane) across
-      // the warp; holes last) so that equal cells are walked together
-      int key = cell < 0 ? INT_MAX : cell, idx = lane;
+      // rank of each lane's particle in cell order: bitonic sort of the
+      // packed keys across the warp, then the inverse permutation
+      unsigned key = mom_key(cell, lane);
 #pragma unroll
       for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-          const int ok = __shfl_xor_sync(0xffffffffu, key, j);
-          const int oi = __shfl_xor_sync(0xffffffffu, idx, j);
+          const unsigned other = __shfl_xor_sync(0xffffffffu, key, j);
           const bool ascending = (lane & k) == 0, lower = (lane & j) == 0;
-          const bool other_less = ok < key || (ok == key && oi < idx);
-          if (lower == ascending ? other_less : !other_less) {
-            key = ok;
-            idx = oi;
+          key = lower == ascending ? min(key, other) : max(key, other);
+        }
+      }
+      rk[key & 31u] = lane;
+      __syncwarp();
+      const int rank = rk[lane];
+      if (cell >= 0) {
+#pragma unroll
+        for (int k = 0; k < kMoments; ++k) {
+#pragma unroll
+          for (int h = 0; h < 4; h += kPerStore) {
+            typename Sh::Store v;
+            Real* e = reinterpret_cast<Real*>(&v);
+#pragma unroll
+            for (int t = 0; t < kPerStore; ++t) e[t] = g[k] * c[h + t];
+            *reinterpret_cast<typename Sh::Store*>(&row[rank][4 * k + h]) = v;
           }
         }
       }
-      rc[lane] = key == INT_MAX ? -1 : key;
-      rp[lane] = idx;
+      // runs of equal cells among the sorted rows (holes last): lane r
+      // holds the r-th key
+      const unsigned prev = __shfl_up_sync(0xffffffffu, key, 1);
+      const bool valid = key < 0xFFFFFFE0u;
+      const unsigned heads =
+          __ballot_sync(0xffffffffu, valid && (lane == 0 || (prev >> 5) != (key >> 5)));
+      const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
       __syncwarp();
-      int walk_cell = -1;
-      Real part0 = Real(0), part1 = Real(0);
-      for (int r = 0; r < 32; ++r) {
-        const int cr = rc[r];   // the same for every lane: uniform branches
-        if (cr < 0) break;      // holes are sorted last
-        if (cr != walk_cell) {
-          if (walk_cell >= 0) merge(walk_cell, part0, part1);
-          walk_cell = cr;
-          part0 = part1 = Real(0);
-        }
-        part0 += row[rp[r]][col0];
-        if (has1) part1 += row[rp[r]][col1];
+      unsigned rest = heads;
+      while (rest) {
+        const int r0 = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const int r1 = rest ? __ffs(rest) - 1 : nvalid;
+        const int cr = key_cell(__shfl_sync(0xffffffffu, key, r0));
+        Real part0, part1;
+        column_sums(r0, r1, part0, part1);
+        merge(cr, part0, part1);
       }
-      if (walk_cell >= 0) merge(walk_cell, part0, part1);
-      __syncwarp();   // the rows are rewritten by the next iteration
+      __syncwarp();   // the rows and ranks are rewritten by the next tile
     }
     if (kReg && reg_tiles > 0) fold();
-    if (run_cell >= 0) {
+    if (run_cell >= 0 && owner) {
       moment_flush<Real>(F, ws, run_cell, col0, run0, M, nzp, nnodes);
-      if (has1) moment_flush<Real>(F, ws, run_cell, col1, run1, M, nzp, nnodes);
+      moment_flush<Real>(F, ws, run_cell, col0 + 1, run1, M, nzp, nnodes);
     }
   }
 }

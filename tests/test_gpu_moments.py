@@ -62,12 +62,48 @@ def _clustered(cfg, n, seed):
     return r, z, v[0], v[1], v[2], np.arange(n, dtype=np.uint64)
 
 
+def _drifted(cfg, n, seed):
+    """n electrons as a cell-sorted store some steps after its sort: stored
+    in the cell order of their positions, then each moved by up to two
+    cells, so that 32-slot tiles hold a few cells each; a quarter of them
+    in four crowded cells (tiles of one or two cells)."""
+    rng = np.random.default_rng(seed)
+    hr = (cfg["r_out"] - cfg["r_in"]) / cfg["nr"]
+    hz = (cfg["z_max"] - cfg["z_min"]) / cfg["nz"]
+    r = rng.uniform(cfg["r_in"], cfg["r_out"], n)
+    z = rng.uniform(cfg["z_min"], cfg["z_max"], n)
+    crowd = rng.random(n) < 0.25
+    pick = rng.integers(0, 4, n)
+    r[crowd] = cfg["r_in"] + (np.array([1, 2, cfg["nr"] // 2, cfg["nr"] - 1])[pick[crowd]]
+                              + rng.uniform(0, 1, crowd.sum())) * hr
+    z[crowd] = cfg["z_min"] + (np.array([0, 5, cfg["nz"] // 2, cfg["nz"] - 1])[pick[crowd]]
+                               + rng.uniform(0, 1, crowd.sum())) * hz
+    ir = np.minimum(((r - cfg["r_in"]) / hr).astype(np.int64), cfg["nr"] - 1)
+    iz = np.minimum(((z - cfg["z_min"]) / hz).astype(np.int64), cfg["nz"] - 1)
+    order = np.argsort(ir * (cfg["nz"] + 1) + iz, kind="stable")
+    r, z = r[order], z[order]
+    move = ~crowd[order]
+    r[move] = np.clip(r[move] + rng.uniform(-2, 2, move.sum()) * hr, cfg["r_in"] + 1e-3 * hr,
+                      cfg["r_out"] - 1e-3 * hr)
+    z[move] = np.clip(z[move] + rng.uniform(-2, 2, move.sum()) * hz, cfg["z_min"] + 1e-3 * hz,
+                      cfg["z_max"] - 1e-3 * hz)
+    v = rng.normal(0, 3e6, (3, n))
+    return r, z, v[0], v[1], v[2], np.arange(n, dtype=np.uint64)
+
+
+def _layout(cfg, layout, n, seed):
+    if layout == "scattered":
+        return seed_particles(cfg, n=n, seed=seed)
+    return (_clustered if layout == "clustered" else _drifted)(cfg, n, seed + 1)
+
+
 @pytest.mark.parametrize("precision,layout,bkind", [(64, "scattered", 0), (64, "clustered", 1),
-                                                    (32, "scattered", 1), (32, "clustered", 0)])
+                                                    (32, "scattered", 1), (32, "clustered", 0),
+                                                    (64, "drifted", 0), (32, "drifted", 1)])
 def test_loaded_moments_match_oracle(precision, layout, bkind):
     cfg = _cfg(precision, bfield_kind=bkind)
     n = 20_000 + 37
-    parts = seed_particles(cfg, n=n, seed=21) if layout == "scattered" else _clustered(cfg, n, 22)
+    parts = _layout(cfg, layout, n, 21)
     sim = make_gpu(cfg, parts)
     got = sim.moments()
     w = sim.diagnostics()["weight"]
@@ -75,6 +111,19 @@ def test_loaded_moments_match_oracle(precision, layout, bkind):
     w_or = oracle.derived(cfg)["weight"]
     assert w == pytest.approx(w_or, rel=1e-14)
     want = fluid.moments(cfg, *parts[:5], w_or)
+    _compare_moments(got, want, MOM_TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_moments_on_the_widest_grid(precision):
+    """nz = 4096 cells, the library's limit, and 300 radial cells: the walk
+    packs the cell (ir, iz) in 32-bit sort keys."""
+    cfg = _cfg(precision, nr=300, nz=4096)
+    parts = _drifted(cfg, 30_000 + 11, 71)
+    sim = make_gpu(cfg, parts)
+    got = sim.moments()
+    sim.close()
+    want = fluid.moments(cfg, *parts[:5], oracle.derived(cfg)["weight"])
     _compare_moments(got, want, MOM_TOL[precision])
 
 
