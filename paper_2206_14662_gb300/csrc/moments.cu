@@ -95,30 +95,83 @@ __device__ __forceinline__ double node_volume(const ForceParams& F, int i, int j
 //    32-bit key packing the cell and the lane, holes last), each lane writes
 //    its products to the row of its rank, and the lanes sum their columns
 //    down the runs of equal cells.
-// Both carry an FP64 running sum per column while the cell stays the same
-// and add it, times w / V of the node, to M with one atomic per column
-// when the cell changes: a tile flushes once per distinct cell whatever
-// the order of its slots.
+// Both add a column pair's sums to a running sum while the cell stays the
+// same.  When the cell changes the running sum is parked in a per-warp
+// cache of kMomSlots cells in shared memory (added to its cell's entry, or
+// replacing the oldest entry, which is then flushed); the entries left at
+// the end of a chunk are flushed too.  A flush adds the sum, times w / V of
+// the node, to M with one FP64 atomic per column, so a chunk flushes about
+// once per distinct cell whatever the order of its slots.  FP32 running
+// sums are compensated (each addition's rounding error is collected in a
+// second FP32 word, both words flushed), and the FP32 -> FP64 conversion
+// at a flush runs on the integer pipe: no FP64 arithmetic is left in the
+// FP32 pass (on this part FP64 instructions take about 64 times the issue
+// slots of FP32 ones).
 constexpr int kMomCols = 4 * kMoments;   // column 4 k + j
 constexpr int kMomPairs = kMomCols / 2;  // lanes owning a column pair
 constexpr int kMomIters = 32;
 constexpr int kRegTiles = 8;   // additions summed in registers before a fold
+constexpr int kMomSlots = 16;  // cells parked per warp
 template <typename Real>
 struct MomShape;
 template <>
 struct MomShape<float> {
   static constexpr int warps = 4;
   static constexpr int row = 52;   // 208 B: 16-byte stores of 8 lanes in distinct banks
-  using Store = float4;            // 4 columns (one moment)
+  using Store = float4;            // 4 columns (one moment); a cache entry (2 sums + 2 errors)
   using Pair = float2;
 };
 template <>
 struct MomShape<double> {
   static constexpr int warps = 2;
   static constexpr int row = 50;   // 400 B
-  using Store = double2;           // 2 columns
+  using Store = double2;           // 2 columns; a cache entry (2 sums)
   using Pair = double2;
 };
+
+// Running sum of a column: FP32 pairs (s, e) with s the rounded sum and e
+// the accumulated rounding errors of the additions (Knuth's two-sum), so
+// that s + e carries about twice FP32's precision; FP64 plain.
+template <typename Real>
+struct MomSum {
+  Real s, e;
+};
+template <typename Real>
+__device__ __forceinline__ void sum_add(MomSum<Real>& a, Real x) {
+  if (sizeof(Real) == 8) {
+    a.s += x;
+    return;
+  }
+  const Real t = a.s + x;
+  const Real xp = t - a.s;
+  a.e += (a.s - (t - xp)) + (x - xp);
+  a.s = t;
+}
+
+// exact FP32 -> FP64 conversion in integer arithmetic (IEEE 754 binary32
+// to binary64: exponent rebiased by 1023 - 127, fraction widened by 29
+// bits; a subnormal is renormalised, infinities and NaNs keep their class)
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned ex = (u >> 23) & 0xFFu, fr = u & 0x7FFFFFu;
+  unsigned long long bits;
+  if (ex == 0xFFu) {
+    bits = (0x7FFULL << 52) | ((unsigned long long)fr << 29);
+  } else if (ex != 0) {
+    bits = ((unsigned long long)(ex + 896) << 52) | ((unsigned long long)fr << 29);
+  } else if (fr == 0) {
+    bits = 0;
+  } else {
+    // fr 2^-149 with its leading one at bit p: 2^(p - 149) (1 + fraction)
+    const int p = 31 - __clz((int)fr);
+    bits = ((unsigned long long)(p + 874) << 52) |
+           (((unsigned long long)fr << (52 - p)) & 0xFFFFFFFFFFFFFULL);
+  }
+  return __longlong_as_double((long long)(sign | bits));
+}
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
 
 // 32-bit sort key: ((ir << 12 | iz) << 5 | lane), iz < 4096 and ir < 32768;
 // holes 0xFFFFFFE0 | lane, above every cell's key
@@ -133,22 +186,29 @@ __device__ __forceinline__ int key_cell(unsigned key) {
 // w / V of node (i, j) in the particles' precision (an FP64 division costs
 // dozens of FP64 operations; FP32 simulations are held to 1e-5 anyway)
 template <typename Real>
-__device__ __forceinline__ double weight_per_volume(const ForceParams& F, double ws, int i, int j) {
-  if (sizeof(Real) == 8) return ws / node_volume(F, i, j);
+__device__ __forceinline__ Real weight_per_volume(const ForceParams& F, double ws, int i, int j) {
+  if (sizeof(Real) == 8) return (Real)(ws / node_volume(F, i, j));
   const float hr = (float)F.hr, hz = (float)F.hz, r_in = (float)F.r_in;
   const float R = i == 0 ? hr * (0.5f * r_in + hr / 6.0f)
                          : (i == F.nr ? hr * (0.5f * (r_in + F.nr * hr) - hr / 6.0f)
                                       : (r_in + i * hr) * hr);
   const float Z = (j == 0 || j == F.nz) ? 0.5f * hz : hz;
-  return (double)((float)ws / ((float)(2.0 * kPi) * R * Z));
+  return (Real)((float)ws / ((float)(2.0 * kPi) * R * Z));
 }
 
+// adds column col's sum v over cell `cell`, times w / V of its node, to M
 template <typename Real>
 __device__ __forceinline__ void moment_flush(const ForceParams& F, double ws, int cell, int col,
-                                             double v, double* M, int nzp, int nnodes) {
+                                             const MomSum<Real>& v, double* M, int nzp,
+                                             int nnodes) {
   const int k = col >> 2, j = col & 3;
   const int i = (cell >> 16) + (j & 1), jz = (cell & 0xFFFF) + (j >> 1);
-  atomicAdd(M + (size_t)k * nnodes + i * nzp + jz, v * weight_per_volume<Real>(F, ws, i, jz));
+  const Real w = weight_per_volume<Real>(F, ws, i, jz);
+  double* at = M + (size_t)k * nnodes + i * nzp + jz;
+  const Real p = v.s * w;
+  // an FP32 product beyond FP32's range is formed in FP64 instead
+  atomicAdd(at, isfinite(p) || !isfinite(v.s) ? to_f64(p) : to_f64(v.s) * to_f64(w));
+  if (sizeof(Real) == 4 && v.e != Real(0)) atomicAdd(at, to_f64(v.e * w));
 }
 
 template <typename Real>
@@ -160,6 +220,7 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
   constexpr int kPerStore = (int)(sizeof(typename Sh::Store) / sizeof(Real));
   __shared__ __align__(16) Real rows[W][32][RW];
   __shared__ int rrank[W][32];
+  __shared__ typename Sh::Store cache[W][kMomSlots][kMomPairs];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long n = st->n_slots;
   const int nzp = F.nz + 1, nnodes = (F.nr + 1) * nzp;
@@ -170,26 +231,85 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
   const int col0 = 2 * lane;
   Real(*row)[RW] = rows[wib];
   int* rk = rrank[wib];
+  // cache entry of lane l < kMomPairs: its two columns' sums (and, FP32,
+  // their errors); each lane touches only its own entries
+  typename Sh::Store(*slot_data)[kMomPairs] = cache[wib];
   // register runs: FP32 only (48 FP64 registers a lane would halve the
   // resident warps; FP64 simulations are the small validation cases)
   constexpr bool kReg = sizeof(Real) == 4;
   for (long long ch = (long long)blockIdx.x * W + wib; ch < nchunks;
        ch += (long long)gridDim.x * W) {
     int run_cell = -1;
-    double run0 = 0.0, run1 = 0.0;
-    // adds a column pair's sums over cell cr to the running sums, flushing
+    MomSum<Real> run0{Real(0), Real(0)}, run1{Real(0), Real(0)};
+    // lane t < kMomSlots holds the cell of cache slot t (-1: empty); the
+    // slots are replaced oldest first
+    int slot_cell = -1, next_slot = 0;
+    auto entry_load = [&](int t, MomSum<Real>& a, MomSum<Real>& b) {
+      const typename Sh::Store v = slot_data[t][lane];
+      if (sizeof(Real) == 4) {
+        const Real* e = reinterpret_cast<const Real*>(&v);
+        a = {e[0], e[2 % kPerStore]};
+        b = {e[1], e[3 % kPerStore]};
+      } else {
+        const Real* e = reinterpret_cast<const Real*>(&v);
+        a = {e[0], Real(0)};
+        b = {e[1], Real(0)};
+      }
+    };
+    auto entry_store = [&](int t, const MomSum<Real>& a, const MomSum<Real>& b) {
+      typename Sh::Store v;
+      Real* e = reinterpret_cast<Real*>(&v);
+      e[0] = a.s;
+      e[1] = b.s;
+      if (sizeof(Real) == 4) {
+        e[2 % kPerStore] = a.e;
+        e[3 % kPerStore] = b.e;
+      }
+      slot_data[t][lane] = v;
+    };
+    auto flush_pair = [&](int cell, const MomSum<Real>& a, const MomSum<Real>& b) {
+      moment_flush<Real>(F, ws, cell, col0, a, M, nzp, nnodes);
+      moment_flush<Real>(F, ws, cell, col0 + 1, b, M, nzp, nnodes);
+    };
+    // parks the running sums of run_cell in the cache
+    auto park = [&]() {
+      const unsigned hit = __ballot_sync(0xffffffffu, lane < kMomSlots && slot_cell == run_cell);
+      if (hit) {
+        const int t = __ffs(hit) - 1;
+        if (owner) {
+          MomSum<Real> a, b;
+          entry_load(t, a, b);
+          sum_add(a, run0.s);
+          a.e += run0.e;
+          sum_add(b, run1.s);
+          b.e += run1.e;
+          entry_store(t, a, b);
+        }
+        return;
+      }
+      const int t = next_slot;
+      next_slot = next_slot + 1 == kMomSlots ? 0 : next_slot + 1;
+      const int old = __shfl_sync(0xffffffffu, slot_cell, t);
+      if (owner) {
+        if (old >= 0) {
+          MomSum<Real> a, b;
+          entry_load(t, a, b);
+          flush_pair(old, a, b);
+        }
+        entry_store(t, run0, run1);
+      }
+      if (lane == t) slot_cell = run_cell;
+    };
+    // adds a column pair's sums over cell cr to the running sums, parking
     // them first if the cell changes
     auto merge = [&](int cr, Real part0, Real part1) {
       if (cr != run_cell) {
-        if (run_cell >= 0 && owner) {
-          moment_flush<Real>(F, ws, run_cell, col0, run0, M, nzp, nnodes);
-          moment_flush<Real>(F, ws, run_cell, col0 + 1, run1, M, nzp, nnodes);
-        }
+        if (run_cell >= 0) park();
         run_cell = cr;
-        run0 = run1 = 0.0;
+        run0 = run1 = MomSum<Real>{Real(0), Real(0)};
       }
-      run0 += (double)part0;
-      run1 += (double)part1;
+      sum_add(run0, part0);
+      sum_add(run1, part1);
     };
     // sums of the column pair down rows [r0, r1)
     auto column_sums = [&](int r0, int r1, Real& part0, Real& part1) {
@@ -350,9 +470,16 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
       __syncwarp();   // the rows and ranks are rewritten by the next tile
     }
     if (kReg && reg_tiles > 0) fold();
-    if (run_cell >= 0 && owner) {
-      moment_flush<Real>(F, ws, run_cell, col0, run0, M, nzp, nnodes);
-      moment_flush<Real>(F, ws, run_cell, col0 + 1, run1, M, nzp, nnodes);
+    if (run_cell >= 0) park();
+    // flush the chunk's parked cells
+#pragma unroll 1
+    for (int t = 0; t < kMomSlots; ++t) {
+      const int cell = __shfl_sync(0xffffffffu, slot_cell, t);
+      if (cell >= 0 && owner) {
+        MomSum<Real> a, b;
+        entry_load(t, a, b);
+        flush_pair(cell, a, b);
+      }
     }
   }
 }
