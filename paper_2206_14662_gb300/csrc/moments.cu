@@ -53,7 +53,9 @@ namespace pic {
 // elastic and ionisation frequencies at speed^2 v2, in arithmetic type T
 template <typename Real, typename T>
 __device__ __forceinline__ void nu_parts(const PushParams<Real>& P, T v2, T& nu_el, T& nu_io) {
-  const T speed = sqrt(v2);
+  // FP32: speed from the hardware reciprocal square root (the collision
+  // moments are diagnostics held to 1e-5)
+  const T speed = sizeof(T) == 4 ? (v2 > T(0) ? (T)(v2 * rsqrtf((float)v2)) : T(0)) : (T)sqrt((double)v2);
   const T Ek = (T)(0.5 * kMe) * v2;
   if (P.xs_n > 0) {
     const Xs3<Real> x = xs_eval<Real>(P.xs_n, P.xs_E, P.xs_nel, P.xs_nio, P.xs_xi, P.xi, (Real)Ek);
@@ -64,7 +66,8 @@ __device__ __forceinline__ void nu_parts(const PushParams<Real>& P, T v2, T& nu_
   T sio = T(0);
   if (Ek > (T)P.e_th) {
     const T qq = (Ek - (T)P.e_th) * (T)P.e_span_inv;
-    sio = (T)P.sig_pk * T(2) * qq / (T(1) + qq * qq);
+    const T num = (T)P.sig_pk * T(2) * qq, den = T(1) + qq * qq;
+    sio = sizeof(T) == 4 ? (T)__fdividef((float)num, (float)den) : num / den;
   }
   nu_el = (T)P.nsig_el * speed;
   nu_io = (T)P.n_gas * sio * speed;
@@ -110,7 +113,7 @@ __device__ __forceinline__ double node_volume(const ForceParams& F, int i, int j
 constexpr int kMomCols = 4 * kMoments;   // column 4 k + j
 constexpr int kMomPairs = kMomCols / 2;  // lanes owning a column pair
 constexpr int kMomIters = 32;
-constexpr int kRegTiles = 8;   // additions summed in registers before a fold
+constexpr int kRegTiles = 32;  // additions summed in registers before a fold
 constexpr int kMomSlots = 16;  // cells parked per warp
 template <typename Real>
 struct MomShape;
@@ -172,6 +175,19 @@ __device__ __forceinline__ double f32_to_f64(float x) {
 }
 __device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }
 __device__ __forceinline__ double to_f64(double x) { return x; }
+
+// packed pair arithmetic: FP32 pairs in one instruction (Blackwell's
+// paired FP32 pipe), FP64 pairs as two
+__device__ __forceinline__ float2 pair_fma(float a, float2 b, float2 c) {
+  return __ffma2_rn(make_float2(a, a), b, c);
+}
+__device__ __forceinline__ double2 pair_fma(double a, double2 b, double2 c) {
+  return make_double2(fma(a, b.x, c.x), fma(a, b.y, c.y));
+}
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 pair_add(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
 
 // 32-bit sort key: ((ir << 12 | iz) << 5 | lane), iz < 4096 and ir < 32768;
 // holes 0xFFFFFFE0 | lane, above every cell's key
@@ -313,17 +329,23 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
     };
     // sums of the column pair down rows [r0, r1)
     auto column_sums = [&](int r0, int r1, Real& part0, Real& part1) {
-      part0 = part1 = Real(0);
-      if (owner)
-        for (int r = r0; r < r1; ++r) {
-          const typename Sh::Pair v = *reinterpret_cast<const typename Sh::Pair*>(&row[r][col0]);
-          part0 += v.x;
-          part1 += v.y;
+      using Pr = typename Sh::Pair;
+      Pr s0{Real(0), Real(0)}, s1{Real(0), Real(0)};
+      if (owner) {
+        int r = r0;
+        for (; r + 1 < r1; r += 2) {
+          s0 = pair_add(s0, *reinterpret_cast<const Pr*>(&row[r][col0]));
+          s1 = pair_add(s1, *reinterpret_cast<const Pr*>(&row[r + 1][col0]));
         }
+        if (r < r1) s0 = pair_add(s0, *reinterpret_cast<const Pr*>(&row[r][col0]));
+        s0 = pair_add(s0, s1);
+      }
+      part0 = s0.x;
+      part1 = s0.y;
     };
-    Real acc[kMomCols];
+    typename Sh::Pair acc[kMomCols / 2];   // columns (2 q, 2 q + 1)
 #pragma unroll
-    for (int q = 0; q < kMomCols; ++q) acc[q] = Real(0);
+    for (int q = 0; q < kMomCols / 2; ++q) acc[q] = typename Sh::Pair{Real(0), Real(0)};
     int reg_cell = -1, reg_tiles = 0;
     // folds the register run into the running sums through the rows
     auto fold = [&]() {
@@ -333,8 +355,8 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
         Real* e = reinterpret_cast<Real*>(&v);
 #pragma unroll
         for (int t = 0; t < kPerStore; ++t) {
-          e[t] = acc[q + t];
-          acc[q + t] = Real(0);
+          e[t] = reinterpret_cast<const Real*>(acc)[q + t];
+          reinterpret_cast<Real*>(acc)[q + t] = Real(0);
         }
         *reinterpret_cast<typename Sh::Store*>(&row[lane][q]) = v;
       }
@@ -412,10 +434,12 @@ k_moments(Soa<Real> s, const DevState* st, PushParams<Real> P, ForceParams F, do
             Real cm[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) cm[j] = mine ? c[j] : Real(0);
+            const typename Sh::Pair c01{cm[0], cm[1]}, c23{cm[2], cm[3]};
 #pragma unroll
-            for (int k = 0; k < kMoments; ++k)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) acc[4 * k + j] += g[k] * cm[j];
+            for (int k = 0; k < kMoments; ++k) {
+              acc[2 * k] = pair_fma(g[k], c01, acc[2 * k]);
+              acc[2 * k + 1] = pair_fma(g[k], c23, acc[2 * k + 1]);
+            }
           }
           continue;
         }
