@@ -286,11 +286,15 @@ bool eigen(Tables& T) {
   return true;
 }
 
-// band Cholesky factors of lam_k M_z + K_z (bandwidth n), layout [j][d][k]
-// with L_k[j][j - d] at (j (n + 1) + d) mr + k
+// band Cholesky factors L_k of lam_k M_z + K_z (bandwidth n), as the two
+// tables of the device sweeps, each laid out [j][d][k] at (j (n + 1) + d)
+// mr + k: d = 0 holds 1 / L_k[j][j]; d >= 1 holds, in the forward table,
+// L_k[j][j - d] / L_k[j][j] and, in the backward table (after the forward
+// one), L_k[j + d][j] / L_k[j][j] (0 beyond the ends)
 bool band_factors(Tables& T) {
   const int n = T.n, mz = T.mz, mr = T.mr;
-  T.band.assign((size_t)mz * (n + 1) * mr, 0.0);
+  const size_t half = (size_t)mz * (n + 1) * mr;
+  T.band.assign(2 * half, 0.0);
   std::vector<double> L((size_t)mz * (n + 1));
   for (int k = 0; k < mr; ++k) {
     const double lam = T.lam[k];
@@ -307,9 +311,15 @@ bool band_factors(Tables& T) {
         }
       }
     }
-    for (int j = 0; j < mz; ++j)
-      for (int d = 0; d <= n; ++d)
-        T.band[((size_t)j * (n + 1) + d) * mr + k] = L[(size_t)j * (n + 1) + d];
+    for (int j = 0; j < mz; ++j) {
+      const double inv = 1.0 / L[(size_t)j * (n + 1)];
+      for (int d = 0; d <= n; ++d) {
+        const size_t at = ((size_t)j * (n + 1) + d) * mr + k;
+        T.band[at] = d == 0 ? inv : (d <= j ? L[(size_t)j * (n + 1) + d] * inv : 0.0);
+        T.band[half + at] =
+            d == 0 ? inv : (j + d < mz ? L[(size_t)(j + d) * (n + 1) + d] * inv : 0.0);
+      }
+    }
   }
   return true;
 }
@@ -364,25 +374,69 @@ __global__ void k_gemm(int M, int N, int K, const double* __restrict__ A, long l
   if (m < M && n < N) C[m * scm + n * scn] = acc;
 }
 
-// one thread per r-mode k: forward and back substitution with the band
-// factor, in place on x[j mr + k]
-__global__ void k_band_solve(const double* __restrict__ band, int n, int mz, int mr,
-                             double* __restrict__ x) {
+// One thread per r-mode k: forward and back substitution with the band
+// factor's two scaled tables (band_factors): y_j = x_j / L[j][j] -
+// sum_d (L[j][j - d] / L[j][j]) y_{j - d}, then c_j = y_j / L[j][j] -
+// sum_d (L[j + d][j] / L[j][j]) c_{j + d}.  The forward sweep reads x (the
+// modes) and writes y to `tmp`, the backward sweep reads y and writes the
+// solution back to x, so neither sweep stores into the array it loads
+// from: the loads of the next B steps are issued before the current B
+// steps are computed.  The last N values of a sweep stay in registers and
+// a step adds its terms oldest first, so that one FP64 multiply-add a step
+// waits on the previous step.  (Sequential along z, a step that waited for
+// its own loads after the previous store and for an FP64 division took ~1
+// ms a solve.)
+template <int N, int B>
+__global__ void __launch_bounds__(64) k_band_solve(const double* __restrict__ band, int mz, int mr,
+                                                   double* __restrict__ x,
+                                                   double* __restrict__ tmp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= mr) return;
-  const int w = n + 1;
-  for (int j = 0; j < mz; ++j) {
-    double s = x[(size_t)j * mr + k];
-    for (int d = 1; d <= n && d <= j; ++d)
-      s -= band[((size_t)j * w + d) * mr + k] * x[(size_t)(j - d) * mr + k];
-    x[(size_t)j * mr + k] = s / band[((size_t)j * w) * mr + k];
-  }
-  for (int j = mz - 1; j >= 0; --j) {
-    double s = x[(size_t)j * mr + k];
-    for (int d = 1; d <= n && j + d < mz; ++d)
-      s -= band[((size_t)(j + d) * w + d) * mr + k] * x[(size_t)(j + d) * mr + k];
-    x[(size_t)j * mr + k] = s / band[((size_t)j * w) * mr + k];
-  }
+  constexpr int w = N + 1;
+  const double* __restrict__ bf = band;
+  const double* __restrict__ bb = band + (size_t)mz * w * mr;
+  double win[N];   // win[d - 1]: the value d steps back (0 beyond the ends)
+  double xc[B], bc[B][w], xn[B], bn[B][w];
+  // one sweep: rows j0, j0 + step, .. (B of them; outside [0, mz): zeros)
+  auto load = [&](const double* src, const double* tab, bool nc, int j0, int step, double* xs,
+                  double (*bs)[w]) {
+#pragma unroll
+    for (int t = 0; t < B; ++t) {
+      const int j = j0 + t * step;
+      const bool ok = j >= 0 && j < mz;
+      xs[t] = ok ? (nc ? __ldg(src + (size_t)j * mr + k) : src[(size_t)j * mr + k]) : 0.0;
+#pragma unroll
+      for (int d = 0; d <= N; ++d)
+        bs[t][d] = ok ? __ldg(tab + ((size_t)j * w + d) * mr + k) : 0.0;
+    }
+  };
+  auto sweep = [&](const double* src, const double* tab, bool nc, double* dst, int j0, int step) {
+#pragma unroll
+    for (int d = 0; d < N; ++d) win[d] = 0.0;
+    load(src, tab, nc, j0, step, xc, bc);
+    for (int jb = j0; jb >= 0 && jb < mz; jb += B * step) {
+      load(src, tab, nc, jb + B * step, step, xn, bn);
+#pragma unroll
+      for (int t = 0; t < B; ++t) {
+        double s = xc[t] * bc[t][0];
+#pragma unroll
+        for (int d = N; d >= 1; --d) s = fma(-bc[t][d], win[d - 1], s);
+        const int j = jb + t * step;
+        if (j >= 0 && j < mz) dst[(size_t)j * mr + k] = s;
+#pragma unroll
+        for (int d = N - 1; d >= 1; --d) win[d] = win[d - 1];
+        win[0] = s;
+      }
+#pragma unroll
+      for (int t = 0; t < B; ++t) {
+        xc[t] = xn[t];
+#pragma unroll
+        for (int d = 0; d <= N; ++d) bc[t][d] = bn[t][d];
+      }
+    }
+  };
+  sweep(x, bf, true, tmp, 0, 1);
+  sweep(tmp, bb, false, x, mz - 1, -1);
 }
 
 __global__ void k_deposit(Geo G, const double* __restrict__ r, const double* __restrict__ z,
@@ -528,7 +582,18 @@ int pic_spline_solve(pic_spline* s, const double* f, double* c, int dirichlet) {
   // modes[j][k] = sum_i F'[i][j] V[i][k]   (M = mz rows j, N = mr columns k)
   spl::k_gemm<<<dim3((mr + spl::kTile - 1) / spl::kTile, (mz + spl::kTile - 1) / spl::kTile), tb,
                 0, s->stream>>>(mz, mr, mr, s->work, 1, mz, s->V, mr, 1, s->modes, mr, 1);
-  spl::k_band_solve<<<(mr + 127) / 128, 128, 0, s->stream>>>(s->band, G.n, mz, mr, s->modes);
+  // the band sweeps use the lifted right-hand side's buffer (consumed by
+  // the transform above) for their intermediate
+  const int bb = (mr + 63) / 64;
+  switch (G.n) {
+    case 1: spl::k_band_solve<1, 8><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work); break;
+    case 2: spl::k_band_solve<2, 8><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work); break;
+    case 3: spl::k_band_solve<3, 6><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work); break;
+    case 4: spl::k_band_solve<4, 4><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work); break;
+    default:
+      spl::k_band_solve<spl::kMaxDeg, 4><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work);
+      break;
+  }
   // c[i][j] = sum_k V[i][k] modes[j][k]   (M = mr rows i, N = mz columns j)
   spl::k_gemm<<<dim3((mz + spl::kTile - 1) / spl::kTile, (mr + spl::kTile - 1) / spl::kTile), tb,
                 0, s->stream>>>(mr, mz, mr, s->V, mr, 1, s->modes, 1, mr, c, mz, 1);

@@ -3,7 +3,7 @@ finite elements on weighted B-splines of arbitrary degree, with particle shapes
 from the same basis) against oracle.bspline on the same seeded inputs:
 the deposit, the fast-diagonalisation solve against the oracle's sparse
 LU (residual of the assembled system and the field at the particles), and
-phi / E at the particles, degrees 1 to 3, with and without the wall
+phi / E at the particles, degrees 1 to 5, with and without the wall
 potentials, on small grids and on the 128 x 512 benchmark grid."""
 import numpy as np
 import pytest
@@ -31,7 +31,8 @@ def _rel(got, want):
 
 
 @pytest.mark.parametrize("n,nr,nz,npart", [(1, 16, 12, 3000), (2, 16, 12, 3000),
-                                           (3, 20, 33, 5000), (2, 128, 512, 20_000)])
+                                           (3, 20, 33, 5000), (4, 12, 16, 3000),
+                                           (5, 10, 14, 3000), (2, 128, 512, 20_000)])
 def test_spline_field_matches_oracle(n, nr, nz, npart):
     import torch
     from paper_2206_14662_gb300._capi import SplineSolver
@@ -65,7 +66,10 @@ def test_spline_field_matches_oracle(n, nr, nz, npart):
         res = np.linalg.norm(F.A @ cg.ravel() - rhs) / np.linalg.norm(rhs)
         assert res <= 1e-10, res
         assert _rel(F.phi(cg, r, z, lift), F.phi(c_ref, r, z, lift)) <= 1e-11
-        assert _rel(cg, c_ref) <= 1e-7
+        # degrees 4 and 5: cond(A) 3e10 and 6e13 on these grids, so the
+        # coefficients themselves agree only to about cond(A) eps
+        if n <= 3:
+            assert _rel(cg, c_ref) <= 1e-7
     assert _rel(phi.cpu().numpy(), F.phi(c_or, r, z)) <= 1e-12
     er_or, ez_or = F.efield(c_or, r, z)
     scale = max(np.abs(er_or).max(), np.abs(ez_or).max())
