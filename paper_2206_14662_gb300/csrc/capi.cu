@@ -347,6 +347,8 @@ void fill_params(pic_handle* h, int k, PushParams<Real>& P) {
   P.e_idz = (Real)(c.ellipse[3] > 0 ? 1.0 / c.ellipse[3] : 0.0);
   P.e_s = (Real)(0.5 * std::min(c.ellipse[2], c.ellipse[3]));
   P.spl_dv = (Real)(c.v_outer - c.v_inner);
+  P.spl_inv_wmax = (Real)(4.0 / (c.r_out - c.r_in));
+  P.spl_unit = P.qw * (0.25 * (c.r_out - c.r_in)) / kFixUnit;
 }
 
 // spline mode: the solver on the handle's geometry and its grids

@@ -674,6 +674,117 @@ __device__ __forceinline__ void deposit_chunk(const Dep<Real>* dep, typename Til
   }
 }
 
+// FP32 spline-mode deposit of a chunk.  The block's box of the deposit
+// cells, widened by the N further coefficient rows and columns of a
+// particle's support, holds fixed-point counts of w b_k b_l / w_max (each
+// in [0, 1], P.spl_inv_wmax) in kCopies interleaved copies, like the node
+// tile.  A warp whose k-th particles share one cell (most warps of a
+// cell-sorted store) adds their counts with one integer warp reduction per
+// coefficient and one shared atomic; other warps add per lane to the
+// lane's copy.  The flush adds each touched coefficient's count, times
+// P.spl_unit, to the FP64 load grid with one atomic.  A box beyond the
+// tile falls back to the per-particle FP64 atomics.
+template <int N>
+__device__ __forceinline__ void spline_deposit_chunk(const Dep<float>* dep, unsigned* tile,
+                                                     int (*bbox)[4], int buf,
+                                                     const PushParams<float>& P, int tid,
+                                                     int lane) {
+  int lo_r = INT_MAX, hi_r = INT_MIN, lo_z = INT_MAX, hi_z = INT_MIN;
+#pragma unroll
+  for (int k = 0; k < kPPT; ++k) {
+    if (dep[k].ir >= 0) {
+      lo_r = min(lo_r, dep[k].ir); hi_r = max(hi_r, dep[k].ir);
+      lo_z = min(lo_z, dep[k].iz); hi_z = max(hi_z, dep[k].iz);
+    }
+  }
+  lo_r = __reduce_min_sync(0xffffffffu, lo_r);
+  hi_r = __reduce_max_sync(0xffffffffu, hi_r);
+  lo_z = __reduce_min_sync(0xffffffffu, lo_z);
+  hi_z = __reduce_max_sync(0xffffffffu, hi_z);
+  if (lane == 0 && lo_r <= hi_r) {
+    atomicMin(&bbox[buf][0], lo_r); atomicMax(&bbox[buf][1], hi_r);
+    atomicMin(&bbox[buf][2], lo_z); atomicMax(&bbox[buf][3], hi_z);
+  }
+  __syncthreads();
+  const int br0 = bbox[buf][0], br1 = bbox[buf][1];
+  const int bz0 = bbox[buf][2], bz1 = bbox[buf][3];
+  if (tid < 4) bbox[buf ^ 1][tid] = (tid & 1) ? INT_MIN : INT_MAX;
+  const int rows = br1 - br0 + 1 + N, cols = bz1 - bz0 + 1 + N;
+  const bool any = br0 <= br1;
+  const bool use_tile = any && rows * cols <= kCapF;
+  if (use_tile) {
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+      const bool has = dep[k].ir >= 0;
+      const int cell = has ? (dep[k].ir << 16) | dep[k].iz : -1;
+      const int c0 = __shfl_sync(0xffffffffu, cell, 0);
+      const bool uniform = __all_sync(0xffffffffu, cell == c0) && c0 >= 0;
+      unsigned cnt[N + 1][N + 1];
+      int t = 0;
+      if (has) {
+        const int ir = dep[k].ir, iz = dep[k].iz;
+        const float fr = dep[k].fr, fz = dep[k].fz;
+        float Br[N + 1], Bz[N + 1];
+        spl_span<float, N>(fr, Br);
+        spl_span<float, N>(fz, Bz);
+        const float r = mad((float)ir + fr, P.hr, P.r_in);
+        const float z = mad((float)iz + fz, P.hz, P.z_min);
+        float w, wr, wz, pr, pz;
+        spl_wl<float>(P, r, z, w, wr, wz, pr, pz);
+        const float v = fminf(fmaxf(w * P.spl_inv_wmax, 0.f), 1.f) * kFix;
+#pragma unroll
+        for (int a = 0; a <= N; ++a) {
+          const float va = v * Br[a];
+#pragma unroll
+          for (int b = 0; b <= N; ++b) cnt[a][b] = __float2uint_rn(va * Bz[b]);
+        }
+        t = (ir - br0) * cols + (iz - bz0);
+      } else {
+#pragma unroll
+        for (int a = 0; a <= N; ++a)
+#pragma unroll
+          for (int b = 0; b <= N; ++b) cnt[a][b] = 0u;
+      }
+      if (uniform) {
+#pragma unroll
+        for (int a = 0; a <= N; ++a)
+#pragma unroll
+          for (int b = 0; b <= N; ++b) {
+            const unsigned sum = __reduce_add_sync(0xffffffffu, cnt[a][b]);
+            if (lane == 0 && sum) atomicAdd(tile + kCopies * (t + a * cols + b), sum);
+          }
+      } else if (has) {
+        unsigned* tc = tile + kCopies * t + (lane & 3);
+#pragma unroll
+        for (int a = 0; a <= N; ++a)
+#pragma unroll
+          for (int b = 0; b <= N; ++b)
+            if (cnt[a][b]) atomicAdd(tc + kCopies * (a * cols + b), cnt[a][b]);
+      }
+    }
+  } else if (any) {
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k)
+      if (dep[k].ir >= 0) spline_deposit<float, N>(P, dep[k].ir, dep[k].iz, dep[k].fr, dep[k].fz);
+  }
+  __syncthreads();
+  if (use_tile) {
+    // one warp per tile row, lanes along z
+    const int warp = tid >> 5;
+    for (int rr = warp; rr < rows; rr += kThreads / 32) {
+      for (int cc = lane; cc < cols; cc += 32) {
+        const int t = rr * cols + cc;
+        const uint4 q = reinterpret_cast<const uint4*>(tile)[t];
+        const unsigned v = q.x + q.y + q.z + q.w;
+        if (v) {
+          atomicAdd(P.spl_f + (size_t)(br0 + rr) * P.spl_mz + (bz0 + cc), (double)v * P.spl_unit);
+          reinterpret_cast<uint4*>(tile)[t] = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+    }
+  }
+}
+
 // block tallies: the work sum and particle count, then one global atomic
 // per non-zero slot (weights and energies scaled by the macro weight)
 template <typename Real>
@@ -711,10 +822,10 @@ __device__ __forceinline__ void flush_tallies(BlockTally& bt, Real work, int pus
 // loads with streaming hints in the FP32 path), advances them, stores them
 // back and joins the block's tile deposit.  TAB: some simulation has
 // tabulated cross sections.  SPL > 0: the weighted B-spline field of that
-// degree (gather from its coefficients, deposit into its load grid with
-// FP64 atomics; the tile is not used).
+// degree (gather from its coefficients; deposit into its load grid through
+// the fixed-point tile in FP32, with FP64 atomics per particle in FP64).
 template <typename Real, bool TAB, int SPL>
-__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value ? PIC_MIN_BLOCKS : 4)
+__global__ void __launch_bounds__(kThreads, std::is_same<Real, float>::value && SPL == 0 ? PIC_MIN_BLOCKS : 4)
 k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, DepGrid g,
                 DevState* st, unsigned* __restrict__ spawn_parent, PushParams<Real> P) {
   using TT = typename TileT<Real>::type;
@@ -750,7 +861,7 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, De
         ++pushed;
         dep[k] = advance<Real, TAB, SPL>(q[k], uid[k], 0u, E, s, g, st, spawn_parent, n_slots, step,
                                          P, bt, work);
-        if constexpr (SPL > 0) {
+        if constexpr (SPL > 0 && !std::is_same<Real, float>::value) {
           if (dep[k].ir >= 0) spline_deposit<Real, SPL>(P, dep[k].ir, dep[k].iz, dep[k].fr, dep[k].fz);
         }
       }
@@ -758,6 +869,9 @@ k_particle_step(Soa<Real> s, const typename Vec2<Real>::type* __restrict__ E, De
     store_group<Real>(s, p0, n_slots, q, live, vec);
     if constexpr (SPL == 0) {
       deposit_chunk<Real, kCap>(dep, tile, bbox, buf, g, tid, lane);
+      buf ^= 1;
+    } else if constexpr (std::is_same<Real, float>::value) {
+      spline_deposit_chunk<SPL>(dep, tile, bbox, buf, P, tid, lane);
       buf ^= 1;
     }
   }

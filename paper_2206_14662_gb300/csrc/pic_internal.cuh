@@ -146,6 +146,12 @@ struct PushParams {
   // the ellipse are absorbed
   int spl_ell;
   Real e_r0, e_z0, e_idr, e_idz, e_s, spl_dv;
+  // FP32 tile deposit of the spline load: w b_k b_l / w_max (in [0, 1]:
+  // w <= w_max = (r_out - r_in) / 4, the B-splines a partition of unity)
+  // as fixed-point counts (kFixUnit a unit), each count spl_unit = q weight
+  // w_max / kFixUnit of load
+  Real spl_inv_wmax;
+  double spl_unit;
 };
 
 // ------------------------------------------------------------- batches

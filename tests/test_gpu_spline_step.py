@@ -69,6 +69,36 @@ def test_spline_step_fp32_one_step():
     assert amb <= 5
 
 
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_spline_fp32_load_and_potential(n):
+    """FP32 steps deposit through the block's fixed-point tile (integer warp
+    sums and shared atomics, one FP64 atomic per coefficient and chunk):
+    the potential at the nodes after the steps against the oracle's, to
+    the FP32 positions' and the fixed-point unit's rounding.  The first
+    load (at particle load) is the per-particle path, so the comparison
+    after two steps covers the tile."""
+    from paper_2206_14662_gb300._capi import PIC_GRID_PHI, Simulation
+    cfg = _cfg(32, n, p_mbar=0.0)
+    parts = seed_particles(cfg, n=20_000, seed=40 + n)
+    o = oracle.OracleSim(cfg, *parts)
+    with Simulation(cfg) as sim:
+        sim.load_particles(*parts)
+        for _ in range(2):
+            o.step()
+        sim.step(2)
+        phi = sim.get_grid(PIC_GRID_PHI)
+        d = sim.diagnostics()
+    assert d["error"] == 0
+    r, z = oracle.grid(cfg)
+    R, Z = np.meshgrid(r, z, indexing="ij")
+    want = o.spline.phi(o.coef, R.ravel(), Z.ravel())
+    # the space-charge part of the potential: the difference to the
+    # vacuum potential of the same walls
+    vac = o.spline.phi(np.zeros_like(o.coef), R.ravel(), Z.ravel())
+    err = np.abs(phi.ravel() - want).max()
+    assert err <= 2e-5 * np.abs(want - vac).max(), err / np.abs(want - vac).max()
+
+
 def test_spline_graph_replay_equals_direct():
     from paper_2206_14662_gb300._capi import Simulation
     cfg = _cfg(64, 2, n_init=30_000)

@@ -62,3 +62,28 @@ def test_trap_steps_match_oracle():
     ins = o.spline.geo.inside(R.ravel(), Z.ravel())
     want = o.spline.phi(o.coef, R.ravel(), Z.ravel())
     assert np.abs(phi[ins] - want[ins]).max() <= 1e-9 * np.abs(want[ins]).max()
+
+
+def test_trap_fp32_load_and_potential():
+    """FP32 steps in the trap deposit through the block's fixed-point tile:
+    the potential inside the domain after two steps against the oracle's
+    (no collisions, so both step the same particles)."""
+    from paper_2206_14662_gb300._capi import PIC_GRID_PHI, Simulation
+    cfg = _trap(32, p_mbar=0.0, n_init=20_000)
+    parts = _outside(seed_particles(cfg, n=20_000, seed=33))
+    o = oracle.OracleSim(cfg, *parts)
+    with Simulation(cfg) as sim:
+        sim.load_particles(*parts)
+        for _ in range(2):
+            o.step()
+        sim.step(2)
+        phi = sim.get_grid(PIC_GRID_PHI)
+        d = sim.diagnostics()
+    assert d["error"] == 0
+    r, z = oracle.grid(cfg)
+    R, Z = np.meshgrid(r, z, indexing="ij")
+    ins = o.spline.geo.inside(R.ravel(), Z.ravel())
+    want = o.spline.phi(o.coef, R.ravel(), Z.ravel())
+    vac = o.spline.phi(np.zeros_like(o.coef), R.ravel(), Z.ravel())
+    err = np.abs(phi.ravel()[ins] - want[ins]).max()
+    assert err <= 2e-5 * np.abs(want[ins] - vac[ins]).max(), err
