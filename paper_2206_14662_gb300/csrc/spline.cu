@@ -103,8 +103,14 @@ struct Tables {
   double a, b, z0, hr, hz, v_in, v_out, dphiD;
   std::vector<double> K_r, M_r, g_r, K_z, M_z, m_z;   // dense, row-major
   std::vector<double> V, lam;                          // mr x mr, mr
-  std::vector<double> band;                            // [j][d][k]: L_k[j][j - d]
+  std::vector<double> band;                            // the sweeps' scaled tables
+  std::vector<double> gt;                              // segment responses (band_factors)
 };
+
+// The z sweeps run in kSpikeSeg segments of rows per mode (k_band_spike),
+// kSpikeModes modes a block.
+constexpr int kSpikeSeg = 32;
+constexpr int kSpikeModes = 4;
 
 int check(const pic_config* c, int n) {
   if (!c || n < 1 || n > kMaxDeg) return PIC_EINVAL;
@@ -321,6 +327,34 @@ bool band_factors(Tables& T) {
       }
     }
   }
+  // per sweep, mode and segment: the segment's exit window (its last n
+  // values in the sweep's order) for each unit entry window, the same
+  // recurrence as the device's without the right-hand side
+  const int S = (mz + kSpikeSeg - 1) / kSpikeSeg;
+  T.gt.assign((size_t)2 * mr * kSpikeSeg * n * n, 0.0);
+  std::vector<double> gw((size_t)n * n);
+  for (int sw = 0; sw < 2; ++sw) {
+    const double* tab = T.band.data() + sw * half;
+    for (int k = 0; k < mr; ++k)
+      for (int p = 0; p < kSpikeSeg; ++p) {
+        const int lo = std::min(p * S, mz), hi = std::min(lo + S, mz);
+        for (int m = 0; m < n; ++m)
+          for (int i = 0; i < n; ++i) gw[(size_t)m * n + i] = i == m ? 1.0 : 0.0;
+        for (int q = 0; q < hi - lo; ++q) {
+          const int j = sw == 0 ? lo + q : hi - 1 - q;
+          for (int m = 0; m < n; ++m) {
+            double* w = gw.data() + (size_t)m * n;
+            double v = 0.0;
+            for (int d = n; d >= 1; --d) v = std::fma(-tab[((size_t)j * (n + 1) + d) * mr + k], w[d - 1], v);
+            for (int d = n - 1; d >= 1; --d) w[d] = w[d - 1];
+            w[0] = v;
+          }
+        }
+        double* out = T.gt.data() + (((size_t)sw * mr + k) * kSpikeSeg + p) * n * n;
+        for (int i = 0; i < n; ++i)
+          for (int m = 0; m < n; ++m) out[(size_t)i * n + m] = gw[(size_t)m * n + i];
+      }
+  }
   return true;
 }
 
@@ -374,69 +408,131 @@ __global__ void k_gemm(int M, int N, int K, const double* __restrict__ A, long l
   if (m < M && n < N) C[m * scm + n * scn] = acc;
 }
 
-// One thread per r-mode k: forward and back substitution with the band
-// factor's two scaled tables (band_factors): y_j = x_j / L[j][j] -
-// sum_d (L[j][j - d] / L[j][j]) y_{j - d}, then c_j = y_j / L[j][j] -
-// sum_d (L[j + d][j] / L[j][j]) c_{j + d}.  The forward sweep reads x (the
-// modes) and writes y to `tmp`, the backward sweep reads y and writes the
-// solution back to x, so neither sweep stores into the array it loads
-// from: the loads of the next B steps are issued before the current B
-// steps are computed.  The last N values of a sweep stay in registers and
-// a step adds its terms oldest first, so that one FP64 multiply-add a step
-// waits on the previous step.  (Sequential along z, a step that waited for
-// its own loads after the previous store and for an FP64 division took ~1
-// ms a solve.)
-template <int N, int B>
-__global__ void __launch_bounds__(64) k_band_solve(const double* __restrict__ band, int mz, int mr,
-                                                   double* __restrict__ x,
-                                                   double* __restrict__ tmp) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= mr) return;
+// Per r-mode k, forward and back substitution with the band factor's two
+// scaled tables (band_factors): y_j = x_j / L[j][j] - sum_d (L[j][j - d] /
+// L[j][j]) y_{j - d}, then c_j = y_j / L[j][j] - sum_d (L[j + d][j] /
+// L[j][j]) c_{j + d}; the forward sweep reads x (the modes) and writes y to
+// `tmp`, the backward sweep reads y and writes the solution back to x.
+// Each sweep is split into P segments of rows per mode (the "SPIKE"
+// partition of a banded triangular solve); a block holds MG modes x P
+// segments, thread t mode t % MG and segment t / MG.  Phase 1: each
+// (segment, mode) runs its rows from a zero entry window, keeping its last
+// N values.  Phase 2: one thread per mode chains the segments in the
+// sweep's order: the entry window of the next segment is that exit window
+// plus the segment's responses to unit entry windows (gt, precomputed on
+// the host from the same tables) applied to its own entry window.  Phase
+// 3: each segment reruns its rows from its true entry window and stores
+// them.  The dependency chain is 2 S + P steps instead of mz (S = mz / P
+// rows a segment), and the work spreads over mr / MG blocks: on this part
+// FP64 instructions take ~16 SM cycles a warp, so the number of SMs doing
+// FP64, not latency alone, sets the time.  Segments hold the same rows in
+// both sweeps, so the backward sweep reads the rows its own thread stored.
+template <int N, int B, class F>
+__device__ __forceinline__ void band_rows(const double* __restrict__ src,
+                                          const double* __restrict__ tab, bool nc, int j0,
+                                          int count, int step, int k, int mr, bool valid, F&& f) {
   constexpr int w = N + 1;
-  const double* __restrict__ bf = band;
-  const double* __restrict__ bb = band + (size_t)mz * w * mr;
-  double win[N];   // win[d - 1]: the value d steps back (0 beyond the ends)
   double xc[B], bc[B][w], xn[B], bn[B][w];
-  // one sweep: rows j0, j0 + step, .. (B of them; outside [0, mz): zeros)
-  auto load = [&](const double* src, const double* tab, bool nc, int j0, int step, double* xs,
-                  double (*bs)[w]) {
+  auto load = [&](int i0, double* xs, double (*bs)[w]) {
 #pragma unroll
     for (int t = 0; t < B; ++t) {
-      const int j = j0 + t * step;
-      const bool ok = j >= 0 && j < mz;
+      const int i = i0 + t;
+      const bool ok = valid && i < count;
+      const int j = j0 + i * step;
       xs[t] = ok ? (nc ? __ldg(src + (size_t)j * mr + k) : src[(size_t)j * mr + k]) : 0.0;
 #pragma unroll
-      for (int d = 0; d <= N; ++d)
-        bs[t][d] = ok ? __ldg(tab + ((size_t)j * w + d) * mr + k) : 0.0;
+      for (int d = 0; d <= N; ++d) bs[t][d] = ok ? __ldg(tab + ((size_t)j * w + d) * mr + k) : 0.0;
     }
   };
-  auto sweep = [&](const double* src, const double* tab, bool nc, double* dst, int j0, int step) {
+  load(0, xc, bc);
+  for (int i0 = 0; i0 < count; i0 += B) {
+    load(i0 + B, xn, bn);
 #pragma unroll
-    for (int d = 0; d < N; ++d) win[d] = 0.0;
-    load(src, tab, nc, j0, step, xc, bc);
-    for (int jb = j0; jb >= 0 && jb < mz; jb += B * step) {
-      load(src, tab, nc, jb + B * step, step, xn, bn);
+    for (int t = 0; t < B; ++t)
+      if (i0 + t < count) f(j0 + (i0 + t) * step, xc[t], bc[t]);
 #pragma unroll
-      for (int t = 0; t < B; ++t) {
-        double s = xc[t] * bc[t][0];
+    for (int t = 0; t < B; ++t) {
+      xc[t] = xn[t];
 #pragma unroll
-        for (int d = N; d >= 1; --d) s = fma(-bc[t][d], win[d - 1], s);
-        const int j = jb + t * step;
-        if (j >= 0 && j < mz) dst[(size_t)j * mr + k] = s;
+      for (int d = 0; d <= N; ++d) bc[t][d] = bn[t][d];
+    }
+  }
+}
+
+// one row of a sweep on window win (win[d - 1] the value d rows back in
+// the sweep's order): x / L[j][j] - sum_d t_d win[d - 1], oldest term first
+template <int N>
+__device__ __forceinline__ double band_step(double xs, const double* t, double* win) {
+  double v = xs * t[0];
 #pragma unroll
-        for (int d = N - 1; d >= 1; --d) win[d] = win[d - 1];
-        win[0] = s;
-      }
+  for (int d = N; d >= 1; --d) v = fma(-t[d], win[d - 1], v);
 #pragma unroll
-      for (int t = 0; t < B; ++t) {
-        xc[t] = xn[t];
+  for (int d = N - 1; d >= 1; --d) win[d] = win[d - 1];
+  win[0] = v;
+  return v;
+}
+
+template <int N, int MG, int P, int B>
+__global__ void __launch_bounds__(MG * P) k_band_spike(const double* __restrict__ band,
+                                                      const double* __restrict__ gt, int mz,
+                                                      int mr, double* __restrict__ x,
+                                                      double* __restrict__ tmp) {
+  __shared__ double ztail[P][MG][N], tin[P][MG][N];
+  const int mi = threadIdx.x % MG, p = threadIdx.x / MG;
+  const int k = blockIdx.x * MG + mi;
+  const bool valid = k < mr;
+  const int S = (mz + P - 1) / P;
+  const int lo = min(p * S, mz), hi = min(lo + S, mz), count = hi - lo;
+#pragma unroll 1
+  for (int sw = 0; sw < 2; ++sw) {
+    const bool fwd = sw == 0;
+    const double* src = fwd ? x : tmp;
+    const double* tab = band + (size_t)sw * mz * (N + 1) * mr;
+    double* dst = fwd ? tmp : x;
+    const int j0 = fwd ? lo : hi - 1, step = fwd ? 1 : -1;
+    // phase 1
+    double zw[N];
 #pragma unroll
-        for (int d = 0; d <= N; ++d) bc[t][d] = bn[t][d];
+    for (int i = 0; i < N; ++i) zw[i] = 0.0;
+    band_rows<N, B>(src, tab, fwd, j0, count, step, k, mr, valid,
+                    [&](int, double xs, const double* t) { band_step<N>(xs, t, zw); });
+#pragma unroll
+    for (int i = 0; i < N; ++i) ztail[p][mi][i] = zw[i];
+    __syncthreads();
+    // phase 2
+    if (p == 0 && valid) {
+      double T[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) T[i] = 0.0;
+      const double* g = gt + ((size_t)sw * mr + k) * P * N * N;
+      for (int q = 0; q < P; ++q) {
+        const int seg = fwd ? q : P - 1 - q;
+        const double* gs = g + (size_t)seg * N * N;
+        double Tn[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          tin[seg][mi][i] = T[i];
+          double v = ztail[seg][mi][i];
+#pragma unroll
+          for (int m = 0; m < N; ++m) v = fma(__ldg(gs + i * N + m), T[m], v);
+          Tn[i] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) T[i] = Tn[i];
       }
     }
-  };
-  sweep(x, bf, true, tmp, 0, 1);
-  sweep(tmp, bb, false, x, mz - 1, -1);
+    __syncthreads();
+    // phase 3
+    double win[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) win[i] = tin[p][mi][i];
+    band_rows<N, B>(src, tab, fwd, j0, count, step, k, mr, valid,
+                    [&](int j, double xs, const double* t) {
+                      const double v = band_step<N>(xs, t, win);
+                      if (valid) dst[(size_t)j * mr + k] = v;
+                    });
+    __syncthreads();   // the shared windows are rewritten by the next sweep
+  }
 }
 
 __global__ void k_deposit(Geo G, const double* __restrict__ r, const double* __restrict__ z,
@@ -497,10 +593,26 @@ __global__ void k_eval(Geo G, const double* __restrict__ c, const double* __rest
 
 using namespace pic;
 
+// the band solve of the modes x (mr x mz, row j at j mr) in place, tmp
+// its intermediate
+static int band_solve(int n, const double* band, const double* gt, int mz, int mr, double* x,
+                      double* tmp, cudaStream_t st) {
+  using namespace pic::spl;
+  const int blocks = (mr + kSpikeModes - 1) / kSpikeModes, threads = kSpikeModes * kSpikeSeg;
+  switch (n) {
+    case 1: k_band_spike<1, kSpikeModes, kSpikeSeg, 4><<<blocks, threads, 0, st>>>(band, gt, mz, mr, x, tmp); break;
+    case 2: k_band_spike<2, kSpikeModes, kSpikeSeg, 4><<<blocks, threads, 0, st>>>(band, gt, mz, mr, x, tmp); break;
+    case 3: k_band_spike<3, kSpikeModes, kSpikeSeg, 4><<<blocks, threads, 0, st>>>(band, gt, mz, mr, x, tmp); break;
+    case 4: k_band_spike<4, kSpikeModes, kSpikeSeg, 4><<<blocks, threads, 0, st>>>(band, gt, mz, mr, x, tmp); break;
+    default: k_band_spike<kMaxDeg, kSpikeModes, kSpikeSeg, 4><<<blocks, threads, 0, st>>>(band, gt, mz, mr, x, tmp); break;
+  }
+  return PIC_OK;
+}
+
 struct pic_spline {
   spl::Geo G;
   cudaStream_t stream;
-  double *V, *g_r, *m_z, *band, *work, *modes;
+  double *V, *g_r, *m_z, *band, *gt, *work, *modes;
 };
 
 extern "C" {
@@ -534,7 +646,7 @@ int pic_spline_eigen(const pic_config* cfg, int degree, double* V, double* lambd
 
 void pic_spline_free(pic_spline* s) {
   if (!s) return;
-  for (double* p : {s->V, s->g_r, s->m_z, s->band, s->work, s->modes})
+  for (double* p : {s->V, s->g_r, s->m_z, s->band, s->gt, s->work, s->modes})
     if (p) cudaFree(p);
   delete s;
 }
@@ -554,13 +666,15 @@ int pic_spline_create(const pic_config* cfg, int degree, void* cuda_stream, pic_
             cudaMalloc(&s->g_r, T.g_r.size() * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->m_z, T.m_z.size() * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->band, T.band.size() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&s->gt, T.gt.size() * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->work, cells * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->modes, cells * sizeof(double)) == cudaSuccess;
   ok = ok &&
        cudaMemcpy(s->V, T.V.data(), T.V.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(s->g_r, T.g_r.data(), T.g_r.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(s->m_z, T.m_z.data(), T.m_z.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemcpy(s->band, T.band.data(), T.band.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+       cudaMemcpy(s->band, T.band.data(), T.band.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(s->gt, T.gt.data(), T.gt.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) {
     pic_spline_free(s);
     cudaGetLastError();
@@ -584,16 +698,7 @@ int pic_spline_solve(pic_spline* s, const double* f, double* c, int dirichlet) {
                 0, s->stream>>>(mz, mr, mr, s->work, 1, mz, s->V, mr, 1, s->modes, mr, 1);
   // the band sweeps use the lifted right-hand side's buffer (consumed by
   // the transform above) for their intermediate
-  const int bb = (mr + 63) / 64;
-  switch (G.n) {
-    case 1: spl::k_band_solve<1, 8><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work); break;
-    case 2: spl::k_band_solve<2, 8><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work); break;
-    case 3: spl::k_band_solve<3, 6><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work); break;
-    case 4: spl::k_band_solve<4, 4><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work); break;
-    default:
-      spl::k_band_solve<spl::kMaxDeg, 4><<<bb, 64, 0, s->stream>>>(s->band, mz, mr, s->modes, s->work);
-      break;
-  }
+  if (int rc = band_solve(G.n, s->band, s->gt, mz, mr, s->modes, s->work, s->stream)) return rc;
   // c[i][j] = sum_k V[i][k] modes[j][k]   (M = mr rows i, N = mz columns j)
   spl::k_gemm<<<dim3((mz + spl::kTile - 1) / spl::kTile, (mr + spl::kTile - 1) / spl::kTile), tb,
                 0, s->stream>>>(mr, mz, mr, s->V, mr, 1, s->modes, 1, mr, c, mz, 1);
