@@ -60,7 +60,8 @@ struct DevState {
   unsigned solve_blocks_done; // last-block counter of the residual kernel
   int poisson_iters;          // sweeps of the last solve
   int solve_done;             // set when the solve has converged
-  int pad1;
+  int chunk_next;             // the particle kernel's next chunk (handed out
+                              // by atomics; reset by the spawn finalisation)
   long long n_live;           // live count after the last sort / load
   double relres_init;         // ||r|| / ||b_lifted|| of the last solve's
                               // initial guess (warm start), -1 if cold
