@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -848,25 +849,33 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
   if (n > 0 && (!r || !z || !vr || !vt || !vz || !uid)) return PIC_EINVAL;
   const pic_config& c = h->cfgs[sim];
   SimHost& m = h->sims[sim];
-  uint64_t umax = 0;
-  for (int64_t p = 0; p < n; ++p) {
-    if (!(r[p] > c.r_in && r[p] < c.r_out && z[p] > c.z_min && z[p] < c.z_max)) return PIC_EINVAL;
-    if (!std::isfinite(vr[p]) || !std::isfinite(vt[p]) || !std::isfinite(vz[p]))
-      return PIC_ENONFINITE;
-    if (uid[p] >= 0xFFFFFFFFull) return PIC_EINVAL;
-    umax = std::max(umax, uid[p]);
-  }
-  h->sticky = 0;
-  // staging buffers for the FP64 host arrays
+  // staging buffers for the FP64 host arrays, filled while the host checks
+  // the arguments (nothing of the simulation changes before the checks
+  // pass)
   const size_t bytes = std::max<size_t>((size_t)n, 1) * sizeof(double);
-  double* d[5];
+  double* d[5] = {};
   uint64_t* du = nullptr;
+  auto release = [&]() {
+    for (int k = 0; k < 6; ++k) {
+      void* q = k < 5 ? (void*)d[k] : (void*)du;
+      if (!q) continue;
+      auto it = std::find(h->owned.begin(), h->owned.end(), q);
+      if (it != h->owned.end()) h->owned.erase(it);
+      h_free_one(q, h);
+    }
+  };
   for (int k = 0; k < 5; ++k) {
     d[k] = (double*)h_alloc(bytes, h);
-    if (!d[k]) return PIC_ENOMEM;
+    if (!d[k]) {
+      release();
+      return PIC_ENOMEM;
+    }
   }
   du = (uint64_t*)h_alloc(bytes, h);
-  if (!du) return PIC_ENOMEM;
+  if (!du) {
+    release();
+    return PIC_ENOMEM;
+  }
   const double* src[5] = {r, z, vr, vt, vz};
   int rc = PIC_OK;
   for (int k = 0; k < 5 && n > 0; ++k)
@@ -876,6 +885,50 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
   if (n > 0 && cudaMemcpyAsync(du, uid, (size_t)n * sizeof(uint64_t), cudaMemcpyHostToDevice,
                                h->stream) != cudaSuccess)
     rc = PIC_ECUDA;
+  // the checks, split over the host's cores: the code of the first failing
+  // particle (a position outside the gap or a uid of 2^32 - 1 or more:
+  // PIC_EINVAL; a non-finite velocity: PIC_ENONFINITE) and the largest uid
+  const int nth = (int)std::max<int64_t>(
+      1, std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), n / (1 << 18)));
+  std::vector<int64_t> bad(nth, n);
+  std::vector<int> code(nth, PIC_OK);
+  std::vector<uint64_t> umaxs(nth, 0);
+  auto check = [&](int t) {
+    const int64_t lo = n * t / nth, hi = n * (t + 1) / nth;
+    uint64_t um = 0;
+    for (int64_t p = lo; p < hi; ++p) {
+      int e = PIC_OK;
+      if (!(r[p] > c.r_in && r[p] < c.r_out && z[p] > c.z_min && z[p] < c.z_max)) e = PIC_EINVAL;
+      else if (!std::isfinite(vr[p]) || !std::isfinite(vt[p]) || !std::isfinite(vz[p]))
+        e = PIC_ENONFINITE;
+      else if (uid[p] >= 0xFFFFFFFFull) e = PIC_EINVAL;
+      if (e) {
+        bad[t] = p;
+        code[t] = e;
+        return;
+      }
+      um = std::max(um, uid[p]);
+    }
+    umaxs[t] = um;
+  };
+  if (nth == 1) {
+    check(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(check, t);
+    check(0);
+    for (auto& th : pool) th.join();
+  }
+  uint64_t umax = 0;
+  for (int t = 0; t < nth; ++t) {
+    if (code[t]) {   // the ranges are in slot order: the first one failing
+      cudaStreamSynchronize(h->stream);   // the staging copies end before the buffers go
+      release();
+      return code[t];
+    }
+    umax = std::max(umax, umaxs[t]);
+  }
+  h->sticky = 0;
   // a single simulation restarts from step 0 in buffer set 0; a simulation
   // of a batch is loaded into the current buffer set at the batch's step
   const bool batch = h->nsim > 1;
@@ -909,6 +962,18 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
                   cudaSuccess ||
               cudaMemsetAsync(h->T.phir + go, 0, gb * sizeof(float2), h->stream) != cudaSuccess))
     rc = PIC_ECUDA;
+  // a single simulation that sorts starts in cell order (the same
+  // particles, in the order the step's sort leaves: the first steps then
+  // run at the sorted store's speed instead of the load order's)
+  if (!rc && !batch && c.sort_every > 0 && n > 0) {
+    if (h->prec == 32)
+      launch_sort<float>(soa<float>(h, h->cur), soa<float>(h, h->cur ^ 1), h->st, h->cell_count,
+                         h->ncells, c.nz, h->grid_sort, h->stream);
+    else
+      launch_sort<double>(soa<double>(h, h->cur), soa<double>(h, h->cur ^ 1), h->st,
+                          h->cell_count, h->ncells, c.nz, h->grid_sort, h->stream);
+    h->cur ^= 1;
+  }
   if (!rc) {
     const double qw = -kQe * m.weight;
     if (h->prec == 32)

@@ -370,6 +370,60 @@ def test_invalid_inputs_rejected():
             sim.load_particles([5e-3], [0.0], [np.nan], [0.0], [0.0], np.array([0], dtype=np.uint64))
 
 
+def test_large_load_checks_report_the_first_failure():
+    """Loads of more than half a million particles check their arguments
+    on several host threads while the copies run: the code is the first
+    failing particle's in slot order, and a refused load leaves the
+    simulation as it was."""
+    from paper_2206_14662_gb300._capi import PIC_EINVAL, PIC_ENONFINITE, PicError, Simulation
+    cfg = workload("mirror_128x512_1e7", n_init=1_500_000, sort_every=20)
+    parts = [np.array(a, copy=True) for a in seed_particles(cfg)]
+    with Simulation(cfg) as sim:
+        sim.load_particles(*parts)
+        sim.step(3)
+        before = sim.diagnostics()
+        late, early = 1_400_000, 700_000
+        bad = [a.copy() for a in parts]
+        bad[3][late] = np.inf                       # non-finite velocity, late
+        with pytest.raises(PicError) as ei:
+            sim.load_particles(*bad)
+        assert ei.value.code == PIC_ENONFINITE
+        bad[0][early] = cfg["r_out"] * 2            # outside the gap, earlier
+        with pytest.raises(PicError) as ei:
+            sim.load_particles(*bad)
+        assert ei.value.code == PIC_EINVAL
+        bad = [a.copy() for a in parts]
+        bad[5][late + 1] = np.uint64(2**32 - 1)     # uid beyond the bound
+        with pytest.raises(PicError) as ei:
+            sim.load_particles(*bad)
+        assert ei.value.code == PIC_EINVAL
+        after = sim.diagnostics()
+        assert after["step"] == before["step"] and after["n_particles"] == before["n_particles"]
+        sim.step(2)
+        assert sim.diagnostics()["step"] == before["step"] + 2
+
+
+def test_loaded_store_is_in_cell_order():
+    """A single simulation that sorts starts from its load in cell order:
+    the same particles (bit for bit, by uid) as a load that does not sort,
+    and the same steps after it."""
+    from paper_2206_14662_gb300._capi import Simulation
+    base = dict(n_init=60_000, p_mbar=0.3, T0_eV=20.0)
+    out = []
+    for se in (10, 0):
+        cfg = workload("mirror_128x512_1e7", sort_every=se, **base)
+        parts = seed_particles(cfg)
+        with Simulation(cfg) as sim:
+            sim.load_particles(*parts)
+            g0 = by_uid(sim.export_particles())
+            sim.step(5)     # no sort in these steps for either
+            out.append((g0, by_uid(sim.export_particles())))
+    (a0, a5), (b0, b5) = out
+    for k in a0:
+        assert np.array_equal(a0[k], b0[k]), k
+        assert np.array_equal(a5[k], b5[k]), k
+
+
 def test_checkpoint_restore(tmp_path):
     """Stepping on after a restore reproduces the uninterrupted run (bitwise
     in a fixed field: the random streams depend on seed, uid and step)."""
