@@ -200,11 +200,14 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
  * deposits the charge and, unless fixed_efield, solves the field (Sec. II.A
  * seed load and first field; in a batch every simulation is solved again
  * from its last deposit, which leaves the others' fields as they were).  A
- * single simulation restarts at step 0; a simulation of a batch joins at the
- * batch's current step.  Synchronises (page-locked host arrays make the
- * copies faster).  PIC_EINVAL for out-of-domain positions, uids at or
- * above 2^32 - 1, or n above the simulation's capacity; PIC_ENONFINITE for
- * a non-finite velocity. */
+ * single simulation restarts at step 0 (with sort_every > 0 its store is
+ * put in cell order right away, as the step's sort would); a simulation of
+ * a batch joins at the batch's current step.  The arrays are copied while
+ * the host checks them on its cores; synchronises (page-locked host arrays
+ * make the copies faster).  PIC_EINVAL for out-of-domain positions, uids at
+ * or above 2^32 - 1, or n above the simulation's capacity; PIC_ENONFINITE
+ * for a non-finite velocity (the first failing particle's code); a refused
+ * load changes nothing. */
 int pic_load_particles(pic_handle* h, int sim, const double* r,
                        const double* z, const double* vr, const double* vt,
                        const double* vz, const uint64_t* uid, int64_t n);
