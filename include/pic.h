@@ -202,9 +202,9 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
  * from its last deposit, which leaves the others' fields as they were).  A
  * single simulation restarts at step 0 (with sort_every > 0 its store is
  * put in cell order right away, as the step's sort would); a simulation of
- * a batch joins at the batch's current step.  The arrays are copied while
- * the host checks them on its cores; synchronises (page-locked host arrays
- * make the copies faster).  PIC_EINVAL for out-of-domain positions, uids at
+ * a batch joins at the batch's current step.  The arrays are checked on the
+ * device after their copy; synchronises (page-locked host arrays make the
+ * copies faster).  PIC_EINVAL for out-of-domain positions, uids at
  * or above 2^32 - 1, or n above the simulation's capacity; PIC_ENONFINITE
  * for a non-finite velocity (the first failing particle's code); a refused
  * load changes nothing. */

@@ -21,7 +21,6 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
-#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -842,6 +841,41 @@ void pic_free(pic_handle* h) {
   delete h;
 }
 
+// The load's argument checks on the staged arrays: out[0] = min over the
+// failing particles of 8 p + code (a position outside the open gap or a
+// uid of 2^32 - 1 or more: PIC_EINVAL; a non-finite velocity, tested on
+// the exponent bits: PIC_ENONFINITE; the position test first), out[1] =
+// the largest uid.  out[0] starts at ~0, out[1] at 0.
+__global__ void k_load_check(const double* __restrict__ r, const double* __restrict__ z,
+                             const double* __restrict__ vr, const double* __restrict__ vt,
+                             const double* __restrict__ vz, const uint64_t* __restrict__ uid,
+                             long long n, double r_in, double r_out, double z_min, double z_max,
+                             unsigned long long* out) {
+  auto finite = [](double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7FF) != 0x7FF;
+  };
+  unsigned long long first = ~0ull, um = 0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double rp = r[p], zp = z[p];
+    int e = 0;
+    if (!(rp > r_in && rp < r_out && zp > z_min && zp < z_max)) e = PIC_EINVAL;
+    else if (!finite(vr[p]) || !finite(vt[p]) || !finite(vz[p])) e = PIC_ENONFINITE;
+    else if (uid[p] >= 0xFFFFFFFFull) e = PIC_EINVAL;
+    if (e) first = min(first, 8ull * (unsigned long long)p + (unsigned long long)(-e));
+    else um = max(um, (unsigned long long)uid[p]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+    um = max(um, __shfl_xor_sync(0xffffffffu, um, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (first != ~0ull) atomicMin(out, first);
+    if (um) atomicMax(out + 1, um);
+  }
+}
+
 int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
                        const double* vr, const double* vt, const double* vz,
                        const uint64_t* uid, int64_t n) {
@@ -849,9 +883,8 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
   if (n > 0 && (!r || !z || !vr || !vt || !vz || !uid)) return PIC_EINVAL;
   const pic_config& c = h->cfgs[sim];
   SimHost& m = h->sims[sim];
-  // staging buffers for the FP64 host arrays, filled while the host checks
-  // the arguments (nothing of the simulation changes before the checks
-  // pass)
+  // staging buffers for the FP64 host arrays (checked there, on the
+  // device, before anything of the simulation changes)
   const size_t bytes = std::max<size_t>((size_t)n, 1) * sizeof(double);
   double* d[5] = {};
   uint64_t* du = nullptr;
@@ -885,49 +918,30 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
   if (n > 0 && cudaMemcpyAsync(du, uid, (size_t)n * sizeof(uint64_t), cudaMemcpyHostToDevice,
                                h->stream) != cudaSuccess)
     rc = PIC_ECUDA;
-  // the checks, split over the host's cores: the code of the first failing
-  // particle (a position outside the gap or a uid of 2^32 - 1 or more:
-  // PIC_EINVAL; a non-finite velocity: PIC_ENONFINITE) and the largest uid
-  const int nth = (int)std::max<int64_t>(
-      1, std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), n / (1 << 18)));
-  std::vector<int64_t> bad(nth, n);
-  std::vector<int> code(nth, PIC_OK);
-  std::vector<uint64_t> umaxs(nth, 0);
-  auto check = [&](int t) {
-    const int64_t lo = n * t / nth, hi = n * (t + 1) / nth;
-    uint64_t um = 0;
-    for (int64_t p = lo; p < hi; ++p) {
-      int e = PIC_OK;
-      if (!(r[p] > c.r_in && r[p] < c.r_out && z[p] > c.z_min && z[p] < c.z_max)) e = PIC_EINVAL;
-      else if (!std::isfinite(vr[p]) || !std::isfinite(vt[p]) || !std::isfinite(vz[p]))
-        e = PIC_ENONFINITE;
-      else if (uid[p] >= 0xFFFFFFFFull) e = PIC_EINVAL;
-      if (e) {
-        bad[t] = p;
-        code[t] = e;
-        return;
-      }
-      um = std::max(um, uid[p]);
+  // the checks, on the staged arrays (nothing of the simulation has
+  // changed yet): the first failing particle's code and the largest uid
+  uint64_t chk[2] = {~0ull, 0ull};
+  if (!rc && n > 0) {
+    unsigned long long* out = (unsigned long long*)h->scratch2;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+    if (cudaMemsetAsync(out, 0xFF, sizeof(unsigned long long), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(out + 1, 0, sizeof(unsigned long long), h->stream) != cudaSuccess)
+      rc = PIC_ECUDA;
+    if (!rc) {
+      k_load_check<<<blocks, 256, 0, h->stream>>>(d[0], d[1], d[2], d[3], d[4], du, (long long)n,
+                                                  c.r_in, c.r_out, c.z_min, c.z_max, out);
+      if (cudaMemcpyAsync(chk, out, sizeof(chk), cudaMemcpyDeviceToHost, h->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        rc = PIC_ECUDA;
     }
-    umaxs[t] = um;
-  };
-  if (nth == 1) {
-    check(0);
-  } else {
-    std::vector<std::thread> pool;
-    for (int t = 1; t < nth; ++t) pool.emplace_back(check, t);
-    check(0);
-    for (auto& th : pool) th.join();
   }
-  uint64_t umax = 0;
-  for (int t = 0; t < nth; ++t) {
-    if (code[t]) {   // the ranges are in slot order: the first one failing
-      cudaStreamSynchronize(h->stream);   // the staging copies end before the buffers go
-      release();
-      return code[t];
-    }
-    umax = std::max(umax, umaxs[t]);
+  if (rc || chk[0] != ~0ull) {
+    cudaStreamSynchronize(h->stream);   // the staging copies end before the buffers go
+    release();
+    return rc ? rc : -(int)(chk[0] & 7);
   }
+  const uint64_t umax = chk[1];
   h->sticky = 0;
   // a single simulation restarts from step 0 in buffer set 0; a simulation
   // of a batch is loaded into the current buffer set at the batch's step

@@ -371,9 +371,9 @@ def test_invalid_inputs_rejected():
 
 
 def test_large_load_checks_report_the_first_failure():
-    """Loads of more than half a million particles check their arguments
-    on several host threads while the copies run: the code is the first
-    failing particle's in slot order, and a refused load leaves the
+    """A load's arguments are checked on the device after the copies: the
+    code is the first failing particle's in slot order (with failures of
+    both kinds far apart in a large load), and a refused load leaves the
     simulation as it was."""
     from paper_2206_14662_gb300._capi import PIC_EINVAL, PIC_ENONFINITE, PicError, Simulation
     cfg = workload("mirror_128x512_1e7", n_init=1_500_000, sort_every=20)
