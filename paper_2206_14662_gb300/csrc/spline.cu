@@ -387,25 +387,58 @@ __global__ void k_lift(const double* __restrict__ f, const double* __restrict__ 
   }
 }
 
-// C(m, n) = sum_k A(m, k) B(k, n) with element strides (FP64, 16 x 16 tiles)
-constexpr int kTile = 16;
-__global__ void k_gemm(int M, int N, int K, const double* __restrict__ A, long long sam,
-                       long long sak, const double* __restrict__ B, long long sbk, long long sbn,
-                       double* __restrict__ C, long long scm, long long scn) {
-  __shared__ double As[kTile][kTile + 1], Bs[kTile][kTile + 1];
+constexpr int kTile = 16;   // the transforms' square tiles
+
+// The transforms in double-float (FP32 pairs, ~2^-48 relative): C(m, n) =
+// sum_k A(m, k) B(k, n), FP64 in and out, with the constant operand (the
+// eigenvector matrix, V_IS_A: A, else B) stored as float2 (hi, lo) and the
+// other converted once per tile load.  On this part FP64 instructions take
+// ~16 SM cycles a warp, so the FP64 tile GEMM was bound by the FP64 pipe
+// (23 us a transform at 128 x 512); the double-float form runs on the FP32
+// pipes.  The sums are two-sum based (Knuth), the products Dekker's via
+// FMA.
+__device__ __forceinline__ float2 sdf_split(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+// (the rounded operations are spelled out so that no multiply and add are
+// contracted into one FMA, which would break the error-free steps)
+__device__ __forceinline__ float2 sdf_fma(float2 acc, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = __fadd_rn(acc.x, p);
+  const float v = __fsub_rn(s, acc.x);
+  const float t = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, v)), __fsub_rn(p, v));
+  const float lo = __fadd_rn(__fadd_rn(t, e), acc.y);
+  const float hi = __fadd_rn(s, lo);
+  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+}
+template <bool V_IS_A>
+__global__ void k_gemm_df(int M, int N, int K, const void* __restrict__ A, long long sam,
+                          long long sak, const void* __restrict__ B, long long sbk, long long sbn,
+                          double* __restrict__ C, long long scm, long long scn) {
+  __shared__ float2 As[kTile][kTile + 1], Bs[kTile][kTile + 1];
   const int tm = threadIdx.y, tn = threadIdx.x;
   const int m = blockIdx.y * kTile + tm, n = blockIdx.x * kTile + tn;
-  double acc = 0.0;
+  float2 acc = make_float2(0.f, 0.f);
   for (int k0 = 0; k0 < K; k0 += kTile) {
     const int ka = k0 + tn, kb = k0 + tm;
-    As[tm][tn] = (m < M && ka < K) ? A[m * sam + ka * sak] : 0.0;
-    Bs[tm][tn] = (kb < K && n < N) ? B[kb * sbk + n * sbn] : 0.0;
+    const bool oka = m < M && ka < K, okb = kb < K && n < N;
+    if (V_IS_A) {
+      As[tm][tn] = oka ? ((const float2*)A)[m * sam + ka * sak] : make_float2(0.f, 0.f);
+      Bs[tm][tn] = okb ? sdf_split(((const double*)B)[kb * sbk + n * sbn]) : make_float2(0.f, 0.f);
+    } else {
+      As[tm][tn] = oka ? sdf_split(((const double*)A)[m * sam + ka * sak]) : make_float2(0.f, 0.f);
+      Bs[tm][tn] = okb ? ((const float2*)B)[kb * sbk + n * sbn] : make_float2(0.f, 0.f);
+    }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kTile; ++k) acc = fma(As[tm][k], Bs[k][tn], acc);
+    for (int k = 0; k < kTile; ++k) acc = sdf_fma(acc, As[tm][k], Bs[k][tn]);
     __syncthreads();
   }
-  if (m < M && n < N) C[m * scm + n * scn] = acc;
+  if (m < M && n < N) C[m * scm + n * scn] = (double)acc.x + (double)acc.y;
 }
 
 // Per r-mode k, forward and back substitution with the band factor's two
@@ -612,7 +645,8 @@ static int band_solve(int n, const double* band, const double* gt, int mz, int m
 struct pic_spline {
   spl::Geo G;
   cudaStream_t stream;
-  double *V, *g_r, *m_z, *band, *gt, *work, *modes;
+  double *g_r, *m_z, *band, *gt, *work, *modes;
+  float2* Vdf;   // the eigenvector matrix as double-float (hi, lo)
 };
 
 extern "C" {
@@ -646,7 +680,8 @@ int pic_spline_eigen(const pic_config* cfg, int degree, double* V, double* lambd
 
 void pic_spline_free(pic_spline* s) {
   if (!s) return;
-  for (double* p : {s->V, s->g_r, s->m_z, s->band, s->gt, s->work, s->modes})
+  if (s->Vdf) cudaFree(s->Vdf);
+  for (double* p : {s->g_r, s->m_z, s->band, s->gt, s->work, s->modes})
     if (p) cudaFree(p);
   delete s;
 }
@@ -662,7 +697,13 @@ int pic_spline_create(const pic_config* cfg, int degree, void* cuda_stream, pic_
   s->G = spl::Geo{T.n, T.nr, T.nz, T.mr, T.mz, T.a, T.b, T.z0, T.hr, T.hz, T.v_in, T.dphiD};
   s->stream = (cudaStream_t)cuda_stream;
   const size_t cells = (size_t)T.mr * T.mz;
-  bool ok = cudaMalloc(&s->V, T.V.size() * sizeof(double)) == cudaSuccess &&
+  // V as double-float: hi = V rounded to FP32, lo = the remainder rounded
+  std::vector<float2> vdf(T.V.size());
+  for (size_t i = 0; i < T.V.size(); ++i) {
+    const float hi = (float)T.V[i];
+    vdf[i] = make_float2(hi, (float)(T.V[i] - (double)hi));
+  }
+  bool ok = cudaMalloc(&s->Vdf, T.V.size() * sizeof(float2)) == cudaSuccess &&
             cudaMalloc(&s->g_r, T.g_r.size() * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->m_z, T.m_z.size() * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->band, T.band.size() * sizeof(double)) == cudaSuccess &&
@@ -670,7 +711,7 @@ int pic_spline_create(const pic_config* cfg, int degree, void* cuda_stream, pic_
             cudaMalloc(&s->work, cells * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->modes, cells * sizeof(double)) == cudaSuccess;
   ok = ok &&
-       cudaMemcpy(s->V, T.V.data(), T.V.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(s->Vdf, vdf.data(), vdf.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(s->g_r, T.g_r.data(), T.g_r.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(s->m_z, T.m_z.data(), T.m_z.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(s->band, T.band.data(), T.band.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -694,14 +735,16 @@ int pic_spline_solve(pic_spline* s, const double* f, double* c, int dirichlet) {
                                             dirichlet, mr, mz, s->work);
   const dim3 tb(spl::kTile, spl::kTile);
   // modes[j][k] = sum_i F'[i][j] V[i][k]   (M = mz rows j, N = mr columns k)
-  spl::k_gemm<<<dim3((mr + spl::kTile - 1) / spl::kTile, (mz + spl::kTile - 1) / spl::kTile), tb,
-                0, s->stream>>>(mz, mr, mr, s->work, 1, mz, s->V, mr, 1, s->modes, mr, 1);
+  spl::k_gemm_df<false><<<dim3((mr + spl::kTile - 1) / spl::kTile, (mz + spl::kTile - 1) / spl::kTile),
+                          tb, 0, s->stream>>>(mz, mr, mr, s->work, 1, mz, s->Vdf, mr, 1, s->modes,
+                                              mr, 1);
   // the band sweeps use the lifted right-hand side's buffer (consumed by
   // the transform above) for their intermediate
   if (int rc = band_solve(G.n, s->band, s->gt, mz, mr, s->modes, s->work, s->stream)) return rc;
   // c[i][j] = sum_k V[i][k] modes[j][k]   (M = mr rows i, N = mz columns j)
-  spl::k_gemm<<<dim3((mz + spl::kTile - 1) / spl::kTile, (mr + spl::kTile - 1) / spl::kTile), tb,
-                0, s->stream>>>(mr, mz, mr, s->V, mr, 1, s->modes, 1, mr, c, mz, 1);
+  spl::k_gemm_df<true><<<dim3((mz + spl::kTile - 1) / spl::kTile, (mr + spl::kTile - 1) / spl::kTile),
+                         tb, 0, s->stream>>>(mr, mz, mr, s->Vdf, mr, 1, s->modes, 1, mr, c, mz,
+                                             1);
   return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
