@@ -392,29 +392,10 @@ constexpr int kTile = 16;   // the transforms' square tiles
 // The transforms in double-float (FP32 pairs, ~2^-48 relative): C(m, n) =
 // sum_k A(m, k) B(k, n), FP64 in and out, with the constant operand (the
 // eigenvector matrix, V_IS_A: A, else B) stored as float2 (hi, lo) and the
-// other converted once per tile load.  On this part FP64 instructions take
-// ~16 SM cycles a warp, so the FP64 tile GEMM was bound by the FP64 pipe
-// (23 us a transform at 128 x 512); the double-float form runs on the FP32
-// pipes.  The sums are two-sum based (Knuth), the products Dekker's via
-// FMA.
-__device__ __forceinline__ float2 sdf_split(double x) {
-  const float hi = __double2float_rn(x);
-  return make_float2(hi, __double2float_rn(x - (double)hi));
-}
-// (the rounded operations are spelled out so that no multiply and add are
-// contracted into one FMA, which would break the error-free steps)
-__device__ __forceinline__ float2 sdf_fma(float2 acc, float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  float e = fmaf(a.x, b.x, -p);
-  e = fmaf(a.x, b.y, e);
-  e = fmaf(a.y, b.x, e);
-  const float s = __fadd_rn(acc.x, p);
-  const float v = __fsub_rn(s, acc.x);
-  const float t = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, v)), __fsub_rn(p, v));
-  const float lo = __fadd_rn(__fadd_rn(t, e), acc.y);
-  const float hi = __fadd_rn(s, lo);
-  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
-}
+// other converted once per tile load (sdf_split, sdf_fma).  On this part
+// FP64 instructions take ~16 SM cycles a warp, so the FP64 tile GEMM was
+// bound by the FP64 pipe (23 us a transform at 128 x 512); the
+// double-float form runs on the FP32 pipes.
 template <bool V_IS_A>
 __global__ void k_gemm_df(int M, int N, int K, const void* __restrict__ A, long long sam,
                           long long sak, const void* __restrict__ B, long long sbk, long long sbn,
