@@ -45,7 +45,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     headers = [os.path.join(INCLUDE, "pic.h"), os.path.join(CSRC, "pic_internal.cuh"),
                os.path.join(CSRC, "unet_kernels.cuh"), os.path.join(CSRC, "unet_tc.cuh"),
                os.path.join(CSRC, "field_common.cuh"),
-               os.path.join(CSRC, "fluid.cuh")]
+               os.path.join(CSRC, "fluid.cuh"), os.path.join(CSRC, "dfloat.cuh")]
     nvcc = _nvcc()
     procs, objs = [], []
     for src in SOURCES:

@@ -30,6 +30,7 @@
 
 #include "pic.h"
 #include "pic_internal.cuh"
+#include "dfloat.cuh"
 
 namespace pic {
 namespace spl {
