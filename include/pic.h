@@ -572,9 +572,11 @@ int pic_spline_set_stream(pic_spline* s, void* cuda_stream);
 
 /* c = the Galerkin solution for the load f (DEVICE arrays of mr x mz
  * FP64; f is the charge term sum_p q w_p w(r_p) b_i(r_p) b_j(z_p), in C);
- * dirichlet = 0 solves with both walls at 0 V.  A direct FP64 solve: per
- * r-mode band solves between two dense transforms.  Asynchronous on the
- * solver's stream.  PIC_EINVAL if f and c are the same array. */
+ * dirichlet = 0 solves with both walls at 0 V.  A direct solve: per
+ * r-mode band solves (FP64, along z in segments) between two dense
+ * transforms in double-float (FP32 pairs, about 2^-48 relative).
+ * Asynchronous on the solver's stream.  PIC_EINVAL if f and c are the same
+ * array. */
 int pic_spline_solve(pic_spline* s, const double* f, double* c, int dirichlet);
 
 /* f += qw w(r_p) b_i(r_p) b_j(z_p) for n particles at (r_p, z_p) (DEVICE
