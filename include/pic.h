@@ -207,7 +207,8 @@ int pic_init(const pic_config* cfg, int n_sims, void* cuda_stream,
  * copies faster).  PIC_EINVAL for out-of-domain positions, uids at
  * or above 2^32 - 1, or n above the simulation's capacity; PIC_ENONFINITE
  * for a non-finite velocity (the first failing particle's code); a refused
- * load changes nothing. */
+ * load changes nothing.  The handle keeps the load's staging buffers (48 B
+ * per particle of its largest load) until pic_free. */
 int pic_load_particles(pic_handle* h, int sim, const double* r,
                        const double* z, const double* vr, const double* vt,
                        const double* vz, const uint64_t* uid, int64_t n);

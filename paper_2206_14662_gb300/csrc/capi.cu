@@ -98,6 +98,12 @@ struct pic_handle {
   double* phi;
   void* efield;
   double* scratch2;   // two doubles for reductions
+  // the load's staging buffers (five FP64 arrays and the uids), kept
+  // between loads and grown to the largest one: a load allocates nothing
+  // after the first (a fresh device allocation of a few hundred MB took
+  // 30-40 ms on the GPU machine, against 4.5 ms for the whole load)
+  void* stage[6] = {};
+  size_t stage_n = 0;
   FieldTables T;
 
   // host bookkeeping
@@ -885,30 +891,25 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
   SimHost& m = h->sims[sim];
   // staging buffers for the FP64 host arrays (checked there, on the
   // device, before anything of the simulation changes)
-  const size_t bytes = std::max<size_t>((size_t)n, 1) * sizeof(double);
-  double* d[5] = {};
-  uint64_t* du = nullptr;
-  auto release = [&]() {
-    for (int k = 0; k < 6; ++k) {
-      void* q = k < 5 ? (void*)d[k] : (void*)du;
+  const size_t want = std::max<size_t>((size_t)n, 1);
+  if (want > h->stage_n) {
+    for (void*& q : h->stage) {
       if (!q) continue;
       auto it = std::find(h->owned.begin(), h->owned.end(), q);
       if (it != h->owned.end()) h->owned.erase(it);
       h_free_one(q, h);
+      q = nullptr;
     }
-  };
-  for (int k = 0; k < 5; ++k) {
-    d[k] = (double*)h_alloc(bytes, h);
-    if (!d[k]) {
-      release();
-      return PIC_ENOMEM;
+    h->stage_n = 0;
+    for (void*& q : h->stage) {
+      q = h_alloc(want * sizeof(double), h);   // owned: freed with the handle
+      if (!q) return PIC_ENOMEM;
     }
+    h->stage_n = want;
   }
-  du = (uint64_t*)h_alloc(bytes, h);
-  if (!du) {
-    release();
-    return PIC_ENOMEM;
-  }
+  double* d[5];
+  for (int k = 0; k < 5; ++k) d[k] = (double*)h->stage[k];
+  uint64_t* du = (uint64_t*)h->stage[5];
   const double* src[5] = {r, z, vr, vt, vz};
   int rc = PIC_OK;
   for (int k = 0; k < 5 && n > 0; ++k)
@@ -937,8 +938,7 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
     }
   }
   if (rc || chk[0] != ~0ull) {
-    cudaStreamSynchronize(h->stream);   // the staging copies end before the buffers go
-    release();
+    cudaStreamSynchronize(h->stream);   // the staging copies end before the call returns
     return rc ? rc : -(int)(chk[0] & 7);
   }
   const uint64_t umax = chk[1];
@@ -1026,13 +1026,6 @@ int pic_load_particles(pic_handle* h, int sim, const double* r, const double* z,
     if (!rc && (h->spl || h->web)) rc = spline_refresh(h, true);
   } else {
     cudaStreamSynchronize(h->stream);
-  }
-  // release the staging buffers
-  for (int k = 0; k < 6; ++k) {
-    void* p = k < 5 ? (void*)d[k] : (void*)du;
-    auto it = std::find(h->owned.begin(), h->owned.end(), p);
-    if (it != h->owned.end()) h->owned.erase(it);
-    h_free_one(p, h);
   }
   m.last_diag_step = h->step;
   for (double& a : m.last_abs) a = 0.0;
